@@ -1,0 +1,122 @@
+"""Pins for the oracle's TEBD driver: exact state vectors, Krylov, conservation laws."""
+import numpy as np
+import pytest
+
+from oracle import bond, clock, exact, mps
+
+
+def run_finite(L, d, g, dt, steps, chi_max, scheme="plain", use_svd=False, **kw):
+    st = mps.product_state(L, d, 0, True)
+    half, full = mps.strang_gates(L, d, g, dt, True)
+    for _ in range(steps):
+        mps.tebd_step(st, half, full, use_svd=use_svd, scheme=scheme, chi_max=chi_max, **kw) \
+            if not use_svd else mps.tebd_step(st, half, full, use_svd=True, chi_max=chi_max)
+    return st
+
+
+@pytest.mark.parametrize("scheme", ["plain", "cbe"])
+def test_matches_trotterised_statevector(scheme):
+    # chi_max >= 3^(L/2): no truncation, so TEBD equals the Trotterised state vector
+    L, d, g, dt, steps = 8, 3, 1.5, 0.05, 6
+    st = run_finite(L, d, g, dt, steps, chi_max=81, scheme=scheme, dchi_min=100)
+    psi = exact.trotter_statevector(exact.product_vector(L, d), L, d, g, dt, steps)
+    v = mps.to_statevector(st)
+    assert abs(abs(np.vdot(v, psi)) - 1) < 1e-12
+    Z, X = clock.clock_operators(d)
+    for m in range(L):
+        zm = mps.expectation_1site(st, m, Z)
+        ze = exact.local_expectation(psi, L, d, m, Z)
+        assert abs(zm - ze) < 1e-12
+        xm = mps.expectation_1site(st, m, X + X.conj().T)
+        xe = exact.local_expectation(psi, L, d, m, X + X.conj().T)
+        assert abs(xm - xe) < 1e-12
+    assert st.eps_sum < 1e-16
+
+
+def test_matches_krylov_within_trotter_error():
+    # Strang splitting: the error of <Z> at fixed t shrinks as dt^2
+    L, d, g, t = 6, 3, 1.5, 0.4
+    Z, _ = clock.clock_operators(d)
+    psi_ex = exact.krylov_evolve(exact.product_vector(L, d), L, d, g, t)
+    errs = []
+    for dt in (0.1, 0.05):
+        st = run_finite(L, d, g, dt, int(round(t / dt)), chi_max=27)
+        errs.append(max(abs(mps.expectation_1site(st, m, Z)
+                            - exact.local_expectation(psi_ex, L, d, m, Z)) for m in range(L)))
+    assert errs[1] < 1e-3
+    assert 3.0 < errs[0] / errs[1] < 5.0  # second order
+
+
+def test_energy_and_charge_conjugation():
+    L, d, g, dt = 8, 3, 1.5, 0.025
+    Z, X = clock.clock_operators(d)
+    st = run_finite(L, d, g, dt, 40, chi_max=81)
+    psi = mps.to_statevector(st)
+    E = exact.energy(psi, L, d, g)
+    assert abs(E.imag) < 1e-12
+    # E(0) = -2 (L-1) for |0...0>; Strang conserves it up to O(dt^2)
+    assert abs(E.real - (-2 * (L - 1))) < 5e-3
+    # C: |k> -> |-k> leaves H and |0...0> invariant, so <Z> is real
+    for m in range(L):
+        assert abs(mps.expectation_1site(st, m, Z).imag) < 1e-12
+    # two-site energy from theta (Fig. 1c style) equals the state-vector energy
+    E2 = sum(mps.expectation_2site(st, m, clock.bond_hamiltonian(d, g, wl, wr))
+             for m, (wl, wr) in enumerate(clock.field_weights(L, True)))
+    assert abs(E2 - E) < 1e-11
+
+
+def test_qr_and_svd_tebd_agree_while_error_small():
+    # Sec. IV: the schemes agree closely while eps stays small
+    L, d, g, dt, steps = 10, 3, 1.5, 0.05, 8
+    q = run_finite(L, d, g, dt, steps, chi_max=16, scheme="cbe", dchi_min=100)
+    s = run_finite(L, d, g, dt, steps, chi_max=16, use_svd=True)
+    Z, _ = clock.clock_operators(d)
+    assert q.eps_sum < 1e-6
+    for m in range(L):
+        assert abs(mps.expectation_1site(q, m, Z) - mps.expectation_1site(s, m, Z)) < 1e-6
+
+
+def test_truncated_run_keeps_isometries():
+    L, d, g, dt = 10, 3, 1.5, 0.05
+    st = run_finite(L, d, g, dt, 10, chi_max=8)
+    for m in range(1, L):
+        # B~^n written by the last update of each bond is an exact right isometry
+        if m % 2 == 1:
+            assert mps.right_isometry_error(st.B[m]) < 1e-12
+    for x in st.Xi:
+        assert abs(np.linalg.norm(x) - 1) < 1e-13
+    assert st.eps_sum > 1e-8  # this run does truncate
+    assert max(st.bond_dims()) <= 8
+
+
+def test_uniform_cell_matches_finite_chain_centre():
+    # Lieb-Robinson: at short times the centre of a long open chain behaves like the
+    # infinite chain; pins the uniform cell's bond roles (Xi[0] / Xi[1]).
+    d, g, dt, steps = 3, 1.5, 0.05, 6
+    Z, _ = clock.clock_operators(d)
+    uni = mps.product_state(2, d, 0, finite=False)
+    half, full = mps.strang_gates(2, d, g, dt, False)
+    for _ in range(steps):
+        mps.tebd_step(uni, half, full, scheme="cbe", chi_max=64, dchi_min=100)
+    L = 24
+    fin = run_finite(L, d, g, dt, steps, chi_max=64, scheme="cbe", dchi_min=100)
+    for m in (0, 1):
+        zu = mps.expectation_1site(uni, m, Z)
+        zf = mps.expectation_1site(fin, L // 2 + m, Z)
+        assert abs(zu - zf) < 1e-7
+    # energy per bond at t = 0 is -2; uniform two-site energy stays near it
+    E = mps.expectation_2site(uni, 0, clock.bond_hamiltonian(d, g))
+    assert abs(E.real + 2) < 2e-2
+
+
+def test_uniform_isometric_form():
+    d, g, dt = 3, 2.0, 0.05
+    uni = mps.product_state(2, d, 0, finite=False)
+    half, full = mps.strang_gates(2, d, g, dt, False)
+    for _ in range(10):
+        mps.tebd_step(uni, half, full, scheme="cbe", chi_max=20, dchi_min=100)
+    # site B was last written as B~^n by the bond (A,B): exact right isometry
+    assert mps.right_isometry_error(uni.B[1]) < 1e-12
+    # norms seen from both sites agree (to the truncation level)
+    assert abs(mps.norm2_site(uni, 0) - 1) < 1e-8
+    assert abs(mps.norm2_site(uni, 1) - 1) < 1e-8
