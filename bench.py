@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Bond-update throughput of QR-based TEBD on B300 (one JSON line on stdout).
+
+Workload: one two-site update at chi = 1024, d = 5 (theta of shape (chi, d, d, chi),
+complex64, i.i.d. complex Gaussian with unit Frobenius norm, a random 25 x 25
+unitary gate, B^n a random right isometry, eta = chi, plain QR truncation),
+the single-gate benchmark of Sec. IV / Fig. 5. A step is one full update:
+gate, X = theta~ B^n^dag, Householder QR, Y^dag = theta~^dag Q, Householder QR
+(the LQ), B~^m = theta~' B~^n^dag, FP64 norms and eps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU: the update has no exchange step; N ranks run independent replicas
+(one process per GPU, NCCL only for the barrier and the max-over-ranks time).
+--impl reference times the complex128 CPU oracle on this host's cores.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "QR-TEBD bond updates/s & % TC roofline at χ=1024,d=5 c64; p99 step latency"
+UNIT = "bond updates/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
+TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate on B300
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_update(wl, chi):
+    from oracle import bond
+    th = wl["theta"].astype(np.complex128)
+    Bn = wl["Bn"].astype(np.complex128)
+    t0 = time.perf_counter()
+    bond.qr_update(None, None, Bn, wl["U"], chi_max=chi, theta=th)
+    return time.perf_counter() - t0
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    from paper_2212_09782_b300 import workloads as W
+    wl = W.bond_microbench(args.chi, args.d)
+    for _ in range(args.warmup):
+        cpu_oracle_update(wl, args.chi)
+    times = [cpu_oracle_update(wl, args.chi) for _ in range(args.steps)]
+    tot = sum(times)
+    v = args.steps / tot
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic", "p50_ms": 1e3 * statistics.median(times),
+        "p99_ms": 1e3 * float(np.percentile(times, 99)),
+        "config": {"workload": f"single QR-TEBD bond update chi={args.chi} d={args.d} eta=chi plain",
+                   "global_batch": 1, "parallelism": "none (host oracle)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} full bond updates (complex128 NumPy/LAPACK)"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2212_09782_b300 import lib as L
+    from paper_2212_09782_b300 import workloads as W
+
+    chi, d = args.chi, args.d
+    prec = L.PRECISIONS[args.precision]
+    wl = W.bond_microbench(chi, d, seed=W.BASE_SEED + 2 + rank)
+    cdt = torch.complex128 if prec == L.C128 else torch.complex64
+    th = torch.from_numpy(wl["theta"]).to(dtype=cdt, device="cuda")
+    bn = torch.from_numpy(wl["Bn"]).to(dtype=cdt, device="cuda")
+    gate = torch.from_numpy(wl["U"]).to("cuda")
+    tr = L.trunc_default(L.PLAIN, chi)
+    up = L.BondUpdater(prec, chi, d, chi, chi, tr, xi_kind=0, theta_given=True)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- warm-up
+    for _ in range(args.warmup):
+        up.run(gate, bn, theta=th)
+    L.stream_check()
+    barrier()
+
+    # ---- timed region (inputs live in HBM; theta = 210 MB > 126 MB L2)
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    L.profile_enable(True)
+    n0 = L.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    barrier()
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        up.run(gate, bn, theta=th)
+        ev[i][1].record(stream)
+    barrier()
+    launches = L.launch_count() - n0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = ev[0][0].elapsed_time(ev[-1][1])
+    prof = {f: L.profile_read(f) for f in (L.PROF_TC_GEMM, L.PROF_QR_PANEL, L.PROF_SIMT_GEMM,
+                                           L.PROF_PREP, L.PROF_GATE)}
+    L.profile_enable(False)
+    L.stream_check()
+    t_max = total_ms
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = ws * args.steps / (t_max / 1e3)
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        h_th = torch.from_numpy(wl["theta"]).to(cdt).pin_memory()
+        h_bn = torch.from_numpy(wl["Bn"]).to(cdt).pin_memory()
+        h_u = torch.from_numpy(wl["U"]).pin_memory()
+        o_bm = torch.empty(up.bm_out.shape, dtype=cdt).pin_memory()
+        o_xi = torch.empty(up.xi_out.shape, dtype=cdt).pin_memory()
+        o_bn = torch.empty(up.bn_out.shape, dtype=cdt).pin_memory()
+        o_st = torch.empty(4, dtype=torch.float64).pin_memory()
+        d_th, d_bn, d_u = torch.empty_like(th), torch.empty_like(bn), torch.empty_like(gate)
+
+        def e2e_step():
+            d_th.copy_(h_th, non_blocking=True)
+            d_bn.copy_(h_bn, non_blocking=True)
+            d_u.copy_(h_u, non_blocking=True)
+            up.run(d_u, d_bn, theta=d_th)
+            o_bm.copy_(up.bm_out, non_blocking=True)
+            o_xi.copy_(up.xi_out, non_blocking=True)
+            o_bn.copy_(up.bn_out, non_blocking=True)
+            o_st.copy_(up.stats, non_blocking=True)
+
+        for _ in range(args.warmup):
+            e2e_step()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        b.record(stream)
+        barrier()
+        e_ms = a.elapsed_time(b)
+        if dist is not None:
+            t = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        esz = lambda x: x.numel() * x.element_size()
+        e2e = {"value": ws * args.steps / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": esz(h_th) + esz(h_bn) + esz(h_u),
+               "d2h_bytes_per_step": esz(o_bm) + esz(o_xi) + esz(o_bn) + esz(o_st)}
+        L.stream_check()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    # ---- roofline of the dominant kernel (tcgen05 GEMM for the tensor-core precisions)
+    peaks, src = load_peaks()
+    fam_names = {L.PROF_TC_GEMM: "tc_gemm", L.PROF_QR_PANEL: "qr_panel",
+                 L.PROF_SIMT_GEMM: "simt_gemm", L.PROF_PREP: "tc_prep", L.PROF_GATE: "gate"}
+    breakdown = {fam_names[f]: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                 for f, v in prof.items()}
+    dom = max(prof, key=lambda f: prof[f][0])
+    roof = None
+    tc_ms, tc_n, tc_flops, _ = prof[L.PROF_TC_GEMM]
+    if tc_n > 0:
+        per_launch_s = tc_ms / 1e3 / tc_n
+        achieved = tc_flops / tc_n / per_launch_s / 1e12
+        peak = peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]) * TF32_PER_BF16
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_tc_gemm (3xTF32 complex GEMM)" if prec == L.C64_3XTF32 else "k_tc_gemm (TF32)",
+                "issued_frac": achieved * (3 if prec == L.C64_3XTF32 else 1) / peak,
+                "peak_source": f"{src} bf16 sustained x nominal TF32/BF16 ratio {TF32_PER_BF16:.3f}",
+                "algorithmic_flops_per_launch": tc_flops / tc_n,
+                "launch_ms": tc_ms / tc_n}
+    elif prof[L.PROF_SIMT_GEMM][1] > 0:
+        ms, n, fl, _ = prof[L.PROF_SIMT_GEMM]
+        achieved = fl / n / (ms / 1e3 / n) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s",
+                "frac": None, "traffic": None, "kernel": "k_gemm (CUDA-core complex GEMM)"}
+
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        t = cpu_oracle_update(wl, chi)
+        cpu = {"value": 1.0 / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"1 full bond update chi={chi} d={d} (complex128 NumPy/LAPACK)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"c128": "c128", "c64_3xtf32": "c64 (3xTF32 tensor cores, FP32 accum, FP64 norms)",
+                  "c64_tf32": "c64 (TF32 tensor cores)", "c64_fp32": "c64 (FP32 CUDA cores)"}[args.precision],
+        "data": "synthetic",
+        "p50_ms": statistics.median(step_ms), "p99_ms": float(np.percentile(step_ms, 99)),
+        "config": {"workload": f"single QR-TEBD bond update chi={chi} d={d} eta=chi plain "
+                               f"(theta given, Xi=1)", "global_batch": ws,
+                   "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (theta 210 MB)", "precision": args.precision},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "kernel_breakdown": breakdown, "dominant_family": fam_names[dom], "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", default="c64_3xtf32",
+                    choices=["c64_3xtf32", "c64_tf32", "c64_fp32", "c128"])
+    ap.add_argument("--chi", type=int, default=1024)
+    ap.add_argument("--d", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,249 @@
+/*
+ * qrtebd.h - C ABI of libqrtebd: the QR-based TEBD bond update on one B300 GPU.
+ *
+ * Method: Unfried, Hauschild, Pollmann, "Fast Time-Evolution of Matrix-Product
+ * States using the QR decomposition", arXiv:2212.09782.
+ *   - Sec. II, Fig. 2b steps (i)-(iii): the plain QR truncation.
+ *   - Sec. III, Fig. 3 steps (i)-(v): QR with controlled bond expansion (CBE).
+ *   - Sec. IV, Eqs. 2-3: the d-state clock model used as the workload.
+ *
+ * Conventions shared by every call:
+ *   - Complex numbers are interleaved (re, im): complex128 = 2 doubles,
+ *     complex64 = 2 floats. Every tensor is row-major, left index slowest.
+ *   - Site tensor B (chi_l, d, chi_r); bond matrix Xi (chi, chi); the two-site
+ *     block theta (chi_l, d, d, chi_r) is read as the (chi_l d) x (d chi_r)
+ *     matrix with row alpha*d + i and column j*chi_r + delta.
+ *   - A two-site gate U is a d^2 x d^2 complex128 matrix, row = output (i, j),
+ *     column = input (i', j'), combined index i*d + j (left site most significant).
+ *   - "device" pointers are CUDA device memory of the current device; "host"
+ *     pointers are ordinary host memory. The caller owns every pointer it passes;
+ *     the library never frees caller memory and keeps no pointer past the call.
+ *   - Streams are passed as void* (a cudaStream_t); NULL is the legacy default stream.
+ *   - Every call returns a status code (0 = OK, negative = error). No C++
+ *     exception crosses this boundary. qrtebd_last_error_message() describes the
+ *     most recent failure of the calling thread.
+ */
+#ifndef QRTEBD_H
+#define QRTEBD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define QRTEBD_OK 0
+#define QRTEBD_ERR_INVALID_ARG (-1)  /* bad size, eta > d*chi, NULL where required */
+#define QRTEBD_ERR_OOM (-2)          /* workspace too small or device allocation failed */
+#define QRTEBD_ERR_CUDA (-3)         /* a CUDA runtime call failed */
+#define QRTEBD_ERR_TIMEOUT (-4)      /* a kernel gave up a bounded wait */
+#define QRTEBD_ERR_NUMERIC (-5)      /* NaN/Inf met in a norm */
+#define QRTEBD_ERR_NOT_ADMITTED (-6) /* a request does not fit the memory budget */
+
+/* -------------------------------------------------------------- precision */
+/* Arithmetic of the bond update.
+ *   C128       complex128 tensors, FP64 arithmetic everywhere.
+ *   C64_3XTF32 complex64 tensors; the large contractions run on tcgen05 tensor
+ *              cores as three TF32 products (hi*hi + hi*lo + lo*hi) with FP32
+ *              accumulation; Householder norms and all reductions in FP64.
+ *   C64_TF32   as C64_3XTF32 with one TF32 product (about 1e-3 relative error).
+ *   C64_FP32   complex64 tensors, FP32 CUDA-core arithmetic (no tensor cores). */
+#define QRTEBD_C128 0
+#define QRTEBD_C64_3XTF32 1
+#define QRTEBD_C64_TF32 2
+#define QRTEBD_C64_FP32 3
+
+/* -------------------------------------------------------------- truncation */
+#define QRTEBD_PLAIN 0 /* Sec. II: eta fixed a priori, Xi~ = L (non-diagonal) */
+#define QRTEBD_CBE 1   /* Sec. III: expand to eta, cut on the Schmidt values of L */
+
+typedef struct qrtebd_trunc {
+  int scheme;       /* QRTEBD_PLAIN or QRTEBD_CBE */
+  int chi_max;      /* largest bond dimension kept (>= 1) */
+  int eta;          /* > 0: use this expansion dimension; 0: the policy below */
+  int dchi_min;     /* CBE: dchi = max(dchi_min, ceil(dchi_frac * chi_m)) (Fig. 4: 100) */
+  double dchi_frac; /* CBE: relative expansion per update (Sec. III: about 0.1) */
+  double svd_min;   /* CBE: drop Schmidt values below svd_min * ||S|| (Fig. 4: 1e-14) */
+  double tie_tol;   /* CBE: never cut inside a multiplet closer than tie_tol * S_1 */
+} qrtebd_trunc;
+/* eta policy (Sec. II last paragraph, Sec. III):
+ *   PLAIN: eta = min(chi_max, d chi_l, d chi_r); initial guess Y0 = B^n if
+ *          eta == chi_m, else the first eta rows of theta~.
+ *   CBE:   eta = min(chi_m + dchi, d chi_l, d chi_r); Y0 = first eta rows of theta~. */
+
+/* Fill *tr with the defaults above for the given scheme and chi_max. */
+int qrtebd_trunc_default(qrtebd_trunc* tr, int scheme, int chi_max);
+
+/* ------------------------------------------------------------- bond update */
+/* Inputs and outputs of one two-site update on the bond between sites m and
+ * n = m + 1 (Fig. 2b / Fig. 3). All tensor pointers are DEVICE pointers in the
+ * precision's storage type (complex128 for C128, complex64 otherwise), except
+ * `gate`, which is always a device complex128 d^2 x d^2 matrix. */
+typedef struct qrtebd_bond_io {
+  int precision;             /* QRTEBD_C128 / C64_3XTF32 / C64_TF32 / C64_FP32 */
+  int chi_l, d, chi_m, chi_r;
+  int xi_kind;               /* 0: Xi = identity (xi unused); 1: dense chi_l x chi_l;
+                                2: diagonal, xi holds chi_l complex entries */
+  const void* xi;            /* Xi^[m] on the bond left of site m */
+  const void* bm;            /* B^[m] (chi_l, d, chi_m); unused when theta != NULL */
+  const void* bn;            /* B^[n] (chi_m, d, chi_r); right isometry */
+  const void* theta;         /* optional theta' = B^m B^n (chi_l, d, d, chi_r): step (i)'s
+                                contraction is then skipped and bm is not read */
+  const void* gate;          /* U, device complex128 d^2 x d^2 */
+  void* bm_out;              /* B~^[m] (chi_l, d, chi_new); capacity chi_l*d*eta */
+  void* xi_out;              /* Xi~^[n] (chi_new, chi_new), ||Xi~||_F = 1; capacity eta*eta */
+  void* bn_out;              /* B~^[n] (chi_new, d, chi_r); capacity eta*d*chi_r */
+  double* stats_out;         /* optional device double[4]: eps, ||theta~||^2, kept norm^2,
+                                chi_new. eps = ||theta~ - approx||^2 / ||theta~||^2 */
+  double* schmidt_out;       /* optional device double[eta]: CBE Schmidt values S (descending,
+                                unnormalised, all eta of them); ignored for PLAIN */
+  void* workspace;           /* device scratch of at least qrtebd_bond_workspace_size bytes */
+  size_t workspace_bytes;
+} qrtebd_bond_io;
+
+typedef struct qrtebd_bond_info {
+  int eta;     /* expansion dimension used */
+  int chi_new; /* new bond dimension chi~ (= eta for PLAIN) */
+} qrtebd_bond_info;
+
+/* Bytes of device workspace qrtebd_bond_update needs for these sizes (host call,
+ * no GPU work). `xi_kind` as in qrtebd_bond_io; `theta_given` != 0 when the
+ * caller supplies theta'. */
+int qrtebd_bond_workspace_size(int precision, int chi_l, int d, int chi_m, int chi_r,
+                               int xi_kind, int theta_given, const qrtebd_trunc* tr,
+                               size_t* bytes);
+
+/* One QR-TEBD bond update (Sec. II steps (i)-(iii); Sec. III steps (i)-(v) for CBE):
+ *   theta' = B^m B^n (unless given); theta~' = U theta'; theta~ = Xi theta~';
+ *   X = theta~ Y0^dag; Q R = X (Householder); Y = Q^dag theta~; L Q^[n] = Y (LQ);
+ *   PLAIN: Xi~ = L / ||L||, B~^n = Q^[n];
+ *   CBE:   L^dag L = V^dag S^2 V, keep chi~ values, B~^n = P V Q^[n], Xi~ = P S P / ||.||;
+ *   B~^m = theta~' B~^n^dag (Hastings form, Sec. II).
+ * Enqueued on `stream`. For PLAIN the call returns without synchronising; for
+ * CBE it synchronises `stream` once to read chi~. Errors: INVALID_ARG for bad
+ * sizes or eta > min(d chi_l, d chi_r) or eta > chi_m*... (see trunc), OOM if the
+ * workspace is too small, CUDA on a launch failure, TIMEOUT if a kernel gave up a
+ * bounded wait (reported at the next synchronising call). */
+int qrtebd_bond_update(const qrtebd_bond_io* io, const qrtebd_trunc* tr, void* stream,
+                       qrtebd_bond_info* info);
+
+/* Synchronise `stream` and report any device-side error word (TIMEOUT / NUMERIC)
+ * set by kernels since the last check. */
+int qrtebd_stream_check(void* stream);
+
+/* ------------------------------------------------------------------ MPS state */
+/* A matrix-product state in the right-isometric form of Sec. II (Eq. 1, Fig. 1):
+ * site tensors B[m] (chi_m, d, chi_{m+1}) and bond matrices Xi[m] on the bond left
+ * of site m, all resident in library-owned device memory.
+ *   finite (infinite = 0): L sites, bonds 0..L, Xi[0] = Xi[L] = [[1]]; the gate on
+ *     bond (m, m+1) reads Xi[m] and writes Xi[m+1] (Sec. II, finite systems).
+ *   uniform (infinite = 1): unit cell of L sites (L even, >= 2), bonds 0..L-1 with
+ *     wrap-around; the gate on (m, m+1 mod L) reads Xi[m], writes Xi[m+1 mod L].
+ * Layers (Fig. 2a): parity 0 acts on the bonds (m, m+1) with m even, parity 1 on
+ * m odd. A handle is bound to one stream and one device; it is not thread-safe. */
+typedef struct qrtebd_mps qrtebd_mps;
+
+typedef struct qrtebd_mps_desc {
+  int L;                        /* sites (finite) or unit-cell length (uniform) */
+  int d;                        /* local dimension, 2 <= d <= 8 */
+  int infinite;                 /* 0 finite open chain, 1 uniform MPS */
+  int chi_max;                  /* largest bond dimension the state may reach */
+  int precision;                /* QRTEBD_C128 / C64_* as for qrtebd_bond_update */
+  const double* product_state;  /* host complex128 L x d amplitudes (normalised per site),
+                                   or NULL for |0 ... 0> (the Z = 1 state of Sec. IV) */
+} qrtebd_mps_desc;
+
+/* Allocate the state (device memory sized for chi_max on every bond, plus one
+ * bond-update workspace) and initialise the product state: chi = 1 everywhere,
+ * Xi = [[1]]. stream: cudaStream_t the handle uses for all its work.
+ * Errors: INVALID_ARG (bad sizes, NULL out), OOM (device allocation failed). */
+int qrtebd_mps_create(const qrtebd_mps_desc* desc, void* stream, qrtebd_mps** out);
+/* Free all device memory of the state (synchronises its stream). NULL is a no-op. */
+int qrtebd_mps_destroy(qrtebd_mps* mps);
+/* Apply the two-site gates of one layer with the QR update (Sec. II / Sec. III).
+ * gates_host: host complex128 array of nbonds x d^4 values, gate b acting on
+ * (b, b+1) in the qrtebd.h gate layout; nbonds = L-1 (finite) or L (uniform); only
+ * the bonds of `parity` are read and copied. tr: truncation for every bond.
+ * eps_out: optional host array of nbonds doubles receiving each updated bond's eps
+ * (others untouched); passing it synchronises the stream. Bonds of one layer are
+ * independent (Fig. 2a) and are updated in sequence on the handle's stream. */
+int qrtebd_apply_gate_layer(qrtebd_mps* mps, int parity, const double* gates_host,
+                            const qrtebd_trunc* tr, double* eps_out);
+/* <O> at `site` (nsites = 1: op is d x d, Fig. 1c: tr[(Xi B)^dag O (Xi B)]) or on
+ * (site, site+1) (nsites = 2: op is d^2 x d^2 in the gate layout, evaluated on
+ * theta = Xi B^m B^n). op_host: host complex128. out: host double[2] (re, im).
+ * Synchronises the stream. Accumulation in FP64. */
+int qrtebd_expectation(qrtebd_mps* mps, int site, int nsites, const double* op_host,
+                       double* out);
+/* Truncation error eps accumulated on `bond` (the bond between sites bond-1 and
+ * bond; for a uniform cell, index mod L) since creation, or summed over all bonds
+ * when bond = -1. Synchronises. */
+int qrtebd_truncation_error(qrtebd_mps* mps, int bond, double* out);
+/* Schmidt values of bond `bond` (singular values of Xi, descending, normalised
+ * to unit 2-norm) into host S (capacity entries); *n receives the bond dimension.
+ * Synchronises. INVALID_ARG if capacity is too small. */
+int qrtebd_schmidt(qrtebd_mps* mps, int bond, double* S, int capacity, int* n);
+/* Current bond dimensions (finite: L+1 values, uniform: L values) into dims. */
+int qrtebd_bond_dims(qrtebd_mps* mps, int* dims, int capacity, int* n);
+/* Wait for all work on the handle's stream; reports device-side errors. */
+int qrtebd_sync(qrtebd_mps* mps);
+/* Checkpoint: write / read the whole state (tensors, bond dimensions, accumulated
+ * eps) as a raw host dump. Loading with the same kernels reproduces the run bit
+ * for bit. */
+int qrtebd_mps_save(qrtebd_mps* mps, const char* path);
+int qrtebd_mps_load(const char* path, void* stream, qrtebd_mps** out);
+
+/* -------------------------------------------------------------- complex GEMM */
+/* C = alpha opA opB + beta C on device pointers, the contraction every step of
+ * Sec. II is built from. opA(i, k) = A[i*sam + k*sak] (conjugated if conj_a),
+ * opB(k, j) = B[k*sbk + j*sbn] (conjugated if conj_b), C(i, j) = C[i*scm + j*scn];
+ * strides in complex elements, so transposes are stride choices. alpha, beta:
+ * host complex128 (2 doubles each). precision as above: C128 / C64_FP32 run on
+ * CUDA cores; C64_3XTF32 / C64_TF32 on tcgen05 tensor cores and need `workspace`
+ * of qrtebd_zgemm_workspace_size(m, n, k) bytes (device; NULL/0 allowed for the
+ * CUDA-core precisions). Enqueued on `stream`, no synchronisation. */
+int qrtebd_zgemm(int precision, int m, int n, int k, const void* A, long long sam, long long sak,
+                 int conj_a, const void* B, long long sbk, long long sbn, int conj_b, void* C,
+                 long long scm, long long scn, const double* alpha, const double* beta,
+                 void* workspace, size_t workspace_bytes, void* stream);
+size_t qrtebd_zgemm_workspace_size(int m, int n, int k);
+
+/* ------------------------------------------------------------- clock model */
+/* Host-only: the clock-model bond gate U = exp(-i tau h_b) (Sec. IV, Eqs. 2-3) with
+ * h_b = -(Z x Z^dag + Z^dag x Z) - g (wl (X + X^dag) x 1 + wr 1 x (X + X^dag)),
+ * tau = tau_re + i tau_im. U_out: host complex128 d^2 x d^2. wl = wr = 1/2 except
+ * at the outer site of a finite chain's end bonds (wl or wr = 1). */
+int qrtebd_clock_bond_gate(int d, double g, double wl, double wr, double tau_re, double tau_im,
+                           double* U_out);
+
+/* ------------------------------------------------------------ instrumentation */
+/* Kernel families timed by qrtebd_profile_read. */
+#define QRTEBD_PROF_TC_GEMM 0   /* tcgen05 complex GEMM kernel */
+#define QRTEBD_PROF_QR_PANEL 1  /* cluster Householder panel kernel */
+#define QRTEBD_PROF_SIMT_GEMM 2 /* CUDA-core complex GEMM kernel */
+#define QRTEBD_PROF_PREP 3      /* tensor-core operand preparation (split / embed) */
+#define QRTEBD_PROF_GATE 4      /* two-site gate application */
+/* Number of kernels the library has launched since it was loaded (host counter). */
+long long qrtebd_launch_count(void);
+/* on != 0: record a CUDA event pair around every launch of the families above, on
+ * the launching stream, from now on (earlier records are discarded); on == 0: stop. */
+int qrtebd_profile_enable(int on);
+/* Synchronise the recorded events of `family` and report their summed duration
+ * (ms), number of launches, algorithmic flops and algorithmic bytes (any output
+ * pointer may be NULL). */
+int qrtebd_profile_read(int family, double* total_ms, long long* launches, double* flops,
+                        double* bytes);
+
+/* --------------------------------------------------------------- utilities */
+const char* qrtebd_strerror(int status);
+const char* qrtebd_last_error_message(void);
+/* Library version string. */
+const char* qrtebd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QRTEBD_H */

@@ -1,0 +1,470 @@
+// One QR-TEBD bond update on the device; see bond.cuh and qrtebd.h.
+//
+// Step order (Sec. II, Fig. 2b; Sec. III, Fig. 3):
+//   (i)   theta' = B^m B^n (skipped when theta' is given), theta~' = U theta',
+//         theta~ = Xi theta~', Y0 per the eta policy, X = theta~ Y0^dag, QR(X) -> Q
+//   (ii)  Z = Y^dag = theta~^dag Q, QR(Z) -> Qz, Rz  (LQ of Y: L = Rz^dag, Q^[n] = Qz^dag)
+//   (iv)  CBE only: L^dag L = Rz Rz^dag = V^dag S^2 V (Jacobi, FP64), cut to chi~
+//   (iii/v) B~^n = Q^[n] (PLAIN) or P V Q^[n] (CBE); Xi~ = L or diag(S) normalised;
+//         B~^m = theta~' B~^n^dag (Hastings form)
+//   eps   = 1 - kept / ||theta~||^2 with both norms accumulated in FP64; for
+//         orthogonal projectors this equals ||theta~ - approx||^2 / ||theta~||^2.
+#include "bond.cuh"
+#include "tc_gemm.cuh"
+
+namespace qrtebd {
+
+namespace {
+
+constexpr int RED_BLOCKS = 592;  // 4 x 148 SMs
+
+// ------------------------------------------------------------------ gate
+// theta~'[a, i, j, b] = sum_{k,l} U[(i j), (k l)] theta'[a, k, l, b]; one thread
+// per (a, b), the d^2 inputs in registers, U in shared memory. Optionally also
+// writes theta~ = diag(xi) theta~' (Xi diagonal).
+template <typename T, int D>
+__global__ void k_gate(const cx<T>* __restrict__ th, cx<T>* __restrict__ out,
+                       const double2* __restrict__ U, int chiL, int chiR,
+                       const cx<T>* __restrict__ xi_diag, cx<T>* __restrict__ out_xi) {
+  constexpr int D2 = D * D;
+  __shared__ cx<T> Us[D2 * D2];
+  for (int t = threadIdx.x; t < D2 * D2; t += blockDim.x) {
+    double2 u = U[t];
+    Us[t] = mk<T>((T)u.x, (T)u.y);
+  }
+  __syncthreads();
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)chiL * chiR) return;
+  long long a = idx / chiR, b = idx % chiR;
+  long long base = a * D2 * chiR + b;
+  cx<T> in[D2];
+#pragma unroll
+  for (int q = 0; q < D2; ++q) in[q] = th[base + (long long)q * chiR];
+  cx<T> xa = xi_diag ? xi_diag[a] : mk<T>(1, 0);
+#pragma unroll
+  for (int o = 0; o < D2; ++o) {
+    cx<T> acc = mk<T>(0, 0);
+#pragma unroll
+    for (int q = 0; q < D2; ++q) cfma<T>(acc, Us[o * D2 + q], in[q]);
+    out[base + (long long)o * chiR] = acc;
+    if (out_xi) out_xi[base + (long long)o * chiR] = cmul<T>(xa, acc);
+  }
+}
+
+template <typename T>
+__global__ void k_convert_gate(const double2* U, cx<T>* Ut, int n) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) Ut[t] = mk<T>((T)U[t].x, (T)U[t].y);
+}
+
+template <typename T>
+__global__ void k_scale_rows(const cx<T>* in, cx<T>* out, const cx<T>* xi, long long rows,
+                             long long rowlen) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= rows * rowlen) return;
+  out[idx] = cmul<T>(xi[idx / rowlen], in[idx]);
+}
+
+// ------------------------------------------------------------------ norms
+template <typename T>
+__global__ void k_norm2_partial(const cx<T>* __restrict__ x, long long n, double* partial) {
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    cx<T> v = x[i];
+    s += (double)v.x * v.x + (double)v.y * v.y;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  __shared__ double ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// Deterministic final sum (fixed order) into *out.
+__global__ void k_sum_partials(const double* partial, int n, double* out) {
+  __shared__ double ws[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    *out = t;
+  }
+}
+
+// stats = {eps, ||theta~||^2, kept, chi_new}; scal[0] = 1/sqrt(kept)
+__global__ void k_finalize(const double* th2, const double* kept, double chi_new, double* stats,
+                           double* scal, unsigned* err) {
+  double t = *th2, k = *kept;
+  double eps = t > 0 ? 1.0 - k / t : 0.0;
+  if (eps < 0) eps = 0;
+  if (!isfinite(t) || !isfinite(k)) atomicOr(err, DEVERR_NUMERIC);
+  if (stats) { stats[0] = eps; stats[1] = t; stats[2] = k; stats[3] = chi_new; }
+  scal[0] = k > 0 ? 1.0 / sqrt(k) : 0.0;
+}
+
+// out[j][i] = s * conj(in[i][j]) for i < rows, j < cols (in: ld_in, out: ld_out)
+template <typename T>
+__global__ void k_conj_transpose(const cx<T>* in, long long ld_in, cx<T>* out, long long ld_out,
+                                 int rows, int cols, const double* scale) {
+  __shared__ cx<T> tile[32][33];
+  int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  T s = scale ? (T)scale[0] : T(1);
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int i = i0 + r, j = j0 + threadIdx.x;
+    if (i < rows && j < cols) tile[r][threadIdx.x] = in[i * ld_in + j];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int j = j0 + r, i = i0 + threadIdx.x;
+    if (i < rows && j < cols) {
+      cx<T> v = tile[threadIdx.x][r];
+      out[j * ld_out + i] = mk<T>(s * v.x, -s * v.y);
+    }
+  }
+}
+
+template <typename T>
+int conj_transpose(const cx<T>* in, long long ld_in, cx<T>* out, long long ld_out, int rows,
+                   int cols, const double* scale, cudaStream_t st) {
+  dim3 grid((unsigned)ceil_div(cols, 32), (unsigned)ceil_div(rows, 32));
+  k_conj_transpose<T><<<grid, dim3(32, 8), 0, st>>>(in, ld_in, out, ld_out, rows, cols, scale);
+  note_launch();
+  QR_CUDA_TRY(cudaGetLastError());
+  return QRTEBD_OK;
+}
+
+template <typename T>
+int norm2(const cx<T>* x, long long n, double* partial, double* out, cudaStream_t st) {
+  k_norm2_partial<T><<<RED_BLOCKS, 256, 0, st>>>(x, n, partial);
+  note_launch();
+  QR_CUDA_TRY(cudaGetLastError());
+  k_sum_partials<<<1, 256, 0, st>>>(partial, RED_BLOCKS, out);
+  note_launch();
+  QR_CUDA_TRY(cudaGetLastError());
+  return QRTEBD_OK;
+}
+
+template <typename T>
+int launch_gate(const cx<T>* th, cx<T>* out, const double2* U, int chiL, int d, int chiR,
+                const cx<T>* xi_diag, cx<T>* out_xi, cudaStream_t st) {
+  long long n = (long long)chiL * chiR;
+  unsigned grid = (unsigned)ceil_div(n, 128);
+  ProfScope prof(PROF_GATE, st, 8.0 * n * d * d * d * d,
+                 (double)sizeof(cx<T>) * n * d * d * (out_xi ? 3 : 2));
+  switch (d) {
+#define QR_GATE_CASE(DD) \
+    case DD: k_gate<T, DD><<<grid, 128, 0, st>>>(th, out, U, chiL, chiR, xi_diag, out_xi); note_launch(); break;
+    QR_GATE_CASE(2) QR_GATE_CASE(3) QR_GATE_CASE(4) QR_GATE_CASE(5)
+#undef QR_GATE_CASE
+    default: return QRTEBD_ERR_INVALID_ARG;
+  }
+  QR_CUDA_TRY(cudaGetLastError());
+  return QRTEBD_OK;
+}
+
+// ------------------------------------------------------------------ CBE cut
+// Reads w (descending eigenvalues of L^dag L), writes S = sqrt(max(w, 0)),
+// decides chi~ (Fig. 4 caption: drop S / ||S|| < svd_min, keep <= chi_max, never
+// split a multiplet closer than tie_tol * S_1), kept = sum_{k < chi~} S_k^2.
+__global__ void k_cbe_cut(const double* w, int n, int chi_max, double svd_min, double tie_tol,
+                          double* S, double* kept, int* chi_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double tot = 0;
+  for (int k = 0; k < n; ++k) { double s = w[k] > 0 ? sqrt(w[k]) : 0.0; S[k] = s; tot += s * s; }
+  double nrm = sqrt(tot);
+  int c = 0;
+  if (nrm > 0) { for (int k = 0; k < n; ++k) if (S[k] / nrm >= svd_min) ++c; }
+  if (c > chi_max) c = chi_max;
+  if (c < 1) c = 1;
+  if (nrm > 0) {
+    while (c < n && c > 1 && (S[c - 1] - S[c]) / nrm <= tie_tol * (S[0] / nrm)) --c;
+  }
+  double kk = 0;
+  for (int k = 0; k < c; ++k) kk += S[k] * S[k];
+  *kept = kk;
+  *chi_out = c;
+}
+
+// Xi~ = diag(S[0:c]) / sqrt(kept), dense c x c
+template <typename T>
+__global__ void k_diag_xi(const double* S, int c, const double* scal, cx<T>* xi) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)c * c) return;
+  int i = (int)(idx / c), j = (int)(idx % c);
+  xi[idx] = mk<T>(i == j ? (T)(S[i] * scal[0]) : T(0), 0);
+}
+
+template <typename T> __global__ void k_to_c128(const cx<T>* in, double2* out, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_double2((double)in[i].x, (double)in[i].y);
+}
+template <typename T> __global__ void k_from_c128(const double2* in, cx<T>* out, long long n) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = mk<T>((T)in[i].x, (T)in[i].y);
+}
+
+// ------------------------------------------------------------------ driver
+template <typename T>
+struct GemmRunner {
+  // Routes a GEMM either to CUDA cores or (complex64 tensor-core precisions) to tcgen05.
+  int precision;
+  TcWorkspace* tc;
+  cx<T>* simt_scratch;
+  size_t simt_scratch_elems;
+  int run(const GemmArgs<T>& g, cudaStream_t st) const;
+};
+
+template <>
+int GemmRunner<double>::run(const GemmArgs<double>& g, cudaStream_t st) const {
+  return gemm_simt<double>(g, st, simt_scratch, simt_scratch_elems);
+}
+template <>
+int GemmRunner<float>::run(const GemmArgs<float>& g, cudaStream_t st) const {
+  if ((precision == QRTEBD_C64_3XTF32 || precision == QRTEBD_C64_TF32) && tc &&
+      tc_gemm_eligible(g)) {
+    return tc_gemm(g, precision == QRTEBD_C64_3XTF32, *tc, st);
+  }
+  return gemm_simt<float>(g, st, simt_scratch, simt_scratch_elems);
+}
+
+template <typename T> int qr_gemm_thunk(const GemmArgs<T>& g, cudaStream_t st, void* ctx) {
+  return static_cast<const GemmRunner<T>*>(ctx)->run(g, st);
+}
+
+template <typename T>
+int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t st,
+                  qrtebd_bond_info* info, size_t* bytes) {
+  const int chiL = io->chi_l, d = io->d, chiM = io->chi_m, chiR = io->chi_r;
+  const bool measuring = (bytes != nullptr);
+  const long long mL = (long long)chiL * d, nR = (long long)d * chiR;
+  const int eta = choose_eta(tr, chiL, d, chiM, chiR);
+  if (eta < 1) { set_last_message("bond_update: eta out of range"); return QRTEBD_ERR_INVALID_ARG; }
+  const bool cbe = (tr->scheme == QRTEBD_CBE);
+  const bool theta_given = (io->theta != nullptr) || (measuring && io->bm == nullptr);
+  const bool y0_is_bn = (!cbe && eta == chiM);
+  const bool use_tc = std::is_same<T, float>::value &&
+                      (io->precision == QRTEBD_C64_3XTF32 || io->precision == QRTEBD_C64_TF32);
+
+  Arena ar;
+  ar.measuring = measuring;
+  if (!measuring) { ar.base = static_cast<char*>(io->workspace); ar.cap = io->workspace_bytes; }
+
+  cx<T>* theta_p = theta_given ? nullptr : ar.take<cx<T>>((size_t)mL * nR);
+  cx<T>* theta_tp = ar.take<cx<T>>((size_t)mL * nR);
+  cx<T>* theta_t = (io->xi_kind == 0) ? theta_tp : ar.take<cx<T>>((size_t)mL * nR);
+  cx<T>* X = ar.take<cx<T>>((size_t)mL * eta);
+  cx<T>* Q = ar.take<cx<T>>((size_t)mL * eta);
+  cx<T>* Z = ar.take<cx<T>>((size_t)nR * eta);
+  cx<T>* Qz = ar.take<cx<T>>((size_t)nR * eta);
+  cx<T>* Ut = (d > 5) ? ar.take<cx<T>>((size_t)d * d * d * d) : nullptr;
+  QrScratch<T> qs;
+  qr_carve<T>(ar, (int)std::max(mL, nR), eta, qs);
+  double* partial = ar.take<double>(RED_BLOCKS);
+  double* scal = ar.take<double>(8);  // th2, kept, inv sqrt(kept)
+  double* stats_local = ar.take<double>(4);
+  size_t simt_elems = std::max(gemm_simt_scratch_elems((int)mL, eta, (int)nR, 1),
+                               gemm_simt_scratch_elems((int)nR, eta, (int)mL, 1));
+  simt_elems = std::max(simt_elems, gemm_simt_scratch_elems(chiL, (int)(d * nR), chiL, 1));
+  cx<T>* simt_scratch = simt_elems ? ar.take<cx<T>>(simt_elems) : nullptr;
+  // CBE: eigen-decomposition buffers (FP64)
+  double2* M = nullptr; double2* Vh = nullptr; double* w = nullptr; double2* eig_scr = nullptr;
+  double* Sv = nullptr; cx<T>* Vt = nullptr; cx<T>* Bn_full = nullptr; int* chi_dev = nullptr;
+  size_t eig_elems = 0;
+  if (cbe) {
+    M = ar.take<double2>((size_t)eta * eta);
+    Vh = ar.take<double2>((size_t)eta * eta);
+    w = ar.take<double>(eta);
+    Sv = ar.take<double>(eta);
+    eig_elems = herm_eig_scratch_elems(eta);
+    eig_scr = ar.take<double2>(eig_elems);
+    Vt = ar.take<cx<T>>((size_t)eta * eta);
+    Bn_full = ar.take<cx<T>>((size_t)eta * nR);
+    chi_dev = ar.take<int>(4);
+  }
+  TcWorkspace tcw;
+  if (use_tc) tc_carve(ar, (int)std::max(mL, nR), (int)std::max(mL, nR), eta, tcw);
+
+  if (measuring) { *bytes = ar.off; return QRTEBD_OK; }
+  if (ar.overflow()) {
+    set_last_message("bond_update: workspace too small");
+    return QRTEBD_ERR_OOM;
+  }
+  unsigned* err = device_error_word();
+  GemmRunner<T> runner{io->precision, use_tc ? &tcw : nullptr, simt_scratch, simt_elems};
+  QrGemm<T> qg{qr_gemm_thunk<T>, &runner};
+  const cx<T> one = mk<T>(1, 0), zero = mk<T>(0, 0);
+
+  // (i) theta' = B^m B^n
+  const cx<T>* th = static_cast<const cx<T>*>(io->theta);
+  if (!theta_given) {
+    GemmArgs<T> g{(int)mL, (int)nR, chiM, static_cast<const cx<T>*>(io->bm), chiM, 1, false,
+                  static_cast<const cx<T>*>(io->bn), nR, 1, false, theta_p, nR, 1, one, zero};
+    QR_TRY(runner.run(g, st));
+    th = theta_p;
+  }
+  // (i) gate (and diagonal Xi)
+  const double2* U = static_cast<const double2*>(io->gate);
+  const cx<T>* xi = static_cast<const cx<T>*>(io->xi);
+  if (d <= 5) {
+    QR_TRY(launch_gate<T>(th, theta_tp, U, chiL, d, chiR, io->xi_kind == 2 ? xi : nullptr,
+                          io->xi_kind == 2 ? theta_t : nullptr, st));
+  } else {
+    int n4 = d * d * d * d;
+    k_convert_gate<T><<<(unsigned)ceil_div(n4, 256), 256, 0, st>>>(U, Ut, n4);
+    note_launch();
+    QR_CUDA_TRY(cudaGetLastError());
+    GemmArgs<T> g{d * d, chiR, d * d, Ut, d * d, 1, false, th, chiR, 1, false, theta_tp, chiR, 1,
+                  one, zero};
+    g.batch = chiL; g.bsa = 0; g.bsb = (long long)d * d * chiR; g.bsc = g.bsb;
+    QR_TRY(gemm_simt<T>(g, st, nullptr, 0));
+    if (io->xi_kind == 2) {
+      long long tot = mL * nR;
+      k_scale_rows<T><<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(theta_tp, theta_t, xi, chiL,
+                                                                   d * nR);
+      note_launch();
+      QR_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  if (io->xi_kind == 1) {  // dense Xi: theta~ = Xi theta~' on the left bond index
+    GemmArgs<T> g{chiL, (int)(d * nR), chiL, xi, chiL, 1, false, theta_tp, d * nR, 1, false,
+                  theta_t, d * nR, 1, one, zero};
+    QR_TRY(runner.run(g, st));
+  }
+  QR_TRY(norm2<T>(theta_t, mL * nR, partial, scal + 0, st));
+
+  // (i) X = theta~ Y0^dag, QR(X) -> Q
+  const cx<T>* Y0 = y0_is_bn ? static_cast<const cx<T>*>(io->bn) : theta_t;
+  {
+    GemmArgs<T> g{(int)mL, eta, (int)nR, theta_t, nR, 1, false, Y0, 1, nR, true, X, eta, 1, one,
+                  zero};
+    QR_TRY(runner.run(g, st));
+  }
+  QR_TRY(householder_qr<T>(X, eta, (int)mL, eta, Q, eta, qs, st, err, &qg));
+
+  // (ii) Z = theta~^dag Q, QR(Z) -> Qz, Rz
+  {
+    GemmArgs<T> g{(int)nR, eta, (int)mL, theta_t, 1, nR, true, Q, eta, 1, false, Z, eta, 1, one,
+                  zero};
+    QR_TRY(runner.run(g, st));
+  }
+  QR_TRY(householder_qr<T>(Z, eta, (int)nR, eta, Qz, eta, qs, st, err, &qg));
+
+  cx<T>* bn_out = static_cast<cx<T>*>(io->bn_out);
+  cx<T>* xi_out = static_cast<cx<T>*>(io->xi_out);
+  cx<T>* bm_out = static_cast<cx<T>*>(io->bm_out);
+  int chi_new = eta;
+  if (!cbe) {
+    // (iii) Xi~ = L / ||L||, B~^n = Q^[n] = Qz^dag, B~^m = theta~' Qz
+    QR_TRY(norm2<T>(Z, (long long)eta * eta, partial, scal + 1, st));
+    k_finalize<<<1, 1, 0, st>>>(scal + 0, scal + 1, (double)eta,
+                                io->stats_out ? io->stats_out : stats_local, scal + 2, err);
+    note_launch();
+    QR_CUDA_TRY(cudaGetLastError());
+    QR_TRY(conj_transpose<T>(Z, eta, xi_out, eta, eta, eta, scal + 2, st));
+    QR_TRY(conj_transpose<T>(Qz, eta, bn_out, nR, (int)nR, eta, nullptr, st));
+    GemmArgs<T> g{(int)mL, eta, (int)nR, theta_tp, nR, 1, false, Qz, eta, 1, false, bm_out, eta,
+                  1, one, zero};
+    QR_TRY(runner.run(g, st));
+  } else {
+    // (iv) M = L^dag L = Rz Rz^dag (FP64), eigen-decomposition
+    long long ee = (long long)eta * eta;
+    double2* Rz64 = M;  // reuse: first convert Rz, then form M in Vh's buffer, swap
+    k_to_c128<T><<<(unsigned)ceil_div(ee, 256), 256, 0, st>>>(Z, Rz64, ee);
+    note_launch();
+    QR_CUDA_TRY(cudaGetLastError());
+    {
+      GemmArgs<double> g{eta, eta, eta, Rz64, eta, 1, false, Rz64, 1, eta, true, Vh, eta, 1,
+                         mk<double>(1, 0), mk<double>(0, 0)};
+      QR_TRY(gemm_simt<double>(g, st, nullptr, 0));
+    }
+    // Vh now holds M; eig destroys its input -> copy into M and decompose
+    QR_CUDA_TRY(cudaMemcpyAsync(M, Vh, ee * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    QR_TRY(herm_eig(M, eta, w, Vh, eig_scr, eig_elems, st, err));
+    k_cbe_cut<<<1, 1, 0, st>>>(w, eta, tr->chi_max, tr->svd_min, tr->tie_tol, Sv, scal + 1,
+                               chi_dev);
+    note_launch();
+    QR_CUDA_TRY(cudaGetLastError());
+    int chi_h = 0;
+    QR_CUDA_TRY(cudaMemcpyAsync(&chi_h, chi_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+    QR_CUDA_TRY(cudaStreamSynchronize(st));
+    chi_new = chi_h;
+    if (chi_new < 1 || chi_new > eta) { set_last_message("CBE: bad cut"); return QRTEBD_ERR_NUMERIC; }
+    if (io->schmidt_out)
+      QR_CUDA_TRY(cudaMemcpyAsync(io->schmidt_out, Sv, eta * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    k_finalize<<<1, 1, 0, st>>>(scal + 0, scal + 1, (double)chi_new,
+                                io->stats_out ? io->stats_out : stats_local, scal + 2, err);
+    note_launch();
+    QR_CUDA_TRY(cudaGetLastError());
+    // (v) B~^n = P V Q^[n] = Vh[0:c] Qz^dag; Xi~ = diag(S[0:c]) / ||.||
+    k_from_c128<T><<<(unsigned)ceil_div(ee, 256), 256, 0, st>>>(Vh, Vt, ee);
+    note_launch();
+    QR_CUDA_TRY(cudaGetLastError());
+    {
+      GemmArgs<T> g{chi_new, (int)nR, eta, Vt, eta, 1, false, Qz, 1, eta, true, bn_out, nR, 1,
+                    one, zero};
+      QR_TRY(runner.run(g, st));
+    }
+    k_diag_xi<T><<<(unsigned)ceil_div((long long)chi_new * chi_new, 256), 256, 0, st>>>(
+        Sv, chi_new, scal + 2, xi_out);
+    note_launch();
+    QR_CUDA_TRY(cudaGetLastError());
+    {
+      GemmArgs<T> g{(int)mL, chi_new, (int)nR, theta_tp, nR, 1, false, bn_out, 1, nR, true, bm_out,
+                    chi_new, 1, one, zero};
+      QR_TRY(runner.run(g, st));
+    }
+    (void)Bn_full;
+  }
+  if (info) { info->eta = eta; info->chi_new = chi_new; }
+  return QRTEBD_OK;
+}
+
+}  // namespace
+
+int choose_eta(const qrtebd_trunc* tr, int chi_l, int d, int chi_m, int chi_r) {
+  long long cap = std::min((long long)d * chi_l, (long long)d * chi_r);
+  long long eta;
+  if (tr->eta > 0) {
+    eta = tr->eta;
+  } else if (tr->scheme == QRTEBD_PLAIN) {
+    eta = std::min<long long>(tr->chi_max, cap);
+  } else {
+    long long dchi = (long long)std::ceil(tr->dchi_frac * chi_m - 1e-9);
+    if (dchi < tr->dchi_min) dchi = tr->dchi_min;
+    eta = std::min<long long>(chi_m + dchi, cap);
+  }
+  if (eta < 1 || eta > cap) return -1;
+  return (int)eta;
+}
+
+int bond_update(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t st,
+                qrtebd_bond_info* info, size_t* bytes) {
+  if (!io || !tr) return QRTEBD_ERR_INVALID_ARG;
+  if (io->chi_l < 1 || io->d < 2 || io->chi_m < 1 || io->chi_r < 1 || tr->chi_max < 1)
+    return QRTEBD_ERR_INVALID_ARG;
+  if (io->xi_kind < 0 || io->xi_kind > 2) return QRTEBD_ERR_INVALID_ARG;
+  if (tr->scheme != QRTEBD_PLAIN && tr->scheme != QRTEBD_CBE) return QRTEBD_ERR_INVALID_ARG;
+  if (!bytes) {
+    if (!io->bn || !io->gate || !io->bm_out || !io->xi_out || !io->bn_out) return QRTEBD_ERR_INVALID_ARG;
+    if (!io->theta && !io->bm) return QRTEBD_ERR_INVALID_ARG;
+    if (io->xi_kind != 0 && !io->xi) return QRTEBD_ERR_INVALID_ARG;
+  }
+  switch (io->precision) {
+    case QRTEBD_C128: return bond_update_t<double>(io, tr, st, info, bytes);
+    case QRTEBD_C64_3XTF32:
+    case QRTEBD_C64_TF32:
+    case QRTEBD_C64_FP32: return bond_update_t<float>(io, tr, st, info, bytes);
+    default: return QRTEBD_ERR_INVALID_ARG;
+  }
+}
+
+}  // namespace qrtebd

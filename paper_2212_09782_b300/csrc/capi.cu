@@ -1,0 +1,232 @@
+// extern "C" entry points of libqrtebd (declared in include/qrtebd.h).
+#include <complex>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "bond.cuh"
+#include "tc_gemm.cuh"
+
+namespace qrtebd {
+
+namespace {
+__device__ unsigned g_dev_err;  // device error word (one per device)
+thread_local std::string g_msg;
+std::mutex g_err_mu;
+unsigned* g_err_ptr[64] = {};
+}  // namespace
+
+void set_last_error(cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "%s: %s (%s:%d)", cudaGetErrorString(e), what, file, line);
+  g_msg = buf;
+}
+void set_last_message(const char* msg) { g_msg = msg; }
+
+unsigned* device_error_word() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  if (!g_err_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_dev_err) != cudaSuccess) return nullptr;
+    g_err_ptr[dev] = static_cast<unsigned*>(p);
+  }
+  return g_err_ptr[dev];
+}
+
+// Read-and-clear the device error word (synchronises the stream first).
+int check_device_error(cudaStream_t st) {
+  QR_CUDA_TRY(cudaStreamSynchronize(st));
+  unsigned* p = device_error_word();
+  if (!p) { set_last_message("device error word unavailable"); return QRTEBD_ERR_CUDA; }
+  unsigned h = 0;
+  QR_CUDA_TRY(cudaMemcpy(&h, p, sizeof h, cudaMemcpyDeviceToHost));
+  if (h) {
+    unsigned z = 0;
+    QR_CUDA_TRY(cudaMemcpy(p, &z, sizeof z, cudaMemcpyHostToDevice));
+    if (h & DEVERR_TIMEOUT) { set_last_message("a kernel gave up a bounded wait"); return QRTEBD_ERR_TIMEOUT; }
+    if (h & DEVERR_NUMERIC) { set_last_message("NaN/Inf met in a norm"); return QRTEBD_ERR_NUMERIC; }
+    set_last_message("device bounds check failed");
+    return QRTEBD_ERR_INVALID_ARG;
+  }
+  return QRTEBD_OK;
+}
+
+// ---------------------------------------------------------------- clock gate
+namespace {
+using zc = std::complex<double>;
+
+// Cyclic Jacobi for a small Hermitian matrix (host): A = V diag(w) V^dag.
+void herm_jacobi_host(int n, std::vector<zc>& A, std::vector<zc>& V, std::vector<double>& w) {
+  V.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0, tot = 0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        double a2 = std::norm(A[(size_t)i * n + j]);
+        tot += a2;
+        if (i != j) off += a2;
+      }
+    if (off <= 1e-32 * tot || tot == 0) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        zc apq = A[(size_t)p * n + q];
+        double ab = std::abs(apq);
+        if (ab < 1e-300) continue;
+        double app = A[(size_t)p * n + p].real(), aqq = A[(size_t)q * n + q].real();
+        double z = (aqq - app) / (2 * ab);
+        double t = (z >= 0 ? 1.0 : -1.0) / (std::fabs(z) + std::sqrt(1 + z * z));
+        double c = 1 / std::sqrt(1 + t * t), s = t * c;
+        zc se = s * apq / ab;
+        for (int i = 0; i < n; ++i) {  // columns: A G, V G
+          zc x = A[(size_t)i * n + p], y = A[(size_t)i * n + q];
+          A[(size_t)i * n + p] = c * x - std::conj(se) * y;
+          A[(size_t)i * n + q] = se * x + c * y;
+          x = V[(size_t)i * n + p]; y = V[(size_t)i * n + q];
+          V[(size_t)i * n + p] = c * x - std::conj(se) * y;
+          V[(size_t)i * n + q] = se * x + c * y;
+        }
+        for (int j = 0; j < n; ++j) {  // rows: G^dag A
+          zc x = A[(size_t)p * n + j], y = A[(size_t)q * n + j];
+          A[(size_t)p * n + j] = c * x - se * y;
+          A[(size_t)q * n + j] = std::conj(se) * x + c * y;
+        }
+      }
+  }
+  w.resize(n);
+  for (int i = 0; i < n; ++i) w[i] = A[(size_t)i * n + i].real();
+}
+}  // namespace
+
+}  // namespace qrtebd
+
+using namespace qrtebd;
+
+extern "C" {
+
+int qrtebd_trunc_default(qrtebd_trunc* tr, int scheme, int chi_max) {
+  if (!tr || chi_max < 1 || (scheme != QRTEBD_PLAIN && scheme != QRTEBD_CBE)) return QRTEBD_ERR_INVALID_ARG;
+  tr->scheme = scheme;
+  tr->chi_max = chi_max;
+  tr->eta = 0;
+  tr->dchi_min = 100;
+  tr->dchi_frac = 0.1;
+  tr->svd_min = 1e-14;
+  tr->tie_tol = 1e-10;
+  return QRTEBD_OK;
+}
+
+int qrtebd_bond_workspace_size(int precision, int chi_l, int d, int chi_m, int chi_r, int xi_kind,
+                               int theta_given, const qrtebd_trunc* tr, size_t* bytes) {
+  if (!bytes || !tr) return QRTEBD_ERR_INVALID_ARG;
+  qrtebd_bond_io io;
+  std::memset(&io, 0, sizeof io);
+  io.precision = precision;
+  io.chi_l = chi_l; io.d = d; io.chi_m = chi_m; io.chi_r = chi_r;
+  io.xi_kind = xi_kind;
+  static const char dummy = 0;
+  io.bm = theta_given ? nullptr : &dummy;
+  return bond_update(&io, tr, nullptr, nullptr, bytes);
+}
+
+int qrtebd_bond_update(const qrtebd_bond_io* io, const qrtebd_trunc* tr, void* stream,
+                       qrtebd_bond_info* info) {
+  return bond_update(io, tr, static_cast<cudaStream_t>(stream), info, nullptr);
+}
+
+int qrtebd_stream_check(void* stream) { return check_device_error(static_cast<cudaStream_t>(stream)); }
+
+int qrtebd_zgemm(int precision, int m, int n, int k, const void* A, long long sam, long long sak,
+                 int conj_a, const void* B, long long sbk, long long sbn, int conj_b, void* C,
+                 long long scm, long long scn, const double* alpha, const double* beta,
+                 void* workspace, size_t workspace_bytes, void* stream) {
+  if (m < 0 || n < 0 || k < 0 || !A || !B || !C || !alpha || !beta) return QRTEBD_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (precision == QRTEBD_C128) {
+    GemmArgs<double> g{m, n, k, static_cast<const double2*>(A), sam, sak, conj_a != 0,
+                       static_cast<const double2*>(B), sbk, sbn, conj_b != 0,
+                       static_cast<double2*>(C), scm, scn,
+                       make_double2(alpha[0], alpha[1]), make_double2(beta[0], beta[1])};
+    return gemm_simt<double>(g, st, nullptr, 0);
+  }
+  GemmArgs<float> g{m, n, k, static_cast<const float2*>(A), sam, sak, conj_a != 0,
+                    static_cast<const float2*>(B), sbk, sbn, conj_b != 0,
+                    static_cast<float2*>(C), scm, scn,
+                    make_float2((float)alpha[0], (float)alpha[1]),
+                    make_float2((float)beta[0], (float)beta[1])};
+  if (precision == QRTEBD_C64_FP32) return gemm_simt<float>(g, st, nullptr, 0);
+  if (precision != QRTEBD_C64_3XTF32 && precision != QRTEBD_C64_TF32) return QRTEBD_ERR_INVALID_ARG;
+  Arena ar;
+  ar.base = static_cast<char*>(workspace);
+  ar.cap = workspace_bytes;
+  TcWorkspace w;
+  tc_carve(ar, m, k, n, w);
+  if (ar.overflow() || !workspace) { set_last_message("zgemm: workspace too small"); return QRTEBD_ERR_OOM; }
+  return tc_gemm(g, precision == QRTEBD_C64_3XTF32, w, st);
+}
+
+size_t qrtebd_zgemm_workspace_size(int m, int n, int k) {
+  Arena ar;
+  ar.measuring = true;
+  TcWorkspace w;
+  tc_carve(ar, m, k, n, w);
+  return ar.off;
+}
+
+int qrtebd_clock_bond_gate(int d, double g, double wl, double wr, double tau_re, double tau_im,
+                           double* U_out) {
+  if (d < 2 || d > 64 || !U_out) return QRTEBD_ERR_INVALID_ARG;
+  const int n = d * d;
+  const double pi = 3.14159265358979323846;
+  std::vector<zc> Z(d), X((size_t)d * d, 0.0);
+  for (int k = 0; k < d; ++k) Z[k] = std::polar(1.0, 2 * pi * k / d);
+  for (int k = 0; k < d; ++k) X[(size_t)k * d + (k + 1) % d] = 1.0;
+  std::vector<zc> Xs((size_t)d * d);
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) Xs[(size_t)i * d + j] = X[(size_t)i * d + j] + std::conj(X[(size_t)j * d + i]);
+  std::vector<zc> h((size_t)n * n, 0.0);
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j)
+      for (int k = 0; k < d; ++k)
+        for (int l = 0; l < d; ++l) {
+          zc v = 0;
+          if (i == k && j == l) v -= Z[i] * std::conj(Z[j]) + std::conj(Z[i]) * Z[j];
+          if (j == l) v -= g * wl * Xs[(size_t)i * d + k];
+          if (i == k) v -= g * wr * Xs[(size_t)j * d + l];
+          h[(size_t)(i * d + j) * n + (k * d + l)] = v;
+        }
+  std::vector<zc> V;
+  std::vector<double> w;
+  herm_jacobi_host(n, h, V, w);
+  const zc tau(tau_re, tau_im), I(0, 1);
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) {
+      zc s = 0;
+      for (int k = 0; k < n; ++k) s += V[(size_t)r * n + k] * std::exp(-I * tau * w[k]) * std::conj(V[(size_t)c * n + k]);
+      U_out[2 * ((size_t)r * n + c)] = s.real();
+      U_out[2 * ((size_t)r * n + c) + 1] = s.imag();
+    }
+  return QRTEBD_OK;
+}
+
+const char* qrtebd_strerror(int status) {
+  switch (status) {
+    case QRTEBD_OK: return "ok";
+    case QRTEBD_ERR_INVALID_ARG: return "invalid argument";
+    case QRTEBD_ERR_OOM: return "out of memory";
+    case QRTEBD_ERR_CUDA: return "CUDA error";
+    case QRTEBD_ERR_TIMEOUT: return "bounded wait expired";
+    case QRTEBD_ERR_NUMERIC: return "numerical error (NaN/Inf)";
+    case QRTEBD_ERR_NOT_ADMITTED: return "not admitted";
+    default: return "unknown status";
+  }
+}
+
+const char* qrtebd_last_error_message(void) { return g_msg.c_str(); }
+
+const char* qrtebd_version(void) { return "qrtebd 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,122 @@
+// Shared device/host helpers for libqrtebd (sm_103a).
+//
+// Complex numbers are stored interleaved (re, im) as float2 (complex64) or
+// double2 (complex128); every matrix is row-major with an explicit leading
+// dimension counted in complex elements.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+
+#include "../../include/qrtebd.h"
+
+namespace qrtebd {
+
+// ---------------------------------------------------------------- complex
+template <typename T> struct cplx;
+template <> struct cplx<float> { using type = float2; };
+template <> struct cplx<double> { using type = double2; };
+template <typename T> using cx = typename cplx<T>::type;
+
+template <typename T> __host__ __device__ __forceinline__ cx<T> mk(T r, T i) {
+  cx<T> z; z.x = r; z.y = i; return z;
+}
+template <typename T> __host__ __device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) {
+  return mk<T>(a.x + b.x, a.y + b.y);
+}
+template <typename T> __host__ __device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) {
+  return mk<T>(a.x - b.x, a.y - b.y);
+}
+template <typename T> __host__ __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename T> __host__ __device__ __forceinline__ cx<T> cconj(cx<T> a) {
+  return mk<T>(a.x, -a.y);
+}
+// conj(a) * b
+template <typename T> __host__ __device__ __forceinline__ cx<T> cmulc(cx<T> a, cx<T> b) {
+  return mk<T>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+// acc += a * b
+template <typename T> __device__ __forceinline__ void cfma(cx<T>& acc, cx<T> a, cx<T> b) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+}
+template <typename T> __host__ __device__ __forceinline__ T cabs2(cx<T> a) {
+  return a.x * a.x + a.y * a.y;
+}
+
+// ---------------------------------------------------------------- errors
+// Device-side error word: kernels that give up a bounded wait set a bit here
+// and return; the host maps it to QRTEBD_ERR_TIMEOUT at the next sync point.
+enum : unsigned { DEVERR_TIMEOUT = 1u, DEVERR_NUMERIC = 2u, DEVERR_BOUNDS = 4u };
+
+// Iteration limit for every spin on an mbarrier or a flag (~1 s on B300).
+constexpr long long kSpinLimit = 1ll << 24;
+
+#define QR_CUDA_TRY(expr)                                                           \
+  do {                                                                              \
+    cudaError_t e_ = (expr);                                                        \
+    if (e_ != cudaSuccess) {                                                        \
+      qrtebd::set_last_error(e_, #expr, __FILE__, __LINE__);                        \
+      return QRTEBD_ERR_CUDA;                                                       \
+    }                                                                               \
+  } while (0)
+
+#define QR_TRY(expr)                                                                \
+  do {                                                                              \
+    int s_ = (expr);                                                                \
+    if (s_ != QRTEBD_OK) return s_;                                                 \
+  } while (0)
+
+void set_last_error(cudaError_t e, const char* what, const char* file, int line);
+void set_last_message(const char* msg);
+
+// Address of the library's device error word on the current device (kernels
+// atomicOr DEVERR_* bits into it; qrtebd_stream_check reads and clears it).
+unsigned* device_error_word();
+
+// Kernel-launch accounting (every launch site calls it) and event timing of
+// kernel families (see prof.cu and qrtebd_profile_enable).
+void note_launch(int n = 1);
+enum ProfFamily { PROF_TC_GEMM = 0, PROF_QR_PANEL = 1, PROF_SIMT_GEMM = 2, PROF_PREP = 3,
+                  PROF_GATE = 4, PROF_NFAM = 5 };
+class ProfScope {
+ public:
+  ProfScope(int fam, cudaStream_t st, double flops = 0, double bytes = 0);
+  ~ProfScope();
+ private:
+  int fam_; cudaStream_t st_; double flops_, bytes_;
+  void* a_ = nullptr; void* b_ = nullptr;
+};
+
+__host__ __device__ __forceinline__ long long ceil_div(long long a, long long b) {
+  return (a + b - 1) / b;
+}
+__host__ __device__ __forceinline__ size_t align_up(size_t x, size_t a) {
+  return (x + a - 1) / a * a;
+}
+
+// Bump allocator over a caller-provided workspace; used to carve scratch.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t off = 0;
+  bool measuring = false;  // size-query mode: hands out nullptr, only counts
+  template <typename P> P* take(size_t count) {
+    size_t bytes = align_up(count * sizeof(P), 256);
+    size_t o = off;
+    off += bytes;
+    if (measuring) return nullptr;
+    if (off > cap) return nullptr;
+    return reinterpret_cast<P*>(base + o);
+  }
+  bool overflow() const { return !measuring && off > cap; }
+};
+
+}  // namespace qrtebd

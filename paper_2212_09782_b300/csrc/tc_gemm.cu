@@ -1,0 +1,464 @@
+// Complex64 GEMM on tcgen05 tensor cores; see tc_gemm.cuh.
+//
+// Kernel: one 128 x 256 real output tile per CTA (one CTA per SM: ~197 KB of
+// shared memory), 192 threads in three roles:
+//   warp 0      TMA producer: 128B-swizzled K-major tiles of A' (128 x 32 fp32) and
+//               B'^T (256 x 32 fp32) per stage, hi and lo parts, into a ring of
+//               stages guarded by full/empty mbarriers;
+//   warp 1      TMEM allocation (256 columns) and the single MMA-issuing thread:
+//               per stage 4 K-steps of tcgen05.mma.kind::tf32 M=128 N=256 K=8
+//               (x3 for hi*hi, hi*lo, lo*hi), tcgen05.commit frees the stage;
+//   warps 2-5   epilogue: tcgen05.ld of the FP32 accumulator (one TMEM lane per
+//               output row), alpha/beta, complex stores.
+// Every mbarrier wait is bounded (kSpinLimit); on expiry the kernel sets
+// DEVERR_TIMEOUT in the error word, drains what it issued and returns.
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "tc_gemm.cuh"
+
+namespace qrtebd {
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BK = 32;     // BK in fp32 elements = one 128 B swizzle row
+constexpr int A_TILE = BM * BK * 4;            // 16 KB
+constexpr int B_TILE = BN * BK * 4;            // 32 KB
+constexpr int NTHREADS = 192;
+constexpr int TMEM_COLS = 256;
+
+template <bool THREE> struct Cfg {
+  static constexpr int STAGES = THREE ? 2 : 4;
+  static constexpr int STAGE_BYTES = THREE ? 2 * (A_TILE + B_TILE) : (A_TILE + B_TILE);
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+};
+
+struct Epi {
+  float2* C; long long scm, scn;
+  float2 alpha, beta;
+  int M, Nc;  // rows, complex columns
+};
+
+__device__ __forceinline__ uint32_t s_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t n) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(s_u32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(s_u32(b)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(s_u32(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  for (long long i = 0; i < kSpinLimit; ++i)
+    if (mbar_try(b, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load(void* dst, const CUtensorMap* tm, uint64_t* bar, int x,
+                                         int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(s_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(s_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                       uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          s_u32(bar))
+      : "memory");
+}
+// K-major operand tile, 128-byte swizzle: rows of 128 B, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;                // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;      // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                // descriptor version (tcgen05)
+  d |= (uint64_t)2 << 61;                // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor: D fp32, A/B tf32, both K-major, M=128, N=256.
+constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+#define TMEM_LD32(taddr, r)                                                                  \
+  asm volatile(                                                                              \
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13," \
+      "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"     \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),  \
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),          \
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),       \
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),       \
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),       \
+        "=r"(r[31])                                                                          \
+      : "r"(taddr))
+
+template <bool THREE>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_tc_gemm(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
+              const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
+              Epi epi, int Kp, unsigned* err) {
+  using C = Cfg<THREE>;
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024 - (s_u32(smem_raw) & 1023)) & 1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* tmem_full = empty + C::STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_full + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  const int nk = (Kp + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
+    mbar_init(tmem_full, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     s_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto stage_a_hi = [&](int s) { return smem + s * C::STAGE_BYTES; };
+  auto stage_b_hi = [&](int s) { return smem + s * C::STAGE_BYTES + A_TILE; };
+  auto stage_a_lo = [&](int s) { return smem + s * C::STAGE_BYTES + A_TILE + B_TILE; };
+  auto stage_b_lo = [&](int s) { return smem + s * C::STAGE_BYTES + 2 * A_TILE + B_TILE; };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      bool ok = true;
+      int issued = 0;
+      for (int kt = 0; kt < nk && ok; ++kt) {
+        const int s = kt % C::STAGES;
+        const uint32_t ph = (uint32_t)((kt / C::STAGES) & 1);
+        if (!mbar_wait(&empty[s], ph ^ 1u)) { ok = false; break; }
+        mbar_expect_tx(&full[s], C::STAGE_BYTES);
+        tma_load(stage_a_hi(s), &tA_hi, &full[s], kt * BK, m0);
+        tma_load(stage_b_hi(s), &tB_hi, &full[s], kt * BK, n0);
+        if (THREE) {
+          tma_load(stage_a_lo(s), &tA_lo, &full[s], kt * BK, m0);
+          tma_load(stage_b_lo(s), &tB_lo, &full[s], kt * BK, n0);
+        }
+        ++issued;
+      }
+      if (!ok) atomicOr(err, DEVERR_TIMEOUT);
+      // drain: every issued stage must have landed before shared memory goes away
+      for (int kt = (issued > C::STAGES ? issued - C::STAGES : 0); kt < issued; ++kt) {
+        const int s = kt % C::STAGES;
+        if (!mbar_wait(&full[s], (uint32_t)((kt / C::STAGES) & 1))) { atomicOr(err, DEVERR_TIMEOUT); break; }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = true;
+      for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt % C::STAGES;
+        const uint32_t ph = (uint32_t)((kt / C::STAGES) & 1);
+        if (!mbar_wait(&full[s], ph)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t a_hi = s_u32(stage_a_hi(s)), b_hi = s_u32(stage_b_hi(s));
+        const uint32_t a_lo = s_u32(stage_a_lo(s)), b_lo = s_u32(stage_b_lo(s));
+#pragma unroll
+        for (int k = 0; k < BK / 8; ++k) {
+          const uint32_t off = k * 32;  // 8 tf32 = 32 bytes along K inside the swizzle row
+          const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
+          if (THREE) {
+            tc_mma(tmem, desc_sw128(a_lo + off), desc_sw128(b_hi + off), kIdesc, acc);
+            tc_mma(tmem, desc_sw128(a_hi + off), desc_sw128(b_lo + off), kIdesc, 1u);
+            tc_mma(tmem, desc_sw128(a_hi + off), desc_sw128(b_hi + off), kIdesc, 1u);
+          } else {
+            tc_mma(tmem, desc_sw128(a_hi + off), desc_sw128(b_hi + off), kIdesc, acc);
+          }
+        }
+        tc_commit(&empty[s]);
+      }
+      if (!ok) atomicOr(err, DEVERR_TIMEOUT);
+      tc_commit(tmem_full);  // arrives once every MMA issued above has completed
+    }
+  } else {
+    // epilogue warps 2..5 -> TMEM lane quarters 2, 3, 0, 1
+    const int q = warp & 3;
+    const int row = m0 + q * 32 + lane;
+    const bool ok = mbar_wait(tmem_full, 0);
+    tc_fence_after();
+    if (!ok) {
+      if (lane == 0) atomicOr(err, DEVERR_TIMEOUT);
+    } else {
+      const bool use_beta = (epi.beta.x != 0.f || epi.beta.y != 0.f);
+#pragma unroll 1
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        if (n0 + ch * 32 >= 2 * epi.Nc) break;  // warp-uniform
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 32);
+        TMEM_LD32(taddr, r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (row < epi.M) {
+          const int nb = (n0 + ch * 32) >> 1;
+          float2* crow = epi.C + (long long)row * epi.scm;
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int n = nb + j;
+            if (n < epi.Nc) {
+              float ar = __uint_as_float(r[2 * j]), ai = __uint_as_float(r[2 * j + 1]);
+              float2 v;
+              v.x = epi.alpha.x * ar - epi.alpha.y * ai;
+              v.y = epi.alpha.x * ai + epi.alpha.y * ar;
+              float2* p = crow + (long long)n * epi.scn;
+              if (use_beta) {
+                float2 c = *p;
+                v.x += epi.beta.x * c.x - epi.beta.y * c.y;
+                v.y += epi.beta.x * c.y + epi.beta.y * c.x;
+              }
+              *p = v;
+            }
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    // tmem_full has fired (epilogue waited on it) unless a wait expired; wait once more
+    // (bounded) so no MMA still writes the columns being freed.
+    if (!mbar_wait(tmem_full, 0) && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+// ------------------------------------------------------------------ prep
+__device__ __forceinline__ float tf32_rna(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// A'[m][2k..2k+1] = (Re, Im) opA(m, k), split hi/lo
+__global__ void k_prep_a(const float2* __restrict__ A, long long sam, long long sak, int conj,
+                         int M, int K, float* __restrict__ hi, float* __restrict__ lo, int ld,
+                         int three) {
+  __shared__ float2 t[32][33];
+  const int m0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const bool kc = (sak == 1);
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int mm = kc ? r : threadIdx.x, kk = kc ? threadIdx.x : r;
+    int m = m0 + mm, k = k0 + kk;
+    float2 v = make_float2(0.f, 0.f);
+    if (m < M && k < K) v = A[m * sam + k * sak];
+    if (conj) v.y = -v.y;
+    t[mm][kk] = v;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int m = m0 + r, k = k0 + threadIdx.x;
+    if (m < M && k < K) {
+      float2 v = t[r][threadIdx.x];
+      float2 h = make_float2(tf32_rna(v.x), tf32_rna(v.y));
+      long long o = (long long)m * ld + 2 * k;
+      *reinterpret_cast<float2*>(hi + o) = h;
+      if (three) *reinterpret_cast<float2*>(lo + o) = make_float2(v.x - h.x, v.y - h.y);
+    }
+  }
+}
+
+// B'^T rows 2n: (Re b, -Im b), 2n+1: (Im b, Re b) at columns 2k, 2k+1; b = opB(k, n)
+__global__ void k_prep_b(const float2* __restrict__ B, long long sbk, long long sbn, int conj,
+                         int K, int N, float* __restrict__ hi, float* __restrict__ lo, int ld,
+                         int three) {
+  __shared__ float2 t[32][33];  // [n][k]
+  const int n0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const bool kc = (sbk == 1);
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int nn = kc ? r : threadIdx.x, kk = kc ? threadIdx.x : r;
+    int n = n0 + nn, k = k0 + kk;
+    float2 v = make_float2(0.f, 0.f);
+    if (n < N && k < K) v = B[k * sbk + n * sbn];
+    if (conj) v.y = -v.y;
+    t[nn][kk] = v;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    int n = n0 + r, k = k0 + threadIdx.x;
+    if (n < N && k < K) {
+      float2 b = t[r][threadIdx.x];
+      float br = tf32_rna(b.x), bi = tf32_rna(b.y);
+      long long o0 = (long long)(2 * n) * ld + 2 * k, o1 = o0 + ld;
+      *reinterpret_cast<float2*>(hi + o0) = make_float2(br, -bi);
+      *reinterpret_cast<float2*>(hi + o1) = make_float2(bi, br);
+      if (three) {
+        float lr = b.x - br, li = b.y - bi;
+        *reinterpret_cast<float2*>(lo + o0) = make_float2(lr, -li);
+        *reinterpret_cast<float2*>(lo + o1) = make_float2(li, lr);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ host
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+int get_encode() {
+  std::call_once(g_encode_once, [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  });
+  if (!g_encode) { set_last_message("cuTensorMapEncodeTiled unavailable"); return QRTEBD_ERR_CUDA; }
+  return QRTEBD_OK;
+}
+
+int make_map(CUtensorMap* tm, const float* base, int rows, int cols, int ld, int box_rows) {
+  cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), gdim,
+                        gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) { set_last_message("cuTensorMapEncodeTiled failed"); return QRTEBD_ERR_CUDA; }
+  return QRTEBD_OK;
+}
+
+inline int ld_for(int k) { return (int)align_up((size_t)2 * k, 32); }
+
+bool g_attr3 = false, g_attr1 = false;
+
+}  // namespace
+
+void tc_carve(Arena& ar, int max_m, int max_k, int max_n, TcWorkspace& w) {
+  size_t ld = (size_t)ld_for(max_k);
+  w.a_cap = (size_t)max_m * ld;
+  w.b_cap = (size_t)2 * max_n * ld;
+  for (int i = 0; i < 2; ++i) {
+    w.a[i] = TcSlot{};
+    w.a[i].hi = ar.take<float>(w.a_cap);
+    w.a[i].lo = ar.take<float>(w.a_cap);
+  }
+  w.b = TcSlot{};
+  w.b.hi = ar.take<float>(w.b_cap);
+  w.b.lo = ar.take<float>(w.b_cap);
+  w.a_next = 0;
+}
+
+void tc_invalidate(TcWorkspace& w) {
+  w.a[0].valid = w.a[1].valid = false;
+  w.b.valid = false;
+}
+
+bool tc_gemm_eligible(const GemmArgs<float>& g) {
+  return g.batch == 1 && g.M >= 128 && g.N >= 64 && g.K >= 128 &&
+         (double)g.M * g.N * g.K >= (double)(1 << 22);
+}
+
+int tc_gemm(const GemmArgs<float>& g, bool three, TcWorkspace& w, cudaStream_t st) {
+  const int M = g.M, N = g.N, K = g.K;
+  const int ld = ld_for(K);
+  if ((size_t)M * ld > w.a_cap || (size_t)2 * N * ld > w.b_cap || !w.a[0].hi || !w.b.hi)
+    return gemm_simt<float>(g, st, nullptr, 0);
+  QR_TRY(get_encode());
+
+  // ---- A' (cached per source/op within one bond update)
+  TcSlot* sa = nullptr;
+  for (int i = 0; i < 2; ++i) {
+    TcSlot& s = w.a[i];
+    if (s.valid && s.src == g.A && s.s0 == g.sam && s.s1 == g.sak && s.rows == M && s.cols == K &&
+        s.conj == g.conj_a && s.three == three && s.ld == ld)
+      sa = &s;
+  }
+  if (!sa) {
+    sa = &w.a[w.a_next];
+    w.a_next ^= 1;
+    dim3 grid((unsigned)ceil_div(K, 32), (unsigned)ceil_div(M, 32));
+    ProfScope prof(PROF_PREP, st, 0, 8.0 * M * K + (three ? 16.0 : 8.0) * M * K);
+    k_prep_a<<<grid, dim3(32, 8), 0, st>>>(g.A, g.sam, g.sak, g.conj_a ? 1 : 0, M, K, sa->hi,
+                                           sa->lo, ld, three ? 1 : 0);
+    note_launch();
+    QR_CUDA_TRY(cudaGetLastError());
+    sa->valid = true; sa->src = g.A; sa->s0 = g.sam; sa->s1 = g.sak; sa->rows = M; sa->cols = K;
+    sa->conj = g.conj_a; sa->three = three; sa->ld = ld;
+  }
+  // ---- B'^T
+  {
+    dim3 grid((unsigned)ceil_div(K, 32), (unsigned)ceil_div(N, 32));
+    ProfScope prof(PROF_PREP, st, 0, 8.0 * N * K + (three ? 32.0 : 16.0) * N * K);
+    k_prep_b<<<grid, dim3(32, 8), 0, st>>>(g.B, g.sbk, g.sbn, g.conj_b ? 1 : 0, K, N, w.b.hi,
+                                           w.b.lo, ld, three ? 1 : 0);
+    note_launch();
+    QR_CUDA_TRY(cudaGetLastError());
+  }
+  CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
+  QR_TRY(make_map(&ta_hi, sa->hi, M, 2 * K, ld, BM));
+  QR_TRY(make_map(&ta_lo, three ? sa->lo : sa->hi, M, 2 * K, ld, BM));
+  QR_TRY(make_map(&tb_hi, w.b.hi, 2 * N, 2 * K, ld, BN));
+  QR_TRY(make_map(&tb_lo, three ? w.b.lo : w.b.hi, 2 * N, 2 * K, ld, BN));
+
+  Epi epi{g.C, g.scm, g.scn, g.alpha, g.beta, M, N};
+  dim3 grid((unsigned)ceil_div(2LL * N, BN), (unsigned)ceil_div(M, BM));
+  unsigned* err = device_error_word();
+  ProfScope prof(PROF_TC_GEMM, st, 8.0 * M * N * K);
+  if (three) {
+    if (!g_attr3) {
+      QR_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Cfg<true>::SMEM));
+      g_attr3 = true;
+    }
+    k_tc_gemm<true><<<grid, NTHREADS, Cfg<true>::SMEM, st>>>(ta_hi, ta_lo, tb_hi, tb_lo, epi,
+                                                             2 * K, err);
+    note_launch();
+  } else {
+    if (!g_attr1) {
+      QR_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       Cfg<false>::SMEM));
+      g_attr1 = true;
+    }
+    k_tc_gemm<false><<<grid, NTHREADS, Cfg<false>::SMEM, st>>>(ta_hi, ta_lo, tb_hi, tb_lo, epi,
+                                                               2 * K, err);
+    note_launch();
+  }
+  QR_CUDA_TRY(cudaGetLastError());
+  return QRTEBD_OK;
+}
+
+}  // namespace qrtebd

@@ -1,0 +1,46 @@
+// Complex64 GEMM on sm_103a tensor cores (tcgen05, kind::tf32, TMEM accumulators).
+//
+// A complex product C = opA * opB becomes one real GEMM C' = A' B'^T:
+//   A' (M x 2K): row m = (Re, Im) of opA(m, k) interleaved - the natural
+//                complex64 layout of a K-contiguous operand;
+//   B'^T (2N x 2K): rows 2n and 2n+1 hold (Re b, -Im b) and (Im b, Re b) for
+//                b = opB(k, n) (the 2 x 2 real embedding of a complex number);
+//   C' (M x 2N) is then C in the interleaved complex layout: 8 real flops per
+//   complex multiply-add, no wasted work.
+// 3xTF32: every operand is split x = hi + lo with hi = tf32(x), and the MMA
+// pipe accumulates hi*hi + hi*lo + lo*hi in FP32 (about FP32 accuracy).
+#pragma once
+#include "common.cuh"
+#include "gemm_simt.cuh"
+
+namespace qrtebd {
+
+struct TcSlot {
+  float* hi = nullptr;
+  float* lo = nullptr;
+  // cache key of the prepared operand (valid within one bond update)
+  const void* src = nullptr; long long s0 = 0, s1 = 0; int rows = 0, cols = 0; bool conj = false;
+  bool three = false; bool valid = false; int ld = 0;
+};
+
+struct TcWorkspace {
+  TcSlot a[2];
+  TcSlot b;
+  size_t a_cap = 0, b_cap = 0;  // floats per hi (or lo) array
+  int a_next = 0;
+};
+
+// Carve operand buffers able to hold A' for max_m x max_k and B'^T for max_n x max_k.
+void tc_carve(Arena& ar, int max_m, int max_k, int max_n, TcWorkspace& w);
+
+// Shapes worth (and able to be) run on the tensor cores.
+bool tc_gemm_eligible(const GemmArgs<float>& g);
+
+// C = alpha opA opB + beta C through tcgen05. Falls back to the CUDA-core GEMM
+// when the prepared operands would not fit the workspace.
+int tc_gemm(const GemmArgs<float>& g, bool three, TcWorkspace& w, cudaStream_t st);
+
+// Invalidate cached prepared operands (call when their sources may change).
+void tc_invalidate(TcWorkspace& w);
+
+}  // namespace qrtebd

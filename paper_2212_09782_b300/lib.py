@@ -1,0 +1,401 @@
+"""ctypes binding of libqrtebd (include/qrtebd.h): argument marshalling only.
+
+Device memory comes from torch CUDA tensors (complex64 / complex128); every step
+of the bond update runs in the library's CUDA kernels. Loading fails loudly if
+the shared library is missing: there is no CPU fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libqrtebd.so")
+
+OK = 0
+ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC, ERR_NOT_ADMITTED = -1, -2, -3, -4, -5, -6
+C128, C64_3XTF32, C64_TF32, C64_FP32 = 0, 1, 2, 3
+PLAIN, CBE = 0, 1
+PRECISIONS = {"c128": C128, "c64_3xtf32": C64_3XTF32, "c64_tf32": C64_TF32, "c64_fp32": C64_FP32}
+
+
+class Trunc(C.Structure):
+    _fields_ = [("scheme", C.c_int), ("chi_max", C.c_int), ("eta", C.c_int), ("dchi_min", C.c_int),
+                ("dchi_frac", C.c_double), ("svd_min", C.c_double), ("tie_tol", C.c_double)]
+
+
+class BondIO(C.Structure):
+    _fields_ = [("precision", C.c_int), ("chi_l", C.c_int), ("d", C.c_int), ("chi_m", C.c_int),
+                ("chi_r", C.c_int), ("xi_kind", C.c_int), ("xi", C.c_void_p), ("bm", C.c_void_p),
+                ("bn", C.c_void_p), ("theta", C.c_void_p), ("gate", C.c_void_p),
+                ("bm_out", C.c_void_p), ("xi_out", C.c_void_p), ("bn_out", C.c_void_p),
+                ("stats_out", C.c_void_p), ("schmidt_out", C.c_void_p),
+                ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
+
+
+class BondInfo(C.Structure):
+    _fields_ = [("eta", C.c_int), ("chi_new", C.c_int)]
+
+
+class QrtebdError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib.qrtebd_last_error_message().decode() if _lib else ""
+        super().__init__(f"{where}: {strerror(status)} ({status}) {msg}")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libqrtebd.so not built ({LIB_PATH}); run python -m paper_2212_09782_b300.build")
+    lib = C.CDLL(LIB_PATH)
+    P, I, D, S = C.c_void_p, C.c_int, C.c_double, C.c_size_t
+    LL = C.c_longlong
+    sig = {
+        "qrtebd_trunc_default": (I, [C.POINTER(Trunc), I, I]),
+        "qrtebd_bond_workspace_size": (I, [I, I, I, I, I, I, I, C.POINTER(Trunc), C.POINTER(S)]),
+        "qrtebd_bond_update": (I, [C.POINTER(BondIO), C.POINTER(Trunc), P, C.POINTER(BondInfo)]),
+        "qrtebd_stream_check": (I, [P]),
+        "qrtebd_zgemm": (I, [I, I, I, I, P, LL, LL, I, P, LL, LL, I, P, LL, LL,
+                             C.POINTER(D), C.POINTER(D), P, S, P]),
+        "qrtebd_zgemm_workspace_size": (S, [I, I, I]),
+        "qrtebd_clock_bond_gate": (I, [I, D, D, D, D, D, C.POINTER(D)]),
+        "qrtebd_strerror": (C.c_char_p, [I]),
+        "qrtebd_last_error_message": (C.c_char_p, []),
+        "qrtebd_version": (C.c_char_p, []),
+        "qrtebd_launch_count": (C.c_longlong, []),
+        "qrtebd_profile_enable": (I, [I]),
+        "qrtebd_profile_read": (I, [I, C.POINTER(D), C.POINTER(C.c_longlong), C.POINTER(D),
+                                    C.POINTER(D)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+def raw():
+    """The ctypes CDLL handle."""
+    return _lib
+
+
+def strerror(status):
+    return _lib.qrtebd_strerror(status).decode()
+
+
+def check(status, where):
+    if status != OK:
+        raise QrtebdError(status, where)
+
+
+def version():
+    return _lib.qrtebd_version().decode()
+
+
+def trunc_default(scheme=PLAIN, chi_max=1024, **over):
+    t = Trunc()
+    check(_lib.qrtebd_trunc_default(C.byref(t), scheme, chi_max), "trunc_default")
+    for k, v in over.items():
+        setattr(t, k, v)
+    return t
+
+
+def clock_bond_gate(d, g, wl, wr, tau):
+    """exp(-i tau h_b) of the clock model as a complex128 numpy (d^2, d^2) array (host)."""
+    out = np.zeros(2 * d ** 4, np.float64)
+    tau = complex(tau)
+    check(_lib.qrtebd_clock_bond_gate(d, g, wl, wr, tau.real, tau.imag,
+                                      out.ctypes.data_as(C.POINTER(C.c_double))), "clock_bond_gate")
+    return out.view(np.complex128).reshape(d * d, d * d)
+
+
+def bond_workspace_size(precision, chi_l, d, chi_m, chi_r, trunc, xi_kind=1, theta_given=False):
+    n = C.c_size_t(0)
+    check(_lib.qrtebd_bond_workspace_size(precision, chi_l, d, chi_m, chi_r, xi_kind,
+                                          1 if theta_given else 0, C.byref(trunc), C.byref(n)),
+          "bond_workspace_size")
+    return n.value
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def stream_handle(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class BondUpdater:
+    """Holds the workspace and output buffers for repeated updates of one shape.
+
+    Inputs are torch CUDA tensors of the precision's dtype (complex128 for c128,
+    complex64 otherwise); ``gate`` is a complex128 CUDA tensor (d^2, d^2).
+    """
+
+    def __init__(self, precision, chi_l, d, chi_m, chi_r, trunc, xi_kind=1, theta_given=False,
+                 device="cuda"):
+        import torch
+        self.torch = torch
+        self.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
+        self.dtype = torch.complex128 if self.precision == C128 else torch.complex64
+        self.dims = (chi_l, d, chi_m, chi_r)
+        self.trunc = trunc
+        self.xi_kind = xi_kind
+        self.theta_given = theta_given
+        nbytes = bond_workspace_size(self.precision, chi_l, d, chi_m, chi_r, trunc, xi_kind, theta_given)
+        self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+        eta = self.eta_bound()
+        self.bm_out = torch.empty(chi_l * d * eta, dtype=self.dtype, device=device)
+        self.xi_out = torch.empty(eta * eta, dtype=self.dtype, device=device)
+        self.bn_out = torch.empty(eta * d * chi_r, dtype=self.dtype, device=device)
+        self.stats = torch.zeros(4, dtype=torch.float64, device=device)
+        self.schmidt = torch.zeros(max(eta, 1), dtype=torch.float64, device=device)
+
+    def eta_bound(self):
+        chi_l, d, chi_m, chi_r = self.dims
+        t = self.trunc
+        cap = min(d * chi_l, d * chi_r)
+        if t.eta > 0:
+            return min(t.eta, cap)
+        if t.scheme == PLAIN:
+            return min(t.chi_max, cap)
+        import math
+        dchi = max(t.dchi_min, int(math.ceil(t.dchi_frac * chi_m - 1e-9)))
+        return min(chi_m + dchi, cap)
+
+    def run(self, gate, bn, theta=None, bm=None, xi=None, stream=None):
+        """Enqueue one update; returns BondInfo (eta, chi_new). Outputs stay in this object."""
+        chi_l, d, chi_m, chi_r = self.dims
+        io = BondIO()
+        io.precision = self.precision
+        io.chi_l, io.d, io.chi_m, io.chi_r = chi_l, d, chi_m, chi_r
+        io.xi_kind = self.xi_kind if xi is not None else 0
+        io.xi = _ptr(xi)
+        io.bm = _ptr(bm)
+        io.bn = _ptr(bn)
+        io.theta = _ptr(theta)
+        io.gate = _ptr(gate)
+        io.bm_out = _ptr(self.bm_out)
+        io.xi_out = _ptr(self.xi_out)
+        io.bn_out = _ptr(self.bn_out)
+        io.stats_out = _ptr(self.stats)
+        io.schmidt_out = _ptr(self.schmidt)
+        io.workspace = _ptr(self.workspace)
+        io.workspace_bytes = self.workspace.numel()
+        info = BondInfo()
+        check(_lib.qrtebd_bond_update(C.byref(io), C.byref(self.trunc), stream_handle(stream),
+                                      C.byref(info)), "bond_update")
+        self.info = info
+        return info
+
+    def outputs(self):
+        """(Bm_new (chi_l, d, c), Xi_new (c, c), Bn_new (c, d, chi_r), stats) as torch views."""
+        chi_l, d, chi_m, chi_r = self.dims
+        c = self.info.chi_new
+        return (self.bm_out[: chi_l * d * c].view(chi_l, d, c),
+                self.xi_out[: c * c].view(c, c),
+                self.bn_out[: c * d * chi_r].view(c, d, chi_r),
+                self.stats)
+
+
+PROF_TC_GEMM, PROF_QR_PANEL, PROF_SIMT_GEMM, PROF_PREP, PROF_GATE = 0, 1, 2, 3, 4
+
+
+def launch_count():
+    return int(_lib.qrtebd_launch_count())
+
+
+def profile_enable(on=True):
+    check(_lib.qrtebd_profile_enable(1 if on else 0), "profile_enable")
+
+
+def profile_read(family):
+    """(total_ms, launches, flops, bytes) of one kernel family since profile_enable."""
+    t, f, b = C.c_double(0), C.c_double(0), C.c_double(0)
+    n = C.c_longlong(0)
+    check(_lib.qrtebd_profile_read(family, C.byref(t), C.byref(n), C.byref(f), C.byref(b)),
+          "profile_read")
+    return t.value, n.value, f.value, b.value
+
+
+def stream_check(stream=None):
+    check(_lib.qrtebd_stream_check(stream_handle(stream)), "stream_check")
+
+
+def zgemm(precision, A, B, conj_a=False, conj_b=False, trans_a=False, trans_b=False,
+          alpha=1.0, beta=0.0, C_out=None, stream=None):
+    """C = alpha op(A) op(B) + beta C for 2-D torch CUDA tensors (row-major, contiguous)."""
+    import torch
+    prec = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
+    m = A.shape[1] if trans_a else A.shape[0]
+    k = A.shape[0] if trans_a else A.shape[1]
+    n = B.shape[0] if trans_b else B.shape[1]
+    sam, sak = (1, A.shape[1]) if trans_a else (A.shape[1], 1)
+    sbk, sbn = (1, B.shape[1]) if trans_b else (B.shape[1], 1)
+    if C_out is None:
+        C_out = torch.zeros(m, n, dtype=A.dtype, device=A.device)
+    ws = None
+    nb = 0
+    if prec in (C64_3XTF32, C64_TF32):
+        nb = _lib.qrtebd_zgemm_workspace_size(m, n, k)
+        ws = torch.empty(nb, dtype=torch.uint8, device=A.device)
+    al = (C.c_double * 2)(complex(alpha).real, complex(alpha).imag)
+    be = (C.c_double * 2)(complex(beta).real, complex(beta).imag)
+    check(_lib.qrtebd_zgemm(prec, m, n, k, _ptr(A), sam, sak, int(conj_a), _ptr(B), sbk, sbn,
+                            int(conj_b), _ptr(C_out), C_out.shape[1], 1, al, be, _ptr(ws), nb,
+                            stream_handle(stream)), "zgemm")
+    return C_out
+
+
+class MpsDesc(C.Structure):
+    _fields_ = [("L", C.c_int), ("d", C.c_int), ("infinite", C.c_int), ("chi_max", C.c_int),
+                ("precision", C.c_int), ("product_state", C.c_void_p)]
+
+
+def _mps_sigs():
+    P, I, D = C.c_void_p, C.c_int, C.c_double
+    PP = C.POINTER(C.c_void_p)
+    sig = {
+        "qrtebd_mps_create": (I, [C.POINTER(MpsDesc), P, PP]),
+        "qrtebd_mps_destroy": (I, [P]),
+        "qrtebd_apply_gate_layer": (I, [P, I, C.POINTER(D), C.POINTER(Trunc), C.POINTER(D)]),
+        "qrtebd_expectation": (I, [P, I, I, C.POINTER(D), C.POINTER(D)]),
+        "qrtebd_truncation_error": (I, [P, I, C.POINTER(D)]),
+        "qrtebd_schmidt": (I, [P, I, C.POINTER(D), I, C.POINTER(I)]),
+        "qrtebd_bond_dims": (I, [P, C.POINTER(I), I, C.POINTER(I)]),
+        "qrtebd_sync": (I, [P]),
+        "qrtebd_mps_save": (I, [P, C.c_char_p]),
+        "qrtebd_mps_load": (I, [C.c_char_p, P, PP]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(_lib, name)
+        f.restype = res
+        f.argtypes = args
+
+
+_mps_sigs()
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class MPS:
+    """Device-resident MPS (qrtebd_mps_*). Gates and operators are complex128 numpy arrays."""
+
+    def __init__(self, L, d, chi_max, precision="c128", infinite=False, product_state=None,
+                 stream=None, _handle=None):
+        self.L, self.d, self.infinite = L, d, bool(infinite)
+        self.stream = stream
+        if _handle is not None:
+            self.h = _handle
+            return
+        prec = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
+        self._ps = None
+        if product_state is not None:
+            self._ps = np.ascontiguousarray(np.asarray(product_state, np.complex128).reshape(L, d))
+        desc = MpsDesc(L, d, 1 if infinite else 0, chi_max, prec,
+                       None if self._ps is None else self._ps.ctypes.data)
+        h = C.c_void_p()
+        check(_lib.qrtebd_mps_create(C.byref(desc), stream_handle(stream), C.byref(h)), "mps_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.qrtebd_mps_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nbonds(self):
+        return self.L if self.infinite else self.L - 1
+
+    def apply_layer(self, parity, gates, trunc, want_eps=False):
+        g = np.ascontiguousarray(np.asarray(gates, np.complex128).reshape(self.nbonds, -1))
+        eps = np.zeros(self.nbonds) if want_eps else None
+        check(_lib.qrtebd_apply_gate_layer(self.h, parity, _dptr(g.view(np.float64)), C.byref(trunc),
+                                           None if eps is None else _dptr(eps)), "apply_gate_layer")
+        return eps
+
+    def expectation(self, site, op):
+        op = np.ascontiguousarray(np.asarray(op, np.complex128))
+        ns = 1 if op.shape[0] == self.d else 2
+        out = np.zeros(2)
+        check(_lib.qrtebd_expectation(self.h, site, ns, _dptr(op.view(np.float64)), _dptr(out)),
+              "expectation")
+        return complex(out[0], out[1])
+
+    def truncation_error(self, bond=-1):
+        out = C.c_double(0)
+        check(_lib.qrtebd_truncation_error(self.h, bond, C.byref(out)), "truncation_error")
+        return out.value
+
+    def bond_dims(self):
+        buf = (C.c_int * (self.L + 1))()
+        n = C.c_int(0)
+        check(_lib.qrtebd_bond_dims(self.h, buf, self.L + 1, C.byref(n)), "bond_dims")
+        return list(buf[: n.value])
+
+    def schmidt(self, bond):
+        cap = max(self.bond_dims())
+        S = np.zeros(cap)
+        n = C.c_int(0)
+        check(_lib.qrtebd_schmidt(self.h, bond, _dptr(S), cap, C.byref(n)), "schmidt")
+        return S[: n.value]
+
+    def entropy(self, bond):
+        s = self.schmidt(bond)
+        p = s ** 2
+        p = p[p > 1e-300]
+        return float(-(p * np.log(p)).sum())
+
+    def sync(self):
+        check(_lib.qrtebd_sync(self.h), "sync")
+
+    def save(self, path):
+        check(_lib.qrtebd_mps_save(self.h, str(path).encode()), "mps_save")
+
+    @classmethod
+    def load(cls, path, stream=None):
+        h = C.c_void_p()
+        check(_lib.qrtebd_mps_load(str(path).encode(), stream_handle(stream), C.byref(h)), "mps_load")
+        # shape information is read back through bond_dims
+        import struct
+        with open(path, "rb") as f:
+            _, L, d, inf, _chi, _prec = struct.unpack("6i", f.read(24))
+        obj = cls.__new__(cls)
+        obj.h = h
+        obj.stream = stream
+        obj.L, obj.d, obj.infinite = L, d, bool(inf)
+        return obj
+
+
+def clock_layer_gates(L, d, g, tau, infinite=False):
+    """Gates of every bond (library clock-model builder), shape (nbonds, d^2, d^2)."""
+    nb = L if infinite else L - 1
+    out = np.zeros((nb, d * d, d * d), np.complex128)
+    for b in range(nb):
+        if infinite:
+            wl = wr = 0.5
+        else:
+            wl = 1.0 if b == 0 else 0.5
+            wr = 1.0 if b == L - 2 else 0.5
+        out[b] = clock_bond_gate(d, g, wl, wr, tau)
+    return out
+
+
+def tebd_step(mps, half, full, trunc):
+    """Strang step even(dt/2), odd(dt), even(dt/2) (Fig. 2a)."""
+    mps.apply_layer(0, half, trunc)
+    mps.apply_layer(1, full, trunc)
+    mps.apply_layer(0, half, trunc)

@@ -1,0 +1,65 @@
+"""The C-ABI library loads and exports every symbol include/qrtebd.h declares (no GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import clock
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "qrtebd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qrtebd_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2212_09782_b300 import lib
+    return lib
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared_functions()
+    assert len(names) >= 8
+    so = ctypes.CDLL(L.LIB_PATH)
+    missing = [n for n in names if not hasattr(so, n)]
+    assert not missing, missing
+
+
+def test_version_and_strerror(L):
+    assert "qrtebd" in L.version()
+    assert L.strerror(0) == "ok"
+    assert L.strerror(L.ERR_TIMEOUT) == "bounded wait expired"
+
+
+def test_trunc_defaults(L):
+    t = L.trunc_default(L.CBE, 1024)
+    assert (t.scheme, t.chi_max, t.eta, t.dchi_min) == (L.CBE, 1024, 0, 100)
+    assert t.dchi_frac == 0.1 and t.svd_min == 1e-14
+
+
+def test_workspace_size_query_needs_no_gpu(L):
+    t = L.trunc_default(L.PLAIN, 1024)
+    n64 = L.bond_workspace_size(L.C64_3XTF32, 1024, 5, 1024, 1024, t, xi_kind=0, theta_given=True)
+    n128 = L.bond_workspace_size(L.C128, 1024, 5, 1024, 1024, t, xi_kind=0, theta_given=True)
+    assert n64 > 5120 * 5120 * 8 and n128 > 5120 * 5120 * 16
+    with pytest.raises(L.QrtebdError):  # eta larger than d * chi
+        L.bond_workspace_size(L.C128, 2, 2, 2, 2, L.trunc_default(L.PLAIN, 100, eta=50))
+
+
+@pytest.mark.parametrize("d,g,wl,wr,tau", [(2, 1.0, 0.5, 0.5, 0.05), (3, 1.5, 1.0, 0.5, 0.025),
+                                           (5, 2.0, 0.5, 1.0, 0.01), (4, 0.7, 0.5, 0.5, -0.3j)])
+def test_clock_gate_matches_oracle(L, d, g, wl, wr, tau):
+    U = L.clock_bond_gate(d, g, wl, wr, tau)
+    Uo = clock.trotter_gate(clock.bond_hamiltonian(d, g, wl, wr), tau)
+    assert np.abs(U - Uo).max() < 1e-12
+
+
+def test_invalid_arguments_rejected(L):
+    with pytest.raises(L.QrtebdError):
+        L.clock_bond_gate(1, 1.0, 0.5, 0.5, 0.1)

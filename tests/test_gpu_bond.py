@@ -1,0 +1,145 @@
+"""GPU parity: the CUDA bond update against the oracle on the same seeded inputs.
+
+Compared quantities are gauge invariant (Sec. II: the isometric form leaves a
+unitary freedom on the new bond): the Schmidt values of Xi~, the projector
+B~^n^dag B~^n, the block B~^m B~^n, (Xi~ B~^n)^dag (Xi~ B~^n), and eps.
+"""
+import numpy as np
+import pytest
+
+from oracle import bond
+from paper_2212_09782_b300 import workloads as W
+from tests.gpu_helpers import TOL, compare, rounded, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["c128", "c64_fp32", "c64_3xtf32", "c64_tf32"]
+
+
+def _case(dims, seed, xi, prec):
+    chiL, d, chiM, chiR = dims
+    bd = W.random_bond(chiL, d, chiM, chiR, seed=seed, xi=xi)
+    return {k: rounded(v, prec) if k != "U" else v for k, v in bd.items()}
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("dims,xi", [
+    ((4, 3, 4, 4), "dense"),
+    ((16, 5, 16, 16), "dense"),
+    ((33, 3, 33, 33), "diag"),      # ragged: dchi = 99
+    ((48, 5, 48, 48), "eye"),       # two QR panels, cluster of 2
+    ((100, 3, 100, 100), "dense"),
+    ((130, 4, 130, 130), "diag"),   # dchi = 520: several tensor-core tiles, ragged tail
+])
+def test_plain_truncating(prec, dims, xi):
+    bd = _case(dims, seed=sum(dims) * 7 + len(xi), xi=xi, prec=prec)
+    chiM = dims[2]
+    tr_o = dict(scheme="plain", chi_max=chiM)
+    orc = bond.qr_update(bd["Xi"], bd["Bm"], bd["Bn"], bd["U"], **tr_o)
+    from paper_2212_09782_b300 import lib as L
+    t = L.trunc_default(L.PLAIN, chiM)
+    xk = {"dense": 1, "diag": 2, "eye": 1}[xi]
+    gpu = run_gpu(prec, bd["Xi"], bd["Bm"], bd["Bn"], bd["U"], t, xi_kind=xk)
+    assert gpu["eta"] == orc["eta"] == chiM
+    compare(gpu, orc, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64_3xtf32"])
+def test_identity_xi_and_theta_given(prec):
+    # the C2 form: theta' supplied, Xi = 1
+    r = W.rng(11)
+    chi, d = 64, 5
+    th = W.complex_gaussian(r, (chi, d, d, chi))
+    th = rounded(th / np.linalg.norm(th), prec)
+    U = W.random_unitary(r, d * d)
+    Bn = rounded(W.random_right_isometry(r, chi, d, chi), prec)
+    orc = bond.qr_update(None, None, Bn, U, chi_max=chi, theta=th)
+    from paper_2212_09782_b300 import lib as L
+    gpu = run_gpu(prec, None, None, Bn, U, L.trunc_default(L.PLAIN, chi), theta=th)
+    compare(gpu, orc, TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64_3xtf32"])
+@pytest.mark.parametrize("dims", [(8, 3, 5, 8), (1, 2, 1, 1), (2, 4, 3, 5)])
+def test_plain_slice_guess(prec, dims):
+    # eta != chi_m: Y0 is the first eta rows of theta~ (Sec. II last paragraph)
+    chiL, d, chiM, chiR = dims
+    bd = _case(dims, seed=77 + sum(dims), xi="dense", prec=prec)
+    chi_max = 16
+    orc = bond.qr_update(bd["Xi"], bd["Bm"], bd["Bn"], bd["U"], chi_max=chi_max)
+    from paper_2212_09782_b300 import lib as L
+    gpu = run_gpu(prec, bd["Xi"], bd["Bm"], bd["Bn"], bd["U"], L.trunc_default(L.PLAIN, chi_max))
+    assert gpu["eta"] == orc["eta"]
+    keys = ("s", "BB", "G")
+    rank = np.linalg.matrix_rank(orc["theta_t"].reshape(chiL * d, -1))
+    if rank >= orc["eta"]:
+        keys = keys + ("P",)
+    compare(gpu, orc, TOL[prec], keys=keys)
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64_3xtf32", "c64_fp32"])
+@pytest.mark.parametrize("dims", [(6, 3, 6, 6), (20, 4, 24, 20), (40, 3, 37, 45)])
+def test_cbe(prec, dims):
+    chiL, d, chiM, chiR = dims
+    bd = _case(dims, seed=500 + sum(dims), xi="diag", prec=prec)
+    chi_max = max(chiM - 2, 1)
+    kw = dict(dchi_min=4, dchi_frac=0.1)
+    orc = bond.qr_update(bd["Xi"], bd["Bm"], bd["Bn"], bd["U"], scheme="cbe", chi_max=chi_max, **kw)
+    from paper_2212_09782_b300 import lib as L
+    t = L.trunc_default(L.CBE, chi_max, dchi_min=4, dchi_frac=0.1)
+    gpu = run_gpu(prec, bd["Xi"], bd["Bm"], bd["Bn"], bd["U"], t, xi_kind=2)
+    assert gpu["eta"] == orc["eta"]
+    assert gpu["chi_new"] == orc["chi_new"]
+    S = orc["S"]
+    k = S >= 1e-6 * S[0]
+    assert np.allclose(gpu["S"][: len(S)][k], S[k], rtol=TOL[prec] * 10, atol=0)
+    # Xi~ diagonal, positive, descending (canonical form)
+    x = gpu["Xi_new"]
+    assert np.abs(x - np.diag(np.diag(x))).max() < 1e-6
+    compare(gpu, orc, TOL[prec] * 10 if prec != "c128" else TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64_3xtf32"])
+def test_exact_when_eta_covers_rank(prec):
+    # Sec. II / III: eta >= rank theta~ reproduces theta~: eps ~ 0, Xi B~^m B~^n = theta~
+    r = W.rng(5)
+    chiL, d, chiR, rank = 10, 3, 12, 6
+    T0 = W.complex_gaussian(r, (chiL * d, rank)) @ W.complex_gaussian(r, (rank, d * chiR))
+    T0 = (T0 / np.linalg.norm(T0)).reshape(chiL, d, d, chiR)
+    U = W.random_unitary(r, d * d)
+    th = rounded(bond.apply_gate(U.conj().T, T0), prec)
+    Bn = rounded(W.random_right_isometry(r, 4, d, chiR), prec)
+    from paper_2212_09782_b300 import lib as L
+    gpu = run_gpu(prec, None, None, Bn, U, L.trunc_default(L.CBE, 100, dchi_min=0, eta=8),
+                  theta=th)
+    assert gpu["chi_new"] == rank
+    assert gpu["eps"] < (1e-20 if prec == "c128" else 1e-6)
+
+
+def test_c2_full_size_against_oracle():
+    """The bench workload (chi = 1024, d = 5, complex64 3xTF32) against the full oracle."""
+    import torch
+    from paper_2212_09782_b300 import lib as L
+    wl = W.bond_microbench(1024, 5)
+    th = wl["theta"].astype(np.complex128)
+    Bn = wl["Bn"].astype(np.complex128)
+    U = wl["U"]
+    orc = bond.qr_update(None, None, Bn, U, chi_max=1024, theta=th)
+    gpu = run_gpu("c64_3xtf32", None, None, Bn, U, L.trunc_default(L.PLAIN, 1024), theta=th)
+    s_g = np.linalg.svd(gpu["Xi_new"], compute_uv=False)
+    s_o = np.linalg.svd(orc["Xi_new"], compute_uv=False)
+    assert np.linalg.norm(s_g - s_o) / np.linalg.norm(s_o) < 1e-5
+    assert abs(gpu["eps"] - orc["eps"]) / orc["eps"] < 1e-5
+    # principal angles between the GPU and oracle right spaces: all cosines ~ 1
+    Bg = gpu["Bn_new"].reshape(1024, -1)
+    Bo = orc["Bn_new"].reshape(1024, -1)
+    cosines = np.linalg.svd(Bg @ Bo.conj().T, compute_uv=False)
+    assert 1 - cosines.min() < 1e-5
+    # B~^m B~^n applied to random probes
+    r = W.rng(9)
+    v = W.complex_gaussian(r, (Bg.shape[1], 8))
+    bm_g = gpu["Bm_new"].reshape(-1, 1024)
+    bm_o = orc["Bm_new"].reshape(-1, 1024)
+    a, b = bm_g @ (Bg @ v), bm_o @ (Bo @ v)
+    assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-5
+    torch.cuda.synchronize()

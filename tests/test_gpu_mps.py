@@ -1,0 +1,114 @@
+"""GPU parity of the TEBD driver (qrtebd_mps_* / apply_gate_layer / expectation /
+truncation_error) against the oracle's driver on the same gates."""
+import numpy as np
+import pytest
+
+from oracle import bond as obond
+from oracle import clock, mps as omps
+
+pytestmark = pytest.mark.gpu
+
+
+def run_both(L, d, g, dt, steps, chi_max, scheme, prec, infinite=False, dchi_min=100):
+    from paper_2212_09782_b300 import lib as Lb
+    Z, X = clock.clock_operators(d)
+    # oracle
+    o = omps.product_state(L, d, 0, finite=not infinite)
+    half, full = omps.strang_gates(L, d, g, dt, finite=not infinite)
+    kw = dict(scheme=scheme, chi_max=chi_max, dchi_min=dchi_min)
+    # GPU, gates from the library's own clock-model builder
+    s = Lb.MPS(L, d, chi_max, precision=prec, infinite=infinite)
+    gh = Lb.clock_layer_gates(L, d, g, dt / 2, infinite)
+    gf = Lb.clock_layer_gates(L, d, g, dt, infinite)
+    tr = Lb.trunc_default(Lb.CBE if scheme == "cbe" else Lb.PLAIN, chi_max, dchi_min=dchi_min)
+    zo, zg = [], []
+    for _ in range(steps):
+        omps.tebd_step(o, half, full, **kw)
+        Lb.tebd_step(s, gh, gf, tr)
+        zo.append([omps.expectation_1site(o, m, Z) for m in range(L)])
+        zg.append([s.expectation(m, Z) for m in range(L)])
+    s.sync()
+    return o, s, np.array(zo), np.array(zg)
+
+
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-10), ("c64_3xtf32", 1e-5)])
+def test_c1_finite_plain(prec, tol):
+    # L=16, d=3 clock model, g=1.5, |0...0>, Strang dt=0.05, chi_max=32, plain QR
+    L, d, g, dt, steps, chi = 16, 3, 1.5, 0.05, 20, 32
+    o, s, zo, zg = run_both(L, d, g, dt, steps, chi, "plain", prec)
+    assert np.abs(zg - zo).max() < tol
+    assert s.bond_dims() == o.bond_dims()
+    eo = o.eps_sum
+    eg = s.truncation_error(-1)
+    assert abs(eg - eo) <= max(tol * eo, 1e-7 if prec != "c128" else 1e-14)
+    for b in (4, 8, 12):
+        Sg = s.schmidt(b)
+        So = obond.schmidt_values(o.Xi[b])
+        So = So / np.linalg.norm(So)
+        k = So > 1e-6
+        assert np.abs(Sg[: len(So)][k] - So[k]).max() < tol * 10
+
+
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-10), ("c64_3xtf32", 1e-5)])
+def test_finite_cbe(prec, tol):
+    L, d, g, dt, steps, chi = 10, 3, 1.5, 0.05, 8, 16
+    o, s, zo, zg = run_both(L, d, g, dt, steps, chi, "cbe", prec)
+    assert np.abs(zg - zo).max() < tol
+    assert s.bond_dims() == o.bond_dims()
+    Sg = s.schmidt(5)
+    So = np.diag(o.Xi[5]).real
+    assert np.abs(Sg - So / np.linalg.norm(So)).max() < tol * 10
+
+
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-10), ("c64_3xtf32", 1e-5)])
+def test_uniform_cbe(prec, tol):
+    d, g, dt, steps, chi = 3, 2.0, 0.05, 10, 24
+    o, s, zo, zg = run_both(2, d, g, dt, steps, chi, "cbe", prec, infinite=True)
+    assert np.abs(zg - zo).max() < tol
+    h = clock.bond_hamiltonian(d, g)
+    assert abs(s.expectation(0, h) - omps.expectation_2site(o, 0, h)) < tol * 10
+
+
+def test_two_site_energy_and_exact_statevector():
+    # no truncation (chi_max >= 3^(L/2)): matches the Trotterised state vector
+    from oracle import exact
+    from paper_2212_09782_b300 import lib as Lb
+    L, d, g, dt, steps = 8, 3, 1.5, 0.05, 6
+    s = Lb.MPS(L, d, 81, precision="c128")
+    gh = Lb.clock_layer_gates(L, d, g, dt / 2)
+    gf = Lb.clock_layer_gates(L, d, g, dt)
+    tr = Lb.trunc_default(Lb.PLAIN, 81)
+    for _ in range(steps):
+        Lb.tebd_step(s, gh, gf, tr)
+    psi = exact.trotter_statevector(exact.product_vector(L, d), L, d, g, dt, steps)
+    Z, X = clock.clock_operators(d)
+    for m in range(L):
+        assert abs(s.expectation(m, Z) - exact.local_expectation(psi, L, d, m, Z)) < 1e-11
+    E = sum(s.expectation(m, clock.bond_hamiltonian(d, g, wl, wr))
+            for m, (wl, wr) in enumerate(clock.field_weights(L, True)))
+    assert abs(E - exact.energy(psi, L, d, g)) < 1e-10
+    assert s.truncation_error(-1) < 1e-12
+
+
+def test_checkpoint_resume_bit_exact(tmp_path):
+    from paper_2212_09782_b300 import lib as Lb
+    L, d, g, dt, chi = 8, 3, 1.5, 0.05, 12
+    gh = Lb.clock_layer_gates(L, d, g, dt / 2)
+    gf = Lb.clock_layer_gates(L, d, g, dt)
+    tr = Lb.trunc_default(Lb.CBE, chi, dchi_min=4)
+    Z, _ = clock.clock_operators(d)
+    a = Lb.MPS(L, d, chi, precision="c64_3xtf32")
+    for _ in range(3):
+        Lb.tebd_step(a, gh, gf, tr)
+    path = tmp_path / "state.qrtebd"
+    a.save(path)
+    for _ in range(3):
+        Lb.tebd_step(a, gh, gf, tr)
+    b = Lb.MPS.load(path)
+    for _ in range(3):
+        Lb.tebd_step(b, gh, gf, tr)
+    za = [a.expectation(m, Z) for m in range(L)]
+    zb = [b.expectation(m, Z) for m in range(L)]
+    assert za == zb
+    assert a.truncation_error(-1) == b.truncation_error(-1)
+    assert a.bond_dims() == b.bond_dims()
