@@ -67,6 +67,10 @@ typedef struct qrtebd_trunc {
   double dchi_frac; /* CBE: relative expansion per update (Sec. III: about 0.1) */
   double svd_min;   /* CBE: drop Schmidt values below svd_min * ||S|| (Fig. 4: 1e-14) */
   double tie_tol;   /* CBE: never cut inside a multiplet closer than tie_tol * S_1 */
+  int eps_explicit; /* 0: eps = 1 - kept / ||theta~||^2 (FP64 norms; exact for the orthogonal
+                       projections of Sec. II, but with a floor of about the storage precision,
+                       ~1e-7 in complex64); 1: eps from the explicit residual
+                       ||theta~ - approx||^2 (one more contraction; the distance of Sec. IV) */
 } qrtebd_trunc;
 /* eta policy (Sec. II last paragraph, Sec. III):
  *   PLAIN: eta = min(chi_max, d chi_l, d chi_r); initial guess Y0 = B^n if
@@ -209,6 +213,19 @@ int qrtebd_zgemm(int precision, int m, int n, int k, const void* A, long long sa
                  long long scm, long long scn, const double* alpha, const double* beta,
                  void* workspace, size_t workspace_bytes, void* stream);
 size_t qrtebd_zgemm_workspace_size(int m, int n, int k);
+
+/* ------------------------------------------------------------- Householder QR */
+/* A = Q R for a device matrix A (m x n, m >= n, row-major, leading dimension lda, in the
+ * precision's storage type): the factorisation of Sec. II (i) (and, applied to Y^dag,
+ * the LQ of step (ii)). On return A holds R in its upper n x n triangle (real
+ * diagonal, LAPACK geqrf sign convention) and zeros below; Q (m x n, ldq) holds the
+ * explicit isometry. Blocked Householder: thread-block-cluster panels with FP64
+ * reflector norms, compact-WY trailing updates. workspace: device, at least
+ * qrtebd_qr_workspace_size bytes. Enqueued on `stream`. INVALID_ARG if m < n, n < 1
+ * or the panel does not fit shared memory. */
+int qrtebd_householder_qr(int precision, int m, int n, void* A, long long lda, void* Q,
+                          long long ldq, void* workspace, size_t workspace_bytes, void* stream);
+size_t qrtebd_qr_workspace_size(int precision, int m, int n);
 
 /* ------------------------------------------------------------- clock model */
 /* Host-only: the clock-model bond gate U = exp(-i tau h_b) (Sec. IV, Eqs. 2-3) with

@@ -111,6 +111,12 @@ __global__ void k_finalize(const double* th2, const double* kept, double chi_new
   scal[0] = k > 0 ? 1.0 / sqrt(k) : 0.0;
 }
 
+// explicit eps = ||theta~ - approx||^2 / ||theta~||^2 overrides stats[0]
+__global__ void k_eps_explicit(const double* th2, const double* r2, double* stats) {
+  double t = *th2;
+  stats[0] = t > 0 ? *r2 / t : 0.0;
+}
+
 // out[j][i] = s * conj(in[i][j]) for i < rows, j < cols (in: ld_in, out: ld_out)
 template <typename T>
 __global__ void k_conj_transpose(const cx<T>* in, long long ld_in, cx<T>* out, long long ld_out,
@@ -274,6 +280,9 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
   size_t simt_elems = std::max(gemm_simt_scratch_elems((int)mL, eta, (int)nR, 1),
                                gemm_simt_scratch_elems((int)nR, eta, (int)mL, 1));
   simt_elems = std::max(simt_elems, gemm_simt_scratch_elems(chiL, (int)(d * nR), chiL, 1));
+  // block-reflector contractions of the QR (kb x n with K = m, and smaller)
+  for (int kb = 1; kb <= 128; kb *= 2)
+    simt_elems = std::max(simt_elems, gemm_simt_scratch_elems(kb, eta, (int)std::max(mL, nR), 1));
   cx<T>* simt_scratch = simt_elems ? ar.take<cx<T>>(simt_elems) : nullptr;
   // CBE: eigen-decomposition buffers (FP64)
   double2* M = nullptr; double2* Vh = nullptr; double* w = nullptr; double2* eig_scr = nullptr;
@@ -290,6 +299,11 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
     Bn_full = ar.take<cx<T>>((size_t)eta * nR);
     chi_dev = ar.take<int>(4);
   }
+  const bool eps_explicit = tr->eps_explicit != 0;
+  cx<T>* Rbuf = eps_explicit ? ar.take<cx<T>>((size_t)mL * nR) : nullptr;
+  cx<T>* Zc = (eps_explicit && !cbe) ? ar.take<cx<T>>((size_t)nR * eta) : nullptr;
+  cx<T>* LV = (eps_explicit && cbe) ? ar.take<cx<T>>((size_t)eta * eta) : nullptr;
+  cx<T>* Yt = (eps_explicit && cbe) ? ar.take<cx<T>>((size_t)eta * nR) : nullptr;
   TcWorkspace tcw;
   if (use_tc) tc_carve(ar, (int)std::max(mL, nR), (int)std::max(mL, nR), eta, tcw);
 
@@ -346,6 +360,7 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
   {
     GemmArgs<T> g{(int)mL, eta, (int)nR, theta_t, nR, 1, false, Y0, 1, nR, true, X, eta, 1, one,
                   zero};
+    g.reuse_a = true;  // theta~ is read again, unchanged, by the last contraction
     QR_TRY(runner.run(g, st));
   }
   QR_TRY(householder_qr<T>(X, eta, (int)mL, eta, Q, eta, qs, st, err, &qg));
@@ -356,6 +371,7 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
                   zero};
     QR_TRY(runner.run(g, st));
   }
+  if (Zc) QR_CUDA_TRY(cudaMemcpyAsync(Zc, Z, (size_t)nR * eta * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st));
   QR_TRY(householder_qr<T>(Z, eta, (int)nR, eta, Qz, eta, qs, st, err, &qg));
 
   cx<T>* bn_out = static_cast<cx<T>*>(io->bn_out);
@@ -373,7 +389,19 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
     QR_TRY(conj_transpose<T>(Qz, eta, bn_out, nR, (int)nR, eta, nullptr, st));
     GemmArgs<T> g{(int)mL, eta, (int)nR, theta_tp, nR, 1, false, Qz, eta, 1, false, bm_out, eta,
                   1, one, zero};
+    g.reuse_a = true;
     QR_TRY(runner.run(g, st));
+    if (eps_explicit) {
+      // residual theta~ - Q Y with Y = Zc^dag (Sec. IV: the explicit distance)
+      QR_CUDA_TRY(cudaMemcpyAsync(Rbuf, theta_t, (size_t)mL * nR * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st));
+      GemmArgs<T> r{(int)mL, (int)nR, eta, Q, eta, 1, false, Zc, 1, eta, true, Rbuf, nR, 1,
+                    mk<T>(-1, 0), one};
+      QR_TRY(runner.run(r, st));
+      QR_TRY(norm2<T>(Rbuf, mL * nR, partial, scal + 3, st));
+      k_eps_explicit<<<1, 1, 0, st>>>(scal + 0, scal + 3, io->stats_out ? io->stats_out : stats_local);
+      note_launch();
+      QR_CUDA_TRY(cudaGetLastError());
+    }
   } else {
     // (iv) M = L^dag L = Rz Rz^dag (FP64), eigen-decomposition
     long long ee = (long long)eta * eta;
@@ -421,6 +449,22 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
       GemmArgs<T> g{(int)mL, chi_new, (int)nR, theta_tp, nR, 1, false, bn_out, 1, nR, true, bm_out,
                     chi_new, 1, one, zero};
       QR_TRY(runner.run(g, st));
+    }
+    if (eps_explicit) {
+      // approx = Q L V_c^dag B~^n; residual theta~ - approx (Sec. IV)
+      GemmArgs<T> g1{eta, chi_new, eta, Z, 1, eta, true, Vt, 1, eta, true, LV, chi_new, 1, one, zero};
+      QR_TRY(runner.run(g1, st));
+      GemmArgs<T> g2{eta, (int)nR, chi_new, LV, chi_new, 1, false, bn_out, nR, 1, false, Yt, nR, 1,
+                     one, zero};
+      QR_TRY(runner.run(g2, st));
+      QR_CUDA_TRY(cudaMemcpyAsync(Rbuf, theta_t, (size_t)mL * nR * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st));
+      GemmArgs<T> r{(int)mL, (int)nR, eta, Q, eta, 1, false, Yt, nR, 1, false, Rbuf, nR, 1,
+                    mk<T>(-1, 0), one};
+      QR_TRY(runner.run(r, st));
+      QR_TRY(norm2<T>(Rbuf, mL * nR, partial, scal + 3, st));
+      k_eps_explicit<<<1, 1, 0, st>>>(scal + 0, scal + 3, io->stats_out ? io->stats_out : stats_local);
+      note_launch();
+      QR_CUDA_TRY(cudaGetLastError());
     }
     (void)Bn_full;
   }

@@ -105,6 +105,39 @@ void herm_jacobi_host(int n, std::vector<zc>& A, std::vector<zc>& V, std::vector
 
 using namespace qrtebd;
 
+namespace qrtebd {
+namespace {
+template <typename T>
+int qr_entry(int precision, int m, int n, void* A, long long lda, void* Q, long long ldq,
+             void* ws, size_t bytes, cudaStream_t st, size_t* need) {
+  Arena ar;
+  ar.measuring = (need != nullptr);
+  if (!need) { ar.base = static_cast<char*>(ws); ar.cap = bytes; }
+  QrScratch<T> qs;
+  qr_carve<T>(ar, m, n, qs);
+  TcWorkspace tcw;
+  const bool tc = std::is_same<T, float>::value &&
+                  (precision == QRTEBD_C64_3XTF32 || precision == QRTEBD_C64_TF32);
+  if (tc) tc_carve(ar, std::max(m, n), m, std::max(m, n), tcw);
+  if (need) { *need = ar.off; return QRTEBD_OK; }
+  if (ar.overflow() || !ws) { set_last_message("qr: workspace too small"); return QRTEBD_ERR_OOM; }
+  struct Ctx { TcWorkspace* w; bool three; bool tc; };
+  Ctx ctx{&tcw, precision == QRTEBD_C64_3XTF32, tc};
+  QrGemm<T> qg;
+  qg.ctx = &ctx;
+  qg.fn = [](const GemmArgs<T>& g, cudaStream_t s, void* c) -> int {
+    Ctx* x = static_cast<Ctx*>(c);
+    if constexpr (std::is_same<T, float>::value) {
+      if (x->tc && tc_gemm_eligible(g)) return tc_gemm(g, x->three, *x->w, s);
+    }
+    return gemm_simt<T>(g, s, nullptr, 0);
+  };
+  return householder_qr<T>(static_cast<cx<T>*>(A), lda, m, n, static_cast<cx<T>*>(Q), ldq, qs, st,
+                           device_error_word(), &qg);
+}
+}  // namespace
+}  // namespace qrtebd
+
 extern "C" {
 
 int qrtebd_trunc_default(qrtebd_trunc* tr, int scheme, int chi_max) {
@@ -116,6 +149,7 @@ int qrtebd_trunc_default(qrtebd_trunc* tr, int scheme, int chi_max) {
   tr->dchi_frac = 0.1;
   tr->svd_min = 1e-14;
   tr->tie_tol = 1e-10;
+  tr->eps_explicit = 0;
   return QRTEBD_OK;
 }
 
@@ -163,7 +197,7 @@ int qrtebd_zgemm(int precision, int m, int n, int k, const void* A, long long sa
   ar.base = static_cast<char*>(workspace);
   ar.cap = workspace_bytes;
   TcWorkspace w;
-  tc_carve(ar, m, k, n, w);
+  tc_carve(ar, std::max(m, n), k, std::max(m, n), w);
   if (ar.overflow() || !workspace) { set_last_message("zgemm: workspace too small"); return QRTEBD_ERR_OOM; }
   return tc_gemm(g, precision == QRTEBD_C64_3XTF32, w, st);
 }
@@ -172,8 +206,29 @@ size_t qrtebd_zgemm_workspace_size(int m, int n, int k) {
   Arena ar;
   ar.measuring = true;
   TcWorkspace w;
-  tc_carve(ar, m, k, n, w);
+  tc_carve(ar, std::max(m, n), k, std::max(m, n), w);
   return ar.off;
+}
+
+
+int qrtebd_householder_qr(int precision, int m, int n, void* A, long long lda, void* Q,
+                          long long ldq, void* workspace, size_t workspace_bytes, void* stream) {
+  if (m < n || n < 1 || !A || !Q || lda < n || ldq < n) return QRTEBD_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (precision == QRTEBD_C128)
+    return qr_entry<double>(precision, m, n, A, lda, Q, ldq, workspace, workspace_bytes, st, nullptr);
+  if (precision < QRTEBD_C128 || precision > QRTEBD_C64_FP32) return QRTEBD_ERR_INVALID_ARG;
+  return qr_entry<float>(precision, m, n, A, lda, Q, ldq, workspace, workspace_bytes, st, nullptr);
+}
+
+size_t qrtebd_qr_workspace_size(int precision, int m, int n) {
+  size_t need = 0;
+  if (m < n || n < 1) return 0;
+  if (precision == QRTEBD_C128)
+    qr_entry<double>(precision, m, n, nullptr, n, nullptr, n, nullptr, 0, nullptr, &need);
+  else
+    qr_entry<float>(precision, m, n, nullptr, n, nullptr, n, nullptr, 0, nullptr, &need);
+  return need;
 }
 
 int qrtebd_clock_bond_gate(int d, double g, double wl, double wr, double tau_re, double tau_im,

@@ -19,6 +19,9 @@ template <typename T> struct GemmArgs {
   cx<T> alpha, beta;
   int batch = 1;
   long long bsa = 0, bsb = 0, bsc = 0;  // batch strides (elements)
+  // tensor-core path only: A is unchanged since an earlier call with the same
+  // pointer, strides and shape in this workspace, so its prepared operand may be reused
+  bool reuse_a = false;
 };
 
 // Enqueue the GEMM. `scratch` (may be null) lets the launcher split K for

@@ -27,7 +27,8 @@ namespace {
 
 constexpr int PT = 256;      // threads per panel CTA
 constexpr int KBMAX = 32;    // widest panel
-constexpr int RED = 2 * KBMAX + 4;
+constexpr int NBO = 128;     // outer block of the two-level blocking
+constexpr int RED = 3 * 16 + 4;  // 3 doubles per cluster rank
 constexpr int SMEM_CAP = 220 * 1024;
 
 template <typename T> struct PanelArgs {
@@ -40,12 +41,13 @@ template <typename T> struct PanelArgs {
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
 
 template <typename T> __host__ __device__ inline size_t panel_fixed_bytes() {
-  return a16(2 * RED * sizeof(double)) + a16(RED * sizeof(double)) +
-         2 * a16(KBMAX * KBMAX * sizeof(double)) + a16(32 * sizeof(double)) +
-         a16(KBMAX * sizeof(cx<T>)) + a16(KBMAX * (KBMAX + 1) * sizeof(cx<T>));
+  return a16(2 * RED * sizeof(double)) + a16(2 * 16 * KBMAX * sizeof(cx<T>)) +
+         2 * a16(KBMAX * sizeof(cx<T>)) + a16(4 * sizeof(cx<T>)) + a16(KBMAX * sizeof(cx<T>)) +
+         a16(KBMAX * (KBMAX + 1) * sizeof(cx<T>));
 }
 template <typename T> __host__ __device__ inline size_t panel_smem_bytes(int rpc, int kb) {
-  return a16((size_t)rpc * (kb + 1) * sizeof(cx<T>)) + panel_fixed_bytes<T>();
+  return a16((size_t)rpc * (kb + 1) * sizeof(cx<T>)) + a16((size_t)rpc * sizeof(cx<T>)) +
+         panel_fixed_bytes<T>();
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -53,7 +55,21 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
+template <typename T> __device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
 
+// Panel kernel. Per column j, two cluster-wide reductions, both push-style (each
+// CTA stores its partial into slot [rank] of every CTA's buffer before the
+// cluster barrier; after it all reads are local):
+//   1. ||x||^2 below the pivot (FP64) and alpha;
+//   2. w_c = v_j^dag P[:, c] for the columns c > j, and g_a = v_a^dag v_j for the
+//      earlier reflectors a < j, which give column j of the compact-WY factor:
+//      T(0:j, j) = -tau_j T(0:j, 0:j) g,  T(j, j) = tau_j.
+// FP64 is used only for the norm and its square root (B300's FP64 pipe is narrow);
+// the reflector scalars use Smith's complex division in the working precision.
 template <typename T>
 __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
   extern __shared__ __align__(16) unsigned char sm[];
@@ -68,182 +84,157 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
 
   unsigned char* q = sm;
   cx<T>* P = reinterpret_cast<cx<T>*>(q); q += a16((size_t)rpc * ldp * sizeof(cx<T>));
+  cx<T>* VV = reinterpret_cast<cx<T>*>(q); q += a16((size_t)rpc * sizeof(cx<T>));
   double* red = reinterpret_cast<double*>(q); q += a16(2 * RED * sizeof(double));
-  double* bc = reinterpret_cast<double*>(q); q += a16(RED * sizeof(double));
-  double* gp_ = reinterpret_cast<double*>(q); q += a16(KBMAX * KBMAX * sizeof(double));
-  double* gsum = reinterpret_cast<double*>(q); q += a16(KBMAX * KBMAX * sizeof(double));
-  double* wsum = reinterpret_cast<double*>(q); q += a16(32 * sizeof(double));
+  cx<T>* redT = reinterpret_cast<cx<T>*>(q); q += a16(2 * 16 * KBMAX * sizeof(cx<T>));
+  cx<T>* wT = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * sizeof(cx<T>));
+  cx<T>* gT = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * sizeof(cx<T>));
+  cx<T>* bc = reinterpret_cast<cx<T>*>(q); q += a16(4 * sizeof(cx<T>));
   cx<T>* taus = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * sizeof(cx<T>));
-  cx<T>* Ts = reinterpret_cast<cx<T>*>(q);
+  cx<T>* Ts = reinterpret_cast<cx<T>*>(q);  // KBMAX x (KBMAX + 1)
 
   const long long k0 = a.k0;
   for (int idx = tid; idx < nloc * kb; idx += PT) {
-    int p = idx / kb, c = idx % kb;
+    const int p = idx / kb, c = idx % kb;
     P[p * ldp + c] = a.A[(k0 + row0 + p) * a.lda + k0 + c];
   }
   __syncthreads();
 
-  int buf = 0;
   for (int j = 0; j < kb; ++j) {
-    // ---- reduction 1: ||x||^2 (rows below the pivot) in FP64, plus alpha
-    double s = 0.0, ar = 0.0, ai = 0.0;
-    for (int p = tid; p < nloc; p += PT) {
-      int g = row0 + p;
-      cx<T> v = P[p * ldp + j];
-      if (g > j) s += (double)v.x * v.x + (double)v.y * v.y;
-      else if (g == j) { ar = v.x; ai = v.y; }
-    }
-    s = warp_sum(s); ar = warp_sum(ar); ai = warp_sum(ai);
-    if (lane == 0) { wsum[warp * 4 + 0] = s; wsum[warp * 4 + 1] = ar; wsum[warp * 4 + 2] = ai; }
-    __syncthreads();
-    if (tid == 0) {
-      double t0 = 0, t1 = 0, t2 = 0;
-      for (int w = 0; w < nwarps; ++w) { t0 += wsum[w * 4]; t1 += wsum[w * 4 + 1]; t2 += wsum[w * 4 + 2]; }
-      red[buf * RED + 0] = t0; red[buf * RED + 1] = t1; red[buf * RED + 2] = t2;
+    const int buf = j & 1;
+    // ---- reduction 1 (warp 0): ||x||^2 below the pivot in FP64, and alpha
+    if (warp == 0) {
+      double s = 0.0;
+      T ar = 0, ai = 0;
+      for (int p = lane; p < nloc; p += 32) {
+        const int g = row0 + p;
+        const cx<T> v = P[p * ldp + j];
+        if (g > j) s = fma((double)v.x, (double)v.x, fma((double)v.y, (double)v.y, s));
+        else if (g == j) { ar = v.x; ai = v.y; }
+      }
+      s = warp_sum(s);
+      ar = warp_sum_t<T>(ar); ai = warp_sum_t<T>(ai);
+      if (lane < CS) {
+        double* dst = cl.map_shared_rank(red, lane) + buf * RED + 3 * rank;
+        dst[0] = s; dst[1] = (double)ar; dst[2] = (double)ai;
+      }
     }
     cl.sync();
-    if (warp == 0) {
-      double t0 = 0, t1 = 0, t2 = 0;
-      if (lane < CS) {
-        const double* r = cl.map_shared_rank(red, lane) + buf * RED;
-        t0 = r[0]; t1 = r[1]; t2 = r[2];
-      }
-      t0 = warp_sum(t0); t1 = warp_sum(t1); t2 = warp_sum(t2);
-      if (lane == 0) { bc[0] = t0; bc[1] = t1; bc[2] = t2; }
-    }
-    __syncthreads();
-    buf ^= 1;
-    const double xn2 = bc[0], alr = bc[1], ali = bc[2];
-    double beta, tr, ti, sr, si;
-    if (xn2 == 0.0 && ali == 0.0) {
-      beta = alr; tr = 0.0; ti = 0.0; sr = 0.0; si = 0.0;
-    } else {
-      beta = -copysign(sqrt(alr * alr + ali * ali + xn2), alr);
-      tr = (beta - alr) / beta; ti = -ali / beta;
-      double dr = alr - beta, di = ali, den = dr * dr + di * di;
-      sr = dr / den; si = -di / den;
-    }
-    if (!isfinite(beta) && tid == 0 && rank == 0) atomicOr(a.err, DEVERR_NUMERIC);
-    const cx<T> scale = mk<T>((T)sr, (T)si);
-    for (int p = tid; p < nloc; p += PT) {
-      int g = row0 + p;
-      if (g > j) P[p * ldp + j] = cmul<T>(P[p * ldp + j], scale);
-      else if (g == j) P[p * ldp + j] = mk<T>((T)beta, (T)0);
-    }
-    if (tid == 0) taus[j] = mk<T>((T)tr, (T)ti);
-    __syncthreads();
-
-    // ---- reduction 2: w_c = sum_{g >= j} conj(v_g) P[g][c], c > j
-    const int nc = kb - j - 1;
-    if (nc > 0) {
-      for (int c = j + 1 + warp; c < kb; c += nwarps) {
-        T wr = 0, wi = 0;
-        for (int p = lane; p < nloc; p += 32) {
-          int g = row0 + p;
-          if (g < j) continue;
-          cx<T> v = (g == j) ? mk<T>(1, 0) : P[p * ldp + j];
-          cx<T> x = P[p * ldp + c];
-          wr += v.x * x.x + v.y * x.y;
-          wi += v.x * x.y - v.y * x.x;
+    if (tid == 0) {
+      double xn2 = 0;
+      T alr = 0, ali = 0;
+      const double* rr = red + buf * RED;
+#pragma unroll 4
+      for (int r = 0; r < CS; ++r) { xn2 += rr[3 * r]; alr += (T)rr[3 * r + 1]; ali += (T)rr[3 * r + 2]; }
+      // zlarfg: beta = -sign(Re alpha) ||(alpha, x)||, tau = (beta - alpha) / beta,
+      // v = x / (alpha - beta)
+      T beta = alr, tr = 0, ti = 0, sr = 0, si = 0;
+      if (!(xn2 == 0.0 && ali == T(0))) {
+        const double nrm = sqrt(fma((double)alr, (double)alr, fma((double)ali, (double)ali, xn2)));
+        beta = (T)(alr >= T(0) ? -nrm : nrm);
+        tr = (beta - alr) / beta;
+        ti = -ali / beta;
+        // scale = 1 / (alpha - beta) by Smith's division (no squares of small numbers)
+        const T dr = alr - beta, di = ali;
+        if (fabs((double)dr) >= fabs((double)di)) {
+          const T rt = di / dr, den = dr + di * rt;
+          sr = T(1) / den; si = -rt / den;
+        } else {
+          const T rt = dr / di, den = di + dr * rt;
+          sr = rt / den; si = T(-1) / den;
         }
-        double dwr = warp_sum((double)wr), dwi = warp_sum((double)wi);
-        if (lane == 0) { red[buf * RED + 2 * (c - j - 1)] = dwr; red[buf * RED + 2 * (c - j - 1) + 1] = dwi; }
+      }
+      if (!(isfinite((double)beta) && isfinite((double)sr) && isfinite((double)si)) && rank == 0)
+        atomicOr(a.err, DEVERR_NUMERIC);
+      bc[0] = mk<T>(beta, 0); bc[1] = mk<T>(tr, ti); bc[2] = mk<T>(sr, si);
+      taus[j] = mk<T>(tr, ti);
+    }
+    __syncthreads();
+    const T beta = bc[0].x;
+    const cx<T> tau = bc[1], scale = bc[2];
+
+    // ---- reduction 2: slots s < nc give w_{j+1+s}; slots s >= nc give g_{s-nc}
+    const int nc = kb - j - 1;
+    const int nslot = nc + j;
+    if (nslot > 0) {
+      for (int sl = warp; sl < nslot; sl += nwarps) {
+        T wr = 0, wi = 0;
+        const bool is_w = sl < nc;
+        const int col = is_w ? j + 1 + sl : sl - nc;
+        for (int p = lane; p < nloc; p += 32) {
+          const int g = row0 + p;
+          if (g < j) continue;
+          const cx<T> v = (g == j) ? mk<T>(1, 0) : cmul<T>(P[p * ldp + j], scale);
+          if (sl == 0) VV[p] = v;  // scaled reflector for the update pass
+          const cx<T> x = P[p * ldp + col];
+          if (is_w) { wr += v.x * x.x + v.y * x.y; wi += v.x * x.y - v.y * x.x; }   // conj(v) x
+          else { wr += x.x * v.x + x.y * v.y; wi += x.x * v.y - x.y * v.x; }        // conj(v_a) v
+        }
+        wr = warp_sum_t<T>(wr); wi = warp_sum_t<T>(wi);
+        if (lane < CS) cl.map_shared_rank(redT, lane)[buf * (KBMAX * 16) + rank * KBMAX + sl] = mk<T>(wr, wi);
       }
       cl.sync();
-      if (tid < nc) {
-        double wr = 0, wi = 0;
-        for (int r = 0; r < CS; ++r) {
-          const double* rr = cl.map_shared_rank(red, r) + buf * RED;
-          wr += rr[2 * tid]; wi += rr[2 * tid + 1];
-        }
-        bc[4 + 2 * tid] = wr; bc[4 + 2 * tid + 1] = wi;
+      if (tid < nslot) {
+        cx<T> w = mk<T>(0, 0);
+        const cx<T>* rr = redT + buf * (KBMAX * 16) + tid;
+#pragma unroll 4
+        for (int r = 0; r < CS; ++r) w = cadd<T>(w, rr[r * KBMAX]);
+        if (tid < nc) wT[tid] = cmul<T>(cconj<T>(tau), w);  // conj(tau) w
+        else gT[tid - nc] = w;
       }
       __syncthreads();
-      buf ^= 1;
-      // P <- (I - conj(tau) v v^dag) P on columns c > j
-      const cx<T> ctau = mk<T>((T)tr, (T)-ti);
-      for (int idx = tid; idx < nloc * nc; idx += PT) {
-        int p = idx / nc, cc = idx % nc;
-        int g = row0 + p;
-        if (g < j) continue;
-        cx<T> v = (g == j) ? mk<T>(1, 0) : P[p * ldp + j];
-        cx<T> w = mk<T>((T)bc[4 + 2 * cc], (T)bc[4 + 2 * cc + 1]);
-        cx<T> t = cmul<T>(ctau, w);
-        P[p * ldp + j + 1 + cc] = csub<T>(P[p * ldp + j + 1 + cc], cmul<T>(v, t));
+      if (warp == 0) {
+        // T(0:j, j) = -tau_j T(0:j, 0:j) g ; T(j, j) = tau_j
+        if (lane < j) {
+          cx<T> acc = mk<T>(0, 0);
+          for (int l = lane; l < j; ++l) cfma<T>(acc, Ts[lane * (KBMAX + 1) + l], gT[l]);
+          const cx<T> r = cmul<T>(tau, acc);
+          Ts[lane * (KBMAX + 1) + j] = mk<T>(-r.x, -r.y);
+        }
+        if (lane == 0) Ts[j * (KBMAX + 1) + j] = tau;
       }
+      // P <- (I - conj(tau) v v^dag) P on columns c > j; column j <- v, pivot <- beta
+      const int ncc = nc + 1;
+      for (int idx = tid; idx < nloc * ncc; idx += PT) {
+        const int p = idx / ncc, cc = idx % ncc;
+        const int g = row0 + p;
+        if (g < j) continue;
+        if (cc == nc) {
+          P[p * ldp + j] = (g > j) ? VV[p] : mk<T>(beta, T(0));
+        } else {
+          const cx<T> v = (g == j) ? mk<T>(1, 0) : VV[p];
+          P[p * ldp + j + 1 + cc] = csub<T>(P[p * ldp + j + 1 + cc], cmul<T>(v, wT[cc]));
+        }
+      }
+      __syncthreads();
+    } else {
+      // kb == 1: single column, no update and T = tau
+      for (int p = tid; p < nloc; p += PT) {
+        const int g = row0 + p;
+        if (g > j) P[p * ldp + j] = cmul<T>(P[p * ldp + j], scale);
+        else if (g == j) P[p * ldp + j] = mk<T>(beta, T(0));
+      }
+      if (tid == 0) Ts[0] = tau;
       __syncthreads();
     }
   }
 
-  // ---- compact-WY T from G = V^dag V (strictly upper part)
-  const int npairs = kb * (kb - 1) / 2;
-  for (int idx = tid; idx < npairs; idx += PT) {
-    int b = (int)((1.0 + sqrt(1.0 + 8.0 * idx)) * 0.5);
-    while (b * (b - 1) / 2 > idx) --b;
-    while ((b + 1) * b / 2 <= idx) ++b;
-    int aa = idx - b * (b - 1) / 2;
-    T gr = 0, gi = 0;
-    for (int p = max(0, b - row0); p < nloc; ++p) {
-      // v_b is zero above row b (and v_a above row a < b)
-      int g = row0 + p;
-      cx<T> va = P[p * ldp + aa];
-      cx<T> vb = (g == b) ? mk<T>(1, 0) : P[p * ldp + b];
-      gr += va.x * vb.x + va.y * vb.y;
-      gi += va.x * vb.y - va.y * vb.x;
-    }
-    gp_[2 * idx] = (double)gr; gp_[2 * idx + 1] = (double)gi;
-  }
-  cl.sync();
   if (rank == 0) {
-    for (int idx = tid; idx < npairs; idx += PT) {
-      double gr = 0, gi = 0;
-      for (int r = 0; r < CS; ++r) {
-        const double* rr = cl.map_shared_rank(gp_, r);
-        gr += rr[2 * idx]; gi += rr[2 * idx + 1];
-      }
-      gsum[2 * idx] = gr; gsum[2 * idx + 1] = gi;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      // T(0:j, j) = -tau_j T(0:j, 0:j) G(0:j, j); T(j, j) = tau_j
-      for (int j = 0; j < kb; ++j) {
-        cx<T> tj = taus[j];
-        if (lane < j) {
-          double sr2 = 0, si2 = 0;
-          for (int l = lane; l < j; ++l) {
-            cx<T> t = Ts[lane * (KBMAX + 1) + l];
-            int pi = j * (j - 1) / 2 + l;
-            double gr = gsum[2 * pi], gi = gsum[2 * pi + 1];
-            sr2 += (double)t.x * gr - (double)t.y * gi;
-            si2 += (double)t.x * gi + (double)t.y * gr;
-          }
-          double rr = -((double)tj.x * sr2 - (double)tj.y * si2);
-          double ri = -((double)tj.x * si2 + (double)tj.y * sr2);
-          Ts[lane * (KBMAX + 1) + j] = mk<T>((T)rr, (T)ri);
-        } else if (lane == j) {
-          Ts[j * (KBMAX + 1) + j] = tj;
-        }
-        __syncwarp();
-      }
-    }
-    __syncthreads();
     for (int idx = tid; idx < kb * kb; idx += PT) {
-      int i = idx / kb, j = idx % kb;
-      a.Tf[i * a.ldt + j] = (j >= i) ? Ts[i * (KBMAX + 1) + j] : mk<T>(0, 0);
+      const int i = idx / kb, jj = idx % kb;
+      a.Tf[i * a.ldt + jj] = (jj >= i) ? Ts[i * (KBMAX + 1) + jj] : mk<T>(0, 0);
     }
     if (tid < kb) a.tau[k0 + tid] = taus[tid];
   }
-
   // ---- write V (explicit, unit lower trapezoidal) and R / zeros into A
   for (int idx = tid; idx < nloc * kb; idx += PT) {
-    int p = idx / kb, c = idx % kb;
-    int g = row0 + p;
-    cx<T> pv = P[p * ldp + c];
-    cx<T> v = (g == c) ? mk<T>(1, 0) : (g > c ? pv : mk<T>(0, 0));
-    a.V[(k0 + g) * a.ldv + k0 + c] = v;
+    const int p = idx / kb, c = idx % kb;
+    const int g = row0 + p;
+    const cx<T> pv = P[p * ldp + c];
+    a.V[(k0 + g) * a.ldv + k0 + c] = (g == c) ? mk<T>(1, 0) : (g > c ? pv : mk<T>(0, 0));
     a.A[(k0 + g) * a.lda + k0 + c] = (c >= g) ? pv : mk<T>(0, 0);
   }
-  cl.sync();  // keep shared memory alive until every remote read has finished
+  cl.sync();  // no CTA leaves while others may still store into its shared memory
 }
 
 template <typename T>
@@ -339,17 +330,23 @@ int qr_panel_width(int m, int n, int elem_bytes) {
 }
 
 template <typename T> void qr_carve(Arena& ar, int m, int n, QrScratch<T>& s) {
-  // sized for the widest panel: ceil(n/nb) * nb * nb <= (n + KBMAX) * KBMAX for any nb <= KBMAX
-  const int nb = KBMAX;
+  // one NBO x NBO compact-WY factor per outer block; W, W2 hold NBO x n
+  const int nbo = NBO;
   s.V = ar.take<cx<T>>((size_t)m * n);
   s.tau = ar.take<cx<T>>(n);
-  s.Tf = ar.take<cx<T>>((size_t)(n + nb) * nb);
-  s.W = ar.take<cx<T>>((size_t)nb * n);
-  s.W2 = ar.take<cx<T>>((size_t)nb * n);
-  size_t e1 = gemm_simt_scratch_elems(nb, n, m, 1);
-  size_t e2 = gemm_simt_scratch_elems(m, n, nb, 1);
-  s.gemm_scratch_elems = e1 > e2 ? e1 : e2;
-  s.gemm_scratch = s.gemm_scratch_elems ? ar.take<cx<T>>(s.gemm_scratch_elems) : nullptr;
+  s.Tf = ar.take<cx<T>>((size_t)(n + nbo) * nbo);
+  s.W = ar.take<cx<T>>((size_t)nbo * n);
+  s.W2 = ar.take<cx<T>>((size_t)nbo * n);
+  s.G = ar.take<cx<T>>((size_t)nbo * nbo);
+  s.tmp = ar.take<cx<T>>((size_t)nbo * KBMAX);
+  size_t e = 0;
+  for (int k = 1; k <= nbo; k *= 2) {
+    e = std::max(e, gemm_simt_scratch_elems(k, n, m, 1));
+    e = std::max(e, gemm_simt_scratch_elems(k, k, m, 1));
+  }
+  e = std::max(e, gemm_simt_scratch_elems(m, n, nbo, 1));
+  s.gemm_scratch_elems = e;
+  s.gemm_scratch = e ? ar.take<cx<T>>(e) : nullptr;
 }
 
 template <typename T>
@@ -360,56 +357,86 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
   const int nb = qr_panel_width(m, n, sizeof(cx<T>));
   if (nb < 1) { set_last_message("QR: matrix too tall for the shared-memory panel"); return QRTEBD_ERR_INVALID_ARG; }
   const long long ldv = n;
+  const int nbo = NBO;  // outer block: inner panels of nb columns inside it
   const cx<T> one = mk<T>(1, 0), zero = mk<T>(0, 0), mone = mk<T>(-1, 0);
+  // V must be zero above each panel's diagonal block: an outer block reads the rows
+  // above its later inner panels, which those panels do not write
+  QR_CUDA_TRY(cudaMemsetAsync(s.V, 0, (size_t)m * n * sizeof(cx<T>), st));
 
-  for (int k0 = 0; k0 < n; k0 += nb) {
-    const int kb = std::min(nb, n - k0);
-    const int mr = m - k0;
-    ClusterChoice cc = choose_cluster<T>(mr, kb);
-    if (cc.cs < 0 || cc.kb != kb) {
-      cc.kb = kb;  // kb was validated at k0 = 0 (largest mr); recompute rows per CTA
-      cc.cs = 16; cc.rpc = (int)ceil_div(mr, 16);
+  for (int ko = 0; ko < n; ko += nbo) {
+    const int kbo = std::min(nbo, n - ko);
+    const int mo = m - ko;
+    cx<T>* Tb = s.Tf + (size_t)(ko / nbo) * nbo * nbo;
+    QR_CUDA_TRY(cudaMemsetAsync(Tb, 0, (size_t)nbo * nbo * sizeof(cx<T>), st));
+    for (int ki = ko; ki < ko + kbo; ki += nb) {
+      const int kb = std::min(nb, ko + kbo - ki);
+      const int mr = m - ki;
+      ClusterChoice cc = choose_cluster<T>(mr, kb);
+      if (cc.cs < 0 || cc.kb != kb) { cc.kb = kb; cc.cs = 16; cc.rpc = (int)ceil_div(mr, 16); }
+      cx<T>* Ti = Tb + (size_t)(ki - ko) * nbo + (ki - ko);
+      PanelArgs<T> pa{A, lda, m, ki, kb, s.V, ldv, s.tau, Ti, nbo, cc.rpc, err};
+      QR_TRY(launch_panel<T>(pa, cc.cs, st));
+      // inner update: the rest of this outer block
+      const int nc = ko + kbo - ki - kb;
+      if (nc > 0) {
+        const cx<T>* Vk = s.V + (long long)ki * ldv + ki;
+        cx<T>* C = A + (long long)ki * lda + ki + kb;
+        GemmArgs<T> g1{kb, nc, mr, Vk, 1, ldv, true, C, lda, 1, false, s.W, nc, 1, one, zero};
+        QR_TRY(gemm_simt<T>(g1, st, s.gemm_scratch, s.gemm_scratch_elems));
+        GemmArgs<T> g2{kb, nc, kb, Ti, 1, nbo, true, s.W, nc, 1, false, s.W2, nc, 1, one, zero};
+        QR_TRY(gemm_simt<T>(g2, st, s.gemm_scratch, s.gemm_scratch_elems));
+        GemmArgs<T> g3{mr, nc, kb, Vk, ldv, 1, false, s.W2, nc, 1, false, C, lda, 1, mone, one};
+        QR_TRY(run_gemm<T>(g3, s, st, gm));
+      }
     }
-    PanelArgs<T> pa{A, lda, m, k0, kb, s.V, ldv, s.tau, s.Tf + (size_t)(k0 / nb) * nb * nb, nb,
-                    cc.rpc, err};
-    QR_TRY(launch_panel<T>(pa, cc.cs, st));
-    const int nc = n - k0 - kb;
+    const cx<T>* Vb = s.V + (long long)ko * ldv + ko;
+    if (kbo > nb) {
+      // T of the outer block from the inner ones: with G = V^dag V,
+      // T[0:c0, c0:c0+w] = -T[0:c0, 0:c0] G[0:c0, c0:c0+w] T[c0:c0+w, c0:c0+w]
+      GemmArgs<T> gg{kbo, kbo, mo, Vb, 1, ldv, true, Vb, ldv, 1, false, s.G, nbo, 1, one, zero};
+      QR_TRY(run_gemm<T>(gg, s, st, gm));
+      for (int c0 = nb; c0 < kbo; c0 += nb) {
+        const int w = std::min(nb, kbo - c0);
+        GemmArgs<T> t1{c0, w, w, s.G + c0, nbo, 1, false, Tb + (size_t)c0 * nbo + c0, nbo, 1, false,
+                       s.tmp, w, 1, one, zero};
+        QR_TRY(gemm_simt<T>(t1, st, s.gemm_scratch, s.gemm_scratch_elems));
+        GemmArgs<T> t2{c0, w, c0, Tb, nbo, 1, false, s.tmp, w, 1, false, Tb + c0, nbo, 1, mone, zero};
+        QR_TRY(gemm_simt<T>(t2, st, s.gemm_scratch, s.gemm_scratch_elems));
+      }
+    }
+    // outer trailing update: C <- (I - V T V^dag)^dag C
+    const int nc = n - ko - kbo;
     if (nc > 0) {
-      const cx<T>* Vk = s.V + (long long)k0 * ldv + k0;
-      cx<T>* C = A + (long long)k0 * lda + k0 + kb;
-      const cx<T>* Tk = s.Tf + (size_t)(k0 / nb) * nb * nb;
-      // W = V^dag C  (kb x nc)
-      GemmArgs<T> g1{kb, nc, mr, Vk, 1, ldv, true, C, lda, 1, false, s.W, nc, 1, one, zero};
+      cx<T>* C = A + (long long)ko * lda + ko + kbo;
+      GemmArgs<T> g1{kbo, nc, mo, Vb, 1, ldv, true, C, lda, 1, false, s.W, nc, 1, one, zero};
       QR_TRY(run_gemm<T>(g1, s, st, gm));
-      // W2 = T^dag W
-      GemmArgs<T> g2{kb, nc, kb, Tk, 1, nb, true, s.W, nc, 1, false, s.W2, nc, 1, one, zero};
+      GemmArgs<T> g2{kbo, nc, kbo, Tb, 1, nbo, true, s.W, nc, 1, false, s.W2, nc, 1, one, zero};
       QR_TRY(run_gemm<T>(g2, s, st, gm));
-      // C -= V W2
-      GemmArgs<T> g3{mr, nc, kb, Vk, ldv, 1, false, s.W2, nc, 1, false, C, lda, 1, mone, one};
+      GemmArgs<T> g3{mo, nc, kbo, Vb, ldv, 1, false, s.W2, nc, 1, false, C, lda, 1, mone, one};
       QR_TRY(run_gemm<T>(g3, s, st, gm));
     }
   }
 
-  // explicit Q by backward accumulation
+  // explicit Q by backward accumulation over the outer blocks
   {
     long long tot = (long long)m * n;
     k_eye<T><<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(Q, ldq, m, n);
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());
   }
-  const int np = (int)ceil_div(n, nb);
-  for (int p = np - 1; p >= 0; --p) {
-    const int k0 = p * nb;
-    const int kb = std::min(nb, n - k0);
-    const int mr = m - k0, nq = n - k0;
-    const cx<T>* Vk = s.V + (long long)k0 * ldv + k0;
-    const cx<T>* Tk = s.Tf + (size_t)p * nb * nb;
-    cx<T>* Qs = Q + (long long)k0 * ldq + k0;
-    GemmArgs<T> g1{kb, nq, mr, Vk, 1, ldv, true, Qs, ldq, 1, false, s.W, nq, 1, one, zero};
+  const int npo = (int)ceil_div(n, nbo);
+  for (int p = npo - 1; p >= 0; --p) {
+    const int ko = p * nbo;
+    const int kbo = std::min(nbo, n - ko);
+    const int mo = m - ko, nq = n - ko;
+    const cx<T>* Vb = s.V + (long long)ko * ldv + ko;
+    const cx<T>* Tb = s.Tf + (size_t)p * nbo * nbo;
+    cx<T>* Qs = Q + (long long)ko * ldq + ko;
+    GemmArgs<T> g1{kbo, nq, mo, Vb, 1, ldv, true, Qs, ldq, 1, false, s.W, nq, 1, one, zero};
     QR_TRY(run_gemm<T>(g1, s, st, gm));
-    GemmArgs<T> g2{kb, nq, kb, Tk, nb, 1, false, s.W, nq, 1, false, s.W2, nq, 1, one, zero};
+    GemmArgs<T> g2{kbo, nq, kbo, Tb, nbo, 1, false, s.W, nq, 1, false, s.W2, nq, 1, one, zero};
     QR_TRY(run_gemm<T>(g2, s, st, gm));
-    GemmArgs<T> g3{mr, nq, kb, Vk, ldv, 1, false, s.W2, nq, 1, false, Qs, ldq, 1, mone, one};
+    GemmArgs<T> g3{mo, nq, kbo, Vb, ldv, 1, false, s.W2, nq, 1, false, Qs, ldq, 1, mone, one};
     QR_TRY(run_gemm<T>(g3, s, st, gm));
   }
   return QRTEBD_OK;

@@ -20,6 +20,8 @@ template <typename T> struct QrScratch {
   cx<T>* Tf = nullptr;     // ceil(n/nb) blocks of nb x nb triangular factors
   cx<T>* W = nullptr;      // nb x n
   cx<T>* W2 = nullptr;     // nb x n
+  cx<T>* G = nullptr;      // outer-block Gram matrix V^dag V
+  cx<T>* tmp = nullptr;    // T assembly scratch
   cx<T>* gemm_scratch = nullptr;
   size_t gemm_scratch_elems = 0;
 };

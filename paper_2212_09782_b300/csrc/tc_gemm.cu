@@ -1,15 +1,19 @@
 // Complex64 GEMM on tcgen05 tensor cores; see tc_gemm.cuh.
 //
 // Kernel: one 128 x 256 real output tile per CTA (one CTA per SM: ~197 KB of
-// shared memory), 192 threads in three roles:
+// shared memory), 320 threads in three roles:
 //   warp 0      TMA producer: 128B-swizzled K-major tiles of A' (128 x 32 fp32) and
 //               B'^T (256 x 32 fp32) per stage, hi and lo parts, into a ring of
 //               stages guarded by full/empty mbarriers;
-//   warp 1      TMEM allocation (256 columns) and the single MMA-issuing thread:
+//   warp 1      TMEM allocation (512 columns) and the single MMA-issuing thread:
 //               per stage 4 K-steps of tcgen05.mma.kind::tf32 M=128 N=256 K=8
 //               (x3 for hi*hi, hi*lo, lo*hi), tcgen05.commit frees the stage;
-//   warps 2-5   epilogue: tcgen05.ld of the FP32 accumulator (one TMEM lane per
-//               output row), alpha/beta, complex stores.
+//   warps 2-9   epilogue: every CHUNK stages the accumulator (two TMEM buffers,
+//               ping-pong) is added into FP32 registers, one row and 128 columns
+//               per thread; at the end alpha/beta and complex stores.
+// The promotion matters: the tensor core's own accumulation loses low-order bits
+// at every step, so accumulating all of K in TMEM gives an error growing like K
+// rather than sqrt(K); chunked promotion restores FP32-like accuracy.
 // Every mbarrier wait is bounded (kSpinLimit); on expiry the kernel sets
 // DEVERR_TIMEOUT in the error word, drains what it issued and returns.
 #include <cudaTypedefs.h>
@@ -25,8 +29,10 @@ namespace {
 constexpr int BM = 128, BN = 256, BK = 32;     // BK in fp32 elements = one 128 B swizzle row
 constexpr int A_TILE = BM * BK * 4;            // 16 KB
 constexpr int B_TILE = BN * BK * 4;            // 32 KB
-constexpr int NTHREADS = 192;
-constexpr int TMEM_COLS = 256;
+constexpr int NEPI = 8;                         // epilogue warps
+constexpr int NTHREADS = 64 + 32 * NEPI;        // producer, MMA, epilogue
+constexpr int TMEM_COLS = 512;                  // two 256-column accumulators
+constexpr int CHUNK = 4;                        // stages per FP32 promotion
 
 template <bool THREE> struct Cfg {
   static constexpr int STAGES = THREE ? 2 : 4;
@@ -119,26 +125,42 @@ constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(BN 
         "=r"(r[31])                                                                          \
       : "r"(taddr))
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_u32(b)) : "memory");
+}
+
+// Kernel. Roles: warp 0 TMA producer, warp 1 TMEM allocator + MMA issuer, warps
+// 2..9 epilogue. The K loop is cut into chunks of CHUNK stages; each chunk
+// accumulates into one of two TMEM buffers (columns [0,256) and [256,512)) and the
+// epilogue warps add every finished chunk into FP32 registers (each thread one row,
+// 128 columns), so at most 4*CHUNK*3 tensor-core accumulations build on each other
+// before a correctly rounded FP32 add. grid.z splits K (partial != nullptr: raw
+// partial sums are written for a separate reduction).
 template <bool THREE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
               const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
-              Epi epi, int Kp, unsigned* err) {
+              Epi epi, int Kp, int kt_per_split, float* partial, unsigned* err) {
   using C = Cfg<THREE>;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024 - (s_u32(smem_raw) & 1023)) & 1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES);
   uint64_t* empty = full + C::STAGES;
-  uint64_t* tmem_full = empty + C::STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_full + 1);
+  uint64_t* accf = empty + C::STAGES;  // [2] chunk accumulated
+  uint64_t* acce = accf + 2;           // [2] chunk drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
-  const int nk = (Kp + BK - 1) / BK;
+  const int nk_all = (Kp + BK - 1) / BK;
+  const int kt0 = blockIdx.z * kt_per_split;
+  const int kt1 = min(nk_all, kt0 + kt_per_split);
+  const int nk = max(0, kt1 - kt0);
+  const int nchunks = (nk + CHUNK - 1) / CHUNK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
-    mbar_init(tmem_full, 1);
+    for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], NEPI); }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -162,89 +184,116 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     if (lane == 0) {
       bool ok = true;
       int issued = 0;
-      for (int kt = 0; kt < nk && ok; ++kt) {
-        const int s = kt % C::STAGES;
-        const uint32_t ph = (uint32_t)((kt / C::STAGES) & 1);
+      for (int i = 0; i < nk && ok; ++i) {
+        const int s = i % C::STAGES;
+        const uint32_t ph = (uint32_t)((i / C::STAGES) & 1);
         if (!mbar_wait(&empty[s], ph ^ 1u)) { ok = false; break; }
+        const int kx = (kt0 + i) * BK;
         mbar_expect_tx(&full[s], C::STAGE_BYTES);
-        tma_load(stage_a_hi(s), &tA_hi, &full[s], kt * BK, m0);
-        tma_load(stage_b_hi(s), &tB_hi, &full[s], kt * BK, n0);
+        tma_load(stage_a_hi(s), &tA_hi, &full[s], kx, m0);
+        tma_load(stage_b_hi(s), &tB_hi, &full[s], kx, n0);
         if (THREE) {
-          tma_load(stage_a_lo(s), &tA_lo, &full[s], kt * BK, m0);
-          tma_load(stage_b_lo(s), &tB_lo, &full[s], kt * BK, n0);
+          tma_load(stage_a_lo(s), &tA_lo, &full[s], kx, m0);
+          tma_load(stage_b_lo(s), &tB_lo, &full[s], kx, n0);
         }
         ++issued;
       }
       if (!ok) atomicOr(err, DEVERR_TIMEOUT);
       // drain: every issued stage must have landed before shared memory goes away
-      for (int kt = (issued > C::STAGES ? issued - C::STAGES : 0); kt < issued; ++kt) {
-        const int s = kt % C::STAGES;
-        if (!mbar_wait(&full[s], (uint32_t)((kt / C::STAGES) & 1))) { atomicOr(err, DEVERR_TIMEOUT); break; }
+      for (int i = (issued > C::STAGES ? issued - C::STAGES : 0); i < issued; ++i) {
+        if (!mbar_wait(&full[i % C::STAGES], (uint32_t)((i / C::STAGES) & 1))) {
+          atomicOr(err, DEVERR_TIMEOUT);
+          break;
+        }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       bool ok = true;
-      for (int kt = 0; kt < nk; ++kt) {
-        const int s = kt % C::STAGES;
-        const uint32_t ph = (uint32_t)((kt / C::STAGES) & 1);
-        if (!mbar_wait(&full[s], ph)) { ok = false; break; }
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int b = c & 1;
+        if (c >= 2 && !mbar_wait(&acce[b], (uint32_t)(((c >> 1) - 1) & 1))) { ok = false; break; }
         tc_fence_after();
-        const uint32_t a_hi = s_u32(stage_a_hi(s)), b_hi = s_u32(stage_b_hi(s));
-        const uint32_t a_lo = s_u32(stage_a_lo(s)), b_lo = s_u32(stage_b_lo(s));
+        const uint32_t acc_t = tmem + (uint32_t)(b * BN);
+        const int i1 = min(nk, (c + 1) * CHUNK);
+        for (int i = c * CHUNK; i < i1; ++i) {
+          const int s = i % C::STAGES;
+          if (!mbar_wait(&full[s], (uint32_t)((i / C::STAGES) & 1))) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a_hi = s_u32(stage_a_hi(s)), b_hi = s_u32(stage_b_hi(s));
+          const uint32_t a_lo = s_u32(stage_a_lo(s)), b_lo = s_u32(stage_b_lo(s));
 #pragma unroll
-        for (int k = 0; k < BK / 8; ++k) {
-          const uint32_t off = k * 32;  // 8 tf32 = 32 bytes along K inside the swizzle row
-          const uint32_t acc = (kt > 0 || k > 0) ? 1u : 0u;
-          if (THREE) {
-            tc_mma(tmem, desc_sw128(a_lo + off), desc_sw128(b_hi + off), kIdesc, acc);
-            tc_mma(tmem, desc_sw128(a_hi + off), desc_sw128(b_lo + off), kIdesc, 1u);
-            tc_mma(tmem, desc_sw128(a_hi + off), desc_sw128(b_hi + off), kIdesc, 1u);
-          } else {
-            tc_mma(tmem, desc_sw128(a_hi + off), desc_sw128(b_hi + off), kIdesc, acc);
+          for (int k = 0; k < BK / 8; ++k) {
+            const uint32_t off = k * 32;  // 8 tf32 = 32 bytes along K inside the swizzle row
+            const uint32_t acc = (i > c * CHUNK || k > 0) ? 1u : 0u;
+            if (THREE) {
+              tc_mma(acc_t, desc_sw128(a_lo + off), desc_sw128(b_hi + off), kIdesc, acc);
+              tc_mma(acc_t, desc_sw128(a_hi + off), desc_sw128(b_lo + off), kIdesc, 1u);
+              tc_mma(acc_t, desc_sw128(a_hi + off), desc_sw128(b_hi + off), kIdesc, 1u);
+            } else {
+              tc_mma(acc_t, desc_sw128(a_hi + off), desc_sw128(b_hi + off), kIdesc, acc);
+            }
           }
+          tc_commit(&empty[s]);
         }
-        tc_commit(&empty[s]);
+        tc_commit(&accf[b]);  // fires once this chunk's MMAs have completed
       }
       if (!ok) atomicOr(err, DEVERR_TIMEOUT);
-      tc_commit(tmem_full);  // arrives once every MMA issued above has completed
     }
   } else {
-    // epilogue warps 2..5 -> TMEM lane quarters 2, 3, 0, 1
+    // epilogue warps 2..9: TMEM lane quarter q, column half h
     const int q = warp & 3;
+    const int h = (warp - 2) >> 2;
     const int row = m0 + q * 32 + lane;
-    const bool ok = mbar_wait(tmem_full, 0);
-    tc_fence_after();
-    if (!ok) {
-      if (lane == 0) atomicOr(err, DEVERR_TIMEOUT);
-    } else {
-      const bool use_beta = (epi.beta.x != 0.f || epi.beta.y != 0.f);
-#pragma unroll 1
-      for (int ch = 0; ch < BN / 32; ++ch) {
-        if (n0 + ch * 32 >= 2 * epi.Nc) break;  // warp-uniform
+    float sum[128];
+#pragma unroll
+    for (int j = 0; j < 128; ++j) sum[j] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int b = c & 1;
+      if (!mbar_wait(&accf[b], (uint32_t)((c >> 1) & 1))) { ok = false; break; }
+      tc_fence_after();
+#pragma unroll
+      for (int blk = 0; blk < 4; ++blk) {
         uint32_t r[32];
-        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ch * 32);
+        const uint32_t taddr =
+            tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + h * 128 + blk * 32);
         TMEM_LD32(taddr, r);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (row < epi.M) {
-          const int nb = (n0 + ch * 32) >> 1;
-          float2* crow = epi.C + (long long)row * epi.scm;
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int n = nb + j;
-            if (n < epi.Nc) {
-              float ar = __uint_as_float(r[2 * j]), ai = __uint_as_float(r[2 * j + 1]);
-              float2 v;
-              v.x = epi.alpha.x * ar - epi.alpha.y * ai;
-              v.y = epi.alpha.x * ai + epi.alpha.y * ar;
-              float2* p = crow + (long long)n * epi.scn;
-              if (use_beta) {
-                float2 c = *p;
-                v.x += epi.beta.x * c.x - epi.beta.y * c.y;
-                v.y += epi.beta.x * c.y + epi.beta.y * c.x;
-              }
-              *p = v;
+        for (int j = 0; j < 32; ++j) sum[blk * 32 + j] += __uint_as_float(r[j]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[b]);
+    }
+    if (!ok) {
+      if (lane == 0) atomicOr(err, DEVERR_TIMEOUT);
+    } else if (row < epi.M) {
+      const int col0 = n0 + h * 128;  // first real column of this thread's half
+      if (partial) {
+        float* prow = partial + ((long long)blockIdx.z * epi.M + row) * (2LL * epi.Nc);
+#pragma unroll
+        for (int j = 0; j < 128; ++j)
+          if (col0 + j < 2 * epi.Nc) prow[col0 + j] = sum[j];
+      } else {
+        const bool use_beta = (epi.beta.x != 0.f || epi.beta.y != 0.f);
+        float2* crow = epi.C + (long long)row * epi.scm;
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+          const int n = (col0 >> 1) + j;
+          if (n < epi.Nc) {
+            const float ar = sum[2 * j], ai = sum[2 * j + 1];
+            float2 v;
+            v.x = epi.alpha.x * ar - epi.alpha.y * ai;
+            v.y = epi.alpha.x * ai + epi.alpha.y * ar;
+            float2* p = crow + (long long)n * epi.scn;
+            if (use_beta) {
+              const float2 cv = *p;
+              v.x += epi.beta.x * cv.x - epi.beta.y * cv.y;
+              v.y += epi.beta.x * cv.y + epi.beta.y * cv.x;
             }
+            *p = v;
           }
         }
       }
@@ -253,14 +302,41 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {
-    // tmem_full has fired (epilogue waited on it) unless a wait expired; wait once more
-    // (bounded) so no MMA still writes the columns being freed.
-    if (!mbar_wait(tmem_full, 0) && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
+    // every chunk commit has fired (the epilogue waited on them) unless a wait
+    // expired; wait once more (bounded) so no MMA still writes the columns being freed
+    if (nchunks > 0) {
+      const int c = nchunks - 1;
+      if (!mbar_wait(&accf[c & 1], (uint32_t)((c >> 1) & 1)) && lane == 0)
+        atomicOr(err, DEVERR_TIMEOUT);
+    }
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(TMEM_COLS)
                  : "memory");
   }
+}
+
+// C = alpha * sum_z partial[z] + beta * C (partials: split x M x 2N floats)
+__global__ void k_splitk_sum(const float* partial, int splits, Epi epi) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long MN = (long long)epi.M * epi.Nc;
+  if (idx >= MN) return;
+  const int m = (int)(idx / epi.Nc), n = (int)(idx % epi.Nc);
+  float ar = 0.f, ai = 0.f;
+  for (int z = 0; z < splits; ++z) {
+    const float* p = partial + ((long long)z * epi.M + m) * (2LL * epi.Nc) + 2 * n;
+    ar += p[0]; ai += p[1];
+  }
+  float2 v;
+  v.x = epi.alpha.x * ar - epi.alpha.y * ai;
+  v.y = epi.alpha.x * ai + epi.alpha.y * ar;
+  float2* c = epi.C + (long long)m * epi.scm + (long long)n * epi.scn;
+  if (epi.beta.x != 0.f || epi.beta.y != 0.f) {
+    const float2 cv = *c;
+    v.x += epi.beta.x * cv.x - epi.beta.y * cv.y;
+    v.y += epi.beta.x * cv.y + epi.beta.y * cv.x;
+  }
+  *c = v;
 }
 
 // ------------------------------------------------------------------ prep
@@ -379,6 +455,8 @@ void tc_carve(Arena& ar, int max_m, int max_k, int max_n, TcWorkspace& w) {
   w.b = TcSlot{};
   w.b.hi = ar.take<float>(w.b_cap);
   w.b.lo = ar.take<float>(w.b_cap);
+  w.p_cap = (size_t)1 << 22;  // 16 MB of split-K partial sums
+  w.partial = ar.take<float>(w.p_cap);
   w.a_next = 0;
 }
 
@@ -388,20 +466,30 @@ void tc_invalidate(TcWorkspace& w) {
 }
 
 bool tc_gemm_eligible(const GemmArgs<float>& g) {
-  return g.batch == 1 && g.M >= 128 && g.N >= 64 && g.K >= 128 &&
-         (double)g.M * g.N * g.K >= (double)(1 << 22);
+  return g.batch == 1 && std::max(g.M, g.N) >= 128 && std::min(g.M, g.N) >= 16 && g.K >= 32 &&
+         (double)g.M * g.N * g.K >= (double)(1 << 21);
 }
 
-int tc_gemm(const GemmArgs<float>& g, bool three, TcWorkspace& w, cudaStream_t st) {
+int tc_gemm(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStream_t st) {
+  // C = A B with a short M is run as C^T = B^T A^T (the tile is 128 rows tall)
+  GemmArgs<float> g = g0;
+  bool cacheable = g0.reuse_a;
+  if (g0.M < 128 && g0.N > g0.M) {
+    cacheable = false;
+    g.M = g0.N; g.N = g0.M;
+    g.A = g0.B; g.sam = g0.sbn; g.sak = g0.sbk; g.conj_a = g0.conj_b;
+    g.B = g0.A; g.sbk = g0.sak; g.sbn = g0.sam; g.conj_b = g0.conj_a;
+    g.scm = g0.scn; g.scn = g0.scm;
+  }
   const int M = g.M, N = g.N, K = g.K;
   const int ld = ld_for(K);
   if ((size_t)M * ld > w.a_cap || (size_t)2 * N * ld > w.b_cap || !w.a[0].hi || !w.b.hi)
-    return gemm_simt<float>(g, st, nullptr, 0);
+    return gemm_simt<float>(g0, st, nullptr, 0);
   QR_TRY(get_encode());
 
   // ---- A' (cached per source/op within one bond update)
   TcSlot* sa = nullptr;
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 2 && cacheable; ++i) {
     TcSlot& s = w.a[i];
     if (s.valid && s.src == g.A && s.s0 == g.sam && s.s1 == g.sak && s.rows == M && s.cols == K &&
         s.conj == g.conj_a && s.three == three && s.ld == ld)
@@ -416,7 +504,7 @@ int tc_gemm(const GemmArgs<float>& g, bool three, TcWorkspace& w, cudaStream_t s
                                            sa->lo, ld, three ? 1 : 0);
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());
-    sa->valid = true; sa->src = g.A; sa->s0 = g.sam; sa->s1 = g.sak; sa->rows = M; sa->cols = K;
+    sa->valid = cacheable; sa->src = g.A; sa->s0 = g.sam; sa->s1 = g.sak; sa->rows = M; sa->cols = K;
     sa->conj = g.conj_a; sa->three = three; sa->ld = ld;
   }
   // ---- B'^T
@@ -435,29 +523,48 @@ int tc_gemm(const GemmArgs<float>& g, bool three, TcWorkspace& w, cudaStream_t s
   QR_TRY(make_map(&tb_lo, three ? w.b.lo : w.b.hi, 2 * N, 2 * K, ld, BN));
 
   Epi epi{g.C, g.scm, g.scn, g.alpha, g.beta, M, N};
-  dim3 grid((unsigned)ceil_div(2LL * N, BN), (unsigned)ceil_div(M, BM));
-  unsigned* err = device_error_word();
-  ProfScope prof(PROF_TC_GEMM, st, 8.0 * M * N * K);
-  if (three) {
-    if (!g_attr3) {
-      QR_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       Cfg<true>::SMEM));
-      g_attr3 = true;
-    }
-    k_tc_gemm<true><<<grid, NTHREADS, Cfg<true>::SMEM, st>>>(ta_hi, ta_lo, tb_hi, tb_lo, epi,
-                                                             2 * K, err);
-    note_launch();
-  } else {
-    if (!g_attr1) {
-      QR_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       Cfg<false>::SMEM));
-      g_attr1 = true;
-    }
-    k_tc_gemm<false><<<grid, NTHREADS, Cfg<false>::SMEM, st>>>(ta_hi, ta_lo, tb_hi, tb_lo, epi,
-                                                               2 * K, err);
-    note_launch();
+  const int nx = (int)ceil_div(2LL * N, BN), ny = (int)ceil_div(M, BM);
+  const int nk = (int)ceil_div(2LL * K, BK);
+  // split K when the tile grid leaves most SMs idle
+  int splits = 1;
+  const int tiles = nx * ny;
+  if (tiles < 100 && nk >= 2 * CHUNK) {
+    splits = std::min<int>((int)ceil_div(148, tiles), nk / CHUNK);
+    splits = std::min(splits, 32);
+    while (splits > 1 && (size_t)splits * M * 2 * N > w.p_cap) --splits;
   }
-  QR_CUDA_TRY(cudaGetLastError());
+  int per = (int)ceil_div(nk, splits);
+  splits = (int)ceil_div(nk, per);
+  float* part = splits > 1 ? w.partial : nullptr;
+  dim3 grid((unsigned)nx, (unsigned)ny, (unsigned)splits);
+  unsigned* err = device_error_word();
+  {
+    ProfScope prof(PROF_TC_GEMM, st, 8.0 * M * N * K);
+    if (three) {
+      if (!g_attr3) {
+        QR_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg<true>::SMEM));
+        g_attr3 = true;
+      }
+      k_tc_gemm<true><<<grid, NTHREADS, Cfg<true>::SMEM, st>>>(ta_hi, ta_lo, tb_hi, tb_lo, epi,
+                                                               2 * K, per, part, err);
+    } else {
+      if (!g_attr1) {
+        QR_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         Cfg<false>::SMEM));
+        g_attr1 = true;
+      }
+      k_tc_gemm<false><<<grid, NTHREADS, Cfg<false>::SMEM, st>>>(ta_hi, ta_lo, tb_hi, tb_lo, epi,
+                                                                 2 * K, per, part, err);
+    }
+    note_launch();
+    QR_CUDA_TRY(cudaGetLastError());
+  }
+  if (splits > 1) {
+    k_splitk_sum<<<(unsigned)ceil_div((long long)M * N, 256), 256, 0, st>>>(part, splits, epi);
+    note_launch();
+    QR_CUDA_TRY(cudaGetLastError());
+  }
   return QRTEBD_OK;
 }
 

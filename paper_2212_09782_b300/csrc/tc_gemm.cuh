@@ -27,6 +27,8 @@ struct TcWorkspace {
   TcSlot a[2];
   TcSlot b;
   size_t a_cap = 0, b_cap = 0;  // floats per hi (or lo) array
+  float* partial = nullptr;     // split-K partial sums
+  size_t p_cap = 0;             // floats
   int a_next = 0;
 };
 

@@ -21,7 +21,8 @@ PRECISIONS = {"c128": C128, "c64_3xtf32": C64_3XTF32, "c64_tf32": C64_TF32, "c64
 
 class Trunc(C.Structure):
     _fields_ = [("scheme", C.c_int), ("chi_max", C.c_int), ("eta", C.c_int), ("dchi_min", C.c_int),
-                ("dchi_frac", C.c_double), ("svd_min", C.c_double), ("tie_tol", C.c_double)]
+                ("dchi_frac", C.c_double), ("svd_min", C.c_double), ("tie_tol", C.c_double),
+                ("eps_explicit", C.c_int)]
 
 
 class BondIO(C.Structure):
@@ -63,6 +64,8 @@ def _load():
         "qrtebd_last_error_message": (C.c_char_p, []),
         "qrtebd_version": (C.c_char_p, []),
         "qrtebd_launch_count": (C.c_longlong, []),
+        "qrtebd_householder_qr": (I, [I, I, I, P, LL, P, LL, P, S, P]),
+        "qrtebd_qr_workspace_size": (S, [I, I, I]),
         "qrtebd_profile_enable": (I, [I]),
         "qrtebd_profile_read": (I, [I, C.POINTER(D), C.POINTER(C.c_longlong), C.POINTER(D),
                                     C.POINTER(D)]),
@@ -225,6 +228,20 @@ def profile_read(family):
 
 def stream_check(stream=None):
     check(_lib.qrtebd_stream_check(stream_handle(stream)), "stream_check")
+
+
+def householder_qr(precision, A, stream=None):
+    """QR of a 2-D torch CUDA tensor (m x n, m >= n): returns (Q, R); A is left untouched."""
+    import torch
+    prec = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
+    m, n = A.shape
+    W = A.clone().contiguous()
+    Q = torch.empty(m, n, dtype=A.dtype, device=A.device)
+    nb = _lib.qrtebd_qr_workspace_size(prec, m, n)
+    ws = torch.empty(max(nb, 256), dtype=torch.uint8, device=A.device)
+    check(_lib.qrtebd_householder_qr(prec, m, n, _ptr(W), n, _ptr(Q), n, _ptr(ws), ws.numel(),
+                                     stream_handle(stream)), "householder_qr")
+    return Q, torch.triu(W[:n])
 
 
 def zgemm(precision, A, B, conj_a=False, conj_b=False, trans_a=False, trans_b=False,
