@@ -214,6 +214,27 @@ int qrtebd_zgemm(int precision, int m, int n, int k, const void* A, long long sa
                  void* workspace, size_t workspace_bytes, void* stream);
 size_t qrtebd_zgemm_workspace_size(int m, int n, int k);
 
+/* Variant of qrtebd_zgemm that allocates nothing (the paper has no counterpart).
+ * For callers that cannot call cudaMalloc around a GEMM: code recorded into a CUDA
+ * graph under a capture mode that forbids allocation, latency-critical loops that
+ * cannot afford an allocation or the device-wide synchronisation of a later free,
+ * and frameworks that own all device memory through their own pool. The scratch
+ * this GEMM needs (split/embedded TF32 operands, split-K partial sums) lives in one
+ * file-scope device array of QRTEBD_NOALLOC_SCRATCH_BYTES, held on every GPU that
+ * loads the library until the process exits; the caller still passes A, B and C.
+ * precision: QRTEBD_C64_3XTF32 or QRTEBD_C64_TF32 only; m, n, k each at most
+ * QRTEBD_NOALLOC_MAX_DIM, otherwise QRTEBD_ERR_INVALID_ARG with a message. The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress), so
+ * make one call on each device before any stream capture. All calls share the array:
+ * calls that overlap on the GPU (several streams or host threads) race on it and must
+ * be serialised by the caller. Other arguments and semantics as qrtebd_zgemm. */
+#define QRTEBD_NOALLOC_MAX_DIM 512
+#define QRTEBD_NOALLOC_SCRATCH_BYTES 16777216
+int qrtebd_zgemm_noalloc(int precision, int m, int n, int k, const void* A, long long sam,
+                         long long sak, int conj_a, const void* B, long long sbk, long long sbn,
+                         int conj_b, void* C, long long scm, long long scn, const double* alpha,
+                         const double* beta, void* stream);
+
 /* ------------------------------------------------------------- Householder QR */
 /* A = Q R for a device matrix A (m x n, m >= n, row-major, leading dimension lda, in the
  * precision's storage type): the factorisation of Sec. II (i) (and, applied to Y^dag,

@@ -86,6 +86,12 @@ unsigned* device_error_word();
 void note_launch(int n = 1);
 enum ProfFamily { PROF_TC_GEMM = 0, PROF_QR_PANEL = 1, PROF_SIMT_GEMM = 2, PROF_PREP = 3,
                   PROF_GATE = 4, PROF_NFAM = 5 };
+// While a ProfSuppress is alive on this thread, ProfScope records nothing (used by
+// entry points that must not create CUDA objects).
+struct ProfSuppress {
+  ProfSuppress();
+  ~ProfSuppress();
+};
 class ProfScope {
  public:
   ProfScope(int fam, cudaStream_t st, double flops = 0, double bytes = 0);

@@ -27,10 +27,16 @@ cudaEvent_t take_event() {
 }
 }  // namespace
 
+thread_local int t_suppress = 0;
+
 void note_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+ProfSuppress::ProfSuppress() { ++t_suppress; }
+ProfSuppress::~ProfSuppress() { --t_suppress; }
 
 ProfScope::ProfScope(int fam, cudaStream_t st, double flops, double bytes)
     : fam_(fam), st_(st), flops_(flops), bytes_(bytes) {
+  if (t_suppress) return;
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_enabled) return;
   a_ = take_event();
