@@ -17,6 +17,8 @@
 // tcgen05 tensor cores in the complex64 tensor-core path).
 #include <cooperative_groups.h>
 
+#include <limits>
+
 #include "qr.cuh"
 
 namespace cg = cooperative_groups;
@@ -40,15 +42,8 @@ template <typename T> struct PanelArgs {
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
 
-template <typename T> __host__ __device__ inline size_t panel_fixed_bytes() {
-  return a16(2 * RED * sizeof(double)) + a16(2 * 16 * KBMAX * sizeof(cx<T>)) +
-         2 * a16(KBMAX * sizeof(cx<T>)) + a16(4 * sizeof(cx<T>)) + a16(KBMAX * sizeof(cx<T>)) +
-         a16(KBMAX * (KBMAX + 1) * sizeof(cx<T>));
-}
-template <typename T> __host__ __device__ inline size_t panel_smem_bytes(int rpc, int kb) {
-  return a16((size_t)rpc * (kb + 1) * sizeof(cx<T>)) + a16((size_t)rpc * sizeof(cx<T>)) +
-         panel_fixed_bytes<T>();
-}
+template <typename T> struct PanelSmem;
+template <typename T> __host__ __device__ inline size_t panel_smem_bytes(int rpc, int kb);
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -61,163 +56,286 @@ template <typename T> __device__ __forceinline__ T warp_sum_t(T v) {
   return v;
 }
 
-// Panel kernel. Per column j, two cluster-wide reductions, both push-style (each
-// CTA stores its partial into slot [rank] of every CTA's buffer before the
-// cluster barrier; after it all reads are local):
-//   1. ||x||^2 below the pivot (FP64) and alpha;
-//   2. w_c = v_j^dag P[:, c] for the columns c > j, and g_a = v_a^dag v_j for the
-//      earlier reflectors a < j, which give column j of the compact-WY factor:
-//      T(0:j, j) = -tau_j T(0:j, 0:j) g,  T(j, j) = tau_j.
-// FP64 is used only for the norm and its square root (B300's FP64 pipe is narrow);
-// the reflector scalars use Smith's complex division in the working precision.
+// ---------------------------------------------------------------- panel kernel
+// One 32-column Householder panel on a cluster of CS CTAs; CTA r holds panel rows
+// [r*rpc, (r+1)*rpc) in shared memory. Per column j:
+//   A. partial ||x||^2 below the pivot and alpha, summed over the CTA's warps;
+//   B. all-to-all: every CTA copies its partial into slot [rank] of every CTA's
+//      receive buffer with one cp.async.bulk (distributed shared memory) whose
+//      completion is counted on the receiver's mbarrier; no cluster barrier;
+//   C. every thread forms the reflector (zlarfg convention) from the CS partials;
+//   D. per-warp rows: v = x * scale, dot products with lane = slot: slots < nc give
+//      w_c = v^dag P[:, c], slots >= nc give g_a = v_a^dag v (compact-WY T column);
+//   E. all-to-all of the slot partials as in B;
+//   F. P[:, c] -= v conj(tau) w_c (lane = column), T(0:j, j) = -tau T(0:j, 0:j) g.
+// The norm accumulates in double-float for complex64 (two FP32 words, error-free
+// FMA products and TwoSum additions, ~48-bit significand) and in FP64 for complex128:
+// B300's FP64 pipe is too narrow for the panel's critical path, and the reflector is
+// stored in FP32 anyway, so FP64-class accuracy is what the norm needs.
+template <typename T> struct NAcc;  // norm accumulator: double-float (float) or FP64 (double)
+template <> struct NAcc<float> {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {  // += (a_hi, a_lo) pair
+    const float s = hi + a, bb = s - hi, e = (hi - (s - bb)) + (a - bb);
+    const float t = e + lo + b;
+    hi = s + t; lo = t - (hi - s);
+  }
+  __device__ __forceinline__ void add_sq(float x) { const float p = x * x; add(p, fmaf(x, x, -p)); }
+  __device__ __forceinline__ void add(const NAcc& o) { add(o.hi, o.lo); }
+  __device__ __forceinline__ void shfl_sum() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h = __shfl_xor_sync(0xffffffffu, hi, o), l = __shfl_xor_sync(0xffffffffu, lo, o);
+      add(h, l);
+    }
+  }
+  __device__ __forceinline__ float value() const { return hi + lo; }
+};
+template <> struct NAcc<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double a, double b) { v += a + b; }
+  __device__ __forceinline__ void add_sq(double x) { v = fma(x, x, v); }
+  __device__ __forceinline__ void add(const NAcc& o) { v += o.v; }
+  __device__ __forceinline__ void shfl_sum() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  }
+  __device__ __forceinline__ double value() const { return v; }
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t map_rank(uint32_t a, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_init1(uint64_t* b) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_arm(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_cl(uint64_t* b, uint32_t parity) {
+  for (long long i = 0; i < kSpinLimit; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(smem_addr(b)), "r"(parity) : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+// copy `bytes` (multiple of 16) from this CTA's shared memory to CTA `rank`, counted on
+// that CTA's mbarrier
+__device__ __forceinline__ void dsmem_send(const void* src, void* dst_local, uint64_t* mbar_local,
+                                           int rank, uint32_t bytes) {
+  const uint32_t d = map_rank(smem_addr(dst_local), rank);
+  const uint32_t m = map_rank(smem_addr(mbar_local), rank);
+  asm volatile(
+      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(d), "r"(smem_addr(src)), "r"(bytes), "r"(m) : "memory");
+}
+
+constexpr int SLOTS = KBMAX;              // slot partials per exchange (padded)
+
+template <typename T> struct PanelSmem {
+  // per-column exchange buffers, double-buffered by column parity
+  static constexpr int R1 = 4;            // reduction-1 payload: norm (hi, lo) or (v, 0), alpha re, im
+  static constexpr size_t fixed() {
+    return a16(2 * 16 * R1 * sizeof(T))            // recv1 [2][16][R1]
+         + a16(R1 * sizeof(T))                     // send1
+         + a16(2 * 16 * SLOTS * sizeof(cx<T>))     // recv2 [2][16][SLOTS]
+         + a16(SLOTS * sizeof(cx<T>))              // send2
+         + a16(8 * R1 * sizeof(T))                 // per-warp reduction-1 partials
+         + a16(8 * SLOTS * sizeof(cx<T>))          // per-warp slot partials
+         + a16(KBMAX * sizeof(cx<T>))              // taus
+         + a16(KBMAX * (KBMAX + 1) * sizeof(cx<T>))  // T
+         + 64;                                     // 4 mbarriers
+  }
+};
+
+template <typename T> __host__ __device__ inline size_t panel_smem_bytes(int rpc, int kb) {
+  return a16((size_t)rpc * (kb + 1) * sizeof(cx<T>)) + a16((size_t)rpc * sizeof(cx<T>)) +
+         PanelSmem<T>::fixed();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
   extern __shared__ __align__(16) unsigned char sm[];
   cg::cluster_group cl = cg::this_cluster();
   const int CS = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = PT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = PT / 32;
+  constexpr int R1 = PanelSmem<T>::R1;
   const int kb = a.kb, ldp = kb + 1, rpc = a.rpc;
   const int mr = a.m - a.k0;
   const int row0 = rank * rpc;
   const int nloc = max(0, min(rpc, mr - row0));
+  const int rpw = (nloc + NW - 1) / NW;              // rows per warp
+  const int p0 = min(nloc, warp * rpw), p1 = min(nloc, p0 + rpw);
 
   unsigned char* q = sm;
   cx<T>* P = reinterpret_cast<cx<T>*>(q); q += a16((size_t)rpc * ldp * sizeof(cx<T>));
   cx<T>* VV = reinterpret_cast<cx<T>*>(q); q += a16((size_t)rpc * sizeof(cx<T>));
-  double* red = reinterpret_cast<double*>(q); q += a16(2 * RED * sizeof(double));
-  cx<T>* redT = reinterpret_cast<cx<T>*>(q); q += a16(2 * 16 * KBMAX * sizeof(cx<T>));
-  cx<T>* wT = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * sizeof(cx<T>));
-  cx<T>* gT = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * sizeof(cx<T>));
-  cx<T>* bc = reinterpret_cast<cx<T>*>(q); q += a16(4 * sizeof(cx<T>));
+  T* recv1 = reinterpret_cast<T*>(q); q += a16(2 * 16 * R1 * sizeof(T));
+  T* send1 = reinterpret_cast<T*>(q); q += a16(R1 * sizeof(T));
+  cx<T>* recv2 = reinterpret_cast<cx<T>*>(q); q += a16(2 * 16 * SLOTS * sizeof(cx<T>));
+  cx<T>* send2 = reinterpret_cast<cx<T>*>(q); q += a16(SLOTS * sizeof(cx<T>));
+  T* wp1 = reinterpret_cast<T*>(q); q += a16(8 * R1 * sizeof(T));
+  cx<T>* wp2 = reinterpret_cast<cx<T>*>(q); q += a16(8 * SLOTS * sizeof(cx<T>));
   cx<T>* taus = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * sizeof(cx<T>));
-  cx<T>* Ts = reinterpret_cast<cx<T>*>(q);  // KBMAX x (KBMAX + 1)
+  cx<T>* Ts = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * (KBMAX + 1) * sizeof(cx<T>));
+  uint64_t* mb = reinterpret_cast<uint64_t*>(q);     // mb[0..1] reduction 1, mb[2..3] reduction 2
 
   const long long k0 = a.k0;
   for (int idx = tid; idx < nloc * kb; idx += PT) {
     const int p = idx / kb, c = idx % kb;
     P[p * ldp + c] = a.A[(k0 + row0 + p) * a.lda + k0 + c];
   }
-  __syncthreads();
+  if (tid == 0) {
+    for (int i = 0; i < 4; ++i) mbar_init1(&mb[i]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  cl.sync();  // every CTA's barriers exist before anyone sends
+  bool ok = true;
 
   for (int j = 0; j < kb; ++j) {
     const int buf = j & 1;
-    // ---- reduction 1 (warp 0): ||x||^2 below the pivot in FP64, and alpha
-    if (warp == 0) {
-      double s = 0.0;
+    const uint32_t ph = (uint32_t)((j >> 1) & 1);
+    // ---- A: partial norm below the pivot, alpha
+    {
+      NAcc<T> acc;
       T ar = 0, ai = 0;
-      for (int p = lane; p < nloc; p += 32) {
+      for (int p = p0 + lane; p < p1; p += 32) {
         const int g = row0 + p;
         const cx<T> v = P[p * ldp + j];
-        if (g > j) s = fma((double)v.x, (double)v.x, fma((double)v.y, (double)v.y, s));
+        if (g > j) { acc.add_sq(v.x); acc.add_sq(v.y); }
         else if (g == j) { ar = v.x; ai = v.y; }
       }
-      s = warp_sum(s);
+      acc.shfl_sum();
       ar = warp_sum_t<T>(ar); ai = warp_sum_t<T>(ai);
-      if (lane < CS) {
-        double* dst = cl.map_shared_rank(red, lane) + buf * RED + 3 * rank;
-        dst[0] = s; dst[1] = (double)ar; dst[2] = (double)ai;
+      if (lane == 0) {
+        if constexpr (std::is_same<T, float>::value) { wp1[warp * R1 + 0] = acc.hi; wp1[warp * R1 + 1] = acc.lo; }
+        else { wp1[warp * R1 + 0] = acc.value(); wp1[warp * R1 + 1] = 0; }
+        wp1[warp * R1 + 2] = ar; wp1[warp * R1 + 3] = ai;
       }
-    }
-    cl.sync();
-    if (tid == 0) {
-      double xn2 = 0;
-      T alr = 0, ali = 0;
-      const double* rr = red + buf * RED;
-#pragma unroll 4
-      for (int r = 0; r < CS; ++r) { xn2 += rr[3 * r]; alr += (T)rr[3 * r + 1]; ali += (T)rr[3 * r + 2]; }
-      // zlarfg: beta = -sign(Re alpha) ||(alpha, x)||, tau = (beta - alpha) / beta,
-      // v = x / (alpha - beta)
-      T beta = alr, tr = 0, ti = 0, sr = 0, si = 0;
-      if (!(xn2 == 0.0 && ali == T(0))) {
-        const double nrm = sqrt(fma((double)alr, (double)alr, fma((double)ali, (double)ali, xn2)));
-        beta = (T)(alr >= T(0) ? -nrm : nrm);
-        tr = (beta - alr) / beta;
-        ti = -ali / beta;
-        // scale = 1 / (alpha - beta) by Smith's division (no squares of small numbers)
-        const T dr = alr - beta, di = ali;
-        if (fabs((double)dr) >= fabs((double)di)) {
-          const T rt = di / dr, den = dr + di * rt;
-          sr = T(1) / den; si = -rt / den;
-        } else {
-          const T rt = dr / di, den = di + dr * rt;
-          sr = rt / den; si = T(-1) / den;
-        }
-      }
-      if (!(isfinite((double)beta) && isfinite((double)sr) && isfinite((double)si)) && rank == 0)
-        atomicOr(a.err, DEVERR_NUMERIC);
-      bc[0] = mk<T>(beta, 0); bc[1] = mk<T>(tr, ti); bc[2] = mk<T>(sr, si);
-      taus[j] = mk<T>(tr, ti);
     }
     __syncthreads();
-    const T beta = bc[0].x;
-    const cx<T> tau = bc[1], scale = bc[2];
-
-    // ---- reduction 2: slots s < nc give w_{j+1+s}; slots s >= nc give g_{s-nc}
+    if (warp == 0) {
+      if (lane == 0) {
+        NAcc<T> s;
+        T ar = 0, ai = 0;
+        for (int w = 0; w < NW; ++w) { s.add(wp1[w * R1], wp1[w * R1 + 1]); ar += wp1[w * R1 + 2]; ai += wp1[w * R1 + 3]; }
+        if constexpr (std::is_same<T, float>::value) { send1[0] = s.hi; send1[1] = s.lo; }
+        else { send1[0] = s.value(); send1[1] = 0; }
+        send1[2] = ar; send1[3] = ai;
+        mbar_arm(&mb[buf], (uint32_t)(CS * R1 * sizeof(T)));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      __syncwarp();
+      if (lane < CS)
+        dsmem_send(send1, recv1 + (buf * 16 + rank) * R1, &mb[buf], lane, R1 * sizeof(T));
+    }
+    if (!mbar_wait_cl(&mb[buf], ph)) ok = false;
+    // ---- C: the reflector, redundantly in every thread (working precision only)
+    T beta, tr, ti, sr, si;
+    {
+      NAcc<T> s;
+      T alr = 0, ali = 0;
+      const T* rr = recv1 + buf * 16 * R1;
+      for (int r = 0; r < CS; ++r) { s.add(rr[r * R1], rr[r * R1 + 1]); alr += rr[r * R1 + 2]; ali += rr[r * R1 + 3]; }
+      const T xn2 = s.value();
+      beta = alr; tr = ti = sr = si = T(0);
+      // A column whose squared norm is below the normal range (noise of a rank-deficient
+      // block) is left as is: tau = 0, H = I, which is exactly unitary.
+      const T tot = alr * alr + ali * ali + xn2;
+      if (!(xn2 == T(0) && ali == T(0)) && tot > T(16) * std::numeric_limits<T>::min()) {
+        const T nrm = sqrt(tot);
+        beta = alr >= T(0) ? -nrm : nrm;
+        tr = (beta - alr) / beta;
+        ti = -ali / beta;
+        const T dr = alr - beta, di = ali;  // scale = 1 / (alpha - beta), Smith's division
+        if (fabs(dr) >= fabs(di)) { const T rt = di / dr, den = dr + di * rt; sr = T(1) / den; si = -rt / den; }
+        else { const T rt = dr / di, den = di + dr * rt; sr = rt / den; si = T(-1) / den; }
+      }
+      if (tid == 0 && rank == 0 && !(isfinite(beta) && isfinite(sr) && isfinite(si)))
+        atomicOr(a.err, DEVERR_NUMERIC);
+    }
+    const cx<T> scale = mk<T>(sr, si), tau = mk<T>(tr, ti);
+    if (tid == 0) taus[j] = tau;
+    // ---- D: v for this warp's rows, then slot partials (lane = slot)
     const int nc = kb - j - 1;
     const int nslot = nc + j;
+    for (int p = p0 + lane; p < p1; p += 32) {
+      const int g = row0 + p;
+      if (g > j) VV[p] = cmul<T>(P[p * ldp + j], scale);
+      else if (g == j) VV[p] = mk<T>(1, 0);
+    }
+    __syncwarp();
     if (nslot > 0) {
-      for (int sl = warp; sl < nslot; sl += nwarps) {
-        T wr = 0, wi = 0;
-        const bool is_w = sl < nc;
-        const int col = is_w ? j + 1 + sl : sl - nc;
-        for (int p = lane; p < nloc; p += 32) {
-          const int g = row0 + p;
-          if (g < j) continue;
-          const cx<T> v = (g == j) ? mk<T>(1, 0) : cmul<T>(P[p * ldp + j], scale);
-          if (sl == 0) VV[p] = v;  // scaled reflector for the update pass
+      cx<T> acc = mk<T>(0, 0);
+      if (lane < nslot) {
+        const bool is_w = lane < nc;
+        const int col = is_w ? j + 1 + lane : lane - nc;
+        for (int p = max(p0, j - row0); p < p1; ++p) {
+          const cx<T> v = VV[p];
           const cx<T> x = P[p * ldp + col];
-          if (is_w) { wr += v.x * x.x + v.y * x.y; wi += v.x * x.y - v.y * x.x; }   // conj(v) x
-          else { wr += x.x * v.x + x.y * v.y; wi += x.x * v.y - x.y * v.x; }        // conj(v_a) v
+          if (is_w) { acc.x += v.x * x.x + v.y * x.y; acc.y += v.x * x.y - v.y * x.x; }  // conj(v) x
+          else { acc.x += x.x * v.x + x.y * v.y; acc.y += x.x * v.y - x.y * v.x; }        // conj(v_a) v
         }
-        wr = warp_sum_t<T>(wr); wi = warp_sum_t<T>(wi);
-        if (lane < CS) cl.map_shared_rank(redT, lane)[buf * (KBMAX * 16) + rank * KBMAX + sl] = mk<T>(wr, wi);
       }
-      cl.sync();
-      if (tid < nslot) {
-        cx<T> w = mk<T>(0, 0);
-        const cx<T>* rr = redT + buf * (KBMAX * 16) + tid;
-#pragma unroll 4
-        for (int r = 0; r < CS; ++r) w = cadd<T>(w, rr[r * KBMAX]);
-        if (tid < nc) wT[tid] = cmul<T>(cconj<T>(tau), w);  // conj(tau) w
-        else gT[tid - nc] = w;
-      }
+      wp2[warp * SLOTS + lane] = acc;
       __syncthreads();
       if (warp == 0) {
-        // T(0:j, j) = -tau_j T(0:j, 0:j) g ; T(j, j) = tau_j
-        if (lane < j) {
-          cx<T> acc = mk<T>(0, 0);
-          for (int l = lane; l < j; ++l) cfma<T>(acc, Ts[lane * (KBMAX + 1) + l], gT[l]);
-          const cx<T> r = cmul<T>(tau, acc);
-          Ts[lane * (KBMAX + 1) + j] = mk<T>(-r.x, -r.y);
-        }
-        if (lane == 0) Ts[j * (KBMAX + 1) + j] = tau;
+        cx<T> s = mk<T>(0, 0);
+        for (int w = 0; w < NW; ++w) s = cadd<T>(s, wp2[w * SLOTS + lane]);
+        send2[lane] = s;
+        // every sender copies its nslot values rounded up to 16 bytes
+        const uint32_t bytes = (uint32_t)(nslot * sizeof(cx<T>) + 15) & ~15u;
+        if (lane == 0) mbar_arm(&mb[2 + buf], (uint32_t)CS * bytes);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane < CS) dsmem_send(send2, recv2 + (buf * 16 + rank) * SLOTS, &mb[2 + buf], lane, bytes);
       }
-      // P <- (I - conj(tau) v v^dag) P on columns c > j; column j <- v, pivot <- beta
-      const int ncc = nc + 1;
-      for (int idx = tid; idx < nloc * ncc; idx += PT) {
-        const int p = idx / ncc, cc = idx % ncc;
-        const int g = row0 + p;
-        if (g < j) continue;
-        if (cc == nc) {
-          P[p * ldp + j] = (g > j) ? VV[p] : mk<T>(beta, T(0));
-        } else {
-          const cx<T> v = (g == j) ? mk<T>(1, 0) : VV[p];
-          P[p * ldp + j + 1 + cc] = csub<T>(P[p * ldp + j + 1 + cc], cmul<T>(v, wT[cc]));
-        }
+      if (!mbar_wait_cl(&mb[2 + buf], ph)) ok = false;
+      // ---- F: update (lane = column) and the T column
+      cx<T> w = mk<T>(0, 0);
+      if (lane < nslot) {
+        const cx<T>* rr = recv2 + buf * 16 * SLOTS + lane;
+        for (int r = 0; r < CS; ++r) w = cadd<T>(w, rr[r * SLOTS]);
       }
-      __syncthreads();
+      if (lane < nc) {
+        const cx<T> cw = cmul<T>(cconj<T>(tau), w);  // conj(tau) w_c
+        for (int p = max(p0, j - row0); p < p1; ++p)
+          P[p * ldp + j + 1 + lane] = csub<T>(P[p * ldp + j + 1 + lane], cmul<T>(VV[p], cw));
+      }
+      if (warp == 0) {
+        // g_a (a < j) sits in lane nc + a; T(0:j, j) = -tau_j T(0:j, 0:j) g
+        cx<T> acc2 = mk<T>(0, 0);
+        for (int l = 0; l < j; ++l) {
+          const cx<T> gl = mk<T>(__shfl_sync(0xffffffffu, w.x, nc + l), __shfl_sync(0xffffffffu, w.y, nc + l));
+          if (lane <= l) cfma<T>(acc2, Ts[lane * (KBMAX + 1) + l], gl);
+        }
+        if (lane < j) { const cx<T> r = cmul<T>(tau, acc2); Ts[lane * (KBMAX + 1) + j] = mk<T>(-r.x, -r.y); }
+        if (lane == j) Ts[j * (KBMAX + 1) + j] = tau;
+      }
     } else {
-      // kb == 1: single column, no update and T = tau
-      for (int p = tid; p < nloc; p += PT) {
-        const int g = row0 + p;
-        if (g > j) P[p * ldp + j] = cmul<T>(P[p * ldp + j], scale);
-        else if (g == j) P[p * ldp + j] = mk<T>(beta, T(0));
-      }
       if (tid == 0) Ts[0] = tau;
-      __syncthreads();
     }
+    // column j <- v below the pivot, beta on it
+    for (int p = p0 + lane; p < p1; p += 32) {
+      const int g = row0 + p;
+      if (g > j) P[p * ldp + j] = VV[p];
+      else if (g == j) P[p * ldp + j] = mk<T>(beta, T(0));
+    }
+    __syncthreads();
   }
+  if (!ok && tid == 0) atomicOr(a.err, DEVERR_TIMEOUT);
 
   if (rank == 0) {
     for (int idx = tid; idx < kb * kb; idx += PT) {
@@ -234,7 +352,7 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
     a.V[(k0 + g) * a.ldv + k0 + c] = (g == c) ? mk<T>(1, 0) : (g > c ? pv : mk<T>(0, 0));
     a.A[(k0 + g) * a.lda + k0 + c] = (c >= g) ? pv : mk<T>(0, 0);
   }
-  cl.sync();  // no CTA leaves while others may still store into its shared memory
+  cl.sync();  // no CTA exits while a copy into its shared memory could be pending
 }
 
 template <typename T>

@@ -51,3 +51,19 @@ def test_qr_rank_deficient_gives_isometry(prec):
     tol = TOL[prec]
     assert np.abs(Q.conj().T @ Q - np.eye(60)).max() < tol * 5
     assert np.linalg.norm(Q @ R - A) / np.linalg.norm(A) < tol
+
+
+@pytest.mark.parametrize("prec", list(TOL))
+def test_qr_zero_and_tiny_columns(prec):
+    # columns that are exactly zero or at the underflow edge (the rank-deficient blocks
+    # of a product-state start) must give finite, unitary reflectors
+    tiny = 1e-23 if prec != "c128" else 1e-160
+    A = np.zeros((6, 4), np.complex128)
+    A[0, 0] = 1.0
+    A[2, 1] = tiny
+    A[1, 2] = 0.5 + 0.5j
+    A[3, 3] = tiny * 1j
+    Q, R = _run(prec, A)
+    assert np.isfinite(Q).all() and np.isfinite(R).all()
+    assert np.abs(Q.conj().T @ Q - np.eye(4)).max() < TOL[prec] * 5
+    assert np.abs(Q @ R - A).max() < TOL[prec]
