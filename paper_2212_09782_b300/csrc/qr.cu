@@ -245,10 +245,15 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
     // ---- C: the reflector, redundantly in every thread (working precision only)
     T beta, tr, ti, sr, si;
     {
+      // every warp sums the CS partials with a shuffle tree (lane r holds rank r's)
       NAcc<T> s;
       T alr = 0, ali = 0;
-      const T* rr = recv1 + buf * 16 * R1;
-      for (int r = 0; r < CS; ++r) { s.add(rr[r * R1], rr[r * R1 + 1]); alr += rr[r * R1 + 2]; ali += rr[r * R1 + 3]; }
+      if (lane < CS) {
+        const T* rr = recv1 + (buf * 16 + lane) * R1;
+        s.add(rr[0], rr[1]); alr = rr[2]; ali = rr[3];
+      }
+      s.shfl_sum();
+      alr = warp_sum_t<T>(alr); ali = warp_sum_t<T>(ali);
       const T xn2 = s.value();
       beta = alr; tr = ti = sr = si = T(0);
       // A column whose squared norm is below the normal range (noise of a rank-deficient
@@ -280,14 +285,29 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
     if (nslot > 0) {
       cx<T> acc = mk<T>(0, 0);
       if (lane < nslot) {
+        // slot < nc: conj(v) . P[:, c];  slot >= nc: conj(v_a) . v  (= conj of v^dag v_a)
         const bool is_w = lane < nc;
         const int col = is_w ? j + 1 + lane : lane - nc;
-        for (int p = max(p0, j - row0); p < p1; ++p) {
-          const cx<T> v = VV[p];
-          const cx<T> x = P[p * ldp + col];
-          if (is_w) { acc.x += v.x * x.x + v.y * x.y; acc.y += v.x * x.y - v.y * x.x; }  // conj(v) x
-          else { acc.x += x.x * v.x + x.y * v.y; acc.y += x.x * v.y - x.y * v.x; }        // conj(v_a) v
+        const T sg = is_w ? T(1) : T(-1);
+        cx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0), a2 = mk<T>(0, 0), a3 = mk<T>(0, 0);
+        int p = max(p0, j - row0);
+        for (; p + 3 < p1; p += 4) {
+          cx<T> v, x;
+          v = VV[p]; x = P[p * ldp + col];
+          a0.x += v.x * x.x + v.y * x.y; a0.y += v.x * x.y - v.y * x.x;
+          v = VV[p + 1]; x = P[(p + 1) * ldp + col];
+          a1.x += v.x * x.x + v.y * x.y; a1.y += v.x * x.y - v.y * x.x;
+          v = VV[p + 2]; x = P[(p + 2) * ldp + col];
+          a2.x += v.x * x.x + v.y * x.y; a2.y += v.x * x.y - v.y * x.x;
+          v = VV[p + 3]; x = P[(p + 3) * ldp + col];
+          a3.x += v.x * x.x + v.y * x.y; a3.y += v.x * x.y - v.y * x.x;
         }
+        for (; p < p1; ++p) {
+          const cx<T> v = VV[p], x = P[p * ldp + col];
+          a0.x += v.x * x.x + v.y * x.y; a0.y += v.x * x.y - v.y * x.x;
+        }
+        acc.x = (a0.x + a1.x) + (a2.x + a3.x);
+        acc.y = sg * ((a0.y + a1.y) + (a2.y + a3.y));
       }
       wp2[warp * SLOTS + lane] = acc;
       __syncthreads();
@@ -311,21 +331,18 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
       }
       if (lane < nc) {
         const cx<T> cw = cmul<T>(cconj<T>(tau), w);  // conj(tau) w_c
-        for (int p = max(p0, j - row0); p < p1; ++p)
-          P[p * ldp + j + 1 + lane] = csub<T>(P[p * ldp + j + 1 + lane], cmul<T>(VV[p], cw));
-      }
-      if (warp == 0) {
-        // g_a (a < j) sits in lane nc + a; T(0:j, j) = -tau_j T(0:j, 0:j) g
-        cx<T> acc2 = mk<T>(0, 0);
-        for (int l = 0; l < j; ++l) {
-          const cx<T> gl = mk<T>(__shfl_sync(0xffffffffu, w.x, nc + l), __shfl_sync(0xffffffffu, w.y, nc + l));
-          if (lane <= l) cfma<T>(acc2, Ts[lane * (KBMAX + 1) + l], gl);
+        cx<T>* col = P + j + 1 + lane;
+        int p = max(p0, j - row0);
+        for (; p + 1 < p1; p += 2) {
+          const cx<T> x0 = col[p * ldp], x1 = col[(p + 1) * ldp];
+          const cx<T> v0 = VV[p], v1 = VV[p + 1];
+          col[p * ldp] = csub<T>(x0, cmul<T>(v0, cw));
+          col[(p + 1) * ldp] = csub<T>(x1, cmul<T>(v1, cw));
         }
-        if (lane < j) { const cx<T> r = cmul<T>(tau, acc2); Ts[lane * (KBMAX + 1) + j] = mk<T>(-r.x, -r.y); }
-        if (lane == j) Ts[j * (KBMAX + 1) + j] = tau;
+        if (p < p1) col[p * ldp] = csub<T>(col[p * ldp], cmul<T>(VV[p], cw));
       }
-    } else {
-      if (tid == 0) Ts[0] = tau;
+      // g_a = v_a^dag v_j (a < j) is kept in column j of Ts for the T recurrence at the end
+      if (warp == 0 && lane >= nc && lane < nslot) Ts[(lane - nc) * (KBMAX + 1) + j] = w;
     }
     // column j <- v below the pivot, beta on it
     for (int p = p0 + lane; p < p1; p += 32) {
@@ -336,6 +353,22 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
     __syncthreads();
   }
   if (!ok && tid == 0) atomicOr(a.err, DEVERR_TIMEOUT);
+
+  // compact-WY T, column by column (forward, columnwise): Ts[0:j, j] holds g = V^dag v_j,
+  // T(0:j, j) = -tau_j T(0:j, 0:j) g, T(j, j) = tau_j
+  if (rank == 0 && warp == 0) {
+    for (int j = 0; j < kb; ++j) {
+      const cx<T> tj = taus[j];
+      cx<T> acc2 = mk<T>(0, 0);
+      if (lane < j)
+        for (int l = lane; l < j; ++l) cfma<T>(acc2, Ts[lane * (KBMAX + 1) + l], Ts[l * (KBMAX + 1) + j]);
+      __syncwarp();
+      if (lane < j) { const cx<T> r = cmul<T>(tj, acc2); Ts[lane * (KBMAX + 1) + j] = mk<T>(-r.x, -r.y); }
+      if (lane == j) Ts[j * (KBMAX + 1) + j] = tj;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
 
   if (rank == 0) {
     for (int idx = tid; idx < kb * kb; idx += PT) {
