@@ -305,6 +305,61 @@ def run_ours(args):
     return 0
 
 
+def run_chain(args):
+    """Finite-chain TEBD throughput: L = 128, d = 4 clock model (g = 1.0), bond dimensions
+    min(4^k, 4^(L-k), 512) from a seeded random right-canonical state, plain QR at saturated
+    eta, complex64; each Strang step is three layers, batched across the chain's bonds
+    (--no-batch: one bond after another). A step = 64 + 63 + 64 bond updates."""
+    import torch
+    from paper_2212_09782_b300 import lib as L
+    from paper_2212_09782_b300 import workloads as W
+    Lc, d, chi, g, dt = args.chain_L, 4, args.chain_chi, 1.0, 0.05
+    dims, B, Xi = W.random_right_canonical_mps(Lc, d, chi, seed=W.BASE_SEED + 4)
+    s = L.MPS(Lc, d, chi, precision=args.precision)
+    for m in range(Lc):
+        s.set_site(m, B[m])
+    for b in range(Lc + 1):
+        s.set_bond(b, Xi[b], diagonal=True)
+    gh = L.clock_layer_gates(Lc, d, g, dt / 2)
+    gf = L.clock_layer_gates(Lc, d, g, dt)
+    tr = L.trunc_default(L.PLAIN, chi)
+    step = (lambda: L.tebd_step(s, gh, gf, tr)) if args.no_batch else \
+        (lambda: L.tebd_step_batched([s], [gh], [gf], tr))
+    for _ in range(args.warmup):
+        step()
+    s.sync()
+    torch.cuda.synchronize()
+    n0 = L.launch_count()
+    t0 = time.perf_counter()
+    ev = []
+    for _ in range(args.steps):
+        a = torch.cuda.Event(enable_timing=True)
+        a.record()
+        step()
+        ev.append(a)
+    b = torch.cuda.Event(enable_timing=True)
+    b.record()
+    s.sync()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ms = ev[0].elapsed_time(b)
+    per_step = [ev[i].elapsed_time(ev[i + 1] if i + 1 < len(ev) else b) for i in range(len(ev))]
+    nupd = sum(len(range(p, Lc - 1, 2)) for p in (0, 1, 0))
+    line = {
+        "metric": "TEBD bond updates/s, finite chain L=128 d=4 chi<=512 (batched layers)",
+        "value": args.steps * nupd / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "p50_ms": statistics.median(per_step), "p99_ms": float(np.percentile(per_step, 99)),
+        "host_wall_s": wall, "updates_per_step": nupd, "gpu_launches": L.launch_count() - n0,
+        "dtype": args.precision, "data": "synthetic",
+        "config": {"workload": f"finite chain L={Lc} d=4 chi<={chi} plain, Strang step",
+                   "batched": not args.no_batch},
+    }
+    print(json.dumps(line), flush=True)
+    s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -317,11 +372,17 @@ def main():
     ap.add_argument("--d", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", choices=["bond", "chain"], default="bond")
+    ap.add_argument("--chain-L", type=int, default=128)
+    ap.add_argument("--chain-chi", type=int, default=512)
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "chain":
+        return run_chain(args)
     return run_ours(args)
 
 

@@ -199,6 +199,26 @@ int qrtebd_sync(qrtebd_mps* mps);
 int qrtebd_mps_save(qrtebd_mps* mps, const char* path);
 int qrtebd_mps_load(const char* path, void* stream, qrtebd_mps** out);
 
+/* One layer (parity) applied to several states at once (the bonds of a layer are
+ * independent, Fig. 2a). Every bond of `parity` of every state runs concurrently on a
+ * pool of library-owned worker streams (one bond-update workspace each), ordered after
+ * earlier work on each state's stream and before later work on it. gates_host[i]: the
+ * gates of state i (as for qrtebd_apply_gate_layer); eps_out: NULL, or per-state arrays
+ * (entries may be NULL) that receive each updated bond's eps (synchronises). For the
+ * PLAIN scheme no host synchronisation happens, and a layer whose shapes repeat is
+ * recorded as a CUDA graph the second time and replayed afterwards; CBE reads each new
+ * bond dimension back. A state may appear at most once. Not thread-safe per device. */
+int qrtebd_apply_gate_layer_batched(qrtebd_mps* const* states, int nstates, int parity,
+                                    const double* const* gates_host, const qrtebd_trunc* tr,
+                                    double* const* eps_out);
+/* Load a site tensor / bond matrix from host complex128 data (e.g. a random
+ * right-canonical state, or a state produced elsewhere). B_host: (chi_l, d, chi_r);
+ * sets the bond dimensions of bonds `site` and `site+1`. xi_host: chi x chi dense, or
+ * chi diagonal entries when diagonal != 0. INVALID_ARG if a dimension exceeds the
+ * state's capacity. Synchronises. The caller keeps neighbouring dimensions consistent. */
+int qrtebd_mps_set_site(qrtebd_mps* mps, int site, const double* B_host, int chi_l, int chi_r);
+int qrtebd_mps_set_bond(qrtebd_mps* mps, int bond, const double* xi_host, int chi, int diagonal);
+
 /* -------------------------------------------------------------- complex GEMM */
 /* C = alpha opA opB + beta C on device pointers, the contraction every step of
  * Sec. II is built from. opA(i, k) = A[i*sam + k*sak] (conjugated if conj_a),

@@ -4,28 +4,9 @@
 #include <cstring>
 #include <vector>
 
-#include "bond.cuh"
+#include "mps_impl.cuh"
 
 
-struct qrtebd_mps {
-  int L = 0, d = 0, infinite = 0, chi_max = 0, precision = 0;
-  cudaStream_t st = nullptr;
-  int nbonds_store = 0;           // finite: L+1, uniform: L
-  std::vector<int> chi, cap;      // per stored bond
-  std::vector<void*> B;           // per site, capacity cap[m] * d * cap[m+1]
-  std::vector<void*> Xi;          // per bond, dense cap x cap
-  std::vector<void*> xiv;         // per bond, diagonal vector (valid if xi_diag)
-  std::vector<char> xi_diag;
-  double* eps_acc = nullptr;      // per bond, device
-  double* stats = nullptr;        // device double[4]
-  double* layer_eps = nullptr;    // device, per gate bond
-  double2* gates = nullptr;       // device, ngates * d^4
-  void* ws = nullptr;
-  size_t ws_bytes = 0;
-  void* aux = nullptr;            // expectation / schmidt scratch
-  size_t aux_bytes = 0;
-  size_t esz = 0;                 // bytes per complex element
-};
 
 namespace qrtebd {
 namespace {
@@ -149,7 +130,7 @@ int allocate(qrtebd_mps* s) {
     QR_TRY(dev_alloc(&s->xiv[b], (size_t)s->cap[b] * s->esz));
   }
   QR_TRY(dev_alloc((void**)&s->eps_acc, s->nbonds_store * sizeof(double)));
-  QR_TRY(dev_alloc((void**)&s->stats, 8 * sizeof(double)));
+  QR_TRY(dev_alloc((void**)&s->stats, 4 * (size_t)(gate_count(s) + 1) * sizeof(double)));
   QR_TRY(dev_alloc((void**)&s->layer_eps, (gate_count(s) + 1) * sizeof(double)));
   QR_TRY(dev_alloc((void**)&s->gates, (size_t)(gate_count(s) + 1) * d * d * d * d * sizeof(double2)));
   QR_CUDA_TRY(cudaMemsetAsync(s->eps_acc, 0, s->nbonds_store * sizeof(double), s->st));
@@ -191,55 +172,56 @@ template <typename T> int init_product(qrtebd_mps* s, const double* amps) {
 }
 
 template <typename T>
+int update_bond_t(qrtebd_mps* s, int m, const qrtebd_trunc* tr, cudaStream_t st, void* ws,
+                  size_t ws_bytes) {
+  const int d = s->d, d4 = d * d * d * d;
+  const int n = s->infinite ? (m + 1) % s->L : m + 1;
+  const int bl = bond_index(s, m), bmid = bond_index(s, m + 1), br = bond_index(s, m + 2);
+  qrtebd_bond_io io;
+  std::memset(&io, 0, sizeof io);
+  io.precision = s->precision;
+  io.chi_l = s->chi[bl]; io.d = d; io.chi_m = s->chi[bmid]; io.chi_r = s->chi[br];
+  const bool diag = s->xi_diag[bl] != 0;
+  io.xi_kind = diag ? 2 : 1;
+  io.xi = diag ? s->xiv[bl] : s->Xi[bl];
+  io.bm = s->B[m]; io.bn = s->B[n];
+  io.gate = s->gates + (size_t)m * d4;
+  io.bm_out = s->B[m]; io.bn_out = s->B[n]; io.xi_out = s->Xi[bmid];
+  io.stats_out = s->stats + 4 * (size_t)m;
+  io.workspace = ws; io.workspace_bytes = ws_bytes;
+  qrtebd_trunc t = *tr;
+  if (t.chi_max > s->cap[bmid]) t.chi_max = s->cap[bmid];
+  qrtebd_bond_info info;
+  QR_TRY(bond_update(&io, &t, st, &info, nullptr));
+  s->chi[bmid] = info.chi_new;
+  s->xi_diag[bmid] = (t.scheme == QRTEBD_CBE) ? 1 : 0;
+  if (s->xi_diag[bmid]) {
+    k_diag_of<T><<<(unsigned)ceil_div(info.chi_new, 128), 128, 0, st>>>(
+        static_cast<cx<T>*>(s->Xi[bmid]), info.chi_new, static_cast<cx<T>*>(s->xiv[bmid]));
+    note_launch();
+  }
+  k_acc_eps<<<1, 1, 0, st>>>(s->stats + 4 * (size_t)m, s->eps_acc + bmid, s->layer_eps + m);
+  note_launch();
+  QR_CUDA_TRY(cudaGetLastError());
+  return QRTEBD_OK;
+}
+
+template <typename T>
 int apply_layer_t(qrtebd_mps* s, int parity, const double* gates_host, const qrtebd_trunc* tr,
                   double* eps_out) {
-  const int d = s->d, d4 = d * d * d * d, ng = gate_count(s);
-  std::vector<int> bonds;
-  for (int m = parity; m < ng; m += 2) bonds.push_back(m);
-  for (int m : bonds)
-    QR_CUDA_TRY(cudaMemcpyAsync(s->gates + (size_t)m * d4, gates_host + 2 * (size_t)m * d4,
-                                d4 * sizeof(double2), cudaMemcpyHostToDevice, s->st));
-  for (int m : bonds) {
-    const int n = s->infinite ? (m + 1) % s->L : m + 1;
-    const int bl = bond_index(s, m), bmid = bond_index(s, m + 1), br = bond_index(s, m + 2);
-    qrtebd_bond_io io;
-    std::memset(&io, 0, sizeof io);
-    io.precision = s->precision;
-    io.chi_l = s->chi[bl]; io.d = d; io.chi_m = s->chi[bmid]; io.chi_r = s->chi[br];
-    const bool diag = s->xi_diag[bl] != 0;
-    io.xi_kind = diag ? 2 : 1;
-    io.xi = diag ? s->xiv[bl] : s->Xi[bl];
-    io.bm = s->B[m]; io.bn = s->B[n];
-    io.gate = s->gates + (size_t)m * d4;
-    io.bm_out = s->B[m]; io.bn_out = s->B[n]; io.xi_out = s->Xi[bmid];
-    io.stats_out = s->stats;
-    qrtebd_trunc t = *tr;
-    if (t.chi_max > s->cap[bmid]) t.chi_max = s->cap[bmid];
+  const int ng = gate_count(s);
+  QR_TRY(mps_upload_gates(s, parity, gates_host));
+  for (int m = parity; m < ng; m += 2) {
     size_t need = 0;
-    {
-      qrtebd_bond_io q = io;
-      QR_TRY(bond_update(&q, &t, nullptr, nullptr, &need));
-    }
+    QR_TRY(mps_bond_ws_need(s, m, tr, &need));
     QR_TRY(ensure_ws(s, need));
-    io.workspace = s->ws; io.workspace_bytes = s->ws_bytes;
-    qrtebd_bond_info info;
-    QR_TRY(bond_update(&io, &t, s->st, &info, nullptr));
-    s->chi[bmid] = info.chi_new;
-    s->xi_diag[bmid] = (t.scheme == QRTEBD_CBE) ? 1 : 0;
-    if (s->xi_diag[bmid]) {
-      k_diag_of<T><<<(unsigned)ceil_div(info.chi_new, 128), 128, 0, s->st>>>(
-          static_cast<cx<T>*>(s->Xi[bmid]), info.chi_new, static_cast<cx<T>*>(s->xiv[bmid]));
-      note_launch();
-    }
-    k_acc_eps<<<1, 1, 0, s->st>>>(s->stats, s->eps_acc + bmid, eps_out ? s->layer_eps + m : nullptr);
-    note_launch();
-    QR_CUDA_TRY(cudaGetLastError());
+    QR_TRY(update_bond_t<T>(s, m, tr, s->st, s->ws, s->ws_bytes));
   }
   if (eps_out) {
     std::vector<double> le(ng + 1);
     QR_CUDA_TRY(cudaMemcpyAsync(le.data(), s->layer_eps, ng * sizeof(double), cudaMemcpyDeviceToHost, s->st));
     QR_CUDA_TRY(cudaStreamSynchronize(s->st));
-    for (int m : bonds) eps_out[m] = le[m];
+    for (int m = parity; m < ng; m += 2) eps_out[m] = le[m];
   }
   return QRTEBD_OK;
 }
@@ -354,6 +336,37 @@ template <typename T> int schmidt_t(qrtebd_mps* s, int b, double* S, int capacit
 const unsigned kMagic = 0x51525442u;  // "QRTB"
 
 }  // namespace
+
+int mps_gate_count(const qrtebd_mps* s) { return gate_count(s); }
+
+int mps_upload_gates(qrtebd_mps* s, int parity, const double* gates_host) {
+  const int d = s->d, d4 = d * d * d * d, ng = gate_count(s);
+  for (int m = parity; m < ng; m += 2)
+    QR_CUDA_TRY(cudaMemcpyAsync(s->gates + (size_t)m * d4, gates_host + 2 * (size_t)m * d4,
+                                d4 * sizeof(double2), cudaMemcpyHostToDevice, s->st));
+  return QRTEBD_OK;
+}
+
+int mps_bond_ws_need(const qrtebd_mps* s, int m, const qrtebd_trunc* tr, size_t* need) {
+  const int bl = bond_index(s, m), bmid = bond_index(s, m + 1), br = bond_index(s, m + 2);
+  qrtebd_bond_io io;
+  std::memset(&io, 0, sizeof io);
+  io.precision = s->precision;
+  io.chi_l = s->chi[bl]; io.d = s->d; io.chi_m = s->chi[bmid]; io.chi_r = s->chi[br];
+  io.xi_kind = s->xi_diag[bl] ? 2 : 1;
+  static const char dummy = 0;
+  io.bm = &dummy;
+  qrtebd_trunc t = *tr;
+  if (t.chi_max > s->cap[bmid]) t.chi_max = s->cap[bmid];
+  return bond_update(&io, &t, nullptr, nullptr, need);
+}
+
+int mps_update_bond(qrtebd_mps* s, int m, const qrtebd_trunc* tr, cudaStream_t st, void* ws,
+                    size_t ws_bytes) {
+  return s->precision == QRTEBD_C128 ? update_bond_t<double>(s, m, tr, st, ws, ws_bytes)
+                                     : update_bond_t<float>(s, m, tr, st, ws, ws_bytes);
+}
+
 }  // namespace qrtebd
 
 using namespace qrtebd;
@@ -382,7 +395,8 @@ int qrtebd_mps_create(const qrtebd_mps_desc* desc, void* stream, qrtebd_mps** ou
 
 int qrtebd_mps_destroy(qrtebd_mps* s) {
   if (!s) return QRTEBD_OK;
-  cudaStreamSynchronize(s->st);
+  executor_forget_state(s);
+  cudaDeviceSynchronize();  // batched layers may still run on the executor's streams
   free_all(s);
   delete s;
   return QRTEBD_OK;

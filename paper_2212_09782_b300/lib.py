@@ -288,6 +288,10 @@ def _mps_sigs():
         "qrtebd_sync": (I, [P]),
         "qrtebd_mps_save": (I, [P, C.c_char_p]),
         "qrtebd_mps_load": (I, [C.c_char_p, P, PP]),
+        "qrtebd_apply_gate_layer_batched": (I, [C.POINTER(C.c_void_p), I, I, C.POINTER(C.POINTER(D)),
+                                                C.POINTER(Trunc), C.POINTER(C.POINTER(D))]),
+        "qrtebd_mps_set_site": (I, [P, I, C.POINTER(D), I, I]),
+        "qrtebd_mps_set_bond": (I, [P, I, C.POINTER(D), I, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(_lib, name)
@@ -379,6 +383,19 @@ class MPS:
     def sync(self):
         check(_lib.qrtebd_sync(self.h), "sync")
 
+    def set_site(self, site, B):
+        """Load site tensor B (chi_l, d, chi_r) from host data."""
+        B = np.ascontiguousarray(np.asarray(B, np.complex128))
+        check(_lib.qrtebd_mps_set_site(self.h, site, _dptr(B.view(np.float64)), B.shape[0],
+                                       B.shape[2]), "mps_set_site")
+
+    def set_bond(self, bond, xi, diagonal=False):
+        """Load bond matrix Xi (chi x chi, or its chi diagonal entries) from host data."""
+        xi = np.ascontiguousarray(np.asarray(xi, np.complex128))
+        chi = xi.shape[0]
+        check(_lib.qrtebd_mps_set_bond(self.h, bond, _dptr(xi.view(np.float64)), chi,
+                                       1 if diagonal else 0), "mps_set_bond")
+
     def save(self, path):
         check(_lib.qrtebd_mps_save(self.h, str(path).encode()), "mps_save")
 
@@ -409,6 +426,27 @@ def clock_layer_gates(L, d, g, tau, infinite=False):
             wr = 1.0 if b == L - 2 else 0.5
         out[b] = clock_bond_gate(d, g, wl, wr, tau)
     return out
+
+
+def apply_layer_batched(states, parity, gates, trunc, want_eps=False):
+    """One layer on several states at once (qrtebd_apply_gate_layer_batched)."""
+    n = len(states)
+    arrs = [np.ascontiguousarray(np.asarray(g, np.complex128).reshape(s.nbonds, -1)).view(np.float64)
+            for s, g in zip(states, gates)]
+    hs = (C.c_void_p * n)(*[s.h.value if isinstance(s.h, C.c_void_p) else s.h for s in states])
+    gp = (C.POINTER(C.c_double) * n)(*[_dptr(a) for a in arrs])
+    eps = [np.zeros(s.nbonds) for s in states] if want_eps else None
+    ep = (C.POINTER(C.c_double) * n)(*[_dptr(e) for e in eps]) if want_eps else None
+    check(_lib.qrtebd_apply_gate_layer_batched(hs, n, parity, gp, C.byref(trunc), ep),
+          "apply_gate_layer_batched")
+    return eps
+
+
+def tebd_step_batched(states, halves, fulls, trunc):
+    """Strang step on several states, each layer batched across them."""
+    apply_layer_batched(states, 0, halves, trunc)
+    apply_layer_batched(states, 1, fulls, trunc)
+    apply_layer_batched(states, 0, halves, trunc)
 
 
 def tebd_step(mps, half, full, trunc):

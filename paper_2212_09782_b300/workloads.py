@@ -74,3 +74,16 @@ def near_identity_gate(r, d, scale):
     H = (A + A.conj().T) / 2
     w, V = np.linalg.eigh(H)
     return (V * np.exp(-1j * scale * w)) @ V.conj().T
+
+
+def random_right_canonical_mps(L, d, chi_max, seed):
+    """Random finite MPS with bond dimensions chi_b = min(d^b, d^(L-b), chi_max):
+    right-isometric site tensors and diagonal, positive, descending, unit-norm Xi."""
+    r = rng(seed)
+    dims = [min(d ** min(b, L - b), chi_max) if min(b, L - b) < 64 else chi_max for b in range(L + 1)]
+    B = [random_right_isometry(r, dims[m], d, dims[m + 1]) for m in range(L)]
+    Xi = []
+    for b in range(L + 1):
+        x = np.sort(r.random(dims[b]))[::-1] + 1e-3
+        Xi.append(x / np.linalg.norm(x))
+    return dims, B, Xi
