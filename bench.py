@@ -360,6 +360,27 @@ def run_chain(args):
     return 0
 
 
+def run_serve(args):
+    """Continuous-batching quench service: a seeded Poisson mix (rate 4/s) with L in
+    {32, 64, 128}, d in {3, 4, 5}, chi_max in {128, 256, 512, 1024}, g in [0.5, 2],
+    dt = 0.05, plain QR, complex64; --serve-requests / --serve-steps bound the run."""
+    from paper_2212_09782_b300 import serve
+    reqs = serve.poisson_mix(args.serve_requests, 4.0, seed=2212_09782 + 5, steps=args.serve_steps)
+    srv = serve.QuenchServer(precision=args.precision)
+    for r in reqs:
+        srv.submit(r)
+    m = srv.run()
+    line = {"metric": "quench serving: aggregate bond updates/s, p50/p99 per-step latency",
+            "value": m["bond_updates_per_s"], "unit": UNIT, "n_gpus": 1,
+            "p50_ms": m["p50_step_latency_ms"], "p99_ms": m["p99_step_latency_ms"],
+            "higher_is_better": True, "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": f"{args.serve_requests} quench requests, Poisson 4/s, "
+                                   f"{args.serve_steps} Strang steps each"},
+            "detail": m}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -372,7 +393,9 @@ def main():
     ap.add_argument("--d", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["bond", "chain"], default="bond")
+    ap.add_argument("--workload", choices=["bond", "chain", "serve"], default="bond")
+    ap.add_argument("--serve-requests", type=int, default=12)
+    ap.add_argument("--serve-steps", type=int, default=6)
     ap.add_argument("--chain-L", type=int, default=128)
     ap.add_argument("--chain-chi", type=int, default=512)
     ap.add_argument("--no-batch", action="store_true")
@@ -383,6 +406,8 @@ def main():
         return run_reference(args)
     if args.workload == "chain":
         return run_chain(args)
+    if args.workload == "serve":
+        return run_serve(args)
     return run_ours(args)
 
 

@@ -134,22 +134,9 @@ int allocate(qrtebd_mps* s) {
   QR_TRY(dev_alloc((void**)&s->layer_eps, (gate_count(s) + 1) * sizeof(double)));
   QR_TRY(dev_alloc((void**)&s->gates, (size_t)(gate_count(s) + 1) * d * d * d * d * sizeof(double2)));
   QR_CUDA_TRY(cudaMemsetAsync(s->eps_acc, 0, s->nbonds_store * sizeof(double), s->st));
-  // initial workspace: the largest plain update over all bonds
-  qrtebd_trunc tr;
-  qrtebd_trunc_default(&tr, QRTEBD_PLAIN, s->chi_max);
-  size_t need = 0;
-  for (int m = 0; m < gate_count(s); ++m) {
-    int bl = bond_index(s, m), bmid = bond_index(s, m + 1), br = bond_index(s, m + 2);
-    size_t bytes = 0;
-    qrtebd_bond_io io;
-    std::memset(&io, 0, sizeof io);
-    io.precision = s->precision; io.chi_l = s->cap[bl]; io.d = d; io.chi_m = s->cap[bmid];
-    io.chi_r = s->cap[br]; io.xi_kind = 1;
-    static const char dummy = 0;
-    io.bm = &dummy;
-    if (bond_update(&io, &tr, nullptr, nullptr, &bytes) == QRTEBD_OK) need = std::max(need, bytes);
-  }
-  return ensure_ws(s, need);
+  // the bond-update workspace is allocated on first use (single-state layers);
+  // batched layers use the executor's per-worker workspaces instead
+  return QRTEBD_OK;
 }
 
 template <typename T> int init_product(qrtebd_mps* s, const double* amps) {

@@ -1,0 +1,43 @@
+"""Host-side pieces of the quench server: footprints, admission decisions, request mix."""
+import numpy as np
+
+from paper_2212_09782_b300 import serve
+
+
+def test_state_bytes_scale_with_caps():
+    small = serve.Request(0, 32, 3, 128, 1.0, 5)
+    big = serve.Request(1, 128, 5, 1024, 1.0, 5)
+    a = serve.state_bytes(small, "c64_3xtf32")
+    b = serve.state_bytes(big, "c64_3xtf32")
+    assert b > 100 * a
+    # complex128 doubles the tensor bytes
+    assert serve.state_bytes(big, "c128") > 1.9 * b
+    caps = serve.chain_caps(8, 3, 10)
+    assert caps == [1, 3, 9, 10, 10, 10, 9, 3, 1]
+
+
+def test_admission_waits_then_rejects_what_never_fits():
+    free = {"v": 0}
+    srv = serve.QuenchServer(mem_free=lambda: free["v"], mem_total=lambda: 40 << 30,
+                             reserve_bytes=0)
+    req = serve.Request(0, 64, 4, 512, 1.0, 5)
+    need = srv.footprint(req)
+    free["v"] = need - 1
+    ok, ever = srv._fits(req)
+    assert not ok and ever
+    free["v"] = need
+    ok, ever = srv._fits(req)
+    assert ok and ever
+    huge = serve.Request(1, 128, 5, 1 << 16, 1.0, 5)
+    ok, ever = srv._fits(huge)
+    assert not ever
+
+
+def test_poisson_mix_is_seeded():
+    a = serve.poisson_mix(16, 4.0, seed=5)
+    b = serve.poisson_mix(16, 4.0, seed=5)
+    assert [(r.L, r.d, r.chi_max, r.g, r.arrival) for r in a] == \
+           [(r.L, r.d, r.chi_max, r.g, r.arrival) for r in b]
+    gaps = np.diff([0.0] + [r.arrival for r in a])
+    assert np.all(gaps > 0)
+    assert {r.L for r in a} <= {32, 64, 128} and {r.d for r in a} <= {3, 4, 5}
