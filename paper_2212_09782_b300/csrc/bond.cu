@@ -304,8 +304,11 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
   cx<T>* Zc = (eps_explicit && !cbe) ? ar.take<cx<T>>((size_t)nR * eta) : nullptr;
   cx<T>* LV = (eps_explicit && cbe) ? ar.take<cx<T>>((size_t)eta * eta) : nullptr;
   cx<T>* Yt = (eps_explicit && cbe) ? ar.take<cx<T>>((size_t)eta * nR) : nullptr;
-  TcWorkspace tcw;
+  TcWorkspace tcw, tcw_side;
   if (use_tc) tc_carve(ar, (int)std::max(mL, nR), (int)std::max(mL, nR), eta, tcw);
+  // the QR's look-ahead updates run on a side stream with their own workspaces
+  if (use_tc) tc_carve(ar, (int)std::max(mL, nR), (int)std::max(mL, nR), eta, tcw_side);
+  cx<T>* simt_scratch_side = simt_elems ? ar.take<cx<T>>(simt_elems) : nullptr;
 
   if (measuring) { *bytes = ar.off; return QRTEBD_OK; }
   if (ar.overflow()) {
@@ -315,6 +318,8 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
   unsigned* err = device_error_word();
   GemmRunner<T> runner{io->precision, use_tc ? &tcw : nullptr, simt_scratch, simt_elems};
   QrGemm<T> qg{qr_gemm_thunk<T>, &runner};
+  GemmRunner<T> runner_side{io->precision, use_tc ? &tcw_side : nullptr, simt_scratch_side, simt_elems};
+  QrGemm<T> qg_side{qr_gemm_thunk<T>, &runner_side};
   const cx<T> one = mk<T>(1, 0), zero = mk<T>(0, 0);
 
   // (i) theta' = B^m B^n
@@ -363,7 +368,7 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
     g.reuse_a = true;  // theta~ is read again, unchanged, by the last contraction
     QR_TRY(runner.run(g, st));
   }
-  QR_TRY(householder_qr<T>(X, eta, (int)mL, eta, Q, eta, qs, st, err, &qg));
+  QR_TRY(householder_qr<T>(X, eta, (int)mL, eta, Q, eta, qs, st, err, &qg, &qg_side));
 
   // (ii) Z = theta~^dag Q, QR(Z) -> Qz, Rz
   {
@@ -372,7 +377,7 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
     QR_TRY(runner.run(g, st));
   }
   if (Zc) QR_CUDA_TRY(cudaMemcpyAsync(Zc, Z, (size_t)nR * eta * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st));
-  QR_TRY(householder_qr<T>(Z, eta, (int)nR, eta, Qz, eta, qs, st, err, &qg));
+  QR_TRY(householder_qr<T>(Z, eta, (int)nR, eta, Qz, eta, qs, st, err, &qg, &qg_side));
 
   cx<T>* bn_out = static_cast<cx<T>*>(io->bn_out);
   cx<T>* xi_out = static_cast<cx<T>*>(io->xi_out);

@@ -115,25 +115,28 @@ int qr_entry(int precision, int m, int n, void* A, long long lda, void* Q, long 
   if (!need) { ar.base = static_cast<char*>(ws); ar.cap = bytes; }
   QrScratch<T> qs;
   qr_carve<T>(ar, m, n, qs);
-  TcWorkspace tcw;
+  TcWorkspace tcw, tcw_side;
   const bool tc = std::is_same<T, float>::value &&
                   (precision == QRTEBD_C64_3XTF32 || precision == QRTEBD_C64_TF32);
   if (tc) tc_carve(ar, std::max(m, n), m, std::max(m, n), tcw);
+  if (tc) tc_carve(ar, std::max(m, n), m, std::max(m, n), tcw_side);
   if (need) { *need = ar.off; return QRTEBD_OK; }
   if (ar.overflow() || !ws) { set_last_message("qr: workspace too small"); return QRTEBD_ERR_OOM; }
   struct Ctx { TcWorkspace* w; bool three; bool tc; };
   Ctx ctx{&tcw, precision == QRTEBD_C64_3XTF32, tc};
-  QrGemm<T> qg;
-  qg.ctx = &ctx;
-  qg.fn = [](const GemmArgs<T>& g, cudaStream_t s, void* c) -> int {
+  Ctx ctx_side{&tcw_side, precision == QRTEBD_C64_3XTF32, tc};
+  auto fn = [](const GemmArgs<T>& g, cudaStream_t s, void* c) -> int {
     Ctx* x = static_cast<Ctx*>(c);
     if constexpr (std::is_same<T, float>::value) {
       if (x->tc && tc_gemm_eligible(g)) return tc_gemm(g, x->three, *x->w, s);
     }
     return gemm_simt<T>(g, s, nullptr, 0);
   };
+  QrGemm<T> qg, qg_side;
+  qg.ctx = &ctx; qg.fn = fn;
+  qg_side.ctx = &ctx_side; qg_side.fn = fn;
   return householder_qr<T>(static_cast<cx<T>*>(A), lda, m, n, static_cast<cx<T>*>(Q), ldq, qs, st,
-                           device_error_word(), &qg);
+                           device_error_word(), &qg, &qg_side);
 }
 }  // namespace
 }  // namespace qrtebd

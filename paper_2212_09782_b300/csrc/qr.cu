@@ -18,6 +18,9 @@
 #include <cooperative_groups.h>
 
 #include <limits>
+#include <map>
+#include <mutex>
+#include <vector>
 
 #include "qr.cuh"
 
@@ -461,6 +464,29 @@ template <typename T> int launch_panel(const PanelArgs<T>& pa, int cs, cudaStrea
   return QRTEBD_OK;
 }
 
+// Side streams for look-ahead, one per (device, main stream), with reusable events.
+struct SideStream {
+  cudaStream_t st = nullptr;
+  std::vector<cudaEvent_t> ev;
+};
+std::mutex g_side_mu;
+std::map<std::pair<int, cudaStream_t>, SideStream> g_side;
+
+int side_stream(cudaStream_t main, int nev, SideStream** out) {
+  int dev = 0;
+  QR_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_side_mu);
+  SideStream& ss = g_side[std::make_pair(dev, main)];
+  if (!ss.st) QR_CUDA_TRY(cudaStreamCreateWithFlags(&ss.st, cudaStreamNonBlocking));
+  while ((int)ss.ev.size() < nev) {
+    cudaEvent_t e;
+    QR_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ss.ev.push_back(e);
+  }
+  *out = &ss;
+  return QRTEBD_OK;
+}
+
 template <typename T>
 int run_gemm(const GemmArgs<T>& g, const QrScratch<T>& s, cudaStream_t st, const QrGemm<T>* gm) {
   if (gm && gm->fn) return gm->fn(g, st, gm->ctx);
@@ -488,6 +514,8 @@ template <typename T> void qr_carve(Arena& ar, int m, int n, QrScratch<T>& s) {
   s.Tf = ar.take<cx<T>>((size_t)(n + nbo) * nbo);
   s.W = ar.take<cx<T>>((size_t)nbo * n);
   s.W2 = ar.take<cx<T>>((size_t)nbo * n);
+  s.Ws = ar.take<cx<T>>((size_t)nbo * n);
+  s.W2s = ar.take<cx<T>>((size_t)nbo * n);
   s.G = ar.take<cx<T>>((size_t)nbo * nbo);
   s.tmp = ar.take<cx<T>>((size_t)nbo * KBMAX);
   size_t e = 0;
@@ -502,7 +530,8 @@ template <typename T> void qr_carve(Arena& ar, int m, int n, QrScratch<T>& s) {
 
 template <typename T>
 int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ldq,
-                   QrScratch<T>& s, cudaStream_t st, unsigned* err, const QrGemm<T>* gm) {
+                   QrScratch<T>& s, cudaStream_t st, unsigned* err, const QrGemm<T>* gm,
+                   const QrGemm<T>* side) {
   if (m < n || n < 1) return QRTEBD_ERR_INVALID_ARG;
   QR_TRY(probe_max_cluster<T>());
   const int nb = qr_panel_width(m, n, sizeof(cx<T>));
@@ -514,9 +543,19 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
   // above its later inner panels, which those panels do not write
   QR_CUDA_TRY(cudaMemsetAsync(s.V, 0, (size_t)m * n * sizeof(cx<T>), st));
 
+  const int nblk = (int)ceil_div(n, nbo);
+  SideStream* ss = nullptr;
+  if (side && side->fn && nblk > 2) QR_TRY(side_stream(st, 2 * nblk, &ss));
+  std::vector<char> rec(nblk, 0);  // which blocks recorded a side-stream update
+  // latest side-stream update of a block <= k (the side stream runs them in order)
+  auto latest = [&](int k) { for (int j = std::min(k, nblk - 1); j >= 0; --j) if (rec[j]) return j; return -1; };
   for (int ko = 0; ko < n; ko += nbo) {
     const int kbo = std::min(nbo, n - ko);
     const int mo = m - ko;
+    const int kblk = ko / nbo;
+    // this block's columns must have received the side-stream updates of blocks <= k-2
+    if (ss && latest(kblk - 2) >= 0)
+      QR_CUDA_TRY(cudaStreamWaitEvent(st, ss->ev[nblk + latest(kblk - 2)], 0));
     cx<T>* Tb = s.Tf + (size_t)(ko / nbo) * nbo * nbo;
     QR_CUDA_TRY(cudaMemsetAsync(Tb, 0, (size_t)nbo * nbo * sizeof(cx<T>), st));
     for (int ki = ko; ki < ko + kbo; ki += nb) {
@@ -555,18 +594,38 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
         QR_TRY(gemm_simt<T>(t2, st, s.gemm_scratch, s.gemm_scratch_elems));
       }
     }
-    // outer trailing update: C <- (I - V T V^dag)^dag C
+    // outer trailing update: C <- (I - V T V^dag)^dag C. With look-ahead the next outer
+    // block's columns are updated here and the rest on the side stream, overlapping the
+    // next block's panels.
     const int nc = n - ko - kbo;
     if (nc > 0) {
-      cx<T>* C = A + (long long)ko * lda + ko + kbo;
-      GemmArgs<T> g1{kbo, nc, mo, Vb, 1, ldv, true, C, lda, 1, false, s.W, nc, 1, one, zero};
-      QR_TRY(run_gemm<T>(g1, s, st, gm));
-      GemmArgs<T> g2{kbo, nc, kbo, Tb, 1, nbo, true, s.W, nc, 1, false, s.W2, nc, 1, one, zero};
-      QR_TRY(run_gemm<T>(g2, s, st, gm));
-      GemmArgs<T> g3{mo, nc, kbo, Vb, ldv, 1, false, s.W2, nc, 1, false, C, lda, 1, mone, one};
-      QR_TRY(run_gemm<T>(g3, s, st, gm));
+      auto update = [&](int c0, int cw, cudaStream_t stream, cx<T>* W, cx<T>* W2,
+                        const QrGemm<T>* g) -> int {
+        cx<T>* C = A + (long long)ko * lda + ko + kbo + c0;
+        GemmArgs<T> g1{kbo, cw, mo, Vb, 1, ldv, true, C, lda, 1, false, W, cw, 1, one, zero};
+        QR_TRY(run_gemm<T>(g1, s, stream, g));
+        GemmArgs<T> g2{kbo, cw, kbo, Tb, 1, nbo, true, W, cw, 1, false, W2, cw, 1, one, zero};
+        QR_TRY(run_gemm<T>(g2, s, stream, g));
+        GemmArgs<T> g3{mo, cw, kbo, Vb, ldv, 1, false, W2, cw, 1, false, C, lda, 1, mone, one};
+        QR_TRY(run_gemm<T>(g3, s, stream, g));
+        return QRTEBD_OK;
+      };
+      const int n1 = ss ? std::min(nbo, nc) : nc;
+      // the next block's columns also carry block k-1's side-stream update: order after it
+      if (ss && latest(kblk - 1) >= 0)
+        QR_CUDA_TRY(cudaStreamWaitEvent(st, ss->ev[nblk + latest(kblk - 1)], 0));
+      QR_TRY(update(0, n1, st, s.W, s.W2, gm));
+      if (ss && nc > n1) {
+        QR_CUDA_TRY(cudaEventRecord(ss->ev[kblk], st));  // V, T of this block are ready
+        QR_CUDA_TRY(cudaStreamWaitEvent(ss->st, ss->ev[kblk], 0));
+        QR_TRY(update(n1, nc - n1, ss->st, s.Ws, s.W2s, side));
+        QR_CUDA_TRY(cudaEventRecord(ss->ev[nblk + kblk], ss->st));
+        rec[kblk] = 1;
+      }
     }
   }
+  if (ss && latest(nblk - 1) >= 0)
+    QR_CUDA_TRY(cudaStreamWaitEvent(st, ss->ev[nblk + latest(nblk - 1)], 0));
 
   // explicit Q by backward accumulation over the outer blocks
   {
@@ -596,8 +655,10 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
 template void qr_carve<float>(Arena&, int, int, QrScratch<float>&);
 template void qr_carve<double>(Arena&, int, int, QrScratch<double>&);
 template int householder_qr<float>(float2*, long long, int, int, float2*, long long,
-                                   QrScratch<float>&, cudaStream_t, unsigned*, const QrGemm<float>*);
+                                   QrScratch<float>&, cudaStream_t, unsigned*, const QrGemm<float>*,
+                                   const QrGemm<float>*);
 template int householder_qr<double>(double2*, long long, int, int, double2*, long long,
-                                    QrScratch<double>&, cudaStream_t, unsigned*, const QrGemm<double>*);
+                                    QrScratch<double>&, cudaStream_t, unsigned*,
+                                    const QrGemm<double>*, const QrGemm<double>*);
 
 }  // namespace qrtebd

@@ -20,6 +20,8 @@ template <typename T> struct QrScratch {
   cx<T>* Tf = nullptr;     // ceil(n/nb) blocks of nb x nb triangular factors
   cx<T>* W = nullptr;      // nb x n
   cx<T>* W2 = nullptr;     // nb x n
+  cx<T>* Ws = nullptr;     // W, W2 of the look-ahead (side-stream) updates
+  cx<T>* W2s = nullptr;
   cx<T>* G = nullptr;      // outer-block Gram matrix V^dag V
   cx<T>* tmp = nullptr;    // T assembly scratch
   cx<T>* gemm_scratch = nullptr;
@@ -36,9 +38,12 @@ template <typename T> void qr_carve(Arena& ar, int m, int n, QrScratch<T>& s);
 // upper n x n triangle holds R (real diagonal, LAPACK geqrf sign convention) and
 // everything below is zeroed. Q (m x n, leading dimension ldq) receives the
 // explicit isometry with A_in = Q R. err: device error word.
+// side_gemm (optional, with its own workspaces): runs the part of each outer trailing
+// update beyond the next outer block on a library-owned side stream (look-ahead), so the
+// next block's panel chain starts as soon as its own columns are updated.
 template <typename T>
 int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ldq,
                    QrScratch<T>& s, cudaStream_t st, unsigned* err,
-                   const QrGemm<T>* gemm = nullptr);
+                   const QrGemm<T>* gemm = nullptr, const QrGemm<T>* side_gemm = nullptr);
 
 }  // namespace qrtebd
