@@ -1,15 +1,15 @@
 // Blocked Householder QR with explicit Q; see qr.cuh.
 //
 // Panel (nb columns): one thread-block cluster of up to 16 CTAs holds the panel
-// in shared memory, each CTA a contiguous slab of rows. Every column needs two
-// cluster-wide reductions - the reflector norm ||x||^2 (always FP64, with the
-// pivot alpha riding along) and w = v^dag A_panel - done with partial sums in
-// each CTA's shared memory, a hardware cluster barrier and distributed-shared-
-// memory reads. Reflectors follow LAPACK's zlarfg convention
-// (beta = -sign(Re alpha) ||(alpha, x)||, tau = (beta - alpha) / beta,
-// v = [1, x / (alpha - beta)]), so R has a real diagonal. The panel also builds
-// the compact-WY factor T (upper triangular, forward columnwise) from the Gram
-// matrix V^dag V, so that H_1 ... H_nb = I - V T V^dag.
+// in shared memory: every CTA a copy of the panel's first nb rows (the pivot rows)
+// and a contiguous slab of the rows below. Every column needs one cluster-wide
+// reduction - the reflector norm together with the raw column dot products, from
+// which w = v^dag A_panel follows - pushed into every CTA's shared memory by remote
+// stores that complete on the receiver's mbarrier. Reflectors follow LAPACK's zlarfg
+// convention (beta = -sign(Re alpha) ||(alpha, x)||, tau = (beta - alpha) / beta,
+// v = [1, x / (alpha - beta)]), so R has a real diagonal. The panel also builds the
+// compact-WY factor T (upper triangular) from the Gram values v_a^dag v_j, so that
+// H_1 ... H_nb = I - V T V^dag.
 //
 // Trailing update per panel:   C <- (I - V T V^dag)^dag C = C - V (T^dag (V^dag C))
 // Explicit Q (backward):       Q[k0:, k0:] <- (I - V T V^dag) Q[k0:, k0:], Q = [I; 0] initially
@@ -33,20 +33,16 @@ namespace {
 constexpr int PT = 256;      // threads per panel CTA
 constexpr int KBMAX = 32;    // widest panel
 constexpr int NBO = 128;     // outer block of the two-level blocking
-constexpr int RED = 3 * 16 + 4;  // 3 doubles per cluster rank
-constexpr int SMEM_CAP = 220 * 1024;
 
 template <typename T> struct PanelArgs {
   cx<T>* A; long long lda; int m; int k0; int kb;
   cx<T>* V; long long ldv;
   cx<T>* tau; cx<T>* Tf; int ldt;
-  int rpc; unsigned* err;
+  int rps; unsigned* err;  // rps: slab rows per CTA below the replicated first kb rows
 };
 
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
 
-template <typename T> struct PanelSmem;
-template <typename T> __host__ __device__ inline size_t panel_smem_bytes(int rpc, int kb);
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -60,17 +56,24 @@ template <typename T> __device__ __forceinline__ T warp_sum_t(T v) {
 }
 
 // ---------------------------------------------------------------- panel kernel
-// One 32-column Householder panel on a cluster of CS CTAs; CTA r holds panel rows
-// [r*rpc, (r+1)*rpc) in shared memory. Per column j:
-//   A. partial ||x||^2 below the pivot and alpha, summed over the CTA's warps;
-//   B. all-to-all: every CTA copies its partial into slot [rank] of every CTA's
-//      receive buffer with one cp.async.bulk (distributed shared memory) whose
-//      completion is counted on the receiver's mbarrier; no cluster barrier;
-//   C. every thread forms the reflector (zlarfg convention) from the CS partials;
-//   D. per-warp rows: v = x * scale, dot products with lane = slot: slots < nc give
-//      w_c = v^dag P[:, c], slots >= nc give g_a = v_a^dag v (compact-WY T column);
-//   E. all-to-all of the slot partials as in B;
-//   F. P[:, c] -= v conj(tau) w_c (lane = column), T(0:j, j) = -tau T(0:j, 0:j) g.
+// One Householder panel of kb <= 32 columns on a cluster of CS CTAs. Local rows of
+// every CTA: the panel's first kb rows (a replica, updated identically everywhere, so
+// each CTA has the pivot row of every column) followed by its slab of rps rows below;
+// the replica enters rank 0's partial sums only.
+// A reflector needs ||x||^2 below its pivot and w_c = v^dag P[:, c] for the columns it
+// updates. With v = scale * x below the pivot and 1 on it, w_c = P[j, c] + conj(scale) S_c
+// where S_c = sum_{g > j} conj(x_g) P[g, c] does not depend on scale; the Gram values of
+// the compact-WY factor, g_a = v_a^dag v_j, come from the same sums. So each column takes
+// ONE cluster-wide exchange of (||x||^2 partial, S_c partials), and the pass over the rows
+// that applies reflector j also forms the partials of column j+1:
+//   1. lane = row: v of reflector j, column j+1 updated in place, ||x_{j+1}||^2 partial;
+//   2. lane = column c: P[:, c] -= v conj(tau) w_c (c > j+1), S_c partial (every c);
+//   3. warp 0 sums the warps' partials and pushes them to every CTA: 16-byte st.async
+//      remote stores, counted on the receiver's mbarrier (double-buffered by parity);
+//   4. warp 0 forms the next reflector (zlarfg convention) and conj(tau) w_c for every
+//      column, and hands them to the other warps through shared memory.
+// Columns are stored raw (x, not v) during the panel; v = scale * x is written at the
+// end. T comes last, by recursive doubling over the Gram values.
 // The norm accumulates in double-float for complex64 (two FP32 words, error-free
 // FMA products and TwoSum additions, ~48-bit significand) and in FP64 for complex128:
 // B300's FP64 pipe is too narrow for the panel's critical path, and the reflector is
@@ -132,263 +135,307 @@ __device__ __forceinline__ bool mbar_wait_cl(uint64_t* b, uint32_t parity) {
   }
   return false;
 }
-// copy `bytes` (multiple of 16) from this CTA's shared memory to CTA `rank`, counted on
-// that CTA's mbarrier
-__device__ __forceinline__ void dsmem_send(const void* src, void* dst_local, uint64_t* mbar_local,
-                                           int rank, uint32_t bytes) {
-  const uint32_t d = map_rank(smem_addr(dst_local), rank);
-  const uint32_t m = map_rank(smem_addr(mbar_local), rank);
-  asm volatile(
-      "cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-      ::"r"(d), "r"(smem_addr(src)), "r"(bytes), "r"(m) : "memory");
+constexpr int SLOTS = KBMAX;              // column slots per message (padded)
+
+template <typename T> __device__ __forceinline__ cx<T> shfl_cx(cx<T> v, int src) {
+  return mk<T>(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
+}
+__device__ __forceinline__ void st_async_16(uint32_t addr, float4 v, uint32_t mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+               ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void st_async_16(uint32_t addr, double2 v, uint32_t mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];"
+               ::"r"(addr), "d"(v.x), "d"(v.y), "r"(mbar) : "memory");
 }
 
-constexpr int SLOTS = KBMAX;              // slot partials per exchange (padded)
+// reflector scalars (zlarfg convention) from ||x||^2 below the pivot and alpha, with
+// correctly rounded square root and divisions: the unitarity of H = I - tau v v^dag
+// rests on tau and scale agreeing with ||v|| to working precision
+template <typename T>
+__device__ __forceinline__ void reflector(T xn2, T alr, T ali, T& beta, T& tr, T& ti, T& sr, T& si) {
+  beta = alr; tr = ti = sr = si = T(0);
+  // A column whose squared norm is below the normal range (noise of a rank-deficient
+  // block) is left as is: tau = 0, H = I, which is exactly unitary.
+  const T tot = alr * alr + ali * ali + xn2;
+  if (!(xn2 == T(0) && ali == T(0)) && tot > T(16) * std::numeric_limits<T>::min()) {
+    const T nrm = sqrt(tot);
+    beta = alr >= T(0) ? -nrm : nrm;
+    tr = (beta - alr) / beta;
+    ti = -ali / beta;
+    // scale = 1 / (alpha - beta) by Smith's division; |alr - beta| >= |ali|
+    const T dr = alr - beta, di = ali;
+    const T rt = di / dr, den = dr + di * rt;
+    sr = T(1) / den; si = -rt / den;
+  }
+}
 
 template <typename T> struct PanelSmem {
-  // per-column exchange buffers, double-buffered by column parity
-  static constexpr int R1 = 4;            // reduction-1 payload: norm (hi, lo) or (v, 0), alpha re, im
-  static constexpr size_t fixed() {
-    return a16(2 * 16 * R1 * sizeof(T))            // recv1 [2][16][R1]
-         + a16(R1 * sizeof(T))                     // send1
-         + a16(2 * 16 * SLOTS * sizeof(cx<T>))     // recv2 [2][16][SLOTS]
-         + a16(SLOTS * sizeof(cx<T>))              // send2
-         + a16(8 * R1 * sizeof(T))                 // per-warp reduction-1 partials
-         + a16(8 * SLOTS * sizeof(cx<T>))          // per-warp slot partials
-         + a16(KBMAX * sizeof(cx<T>))              // taus
-         + a16(KBMAX * (KBMAX + 1) * sizeof(cx<T>))  // T
-         + 64;                                     // 4 mbarriers
+  static constexpr int HDR = 16;
+  static constexpr int MSG = HDR + SLOTS * (int)sizeof(cx<T>);
+  static constexpr size_t fixed(int nw) {
+    return a16(2 * 16 * MSG)                               // recv [2][16]
+         + a16(2 * SLOTS * sizeof(cx<T>))                  // pivot row copies [2]
+         + a16((size_t)nw * 16)                            // per-warp norm partials
+         + a16((size_t)nw * SLOTS * sizeof(cx<T>))         // per-warp slot partials
+         + 3 * a16(KBMAX * sizeof(cx<T>))                  // tau, scale, beta
+         + a16(KBMAX * (KBMAX + 1) * sizeof(cx<T>))        // g, then T
+         + a16(2 * (SLOTS + 2) * sizeof(cx<T>))            // broadcast: cw[32], scale, tau
+         + 64;
   }
 };
-
-template <typename T> __host__ __device__ inline size_t panel_smem_bytes(int rpc, int kb) {
-  return a16((size_t)rpc * (kb + 1) * sizeof(cx<T>)) + a16((size_t)rpc * sizeof(cx<T>)) +
-         PanelSmem<T>::fixed();
+// local rows: the panel's first kb rows (every CTA) followed by this CTA's slab
+template <typename T> __host__ __device__ inline size_t panel_smem_bytes(int rps, int kb) {
+  const size_t rows = (size_t)kb + rps;
+  return a16(rows * (kb + 1) * sizeof(cx<T>)) + a16(rows * sizeof(cx<T>)) + PanelSmem<T>::fixed(PT / 32);
 }
-
 template <typename T>
 __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
+  constexpr int NT = PT;
+  using L = PanelSmem<T>;
+  constexpr int NW = NT / 32;
   extern __shared__ __align__(16) unsigned char sm[];
   cg::cluster_group cl = cg::this_cluster();
   const int CS = (int)cl.num_blocks();
   const int rank = (int)cl.block_rank();
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int NW = PT / 32;
-  constexpr int R1 = PanelSmem<T>::R1;
-  const int kb = a.kb, ldp = kb + 1, rpc = a.rpc;
+  const int kb = a.kb, ldp = kb + 1, rps = a.rps;
   const int mr = a.m - a.k0;
-  const int row0 = rank * rpc;
-  const int nloc = max(0, min(rpc, mr - row0));
-  const int rpw = (nloc + NW - 1) / NW;              // rows per warp
+  const int s0 = kb + rank * rps;                           // first slab row (panel index)
+  const int nslab = max(0, min(rps, mr - s0));
+  const int nloc = kb + nslab;
+  const int rpw = (nloc + NW - 1) / NW;
   const int p0 = min(nloc, warp * rpw), p1 = min(nloc, p0 + rpw);
+  const bool top_counts = rank == 0;                        // top rows enter rank 0's sums only
+  auto grow = [&](int p) { return p < kb ? p : s0 + (p - kb); };
 
   unsigned char* q = sm;
-  cx<T>* P = reinterpret_cast<cx<T>*>(q); q += a16((size_t)rpc * ldp * sizeof(cx<T>));
-  cx<T>* VV = reinterpret_cast<cx<T>*>(q); q += a16((size_t)rpc * sizeof(cx<T>));
-  T* recv1 = reinterpret_cast<T*>(q); q += a16(2 * 16 * R1 * sizeof(T));
-  T* send1 = reinterpret_cast<T*>(q); q += a16(R1 * sizeof(T));
-  cx<T>* recv2 = reinterpret_cast<cx<T>*>(q); q += a16(2 * 16 * SLOTS * sizeof(cx<T>));
-  cx<T>* send2 = reinterpret_cast<cx<T>*>(q); q += a16(SLOTS * sizeof(cx<T>));
-  T* wp1 = reinterpret_cast<T*>(q); q += a16(8 * R1 * sizeof(T));
-  cx<T>* wp2 = reinterpret_cast<cx<T>*>(q); q += a16(8 * SLOTS * sizeof(cx<T>));
+  cx<T>* P = reinterpret_cast<cx<T>*>(q); q += a16((size_t)(kb + rps) * ldp * sizeof(cx<T>));
+  cx<T>* VB = reinterpret_cast<cx<T>*>(q); q += a16((size_t)(kb + rps) * sizeof(cx<T>));
+  unsigned char* recvm = q; q += a16(2 * 16 * L::MSG);
+  cx<T>* pivb = reinterpret_cast<cx<T>*>(q); q += a16(2 * SLOTS * sizeof(cx<T>));
+  T* wpn = reinterpret_cast<T*>(q); q += a16((size_t)NW * 16);
+  cx<T>* wps = reinterpret_cast<cx<T>*>(q); q += a16((size_t)NW * SLOTS * sizeof(cx<T>));
   cx<T>* taus = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * sizeof(cx<T>));
+  cx<T>* scl = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * sizeof(cx<T>));
+  cx<T>* bet = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * sizeof(cx<T>));
   cx<T>* Ts = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * (KBMAX + 1) * sizeof(cx<T>));
-  uint64_t* mb = reinterpret_cast<uint64_t*>(q);     // mb[0..1] reduction 1, mb[2..3] reduction 2
+  cx<T>* bc = reinterpret_cast<cx<T>*>(q); q += a16(2 * (SLOTS + 2) * sizeof(cx<T>));
+  uint64_t* mb = reinterpret_cast<uint64_t*>(q);
 
   const long long k0 = a.k0;
-  for (int idx = tid; idx < nloc * kb; idx += PT) {
-    const int p = idx / kb, c = idx % kb;
-    P[p * ldp + c] = a.A[(k0 + row0 + p) * a.lda + k0 + c];
-  }
   if (tid == 0) {
-    for (int i = 0; i < 4; ++i) mbar_init1(&mb[i]);
+    mbar_init1(&mb[0]);
+    mbar_init1(&mb[1]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  cl.sync();  // every CTA's barriers exist before anyone sends
+  // load: lane = column, this warp's rows, all copies in flight (cp.async, no registers)
+  if (lane < kb) {
+    for (int p = p0; p < p1; ++p) {
+      const cx<T>* src = a.A + (k0 + grow(p)) * a.lda + k0 + lane;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(P + p * ldp + lane)),
+                   "l"(src), "n"((int)sizeof(cx<T>)) : "memory");
+    }
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  cl.sync();  // every CTA's barriers exist before anyone sends; panel loaded
   bool ok = true;
+  const uint32_t txb = (uint32_t)(CS * L::MSG);
 
-  for (int j = 0; j < kb; ++j) {
-    const int buf = j & 1;
-    const uint32_t ph = (uint32_t)((j >> 1) & 1);
-    // ---- A: partial norm below the pivot, alpha
-    {
-      NAcc<T> acc;
-      T ar = 0, ai = 0;
-      for (int p = p0 + lane; p < p1; p += 32) {
-        const int g = row0 + p;
-        const cx<T> v = P[p * ldp + j];
-        if (g > j) { acc.add_sq(v.x); acc.add_sq(v.y); }
-        else if (g == j) { ar = v.x; ai = v.y; }
+  const cx<T> zero = mk<T>(0, 0);
+  cx<T> scale = zero, cw = zero, cwn = zero;
+
+  for (int jn = 0; jn < kb; ++jn) {
+    const int jp = jn - 1;
+    // local index = panel row for the top block, and g(p) is increasing in p
+    const int plo = max(p0, min(p1, max(jp, 0)));
+    // ---- 1. lane = row
+    NAcc<T> nacc;
+    for (int p = plo + lane; p < p1; p += 64) {
+      const bool two = p + 32 < p1;
+      cx<T> r0 = P[p * ldp + jn], r1 = zero, u0 = zero, u1 = zero;
+      if (jp >= 0) u0 = P[p * ldp + jp];
+      if (two) { r1 = P[(p + 32) * ldp + jn]; if (jp >= 0) u1 = P[(p + 32) * ldp + jp]; }
+      cx<T> v0 = zero, v1 = zero;
+      if (jp >= 0) { v0 = (p == jp) ? mk<T>(1, 0) : cmul<T>(scale, u0); v1 = cmul<T>(scale, u1); }
+      r0 = csub<T>(r0, cmul<T>(v0, cwn));
+      r1 = csub<T>(r1, cmul<T>(v1, cwn));
+      P[p * ldp + jn] = r0; VB[p] = v0;
+      if (p > jn && (top_counts || p >= kb)) { nacc.add_sq(r0.x); nacc.add_sq(r0.y); }
+      if (two) {
+        P[(p + 32) * ldp + jn] = r1; VB[p + 32] = v1;
+        if (p + 32 > jn && (top_counts || p + 32 >= kb)) { nacc.add_sq(r1.x); nacc.add_sq(r1.y); }
       }
-      acc.shfl_sum();
-      ar = warp_sum_t<T>(ar); ai = warp_sum_t<T>(ai);
-      if (lane == 0) {
-        if constexpr (std::is_same<T, float>::value) { wp1[warp * R1 + 0] = acc.hi; wp1[warp * R1 + 1] = acc.lo; }
-        else { wp1[warp * R1 + 0] = acc.value(); wp1[warp * R1 + 1] = 0; }
-        wp1[warp * R1 + 2] = ar; wp1[warp * R1 + 3] = ai;
-      }
-    }
-    __syncthreads();
-    if (warp == 0) {
-      if (lane == 0) {
-        NAcc<T> s;
-        T ar = 0, ai = 0;
-        for (int w = 0; w < NW; ++w) { s.add(wp1[w * R1], wp1[w * R1 + 1]); ar += wp1[w * R1 + 2]; ai += wp1[w * R1 + 3]; }
-        if constexpr (std::is_same<T, float>::value) { send1[0] = s.hi; send1[1] = s.lo; }
-        else { send1[0] = s.value(); send1[1] = 0; }
-        send1[2] = ar; send1[3] = ai;
-        mbar_arm(&mb[buf], (uint32_t)(CS * R1 * sizeof(T)));
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      }
-      __syncwarp();
-      if (lane < CS)
-        dsmem_send(send1, recv1 + (buf * 16 + rank) * R1, &mb[buf], lane, R1 * sizeof(T));
-    }
-    if (!mbar_wait_cl(&mb[buf], ph)) ok = false;
-    // ---- C: the reflector, redundantly in every thread (working precision only)
-    T beta, tr, ti, sr, si;
-    {
-      // every warp sums the CS partials with a shuffle tree (lane r holds rank r's)
-      NAcc<T> s;
-      T alr = 0, ali = 0;
-      if (lane < CS) {
-        const T* rr = recv1 + (buf * 16 + lane) * R1;
-        s.add(rr[0], rr[1]); alr = rr[2]; ali = rr[3];
-      }
-      s.shfl_sum();
-      alr = warp_sum_t<T>(alr); ali = warp_sum_t<T>(ali);
-      const T xn2 = s.value();
-      beta = alr; tr = ti = sr = si = T(0);
-      // A column whose squared norm is below the normal range (noise of a rank-deficient
-      // block) is left as is: tau = 0, H = I, which is exactly unitary.
-      const T tot = alr * alr + ali * ali + xn2;
-      if (!(xn2 == T(0) && ali == T(0)) && tot > T(16) * std::numeric_limits<T>::min()) {
-        const T nrm = sqrt(tot);
-        beta = alr >= T(0) ? -nrm : nrm;
-        tr = (beta - alr) / beta;
-        ti = -ali / beta;
-        const T dr = alr - beta, di = ali;  // scale = 1 / (alpha - beta), Smith's division
-        if (fabs(dr) >= fabs(di)) { const T rt = di / dr, den = dr + di * rt; sr = T(1) / den; si = -rt / den; }
-        else { const T rt = dr / di, den = di + dr * rt; sr = rt / den; si = T(-1) / den; }
-      }
-      if (tid == 0 && rank == 0 && !(isfinite(beta) && isfinite(sr) && isfinite(si)))
-        atomicOr(a.err, DEVERR_NUMERIC);
-    }
-    const cx<T> scale = mk<T>(sr, si), tau = mk<T>(tr, ti);
-    if (tid == 0) taus[j] = tau;
-    // ---- D: v for this warp's rows, then slot partials (lane = slot)
-    const int nc = kb - j - 1;
-    const int nslot = nc + j;
-    for (int p = p0 + lane; p < p1; p += 32) {
-      const int g = row0 + p;
-      if (g > j) VV[p] = cmul<T>(P[p * ldp + j], scale);
-      else if (g == j) VV[p] = mk<T>(1, 0);
     }
     __syncwarp();
-    if (nslot > 0) {
-      cx<T> acc = mk<T>(0, 0);
-      if (lane < nslot) {
-        // slot < nc: conj(v) . P[:, c];  slot >= nc: conj(v_a) . v  (= conj of v^dag v_a)
-        const bool is_w = lane < nc;
-        const int col = is_w ? j + 1 + lane : lane - nc;
-        const T sg = is_w ? T(1) : T(-1);
-        cx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0), a2 = mk<T>(0, 0), a3 = mk<T>(0, 0);
-        int p = max(p0, j - row0);
-        for (; p + 3 < p1; p += 4) {
-          cx<T> v, x;
-          v = VV[p]; x = P[p * ldp + col];
-          a0.x += v.x * x.x + v.y * x.y; a0.y += v.x * x.y - v.y * x.x;
-          v = VV[p + 1]; x = P[(p + 1) * ldp + col];
-          a1.x += v.x * x.x + v.y * x.y; a1.y += v.x * x.y - v.y * x.x;
-          v = VV[p + 2]; x = P[(p + 2) * ldp + col];
-          a2.x += v.x * x.x + v.y * x.y; a2.y += v.x * x.y - v.y * x.x;
-          v = VV[p + 3]; x = P[(p + 3) * ldp + col];
-          a3.x += v.x * x.x + v.y * x.y; a3.y += v.x * x.y - v.y * x.x;
-        }
-        for (; p < p1; ++p) {
-          const cx<T> v = VV[p], x = P[p * ldp + col];
-          a0.x += v.x * x.x + v.y * x.y; a0.y += v.x * x.y - v.y * x.x;
-        }
-        acc.x = (a0.x + a1.x) + (a2.x + a3.x);
-        acc.y = sg * ((a0.y + a1.y) + (a2.y + a3.y));
-      }
-      wp2[warp * SLOTS + lane] = acc;
-      __syncthreads();
-      if (warp == 0) {
-        cx<T> s = mk<T>(0, 0);
-        for (int w = 0; w < NW; ++w) s = cadd<T>(s, wp2[w * SLOTS + lane]);
-        send2[lane] = s;
-        // every sender copies its nslot values rounded up to 16 bytes
-        const uint32_t bytes = (uint32_t)(nslot * sizeof(cx<T>) + 15) & ~15u;
-        if (lane == 0) mbar_arm(&mb[2 + buf], (uint32_t)CS * bytes);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane < CS) dsmem_send(send2, recv2 + (buf * 16 + rank) * SLOTS, &mb[2 + buf], lane, bytes);
-      }
-      if (!mbar_wait_cl(&mb[2 + buf], ph)) ok = false;
-      // ---- F: update (lane = column) and the T column
-      cx<T> w = mk<T>(0, 0);
-      if (lane < nslot) {
-        const cx<T>* rr = recv2 + buf * 16 * SLOTS + lane;
-        for (int r = 0; r < CS; ++r) w = cadd<T>(w, rr[r * SLOTS]);
-      }
-      if (lane < nc) {
-        const cx<T> cw = cmul<T>(cconj<T>(tau), w);  // conj(tau) w_c
-        cx<T>* col = P + j + 1 + lane;
-        int p = max(p0, j - row0);
-        for (; p + 1 < p1; p += 2) {
-          const cx<T> x0 = col[p * ldp], x1 = col[(p + 1) * ldp];
-          const cx<T> v0 = VV[p], v1 = VV[p + 1];
-          col[p * ldp] = csub<T>(x0, cmul<T>(v0, cw));
-          col[(p + 1) * ldp] = csub<T>(x1, cmul<T>(v1, cw));
-        }
-        if (p < p1) col[p * ldp] = csub<T>(col[p * ldp], cmul<T>(VV[p], cw));
-      }
-      // g_a = v_a^dag v_j (a < j) is kept in column j of Ts for the T recurrence at the end
-      if (warp == 0 && lane >= nc && lane < nslot) Ts[(lane - nc) * (KBMAX + 1) + j] = w;
+    // ---- 2. lane = column
+    const int col = (lane < kb) ? lane : jn;
+    const bool upd = lane > jn && lane < kb;
+    const int slo = max(plo, min(p1, jn + 1));
+    const int alo = top_counts ? slo : max(slo, min(p1, kb));
+    for (int p = plo; p < alo; ++p) {
+      const cx<T> y = csub<T>(P[p * ldp + col], cmul<T>(VB[p], cw));
+      if (upd) P[p * ldp + col] = y;
     }
-    // column j <- v below the pivot, beta on it
-    for (int p = p0 + lane; p < p1; p += 32) {
-      const int g = row0 + p;
-      if (g > j) P[p * ldp + j] = VV[p];
-      else if (g == j) P[p * ldp + j] = mk<T>(beta, T(0));
+    cx<T> acc0 = zero, acc1 = zero;
+    int p = alo;
+    for (; p + 3 < p1; p += 4) {
+      cx<T> v[4], x[4], y[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) { v[u] = VB[p + u]; x[u] = P[(p + u) * ldp + jn]; y[u] = P[(p + u) * ldp + col]; }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) y[u] = csub<T>(y[u], cmul<T>(v[u], cw));
+      if (upd) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) P[(p + u) * ldp + col] = y[u];
+      }
+      cfma<T>(acc0, cconj<T>(x[0]), y[0]);
+      cfma<T>(acc1, cconj<T>(x[1]), y[1]);
+      cfma<T>(acc0, cconj<T>(x[2]), y[2]);
+      cfma<T>(acc1, cconj<T>(x[3]), y[3]);
+    }
+    for (; p < p1; ++p) {
+      const cx<T> v0 = VB[p], x0 = P[p * ldp + jn];
+      const cx<T> y0 = csub<T>(P[p * ldp + col], cmul<T>(v0, cw));
+      if (upd) P[p * ldp + col] = y0;
+      cfma<T>(acc0, cconj<T>(x0), y0);
+    }
+    nacc.shfl_sum();
+    wps[warp * SLOTS + lane] = cadd<T>(acc0, acc1);
+    if (lane == 0) {
+      if constexpr (std::is_same<T, float>::value) { wpn[warp * 4 + 0] = nacc.hi; wpn[warp * 4 + 1] = nacc.lo; }
+      else { wpn[warp * 2 + 0] = nacc.value(); wpn[warp * 2 + 1] = 0; }
     }
     __syncthreads();
-  }
-  if (!ok && tid == 0) atomicOr(a.err, DEVERR_TIMEOUT);
-
-  // compact-WY T, column by column (forward, columnwise): Ts[0:j, j] holds g = V^dag v_j,
-  // T(0:j, j) = -tau_j T(0:j, 0:j) g, T(j, j) = tau_j
-  if (rank == 0 && warp == 0) {
-    for (int j = 0; j < kb; ++j) {
-      const cx<T> tj = taus[j];
-      cx<T> acc2 = mk<T>(0, 0);
-      if (lane < j)
-        for (int l = lane; l < j; ++l) cfma<T>(acc2, Ts[lane * (KBMAX + 1) + l], Ts[l * (KBMAX + 1) + j]);
+    // ---- 3. exchange (warp 0): pivot row copy, then (norm, slots) to every rank
+    const int buf = jn & 1;
+    if (warp == 0) {
+      cx<T> s = zero;
+#pragma unroll 4
+      for (int w = 0; w < NW; ++w) s = cadd<T>(s, wps[w * SLOTS + lane]);
+      NAcc<T> n;
+      if (lane < NW) {
+        if constexpr (std::is_same<T, float>::value) n.add(wpn[lane * 4], wpn[lane * 4 + 1]);
+        else n.add(wpn[lane * 2], T(0));
+      }
+      n.shfl_sum();
+      cx<T> h;
+      if constexpr (std::is_same<T, float>::value) h = mk<T>(n.hi, n.lo); else h = mk<T>(n.value(), 0);
+      pivb[buf * SLOTS + lane] = P[jn * ldp + min(lane, kb - 1)];
       __syncwarp();
-      if (lane < j) { const cx<T> r = cmul<T>(tj, acc2); Ts[lane * (KBMAX + 1) + j] = mk<T>(-r.x, -r.y); }
-      if (lane == j) Ts[j * (KBMAX + 1) + j] = tj;
-      __syncwarp();
+      if (lane == 0) mbar_arm(&mb[buf], txb);  // release: the pivot copy is visible to the waiters
+      const uint32_t mine = smem_addr(recvm + (buf * 16 + rank) * L::MSG);
+      const uint32_t mbl = smem_addr(&mb[buf]);
+      if constexpr (std::is_same<T, float>::value) {
+        // 17 chunks of 16 bytes: (norm hi, lo, 0, 0), then slot pairs
+        const cx<T> sa = shfl_cx<T>(s, (2 * lane + 30) & 31), sb = shfl_cx<T>(s, (2 * lane + 31) & 31);
+        const float4 ch = lane == 0 ? make_float4(h.x, h.y, 0.f, 0.f) : make_float4(sa.x, sa.y, sb.x, sb.y);
+        if (lane < 17)
+          for (int r = 0; r < CS; ++r) st_async_16(map_rank(mine + 16 * lane, r), ch, map_rank(mbl, r));
+      } else {
+        for (int r = 0; r < CS; ++r) {
+          const uint32_t rb = map_rank(mine, r), rm = map_rank(mbl, r);
+          st_async_16(rb + 16 + 16 * lane, s, rm);
+          if (lane == 0) st_async_16(rb, h, rm);
+        }
+      }
+    }
+    if (warp == 0) {
+      if (!mbar_wait_cl(&mb[buf], (uint32_t)((jn >> 1) & 1))) ok = false;
+      const cx<T>* piv = pivb + buf * SLOTS;
+      NAcc<T> ns;
+      if (lane < CS) {
+        const T* hh = reinterpret_cast<const T*>(recvm + (buf * 16 + lane) * L::MSG);
+        ns.add(hh[0], hh[1]);
+      }
+      cx<T> S0 = zero, S1 = zero;
+      {
+        const unsigned char* base = recvm + buf * 16 * L::MSG + L::HDR + min(lane, kb - 1) * sizeof(cx<T>);
+        int r = 0;
+        for (; r + 1 < CS; r += 2) {
+          S0 = cadd<T>(S0, *reinterpret_cast<const cx<T>*>(base + r * L::MSG));
+          S1 = cadd<T>(S1, *reinterpret_cast<const cx<T>*>(base + (r + 1) * L::MSG));
+        }
+        if (r < CS) S0 = cadd<T>(S0, *reinterpret_cast<const cx<T>*>(base + r * L::MSG));
+      }
+      const cx<T> S = cadd<T>(S0, S1);
+      const cx<T> pc = piv[min(lane, kb - 1)];
+      const cx<T> alpha = piv[jn];
+      ns.shfl_sum();
+      T beta, tr, ti, sr, si;
+      reflector(ns.value(), alpha.x, alpha.y, beta, tr, ti, sr, si);
+      if (lane == 0 && rank == 0 && !(isfinite(beta) && isfinite(sr) && isfinite(si)))
+        atomicOr(a.err, DEVERR_NUMERIC);
+      const cx<T> sc = mk<T>(sr, si), tau = mk<T>(tr, ti);
+      const bool u = lane > jn && lane < kb;
+      const cx<T> cwl = u ? cmul<T>(cconj<T>(tau), cadd<T>(pc, cmul<T>(cconj<T>(sc), S))) : zero;
+      if (lane < jn) {
+        const cx<T> gv = cmul<T>(cconj<T>(scl[lane]), cadd<T>(cconj<T>(pc), cmul<T>(sc, cconj<T>(S))));
+        Ts[lane * (KBMAX + 1) + jn] = gv;
+      }
+      cx<T>* bb = bc + buf * (SLOTS + 2);
+      bb[lane] = cwl;
+      if (lane == 0) { bb[SLOTS] = sc; taus[jn] = tau; scl[jn] = sc; bet[jn] = mk<T>(beta, 0); }
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+    {
+      const cx<T>* bb = bc + buf * (SLOTS + 2);
+      scale = bb[SLOTS];
+      cw = bb[lane];
+      cwn = (jn + 1 < kb) ? bb[jn + 1] : zero;
     }
   }
+  if (!ok && tid == 0) atomicOr(a.err, DEVERR_TIMEOUT);
   __syncthreads();
 
   if (rank == 0) {
-    for (int idx = tid; idx < kb * kb; idx += PT) {
+    // compact-WY T by recursive doubling: for adjacent blocks 1, 2 with factors T1, T2,
+    // T12 = -T1 G12 T2, where G12 = V1^dag V2 is held in the strict upper part of Ts
+    for (int i = tid; i < kb; i += NT) Ts[i * (KBMAX + 1) + i] = taus[i];
+    __syncthreads();
+    cx<T>* X = reinterpret_cast<cx<T>*>(recvm);  // free after the last exchange
+    for (int b = 1; b < kb; b *= 2) {
+      const int nm = (kb - b + 2 * b - 1) / (2 * b);   // merges with a non-empty block 2
+      for (int idx = tid; idx < nm * b * b; idx += NT) {
+        const int m = idx / (b * b), r = idx % (b * b), aa = r / b, jj = r % b;
+        const int s0 = m * 2 * b, j = s0 + b + jj;
+        if (j < kb) {
+          cx<T> acc = zero;
+          for (int k = s0 + b; k <= j; ++k) cfma<T>(acc, Ts[(s0 + aa) * (KBMAX + 1) + k], Ts[k * (KBMAX + 1) + j]);
+          X[idx] = acc;
+        }
+      }
+      __syncthreads();
+      for (int idx = tid; idx < nm * b * b; idx += NT) {
+        const int m = idx / (b * b), r = idx % (b * b), ii = r / b, jj = r % b;
+        const int s0 = m * 2 * b, j = s0 + b + jj, i = s0 + ii;
+        if (j < kb) {
+          cx<T> acc = zero;
+          for (int aa = ii; aa < b; ++aa) cfma<T>(acc, Ts[i * (KBMAX + 1) + s0 + aa], X[m * b * b + aa * b + jj]);
+          Ts[i * (KBMAX + 1) + j] = mk<T>(-acc.x, -acc.y);
+        }
+      }
+      __syncthreads();
+    }
+    for (int idx = tid; idx < kb * kb; idx += NT) {
       const int i = idx / kb, jj = idx % kb;
-      a.Tf[i * a.ldt + jj] = (jj >= i) ? Ts[i * (KBMAX + 1) + jj] : mk<T>(0, 0);
+      a.Tf[i * a.ldt + jj] = (jj >= i) ? Ts[i * (KBMAX + 1) + jj] : zero;
     }
     if (tid < kb) a.tau[k0 + tid] = taus[tid];
   }
-  // ---- write V (explicit, unit lower trapezoidal) and R / zeros into A
-  for (int idx = tid; idx < nloc * kb; idx += PT) {
-    const int p = idx / kb, c = idx % kb;
-    const int g = row0 + p;
-    const cx<T> pv = P[p * ldp + c];
-    a.V[(k0 + g) * a.ldv + k0 + c] = (g == c) ? mk<T>(1, 0) : (g > c ? pv : mk<T>(0, 0));
-    a.A[(k0 + g) * a.lda + k0 + c] = (c >= g) ? pv : mk<T>(0, 0);
+  // ---- V (v = scale * raw column below the pivot, unit diagonal) and R / zeros into A;
+  //      lane = column, the top block from rank 0 only
+  if (lane < kb) {
+    const cx<T> sc = scl[lane], bc = bet[lane];
+    const int pstart = (rank == 0) ? p0 : max(p0, kb);
+    for (int p = pstart; p < p1; ++p) {
+      const int g = grow(p);
+      const cx<T> pv = P[p * ldp + lane];
+      a.V[(k0 + g) * a.ldv + k0 + lane] = (g == lane) ? mk<T>(1, 0) : (g > lane ? cmul<T>(sc, pv) : zero);
+      a.A[(k0 + g) * a.lda + k0 + lane] = (lane > g) ? pv : (lane == g ? bc : zero);
+    }
   }
-  cl.sync();  // no CTA exits while a copy into its shared memory could be pending
+  cl.sync();
 }
 
 template <typename T>
@@ -399,38 +446,60 @@ __global__ void k_eye(cx<T>* Q, long long ldq, int m, int n) {
   Q[i * ldq + j] = mk<T>(i == j ? T(1) : T(0), 0);
 }
 
-struct ClusterChoice { int cs; int rpc; int kb; };
+struct ClusterChoice { int cs; int rps; int kb; };
 
 // Largest cluster the device co-schedules for the panel kernel (16 needs the
-// non-portable opt-in; probed once per process, falls back to 8).
+// non-portable opt-in; probed once per process, falls back to 8), and the opt-in
+// dynamic shared memory per block.
 int g_max_cluster = 0;
+int g_smem_cap = 0;
 
+int smem_cap() {
+  if (g_smem_cap == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess && v > 0)
+      g_smem_cap = v;
+    else
+      g_smem_cap = 227 * 1024;
+  }
+  return g_smem_cap;
+}
+
+// Cluster size, slab rows per CTA and panel width for a panel of mr rows: the
+// smallest power-of-two cluster giving every CTA at most ~192 slab rows, grown (then
+// the width halved) until the panel fits in shared memory.
 template <typename T> ClusterChoice choose_cluster(int mr, int kb_want) {
-  ClusterChoice c{1, mr, kb_want};
   const int cmax = g_max_cluster > 0 ? g_max_cluster : 16;
+  const size_t cap = (size_t)smem_cap();
   int cs = 1;
   while (cs < cmax && (long long)cs * 192 < mr) cs *= 2;
   for (int kb = kb_want; kb >= 1; kb /= 2) {
     for (int s = cs; s <= cmax; s *= 2) {
-      int rpc = (int)ceil_div(mr, s);
-      if (panel_smem_bytes<T>(rpc, kb) <= (size_t)SMEM_CAP) return ClusterChoice{s, rpc, kb};
+      const int rps = (int)ceil_div(std::max(mr - kb, 0), s);
+      if (panel_smem_bytes<T>(rps, kb) <= cap) return ClusterChoice{s, rps, kb};
     }
   }
-  c.cs = -1;
-  return c;
+  return ClusterChoice{-1, 0, kb_want};
 }
 
 template <typename T> bool g_attr_done = false;
+
+template <typename T> int set_panel_attrs() {
+  if (g_attr_done<T>) return QRTEBD_OK;
+  QR_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap()));
+  QR_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  g_attr_done<T> = true;
+  return QRTEBD_OK;
+}
 
 // Probe once whether 16-CTA clusters of the panel kernel (at the largest shared
 // memory size) can be co-scheduled; otherwise cap clusters at 8 CTAs.
 template <typename T> int probe_max_cluster() {
   if (g_max_cluster > 0) return QRTEBD_OK;
-  QR_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_CAP));
-  QR_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-  g_attr_done<T> = true;
+  QR_TRY(set_panel_attrs<T>());
   cudaLaunchConfig_t q = {};
-  q.gridDim = dim3(16, 1, 1); q.blockDim = dim3(PT, 1, 1); q.dynamicSmemBytes = SMEM_CAP;
+  q.gridDim = dim3(16, 1, 1); q.blockDim = dim3(PT, 1, 1); q.dynamicSmemBytes = smem_cap();
   cudaLaunchAttribute qa[1];
   qa[0].id = cudaLaunchAttributeClusterDimension;
   qa[0].val.clusterDim.x = 16; qa[0].val.clusterDim.y = 1; qa[0].val.clusterDim.z = 1;
@@ -443,12 +512,14 @@ template <typename T> int probe_max_cluster() {
 }
 
 template <typename T> int launch_panel(const PanelArgs<T>& pa, int cs, cudaStream_t st) {
-  size_t smem = panel_smem_bytes<T>(pa.rpc, pa.kb);
-  if (!g_attr_done<T>) {
-    QR_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_CAP));
-    QR_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    g_attr_done<T> = true;
+  const size_t smem = panel_smem_bytes<T>(pa.rps, pa.kb);
+  const int mr = pa.m - pa.k0;
+  if (pa.kb < 1 || pa.kb > KBMAX || mr < pa.kb || cs < 1 || cs > 16 || pa.rps < 0 ||
+      (long long)pa.rps * cs < mr - pa.kb || smem > (size_t)smem_cap()) {
+    set_last_message("QR panel: invalid cluster shape");
+    return QRTEBD_ERR_INVALID_ARG;
   }
+  QR_TRY(set_panel_attrs<T>());
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cs, 1, 1);
   cfg.blockDim = dim3(PT, 1, 1);
@@ -562,9 +633,9 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
       const int kb = std::min(nb, ko + kbo - ki);
       const int mr = m - ki;
       ClusterChoice cc = choose_cluster<T>(mr, kb);
-      if (cc.cs < 0 || cc.kb != kb) { cc.kb = kb; cc.cs = 16; cc.rpc = (int)ceil_div(mr, 16); }
+      if (cc.cs < 0 || cc.kb != kb) { cc.kb = kb; cc.cs = 16; cc.rps = (int)ceil_div(mr - kb, 16); }
       cx<T>* Ti = Tb + (size_t)(ki - ko) * nbo + (ki - ko);
-      PanelArgs<T> pa{A, lda, m, ki, kb, s.V, ldv, s.tau, Ti, nbo, cc.rpc, err};
+      PanelArgs<T> pa{A, lda, m, ki, kb, s.V, ldv, s.tau, Ti, nbo, cc.rps, err};
       QR_TRY(launch_panel<T>(pa, cc.cs, st));
       // inner update: the rest of this outer block
       const int nc = ko + kbo - ki - kb;
