@@ -35,6 +35,56 @@ PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustain
 TF32_PER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rate on B300
 
 
+# FP32 / FP64 CUDA-core peaks of a B300 (148 SMs, 128 FP32 FMA lanes per SM, 2032 MHz
+# maximum SM clock; FP64 at the nominal 1.25 TFLOP/s): the denominators of the kernels
+# that run on CUDA cores
+FP32_ALU_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+FP64_ALU_TFLOPS = 1.25
+
+
+def prof_families(L):
+    names = {L.PROF_BOND_GEMM: "bond_gemm", L.PROF_TC_GEMM: "qr_tc_gemm", L.PROF_QR_PANEL: "qr_panel",
+             L.PROF_SIMT_GEMM: "simt_gemm", L.PROF_PREP: "tc_prep", L.PROF_GATE: "gate"}
+    return list(names), names
+
+
+def family_roofline(L, fam, ms, n, flops, nbytes, prec, peaks, src):
+    """Roofline entry of one kernel family: algorithmic flops (or bytes) per launch over
+    the family's average launch duration, against the measured peak of the unit that
+    bounds it."""
+    sec = ms / 1e3 / n
+    tc = prec in (L.C64_3XTF32, L.C64_TF32)
+    out = {"launches": n, "launch_ms": ms / n, "traffic": None}
+    if fam in (L.PROF_BOND_GEMM, L.PROF_TC_GEMM) and tc:
+        achieved = flops / n / sec / 1e12
+        peak = peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]) * TF32_PER_BF16
+        out.update({"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak,
+                    "issued_frac": achieved * (3 if prec == L.C64_3XTF32 else 1) / peak,
+                    "kernel": "k_tc_gemm (3xTF32 complex GEMM)" if prec == L.C64_3XTF32 else "k_tc_gemm (TF32)",
+                    "peak_source": f"{src} bf16 sustained x nominal TF32/BF16 ratio {TF32_PER_BF16:.3f}",
+                    "algorithmic_flops_per_launch": flops / n})
+    elif fam in (L.PROF_PREP, L.PROF_GATE):
+        achieved = nbytes / n / sec / 1e9
+        peak = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
+        out.update({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_source": f"{src} copy bandwidth",
+                    "kernel": "k_prep_a / k_prep_b" if fam == L.PROF_PREP else "k_gate",
+                    "algorithmic_bytes_per_launch": nbytes / n})
+    else:
+        achieved = flops / n / sec / 1e12
+        peak = FP64_ALU_TFLOPS if prec == L.C128 else FP32_ALU_TFLOPS
+        out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "peak_source": "derived CUDA-core peak (SMs x lanes x clock)",
+                    "algorithmic_flops_per_launch": flops / n,
+                    "kernel": {L.PROF_QR_PANEL: "k_qr_panel", L.PROF_SIMT_GEMM: "k_gemm",
+                               L.PROF_BOND_GEMM: "k_gemm", L.PROF_TC_GEMM: "k_gemm"}[fam]})
+        if fam == L.PROF_QR_PANEL:
+            out["limiter"] = "latency: one cluster-wide exchange per column (sequential in the column)"
+            out["achieved_hbm_gbs"] = nbytes / n / sec / 1e9
+    return out
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -176,11 +226,11 @@ def run_ours(args):
     L.stream_check()
     barrier()
 
-    # ---- timed region (inputs live in HBM; theta = 210 MB > 126 MB L2)
+    # ---- timed region (inputs live in HBM; theta = 210 MB > 126 MB L2); no per-kernel
+    #      events here, so kernels overlap their launches as they do in production
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    L.profile_enable(True)
     n0 = L.launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
           for _ in range(args.steps)]
@@ -194,9 +244,6 @@ def run_ours(args):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = ev[0][0].elapsed_time(ev[-1][1])
-    prof = {f: L.profile_read(f) for f in (L.PROF_TC_GEMM, L.PROF_QR_PANEL, L.PROF_SIMT_GEMM,
-                                           L.PROF_PREP, L.PROF_GATE)}
-    L.profile_enable(False)
     L.stream_check()
     t_max = total_ms
     if dist is not None:
@@ -204,6 +251,22 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         t_max = float(t.item())
     value = ws * args.steps / (t_max / 1e3)
+
+    # ---- per-kernel durations: the same steps again, every launch bracketed by CUDA
+    #      events on its stream (the brackets cost a little, hence a separate pass)
+    L.profile_enable(True)
+    barrier()
+    pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pa.record(stream)
+    for i in range(args.steps):
+        up.run(gate, bn, theta=th)
+    pb.record(stream)
+    barrier()
+    prof_step_ms = pa.elapsed_time(pb) / args.steps
+    fams, PROF_NAMES = prof_families(L)
+    prof = {f: L.profile_read(f) for f in fams}
+    L.profile_enable(False)
+    L.stream_check()
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -252,31 +315,16 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    # ---- roofline of the dominant kernel (tcgen05 GEMM for the tensor-core precisions)
+    # ---- roofline of the dominant kernel family (by device time), and of the others
     peaks, src = load_peaks()
-    fam_names = {L.PROF_TC_GEMM: "tc_gemm", L.PROF_QR_PANEL: "qr_panel",
-                 L.PROF_SIMT_GEMM: "simt_gemm", L.PROF_PREP: "tc_prep", L.PROF_GATE: "gate"}
-    breakdown = {fam_names[f]: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
-                 for f, v in prof.items()}
-    dom = max(prof, key=lambda f: prof[f][0])
-    roof = None
-    tc_ms, tc_n, tc_flops, _ = prof[L.PROF_TC_GEMM]
-    if tc_n > 0:
-        per_launch_s = tc_ms / 1e3 / tc_n
-        achieved = tc_flops / tc_n / per_launch_s / 1e12
-        peak = peaks.get("bf16_tflops_sustained", PEAKS_FALLBACK["bf16_tflops_sustained"]) * TF32_PER_BF16
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "k_tc_gemm (3xTF32 complex GEMM)" if prec == L.C64_3XTF32 else "k_tc_gemm (TF32)",
-                "issued_frac": achieved * (3 if prec == L.C64_3XTF32 else 1) / peak,
-                "peak_source": f"{src} bf16 sustained x nominal TF32/BF16 ratio {TF32_PER_BF16:.3f}",
-                "algorithmic_flops_per_launch": tc_flops / tc_n,
-                "launch_ms": tc_ms / tc_n}
-    elif prof[L.PROF_SIMT_GEMM][1] > 0:
-        ms, n, fl, _ = prof[L.PROF_SIMT_GEMM]
-        achieved = fl / n / (ms / 1e3 / n) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "TFLOP/s",
-                "frac": None, "traffic": None, "kernel": "k_gemm (CUDA-core complex GEMM)"}
+    breakdown = {PROF_NAMES[f]: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                 for f, v in prof.items() if v[1] > 0}
+    roofs = {}
+    for f, (ms, n, fl, by) in prof.items():
+        if n > 0:
+            roofs[PROF_NAMES[f]] = family_roofline(L, f, ms, n, fl, by, prec, peaks, src)
+    dom = max((f for f in prof if prof[f][1] > 0), key=lambda f: prof[f][0])
+    roof = roofs.get(PROF_NAMES[dom])
 
     cpu = None
     if not args.no_cpu_baseline and ws == 1:
@@ -297,7 +345,8 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "inputs larger than L2 (theta 210 MB)", "precision": args.precision},
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-        "kernel_breakdown": breakdown, "dominant_family": fam_names[dom], "clocks": clk,
+        "kernel_breakdown": breakdown, "dominant_family": PROF_NAMES[dom],
+        "roofline_by_family": roofs, "profiled_ms_per_step": prof_step_ms, "clocks": clk,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

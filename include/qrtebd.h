@@ -283,6 +283,9 @@ int qrtebd_clock_bond_gate(int d, double g, double wl, double wr, double tau_re,
 #define QRTEBD_PROF_SIMT_GEMM 2 /* CUDA-core complex GEMM kernel */
 #define QRTEBD_PROF_PREP 3      /* tensor-core operand preparation (split / embed) */
 #define QRTEBD_PROF_GATE 4      /* two-site gate application */
+#define QRTEBD_PROF_BOND_GEMM 5 /* the bond-level contractions X = theta~ Y0^dag, Z = theta~^dag Q and
+                                   the outputs (tensor-core or CUDA-core GEMM); the QR's
+                                   own GEMMs count under QRTEBD_PROF_TC_GEMM / _SIMT_GEMM */
 /* Number of kernels the library has launched since it was loaded (host counter). */
 long long qrtebd_launch_count(void);
 /* on != 0: record a CUDA event pair around every launch of the families above, on

@@ -226,20 +226,23 @@ struct GemmRunner {
   TcWorkspace* tc;
   cx<T>* simt_scratch;
   size_t simt_scratch_elems;
-  int run(const GemmArgs<T>& g, cudaStream_t st) const;
+  // bond: a bond-level contraction (profiled as PROF_BOND_GEMM), else a QR-internal one
+  int run(const GemmArgs<T>& g, cudaStream_t st, bool bond = false) const;
 };
 
 template <>
-int GemmRunner<double>::run(const GemmArgs<double>& g, cudaStream_t st) const {
-  return gemm_simt<double>(g, st, simt_scratch, simt_scratch_elems);
+int GemmRunner<double>::run(const GemmArgs<double>& g, cudaStream_t st, bool bond) const {
+  return gemm_simt<double>(g, st, simt_scratch, simt_scratch_elems,
+                           bond ? PROF_BOND_GEMM : PROF_SIMT_GEMM);
 }
 template <>
-int GemmRunner<float>::run(const GemmArgs<float>& g, cudaStream_t st) const {
+int GemmRunner<float>::run(const GemmArgs<float>& g, cudaStream_t st, bool bond) const {
   if ((precision == QRTEBD_C64_3XTF32 || precision == QRTEBD_C64_TF32) && tc &&
       tc_gemm_eligible(g)) {
-    return tc_gemm(g, precision == QRTEBD_C64_3XTF32, *tc, st);
+    return tc_gemm(g, precision == QRTEBD_C64_3XTF32, *tc, st, bond ? PROF_BOND_GEMM : PROF_TC_GEMM);
   }
-  return gemm_simt<float>(g, st, simt_scratch, simt_scratch_elems);
+  return gemm_simt<float>(g, st, simt_scratch, simt_scratch_elems,
+                          bond ? PROF_BOND_GEMM : PROF_SIMT_GEMM);
 }
 
 template <typename T> int qr_gemm_thunk(const GemmArgs<T>& g, cudaStream_t st, void* ctx) {
@@ -327,7 +330,7 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
   if (!theta_given) {
     GemmArgs<T> g{(int)mL, (int)nR, chiM, static_cast<const cx<T>*>(io->bm), chiM, 1, false,
                   static_cast<const cx<T>*>(io->bn), nR, 1, false, theta_p, nR, 1, one, zero};
-    QR_TRY(runner.run(g, st));
+    QR_TRY(runner.run(g, st, true));
     th = theta_p;
   }
   // (i) gate (and diagonal Xi)
@@ -356,7 +359,7 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
   if (io->xi_kind == 1) {  // dense Xi: theta~ = Xi theta~' on the left bond index
     GemmArgs<T> g{chiL, (int)(d * nR), chiL, xi, chiL, 1, false, theta_tp, d * nR, 1, false,
                   theta_t, d * nR, 1, one, zero};
-    QR_TRY(runner.run(g, st));
+    QR_TRY(runner.run(g, st, true));
   }
   QR_TRY(norm2<T>(theta_t, mL * nR, partial, scal + 0, st));
 
@@ -366,7 +369,7 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
     GemmArgs<T> g{(int)mL, eta, (int)nR, theta_t, nR, 1, false, Y0, 1, nR, true, X, eta, 1, one,
                   zero};
     g.reuse_a = true;  // theta~ is read again, unchanged, by the last contraction
-    QR_TRY(runner.run(g, st));
+    QR_TRY(runner.run(g, st, true));
   }
   QR_TRY(householder_qr<T>(X, eta, (int)mL, eta, Q, eta, qs, st, err, &qg, &qg_side));
 
@@ -374,7 +377,7 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
   {
     GemmArgs<T> g{(int)nR, eta, (int)mL, theta_t, 1, nR, true, Q, eta, 1, false, Z, eta, 1, one,
                   zero};
-    QR_TRY(runner.run(g, st));
+    QR_TRY(runner.run(g, st, true));
   }
   if (Zc) QR_CUDA_TRY(cudaMemcpyAsync(Zc, Z, (size_t)nR * eta * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st));
   QR_TRY(householder_qr<T>(Z, eta, (int)nR, eta, Qz, eta, qs, st, err, &qg, &qg_side));
@@ -395,13 +398,13 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
     GemmArgs<T> g{(int)mL, eta, (int)nR, theta_tp, nR, 1, false, Qz, eta, 1, false, bm_out, eta,
                   1, one, zero};
     g.reuse_a = true;
-    QR_TRY(runner.run(g, st));
+    QR_TRY(runner.run(g, st, true));
     if (eps_explicit) {
       // residual theta~ - Q Y with Y = Zc^dag (Sec. IV: the explicit distance)
       QR_CUDA_TRY(cudaMemcpyAsync(Rbuf, theta_t, (size_t)mL * nR * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st));
       GemmArgs<T> r{(int)mL, (int)nR, eta, Q, eta, 1, false, Zc, 1, eta, true, Rbuf, nR, 1,
                     mk<T>(-1, 0), one};
-      QR_TRY(runner.run(r, st));
+      QR_TRY(runner.run(r, st, true));
       QR_TRY(norm2<T>(Rbuf, mL * nR, partial, scal + 3, st));
       k_eps_explicit<<<1, 1, 0, st>>>(scal + 0, scal + 3, io->stats_out ? io->stats_out : stats_local);
       note_launch();
@@ -444,7 +447,7 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
     {
       GemmArgs<T> g{chi_new, (int)nR, eta, Vt, eta, 1, false, Qz, 1, eta, true, bn_out, nR, 1,
                     one, zero};
-      QR_TRY(runner.run(g, st));
+      QR_TRY(runner.run(g, st, true));
     }
     k_diag_xi<T><<<(unsigned)ceil_div((long long)chi_new * chi_new, 256), 256, 0, st>>>(
         Sv, chi_new, scal + 2, xi_out);
@@ -453,7 +456,7 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
     {
       GemmArgs<T> g{(int)mL, chi_new, (int)nR, theta_tp, nR, 1, false, bn_out, 1, nR, true, bm_out,
                     chi_new, 1, one, zero};
-      QR_TRY(runner.run(g, st));
+      QR_TRY(runner.run(g, st, true));
     }
     if (eps_explicit) {
       // approx = Q L V_c^dag B~^n; residual theta~ - approx (Sec. IV)
@@ -465,7 +468,7 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
       QR_CUDA_TRY(cudaMemcpyAsync(Rbuf, theta_t, (size_t)mL * nR * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st));
       GemmArgs<T> r{(int)mL, (int)nR, eta, Q, eta, 1, false, Yt, nR, 1, false, Rbuf, nR, 1,
                     mk<T>(-1, 0), one};
-      QR_TRY(runner.run(r, st));
+      QR_TRY(runner.run(r, st, true));
       QR_TRY(norm2<T>(Rbuf, mL * nR, partial, scal + 3, st));
       k_eps_explicit<<<1, 1, 0, st>>>(scal + 0, scal + 3, io->stats_out ? io->stats_out : stats_local);
       note_launch();

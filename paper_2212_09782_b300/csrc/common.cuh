@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <utility>
 #include <stdint.h>
 #include <stdio.h>
 
@@ -85,7 +86,7 @@ unsigned* device_error_word();
 // kernel families (see prof.cu and qrtebd_profile_enable).
 void note_launch(int n = 1);
 enum ProfFamily { PROF_TC_GEMM = 0, PROF_QR_PANEL = 1, PROF_SIMT_GEMM = 2, PROF_PREP = 3,
-                  PROF_GATE = 4, PROF_NFAM = 5 };
+                  PROF_GATE = 4, PROF_BOND_GEMM = 5, PROF_NFAM = 6 };
 // While a ProfSuppress is alive on this thread, ProfScope records nothing (used by
 // entry points that must not create CUDA objects).
 struct ProfSuppress {
@@ -100,6 +101,33 @@ class ProfScope {
   int fam_; cudaStream_t st_; double flops_, bytes_;
   void* a_ = nullptr; void* b_ = nullptr;
 };
+
+// Programmatic dependent launch. A kernel started by launch_pdl() may be scheduled
+// while the previous kernel on its stream is still draining (its launch latency and
+// prologue overlap that kernel's tail); it calls pdl_wait() before its first access to
+// global memory, which returns once every earlier kernel on the stream has completed
+// and its writes are visible. pdl_launch_dependents() lets the next such kernel be
+// scheduled as soon as every CTA of this one has started. Launched without the
+// attribute, both are no-ops.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 __host__ __device__ __forceinline__ long long ceil_div(long long a, long long b) {
   return (a + b - 1) / b;

@@ -17,6 +17,8 @@ __global__ void __launch_bounds__(NT) k_gemm(GemmArgs<T> g, int ksplit, int kchu
                                              cx<T>* partial) {
   __shared__ cx<T> As[BK][BM + 1];
   __shared__ cx<T> Bs[BK][BN + 1];
+  pdl_launch_dependents();
+  pdl_wait();
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
@@ -107,6 +109,8 @@ __global__ void __launch_bounds__(NT) k_gemm(GemmArgs<T> g, int ksplit, int kchu
 
 template <typename T>
 __global__ void k_splitk_reduce(GemmArgs<T> g, int ksplit, const cx<T>* partial) {
+  pdl_launch_dependents();
+  pdl_wait();
   long long MN = (long long)g.M * g.N;
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int bz = blockIdx.y;
@@ -138,7 +142,8 @@ size_t gemm_simt_scratch_elems(int M, int N, int K, int batch) {
 }
 
 template <typename T>
-int gemm_simt(const GemmArgs<T>& g, cudaStream_t st, cx<T>* scratch, size_t scratch_elems) {
+int gemm_simt(const GemmArgs<T>& g, cudaStream_t st, cx<T>* scratch, size_t scratch_elems,
+              int prof_family) {
   if (g.M <= 0 || g.N <= 0 || g.batch <= 0) return QRTEBD_OK;
   if (g.K <= 0) {
     // C = beta C: run with K = 0 through the normal path (acc stays zero)
@@ -149,21 +154,22 @@ int gemm_simt(const GemmArgs<T>& g, cudaStream_t st, cx<T>* scratch, size_t scra
   if (ks > 1) ks = (int)ceil_div(g.K, kchunk);
   dim3 grid((unsigned)ceil_div(g.N, BN), (unsigned)ceil_div(g.M, BM), (unsigned)(g.batch * ks));
   if (grid.y > 65535 || grid.z > 65535) return QRTEBD_ERR_INVALID_ARG;
-  ProfScope prof(PROF_SIMT_GEMM, st, 8.0 * g.M * g.N * (double)g.K * g.batch);
-  k_gemm<T><<<grid, NT, 0, st>>>(g, ks, kchunk, scratch);
+  ProfScope prof(prof_family, st, 8.0 * g.M * g.N * (double)g.K * g.batch);
+  QR_CUDA_TRY(launch_pdl(k_gemm<T>, grid, dim3(NT), 0, st, g, ks, kchunk, scratch));
   note_launch();
   QR_CUDA_TRY(cudaGetLastError());
   if (ks > 1) {
     long long MN = (long long)g.M * g.N;
     dim3 rg((unsigned)ceil_div(MN, 256), (unsigned)g.batch);
-    k_splitk_reduce<T><<<rg, 256, 0, st>>>(g, ks, scratch);
+    QR_CUDA_TRY(launch_pdl(k_splitk_reduce<T>, rg, dim3(256), 0, st, g, ks,
+                           static_cast<const cx<T>*>(scratch)));
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());
   }
   return QRTEBD_OK;
 }
 
-template int gemm_simt<float>(const GemmArgs<float>&, cudaStream_t, float2*, size_t);
-template int gemm_simt<double>(const GemmArgs<double>&, cudaStream_t, double2*, size_t);
+template int gemm_simt<float>(const GemmArgs<float>&, cudaStream_t, float2*, size_t, int);
+template int gemm_simt<double>(const GemmArgs<double>&, cudaStream_t, double2*, size_t, int);
 
 }  // namespace qrtebd

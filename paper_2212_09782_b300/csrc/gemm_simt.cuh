@@ -28,7 +28,7 @@ template <typename T> struct GemmArgs {
 // short-wide outputs; scratch_elems is its capacity in complex elements.
 template <typename T>
 int gemm_simt(const GemmArgs<T>& g, cudaStream_t st, cx<T>* scratch = nullptr,
-              size_t scratch_elems = 0);
+              size_t scratch_elems = 0, int prof_family = PROF_SIMT_GEMM);
 
 // Scratch (complex elements) gemm_simt would like for split-K at these sizes.
 size_t gemm_simt_scratch_elems(int M, int N, int K, int batch);

@@ -193,6 +193,8 @@ template <typename T>
 __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
   constexpr int NT = PT;
   using L = PanelSmem<T>;
+  pdl_launch_dependents();
+  pdl_wait();
   constexpr int NW = NT / 32;
   extern __shared__ __align__(16) unsigned char sm[];
   cg::cluster_group cl = cg::this_cluster();
@@ -440,6 +442,8 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
 
 template <typename T>
 __global__ void k_eye(cx<T>* Q, long long ldq, int m, int n) {
+  pdl_launch_dependents();
+  pdl_wait();
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)m * n) return;
   int i = (int)(idx / n), j = (int)(idx % n);
@@ -525,11 +529,15 @@ template <typename T> int launch_panel(const PanelArgs<T>& pa, int cs, cudaStrea
   cfg.blockDim = dim3(PT, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = cs; attr[0].val.clusterDim.y = 1; attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr; cfg.numAttrs = 1;
-  ProfScope prof(PROF_QR_PANEL, st);
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr; cfg.numAttrs = 2;
+  // algorithmic work of a Householder panel: 8 mr kb^2 real flops; traffic: the panel
+  // read once, V and R/zeros written once
+  ProfScope prof(PROF_QR_PANEL, st, 8.0 * mr * pa.kb * pa.kb, 3.0 * mr * pa.kb * sizeof(cx<T>));
   QR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_qr_panel<T>, pa));
   note_launch();
   return QRTEBD_OK;
@@ -701,7 +709,7 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
   // explicit Q by backward accumulation over the outer blocks
   {
     long long tot = (long long)m * n;
-    k_eye<T><<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(Q, ldq, m, n);
+    QR_CUDA_TRY(launch_pdl(k_eye<T>, dim3((unsigned)ceil_div(tot, 256)), dim3(256), 0, st, Q, ldq, m, n));
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());
   }

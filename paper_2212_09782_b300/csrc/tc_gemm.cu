@@ -142,6 +142,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
               Epi epi, int Kp, int kt_per_split, float* partial, unsigned* err) {
   using C = Cfg<THREE>;
+  pdl_launch_dependents();
+  pdl_wait();
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = smem_raw + ((1024 - (s_u32(smem_raw) & 1023)) & 1023);
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES);
@@ -267,34 +269,70 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce[b]);
     }
-    if (!ok) {
-      if (lane == 0) atomicOr(err, DEVERR_TIMEOUT);
-    } else if (row < epi.M) {
-      const int col0 = n0 + h * 128;  // first real column of this thread's half
-      if (partial) {
-        float* prow = partial + ((long long)blockIdx.z * epi.M + row) * (2LL * epi.Nc);
+    if (!ok && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
+    if (partial || epi.scn == 1) {
+      // Rows of the output are contiguous: stage the tile in the idle pipeline buffers
+      // (every MMA has completed) so that each warp then reads and writes whole row
+      // segments - coalesced - instead of one row per thread.
+      constexpr int LDT = BN + 4;  // floats per staged row; conflict-free float4 stores
+      float* tile = reinterpret_cast<float*>(smem);
+      if (ok) {
+        float* trow = tile + (q * 32 + lane) * LDT + h * 128;
 #pragma unroll
-        for (int j = 0; j < 128; ++j)
-          if (col0 + j < 2 * epi.Nc) prow[col0 + j] = sum[j];
-      } else {
+        for (int j = 0; j < 128; j += 4)
+          *reinterpret_cast<float4*>(trow + j) = make_float4(sum[j], sum[j + 1], sum[j + 2], sum[j + 3]);
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
+      if (ok) {
         const bool use_beta = (epi.beta.x != 0.f || epi.beta.y != 0.f);
-        float2* crow = epi.C + (long long)row * epi.scm;
-#pragma unroll
-        for (int j = 0; j < 64; ++j) {
-          const int n = (col0 >> 1) + j;
-          if (n < epi.Nc) {
-            const float ar = sum[2 * j], ai = sum[2 * j + 1];
-            float2 v;
-            v.x = epi.alpha.x * ar - epi.alpha.y * ai;
-            v.y = epi.alpha.x * ai + epi.alpha.y * ar;
-            float2* p = crow + (long long)n * epi.scn;
-            if (use_beta) {
-              const float2 cv = *p;
-              v.x += epi.beta.x * cv.x - epi.beta.y * cv.y;
-              v.y += epi.beta.x * cv.y + epi.beta.y * cv.x;
+        for (int r = warp - 2; r < BM; r += NEPI) {
+          const int grow = m0 + r;
+          if (grow >= epi.M) break;
+          const float* tr = tile + r * LDT;
+          if (partial) {
+            float* prow = partial + ((long long)blockIdx.z * epi.M + grow) * (2LL * epi.Nc);
+            for (int j = lane; j < BN; j += 32)
+              if (n0 + j < 2 * epi.Nc) prow[n0 + j] = tr[j];
+          } else {
+            float2* crow = epi.C + (long long)grow * epi.scm;
+            for (int c = lane; c < BN / 2; c += 32) {
+              const int n = n0 / 2 + c;
+              if (n < epi.Nc) {
+                const float2 a = *reinterpret_cast<const float2*>(tr + 2 * c);
+                float2 v;
+                v.x = epi.alpha.x * a.x - epi.alpha.y * a.y;
+                v.y = epi.alpha.x * a.y + epi.alpha.y * a.x;
+                if (use_beta) {
+                  const float2 cv = crow[n];
+                  v.x += epi.beta.x * cv.x - epi.beta.y * cv.y;
+                  v.y += epi.beta.x * cv.y + epi.beta.y * cv.x;
+                }
+                crow[n] = v;
+              }
             }
-            *p = v;
           }
+        }
+      }
+    } else if (ok && row < epi.M) {
+      // general strides (a transposed output is coalesced across the warp's rows)
+      const int col0 = n0 + h * 128;  // first real column of this thread's half
+      const bool use_beta = (epi.beta.x != 0.f || epi.beta.y != 0.f);
+      float2* crow = epi.C + (long long)row * epi.scm;
+#pragma unroll
+      for (int j = 0; j < 64; ++j) {
+        const int n = (col0 >> 1) + j;
+        if (n < epi.Nc) {
+          const float ar = sum[2 * j], ai = sum[2 * j + 1];
+          float2 v;
+          v.x = epi.alpha.x * ar - epi.alpha.y * ai;
+          v.y = epi.alpha.x * ai + epi.alpha.y * ar;
+          float2* p = crow + (long long)n * epi.scn;
+          if (use_beta) {
+            const float2 cv = *p;
+            v.x += epi.beta.x * cv.x - epi.beta.y * cv.y;
+            v.y += epi.beta.x * cv.y + epi.beta.y * cv.x;
+          }
+          *p = v;
         }
       }
     }
@@ -318,6 +356,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
 // C = alpha * sum_z partial[z] + beta * C (partials: split x M x 2N floats)
 __global__ void k_splitk_sum(const float* partial, int splits, Epi epi) {
+  pdl_launch_dependents();
+  pdl_wait();
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   long long MN = (long long)epi.M * epi.Nc;
   if (idx >= MN) return;
@@ -351,6 +391,8 @@ __global__ void k_prep_a(const float2* __restrict__ A, long long sam, long long 
                          int M, int K, float* __restrict__ hi, float* __restrict__ lo, int ld,
                          int three) {
   __shared__ float2 t[32][33];
+  pdl_launch_dependents();
+  pdl_wait();
   const int m0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
   const bool kc = (sak == 1);
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -379,6 +421,8 @@ __global__ void k_prep_b(const float2* __restrict__ B, long long sbk, long long 
                          int K, int N, float* __restrict__ hi, float* __restrict__ lo, int ld,
                          int three) {
   __shared__ float2 t[32][33];  // [n][k]
+  pdl_launch_dependents();
+  pdl_wait();
   const int n0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
   const bool kc = (sbk == 1);
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
@@ -466,15 +510,19 @@ void tc_invalidate(TcWorkspace& w) {
 }
 
 bool tc_gemm_eligible(const GemmArgs<float>& g) {
-  return g.batch == 1 && std::max(g.M, g.N) >= 128 && std::min(g.M, g.N) >= 16 && g.K >= 32 &&
+  // K < 64: two K-blocks or fewer, where the operand preparation and the fixed cost of
+  // the tensor-core kernel outweigh the CUDA-core GEMM (measured 2x slower at K = 32)
+  return g.batch == 1 && std::max(g.M, g.N) >= 128 && std::min(g.M, g.N) >= 16 && g.K >= 64 &&
          (double)g.M * g.N * g.K >= (double)(1 << 21);
 }
 
-int tc_gemm(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStream_t st) {
-  // C = A B with a short M is run as C^T = B^T A^T (the tile is 128 rows tall)
+int tc_gemm(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStream_t st, int prof_family) {
+  // C = A B with N > M is run as C^T = B^T A^T: the tile is 128 rows tall, and the
+  // B operand is the one stored twice over (2x2 real embedding), so it should be the
+  // smaller one
   GemmArgs<float> g = g0;
   bool cacheable = g0.reuse_a;
-  if (g0.M < 128 && g0.N > g0.M) {
+  if (g0.N > g0.M) {
     cacheable = false;
     g.M = g0.N; g.N = g0.M;
     g.A = g0.B; g.sam = g0.sbn; g.sak = g0.sbk; g.conj_a = g0.conj_b;
@@ -484,7 +532,7 @@ int tc_gemm(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStream_t 
   const int M = g.M, N = g.N, K = g.K;
   const int ld = ld_for(K);
   if ((size_t)M * ld > w.a_cap || (size_t)2 * N * ld > w.b_cap || !w.a[0].hi || !w.b.hi)
-    return gemm_simt<float>(g0, st, nullptr, 0);
+    return gemm_simt<float>(g0, st, nullptr, 0, prof_family == PROF_TC_GEMM ? PROF_SIMT_GEMM : prof_family);
   QR_TRY(get_encode());
 
   // ---- A' (cached per source/op within one bond update)
@@ -500,8 +548,8 @@ int tc_gemm(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStream_t 
     w.a_next ^= 1;
     dim3 grid((unsigned)ceil_div(K, 32), (unsigned)ceil_div(M, 32));
     ProfScope prof(PROF_PREP, st, 0, 8.0 * M * K + (three ? 16.0 : 8.0) * M * K);
-    k_prep_a<<<grid, dim3(32, 8), 0, st>>>(g.A, g.sam, g.sak, g.conj_a ? 1 : 0, M, K, sa->hi,
-                                           sa->lo, ld, three ? 1 : 0);
+    QR_CUDA_TRY(launch_pdl(k_prep_a, grid, dim3(32, 8), 0, st, g.A, g.sam, g.sak, g.conj_a ? 1 : 0,
+                           M, K, sa->hi, sa->lo, ld, three ? 1 : 0));
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());
     sa->valid = cacheable; sa->src = g.A; sa->s0 = g.sam; sa->s1 = g.sak; sa->rows = M; sa->cols = K;
@@ -511,8 +559,8 @@ int tc_gemm(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStream_t 
   {
     dim3 grid((unsigned)ceil_div(K, 32), (unsigned)ceil_div(N, 32));
     ProfScope prof(PROF_PREP, st, 0, 8.0 * N * K + (three ? 32.0 : 16.0) * N * K);
-    k_prep_b<<<grid, dim3(32, 8), 0, st>>>(g.B, g.sbk, g.sbn, g.conj_b ? 1 : 0, K, N, w.b.hi,
-                                           w.b.lo, ld, three ? 1 : 0);
+    QR_CUDA_TRY(launch_pdl(k_prep_b, grid, dim3(32, 8), 0, st, g.B, g.sbk, g.sbn, g.conj_b ? 1 : 0,
+                           K, N, w.b.hi, w.b.lo, ld, three ? 1 : 0));
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());
   }
@@ -539,29 +587,30 @@ int tc_gemm(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStream_t 
   dim3 grid((unsigned)nx, (unsigned)ny, (unsigned)splits);
   unsigned* err = device_error_word();
   {
-    ProfScope prof(PROF_TC_GEMM, st, 8.0 * M * N * K);
+    ProfScope prof(prof_family, st, 8.0 * M * N * K);
     if (three) {
       if (!g_attr3) {
         QR_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Cfg<true>::SMEM));
         g_attr3 = true;
       }
-      k_tc_gemm<true><<<grid, NTHREADS, Cfg<true>::SMEM, st>>>(ta_hi, ta_lo, tb_hi, tb_lo, epi,
-                                                               2 * K, per, part, err);
+      QR_CUDA_TRY(launch_pdl(k_tc_gemm<true>, grid, dim3(NTHREADS), Cfg<true>::SMEM, st, ta_hi, ta_lo,
+                             tb_hi, tb_lo, epi, 2 * K, per, part, err));
     } else {
       if (!g_attr1) {
         QR_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          Cfg<false>::SMEM));
         g_attr1 = true;
       }
-      k_tc_gemm<false><<<grid, NTHREADS, Cfg<false>::SMEM, st>>>(ta_hi, ta_lo, tb_hi, tb_lo, epi,
-                                                                 2 * K, per, part, err);
+      QR_CUDA_TRY(launch_pdl(k_tc_gemm<false>, grid, dim3(NTHREADS), Cfg<false>::SMEM, st, ta_hi,
+                             ta_lo, tb_hi, tb_lo, epi, 2 * K, per, part, err));
     }
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());
   }
   if (splits > 1) {
-    k_splitk_sum<<<(unsigned)ceil_div((long long)M * N, 256), 256, 0, st>>>(part, splits, epi);
+    QR_CUDA_TRY(launch_pdl(k_splitk_sum, dim3((unsigned)ceil_div((long long)M * N, 256)), dim3(256), 0,
+                           st, static_cast<const float*>(part), splits, epi));
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());
   }

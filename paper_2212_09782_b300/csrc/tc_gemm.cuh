@@ -40,7 +40,8 @@ bool tc_gemm_eligible(const GemmArgs<float>& g);
 
 // C = alpha opA opB + beta C through tcgen05. Falls back to the CUDA-core GEMM
 // when the prepared operands would not fit the workspace.
-int tc_gemm(const GemmArgs<float>& g, bool three, TcWorkspace& w, cudaStream_t st);
+int tc_gemm(const GemmArgs<float>& g, bool three, TcWorkspace& w, cudaStream_t st,
+            int prof_family = PROF_TC_GEMM);
 
 // Invalidate cached prepared operands (call when their sources may change).
 void tc_invalidate(TcWorkspace& w);

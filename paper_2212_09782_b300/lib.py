@@ -206,7 +206,7 @@ class BondUpdater:
                 self.stats)
 
 
-PROF_TC_GEMM, PROF_QR_PANEL, PROF_SIMT_GEMM, PROF_PREP, PROF_GATE = 0, 1, 2, 3, 4
+PROF_TC_GEMM, PROF_QR_PANEL, PROF_SIMT_GEMM, PROF_PREP, PROF_GATE, PROF_BOND_GEMM = 0, 1, 2, 3, 4, 5
 
 
 def launch_count():
