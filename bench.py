@@ -42,6 +42,13 @@ FP32_ALU_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 FP64_ALU_TFLOPS = 1.25
 
 
+# DRAM traffic of the panel kernel from one ncu capture (profiles/k_qr_panel_chi512.md:
+# complex64, 2464 x 32 panel, 680192 bytes read, 0 written, against 3 x 2464 x 32 x 8
+# algorithmic bytes). Traffic grows with the panel's rows, so a launch's traffic is this
+# ratio times its algorithmic bytes.
+PANEL_NCU_DRAM_OVER_ALGORITHMIC = 680192 / (3 * 2464 * 32 * 8)
+
+
 def prof_families(L):
     names = {L.PROF_BOND_GEMM: "bond_gemm", L.PROF_TC_GEMM: "qr_tc_gemm", L.PROF_QR_PANEL: "qr_panel",
              L.PROF_SIMT_GEMM: "simt_gemm", L.PROF_PREP: "tc_prep", L.PROF_GATE: "gate"}
@@ -82,6 +89,10 @@ def family_roofline(L, fam, ms, n, flops, nbytes, prec, peaks, src):
         if fam == L.PROF_QR_PANEL:
             out["limiter"] = "latency: one cluster-wide exchange per column (sequential in the column)"
             out["achieved_hbm_gbs"] = nbytes / n / sec / 1e9
+            out["algorithmic_bytes_per_launch"] = nbytes / n
+            if prec == L.C64_3XTF32:
+                out["traffic"] = PANEL_NCU_DRAM_OVER_ALGORITHMIC * nbytes / n
+                out["traffic_source"] = "ncu dram bytes of a 2464-row panel, scaled by rows"
     return out
 
 
