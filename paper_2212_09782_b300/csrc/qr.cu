@@ -450,6 +450,238 @@ __global__ void k_eye(cx<T>* Q, long long ldq, int m, int n) {
   Q[i * ldq + j] = mk<T>(i == j ? T(1) : T(0), 0);
 }
 
+// ------------------------------------------------------ outer compact-WY factor
+// T of an outer block from its inner blocks' factors (on the diagonal of Tb) and the Gram
+// matrix G = V^dag V of the block: column block by column block,
+//   T[0:c0, c0:c0+w] = -T[0:c0, 0:c0] G[0:c0, c0:c0+w] T[c0:c0+w, c0:c0+w].
+// One CTA; tmp holds G T_cc (c0 x w).
+constexpr int TO_NT = 1024;
+template <typename T>
+__global__ void __launch_bounds__(TO_NT) k_t_outer(cx<T>* Tb, int ldt, const cx<T>* G, int ldg,
+                                                   int kbo, int nb, cx<T>* tmp) {
+  pdl_launch_dependents();
+  pdl_wait();
+  for (int c0 = nb; c0 < kbo; c0 += nb) {
+    const int w = min(nb, kbo - c0);
+    for (int o = threadIdx.x; o < c0 * w; o += TO_NT) {
+      const int i = o / w, j = o % w;
+      cx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0);
+      int k = 0;
+      for (; k + 1 <= j; k += 2) {
+        cfma<T>(a0, G[(long long)i * ldg + c0 + k], Tb[(long long)(c0 + k) * ldt + c0 + j]);
+        cfma<T>(a1, G[(long long)i * ldg + c0 + k + 1], Tb[(long long)(c0 + k + 1) * ldt + c0 + j]);
+      }
+      if (k <= j) cfma<T>(a0, G[(long long)i * ldg + c0 + k], Tb[(long long)(c0 + k) * ldt + c0 + j]);
+      tmp[o] = cadd<T>(a0, a1);
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < c0 * w; o += TO_NT) {
+      const int i = o / w, j = o % w;
+      cx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0);
+      int k = i;
+      for (; k + 1 < c0; k += 2) {
+        cfma<T>(a0, Tb[(long long)i * ldt + k], tmp[k * w + j]);
+        cfma<T>(a1, Tb[(long long)i * ldt + k + 1], tmp[(k + 1) * w + j]);
+      }
+      if (k < c0) cfma<T>(a0, Tb[(long long)i * ldt + k], tmp[k * w + j]);
+      const cx<T> r = cadd<T>(a0, a1);
+      Tb[(long long)i * ldt + c0 + j] = mk<T>(-r.x, -r.y);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------ fused narrow block-reflector update
+// C <- (I - V T V^dag)^dag C = C - V T^dag (V^dag C) for the columns of an outer block right
+// of a panel: kb <= 32 reflectors, nc <= WY_NC columns, C and V of mr rows. One cooperative
+// launch, each CTA a slab of rpb rows held in shared memory:
+//   (1) partial V^dag C over the slab; (2) the partials summed, one output per lane;
+//   (3) W2 = T^dag W, then C -= V W2 on the slab.
+// Grid barriers separate the phases; their waits are bounded (DEVERR_TIMEOUT) and the
+// cooperative launch guarantees that every CTA is resident.
+constexpr int WY_NT = 256;
+constexpr int WY_NC = 128;
+constexpr int WY_KB = 32;
+
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long i = 0;
+      while (*gen == g) {
+        if (++i > kSpinLimit) { ok = 0; atomicOr(err, DEVERR_TIMEOUT); break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(WY_NT) k_apply_wy(cx<T>* C, long long ldc, const cx<T>* V,
+                                                    long long ldv, const cx<T>* Tt, int ldt, int mr,
+                                                    int nc, int kb, int rpb, cx<T>* part, cx<T>* Wg,
+                                                    unsigned* bar, unsigned* err) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  cx<T>* Vs = reinterpret_cast<cx<T>*>(sm);  // rpb x kb
+  cx<T>* Cs = Vs + (size_t)rpb * kb;         // rpb x nc
+  cx<T>* Ws = Cs + (size_t)rpb * nc;         // kb x nc
+  cx<T>* Ts = Ws + (size_t)kb * nc;          // kb x kb
+  const int tid = threadIdx.x;
+  const unsigned G = gridDim.x;
+  const int b = blockIdx.x;
+  const int r0 = b * rpb, nr = max(0, min(rpb, mr - r0));
+  const cx<T> zero = mk<T>(0, 0);
+  for (int i = tid; i < nr * kb; i += WY_NT) Vs[i] = V[(long long)(r0 + i / kb) * ldv + i % kb];
+  for (int i = tid; i < nr * nc; i += WY_NT) Cs[i] = C[(long long)(r0 + i / nc) * ldc + i % nc];
+  for (int i = tid; i < kb * kb; i += WY_NT) Ts[i] = Tt[(long long)(i / kb) * ldt + i % kb];
+  __syncthreads();
+  // thread = (column c, parity of a): 16 accumulators
+  const int c = tid % WY_NC, ap = tid / WY_NC;
+  constexpr int NA = WY_KB / 2;
+  // (1) partial V^dag C
+  if (c < nc) {
+    cx<T> acc[NA];
+#pragma unroll
+    for (int i = 0; i < NA; ++i) acc[i] = zero;
+    for (int r = 0; r < nr; ++r) {
+      const cx<T> x = Cs[r * nc + c];
+#pragma unroll
+      for (int i = 0; i < NA; ++i) {
+        const int a = ap + 2 * i;
+        if (a < kb) cfma<T>(acc[i], cconj<T>(Vs[r * kb + a]), x);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      const int a = ap + 2 * i;
+      if (a < kb) part[((size_t)b * kb + a) * nc + c] = acc[i];
+    }
+  }
+  if (!grid_barrier(bar, G, err)) return;
+  // (2) sum of the partials: lanes = 32 consecutive outputs, warps over output groups
+  {
+    const int warp = tid >> 5, lane = tid & 31;
+    const int nout = kb * nc, ngroups = (nout + 31) / 32;
+    for (int grp = b * (WY_NT / 32) + warp; grp < ngroups; grp += G * (WY_NT / 32)) {
+      const int o = grp * 32 + lane;
+      if (o < nout) {
+        cx<T> s0 = zero, s1 = zero;
+        unsigned z = 0;
+        for (; z + 1 < G; z += 2) {
+          s0 = cadd<T>(s0, part[(size_t)z * nout + o]);
+          s1 = cadd<T>(s1, part[(size_t)(z + 1) * nout + o]);
+        }
+        if (z < G) s0 = cadd<T>(s0, part[(size_t)z * nout + o]);
+        Wg[o] = cadd<T>(s0, s1);
+      }
+    }
+  }
+  if (!grid_barrier(bar, G, err)) return;
+  // (3) W2 = T^dag W in shared memory, then C -= V W2 on the slab
+  for (int i = tid; i < kb * nc; i += WY_NT) Ws[i] = Wg[i];
+  __syncthreads();
+  cx<T> w2[NA];
+  if (c < nc) {
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      const int a = ap + 2 * i;
+      cx<T> s = zero;
+      if (a < kb)
+        for (int q = 0; q <= a; ++q) cfma<T>(s, cconj<T>(Ts[q * kb + a]), Ws[q * nc + c]);
+      w2[i] = s;
+    }
+  }
+  __syncthreads();
+  if (c < nc) {
+#pragma unroll
+    for (int i = 0; i < NA; ++i) {
+      const int a = ap + 2 * i;
+      if (a < kb) Ws[a * nc + c] = w2[i];
+    }
+  }
+  __syncthreads();
+  if (c < nc) {
+    for (int r = ap; r < nr; r += 2) {
+      cx<T> s0 = zero, s1 = zero;
+      int a = 0;
+      for (; a + 1 < kb; a += 2) {
+        cfma<T>(s0, Vs[r * kb + a], Ws[a * nc + c]);
+        cfma<T>(s1, Vs[r * kb + a + 1], Ws[(a + 1) * nc + c]);
+      }
+      if (a < kb) cfma<T>(s0, Vs[r * kb + a], Ws[a * nc + c]);
+      const cx<T> s = cadd<T>(s0, s1);
+      C[(long long)(r0 + r) * ldc + c] = csub<T>(Cs[r * nc + c], s);
+    }
+  }
+}
+
+int g_nsm = 0;
+int num_sms() {
+  if (g_nsm == 0) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      g_nsm = v;
+    else
+      g_nsm = 148;
+  }
+  return g_nsm;
+}
+
+template <typename T> size_t wy_smem(int rpb, int kb, int nc) {
+  return ((size_t)rpb * kb + (size_t)rpb * nc + (size_t)kb * nc + (size_t)kb * kb) * sizeof(cx<T>);
+}
+
+// Rows per CTA of the fused update: one CTA per SM at most (co-residency of a
+// cooperative launch), at least 8 rows per CTA.
+template <typename T> int wy_rows_per_block(int mr, int kb, int nc) {
+  if (kb < 1 || kb > WY_KB || nc < 1 || nc > WY_NC || mr < 1) return 0;
+  const int rpb = std::max(8, (int)ceil_div(mr, num_sms()));
+  if (wy_smem<T>(rpb, kb, nc) > (size_t)48 * 1024 * 4) return 0;
+  return rpb;
+}
+
+template <typename T> bool g_wy_attr = false;
+
+template <typename T>
+int apply_wy(cx<T>* C, long long ldc, const cx<T>* V, long long ldv, const cx<T>* Tt, int ldt, int mr,
+             int nc, int kb, int rpb, const QrScratch<T>& s, cudaStream_t st, unsigned* err) {
+  const int G = (int)ceil_div(mr, rpb);
+  const size_t smem = wy_smem<T>(rpb, kb, nc);
+  if (!g_wy_attr<T>) {
+    QR_CUDA_TRY(cudaFuncSetAttribute(k_apply_wy<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     48 * 1024 * 4));
+    g_wy_attr<T> = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)G, 1, 1);
+  cfg.blockDim = dim3(WY_NT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at; cfg.numAttrs = 1;
+  ProfScope prof(PROF_SIMT_GEMM, st, 16.0 * mr * nc * kb);
+  QR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_apply_wy<T>, C, ldc, V, ldv, Tt, ldt, mr, nc, kb, rpb,
+                                 s.wy_part, s.wy_W, s.bar, err));
+  note_launch();
+  return QRTEBD_OK;
+}
+
 struct ClusterChoice { int cs; int rps; int kb; };
 
 // Largest cluster the device co-schedules for the panel kernel (16 needs the
@@ -597,6 +829,9 @@ template <typename T> void qr_carve(Arena& ar, int m, int n, QrScratch<T>& s) {
   s.W2s = ar.take<cx<T>>((size_t)nbo * n);
   s.G = ar.take<cx<T>>((size_t)nbo * nbo);
   s.tmp = ar.take<cx<T>>((size_t)nbo * KBMAX);
+  s.wy_part = ar.take<cx<T>>((size_t)std::max(num_sms(), 1) * WY_KB * WY_NC);
+  s.wy_W = ar.take<cx<T>>((size_t)WY_KB * WY_NC);
+  s.bar = ar.take<unsigned>(64);
   size_t e = 0;
   for (int k = 1; k <= nbo; k *= 2) {
     e = std::max(e, gemm_simt_scratch_elems(k, n, m, 1));
@@ -621,6 +856,7 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
   // V must be zero above each panel's diagonal block: an outer block reads the rows
   // above its later inner panels, which those panels do not write
   QR_CUDA_TRY(cudaMemsetAsync(s.V, 0, (size_t)m * n * sizeof(cx<T>), st));
+  QR_CUDA_TRY(cudaMemsetAsync(s.bar, 0, 2 * sizeof(unsigned), st));
 
   const int nblk = (int)ceil_div(n, nbo);
   SideStream* ss = nullptr;
@@ -647,7 +883,11 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
       QR_TRY(launch_panel<T>(pa, cc.cs, st));
       // inner update: the rest of this outer block
       const int nc = ko + kbo - ki - kb;
-      if (nc > 0) {
+      const int rpb = nc > 0 ? wy_rows_per_block<T>(mr, kb, nc) : 0;
+      if (rpb > 0) {
+        QR_TRY(apply_wy<T>(A + (long long)ki * lda + ki + kb, lda, s.V + (long long)ki * ldv + ki, ldv,
+                           Ti, nbo, mr, nc, kb, rpb, s, st, err));
+      } else if (nc > 0) {
         const cx<T>* Vk = s.V + (long long)ki * ldv + ki;
         cx<T>* C = A + (long long)ki * lda + ki + kb;
         GemmArgs<T> g1{kb, nc, mr, Vk, 1, ldv, true, C, lda, 1, false, s.W, nc, 1, one, zero};
@@ -664,14 +904,9 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
       // T[0:c0, c0:c0+w] = -T[0:c0, 0:c0] G[0:c0, c0:c0+w] T[c0:c0+w, c0:c0+w]
       GemmArgs<T> gg{kbo, kbo, mo, Vb, 1, ldv, true, Vb, ldv, 1, false, s.G, nbo, 1, one, zero};
       QR_TRY(run_gemm<T>(gg, s, st, gm));
-      for (int c0 = nb; c0 < kbo; c0 += nb) {
-        const int w = std::min(nb, kbo - c0);
-        GemmArgs<T> t1{c0, w, w, s.G + c0, nbo, 1, false, Tb + (size_t)c0 * nbo + c0, nbo, 1, false,
-                       s.tmp, w, 1, one, zero};
-        QR_TRY(gemm_simt<T>(t1, st, s.gemm_scratch, s.gemm_scratch_elems));
-        GemmArgs<T> t2{c0, w, c0, Tb, nbo, 1, false, s.tmp, w, 1, false, Tb + c0, nbo, 1, mone, zero};
-        QR_TRY(gemm_simt<T>(t2, st, s.gemm_scratch, s.gemm_scratch_elems));
-      }
+      QR_CUDA_TRY(launch_pdl(k_t_outer<T>, dim3(1), dim3(TO_NT), 0, st, Tb, nbo,
+                             static_cast<const cx<T>*>(s.G), nbo, kbo, nb, s.tmp));
+      note_launch();
     }
     // outer trailing update: C <- (I - V T V^dag)^dag C. With look-ahead the next outer
     // block's columns are updated here and the rest on the side stream, overlapping the

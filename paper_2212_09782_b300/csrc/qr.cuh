@@ -24,6 +24,9 @@ template <typename T> struct QrScratch {
   cx<T>* W2s = nullptr;
   cx<T>* G = nullptr;      // outer-block Gram matrix V^dag V
   cx<T>* tmp = nullptr;    // T assembly scratch
+  cx<T>* wy_part = nullptr;  // fused narrow update: per-CTA partials of V^dag C
+  cx<T>* wy_W = nullptr;     // and their sum
+  unsigned* bar = nullptr;   // grid-barrier counter and generation
   cx<T>* gemm_scratch = nullptr;
   size_t gemm_scratch_elems = 0;
 };
