@@ -11,8 +11,9 @@
 // compact-WY factor T (upper triangular) from the Gram values v_a^dag v_j, so that
 // H_1 ... H_nb = I - V T V^dag.
 //
-// Trailing update per panel:   C <- (I - V T V^dag)^dag C = C - V (T^dag (V^dag C))
-// Explicit Q (backward):       Q[k0:, k0:] <- (I - V T V^dag) Q[k0:, k0:], Q = [I; 0] initially
+// Trailing update per block:   C <- (I - V T V^dag)^dag C = C - V ((V T)^dag C)
+// Explicit Q (backward):       Q[k0:, k0:] <- Q[k0:, k0:] - (V T)(V^dag Q[k0:, k0:]), Q = [I; 0]
+// with V T formed once per outer block.
 // The three contractions of each step go through QrGemm (CUDA cores by default,
 // tcgen05 tensor cores in the complex64 tensor-core path).
 #include <cooperative_groups.h>
@@ -822,6 +823,7 @@ template <typename T> void qr_carve(Arena& ar, int m, int n, QrScratch<T>& s) {
   const int nbo = NBO;
   s.V = ar.take<cx<T>>((size_t)m * n);
   s.tau = ar.take<cx<T>>(n);
+  s.VT = ar.take<cx<T>>((size_t)m * n);
   s.Tf = ar.take<cx<T>>((size_t)(n + nbo) * nbo);
   s.W = ar.take<cx<T>>((size_t)nbo * n);
   s.W2 = ar.take<cx<T>>((size_t)nbo * n);
@@ -908,6 +910,12 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
                              static_cast<const cx<T>*>(s.G), nbo, kbo, nb, s.tmp));
       note_launch();
     }
+    // VT = V T of this block, kept for the trailing updates and the explicit Q
+    cx<T>* VTb = s.VT + (long long)ko * ldv + ko;
+    {
+      GemmArgs<T> gv{mo, kbo, kbo, Vb, ldv, 1, false, Tb, nbo, 1, false, VTb, ldv, 1, one, zero};
+      QR_TRY(run_gemm<T>(gv, s, st, gm));
+    }
     // outer trailing update: C <- (I - V T V^dag)^dag C. With look-ahead the next outer
     // block's columns are updated here and the rest on the side stream, overlapping the
     // next block's panels.
@@ -916,10 +924,10 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
       auto update = [&](int c0, int cw, cudaStream_t stream, cx<T>* W, cx<T>* W2,
                         const QrGemm<T>* g) -> int {
         cx<T>* C = A + (long long)ko * lda + ko + kbo + c0;
-        GemmArgs<T> g1{kbo, cw, mo, Vb, 1, ldv, true, C, lda, 1, false, W, cw, 1, one, zero};
+        // W2 = T^dag V^dag C = (V T)^dag C, then C -= V W2
+        (void)W;
+        GemmArgs<T> g1{kbo, cw, mo, VTb, 1, ldv, true, C, lda, 1, false, W2, cw, 1, one, zero};
         QR_TRY(run_gemm<T>(g1, s, stream, g));
-        GemmArgs<T> g2{kbo, cw, kbo, Tb, 1, nbo, true, W, cw, 1, false, W2, cw, 1, one, zero};
-        QR_TRY(run_gemm<T>(g2, s, stream, g));
         GemmArgs<T> g3{mo, cw, kbo, Vb, ldv, 1, false, W2, cw, 1, false, C, lda, 1, mone, one};
         QR_TRY(run_gemm<T>(g3, s, stream, g));
         return QRTEBD_OK;
@@ -954,13 +962,12 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
     const int kbo = std::min(nbo, n - ko);
     const int mo = m - ko, nq = n - ko;
     const cx<T>* Vb = s.V + (long long)ko * ldv + ko;
-    const cx<T>* Tb = s.Tf + (size_t)p * nbo * nbo;
+    const cx<T>* VTb = s.VT + (long long)ko * ldv + ko;
     cx<T>* Qs = Q + (long long)ko * ldq + ko;
+    // Q_s <- (I - V T V^dag) Q_s = Q_s - (V T)(V^dag Q_s)
     GemmArgs<T> g1{kbo, nq, mo, Vb, 1, ldv, true, Qs, ldq, 1, false, s.W, nq, 1, one, zero};
     QR_TRY(run_gemm<T>(g1, s, st, gm));
-    GemmArgs<T> g2{kbo, nq, kbo, Tb, nbo, 1, false, s.W, nq, 1, false, s.W2, nq, 1, one, zero};
-    QR_TRY(run_gemm<T>(g2, s, st, gm));
-    GemmArgs<T> g3{mo, nq, kbo, Vb, ldv, 1, false, s.W2, nq, 1, false, Qs, ldq, 1, mone, one};
+    GemmArgs<T> g3{mo, nq, kbo, VTb, ldv, 1, false, s.W, nq, 1, false, Qs, ldq, 1, mone, one};
     QR_TRY(run_gemm<T>(g3, s, st, gm));
   }
   return QRTEBD_OK;

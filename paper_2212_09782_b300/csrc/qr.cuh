@@ -17,6 +17,7 @@ template <typename T> struct QrGemm {
 template <typename T> struct QrScratch {
   cx<T>* V = nullptr;      // m x n explicit reflectors (unit lower trapezoidal per panel)
   cx<T>* tau = nullptr;    // n
+  cx<T>* VT = nullptr;     // m x n: V T of every outer block (trailing updates, explicit Q)
   cx<T>* Tf = nullptr;     // ceil(n/nb) blocks of nb x nb triangular factors
   cx<T>* W = nullptr;      // nb x n
   cx<T>* W2 = nullptr;     // nb x n
