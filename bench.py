@@ -279,35 +279,57 @@ def run_ours(args):
     L.profile_enable(False)
     L.stream_check()
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: every step copies its
+    #      inputs from pinned host memory and reads its outputs back, all inside the
+    #      timed region. Two updaters (workspaces) alternate, so step i+1's host->device
+    #      copy and step i's device->host copy run on copy streams under step i+1's
+    #      compute, as a caller of the asynchronous API would arrange it.
     e2e = None
     if not args.no_e2e:
         h_th = torch.from_numpy(wl["theta"]).to(cdt).pin_memory()
         h_bn = torch.from_numpy(wl["Bn"]).to(cdt).pin_memory()
         h_u = torch.from_numpy(wl["U"]).pin_memory()
-        o_bm = torch.empty(up.bm_out.shape, dtype=cdt).pin_memory()
-        o_xi = torch.empty(up.xi_out.shape, dtype=cdt).pin_memory()
-        o_bn = torch.empty(up.bn_out.shape, dtype=cdt).pin_memory()
-        o_st = torch.empty(4, dtype=torch.float64).pin_memory()
-        d_th, d_bn, d_u = torch.empty_like(th), torch.empty_like(bn), torch.empty_like(gate)
+        ups = [up, L.BondUpdater(prec, chi, d, chi, chi, tr, xi_kind=0, theta_given=True)]
+        outs = [tuple(torch.empty(x.shape, dtype=x.dtype).pin_memory()
+                      for x in (u.bm_out, u.xi_out, u.bn_out, u.stats)) for u in ups]
+        dins = [(torch.empty_like(th), torch.empty_like(bn), torch.empty_like(gate)) for _ in ups]
+        h2d, d2h = torch.cuda.Stream(), torch.cuda.Stream()
+        ev = lambda: torch.cuda.Event()
+        in_ready = [ev(), ev()]
+        computed = [ev(), ev()]
+        out_read = [ev(), ev()]
+        for k in range(2):  # nothing pending yet
+            computed[k].record(stream)
+            out_read[k].record(stream)
 
-        def e2e_step():
-            d_th.copy_(h_th, non_blocking=True)
-            d_bn.copy_(h_bn, non_blocking=True)
-            d_u.copy_(h_u, non_blocking=True)
-            up.run(d_u, d_bn, theta=d_th)
-            o_bm.copy_(up.bm_out, non_blocking=True)
-            o_xi.copy_(up.xi_out, non_blocking=True)
-            o_bn.copy_(up.bn_out, non_blocking=True)
-            o_st.copy_(up.stats, non_blocking=True)
+        def e2e_step(i):
+            k = i % 2
+            d_th, d_bn, d_u = dins[k]
+            with torch.cuda.stream(h2d):
+                h2d.wait_event(computed[k])        # step i-2 has finished reading these inputs
+                d_th.copy_(h_th, non_blocking=True)
+                d_bn.copy_(h_bn, non_blocking=True)
+                d_u.copy_(h_u, non_blocking=True)
+                in_ready[k].record(h2d)
+            stream.wait_event(in_ready[k])
+            stream.wait_event(out_read[k])         # step i-2's outputs have been read back
+            ups[k].run(d_u, d_bn, theta=d_th, stream=stream)
+            computed[k].record(stream)
+            with torch.cuda.stream(d2h):
+                d2h.wait_event(computed[k])
+                for o, x in zip(outs[k], (ups[k].bm_out, ups[k].xi_out, ups[k].bn_out, ups[k].stats)):
+                    o.copy_(x, non_blocking=True)
+                out_read[k].record(d2h)
 
-        for _ in range(args.warmup):
-            e2e_step()
+        for i in range(args.warmup):
+            e2e_step(i)
         barrier()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for _ in range(args.steps):
-            e2e_step()
+        for i in range(args.steps):
+            e2e_step(i)
+        for k in range(2):
+            stream.wait_event(out_read[k])
         b.record(stream)
         barrier()
         e_ms = a.elapsed_time(b)
@@ -318,7 +340,8 @@ def run_ours(args):
         esz = lambda x: x.numel() * x.element_size()
         e2e = {"value": ws * args.steps / (e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": esz(h_th) + esz(h_bn) + esz(h_u),
-               "d2h_bytes_per_step": esz(o_bm) + esz(o_xi) + esz(o_bn) + esz(o_st)}
+               "d2h_bytes_per_step": sum(esz(o) for o in outs[0]),
+               "pipelining": "two updaters alternate; copies overlap the next step's compute"}
         L.stream_check()
 
     if rank != 0:
@@ -441,6 +464,68 @@ def run_serve(args):
     return 0
 
 
+def run_svd_arm(args):
+    """Comparison arms of the single-gate benchmark (the paper's Fig. 5 comparison,
+    restated on this GPU): the QR update of this library against the SVD-based update
+    and the eigendecomposition-based update run through torch's cuSOLVER calls, on the
+    same theta (chi, d, d, chi). Measurement only: the library never calls a solver.
+    SVD arm: theta = U S V^dag (reduced), keep chi, B~m = theta V_chi. EIG arm:
+    theta^dag theta = V S^2 V^dag (Hermitian eigensolver), keep the chi largest,
+    B~m = theta V_chi. Both arms skip the gate (supplied theta), as the QR arm does not:
+    the QR arm includes the gate and every step of the update."""
+    import torch
+    from paper_2212_09782_b300 import lib as L
+    from paper_2212_09782_b300 import workloads as W
+    chi, d = args.chi, args.d
+    wl = W.bond_microbench(chi, d, seed=W.BASE_SEED + 2)
+    stream = torch.cuda.current_stream()
+    out = {"metric": f"single bond update time, QR (this library) vs SVD / EIG (cuSOLVER via torch), chi={chi} d={d}",
+           "unit": "ms per update", "higher_is_better": False, "data": "synthetic",
+           "steps": args.steps, "warmup": args.warmup, "arms": {}}
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / args.steps
+
+    arms = [("c64_3xtf32", torch.complex64)] + ([("c128", torch.complex128)] if args.svd_c128 else [])
+    for prec, cdt in arms:
+        th = torch.from_numpy(wl["theta"]).to(dtype=cdt, device="cuda")
+        bn = torch.from_numpy(wl["Bn"]).to(dtype=cdt, device="cuda")
+        gate = torch.from_numpy(wl["U"]).to("cuda")
+        tr = L.trunc_default(L.PLAIN, chi)
+        up = L.BondUpdater(L.PRECISIONS[prec], chi, d, chi, chi, tr, xi_kind=0, theta_given=True)
+        qr_ms = timed(lambda: up.run(gate, bn, theta=th))
+        L.stream_check()
+        M = th.reshape(chi * d, d * chi)
+
+        def svd_arm():
+            U, S, Vh = torch.linalg.svd(M, full_matrices=False)
+            return M @ Vh[:chi].conj().T
+
+        def eig_arm():
+            w, V = torch.linalg.eigh(M.conj().T @ M)
+            return M @ V[:, -chi:]
+
+        svd_ms = timed(svd_arm)
+        eig_ms = timed(eig_arm)
+        key = "c64" if prec != "c128" else "c128"
+        out["arms"][key] = {"qr_ms": qr_ms, "svd_ms": svd_ms, "eig_ms": eig_ms,
+                            "qr_speedup_over_svd": svd_ms / qr_ms, "qr_speedup_over_eig": eig_ms / qr_ms,
+                            "qr_precision": prec}
+        del th, bn, up, M
+        torch.cuda.empty_cache()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -453,12 +538,14 @@ def main():
     ap.add_argument("--d", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["bond", "chain", "serve"], default="bond")
+    ap.add_argument("--workload", choices=["bond", "chain", "serve", "svd"], default="bond")
     ap.add_argument("--serve-requests", type=int, default=12)
     ap.add_argument("--serve-steps", type=int, default=6)
     ap.add_argument("--chain-L", type=int, default=128)
     ap.add_argument("--chain-chi", type=int, default=512)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--svd-c128", action="store_true",
+                    help="svd workload: add the complex128 arms (the cuSOLVER SVD alone takes ~165 s)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -468,6 +555,8 @@ def main():
         return run_chain(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "svd":
+        return run_svd_arm(args)
     return run_ours(args)
 
 
