@@ -386,14 +386,12 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
-// A'[m][2k..2k+1] = (Re, Im) opA(m, k), split hi/lo
-__global__ void k_prep_a(const float2* __restrict__ A, long long sam, long long sak, int conj,
-                         int M, int K, float* __restrict__ hi, float* __restrict__ lo, int ld,
-                         int three) {
-  __shared__ float2 t[32][33];
-  pdl_launch_dependents();
-  pdl_wait();
-  const int m0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+// A'[m][2k..2k+1] = (Re, Im) opA(m, k), split hi/lo; one 32 x 32 tile (bx, by)
+__device__ __forceinline__ void prep_a_tile(const float2* __restrict__ A, long long sam, long long sak,
+                                            int conj, int M, int K, float* __restrict__ hi,
+                                            float* __restrict__ lo, int ld, int three, int bx, int by,
+                                            float2 (*t)[33]) {
+  const int m0 = by * 32, k0 = bx * 32;
   const bool kc = (sak == 1);
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     int mm = kc ? r : threadIdx.x, kk = kc ? threadIdx.x : r;
@@ -417,13 +415,11 @@ __global__ void k_prep_a(const float2* __restrict__ A, long long sam, long long 
 }
 
 // B'^T rows 2n: (Re b, -Im b), 2n+1: (Im b, Re b) at columns 2k, 2k+1; b = opB(k, n)
-__global__ void k_prep_b(const float2* __restrict__ B, long long sbk, long long sbn, int conj,
-                         int K, int N, float* __restrict__ hi, float* __restrict__ lo, int ld,
-                         int three) {
-  __shared__ float2 t[32][33];  // [n][k]
-  pdl_launch_dependents();
-  pdl_wait();
-  const int n0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+__device__ __forceinline__ void prep_b_tile(const float2* __restrict__ B, long long sbk, long long sbn,
+                                            int conj, int K, int N, float* __restrict__ hi,
+                                            float* __restrict__ lo, int ld, int three, int bx, int by,
+                                            float2 (*t)[33]) {  // t: [n][k]
+  const int n0 = by * 32, k0 = bx * 32;
   const bool kc = (sbk == 1);
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     int nn = kc ? r : threadIdx.x, kk = kc ? threadIdx.x : r;
@@ -449,6 +445,25 @@ __global__ void k_prep_b(const float2* __restrict__ B, long long sbk, long long 
       }
     }
   }
+}
+
+struct PrepJob {
+  const float2* src; long long s0, s1; int conj, rows, K;
+  float* hi; float* lo; int ld;
+  int gx, gy;  // tiles along K and along rows
+};
+// One launch prepares both operands: blockIdx.z = 0 the A' tiles, 1 the B' tiles
+// (tiles beyond an operand's own grid return at once).
+__global__ void k_prep(PrepJob a, PrepJob b, int three) {
+  __shared__ float2 t[32][33];
+  pdl_launch_dependents();
+  pdl_wait();
+  const PrepJob& j = blockIdx.z == 0 ? a : b;
+  if ((int)blockIdx.x >= j.gx || (int)blockIdx.y >= j.gy) return;
+  if (blockIdx.z == 0)
+    prep_a_tile(j.src, j.s0, j.s1, j.conj, j.rows, j.K, j.hi, j.lo, j.ld, three, blockIdx.x, blockIdx.y, t);
+  else
+    prep_b_tile(j.src, j.s0, j.s1, j.conj, j.K, j.rows, j.hi, j.lo, j.ld, three, blockIdx.x, blockIdx.y, t);
 }
 
 // ------------------------------------------------------------------ host
@@ -535,7 +550,7 @@ int tc_gemm(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStream_t 
     return gemm_simt<float>(g0, st, nullptr, 0, prof_family == PROF_TC_GEMM ? PROF_SIMT_GEMM : prof_family);
   QR_TRY(get_encode());
 
-  // ---- A' (cached per source/op within one bond update)
+  // ---- A' (cached per source/op within one bond update) and B'^T, in one launch
   TcSlot* sa = nullptr;
   for (int i = 0; i < 2 && cacheable; ++i) {
     TcSlot& s = w.a[i];
@@ -543,26 +558,26 @@ int tc_gemm(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStream_t 
         s.conj == g.conj_a && s.three == three && s.ld == ld)
       sa = &s;
   }
-  if (!sa) {
+  const bool need_a = (sa == nullptr);
+  if (need_a) {
     sa = &w.a[w.a_next];
     w.a_next ^= 1;
-    dim3 grid((unsigned)ceil_div(K, 32), (unsigned)ceil_div(M, 32));
-    ProfScope prof(PROF_PREP, st, 0, 8.0 * M * K + (three ? 16.0 : 8.0) * M * K);
-    QR_CUDA_TRY(launch_pdl(k_prep_a, grid, dim3(32, 8), 0, st, g.A, g.sam, g.sak, g.conj_a ? 1 : 0,
-                           M, K, sa->hi, sa->lo, ld, three ? 1 : 0));
+  }
+  {
+    PrepJob ja{g.A, g.sam, g.sak, g.conj_a ? 1 : 0, M, K, sa->hi, sa->lo, ld,
+               need_a ? (int)ceil_div(K, 32) : 0, need_a ? (int)ceil_div(M, 32) : 0};
+    PrepJob jb{g.B, g.sbk, g.sbn, g.conj_b ? 1 : 0, N, K, w.b.hi, w.b.lo, ld,
+               (int)ceil_div(K, 32), (int)ceil_div(N, 32)};
+    dim3 grid((unsigned)std::max(ja.gx, jb.gx), (unsigned)std::max(ja.gy, jb.gy), 2);
+    ProfScope prof(PROF_PREP, st, 0,
+                   (need_a ? 8.0 * M * K + (three ? 16.0 : 8.0) * M * K : 0.0) +
+                       8.0 * N * K + (three ? 32.0 : 16.0) * N * K);
+    QR_CUDA_TRY(launch_pdl(k_prep, grid, dim3(32, 8), 0, st, ja, jb, three ? 1 : 0));
     note_launch();
-    QR_CUDA_TRY(cudaGetLastError());
+  }
+  if (need_a) {
     sa->valid = cacheable; sa->src = g.A; sa->s0 = g.sam; sa->s1 = g.sak; sa->rows = M; sa->cols = K;
     sa->conj = g.conj_a; sa->three = three; sa->ld = ld;
-  }
-  // ---- B'^T
-  {
-    dim3 grid((unsigned)ceil_div(K, 32), (unsigned)ceil_div(N, 32));
-    ProfScope prof(PROF_PREP, st, 0, 8.0 * N * K + (three ? 32.0 : 16.0) * N * K);
-    QR_CUDA_TRY(launch_pdl(k_prep_b, grid, dim3(32, 8), 0, st, g.B, g.sbk, g.sbn, g.conj_b ? 1 : 0,
-                           K, N, w.b.hi, w.b.lo, ld, three ? 1 : 0));
-    note_launch();
-    QR_CUDA_TRY(cudaGetLastError());
   }
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
   QR_TRY(make_map(&ta_hi, sa->hi, M, 2 * K, ld, BM));
