@@ -526,6 +526,105 @@ def run_svd_arm(args):
     return 0
 
 
+def run_c1(args):
+    """C1: finite chain L = 16, d = 3, g = 1.5, quench from |0...0>, Strang dt = 0.05,
+    20 steps, chi_max = 32, plain QR, complex128. The whole run on the GPU (wall time,
+    synchronised at every step to read <Z> on the middle site) against the oracle's run on
+    the host cores; max |<Z>_gpu - <Z>_oracle| over the steps."""
+    import torch
+    from paper_2212_09782_b300 import lib as L
+    sys.path.insert(0, ROOT)
+    from oracle import mps as omps
+    Lc, d, g, dt, steps, chi = 16, 3, 1.5, 0.05, 20, 32
+    Z = np.diag(np.exp(2j * np.pi * np.arange(d) / d))
+    tr = L.trunc_default(L.PLAIN, chi)
+    half = L.clock_layer_gates(Lc, d, g, dt / 2)
+    full = L.clock_layer_gates(Lc, d, g, dt)
+
+    def gpu_run():
+        s = L.MPS(Lc, d, chi, precision="c128")
+        zs = []
+        for _ in range(steps):
+            L.tebd_step(s, half, full, tr)
+            zs.append(s.expectation(Lc // 2, Z))
+        s.close()
+        return zs
+    for _ in range(max(1, args.warmup)):
+        gpu_run()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    zg = gpu_run()
+    torch.cuda.synchronize()
+    t_gpu = time.perf_counter() - t0
+
+    o = omps.product_state(Lc, d, 0)
+    oh, of = omps.strang_gates(Lc, d, g, dt)
+    zo = []
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        omps.tebd_step(o, oh, of, scheme="plain", chi_max=chi)
+        zo.append(omps.expectation_1site(o, Lc // 2, Z))
+    t_cpu = time.perf_counter() - t0
+    nb = Lc - 1
+    upd = steps * (2 * len(range(0, nb, 2)) + len(range(1, nb, 2)))
+    out = {"metric": "C1 quench run time, L=16 d=3 chi<=32 plain c128 (20 Strang steps)",
+           "value": upd / t_gpu, "unit": "bond updates/s", "higher_is_better": True,
+           "gpu_run_s": t_gpu, "bond_updates": upd,
+           "cpu_baseline": {"value": upd / t_cpu, "unit": "bond updates/s", "cores": os.cpu_count(),
+                            "kind": "oracle", "sample": "the whole C1 run (complex128 NumPy/LAPACK)",
+                            "run_s": t_cpu},
+           "max_abs_dZ": float(np.max(np.abs(np.array(zg) - np.array(zo)))),
+           "data": "synthetic", "dtype": "c128"}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_c3(args):
+    """C3: uniform two-site cell, d = 5, g = 2.0, |00>, dt = 0.02, CBE with
+    dchi = max(100, ceil(0.1 chi)), chi_max = 1024, svd_min = 1e-14, complex64 3xTF32.
+    Steps until --c3-steps or --c3-seconds; each step's device time (synchronised) is
+    binned by the largest bond dimension after the step."""
+    import torch
+    from paper_2212_09782_b300 import lib as L
+    Lc, d, g, dt, chi = 2, 5, 2.0, 0.02, 1024
+    tr = L.trunc_default(L.CBE, chi)
+    half = L.clock_layer_gates(Lc, d, g, dt / 2, infinite=True)
+    full = L.clock_layer_gates(Lc, d, g, dt, infinite=True)
+    s = L.MPS(Lc, d, chi, precision=args.precision, infinite=True)
+    Z = np.diag(np.exp(2j * np.pi * np.arange(d) / d))
+    buckets = [(1, 64), (64, 256), (256, 512), (512, 1025)]
+    acc = {b: [0.0, 0] for b in buckets}
+    t_start = time.perf_counter()
+    rows = []
+    n = 0
+    for step in range(args.c3_steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        L.tebd_step(s, half, full, tr)
+        s.sync()
+        dtm = time.perf_counter() - t0
+        chis = s.bond_dims()
+        cmax = max(chis)
+        for b in buckets:
+            if b[0] <= cmax < b[1]:
+                acc[b][0] += dtm
+                acc[b][1] += 3
+        n += 1
+        if step % 10 == 9 or step == args.c3_steps - 1:
+            rows.append({"step": step + 1, "chi": chis, "z": [s.expectation(0, Z).real],
+                         "eps": s.truncation_error(-1), "s_vN": s.entropy(0)})
+        if time.perf_counter() - t_start > args.c3_seconds:
+            break
+    out = {"metric": "C3 uniform CBE, d=5 g=2 dt=0.02, chi 1->1024: bond updates/s per chi bucket",
+           "unit": "bond updates/s", "higher_is_better": True, "steps_done": n,
+           "per_bucket": {f"{a}-{b - 1}": {"updates": v[1], "updates_per_s": v[1] / v[0] if v[0] else None}
+                          for (a, b), v in acc.items()},
+           "trace": rows, "dtype": args.precision, "data": "synthetic"}
+    print(json.dumps(out), flush=True)
+    s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -538,7 +637,9 @@ def main():
     ap.add_argument("--d", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["bond", "chain", "serve", "svd"], default="bond")
+    ap.add_argument("--workload", choices=["bond", "chain", "serve", "svd", "c1", "c3"], default="bond")
+    ap.add_argument("--c3-steps", type=int, default=200)
+    ap.add_argument("--c3-seconds", type=float, default=240.0)
     ap.add_argument("--serve-requests", type=int, default=12)
     ap.add_argument("--serve-steps", type=int, default=6)
     ap.add_argument("--chain-L", type=int, default=128)
@@ -557,6 +658,10 @@ def main():
         return run_serve(args)
     if args.workload == "svd":
         return run_svd_arm(args)
+    if args.workload == "c1":
+        return run_c1(args)
+    if args.workload == "c3":
+        return run_c3(args)
     return run_ours(args)
 
 

@@ -392,6 +392,15 @@ int qrtebd_mps_destroy(qrtebd_mps* s) {
 int qrtebd_apply_gate_layer(qrtebd_mps* s, int parity, const double* gates_host,
                             const qrtebd_trunc* tr, double* eps_out) {
   if (!s || !gates_host || !tr || (parity != 0 && parity != 1)) return QRTEBD_ERR_INVALID_ARG;
+  // The bonds of one parity are independent (Fig. 2a): with two or more of them the layer
+  // runs on the executor's worker streams, side by side (and, plain scheme, as a replayed
+  // CUDA graph once its shapes repeat); a single bond runs on the state's own stream.
+  if ((gate_count(s) - parity + 1) / 2 >= 2) {
+    qrtebd_mps* const states[1] = {s};
+    const double* const gates[1] = {gates_host};
+    double* const eps[1] = {eps_out};
+    return qrtebd_apply_gate_layer_batched(states, 1, parity, gates, tr, eps);
+  }
   return s->precision == QRTEBD_C128 ? apply_layer_t<double>(s, parity, gates_host, tr, eps_out)
                                      : apply_layer_t<float>(s, parity, gates_host, tr, eps_out);
 }
