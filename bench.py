@@ -166,6 +166,26 @@ def dist_setup():
     return ws, rank, local
 
 
+def replica_seed(base, rank):
+    """Seed of one replica's synthetic workload: every rank updates its own bond."""
+    return base + 2 + rank
+
+
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (replicas run independently; the job ends with the last)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, ws, t_max_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return ws * units_per_rank / (t_max_ms / 1e3)
+
+
 def cpu_oracle_update(wl, chi):
     from oracle import bond
     th = wl["theta"].astype(np.complex128)
@@ -216,7 +236,7 @@ def run_ours(args):
 
     chi, d = args.chi, args.d
     prec = L.PRECISIONS[args.precision]
-    wl = W.bond_microbench(chi, d, seed=W.BASE_SEED + 2 + rank)
+    wl = W.bond_microbench(chi, d, seed=replica_seed(W.BASE_SEED, rank))
     cdt = torch.complex128 if prec == L.C128 else torch.complex64
     th = torch.from_numpy(wl["theta"]).to(dtype=cdt, device="cuda")
     bn = torch.from_numpy(wl["Bn"]).to(dtype=cdt, device="cuda")
@@ -256,12 +276,8 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = ev[0][0].elapsed_time(ev[-1][1])
     L.stream_check()
-    t_max = total_ms
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = ws * args.steps / (t_max / 1e3)
+    t_max = max_over_ranks(total_ms, dist, "cuda")
+    value = job_throughput(args.steps, ws, t_max)
 
     # ---- per-kernel durations: the same steps again, every launch bracketed by CUDA
     #      events on its stream (the brackets cost a little, hence a separate pass)
@@ -332,13 +348,9 @@ def run_ours(args):
             stream.wait_event(out_read[k])
         b.record(stream)
         barrier()
-        e_ms = a.elapsed_time(b)
-        if dist is not None:
-            t = torch.tensor([e_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms = max_over_ranks(a.elapsed_time(b), dist, "cuda")
         esz = lambda x: x.numel() * x.element_size()
-        e2e = {"value": ws * args.steps / (e_ms / 1e3), "unit": UNIT,
+        e2e = {"value": job_throughput(args.steps, ws, e_ms), "unit": UNIT,
                "h2d_bytes_per_step": esz(h_th) + esz(h_bn) + esz(h_u),
                "d2h_bytes_per_step": sum(esz(o) for o in outs[0]),
                "pipelining": "two updaters alternate; copies overlap the next step's compute"}
