@@ -549,9 +549,10 @@ __global__ void __launch_bounds__(WY_NT) k_apply_wy(cx<T>* C, long long ldc, con
   for (int i = tid; i < nr * nc; i += WY_NT) Cs[i] = C[(long long)(r0 + i / nc) * ldc + i % nc];
   for (int i = tid; i < kb * kb; i += WY_NT) Ts[i] = Tt[(long long)(i / kb) * ldt + i % kb];
   __syncthreads();
-  // thread = (column c, parity of a): 16 accumulators
+  // thread = (column c, residue of a modulo APS): NA accumulators
+  constexpr int APS = WY_NT / WY_NC;
   const int c = tid % WY_NC, ap = tid / WY_NC;
-  constexpr int NA = WY_KB / 2;
+  constexpr int NA = WY_KB / APS;
   // (1) partial V^dag C
   if (c < nc) {
     cx<T> acc[NA];
@@ -561,13 +562,13 @@ __global__ void __launch_bounds__(WY_NT) k_apply_wy(cx<T>* C, long long ldc, con
       const cx<T> x = Cs[r * nc + c];
 #pragma unroll
       for (int i = 0; i < NA; ++i) {
-        const int a = ap + 2 * i;
+        const int a = ap + APS * i;
         if (a < kb) cfma<T>(acc[i], cconj<T>(Vs[r * kb + a]), x);
       }
     }
 #pragma unroll
     for (int i = 0; i < NA; ++i) {
-      const int a = ap + 2 * i;
+      const int a = ap + APS * i;
       if (a < kb) part[((size_t)b * kb + a) * nc + c] = acc[i];
     }
   }
@@ -598,7 +599,7 @@ __global__ void __launch_bounds__(WY_NT) k_apply_wy(cx<T>* C, long long ldc, con
   if (c < nc) {
 #pragma unroll
     for (int i = 0; i < NA; ++i) {
-      const int a = ap + 2 * i;
+      const int a = ap + APS * i;
       cx<T> s = zero;
       if (a < kb)
         for (int q = 0; q <= a; ++q) cfma<T>(s, cconj<T>(Ts[q * kb + a]), Ws[q * nc + c]);
@@ -609,13 +610,13 @@ __global__ void __launch_bounds__(WY_NT) k_apply_wy(cx<T>* C, long long ldc, con
   if (c < nc) {
 #pragma unroll
     for (int i = 0; i < NA; ++i) {
-      const int a = ap + 2 * i;
+      const int a = ap + APS * i;
       if (a < kb) Ws[a * nc + c] = w2[i];
     }
   }
   __syncthreads();
   if (c < nc) {
-    for (int r = ap; r < nr; r += 2) {
+    for (int r = ap; r < nr; r += APS) {
       cx<T> s0 = zero, s1 = zero;
       int a = 0;
       for (; a + 1 < kb; a += 2) {
