@@ -459,38 +459,60 @@ __global__ void k_eye(cx<T>* Q, long long ldq, int m, int n) {
 constexpr int TO_NT = 1024;
 template <typename T>
 __global__ void __launch_bounds__(TO_NT) k_t_outer(cx<T>* Tb, int ldt, const cx<T>* G, int ldg,
-                                                   int kbo, int nb, cx<T>* tmp) {
+                                                   int kbo, int nb, cx<T>* tmp_g) {
+  // T (kbo x kbo, upper) in shared memory when it fits (complex64), else in place
+  extern __shared__ __align__(16) unsigned char sm[];
   pdl_launch_dependents();
   pdl_wait();
+  const bool in_smem = sizeof(cx<T>) == 8;
+  const int lds = kbo + 1;
+  cx<T>* Ts = in_smem ? reinterpret_cast<cx<T>*>(sm) : Tb;
+  const int ldT = in_smem ? lds : ldt;
+  cx<T>* tmp = in_smem ? Ts + (size_t)kbo * lds : tmp_g;
+  if (in_smem) {
+    for (int o = threadIdx.x; o < kbo * kbo; o += TO_NT)
+      Ts[(o / kbo) * lds + o % kbo] = Tb[(long long)(o / kbo) * ldt + o % kbo];
+    __syncthreads();
+  }
   for (int c0 = nb; c0 < kbo; c0 += nb) {
     const int w = min(nb, kbo - c0);
+    // tmp = G[0:c0, c0:c0+w] T[c0:c0+w, c0:c0+w]
     for (int o = threadIdx.x; o < c0 * w; o += TO_NT) {
       const int i = o / w, j = o % w;
       cx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0);
       int k = 0;
       for (; k + 1 <= j; k += 2) {
-        cfma<T>(a0, G[(long long)i * ldg + c0 + k], Tb[(long long)(c0 + k) * ldt + c0 + j]);
-        cfma<T>(a1, G[(long long)i * ldg + c0 + k + 1], Tb[(long long)(c0 + k + 1) * ldt + c0 + j]);
+        cfma<T>(a0, G[(long long)i * ldg + c0 + k], Ts[(c0 + k) * ldT + c0 + j]);
+        cfma<T>(a1, G[(long long)i * ldg + c0 + k + 1], Ts[(c0 + k + 1) * ldT + c0 + j]);
       }
-      if (k <= j) cfma<T>(a0, G[(long long)i * ldg + c0 + k], Tb[(long long)(c0 + k) * ldt + c0 + j]);
+      if (k <= j) cfma<T>(a0, G[(long long)i * ldg + c0 + k], Ts[(c0 + k) * ldT + c0 + j]);
       tmp[o] = cadd<T>(a0, a1);
     }
     __syncthreads();
+    // T[0:c0, c0:c0+w] = -T[0:c0, 0:c0] tmp
     for (int o = threadIdx.x; o < c0 * w; o += TO_NT) {
       const int i = o / w, j = o % w;
       cx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0);
       int k = i;
       for (; k + 1 < c0; k += 2) {
-        cfma<T>(a0, Tb[(long long)i * ldt + k], tmp[k * w + j]);
-        cfma<T>(a1, Tb[(long long)i * ldt + k + 1], tmp[(k + 1) * w + j]);
+        cfma<T>(a0, Ts[i * ldT + k], tmp[k * w + j]);
+        cfma<T>(a1, Ts[i * ldT + k + 1], tmp[(k + 1) * w + j]);
       }
-      if (k < c0) cfma<T>(a0, Tb[(long long)i * ldt + k], tmp[k * w + j]);
+      if (k < c0) cfma<T>(a0, Ts[i * ldT + k], tmp[k * w + j]);
       const cx<T> r = cadd<T>(a0, a1);
-      Tb[(long long)i * ldt + c0 + j] = mk<T>(-r.x, -r.y);
+      Ts[i * ldT + c0 + j] = mk<T>(-r.x, -r.y);
     }
     __syncthreads();
   }
+  if (in_smem)
+    for (int o = threadIdx.x; o < kbo * kbo; o += TO_NT)
+      Tb[(long long)(o / kbo) * ldt + o % kbo] = Ts[(o / kbo) * lds + o % kbo];
 }
+
+template <typename T> size_t t_outer_smem(int kbo, int nb) {
+  return sizeof(cx<T>) == 8 ? ((size_t)kbo * (kbo + 1) + (size_t)kbo * nb) * sizeof(cx<T>) : 0;
+}
+template <typename T> bool g_to_attr = false;
 
 // ------------------------------------------------------ fused narrow block-reflector update
 // C <- (I - V T V^dag)^dag C = C - V T^dag (V^dag C) for the columns of an outer block right
@@ -573,22 +595,34 @@ __global__ void __launch_bounds__(WY_NT) k_apply_wy(cx<T>* C, long long ldc, con
     }
   }
   if (!grid_barrier(bar, G, err)) return;
-  // (2) sum of the partials: lanes = 32 consecutive outputs, warps over output groups
+  // (2) sum of the partials: a CTA per group of 32 consecutive outputs; its warps split
+  //     the G partials (independent loads in flight), then combine in shared memory
   {
+    __shared__ cx<T> red[WY_NT / 32][32];
     const int warp = tid >> 5, lane = tid & 31;
     const int nout = kb * nc, ngroups = (nout + 31) / 32;
-    for (int grp = b * (WY_NT / 32) + warp; grp < ngroups; grp += G * (WY_NT / 32)) {
+    for (int grp = b; grp < ngroups; grp += (int)G) {
       const int o = grp * 32 + lane;
+      cx<T> s0 = zero, s1 = zero, s2 = zero, s3 = zero;
       if (o < nout) {
-        cx<T> s0 = zero, s1 = zero;
-        unsigned z = 0;
-        for (; z + 1 < G; z += 2) {
+        unsigned z = warp;
+        constexpr unsigned WS = WY_NT / 32;
+        for (; z + 3 * WS < G; z += 4 * WS) {
           s0 = cadd<T>(s0, part[(size_t)z * nout + o]);
-          s1 = cadd<T>(s1, part[(size_t)(z + 1) * nout + o]);
+          s1 = cadd<T>(s1, part[(size_t)(z + WS) * nout + o]);
+          s2 = cadd<T>(s2, part[(size_t)(z + 2 * WS) * nout + o]);
+          s3 = cadd<T>(s3, part[(size_t)(z + 3 * WS) * nout + o]);
         }
-        if (z < G) s0 = cadd<T>(s0, part[(size_t)z * nout + o]);
-        Wg[o] = cadd<T>(s0, s1);
+        for (; z < G; z += WS) s0 = cadd<T>(s0, part[(size_t)z * nout + o]);
       }
+      red[warp][lane] = cadd<T>(cadd<T>(s0, s1), cadd<T>(s2, s3));
+      __syncthreads();
+      if (warp == 0 && o < nout) {
+        cx<T> t = red[0][lane];
+        for (int w = 1; w < WY_NT / 32; ++w) t = cadd<T>(t, red[w][lane]);
+        Wg[o] = t;
+      }
+      __syncthreads();
     }
   }
   if (!grid_barrier(bar, G, err)) return;
@@ -907,7 +941,13 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
       // T[0:c0, c0:c0+w] = -T[0:c0, 0:c0] G[0:c0, c0:c0+w] T[c0:c0+w, c0:c0+w]
       GemmArgs<T> gg{kbo, kbo, mo, Vb, 1, ldv, true, Vb, ldv, 1, false, s.G, nbo, 1, one, zero};
       QR_TRY(run_gemm<T>(gg, s, st, gm));
-      QR_CUDA_TRY(launch_pdl(k_t_outer<T>, dim3(1), dim3(TO_NT), 0, st, Tb, nbo,
+      const size_t tsm = t_outer_smem<T>(kbo, nb);
+      if (!g_to_attr<T>) {
+        QR_CUDA_TRY(cudaFuncSetAttribute(k_t_outer<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)t_outer_smem<T>(NBO, KBMAX)));
+        g_to_attr<T> = true;
+      }
+      QR_CUDA_TRY(launch_pdl(k_t_outer<T>, dim3(1), dim3(TO_NT), tsm, st, Tb, nbo,
                              static_cast<const cx<T>*>(s.G), nbo, kbo, nb, s.tmp));
       note_launch();
     }
