@@ -451,6 +451,12 @@ __global__ void k_eye(cx<T>* Q, long long ldq, int m, int n) {
   Q[i * ldq + j] = mk<T>(i == j ? T(1) : T(0), 0);
 }
 
+template <typename T> __device__ __forceinline__ void cp_async_cx(cx<T>* dst_smem, const cx<T>* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
+               "l"(src), "n"((int)sizeof(cx<T>)) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // ------------------------------------------------------ outer compact-WY factor
 // T of an outer block from its inner blocks' factors (on the diagonal of Tb) and the Gram
 // matrix G = V^dag V of the block: column block by column block,
@@ -469,23 +475,34 @@ __global__ void __launch_bounds__(TO_NT) k_t_outer(cx<T>* Tb, int ldt, const cx<
   cx<T>* Ts = in_smem ? reinterpret_cast<cx<T>*>(sm) : Tb;
   const int ldT = in_smem ? lds : ldt;
   cx<T>* tmp = in_smem ? Ts + (size_t)kbo * lds : tmp_g;
+  cx<T>* Gs = in_smem ? tmp + (size_t)kbo * nb : nullptr;  // G[0:c0, c0:c0+w]
   if (in_smem) {
     for (int o = threadIdx.x; o < kbo * kbo; o += TO_NT)
-      Ts[(o / kbo) * lds + o % kbo] = Tb[(long long)(o / kbo) * ldt + o % kbo];
+      cp_async_cx<T>(Ts + (o / kbo) * lds + o % kbo, Tb + (long long)(o / kbo) * ldt + o % kbo);
+    cp_async_wait_all();
     __syncthreads();
   }
   for (int c0 = nb; c0 < kbo; c0 += nb) {
     const int w = min(nb, kbo - c0);
+    const cx<T>* Gb = G + c0;
+    int ldgb = ldg;
+    if (in_smem) {
+      for (int o = threadIdx.x; o < c0 * w; o += TO_NT)
+        cp_async_cx<T>(Gs + o, G + (long long)(o / w) * ldg + c0 + o % w);
+      cp_async_wait_all();
+      __syncthreads();
+      Gb = Gs; ldgb = w;
+    }
     // tmp = G[0:c0, c0:c0+w] T[c0:c0+w, c0:c0+w]
     for (int o = threadIdx.x; o < c0 * w; o += TO_NT) {
       const int i = o / w, j = o % w;
       cx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0);
       int k = 0;
       for (; k + 1 <= j; k += 2) {
-        cfma<T>(a0, G[(long long)i * ldg + c0 + k], Ts[(c0 + k) * ldT + c0 + j]);
-        cfma<T>(a1, G[(long long)i * ldg + c0 + k + 1], Ts[(c0 + k + 1) * ldT + c0 + j]);
+        cfma<T>(a0, Gb[(long long)i * ldgb + k], Ts[(c0 + k) * ldT + c0 + j]);
+        cfma<T>(a1, Gb[(long long)i * ldgb + k + 1], Ts[(c0 + k + 1) * ldT + c0 + j]);
       }
-      if (k <= j) cfma<T>(a0, G[(long long)i * ldg + c0 + k], Ts[(c0 + k) * ldT + c0 + j]);
+      if (k <= j) cfma<T>(a0, Gb[(long long)i * ldgb + k], Ts[(c0 + k) * ldT + c0 + j]);
       tmp[o] = cadd<T>(a0, a1);
     }
     __syncthreads();
@@ -510,7 +527,7 @@ __global__ void __launch_bounds__(TO_NT) k_t_outer(cx<T>* Tb, int ldt, const cx<
 }
 
 template <typename T> size_t t_outer_smem(int kbo, int nb) {
-  return sizeof(cx<T>) == 8 ? ((size_t)kbo * (kbo + 1) + (size_t)kbo * nb) * sizeof(cx<T>) : 0;
+  return sizeof(cx<T>) == 8 ? ((size_t)kbo * (kbo + 1) + 2 * (size_t)kbo * nb) * sizeof(cx<T>) : 0;
 }
 template <typename T> bool g_to_attr = false;
 
@@ -567,9 +584,10 @@ __global__ void __launch_bounds__(WY_NT) k_apply_wy(cx<T>* C, long long ldc, con
   const int b = blockIdx.x;
   const int r0 = b * rpb, nr = max(0, min(rpb, mr - r0));
   const cx<T> zero = mk<T>(0, 0);
-  for (int i = tid; i < nr * kb; i += WY_NT) Vs[i] = V[(long long)(r0 + i / kb) * ldv + i % kb];
-  for (int i = tid; i < nr * nc; i += WY_NT) Cs[i] = C[(long long)(r0 + i / nc) * ldc + i % nc];
-  for (int i = tid; i < kb * kb; i += WY_NT) Ts[i] = Tt[(long long)(i / kb) * ldt + i % kb];
+  for (int i = tid; i < nr * kb; i += WY_NT) cp_async_cx<T>(Vs + i, V + (long long)(r0 + i / kb) * ldv + i % kb);
+  for (int i = tid; i < nr * nc; i += WY_NT) cp_async_cx<T>(Cs + i, C + (long long)(r0 + i / nc) * ldc + i % nc);
+  for (int i = tid; i < kb * kb; i += WY_NT) cp_async_cx<T>(Ts + i, Tt + (long long)(i / kb) * ldt + i % kb);
+  cp_async_wait_all();
   __syncthreads();
   // thread = (column c, residue of a modulo APS): NA accumulators
   constexpr int APS = WY_NT / WY_NC;
@@ -627,7 +645,8 @@ __global__ void __launch_bounds__(WY_NT) k_apply_wy(cx<T>* C, long long ldc, con
   }
   if (!grid_barrier(bar, G, err)) return;
   // (3) W2 = T^dag W in shared memory, then C -= V W2 on the slab
-  for (int i = tid; i < kb * nc; i += WY_NT) Ws[i] = Wg[i];
+  for (int i = tid; i < kb * nc; i += WY_NT) cp_async_cx<T>(Ws + i, Wg + i);
+  cp_async_wait_all();
   __syncthreads();
   cx<T> w2[NA];
   if (c < nc) {
