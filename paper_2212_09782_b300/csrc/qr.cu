@@ -843,7 +843,13 @@ int side_stream(cudaStream_t main, int nev, SideStream** out) {
   QR_CUDA_TRY(cudaGetDevice(&dev));
   std::lock_guard<std::mutex> lk(g_side_mu);
   SideStream& ss = g_side[std::make_pair(dev, main)];
-  if (!ss.st) QR_CUDA_TRY(cudaStreamCreateWithFlags(&ss.st, cudaStreamNonBlocking));
+  if (!ss.st) {
+    // lowest priority: the look-ahead work yields SMs to the panel chain on the caller's
+    // stream whenever both have blocks waiting
+    int lo = 0, hi = 0;
+    QR_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+    QR_CUDA_TRY(cudaStreamCreateWithPriority(&ss.st, cudaStreamNonBlocking, lo));
+  }
   while ((int)ss.ev.size() < nev) {
     cudaEvent_t e;
     QR_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
