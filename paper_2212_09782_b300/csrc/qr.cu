@@ -589,96 +589,127 @@ __global__ void __launch_bounds__(WY_NT) k_apply_wy(cx<T>* C, long long ldc, con
   for (int i = tid; i < kb * kb; i += WY_NT) cp_async_cx<T>(Ts + i, Tt + (long long)(i / kb) * ldt + i % kb);
   cp_async_wait_all();
   __syncthreads();
-  // thread = (column c, residue of a modulo APS): NA accumulators
-  constexpr int APS = WY_NT / WY_NC;
-  const int c = tid % WY_NC, ap = tid / WY_NC;
-  constexpr int NA = WY_KB / APS;
+  // register tiles: columns c_q = lane + 32 q (q < 4), and reflectors a_p (phase 1, 3a)
+  // or rows r_p (phase 3b) = warp + 8 p; 16 independent accumulators per thread
+  const int lane = tid & 31, wg = tid >> 5;
+  constexpr int NQ = WY_NC / 32, NP = WY_KB / 8;
   // (1) partial V^dag C
-  if (c < nc) {
-    cx<T> acc[NA];
+  {
+    cx<T> acc[NP][NQ];
 #pragma unroll
-    for (int i = 0; i < NA; ++i) acc[i] = zero;
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) acc[p][q] = zero;
+#pragma unroll 2
     for (int r = 0; r < nr; ++r) {
-      const cx<T> x = Cs[r * nc + c];
+      cx<T> x[NQ], v[NP];
 #pragma unroll
-      for (int i = 0; i < NA; ++i) {
-        const int a = ap + APS * i;
-        if (a < kb) cfma<T>(acc[i], cconj<T>(Vs[r * kb + a]), x);
+      for (int q = 0; q < NQ; ++q) x[q] = (lane + 32 * q < nc) ? Cs[r * nc + lane + 32 * q] : zero;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) v[p] = (wg + 8 * p < kb) ? cconj<T>(Vs[r * kb + wg + 8 * p]) : zero;
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) cfma<T>(acc[p][q], v[p], x[q]);
+    }
+    // through shared memory (Ws is free until phase 3) so that the CTA's partial block,
+    // stored [CTA][column][a], is written with coalesced stores
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int aa = wg + 8 * p, c = lane + 32 * q;
+        if (aa < kb && c < nc) Ws[c * kb + aa] = acc[p][q];
       }
-    }
-#pragma unroll
-    for (int i = 0; i < NA; ++i) {
-      const int a = ap + APS * i;
-      if (a < kb) part[((size_t)b * kb + a) * nc + c] = acc[i];
-    }
+    __syncthreads();
+    for (int i = tid; i < kb * nc; i += WY_NT) part[(size_t)b * kb * nc + i] = Ws[i];
   }
   if (!grid_barrier(bar, G, err)) return;
-  // (2) sum of the partials: a CTA per group of 32 consecutive outputs; its warps split
-  //     the G partials (independent loads in flight), then combine in shared memory
+  // (2) one CTA per column c: lane = reflector index a, the warps split the G partials
+  //     of W[:, c] = V^dag C[:, c] (stored [CTA][column][a], so a warp reads 32 consecutive
+  //     values); warp 0 sums them and applies T^dag (W[k] by shuffle), so W2 = T^dag W is
+  //     formed once
   {
     __shared__ cx<T> red[WY_NT / 32][32];
-    const int warp = tid >> 5, lane = tid & 31;
-    const int nout = kb * nc, ngroups = (nout + 31) / 32;
-    for (int grp = b; grp < ngroups; grp += (int)G) {
-      const int o = grp * 32 + lane;
+    const int warp = tid >> 5, lane2 = tid & 31;
+    constexpr unsigned WS = WY_NT / 32;
+    for (int c = b; c < nc; c += (int)G) {
       cx<T> s0 = zero, s1 = zero, s2 = zero, s3 = zero;
-      if (o < nout) {
+      if (lane2 < kb) {
+        const size_t off = (size_t)c * kb + lane2, stride = (size_t)kb * nc;
         unsigned z = warp;
-        constexpr unsigned WS = WY_NT / 32;
         for (; z + 3 * WS < G; z += 4 * WS) {
-          s0 = cadd<T>(s0, part[(size_t)z * nout + o]);
-          s1 = cadd<T>(s1, part[(size_t)(z + WS) * nout + o]);
-          s2 = cadd<T>(s2, part[(size_t)(z + 2 * WS) * nout + o]);
-          s3 = cadd<T>(s3, part[(size_t)(z + 3 * WS) * nout + o]);
+          s0 = cadd<T>(s0, part[z * stride + off]);
+          s1 = cadd<T>(s1, part[(z + WS) * stride + off]);
+          s2 = cadd<T>(s2, part[(z + 2 * WS) * stride + off]);
+          s3 = cadd<T>(s3, part[(z + 3 * WS) * stride + off]);
         }
-        for (; z < G; z += WS) s0 = cadd<T>(s0, part[(size_t)z * nout + o]);
+        for (; z < G; z += WS) s0 = cadd<T>(s0, part[z * stride + off]);
       }
-      red[warp][lane] = cadd<T>(cadd<T>(s0, s1), cadd<T>(s2, s3));
+      red[warp][lane2] = cadd<T>(cadd<T>(s0, s1), cadd<T>(s2, s3));
       __syncthreads();
-      if (warp == 0 && o < nout) {
-        cx<T> t = red[0][lane];
-        for (int w = 1; w < WY_NT / 32; ++w) t = cadd<T>(t, red[w][lane]);
-        Wg[o] = t;
+      if (warp == 0) {
+        cx<T> wv = zero;
+        for (int w = 0; w < (int)WS; ++w) wv = cadd<T>(wv, red[w][lane2]);
+        cx<T> w2 = zero;
+        for (int k = 0; k < kb; ++k) {
+          const cx<T> wk = shfl_cx<T>(wv, k);
+          if (k <= lane2 && lane2 < kb) cfma<T>(w2, cconj<T>(Ts[k * kb + lane2]), wk);
+        }
+        if (lane2 < kb) Wg[(size_t)lane2 * nc + c] = w2;
       }
       __syncthreads();
     }
   }
   if (!grid_barrier(bar, G, err)) return;
-  // (3) W2 = T^dag W in shared memory, then C -= V W2 on the slab
+  // (3) W2 into shared memory, then C -= V W2 on the slab
   for (int i = tid; i < kb * nc; i += WY_NT) cp_async_cx<T>(Ws + i, Wg + i);
   cp_async_wait_all();
   __syncthreads();
-  cx<T> w2[NA];
-  if (c < nc) {
+  // (3b) C -= V W2 on the slab: 32-row tiles (rows r0c + warp + 8 p), then 8-row steps
+  int r0c = 0;
+  for (; r0c + 8 * NP <= nr; r0c += 8 * NP) {
+    cx<T> acc[NP][NQ];
 #pragma unroll
-    for (int i = 0; i < NA; ++i) {
-      const int a = ap + APS * i;
-      cx<T> s = zero;
-      if (a < kb)
-        for (int q = 0; q <= a; ++q) cfma<T>(s, cconj<T>(Ts[q * kb + a]), Ws[q * nc + c]);
-      w2[i] = s;
-    }
-  }
-  __syncthreads();
-  if (c < nc) {
+    for (int p = 0; p < NP; ++p)
 #pragma unroll
-    for (int i = 0; i < NA; ++i) {
-      const int a = ap + APS * i;
-      if (a < kb) Ws[a * nc + c] = w2[i];
+      for (int q = 0; q < NQ; ++q) acc[p][q] = zero;
+    for (int k = 0; k < kb; ++k) {
+      cx<T> w[NQ], v[NP];
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) w[q] = (lane + 32 * q < nc) ? Ws[k * nc + lane + 32 * q] : zero;
+#pragma unroll
+      for (int p = 0; p < NP; ++p) v[p] = Vs[(r0c + wg + 8 * p) * kb + k];
+#pragma unroll
+      for (int p = 0; p < NP; ++p)
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) cfma<T>(acc[p][q], v[p], w[q]);
     }
-  }
-  __syncthreads();
-  if (c < nc) {
-    for (int r = ap; r < nr; r += APS) {
-      cx<T> s0 = zero, s1 = zero;
-      int a = 0;
-      for (; a + 1 < kb; a += 2) {
-        cfma<T>(s0, Vs[r * kb + a], Ws[a * nc + c]);
-        cfma<T>(s1, Vs[r * kb + a + 1], Ws[(a + 1) * nc + c]);
+#pragma unroll
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int r = r0c + wg + 8 * p, c = lane + 32 * q;
+        if (c < nc) C[(long long)(r0 + r) * ldc + c] = csub<T>(Cs[r * nc + c], acc[p][q]);
       }
-      if (a < kb) cfma<T>(s0, Vs[r * kb + a], Ws[a * nc + c]);
-      const cx<T> s = cadd<T>(s0, s1);
-      C[(long long)(r0 + r) * ldc + c] = csub<T>(Cs[r * nc + c], s);
+  }
+  for (; r0c < nr; r0c += 8) {
+    const int r = r0c + wg;
+    cx<T> acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = zero;
+    if (r < nr) {
+      for (int k = 0; k < kb; ++k) {
+        const cx<T> v = Vs[r * kb + k];
+#pragma unroll
+        for (int q = 0; q < NQ; ++q)
+          if (lane + 32 * q < nc) cfma<T>(acc[q], v, Ws[k * nc + lane + 32 * q]);
+      }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int c = lane + 32 * q;
+        if (c < nc) C[(long long)(r0 + r) * ldc + c] = csub<T>(Cs[r * nc + c], acc[q]);
+      }
     }
   }
 }
