@@ -789,13 +789,14 @@ int smem_cap() {
 }
 
 // Cluster size, slab rows per CTA and panel width for a panel of mr rows: the
-// smallest power-of-two cluster giving every CTA at most ~192 slab rows, grown (then
+// smallest power-of-two cluster giving every CTA at most ~320 slab rows (a 5120-row panel
+// takes 16 CTAs, a 2048-row one 8, which leaves SMs to concurrent updates), grown (then
 // the width halved) until the panel fits in shared memory.
 template <typename T> ClusterChoice choose_cluster(int mr, int kb_want) {
   const int cmax = g_max_cluster > 0 ? g_max_cluster : 16;
   const size_t cap = (size_t)smem_cap();
   int cs = 1;
-  while (cs < cmax && (long long)cs * 192 < mr) cs *= 2;
+  while (cs < cmax && (long long)cs * 320 < mr) cs *= 2;
   for (int kb = kb_want; kb >= 1; kb /= 2) {
     for (int s = cs; s <= cmax; s *= 2) {
       const int rps = (int)ceil_div(std::max(mr - kb, 0), s);
