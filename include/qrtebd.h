@@ -211,6 +211,11 @@ int qrtebd_mps_load(const char* path, void* stream, qrtebd_mps** out);
 int qrtebd_apply_gate_layer_batched(qrtebd_mps* const* states, int nstates, int parity,
                                     const double* const* gates_host, const qrtebd_trunc* tr,
                                     double* const* eps_out);
+
+/* Number of worker streams of the batched-layer executor. Each worker holds one bond-update
+ * workspace sized for the largest bond it has run, so a caller budgeting device memory for
+ * batched layers (e.g. an admission policy) reserves this many workspaces. */
+int qrtebd_layer_workers(void);
 /* Load a site tensor / bond matrix from host complex128 data (e.g. a random
  * right-canonical state, or a state produced elsewhere). B_host: (chi_l, d, chi_r);
  * sets the bond dimensions of bonds `site` and `site+1`. xi_host: chi x chi dense, or

@@ -22,7 +22,7 @@
 namespace qrtebd {
 namespace {
 
-constexpr int kWorkers = 8;
+constexpr int kWorkers = 16;
 
 struct Worker {
   cudaStream_t st = nullptr;
@@ -128,6 +128,8 @@ void executor_forget_state(qrtebd_mps* s) {
 using namespace qrtebd;
 
 extern "C" {
+
+int qrtebd_layer_workers(void) { return kWorkers; }
 
 int qrtebd_apply_gate_layer_batched(qrtebd_mps* const* states, int nstates, int parity,
                                     const double* const* gates_host, const qrtebd_trunc* tr,

@@ -64,6 +64,7 @@ def _load():
         "qrtebd_last_error_message": (C.c_char_p, []),
         "qrtebd_version": (C.c_char_p, []),
         "qrtebd_launch_count": (C.c_longlong, []),
+        "qrtebd_layer_workers": (I, []),
         "qrtebd_householder_qr": (I, [I, I, I, P, LL, P, LL, P, S, P]),
         "qrtebd_qr_workspace_size": (S, [I, I, I]),
         "qrtebd_profile_enable": (I, [I]),
@@ -412,6 +413,11 @@ class MPS:
         obj.stream = stream
         obj.L, obj.d, obj.infinite = L, d, bool(inf)
         return obj
+
+
+def layer_workers():
+    """Worker streams (and bond-update workspaces) of the batched-layer executor."""
+    return int(_lib.qrtebd_layer_workers())
 
 
 def clock_layer_gates(L, d, g, tau, infinite=False):

@@ -72,11 +72,12 @@ def workspace_bytes(req, precision):
 
 class QuenchServer:
     def __init__(self, precision="c64_3xtf32", max_active=32, reserve_bytes=2 << 30,
-                 mem_free=None, mem_total=None, workers=8):
+                 mem_free=None, mem_total=None, workers=None):
         self.precision = precision
         self.max_active = max_active
         self.reserve = reserve_bytes
-        self.workers = workers
+        # one bond-update workspace per executor worker stream
+        self.workers = workers if workers is not None else L.layer_workers()
         self._mem_free = mem_free
         self._mem_total = mem_total
         self.pending = []

@@ -41,3 +41,13 @@ def test_poisson_mix_is_seeded():
     gaps = np.diff([0.0] + [r.arrival for r in a])
     assert np.all(gaps > 0)
     assert {r.L for r in a} <= {32, 64, 128} and {r.d for r in a} <= {3, 4, 5}
+
+
+def test_admission_reserves_one_workspace_per_executor_worker():
+    from paper_2212_09782_b300 import lib as L
+    nw = L.layer_workers()
+    assert nw >= 1
+    srv = serve.QuenchServer(mem_free=lambda: 1 << 40, mem_total=lambda: 1 << 40, reserve_bytes=0)
+    assert srv.workers == nw
+    req = serve.Request(0, 32, 3, 128, 1.0, 2)
+    assert srv.footprint(req) == serve.state_bytes(req, srv.precision) + nw * serve.workspace_bytes(req, srv.precision)
