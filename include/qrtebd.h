@@ -71,6 +71,10 @@ typedef struct qrtebd_trunc {
                        projections of Sec. II, but with a floor of about the storage precision,
                        ~1e-7 in complex64); 1: eps from the explicit residual
                        ||theta~ - approx||^2 (one more contraction; the distance of Sec. IV) */
+  double eps_target;  /* CBE: > 0 keeps the fewest Schmidt values whose discarded weight,
+                         sum_{k > chi~} S_k^2 / sum_k S_k^2, is at most eps_target (within the
+                         chi_max and svd_min cut, before the tie rule); 0: off. Plain: ignored
+                         (its bond dimension is eta). */
 } qrtebd_trunc;
 /* eta policy (Sec. II last paragraph, Sec. III):
  *   PLAIN: eta = min(chi_max, d chi_l, d chi_r); initial guess Y0 = B^n if

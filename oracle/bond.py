@@ -55,21 +55,31 @@ def choose_eta(scheme, chiL, chiM, chiR, d, chi_max, dchi_min=100, dchi_frac=0.1
     return min(chiM + dchi, cap)
 
 
-def cbe_cut(S, chi_max, svd_min=1e-14, tie_tol=1e-10):
-    """Number of Schmidt values kept after CBE (Sec. III (v), Fig. 4 caption)."""
+def cbe_cut(S, chi_max, svd_min=1e-14, tie_tol=1e-10, eps_target=0.0):
+    """Number of Schmidt values kept after CBE (Sec. III (v), Fig. 4 caption).
+
+    eps_target > 0 further keeps only the fewest values whose discarded weight
+    sum_{k >= c} s_k^2 (s = S / ||S||) is at most eps_target; the tie rule comes last."""
     nrm = np.sqrt(np.sum(S ** 2))
     if nrm == 0.0:
         return 1
     s = S / nrm
     c = int(np.sum(s >= svd_min))
     c = max(1, min(c, chi_max))
+    if eps_target > 0:
+        ce = len(s)
+        tail = 0.0
+        while ce > 1 and tail + s[ce - 1] ** 2 <= eps_target:
+            tail += s[ce - 1] ** 2
+            ce -= 1
+        c = min(c, ce)
     while c < len(s) and c > 1 and s[c - 1] - s[c] <= tie_tol * s[0]:
         c -= 1
     return c
 
 
 def qr_update(Xi, Bm, Bn, U, *, scheme="plain", chi_max, eta=None, dchi_min=100,
-              dchi_frac=0.1, svd_min=1e-14, tie_tol=1e-10, theta=None, Y0=None):
+              dchi_frac=0.1, svd_min=1e-14, tie_tol=1e-10, eps_target=0.0, theta=None, Y0=None):
     """One QR-TEBD bond update.
 
     theta, if given, is theta' = B^m B^n of shape (chi_L, d, d, chi_R) (then Bm is
@@ -127,7 +137,7 @@ def qr_update(Xi, Bm, Bn, U, *, scheme="plain", chi_max, eta=None, dchi_min=100,
         W = W[:, ::-1]
         S = np.sqrt(np.maximum(w, 0.0))
         V = W.conj().T
-        c = cbe_cut(S, chi_max, svd_min, tie_tol)
+        c = cbe_cut(S, chi_max, svd_min, tie_tol, eps_target)
         # (v) B~^n = P V Q^[n], Xi~ = P S P
         Bn_new = V[:c] @ Qn
         Xi_new = np.diag(S[:c]).astype(np.complex128)

@@ -182,7 +182,7 @@ int launch_gate(const cx<T>* th, cx<T>* out, const double2* U, int chiL, int d, 
 // decides chi~ (Fig. 4 caption: drop S / ||S|| < svd_min, keep <= chi_max, never
 // split a multiplet closer than tie_tol * S_1), kept = sum_{k < chi~} S_k^2.
 __global__ void k_cbe_cut(const double* w, int n, int chi_max, double svd_min, double tie_tol,
-                          double* S, double* kept, int* chi_out) {
+                          double eps_target, double* S, double* kept, int* chi_out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double tot = 0;
   for (int k = 0; k < n; ++k) { double s = w[k] > 0 ? sqrt(w[k]) : 0.0; S[k] = s; tot += s * s; }
@@ -191,6 +191,13 @@ __global__ void k_cbe_cut(const double* w, int n, int chi_max, double svd_min, d
   if (nrm > 0) { for (int k = 0; k < n; ++k) if (S[k] / nrm >= svd_min) ++c; }
   if (c > chi_max) c = chi_max;
   if (c < 1) c = 1;
+  if (eps_target > 0 && tot > 0) {
+    // fewest values whose discarded weight (relative to the total) is <= eps_target
+    double tail = 0;
+    int ce = n;
+    while (ce > 1 && tail + S[ce - 1] * S[ce - 1] <= eps_target * tot) { tail += S[ce - 1] * S[ce - 1]; --ce; }
+    if (ce < c) c = ce;
+  }
   if (nrm > 0) {
     while (c < n && c > 1 && (S[c - 1] - S[c]) / nrm <= tie_tol * (S[0] / nrm)) --c;
   }
@@ -425,7 +432,7 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
     // Vh now holds M; eig destroys its input -> copy into M and decompose
     QR_CUDA_TRY(cudaMemcpyAsync(M, Vh, ee * sizeof(double2), cudaMemcpyDeviceToDevice, st));
     QR_TRY(herm_eig(M, eta, w, Vh, eig_scr, eig_elems, st, err));
-    k_cbe_cut<<<1, 1, 0, st>>>(w, eta, tr->chi_max, tr->svd_min, tr->tie_tol, Sv, scal + 1,
+    k_cbe_cut<<<1, 1, 0, st>>>(w, eta, tr->chi_max, tr->svd_min, tr->tie_tol, tr->eps_target, Sv, scal + 1,
                                chi_dev);
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());

@@ -153,6 +153,7 @@ int qrtebd_trunc_default(qrtebd_trunc* tr, int scheme, int chi_max) {
   tr->svd_min = 1e-14;
   tr->tie_tol = 1e-10;
   tr->eps_explicit = 0;
+  tr->eps_target = 0.0;
   return QRTEBD_OK;
 }
 

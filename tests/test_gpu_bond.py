@@ -100,6 +100,31 @@ def test_cbe(prec, dims):
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64_3xtf32"])
+def test_cbe_eps_target(prec):
+    # the cut at a target truncation error: the fewest Schmidt values whose discarded
+    # weight is at most eps_target; the target is placed mid-way between two tail sums
+    dims = (20, 4, 24, 20)
+    bd = _case(dims, seed=777, xi="diag", prec=prec)
+    kw = dict(dchi_min=4, dchi_frac=0.1)
+    base = bond.qr_update(bd["Xi"], bd["Bm"], bd["Bn"], bd["U"], scheme="cbe", chi_max=60, **kw)
+    S = base["S"]
+    w = S ** 2 / np.sum(S ** 2)
+    tails = np.cumsum(w[::-1])[::-1]          # tails[c] = weight discarded when keeping c
+    c_want = max(2, len(S) // 3)
+    eps_target = float(np.sqrt(tails[c_want] * tails[c_want - 1]))
+    orc = bond.qr_update(bd["Xi"], bd["Bm"], bd["Bn"], bd["U"], scheme="cbe", chi_max=60,
+                         eps_target=eps_target, **kw)
+    assert orc["chi_new"] == c_want
+    from paper_2212_09782_b300 import lib as L
+    t = L.trunc_default(L.CBE, 60, dchi_min=4, dchi_frac=0.1, eps_target=eps_target)
+    gpu = run_gpu(prec, bd["Xi"], bd["Bm"], bd["Bn"], bd["U"], t, xi_kind=2)
+    assert gpu["chi_new"] == orc["chi_new"] == c_want
+    k = S >= 1e-6 * S[0]
+    assert np.allclose(gpu["S"][: len(S)][k], S[k], rtol=TOL[prec] * 10, atol=0)
+    compare(gpu, orc, TOL[prec] * 10 if prec != "c128" else TOL[prec])
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64_3xtf32"])
 def test_exact_when_eta_covers_rank(prec):
     # Sec. II / III: eta >= rank theta~ reproduces theta~: eps ~ 0, Xi B~^m B~^n = theta~
     r = W.rng(5)

@@ -188,6 +188,28 @@ def test_cbe_schmidt_values_are_singular_values_of_L(seed):
     assert np.allclose(out["Xi_new"], np.diag(np.diag(out["Xi_new"])))
 
 
+def test_cbe_cut_eps_target():
+    # s^2 = (16, 4, 1, 1/4, 1/16) / 21.3125: dropping the last value discards 0.00293 of the
+    # weight, the last two 0.0147, the last three 0.0616
+    S = np.array([4.0, 2.0, 1.0, 0.5, 0.25])
+    assert bond.cbe_cut(S, chi_max=10) == 5
+    assert bond.cbe_cut(S, chi_max=10, eps_target=0.01) == 4
+    assert bond.cbe_cut(S, chi_max=10, eps_target=0.02) == 3
+    assert bond.cbe_cut(S, chi_max=10, eps_target=0.1) == 2
+    assert bond.cbe_cut(S, chi_max=2, eps_target=0.01) == 2      # chi_max still binds
+    assert bond.cbe_cut(S, chi_max=10, eps_target=0.9) == 1      # at least one value kept
+    # the rule: discarded weight <= eps_target, and one more value would exceed it
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        T = np.sort(rng.exponential(size=30))[::-1]
+        eps = float(rng.uniform(1e-4, 0.2))
+        c = bond.cbe_cut(T, chi_max=100, svd_min=0.0, eps_target=eps)
+        w = T ** 2 / np.sum(T ** 2)
+        assert w[c:].sum() <= eps + 1e-15
+        if c > 1:
+            assert w[c - 1:].sum() > eps
+
+
 def test_cbe_cut_rules():
     S = np.array([1.0, 0.5, 0.5 - 1e-12, 0.1, 1e-15, 0.0])
     assert bond.cbe_cut(S, chi_max=10) == 4          # 1e-15 / ||S|| < 1e-14 dropped
