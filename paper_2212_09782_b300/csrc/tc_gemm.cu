@@ -140,7 +140,9 @@ template <bool THREE>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
               const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
-              Epi epi, int Kp, int kt_per_split, float* partial, unsigned* err) {
+              Epi epi, int Kp, int kt_per_split, float* partial, int m_off, unsigned* err) {
+  // m_off: first row of this launch's tiles in A; the epilogue's rows (and epi) are
+  // relative to it
   using C = Cfg<THREE>;
   pdl_launch_dependents();
   pdl_wait();
@@ -192,10 +194,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (!mbar_wait(&empty[s], ph ^ 1u)) { ok = false; break; }
         const int kx = (kt0 + i) * BK;
         mbar_expect_tx(&full[s], C::STAGE_BYTES);
-        tma_load(stage_a_hi(s), &tA_hi, &full[s], kx, m0);
+        tma_load(stage_a_hi(s), &tA_hi, &full[s], kx, m0 + m_off);
         tma_load(stage_b_hi(s), &tB_hi, &full[s], kx, n0);
         if (THREE) {
-          tma_load(stage_a_lo(s), &tA_lo, &full[s], kx, m0);
+          tma_load(stage_a_lo(s), &tA_lo, &full[s], kx, m0 + m_off);
           tma_load(stage_b_lo(s), &tB_lo, &full[s], kx, n0);
         }
         ++issued;
@@ -514,7 +516,7 @@ void tc_carve(Arena& ar, int max_m, int max_k, int max_n, TcWorkspace& w) {
   w.b = TcSlot{};
   w.b.hi = ar.take<float>(w.b_cap);
   w.b.lo = ar.take<float>(w.b_cap);
-  w.p_cap = (size_t)1 << 22;  // 16 MB of split-K partial sums
+  w.p_cap = (size_t)1 << 23;  // 32 MB of split-K partial sums
   w.partial = ar.take<float>(w.p_cap);
   w.a_next = 0;
 }
@@ -588,47 +590,71 @@ int tc_gemm(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStream_t 
   Epi epi{g.C, g.scm, g.scn, g.alpha, g.beta, M, N};
   const int nx = (int)ceil_div(2LL * N, BN), ny = (int)ceil_div(M, BM);
   const int nk = (int)ceil_div(2LL * K, BK);
-  // split K when the tile grid leaves most SMs idle
-  int splits = 1;
+  const int nsm = 148;
+  unsigned* err = device_error_word();
+  if (three && !g_attr3) {
+    QR_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     Cfg<true>::SMEM));
+    g_attr3 = true;
+  }
+  if (!three && !g_attr1) {
+    QR_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     Cfg<false>::SMEM));
+    g_attr1 = true;
+  }
+  // one launch over tile rows [ty0, ty0 + nty) with `splits` K-splits (then their sum)
+  auto run = [&](int ty0, int nty, int splits) -> int {
+    const int per = (int)ceil_div(nk, splits);
+    splits = (int)ceil_div(nk, per);
+    const int m_off = ty0 * BM;
+    Epi e = epi;
+    e.C = epi.C + (long long)m_off * epi.scm;
+    e.M = std::min(M, (ty0 + nty) * BM) - m_off;
+    float* part = splits > 1 ? w.partial : nullptr;
+    dim3 grid((unsigned)nx, (unsigned)nty, (unsigned)splits);
+    {
+      ProfScope prof(prof_family, st, 8.0 * e.M * N * K);
+      if (three)
+        QR_CUDA_TRY(launch_pdl(k_tc_gemm<true>, grid, dim3(NTHREADS), Cfg<true>::SMEM, st, ta_hi, ta_lo,
+                               tb_hi, tb_lo, e, 2 * K, per, part, m_off, err));
+      else
+        QR_CUDA_TRY(launch_pdl(k_tc_gemm<false>, grid, dim3(NTHREADS), Cfg<false>::SMEM, st, ta_hi,
+                               ta_lo, tb_hi, tb_lo, e, 2 * K, per, part, m_off, err));
+      note_launch();
+      QR_CUDA_TRY(cudaGetLastError());
+    }
+    if (splits > 1) {
+      QR_CUDA_TRY(launch_pdl(k_splitk_sum, dim3((unsigned)ceil_div((long long)e.M * N, 256)), dim3(256),
+                             0, st, static_cast<const float*>(part), splits, e));
+      note_launch();
+      QR_CUDA_TRY(cudaGetLastError());
+    }
+    return QRTEBD_OK;
+  };
   const int tiles = nx * ny;
   if (tiles < 100 && nk >= 2 * CHUNK) {
-    splits = std::min<int>((int)ceil_div(148, tiles), nk / CHUNK);
+    // split K when the tile grid leaves most SMs idle
+    int splits = std::min<int>((int)ceil_div(nsm, tiles), nk / CHUNK);
     splits = std::min(splits, 32);
     while (splits > 1 && (size_t)splits * M * 2 * N > w.p_cap) --splits;
+    return run(0, ny, std::max(splits, 1));
   }
-  int per = (int)ceil_div(nk, splits);
-  splits = (int)ceil_div(nk, per);
-  float* part = splits > 1 ? w.partial : nullptr;
-  dim3 grid((unsigned)nx, (unsigned)ny, (unsigned)splits);
-  unsigned* err = device_error_word();
-  {
-    ProfScope prof(prof_family, st, 8.0 * M * N * K);
-    if (three) {
-      if (!g_attr3) {
-        QR_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg<true>::SMEM));
-        g_attr3 = true;
+  if (tiles > nsm && nk >= 4 * CHUNK) {
+    // a last wave of a few tiles would leave most SMs idle for a whole tile's time: run the
+    // full waves, then the remaining tile rows with their K split over the idle SMs
+    const int tail_rows = (int)ceil_div(tiles % nsm, nx);
+    const int tail_tiles = tail_rows * nx;
+    if (tail_rows > 0 && tail_rows < ny && tail_tiles <= nsm / 3) {
+      int ts = std::min(nsm / tail_tiles, nk / CHUNK);
+      ts = std::min(ts, 32);
+      while (ts > 1 && (size_t)ts * tail_rows * BM * 2 * N > w.p_cap) --ts;
+      if (ts >= 2) {
+        QR_TRY(run(0, ny - tail_rows, 1));
+        return run(ny - tail_rows, tail_rows, ts);
       }
-      QR_CUDA_TRY(launch_pdl(k_tc_gemm<true>, grid, dim3(NTHREADS), Cfg<true>::SMEM, st, ta_hi, ta_lo,
-                             tb_hi, tb_lo, epi, 2 * K, per, part, err));
-    } else {
-      if (!g_attr1) {
-        QR_CUDA_TRY(cudaFuncSetAttribute(k_tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         Cfg<false>::SMEM));
-        g_attr1 = true;
-      }
-      QR_CUDA_TRY(launch_pdl(k_tc_gemm<false>, grid, dim3(NTHREADS), Cfg<false>::SMEM, st, ta_hi,
-                             ta_lo, tb_hi, tb_lo, epi, 2 * K, per, part, err));
     }
-    note_launch();
-    QR_CUDA_TRY(cudaGetLastError());
   }
-  if (splits > 1) {
-    QR_CUDA_TRY(launch_pdl(k_splitk_sum, dim3((unsigned)ceil_div((long long)M * N, 256)), dim3(256), 0,
-                           st, static_cast<const float*>(part), splits, epi));
-    note_launch();
-    QR_CUDA_TRY(cudaGetLastError());
-  }
+  return run(0, ny, 1);
   return QRTEBD_OK;
 }
 

@@ -50,3 +50,29 @@ def test_zgemm(prec, m, n, k, ops):
     scale = np.abs(alpha) * np.sqrt(k) + np.abs(beta)
     err = np.abs(got - ref).max() / scale
     assert err < tol(prec, k), err
+
+
+@pytest.mark.parametrize("prec", ["c64_3xtf32", "c64_tf32"])
+@pytest.mark.parametrize("ops", ["nn", "ct"])
+def test_zgemm_tail_wave_split(prec, ops):
+    # 38 x 8 = 304 output tiles: two full waves on 148 SMs and one tile row left over, which
+    # runs with its K split across the idle SMs (then summed); beta != 0 exercises the sum
+    import torch
+    from paper_2212_09782_b300 import lib as L
+    m, n, k = 4864, 1024, 512
+    r = W.rng(4242)
+    ta, ca = ops[0] in "tc", ops[0] == "c"
+    A = W.complex_gaussian(r, (k, m) if ta else (m, k)).astype(np.complex64).astype(np.complex128)
+    B = W.complex_gaussian(r, (k, n)).astype(np.complex64).astype(np.complex128)
+    C0 = W.complex_gaussian(r, (m, n)).astype(np.complex64).astype(np.complex128)
+    opA = A.T if ta else A
+    opA = opA.conj() if ca else opA
+    ref = 0.5 * (opA @ B) + (0.25 - 0.5j) * C0
+    Cd = torch.from_numpy(C0).to(device="cuda", dtype=torch.complex64)
+    out = L.zgemm(prec, torch.from_numpy(A).to(device="cuda", dtype=torch.complex64),
+                  torch.from_numpy(B).to(device="cuda", dtype=torch.complex64), conj_a=ca,
+                  trans_a=ta, alpha=0.5, beta=0.25 - 0.5j, C_out=Cd)
+    L.stream_check()
+    got = out.cpu().numpy().astype(np.complex128)
+    scale = np.abs(opA).max() * np.abs(B).max() * k
+    assert np.abs(got - ref).max() / scale < (tol(prec, k) if prec != "c64_tf32" else 4e-3)
