@@ -919,7 +919,6 @@ template <typename T> void qr_carve(Arena& ar, int m, int n, QrScratch<T>& s) {
   s.Tf = ar.take<cx<T>>((size_t)(n + nbo) * nbo);
   s.W = ar.take<cx<T>>((size_t)nbo * n);
   s.W2 = ar.take<cx<T>>((size_t)nbo * n);
-  s.Ws = ar.take<cx<T>>((size_t)nbo * n);
   s.W2s = ar.take<cx<T>>((size_t)nbo * n);
   s.G = ar.take<cx<T>>((size_t)nbo * nbo);
   s.tmp = ar.take<cx<T>>((size_t)nbo * KBMAX);
@@ -1019,11 +1018,9 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
     // next block's panels.
     const int nc = n - ko - kbo;
     if (nc > 0) {
-      auto update = [&](int c0, int cw, cudaStream_t stream, cx<T>* W, cx<T>* W2,
-                        const QrGemm<T>* g) -> int {
+      auto update = [&](int c0, int cw, cudaStream_t stream, cx<T>* W2, const QrGemm<T>* g) -> int {
         cx<T>* C = A + (long long)ko * lda + ko + kbo + c0;
         // W2 = T^dag V^dag C = (V T)^dag C, then C -= V W2
-        (void)W;
         GemmArgs<T> g1{kbo, cw, mo, VTb, 1, ldv, true, C, lda, 1, false, W2, cw, 1, one, zero};
         QR_TRY(run_gemm<T>(g1, s, stream, g));
         GemmArgs<T> g3{mo, cw, kbo, Vb, ldv, 1, false, W2, cw, 1, false, C, lda, 1, mone, one};
@@ -1034,11 +1031,11 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
       // the next block's columns also carry block k-1's side-stream update: order after it
       if (ss && latest(kblk - 1) >= 0)
         QR_CUDA_TRY(cudaStreamWaitEvent(st, ss->ev[nblk + latest(kblk - 1)], 0));
-      QR_TRY(update(0, n1, st, s.W, s.W2, gm));
+      QR_TRY(update(0, n1, st, s.W2, gm));
       if (ss && nc > n1) {
         QR_CUDA_TRY(cudaEventRecord(ss->ev[kblk], st));  // V, T of this block are ready
         QR_CUDA_TRY(cudaStreamWaitEvent(ss->st, ss->ev[kblk], 0));
-        QR_TRY(update(n1, nc - n1, ss->st, s.Ws, s.W2s, side));
+        QR_TRY(update(n1, nc - n1, ss->st, s.W2s, side));
         QR_CUDA_TRY(cudaEventRecord(ss->ev[nblk + kblk], ss->st));
         rec[kblk] = 1;
       }

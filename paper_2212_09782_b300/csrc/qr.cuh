@@ -21,8 +21,7 @@ template <typename T> struct QrScratch {
   cx<T>* Tf = nullptr;     // ceil(n/nb) blocks of nb x nb triangular factors
   cx<T>* W = nullptr;      // nb x n
   cx<T>* W2 = nullptr;     // nb x n
-  cx<T>* Ws = nullptr;     // W, W2 of the look-ahead (side-stream) updates
-  cx<T>* W2s = nullptr;
+  cx<T>* W2s = nullptr;    // W2 of the look-ahead (side-stream) updates
   cx<T>* G = nullptr;      // outer-block Gram matrix V^dag V
   cx<T>* tmp = nullptr;    // T assembly scratch
   cx<T>* wy_part = nullptr;  // fused narrow update: per-CTA partials of V^dag C
