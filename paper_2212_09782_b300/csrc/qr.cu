@@ -89,9 +89,10 @@ template <> struct NAcc<float> {
   }
   __device__ __forceinline__ void add_sq(float x) { const float p = x * x; add(p, fmaf(x, x, -p)); }
   __device__ __forceinline__ void add(const NAcc& o) { add(o.hi, o.lo); }
-  __device__ __forceinline__ void shfl_sum() {
+  // sum over aligned groups of W lanes (every lane of a group ends with the group's sum)
+  template <int W = 32> __device__ __forceinline__ void shfl_sum() {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = W / 2; o > 0; o >>= 1) {
       const float h = __shfl_xor_sync(0xffffffffu, hi, o), l = __shfl_xor_sync(0xffffffffu, lo, o);
       add(h, l);
     }
@@ -103,9 +104,9 @@ template <> struct NAcc<double> {
   __device__ __forceinline__ void add(double a, double b) { v += a + b; }
   __device__ __forceinline__ void add_sq(double x) { v = fma(x, x, v); }
   __device__ __forceinline__ void add(const NAcc& o) { v += o.v; }
-  __device__ __forceinline__ void shfl_sum() {
+  template <int W = 32> __device__ __forceinline__ void shfl_sum() {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   }
   __device__ __forceinline__ double value() const { return v; }
 };
@@ -310,23 +311,29 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
       else { wpn[warp * 2 + 0] = nacc.value(); wpn[warp * 2 + 1] = 0; }
     }
     __syncthreads();
-    // ---- 3. exchange (warp 0): pivot row copy, then (norm, slots) to every rank
+    // ---- 3. exchange: every warp forms the CTA's message (the warps' partials summed)
+    //      and pushes it to its share of the ranks (r = warp, warp + NW, ...), so the
+    //      remote stores issue in parallel; warp 0 also copies the pivot row and arms
+    //      this CTA's barrier
     const int buf = jn & 1;
-    if (warp == 0) {
+    {
       cx<T> s = zero;
-#pragma unroll 4
+#pragma unroll
       for (int w = 0; w < NW; ++w) s = cadd<T>(s, wps[w * SLOTS + lane]);
       NAcc<T> n;
-      if (lane < NW) {
-        if constexpr (std::is_same<T, float>::value) n.add(wpn[lane * 4], wpn[lane * 4 + 1]);
-        else n.add(wpn[lane * 2], T(0));
+      {
+        const int w = lane & (NW - 1);  // each group of NW lanes holds every warp's partial
+        if constexpr (std::is_same<T, float>::value) n.add(wpn[w * 4], wpn[w * 4 + 1]);
+        else n.add(wpn[w * 2], T(0));
       }
-      n.shfl_sum();
+      n.template shfl_sum<NW>();
       cx<T> h;
       if constexpr (std::is_same<T, float>::value) h = mk<T>(n.hi, n.lo); else h = mk<T>(n.value(), 0);
-      pivb[buf * SLOTS + lane] = P[jn * ldp + min(lane, kb - 1)];
-      __syncwarp();
-      if (lane == 0) mbar_arm(&mb[buf], txb);  // release: the pivot copy is visible to the waiters
+      if (warp == 0) {
+        pivb[buf * SLOTS + lane] = P[jn * ldp + min(lane, kb - 1)];
+        __syncwarp();
+        if (lane == 0) mbar_arm(&mb[buf], txb);  // release: the pivot copy is visible to the waiters
+      }
       const uint32_t mine = smem_addr(recvm + (buf * 16 + rank) * L::MSG);
       const uint32_t mbl = smem_addr(&mb[buf]);
       if constexpr (std::is_same<T, float>::value) {
@@ -334,9 +341,9 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
         const cx<T> sa = shfl_cx<T>(s, (2 * lane + 30) & 31), sb = shfl_cx<T>(s, (2 * lane + 31) & 31);
         const float4 ch = lane == 0 ? make_float4(h.x, h.y, 0.f, 0.f) : make_float4(sa.x, sa.y, sb.x, sb.y);
         if (lane < 17)
-          for (int r = 0; r < CS; ++r) st_async_16(map_rank(mine + 16 * lane, r), ch, map_rank(mbl, r));
+          for (int r = warp; r < CS; r += NW) st_async_16(map_rank(mine + 16 * lane, r), ch, map_rank(mbl, r));
       } else {
-        for (int r = 0; r < CS; ++r) {
+        for (int r = warp; r < CS; r += NW) {
           const uint32_t rb = map_rank(mine, r), rm = map_rank(mbl, r);
           st_async_16(rb + 16 + 16 * lane, s, rm);
           if (lane == 0) st_async_16(rb, h, rm);
@@ -347,8 +354,8 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
       if (!mbar_wait_cl(&mb[buf], (uint32_t)((jn >> 1) & 1))) ok = false;
       const cx<T>* piv = pivb + buf * SLOTS;
       NAcc<T> ns;
-      if (lane < CS) {
-        const T* hh = reinterpret_cast<const T*>(recvm + (buf * 16 + lane) * L::MSG);
+      if ((lane & 15) < CS) {  // both half-warps hold every rank's norm partial
+        const T* hh = reinterpret_cast<const T*>(recvm + (buf * 16 + (lane & 15)) * L::MSG);
         ns.add(hh[0], hh[1]);
       }
       cx<T> S0 = zero, S1 = zero;
@@ -364,7 +371,7 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
       const cx<T> S = cadd<T>(S0, S1);
       const cx<T> pc = piv[min(lane, kb - 1)];
       const cx<T> alpha = piv[jn];
-      ns.shfl_sum();
+      ns.template shfl_sum<16>();
       T beta, tr, ti, sr, si;
       reflector(ns.value(), alpha.x, alpha.y, beta, tr, ti, sr, si);
       if (lane == 0 && rank == 0 && !(isfinite(beta) && isfinite(sr) && isfinite(si)))
@@ -391,38 +398,34 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
   if (!ok && tid == 0) atomicOr(a.err, DEVERR_TIMEOUT);
   __syncthreads();
 
-  if (rank == 0) {
-    // compact-WY T by recursive doubling: for adjacent blocks 1, 2 with factors T1, T2,
-    // T12 = -T1 G12 T2, where G12 = V1^dag V2 is held in the strict upper part of Ts
-    for (int i = tid; i < kb; i += NT) Ts[i * (KBMAX + 1) + i] = taus[i];
-    __syncthreads();
-    cx<T>* X = reinterpret_cast<cx<T>*>(recvm);  // free after the last exchange
-    for (int b = 1; b < kb; b *= 2) {
-      const int nm = (kb - b + 2 * b - 1) / (2 * b);   // merges with a non-empty block 2
-      for (int idx = tid; idx < nm * b * b; idx += NT) {
-        const int m = idx / (b * b), r = idx % (b * b), aa = r / b, jj = r % b;
-        const int s0 = m * 2 * b, j = s0 + b + jj;
-        if (j < kb) {
-          cx<T> acc = zero;
-          for (int k = s0 + b; k <= j; ++k) cfma<T>(acc, Ts[(s0 + aa) * (KBMAX + 1) + k], Ts[k * (KBMAX + 1) + j]);
-          X[idx] = acc;
+  if (rank == CS - 1) {
+    // compact-WY T (the last rank, whose slab is the shortest): with U the strict upper
+    // part of V^dag V (held in Ts), T^{-1} = diag(1/tau) + U, so column j of T solves
+    // t_i = tau_i (delta_ij - sum_{k > i} U_ik t_k), i = j, j-1, ..., 0; this form also
+    // covers tau_i = 0 (H_i = I, row i of T zero). One warp per KBMAX / NW columns,
+    // lane = row; each step finalises t_k on lane k and broadcasts it.
+    constexpr int CPW = KBMAX / NW;
+    static_assert(KBMAX % NW == 0, "columns per warp");
+    cx<T> acc[CPW], t[CPW];
+#pragma unroll
+    for (int c = 0; c < CPW; ++c) { acc[c] = zero; t[c] = zero; }
+    const cx<T> tau_l = lane < kb ? taus[lane] : zero;
+    for (int k = kb - 1; k >= 0; --k) {
+      const cx<T> uk = lane < k ? Ts[lane * (KBMAX + 1) + k] : zero;
+#pragma unroll
+      for (int c = 0; c < CPW; ++c) {
+        const int j = warp + c * NW;
+        if (k <= j) {  // warp-uniform
+          if (lane == k) t[c] = cmul<T>(tau_l, csub<T>(mk<T>(k == j ? T(1) : T(0), T(0)), acc[c]));
+          const cx<T> tk = shfl_cx<T>(t[c], k);
+          cfma<T>(acc[c], uk, tk);  // uk = 0 on lanes >= k
         }
       }
-      __syncthreads();
-      for (int idx = tid; idx < nm * b * b; idx += NT) {
-        const int m = idx / (b * b), r = idx % (b * b), ii = r / b, jj = r % b;
-        const int s0 = m * 2 * b, j = s0 + b + jj, i = s0 + ii;
-        if (j < kb) {
-          cx<T> acc = zero;
-          for (int aa = ii; aa < b; ++aa) cfma<T>(acc, Ts[i * (KBMAX + 1) + s0 + aa], X[m * b * b + aa * b + jj]);
-          Ts[i * (KBMAX + 1) + j] = mk<T>(-acc.x, -acc.y);
-        }
-      }
-      __syncthreads();
     }
-    for (int idx = tid; idx < kb * kb; idx += NT) {
-      const int i = idx / kb, jj = idx % kb;
-      a.Tf[i * a.ldt + jj] = (jj >= i) ? Ts[i * (KBMAX + 1) + jj] : zero;
+#pragma unroll
+    for (int c = 0; c < CPW; ++c) {
+      const int j = warp + c * NW;
+      if (j < kb && lane < kb) a.Tf[lane * a.ldt + j] = t[c];  // t = 0 below the diagonal
     }
     if (tid < kb) a.tau[k0 + tid] = taus[tid];
   }
@@ -431,12 +434,20 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
   if (lane < kb) {
     const cx<T> sc = scl[lane], bc = bet[lane];
     const int pstart = (rank == 0) ? p0 : max(p0, kb);
-    for (int p = pstart; p < p1; ++p) {
+    auto put = [&](int p, cx<T> pv) {
       const int g = grow(p);
-      const cx<T> pv = P[p * ldp + lane];
       a.V[(k0 + g) * a.ldv + k0 + lane] = (g == lane) ? mk<T>(1, 0) : (g > lane ? cmul<T>(sc, pv) : zero);
       a.A[(k0 + g) * a.lda + k0 + lane] = (lane > g) ? pv : (lane == g ? bc : zero);
+    };
+    int p = pstart;
+    for (; p + 3 < p1; p += 4) {  // four rows' loads ahead of their stores
+      cx<T> pv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pv[u] = P[(p + u) * ldp + lane];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) put(p + u, pv[u]);
     }
+    for (; p < p1; ++p) put(p, P[p * ldp + lane]);
   }
   cl.sync();
 }
