@@ -75,6 +75,12 @@ typedef struct qrtebd_trunc {
                          sum_{k > chi~} S_k^2 / sum_k S_k^2, is at most eps_target (within the
                          chi_max and svd_min cut, before the tie rule); 0: off. Plain: ignored
                          (its bond dimension is eta). */
+  int reorth;         /* one re-orthogonalisation pass of the right isometry after the LQ
+                         (both schemes): D = Q^dag Q - 1, Q <- Q (1 - D/2), contractions in
+                         3xTF32 with FP32 accumulation (measured at chi = 130, d = 4:
+                         max |B B^dag - 1| 9e-4 -> 1e-6 after 1xTF32; after 3xTF32 it is
+                         already ~6e-7, the level the pass's Gram matrix resolves).
+                         -1 (default): on for QRTEBD_C64_TF32 only; 0: off; 1: on. */
 } qrtebd_trunc;
 /* eta policy (Sec. II last paragraph, Sec. III):
  *   PLAIN: eta = min(chi_max, d chi_l, d chi_r); initial guess Y0 = B^n if

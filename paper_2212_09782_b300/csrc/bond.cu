@@ -216,6 +216,13 @@ __global__ void k_diag_xi(const double* S, int c, const double* scal, cx<T>* xi)
   xi[idx] = mk<T>(i == j ? (T)(S[i] * scal[0]) : T(0), 0);
 }
 
+// D = v * identity (n x n)
+template <typename T> __global__ void k_scaled_eye(cx<T>* D, int n, T v) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  D[idx] = mk<T>(idx / n == idx % n ? v : T(0), T(0));
+}
+
 template <typename T> __global__ void k_to_c128(const cx<T>* in, double2* out, long long n) {
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < n) out[i] = make_double2((double)in[i].x, (double)in[i].y);
@@ -310,6 +317,12 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
     chi_dev = ar.take<int>(4);
   }
   const bool eps_explicit = tr->eps_explicit != 0;
+  // one re-orthogonalisation pass of Qz (auto: complex64 with 1xTF32 contractions, whose
+  // QR leaves the isometry at the TF32 level; after 3xTF32 it is already at the FP32 floor
+  // that the pass's own Gram matrix resolves)
+  const bool reorth = tr->reorth > 0 || (tr->reorth < 0 && io->precision == QRTEBD_C64_TF32);
+  cx<T>* Dm = reorth ? ar.take<cx<T>>((size_t)eta * eta) : nullptr;
+  cx<T>* Qr = reorth ? ar.take<cx<T>>((size_t)nR * eta) : nullptr;
   cx<T>* Rbuf = eps_explicit ? ar.take<cx<T>>((size_t)mL * nR) : nullptr;
   cx<T>* Zc = (eps_explicit && !cbe) ? ar.take<cx<T>>((size_t)nR * eta) : nullptr;
   cx<T>* LV = (eps_explicit && cbe) ? ar.take<cx<T>>((size_t)eta * eta) : nullptr;
@@ -388,6 +401,28 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
   }
   if (Zc) QR_CUDA_TRY(cudaMemcpyAsync(Zc, Z, (size_t)nR * eta * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st));
   QR_TRY(householder_qr<T>(Z, eta, (int)nR, eta, Qz, eta, qs, st, err, &qg, &qg_side));
+
+  if (reorth) {
+    // One re-orthogonalisation pass of the right isometry (precision pattern (1)): with
+    // D = Qz^dag Qz - 1, Qz <- Qz (1 - D/2), the first-order polar (Newton-Schulz) step,
+    // which leaves ||Qz^dag Qz - 1|| at O(||D||^2) plus the storage rounding. Both
+    // contractions run in 3xTF32 with FP32 accumulation whatever the precision, so that
+    // D is resolved well below the TF32 rounding it corrects; D is formed in the epilogue
+    // (beta = 1 onto -1) and the update is added onto a copy of Qz, so neither result is
+    // swamped by the O(1) parts.
+    const GemmRunner<T> runner3{use_tc ? (int)QRTEBD_C64_3XTF32 : io->precision, runner.tc,
+                                runner.simt_scratch, runner.simt_scratch_elems};
+    k_scaled_eye<T><<<(unsigned)ceil_div((long long)eta * eta, 256), 256, 0, st>>>(Dm, eta, T(-1));
+    note_launch();
+    QR_CUDA_TRY(cudaGetLastError());
+    GemmArgs<T> gd{eta, eta, (int)nR, Qz, 1, eta, true, Qz, eta, 1, false, Dm, eta, 1, one, one};
+    QR_TRY(runner3.run(gd, st, true));
+    QR_CUDA_TRY(cudaMemcpyAsync(Qr, Qz, (size_t)nR * eta * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st));
+    GemmArgs<T> gu{(int)nR, eta, eta, Qz, eta, 1, false, Dm, eta, 1, false, Qr, eta, 1,
+                   mk<T>(-0.5, 0), one};
+    QR_TRY(runner3.run(gu, st, true));
+    std::swap(Qz, Qr);
+  }
 
   cx<T>* bn_out = static_cast<cx<T>*>(io->bn_out);
   cx<T>* xi_out = static_cast<cx<T>*>(io->xi_out);

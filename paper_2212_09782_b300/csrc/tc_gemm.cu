@@ -518,7 +518,6 @@ void tc_carve(Arena& ar, int max_m, int max_k, int max_n, TcWorkspace& w) {
   w.b.lo = ar.take<float>(w.b_cap);
   w.p_cap = (size_t)1 << 23;  // 32 MB of split-K partial sums
   w.partial = ar.take<float>(w.p_cap);
-  w.a_next = 0;
 }
 
 void tc_invalidate(TcWorkspace& w) {
@@ -552,19 +551,18 @@ int tc_gemm(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStream_t 
     return gemm_simt<float>(g0, st, nullptr, 0, prof_family == PROF_TC_GEMM ? PROF_SIMT_GEMM : prof_family);
   QR_TRY(get_encode());
 
-  // ---- A' (cached per source/op within one bond update) and B'^T, in one launch
+  // ---- A' and B'^T, in one launch. A' of an operand marked for reuse lives in slot 0,
+  // which no other operand overwrites, so it survives the GEMMs in between (the QR's);
+  // every other A' goes to slot 1
   TcSlot* sa = nullptr;
-  for (int i = 0; i < 2 && cacheable; ++i) {
-    TcSlot& s = w.a[i];
+  if (cacheable) {
+    TcSlot& s = w.a[0];
     if (s.valid && s.src == g.A && s.s0 == g.sam && s.s1 == g.sak && s.rows == M && s.cols == K &&
         s.conj == g.conj_a && s.three == three && s.ld == ld)
       sa = &s;
   }
   const bool need_a = (sa == nullptr);
-  if (need_a) {
-    sa = &w.a[w.a_next];
-    w.a_next ^= 1;
-  }
+  if (need_a) sa = &w.a[cacheable ? 0 : 1];
   {
     PrepJob ja{g.A, g.sam, g.sak, g.conj_a ? 1 : 0, M, K, sa->hi, sa->lo, ld,
                need_a ? (int)ceil_div(K, 32) : 0, need_a ? (int)ceil_div(M, 32) : 0};

@@ -24,12 +24,11 @@ struct TcSlot {
 };
 
 struct TcWorkspace {
-  TcSlot a[2];
+  TcSlot a[2];  // a[0]: an operand marked for reuse; a[1]: every other A'
   TcSlot b;
   size_t a_cap = 0, b_cap = 0;  // floats per hi (or lo) array
   float* partial = nullptr;     // split-K partial sums
   size_t p_cap = 0;             // floats
-  int a_next = 0;
 };
 
 // Carve operand buffers able to hold A' for max_m x max_k and B'^T for max_n x max_k.

@@ -41,6 +41,26 @@ def test_trunc_defaults(L):
     t = L.trunc_default(L.CBE, 1024)
     assert (t.scheme, t.chi_max, t.eta, t.dchi_min) == (L.CBE, 1024, 0, 100)
     assert t.dchi_frac == 0.1 and t.svd_min == 1e-14
+    assert t.eps_target == 0.0 and t.reorth == -1   # re-orthogonalisation: per precision
+
+
+def test_reorth_pass_workspace(L):
+    # the pass takes D (eta x eta) and a second isometry buffer (d chi_r x eta): by default
+    # on the 1xTF32 precision only, and nothing when it is off
+    args = (1024, 5, 1024, 1024)
+    for prec, auto_on in ((L.C64_TF32, True), (L.C64_3XTF32, False)):
+        auto = L.bond_workspace_size(prec, *args, L.trunc_default(L.PLAIN, 1024), xi_kind=0,
+                                     theta_given=True)
+        on = L.bond_workspace_size(prec, *args, L.trunc_default(L.PLAIN, 1024, reorth=1),
+                                   xi_kind=0, theta_given=True)
+        off = L.bond_workspace_size(prec, *args, L.trunc_default(L.PLAIN, 1024, reorth=0),
+                                    xi_kind=0, theta_given=True)
+        assert on - off >= (1024 * 1024 + 5120 * 1024) * 8
+        assert auto == (on if auto_on else off)
+    c128 = L.trunc_default(L.PLAIN, 1024)
+    assert (L.bond_workspace_size(L.C128, *args, c128, xi_kind=0, theta_given=True) ==
+            L.bond_workspace_size(L.C128, *args, L.trunc_default(L.PLAIN, 1024, reorth=0),
+                                  xi_kind=0, theta_given=True))
 
 
 def test_workspace_size_query_needs_no_gpu(L):
