@@ -249,6 +249,9 @@ def run_ours(args):
     tr = L.trunc_default(L.PLAIN, chi)
     up = L.BondUpdater(prec, chi, d, chi, chi, tr, xi_kind=0, theta_given=True)
     stream = torch.cuda.current_stream()
+    tune = None
+    if args.autotune:  # tile shapes of this update's tensor-core products, before any timing
+        tune = autotune_shapes(L, prec, [(chi, d, chi, chi)], tr, xi_kind=0, theta_given=True)
 
     def barrier():
         torch.cuda.synchronize()
@@ -398,11 +401,25 @@ def run_ours(args):
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "kernel_breakdown": breakdown, "dominant_family": PROF_NAMES[dom],
         "roofline_by_family": roofs, "profiled_ms_per_step": prof_step_ms, "clocks": clk,
+        "autotune": tune,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def autotune_shapes(L, prec, shapes, tr, xi_kind, theta_given):
+    """Run the library's autotuner on each bond shape (chi_l, d, chi_m, chi_r); summary."""
+    t0 = time.perf_counter()
+    n = 0
+    for (cl, dd, cm, cr) in shapes:
+        n += L.autotune_bond(prec, cl, dd, cm, cr, tr, xi_kind=xi_kind, theta_given=theta_given)
+    ents = L.autotune_entries()
+    return {"bond_shapes": len(shapes), "products_tuned": n, "seconds": round(time.perf_counter() - t0, 2),
+            "changed_from_heuristic": sum(1 for e in ents if tuple(e["config"]) != (256, 0, 1)),
+            "sum_ms_tuned": round(sum(e["ms_tuned"] for e in ents), 4),
+            "sum_ms_heuristic": round(sum(e["ms_default"] for e in ents), 4)}
 
 
 def run_chain(args):
@@ -423,6 +440,11 @@ def run_chain(args):
     gh = L.clock_layer_gates(Lc, d, g, dt / 2)
     gf = L.clock_layer_gates(Lc, d, g, dt)
     tr = L.trunc_default(L.PLAIN, chi)
+    tune = None
+    if args.autotune:
+        # every distinct bond shape of the chain (dense Xi after the first update, theta formed)
+        shapes = sorted({(dims[m], d, dims[m + 1], dims[m + 2]) for m in range(Lc - 1)})
+        tune = autotune_shapes(L, L.PRECISIONS[args.precision], shapes, tr, xi_kind=1, theta_given=False)
     step = (lambda: L.tebd_step(s, gh, gf, tr)) if args.no_batch else \
         (lambda: L.tebd_step_batched([s], [gh], [gf], tr))
     for _ in range(args.warmup):
@@ -454,6 +476,7 @@ def run_chain(args):
         "dtype": args.precision, "data": "synthetic",
         "config": {"workload": f"finite chain L={Lc} d=4 chi<={chi} plain, Strang step",
                    "batched": not args.no_batch},
+        "autotune": tune,
     }
     print(json.dumps(line), flush=True)
     s.close()
@@ -662,6 +685,9 @@ def main():
     ap.add_argument("--chain-L", type=int, default=128)
     ap.add_argument("--chain-chi", type=int, default=512)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="skip the library's tile autotuner (run by default on the bond and chain "
+                         "workloads' shapes before any timing)")
     ap.add_argument("--svd-c128", action="store_true",
                     help="svd workload: add the complex128 arms (the cuSOLVER SVD alone takes ~165 s)")
     args = ap.parse_args()

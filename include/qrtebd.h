@@ -270,6 +270,33 @@ int qrtebd_zgemm_noalloc(int precision, int m, int n, int k, const void* A, long
                          int conj_b, void* C, long long scm, long long scn, const double* alpha,
                          const double* beta, void* stream);
 
+/* ------------------------------------------------------------------ autotuner */
+/* Tile shapes of the complex64 tensor-core products (batching pattern (2)). Every
+ * product C = A B is run as a real GEMM over 128-row tiles of BN real output columns;
+ * its launch configuration is (bn, splits, tail): bn = 128 or 256, splits = K-splits of
+ * the whole grid (1 = none, 0 = the built-in heuristic), tail = with splits 1, whether a
+ * short last wave of tiles runs with its K split over the idle SMs. A process-wide table
+ * maps a product's shape (M, N, K, three = 3xTF32; after the library's N > M swap, so
+ * M >= N) to the configuration measured fastest; shapes not in it use the heuristic.
+ *
+ * qrtebd_autotune_bond: runs one bond update of this shape on synthetic data on `stream`
+ * (synchronously; not during stream capture), records the shapes of its tensor-core
+ * products, then times every candidate configuration of each shape not yet in the table
+ * on scratch operands (CUDA events, 2 warm-up + 5 timed runs) and stores the fastest.
+ * Allocates its own device memory (cudaMalloc / cudaFree). Arguments as
+ * qrtebd_bond_workspace_size; *n_shapes (may be NULL) receives the number of shapes
+ * newly tuned. Precisions other than C64_3XTF32 / C64_TF32 tune nothing (OK).
+ * qrtebd_autotune_entry: entry i in shape order: shape {M, N, K, three}, config
+ * {bn, splits, tail}, ms {tuned, heuristic} (0 for entries set by hand).
+ * qrtebd_autotune_set: insert or replace an entry (e.g. a table saved earlier).
+ * The table is shared by all threads (a mutex guards it). */
+int qrtebd_autotune_bond(int precision, int chi_l, int d, int chi_m, int chi_r, int xi_kind,
+                         int theta_given, const qrtebd_trunc* tr, void* stream, int* n_shapes);
+int qrtebd_autotune_count(void);
+int qrtebd_autotune_entry(int i, int shape[4], int config[3], double ms[2]);
+int qrtebd_autotune_set(const int shape[4], const int config[3]);
+void qrtebd_autotune_clear(void);
+
 /* ------------------------------------------------------------- Householder QR */
 /* A = Q R for a device matrix A (m x n, m >= n, row-major, leading dimension lda, in the
  * precision's storage type): the factorisation of Sec. II (i) (and, applied to Y^dag,

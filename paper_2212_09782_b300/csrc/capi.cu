@@ -138,6 +138,21 @@ int qr_entry(int precision, int m, int n, void* A, long long lda, void* Q, long 
   return householder_qr<T>(static_cast<cx<T>*>(A), lda, m, n, static_cast<cx<T>*>(Q), ldq, qs, st,
                            device_error_word(), &qg, &qg_side);
 }
+__global__ void k_fill_unit(float2* x, long long n, unsigned seed) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned h = (unsigned)i * 2654435761u ^ seed;
+  h ^= h >> 15; h *= 2246822519u; h ^= h >> 13;
+  x[i] = make_float2((float)(h & 0xffff) / 32768.f - 1.f, (float)(h >> 16) / 32768.f - 1.f);
+}
+__global__ void k_fill_unit64(double2* x, long long n, unsigned seed) {
+  long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  unsigned h = (unsigned)i * 2654435761u ^ seed;
+  h ^= h >> 15; h *= 2246822519u; h ^= h >> 13;
+  x[i] = make_double2((double)(h & 0xffff) / 32768.0 - 1.0, (double)(h >> 16) / 32768.0 - 1.0);
+}
+std::mutex g_tune_run_mu;  // one tuning pass at a time (the recording is process-wide)
 }  // namespace
 }  // namespace qrtebd
 
@@ -175,6 +190,109 @@ int qrtebd_bond_update(const qrtebd_bond_io* io, const qrtebd_trunc* tr, void* s
                        qrtebd_bond_info* info) {
   return bond_update(io, tr, static_cast<cudaStream_t>(stream), info, nullptr);
 }
+
+
+int qrtebd_autotune_bond(int precision, int chi_l, int d, int chi_m, int chi_r, int xi_kind,
+                         int theta_given, const qrtebd_trunc* tr, void* stream, int* n_shapes) {
+  if (!tr || chi_l < 1 || d < 1 || chi_m < 1 || chi_r < 1 || xi_kind < 0 || xi_kind > 2)
+    return QRTEBD_ERR_INVALID_ARG;
+  if (n_shapes) *n_shapes = 0;
+  if (precision != QRTEBD_C64_3XTF32 && precision != QRTEBD_C64_TF32) return QRTEBD_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  size_t ws = 0;
+  QR_TRY(qrtebd_bond_workspace_size(precision, chi_l, d, chi_m, chi_r, xi_kind, theta_given, tr, &ws));
+  const long long eta = choose_eta(tr, chi_l, d, chi_m, chi_r);
+  if (eta < 1) return QRTEBD_ERR_INVALID_ARG;
+  const long long mL = (long long)chi_l * d, nR = (long long)d * chi_r;
+  // synthetic operands of the bond's shape (values in [-1, 1]); one allocation
+  const long long n_in[4] = {xi_kind == 1 ? (long long)chi_l * chi_l : chi_l,
+                             theta_given ? 0 : mL * chi_m, (long long)chi_m * nR,
+                             theta_given ? mL * nR : 0};
+  const long long n_out[3] = {mL * eta, eta * eta, eta * nR};
+  const long long n_gate = (long long)d * d * d * d;  // complex128
+  size_t off = 0;
+  auto carve = [&](size_t bytes) { size_t o = off; off += align_up(bytes, 256); return o; };
+  size_t o_in[4], o_out[3];
+  for (int i = 0; i < 4; ++i) o_in[i] = carve((size_t)n_in[i] * sizeof(float2));
+  for (int i = 0; i < 3; ++i) o_out[i] = carve((size_t)n_out[i] * sizeof(float2));
+  const size_t o_gate = carve((size_t)n_gate * sizeof(double2));
+  const size_t o_stats = carve(4 * sizeof(double));
+  const size_t o_s = carve((size_t)eta * sizeof(double));
+  const size_t o_ws = carve(ws);
+  char* mem = nullptr;
+  QR_CUDA_TRY(cudaMalloc(&mem, off));
+  std::lock_guard<std::mutex> lk(g_tune_run_mu);
+  int rc = QRTEBD_OK;
+  std::vector<TcShape> shapes;
+  do {
+    for (int i = 0; i < 4; ++i)
+      if (n_in[i] > 0)
+        k_fill_unit<<<(unsigned)ceil_div(n_in[i], 256), 256, 0, st>>>(
+            reinterpret_cast<float2*>(mem + o_in[i]), n_in[i], 17u + i);
+    k_fill_unit64<<<(unsigned)ceil_div(n_gate, 256), 256, 0, st>>>(
+        reinterpret_cast<double2*>(mem + o_gate), n_gate, 5u);
+    if (cudaGetLastError() != cudaSuccess) { rc = QRTEBD_ERR_CUDA; break; }
+    qrtebd_bond_io io;
+    std::memset(&io, 0, sizeof io);
+    io.precision = precision;
+    io.chi_l = chi_l; io.d = d; io.chi_m = chi_m; io.chi_r = chi_r;
+    io.xi_kind = xi_kind;
+    io.xi = xi_kind ? mem + o_in[0] : nullptr;
+    io.bm = theta_given ? nullptr : mem + o_in[1];
+    io.bn = mem + o_in[2];
+    io.theta = theta_given ? mem + o_in[3] : nullptr;
+    io.gate = mem + o_gate;
+    io.bm_out = mem + o_out[0]; io.xi_out = mem + o_out[1]; io.bn_out = mem + o_out[2];
+    io.stats_out = reinterpret_cast<double*>(mem + o_stats);
+    io.schmidt_out = reinterpret_cast<double*>(mem + o_s);
+    io.workspace = mem + o_ws; io.workspace_bytes = ws;
+    // pass 1: record the tensor-core product shapes of one update
+    tc_record_begin();
+    qrtebd_bond_info info;
+    rc = bond_update(&io, tr, st, &info, nullptr);
+    shapes = tc_record_end();
+    if (rc != QRTEBD_OK) break;
+    if (cudaStreamSynchronize(st) != cudaSuccess) { rc = QRTEBD_ERR_CUDA; break; }
+  } while (false);
+  cudaError_t fe = cudaStreamSynchronize(st);
+  cudaFree(mem);
+  if (rc != QRTEBD_OK) return rc;
+  if (fe != cudaSuccess) { set_last_message(cudaGetErrorString(fe)); return QRTEBD_ERR_CUDA; }
+  // pass 2: time the candidates of every shape not tuned yet
+  int n = 0;
+  for (const TcShape& sh : shapes) {
+    TcConfig c;
+    if (tc_tune_get(sh, &c)) continue;
+    QR_TRY(tc_tune_shape(sh, st, nullptr));
+    ++n;
+  }
+  if (n_shapes) *n_shapes = n;
+  return QRTEBD_OK;
+}
+
+int qrtebd_autotune_count(void) { return (int)tc_tune_list().size(); }
+
+int qrtebd_autotune_entry(int i, int shape[4], int config[3], double ms[2]) {
+  const std::vector<TcTuned> v = tc_tune_list();
+  if (i < 0 || i >= (int)v.size() || !shape || !config) return QRTEBD_ERR_INVALID_ARG;
+  const TcTuned& t = v[i];
+  shape[0] = t.shape.M; shape[1] = t.shape.N; shape[2] = t.shape.K; shape[3] = t.shape.three;
+  config[0] = t.cfg.bn; config[1] = t.cfg.splits; config[2] = t.cfg.tail;
+  if (ms) { ms[0] = t.ms_tuned; ms[1] = t.ms_default; }
+  return QRTEBD_OK;
+}
+
+int qrtebd_autotune_set(const int shape[4], const int config[3]) {
+  if (!shape || !config) return QRTEBD_ERR_INVALID_ARG;
+  const TcShape s{shape[0], shape[1], shape[2], shape[3] ? 1 : 0};
+  const TcConfig c{config[0], config[1], config[2] ? 1 : 0};
+  if (s.M < s.N || s.N < 1 || s.K < 1 || (c.bn != 128 && c.bn != 256) || c.splits < 0 || c.splits > 32)
+    return QRTEBD_ERR_INVALID_ARG;
+  tc_tune_put(TcTuned{s, c, 0.0, 0.0});
+  return QRTEBD_OK;
+}
+
+void qrtebd_autotune_clear(void) { tc_tune_clear(); }
 
 int qrtebd_stream_check(void* stream) { return check_device_error(static_cast<cudaStream_t>(stream)); }
 

@@ -13,6 +13,8 @@
 #include "common.cuh"
 #include "gemm_simt.cuh"
 
+#include <vector>
+
 namespace qrtebd {
 
 struct TcSlot {
@@ -44,5 +46,34 @@ int tc_gemm(const GemmArgs<float>& g, bool three, TcWorkspace& w, cudaStream_t s
 
 // Invalidate cached prepared operands (call when their sources may change).
 void tc_invalidate(TcWorkspace& w);
+
+// ---- launch configurations and the autotuner's table
+// A product's shape as the kernel sees it (after the N > M swap): M >= N.
+struct TcShape {
+  int M, N, K, three;
+  bool operator<(const TcShape& o) const {
+    return M != o.M ? M < o.M : N != o.N ? N < o.N : K != o.K ? K < o.K : three < o.three;
+  }
+};
+// bn: real output columns per tile (128 or 256); splits: K-splits of the whole grid
+// (>= 1; 0 = the heuristic); tail: with splits == 1, whether a short last wave runs
+// with its K split over the idle SMs.
+struct TcConfig { int bn = 256; int splits = 0; int tail = 1; };
+struct TcTuned { TcShape shape; TcConfig cfg; double ms_tuned, ms_default; };
+
+// C = alpha opA opB + beta C with a given configuration (nullptr: the table's entry for
+// the shape, else the heuristic).
+int tc_gemm_cfg(const GemmArgs<float>& g, bool three, TcWorkspace& w, cudaStream_t st,
+                const TcConfig* cfg, int prof_family = PROF_TC_GEMM);
+// Shapes seen by tc_gemm between begin and end (the tuner's recording pass).
+void tc_record_begin();
+std::vector<TcShape> tc_record_end();
+// Time the candidate configurations of one shape on scratch operands (synchronous, not
+// during stream capture) and store the fastest in the table.
+int tc_tune_shape(const TcShape& s, cudaStream_t st, TcTuned* out);
+bool tc_tune_get(const TcShape& s, TcConfig* cfg);
+void tc_tune_put(const TcTuned& t);
+std::vector<TcTuned> tc_tune_list();
+void tc_tune_clear();
 
 }  // namespace qrtebd

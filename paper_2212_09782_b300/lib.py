@@ -65,6 +65,11 @@ def _load():
         "qrtebd_version": (C.c_char_p, []),
         "qrtebd_launch_count": (C.c_longlong, []),
         "qrtebd_layer_workers": (I, []),
+        "qrtebd_autotune_bond": (I, [I, I, I, I, I, I, I, C.POINTER(Trunc), P, C.POINTER(I)]),
+        "qrtebd_autotune_count": (I, []),
+        "qrtebd_autotune_entry": (I, [I, C.POINTER(I), C.POINTER(I), C.POINTER(D)]),
+        "qrtebd_autotune_set": (I, [C.POINTER(I), C.POINTER(I)]),
+        "qrtebd_autotune_clear": (None, []),
         "qrtebd_householder_qr": (I, [I, I, I, P, LL, P, LL, P, S, P]),
         "qrtebd_qr_workspace_size": (S, [I, I, I]),
         "qrtebd_profile_enable": (I, [I]),
@@ -413,6 +418,38 @@ class MPS:
         obj.stream = stream
         obj.L, obj.d, obj.infinite = L, d, bool(inf)
         return obj
+
+
+def autotune_bond(precision, chi_l, d, chi_m, chi_r, trunc, xi_kind=1, theta_given=False,
+                  stream=None):
+    """Tune the tensor-core launch configurations of one bond-update shape (synchronous);
+    returns the number of product shapes newly tuned."""
+    prec = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
+    n = C.c_int(0)
+    check(_lib.qrtebd_autotune_bond(prec, chi_l, d, chi_m, chi_r, xi_kind, 1 if theta_given else 0,
+                                    C.byref(trunc), stream_handle(stream), C.byref(n)),
+          "autotune_bond")
+    return n.value
+
+
+def autotune_entries():
+    """The autotuner's table: [{shape: (M, N, K, three), config: (bn, splits, tail),
+    ms_tuned, ms_default}]."""
+    out = []
+    for i in range(_lib.qrtebd_autotune_count()):
+        sh, cf, ms = (C.c_int * 4)(), (C.c_int * 3)(), (C.c_double * 2)()
+        check(_lib.qrtebd_autotune_entry(i, sh, cf, ms), "autotune_entry")
+        out.append({"shape": tuple(sh), "config": tuple(cf), "ms_tuned": ms[0], "ms_default": ms[1]})
+    return out
+
+
+def autotune_set(shape, config):
+    """Insert or replace a table entry (e.g. one saved from autotune_entries)."""
+    check(_lib.qrtebd_autotune_set((C.c_int * 4)(*shape), (C.c_int * 3)(*config)), "autotune_set")
+
+
+def autotune_clear():
+    _lib.qrtebd_autotune_clear()
 
 
 def layer_workers():

@@ -83,3 +83,30 @@ def test_clock_gate_matches_oracle(L, d, g, wl, wr, tau):
 def test_invalid_arguments_rejected(L):
     with pytest.raises(L.QrtebdError):
         L.clock_bond_gate(1, 1.0, 0.5, 0.5, 0.1)
+
+
+def test_autotune_table_host(L):
+    # the autotuner's table on the host: insert, replace, order, validation (no GPU work)
+    import ctypes as C
+    raw = L.raw()
+    L.autotune_clear()
+    try:
+        assert raw.qrtebd_autotune_count() == 0
+        L.autotune_set((512, 256, 1024, 1), (128, 4, 0))
+        L.autotune_set((512, 256, 1024, 0), (256, 0, 1))
+        L.autotune_set((512, 256, 1024, 1), (256, 2, 0))  # replaces the first
+        e = L.autotune_entries()
+        assert [x["shape"] for x in e] == [(512, 256, 1024, 0), (512, 256, 1024, 1)]
+        assert e[1]["config"] == (256, 2, 0) and e[1]["ms_tuned"] == 0.0
+        for bad in [((256, 512, 1024, 1), (128, 1, 0)),   # M < N: not a swapped shape
+                    ((512, 256, 1024, 1), (64, 1, 0)),    # no such tile width
+                    ((512, 256, 1024, 1), (128, 33, 0))]: # more K-splits than allowed
+            with pytest.raises(L.QrtebdError):
+                L.autotune_set(*bad)
+        # precisions without tensor-core products tune nothing and touch no GPU
+        n = C.c_int(-1)
+        t = L.trunc_default(L.PLAIN, 64)
+        assert raw.qrtebd_autotune_bond(L.C128, 64, 3, 64, 64, 0, 1, C.byref(t), None, C.byref(n)) == 0
+        assert n.value == 0
+    finally:
+        L.autotune_clear()

@@ -76,3 +76,65 @@ def test_zgemm_tail_wave_split(prec, ops):
     got = out.cpu().numpy().astype(np.complex128)
     scale = np.abs(opA).max() * np.abs(B).max() * k
     assert np.abs(got - ref).max() / scale < (tol(prec, k) if prec != "c64_tf32" else 4e-3)
+
+
+@pytest.mark.parametrize("prec", ["c64_3xtf32", "c64_tf32"])
+@pytest.mark.parametrize("m,n,k", [(640, 384, 1000), (5000, 160, 333), (300, 170, 2500)])
+@pytest.mark.parametrize("config", [(128, 1, 0), (128, 1, 1), (128, 3, 0), (256, 5, 0),
+                                    (128, 32, 0), (256, 1, 0)])
+def test_zgemm_tuned_configs(prec, m, n, k, config):
+    # every launch configuration the autotuner can choose (tile width 128/256, K-splits,
+    # tail-wave split) gives the same product; entries are keyed on the swapped shape
+    # (M >= N), which these m >= n cases are already
+    import torch
+    from paper_2212_09782_b300 import lib as L
+    r = W.rng(m + 7 * n + 13 * k)
+    A = W.complex_gaussian(r, (m, k)).astype(np.complex64).astype(np.complex128)
+    B = W.complex_gaussian(r, (k, n)).astype(np.complex64).astype(np.complex128)
+    C0 = W.complex_gaussian(r, (m, n)).astype(np.complex64).astype(np.complex128)
+    alpha, beta = 1.0 + 0.5j, 0.5 - 1.0j
+    ref = alpha * (A @ B) + beta * C0
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=torch.complex64)
+    L.autotune_clear()
+    try:
+        L.autotune_set((m, n, k, 1 if prec == "c64_3xtf32" else 0), config)
+        Cd = dev(C0)
+        L.zgemm(prec, dev(A), dev(B), alpha=alpha, beta=beta, C_out=Cd)
+        L.stream_check()
+    finally:
+        L.autotune_clear()
+    got = Cd.cpu().numpy().astype(np.complex128)
+    err = np.abs(got - ref).max() / (np.abs(alpha) * np.sqrt(k) + np.abs(beta))
+    assert err < tol(prec, k), err
+
+
+def test_autotune_bond_table_and_parity():
+    # the tuner records the products of one bond update, times the candidates of each and
+    # keeps the fastest (never slower than the heuristic as measured); an update with the
+    # tuned table still matches the oracle
+    from oracle import bond
+    from paper_2212_09782_b300 import lib as L
+    from tests.gpu_helpers import TOL as BTOL, compare, rounded, run_gpu
+    chi, d = 192, 4
+    t = L.trunc_default(L.PLAIN, chi)
+    L.autotune_clear()
+    try:
+        n = L.autotune_bond("c64_3xtf32", chi, d, chi, chi, t, xi_kind=0, theta_given=True)
+        ents = L.autotune_entries()
+        assert n == len(ents) > 0
+        for e in ents:
+            M, N, K, three = e["shape"]
+            bn, splits, tail = e["config"]
+            assert M >= N and three == 1 and bn in (128, 256) and 0 <= splits <= 32
+            assert 0 < e["ms_tuned"] <= e["ms_default"]
+        assert L.autotune_bond("c64_3xtf32", chi, d, chi, chi, t, xi_kind=0, theta_given=True) == 0
+        r = W.rng(77)
+        th = W.complex_gaussian(r, (chi, d, d, chi))
+        th = rounded(th / np.linalg.norm(th), "c64_3xtf32")
+        U = W.random_unitary(r, d * d)
+        Bn = rounded(W.random_right_isometry(r, chi, d, chi), "c64_3xtf32")
+        orc = bond.qr_update(None, None, Bn, U, chi_max=chi, theta=th)
+        gpu = run_gpu("c64_3xtf32", None, None, Bn, U, t, theta=th)
+        compare(gpu, orc, BTOL["c64_3xtf32"])
+    finally:
+        L.autotune_clear()
