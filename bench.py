@@ -627,7 +627,7 @@ def run_c3(args):
     import torch
     from paper_2212_09782_b300 import lib as L
     Lc, d, g, dt, chi = 2, 5, 2.0, 0.02, 1024
-    tr = L.trunc_default(L.CBE, chi)
+    tr = L.trunc_default(L.CBE, chi, reorth=args.reorth)
     half = L.clock_layer_gates(Lc, d, g, dt / 2, infinite=True)
     full = L.clock_layer_gates(Lc, d, g, dt, infinite=True)
     s = L.MPS(Lc, d, chi, precision=args.precision, infinite=True)
@@ -685,6 +685,8 @@ def main():
     ap.add_argument("--chain-L", type=int, default=128)
     ap.add_argument("--chain-chi", type=int, default=512)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--reorth", type=int, default=-1, choices=[-1, 0, 1],
+                    help="re-orthogonalisation pass (qrtebd_trunc.reorth; -1 = the library default)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="skip the library's tile autotuner (run by default on the bond and chain "
                          "workloads' shapes before any timing)")

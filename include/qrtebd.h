@@ -270,6 +270,21 @@ int qrtebd_zgemm_noalloc(int precision, int m, int n, int k, const void* A, long
                          int conj_b, void* C, long long scm, long long scn, const double* alpha,
                          const double* beta, void* stream);
 
+/* ------------------------------------------------------------ CBE decomposition */
+/* Step (iv) of Sec. III on its own: for Rz (n x n device matrix, row-major, leading
+ * dimension ldr, the precision's storage type), w (device double[n]) receives the
+ * eigenvalues of Rz Rz^dag = L^dag L (L = Rz^dag; the squared singular values of L) in
+ * descending order, and Vh (device complex128 n x n, row-major) the conjugated
+ * eigenvectors as rows: Rz Rz^dag = Vh^dag diag(w) Vh. Complex64 precisions: one-sided
+ * Jacobi in FP32 on the rows of Rz (FP64 norms and rotation parameters), one cooperative
+ * launch; C128: Rz Rz^dag in FP64, then two-sided FP64 Jacobi. sweeps (device int, may be
+ * NULL): Jacobi sweeps run by the one-sided solver (41 = stopped unconverged; 0 for C128).
+ * workspace: device, at least qrtebd_cbe_decompose_workspace_size bytes, else OOM.
+ * INVALID_ARG for n < 1, ldr < n or a null pointer. Enqueued on `stream`. */
+size_t qrtebd_cbe_decompose_workspace_size(int precision, int n);
+int qrtebd_cbe_decompose(int precision, int n, const void* Rz, long long ldr, double* w, void* Vh,
+                         void* workspace, size_t workspace_bytes, int* sweeps, void* stream);
+
 /* ------------------------------------------------------------------ autotuner */
 /* Tile shapes of the complex64 tensor-core products (batching pattern (2)). Every
  * product C = A B is run as a real GEMM over 128-row tiles of BN real output columns;

@@ -100,15 +100,16 @@ __global__ void k_sum_partials(const double* partial, int n, double* out) {
   }
 }
 
-// stats = {eps, ||theta~||^2, kept, chi_new}; scal[0] = 1/sqrt(kept)
+// stats = {eps, ||theta~||^2, kept, chi_new}; scal[0] = 1/sqrt(kept_norm), the scale that
+// normalises the kept values (kept_norm: nullptr = kept)
 __global__ void k_finalize(const double* th2, const double* kept, double chi_new, double* stats,
-                           double* scal, unsigned* err) {
-  double t = *th2, k = *kept;
+                           double* scal, unsigned* err, const double* kept_norm = nullptr) {
+  double t = *th2, k = *kept, kn = kept_norm ? *kept_norm : k;
   double eps = t > 0 ? 1.0 - k / t : 0.0;
   if (eps < 0) eps = 0;
-  if (!isfinite(t) || !isfinite(k)) atomicOr(err, DEVERR_NUMERIC);
+  if (!isfinite(t) || !isfinite(k) || !isfinite(kn)) atomicOr(err, DEVERR_NUMERIC);
   if (stats) { stats[0] = eps; stats[1] = t; stats[2] = k; stats[3] = chi_new; }
-  scal[0] = k > 0 ? 1.0 / sqrt(k) : 0.0;
+  scal[0] = kn > 0 ? 1.0 / sqrt(kn) : 0.0;
 }
 
 // explicit eps = ||theta~ - approx||^2 / ||theta~||^2 overrides stats[0]
@@ -181,11 +182,19 @@ int launch_gate(const cx<T>* th, cx<T>* out, const double2* U, int chiL, int d, 
 // Reads w (descending eigenvalues of L^dag L), writes S = sqrt(max(w, 0)),
 // decides chi~ (Fig. 4 caption: drop S / ||S|| < svd_min, keep <= chi_max, never
 // split a multiplet closer than tie_tol * S_1), kept = sum_{k < chi~} S_k^2.
+// The cut of Sec. III (svd_min, chi_max, eps_target, then the tie rule). kept (for eps):
+// ||L||^2 - sum of the discarded S^2, with ||L||^2 = lnorm2 summed in FP64 from L itself:
+// the discarded values are accurate relative to themselves, whereas the sum of the kept
+// ones carries the decomposition's rounding relative to the largest (~1e-6 for the FP32
+// solver at eta ~ 1000) into eps, which is itself ~1e-6 per update at chi ~ 1000.
+// kept_norm: the sum of the kept S^2, which normalises Xi~ exactly.
 __global__ void k_cbe_cut(const double* w, int n, int chi_max, double svd_min, double tie_tol,
-                          double eps_target, double* S, double* kept, int* chi_out) {
+                          double eps_target, const double* lnorm2, double* S, double* kept,
+                          double* kept_norm, int* chi_out) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double tot = 0;
   for (int k = 0; k < n; ++k) { double s = w[k] > 0 ? sqrt(w[k]) : 0.0; S[k] = s; tot += s * s; }
+  if (*lnorm2 > 0) tot = *lnorm2;
   double nrm = sqrt(tot);
   int c = 0;
   if (nrm > 0) { for (int k = 0; k < n; ++k) if (S[k] / nrm >= svd_min) ++c; }
@@ -201,9 +210,11 @@ __global__ void k_cbe_cut(const double* w, int n, int chi_max, double svd_min, d
   if (nrm > 0) {
     while (c < n && c > 1 && (S[c - 1] - S[c]) / nrm <= tie_tol * (S[0] / nrm)) --c;
   }
-  double kk = 0;
+  double kk = 0, tail = 0;
   for (int k = 0; k < c; ++k) kk += S[k] * S[k];
-  *kept = kk;
+  for (int k = n - 1; k >= c; --k) tail += S[k] * S[k];  // smallest first
+  *kept = tot - tail;
+  *kept_norm = kk;
   *chi_out = c;
 }
 
@@ -292,7 +303,7 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
   QrScratch<T> qs;
   qr_carve<T>(ar, (int)std::max(mL, nR), eta, qs);
   double* partial = ar.take<double>(RED_BLOCKS);
-  double* scal = ar.take<double>(8);  // th2, kept, inv sqrt(kept)
+  double* scal = ar.take<double>(8);  // th2, kept, inv sqrt(kept), r2, norm L, kept (CBE)
   double* stats_local = ar.take<double>(4);
   size_t simt_elems = std::max(gemm_simt_scratch_elems((int)mL, eta, (int)nR, 1),
                                gemm_simt_scratch_elems((int)nR, eta, (int)mL, 1));
@@ -301,20 +312,26 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
   for (int kb = 1; kb <= 128; kb *= 2)
     simt_elems = std::max(simt_elems, gemm_simt_scratch_elems(kb, eta, (int)std::max(mL, nR), 1));
   cx<T>* simt_scratch = simt_elems ? ar.take<cx<T>>(simt_elems) : nullptr;
-  // CBE: eigen-decomposition buffers (FP64)
+  // CBE: the decomposition of L^dag L. complex128: two-sided FP64 Jacobi on M = Rz Rz^dag;
+  // complex64: one-sided FP32 Jacobi on the rows of Rz (M is never formed)
+  constexpr bool kOneSided = std::is_same<T, float>::value;
   double2* M = nullptr; double2* Vh = nullptr; double* w = nullptr; double2* eig_scr = nullptr;
-  double* Sv = nullptr; cx<T>* Vt = nullptr; cx<T>* Bn_full = nullptr; int* chi_dev = nullptr;
-  size_t eig_elems = 0;
+  double* Sv = nullptr; cx<T>* Vt = nullptr; int* chi_dev = nullptr; char* sj_work = nullptr;
+  size_t eig_elems = 0, sj_bytes = 0;
   if (cbe) {
-    M = ar.take<double2>((size_t)eta * eta);
     Vh = ar.take<double2>((size_t)eta * eta);
     w = ar.take<double>(eta);
     Sv = ar.take<double>(eta);
-    eig_elems = herm_eig_scratch_elems(eta);
-    eig_scr = ar.take<double2>(eig_elems);
     Vt = ar.take<cx<T>>((size_t)eta * eta);
-    Bn_full = ar.take<cx<T>>((size_t)eta * nR);
     chi_dev = ar.take<int>(4);
+    if (kOneSided) {
+      sj_bytes = svd32_work_bytes(eta);
+      sj_work = ar.take<char>(sj_bytes);
+    } else {
+      M = ar.take<double2>((size_t)eta * eta);
+      eig_elems = herm_eig_scratch_elems(eta);
+      eig_scr = ar.take<double2>(eig_elems);
+    }
   }
   const bool eps_explicit = tr->eps_explicit != 0;
   // one re-orthogonalisation pass of Qz (auto: complex64 with 1xTF32 contractions, whose
@@ -402,6 +419,9 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
   if (Zc) QR_CUDA_TRY(cudaMemcpyAsync(Zc, Z, (size_t)nR * eta * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st));
   QR_TRY(householder_qr<T>(Z, eta, (int)nR, eta, Qz, eta, qs, st, err, &qg, &qg_side));
 
+  // the re-orthogonalisation passes run in 3xTF32 whatever the precision
+  const GemmRunner<T> runner3{use_tc ? (int)QRTEBD_C64_3XTF32 : io->precision, runner.tc,
+                              runner.simt_scratch, runner.simt_scratch_elems};
   if (reorth) {
     // One re-orthogonalisation pass of the right isometry (precision pattern (1)): with
     // D = Qz^dag Qz - 1, Qz <- Qz (1 - D/2), the first-order polar (Newton-Schulz) step,
@@ -410,8 +430,6 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
     // D is resolved well below the TF32 rounding it corrects; D is formed in the epilogue
     // (beta = 1 onto -1) and the update is added onto a copy of Qz, so neither result is
     // swamped by the O(1) parts.
-    const GemmRunner<T> runner3{use_tc ? (int)QRTEBD_C64_3XTF32 : io->precision, runner.tc,
-                                runner.simt_scratch, runner.simt_scratch_elems};
     k_scaled_eye<T><<<(unsigned)ceil_div((long long)eta * eta, 256), 256, 0, st>>>(Dm, eta, T(-1));
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());
@@ -453,22 +471,28 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
       QR_CUDA_TRY(cudaGetLastError());
     }
   } else {
-    // (iv) M = L^dag L = Rz Rz^dag (FP64), eigen-decomposition
+    // (iv) L^dag L = Rz Rz^dag = V^dag S^2 V: w = S^2 descending, Vh = V (rows)
     long long ee = (long long)eta * eta;
-    double2* Rz64 = M;  // reuse: first convert Rz, then form M in Vh's buffer, swap
-    k_to_c128<T><<<(unsigned)ceil_div(ee, 256), 256, 0, st>>>(Z, Rz64, ee);
-    note_launch();
-    QR_CUDA_TRY(cudaGetLastError());
-    {
-      GemmArgs<double> g{eta, eta, eta, Rz64, eta, 1, false, Rz64, 1, eta, true, Vh, eta, 1,
-                         mk<double>(1, 0), mk<double>(0, 0)};
-      QR_TRY(gemm_simt<double>(g, st, nullptr, 0));
+    QR_TRY(norm2<T>(Z, ee, partial, scal + 4, st));  // ||L||^2 in FP64
+    if constexpr (kOneSided) {
+      QR_TRY(svd_rows_jacobi32(reinterpret_cast<const float2*>(Z), eta, eta, w, Vh, sj_work, sj_bytes,
+                               st, err));
+    } else {
+      double2* Rz64 = M;  // reuse: first convert Rz, then form M in Vh's buffer, swap
+      k_to_c128<T><<<(unsigned)ceil_div(ee, 256), 256, 0, st>>>(Z, Rz64, ee);
+      note_launch();
+      QR_CUDA_TRY(cudaGetLastError());
+      {
+        GemmArgs<double> g{eta, eta, eta, Rz64, eta, 1, false, Rz64, 1, eta, true, Vh, eta, 1,
+                           mk<double>(1, 0), mk<double>(0, 0)};
+        QR_TRY(gemm_simt<double>(g, st, nullptr, 0));
+      }
+      // Vh now holds M; eig destroys its input -> copy into M and decompose
+      QR_CUDA_TRY(cudaMemcpyAsync(M, Vh, ee * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+      QR_TRY(herm_eig(M, eta, w, Vh, eig_scr, eig_elems, st, err));
     }
-    // Vh now holds M; eig destroys its input -> copy into M and decompose
-    QR_CUDA_TRY(cudaMemcpyAsync(M, Vh, ee * sizeof(double2), cudaMemcpyDeviceToDevice, st));
-    QR_TRY(herm_eig(M, eta, w, Vh, eig_scr, eig_elems, st, err));
-    k_cbe_cut<<<1, 1, 0, st>>>(w, eta, tr->chi_max, tr->svd_min, tr->tie_tol, tr->eps_target, Sv, scal + 1,
-                               chi_dev);
+    k_cbe_cut<<<1, 1, 0, st>>>(w, eta, tr->chi_max, tr->svd_min, tr->tie_tol, tr->eps_target, scal + 4,
+                               Sv, scal + 1, scal + 5, chi_dev);
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());
     int chi_h = 0;
@@ -479,7 +503,7 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
     if (io->schmidt_out)
       QR_CUDA_TRY(cudaMemcpyAsync(io->schmidt_out, Sv, eta * sizeof(double), cudaMemcpyDeviceToDevice, st));
     k_finalize<<<1, 1, 0, st>>>(scal + 0, scal + 1, (double)chi_new,
-                                io->stats_out ? io->stats_out : stats_local, scal + 2, err);
+                                io->stats_out ? io->stats_out : stats_local, scal + 2, err, scal + 5);
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());
     // (v) B~^n = P V Q^[n] = Vh[0:c] Qz^dag; Xi~ = diag(S[0:c]) / ||.||
@@ -516,7 +540,6 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
       note_launch();
       QR_CUDA_TRY(cudaGetLastError());
     }
-    (void)Bn_full;
   }
   if (info) { info->eta = eta; info->chi_new = chi_new; }
   return QRTEBD_OK;

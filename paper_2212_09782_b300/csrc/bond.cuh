@@ -22,4 +22,14 @@ int herm_eig(double2* A, int n, double* w, double2* Vh, double2* scratch, size_t
              cudaStream_t st, unsigned* err);
 size_t herm_eig_scratch_elems(int n);
 
+// The CBE decomposition for complex64 (one-sided Jacobi, FP32 rows, FP64 rotation
+// parameters): Rz (n x n, device, row-major, leading dimension ldr) is read; w (device, n)
+// receives the eigenvalues of Rz Rz^dag = L^dag L (the squared singular values of L, FP64)
+// in DESCENDING order and Vh (device, n x n) the conjugated eigenvectors as rows, with the
+// contract of herm_eig. work: device, svd32_work_bytes(n). sweeps (optional, device int):
+// sweeps run (SJ_MAX_SWEEPS + 1 = 41: stopped unconverged). One cooperative launch.
+size_t svd32_work_bytes(int n);
+int svd_rows_jacobi32(const float2* Rz, long long ldr, int n, double* w, double2* Vh, void* work,
+                      size_t work_bytes, cudaStream_t st, unsigned* err, int* sweeps = nullptr);
+
 }  // namespace qrtebd

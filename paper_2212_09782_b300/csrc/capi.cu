@@ -354,6 +354,41 @@ size_t qrtebd_qr_workspace_size(int precision, int m, int n) {
   return need;
 }
 
+size_t qrtebd_cbe_decompose_workspace_size(int precision, int n) {
+  if (n < 1) return 0;
+  if (precision == QRTEBD_C128)
+    return (2 * (size_t)n * n + herm_eig_scratch_elems(n)) * sizeof(double2) +
+           gemm_simt_scratch_elems(n, n, n, 1) * sizeof(double2) + 1024;
+  return svd32_work_bytes(n);
+}
+
+int qrtebd_cbe_decompose(int precision, int n, const void* Rz, long long ldr, double* w, void* Vh,
+                         void* workspace, size_t workspace_bytes, int* sweeps, void* stream) {
+  if (n < 1 || ldr < n || !Rz || !w || !Vh || !workspace) return QRTEBD_ERR_INVALID_ARG;
+  if (precision < QRTEBD_C128 || precision > QRTEBD_C64_FP32) return QRTEBD_ERR_INVALID_ARG;
+  if (workspace_bytes < qrtebd_cbe_decompose_workspace_size(precision, n)) return QRTEBD_ERR_OOM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned* err = device_error_word();
+  if (precision != QRTEBD_C128)
+    return svd_rows_jacobi32(static_cast<const float2*>(Rz), ldr, n, w, static_cast<double2*>(Vh),
+                             workspace, workspace_bytes, st, err, sweeps);
+  // complex128: M = Rz Rz^dag (FP64), two-sided Jacobi
+  const size_t nn = (size_t)n * n;
+  double2* M = static_cast<double2*>(workspace);
+  double2* M2 = M + nn;
+  double2* scr = M2 + nn;
+  const size_t se = herm_eig_scratch_elems(n);
+  double2* gscr = scr + se;
+  const double2* R = static_cast<const double2*>(Rz);
+  GemmArgs<double> g{n, n, n, R, ldr, 1, false, R, 1, ldr, true, M, n, 1, make_double2(1, 0),
+                     make_double2(0, 0)};
+  QR_TRY(gemm_simt<double>(g, st, gscr, gemm_simt_scratch_elems(n, n, n, 1)));
+  QR_TRY(herm_eig(M, n, w, static_cast<double2*>(Vh), scr, se, st, err));
+  if (sweeps) QR_CUDA_TRY(cudaMemsetAsync(sweeps, 0, sizeof(int), st));
+  (void)M2;
+  return QRTEBD_OK;
+}
+
 int qrtebd_clock_bond_gate(int d, double g, double wl, double wr, double tau_re, double tau_im,
                            double* U_out) {
   if (d < 2 || d > 64 || !U_out) return QRTEBD_ERR_INVALID_ARG;

@@ -129,6 +129,36 @@ inline cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, siz
   return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
 }
 
+// Grid-wide barrier of a cooperative launch (every CTA resident): a generation counter in
+// bar[1] and an arrival count in bar[0] (both zero before the launch). The wait is bounded
+// (kSpinLimit polls): on expiry DEVERR_TIMEOUT is set and false returned, and the caller
+// must leave the kernel.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long i = 0;
+      while (*gen == g) {
+        if (++i > kSpinLimit) { ok = 0; atomicOr(err, DEVERR_TIMEOUT); break; }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
 __host__ __device__ __forceinline__ long long ceil_div(long long a, long long b) {
   return (a + b - 1) / b;
 }

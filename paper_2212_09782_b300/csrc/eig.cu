@@ -7,7 +7,16 @@
 //   z = (a_qq - a_pp) / (2 |a|),  c = 1 / sqrt(1 + t^2),  s = t c,
 // zeroes (G^dag A G)_pq. Sweeps repeat until the off-diagonal Frobenius norm is
 // below 1e-15 of the total (checked on the host once per sweep).
+//
+// For complex64 the solver of record is instead a one-sided Jacobi SVD in FP32 on the rows
+// of Rz (svd_rows_jacobi32 below): L^dag L = Rz Rz^dag is never formed, the singular
+// values come out with the relative accuracy of the FP32 input rather than squared, and
+// the whole iteration is one cooperative launch.
 #include "bond.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
 
 namespace qrtebd {
 
@@ -135,7 +144,341 @@ __global__ void k_sort_out(const double2* A, const double2* V, int n, double* w,
   }
 }
 
+// ------------------------------------------------------------ one-sided Jacobi (FP32)
+// Rows r_i of R (n x n) are rotated in pairs until every pair is orthogonal to `tol`
+// (|r_p r_q^dag| <= tol ||r_p|| ||r_q||), the same rotations applied to Jt (from 1): then
+// Jt Rz = R has orthogonal rows, Rz Rz^dag = Jt^dag diag(||r_i||^2) Jt, and the rows of
+// Jt are the conjugated eigenvectors of L^dag L = Rz Rz^dag (L = Rz^dag), ||r_i|| its
+// singular values. A pair's rotation is the 2 x 2 Hermitian Jacobi step of the rows'
+// Gram matrix [[a, g], [conj g, b]] (a = ||r_p||^2, b = ||r_q||^2, g = r_p r_q^dag), as in
+// k_jac_rot: rows p, q <- G^dag (rows p, q).
+// Blocked: the rows form blocks of br (8, 4, 2 or 1, the largest whose block pair fits
+// shared memory; the row count is padded with zero rows to a multiple of br). A sweep
+// pairs the blocks in the round-robin order (nb'/2 disjoint block pairs per round, nb'-1
+// rounds); one CTA per block pair loads its 2 br rows into shared memory, runs one
+// sweep over all pairs among them (2 br - 1 inner rounds of br disjoint pairs, a warp per
+// pair), writes them back and applies the accumulated 2br x 2br rotation W to the same
+// rows of Jt. A grid barrier separates the rounds; sweeps repeat until one applies no
+// rotation (at most SJ_MAX_SWEEPS). No FP64 instruction in the loop (B300's FP64 pipe,
+// about one FMA per clock per SM, made the reductions alone the critical path): the rows
+// are FP32, four FP32 partial sums per lane are combined across the warp in double-float
+// (TwoSum), and the rotation is formed in FP32 from those sums with c = 1 - t^2/(q(1+q)),
+// q = sqrt(1+t^2), rounded once. Both matter: an FP32 tree, or c = 1/q directly, each
+// left the singular values ~10x less accurate (an FP32 emulation at n = 256: 1.4e-5 vs
+// 1.1e-6 relative to the largest squared value). The rotations are unitary only to
+// rounding, and ~10^4 of them per row drift its norm by ~1e-5; the same rotations act on R
+// and Jt, so the outputs use the ratio: S_i^2 = ||r_i||^2 / ||j_i||^2 and the rows of Jt
+// normalised (at n = 1126 this took the rows' orthonormality from 3e-5 to 3e-6 and
+// sum_i S_i^2 to within 1e-7 of ||Rz||^2). Global loads bypass L1 (ld.global.cg): other
+// CTAs rewrite rows between rounds.
+constexpr int SJ_NT = 256;
+constexpr int SJ_MAX_SWEEPS = 40;
+constexpr int SJ_BRMAX = 8;
+struct SjCtl {
+  unsigned bar[2];
+  unsigned rot[SJ_MAX_SWEEPS];  // rotations applied per sweep
+  int sweeps;                   // sweeps run; SJ_MAX_SWEEPS + 1: not converged
+};
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// double-float (hi, lo) sums in FP32 arithmetic (TwoSum): the rows' Gram entries to ~FP64
+// accuracy without FP64 instructions
+struct DF { float hi, lo; };
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const float s = a.hi + b.hi, v = s - a.hi;
+  float e = (a.hi - (s - v)) + (b.hi - v);
+  e += a.lo + b.lo;
+  const float h = s + e;
+  return DF{h, e - (h - s)};
+}
+// the lane's four partial sums, then the whole warp (every lane ends with the total)
+__device__ __forceinline__ DF warp_sum_df(const float f[4]) {
+  DF v = df_add(df_add(DF{f[0], 0.f}, DF{f[1], 0.f}), df_add(DF{f[2], 0.f}, DF{f[3], 0.f}));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = df_add(v, DF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+  return v;
+}
+
+__host__ __device__ inline size_t sj_smem_bytes(int n, int br) {
+  return (size_t)2 * br * n * sizeof(float2) + (size_t)(2 * SJ_BRMAX) * (2 * SJ_BRMAX) * sizeof(float2);
+}
+
+// n: the row length (even; a zero column pads an odd order), nb: blocks of br rows
+__global__ void __launch_bounds__(SJ_NT) k_sj_sweeps(float2* R, float2* Jt, int n, int br, int nb,
+                                                     double tol, SjCtl* ctl, unsigned* err) {
+  extern __shared__ __align__(16) unsigned char sj_sm[];
+  float2* X = reinterpret_cast<float2*>(sj_sm);              // [2 br][n]
+  float2* Wm = X + (size_t)2 * br * n;                         // [2 br][2 br]
+  __shared__ unsigned s_cnt, s_vis;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nr = 2 * br;                    // rows held per visit
+  const int nbp = (nb % 2) ? nb + 1 : nb;   // blocks, with an idle partner when odd
+  const float tolf = (float)tol;
+  for (int sweep = 0; sweep < SJ_MAX_SWEEPS; ++sweep) {
+    if (tid == 0) s_cnt = 0;
+    for (int r = 0; r < nbp - 1; ++r) {
+      for (int k = blockIdx.x; k < nbp / 2; k += gridDim.x) {
+        int P, Q;
+        pair_of(r, k, nbp, P, Q);
+        const bool haveQ = Q < nb;          // uniform in the CTA
+        const int rows = haveQ ? nr : br;
+        // global row of local row a: block P's rows, then block Q's
+        auto grow = [&](int a) { return a < br ? P * br + a : Q * br + (a - br); };
+        {
+          // the rows into shared memory: 16-byte asynchronous copies that bypass L1, all in
+          // flight at once (n is even: rows are 16-byte aligned)
+          const int h = n / 2, tot = rows * h;
+          for (int idx = tid; idx < tot; idx += SJ_NT) {
+            const int a = idx / h, o = 2 * (idx - a * h);
+            const float2* src = R + (long long)grow(a) * n + o;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                             (unsigned)__cvta_generic_to_shared(X + (size_t)a * n + o)),
+                         "l"(src)
+                         : "memory");
+          }
+          asm volatile("cp.async.wait_all;" ::: "memory");
+        }
+        for (int e = tid; e < nr * nr; e += SJ_NT) Wm[e] = make_float2(e / nr == e % nr ? 1.f : 0.f, 0.f);
+        if (tid == 0) s_vis = 0;
+        __syncthreads();
+        // one sweep over the pairs among the rows held (round robin, a warp per pair)
+        const int np2 = rows;               // even: br pairs per inner round when haveQ
+        for (int ir = 0; ir < np2 - 1; ++ir) {
+          if (warp < np2 / 2) {
+            int a, b;
+            pair_of(ir, warp, np2, a, b);
+            float2* xa = X + (size_t)a * n;
+            float2* xb = X + (size_t)b * n;
+            float fa[4] = {0, 0, 0, 0}, fb[4] = {0, 0, 0, 0}, fr[4] = {0, 0, 0, 0}, fi[4] = {0, 0, 0, 0};
+            auto acc = [&](int u, int j) {
+              const float2 x = xa[j], y = xb[j];
+              fa[u] = fmaf(x.x, x.x, fmaf(x.y, x.y, fa[u]));
+              fb[u] = fmaf(y.x, y.x, fmaf(y.y, y.y, fb[u]));
+              fr[u] = fmaf(x.x, y.x, fmaf(x.y, y.y, fr[u]));   // Re(x conj y)
+              fi[u] = fmaf(x.y, y.x, fmaf(-x.x, y.y, fi[u]));  // Im(x conj y)
+            };
+            int i = lane;
+            for (; i + 96 < n; i += 128) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) acc(u, i + 32 * u);
+            }
+            for (; i < n; i += 32) acc(0, i);
+            const DF Ad = warp_sum_df(fa), Bd = warp_sum_df(fb), Grd = warp_sum_df(fr), Gid = warp_sum_df(fi);
+            const float A = Ad.hi, B = Bd.hi, Gr = Grd.hi, Gi = Gid.hi;
+            const float ab = hypotf(Gr, Gi);
+            // warp-uniform: every lane holds the same sums (xor reduction)
+            if (ab > 0.f && ab > tolf * sqrtf(A) * sqrtf(B)) {
+              // z = (b - a) / 2|g| with b - a from the double-float sums (no cancellation)
+              const float z = ((Bd.hi - Ad.hi) + (Bd.lo - Ad.lo)) / (2.f * ab);
+              // t = tan(theta); for |z| beyond 1e18, 1 + z^2 overflows and t = 1/(2z) ~ 0
+              const float t = fabsf(z) > 1e18f ? 0.5f / z
+                                               : copysignf(1.f, z) / (fabsf(z) + sqrtf(fmaf(z, z, 1.f)));
+              // c = 1/sqrt(1 + t^2) as 1 - t^2 / (q (1 + q)), q = sqrt(1 + t^2): rounded once,
+              // so that small rotations do not drift the norms (c ~ 1 - t^2/2 rounded to 1)
+              const float qq = sqrtf(fmaf(t, t, 1.f));
+              const float c = 1.f - (t * t) / (qq * (1.f + qq)), sn = t * c;
+              const float er = sn * (Gr / ab), ei = sn * (Gi / ab);
+              // row_a' = c x - (s e) y ; row_b' = conj(s e) x + c y
+              for (int j = lane; j < n; j += 32) {
+                const float2 x = xa[j], y = xb[j];
+                xa[j] = make_float2(c * x.x - (er * y.x - ei * y.y), c * x.y - (er * y.y + ei * y.x));
+                xb[j] = make_float2((er * x.x + ei * x.y) + c * y.x, (er * x.y - ei * x.x) + c * y.y);
+              }
+              if (lane < nr) {
+                const float2 x = Wm[a * nr + lane], y = Wm[b * nr + lane];
+                Wm[a * nr + lane] = make_float2(c * x.x - (er * y.x - ei * y.y), c * x.y - (er * y.y + ei * y.x));
+                Wm[b * nr + lane] = make_float2((er * x.x + ei * x.y) + c * y.x, (er * x.y - ei * x.x) + c * y.y);
+              }
+              if (lane == 0) { atomicAdd(&s_vis, 1u); }
+            }
+          }
+          __syncthreads();
+        }
+        // when anything rotated: the rows back, and Jt rows <- W (Jt rows)
+        if (s_vis) {
+          const int h = n / 2, tot = rows * h;
+          for (int idx = tid; idx < tot; idx += SJ_NT) {
+            const int a = idx / h, o = 2 * (idx - a * h);
+            *reinterpret_cast<float4*>(R + (long long)grow(a) * n + o) =
+                *reinterpret_cast<const float4*>(X + (size_t)a * n + o);
+          }
+          for (int c = tid; c < n; c += SJ_NT) {
+            float2 in[2 * SJ_BRMAX];
+#pragma unroll
+            for (int a = 0; a < 2 * SJ_BRMAX; ++a)
+              if (a < rows) in[a] = __ldcg(Jt + (long long)grow(a) * n + c);
+#pragma unroll
+            for (int a = 0; a < 2 * SJ_BRMAX; ++a) {
+              if (a < rows) {
+                float2 o = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int b = 0; b < 2 * SJ_BRMAX; ++b) {
+                  if (b < rows) {
+                    const float2 wv = Wm[a * nr + b];
+                    o.x = fmaf(wv.x, in[b].x, fmaf(-wv.y, in[b].y, o.x));
+                    o.y = fmaf(wv.x, in[b].y, fmaf(wv.y, in[b].x, o.y));
+                  }
+                }
+                Jt[(long long)grow(a) * n + c] = o;
+              }
+            }
+          }
+          if (tid == 0) s_cnt += s_vis;
+        }
+        __syncthreads();  // X, Wm and s_vis are reused by this CTA's next block pair
+      }
+      if (!grid_barrier(ctl->bar, gridDim.x, err)) return;
+    }
+    if (tid == 0 && s_cnt) atomicAdd(&ctl->rot[sweep], s_cnt);
+    if (!grid_barrier(ctl->bar, gridDim.x, err)) return;
+    if (*reinterpret_cast<volatile unsigned*>(&ctl->rot[sweep]) == 0) {
+      if (blockIdx.x == 0 && tid == 0) ctl->sweeps = sweep + 1;
+      return;
+    }
+  }
+  if (blockIdx.x == 0 && tid == 0) ctl->sweeps = SJ_MAX_SWEEPS + 1;
+}
+
+__global__ void k_eye32(float2* J, int n, int ld) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  const long long r = idx / n, c = idx % n;
+  J[r * ld + c] = make_float2(r == c ? 1.f : 0.f, 0.f);
+}
+
+// s2[i] = ||r_i||^2 / ||j_i||^2 and jn[i] = 1 / ||j_i|| in FP64, one warp per row. The FP32
+// rotations are unitary only to rounding, and the same ones act on R and Jt, so the drift of
+// a row's norm (~1e-5 after ~10^4 rotations) cancels in the ratio.
+__global__ void k_sj_norms(const float2* R, const float2* Jt, int n, int ld, double* s2, double* jn) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double acc = 0.0, accj = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    const float2 x = R[(long long)row * ld + i], y = Jt[(long long)row * ld + i];
+    acc = fma((double)x.x, (double)x.x, fma((double)x.y, (double)x.y, acc));
+    accj = fma((double)y.x, (double)y.x, fma((double)y.y, (double)y.y, accj));
+  }
+  acc = warp_sum_d(acc);
+  accj = warp_sum_d(accj);
+  if (lane == 0) {
+    s2[row] = accj > 0 ? acc / accj : acc;
+    jn[row] = accj > 0 ? 1.0 / sqrt(accj) : 1.0;
+  }
+}
+
+// descending order of s2 (stable): w[rank] = s2[i], order[rank] = i
+__global__ void k_sj_rank(const double* s2, int n, double* w, int* order) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double li = s2[i];
+  int rank = 0;
+  for (int j = 0; j < n; ++j) {
+    const double lj = s2[j];
+    if (lj > li || (lj == li && j < i)) ++rank;
+  }
+  w[rank] = li;
+  order[rank] = i;
+}
+
+// Vh[rank] = row order[rank] of Jt, normalised (FP64)
+__global__ void k_sj_gather(const float2* Jt, const int* order, const double* jn, int n, int ld,
+                            double2* Vh) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  const int r = (int)(idx / n), c = (int)(idx % n);
+  const int src = order[r];
+  const float2 v = Jt[(long long)src * ld + c];
+  const double f = jn[src];
+  Vh[idx] = make_double2(f * v.x, f * v.y);
+}
+
+// rows per block: the largest of 8, 4, 2, 1 whose block pair fits the shared memory
+int sj_rows_per_block(int n) {
+  for (int br = SJ_BRMAX; br > 1; br /= 2)
+    if (sj_smem_bytes(n, br) <= 200 * 1024) return br;
+  return sj_smem_bytes(n, 1) <= 220 * 1024 ? 1 : 0;
+}
+
+int sj_grid(int npairs, size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sj_sweeps, SJ_NT, smem) != cudaSuccess)
+    return 0;
+  return std::min(npairs, std::min(sms * per, 2 * sms));
+}
+
 }  // namespace
+
+size_t svd32_work_bytes(int n) {
+  const int ld = n + (n & 1);
+  const int br = std::max(1, sj_rows_per_block(ld));
+  const size_t rows = (size_t)ceil_div(n, br) * br;  // padded with zero rows
+  return align_up(2 * rows * ld * sizeof(float2), 256) + align_up((size_t)n * sizeof(double), 256) +
+         align_up((size_t)n * sizeof(int), 256) + align_up(sizeof(SjCtl), 256) +
+         align_up((size_t)n * sizeof(double), 256);
+}
+
+int svd_rows_jacobi32(const float2* Rz, long long ldr, int n, double* w, double2* Vh, void* work,
+                      size_t work_bytes, cudaStream_t st, unsigned* err, int* sweeps) {
+  if (n < 1 || ldr < n || !Rz || !w || !Vh || !work || work_bytes < svd32_work_bytes(n))
+    return QRTEBD_ERR_INVALID_ARG;
+  const int ld = n + (n & 1);  // even row length: 16-byte aligned rows
+  const int br = sj_rows_per_block(ld);
+  if (br < 1) { set_last_message("svd_rows_jacobi32: rows too long for shared memory"); return QRTEBD_ERR_INVALID_ARG; }
+  const int nb = (int)ceil_div(n, br);
+  const size_t rows = (size_t)nb * br;
+  char* q = static_cast<char*>(work);
+  float2* R = reinterpret_cast<float2*>(q);
+  float2* Jt = R + rows * ld;
+  q += align_up(2 * rows * ld * sizeof(float2), 256);
+  double* s2 = reinterpret_cast<double*>(q); q += align_up((size_t)n * sizeof(double), 256);
+  int* order = reinterpret_cast<int*>(q); q += align_up((size_t)n * sizeof(int), 256);
+  SjCtl* ctl = reinterpret_cast<SjCtl*>(q); q += align_up(sizeof(SjCtl), 256);
+  double* jn = reinterpret_cast<double*>(q);
+  // R = Rz, Jt = identity; zero rows below and a zero column right of them when n is odd
+  QR_CUDA_TRY(cudaMemsetAsync(R, 0, 2 * rows * ld * sizeof(float2), st));
+  QR_CUDA_TRY(cudaMemcpy2DAsync(R, (size_t)ld * sizeof(float2), Rz, (size_t)ldr * sizeof(float2),
+                                (size_t)n * sizeof(float2), (size_t)n, cudaMemcpyDeviceToDevice, st));
+  k_eye32<<<(unsigned)ceil_div((long long)n * n, 256), 256, 0, st>>>(Jt, n, ld);
+  note_launch();
+  QR_CUDA_TRY(cudaGetLastError());
+  QR_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(SjCtl), st));
+  if (n > 1) {
+    const size_t smem = sj_smem_bytes(ld, br);
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+      attr = cudaFuncSetAttribute(k_sj_sweeps, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    });
+    QR_CUDA_TRY(attr);
+    const int nbp = (nb % 2) ? nb + 1 : nb;
+    const int grid = sj_grid(nbp / 2, smem);
+    if (grid < 1) { set_last_message("svd_rows_jacobi32: no resident CTA"); return QRTEBD_ERR_CUDA; }
+    // convergence: orthogonal to FP32 working accuracy, sqrt(n) eps (the rows' rounding)
+    double tol = std::sqrt((double)std::max(n, 16)) * 5.96e-8;
+    int nv = ld, brv = br, nbv = nb;
+    void* args[] = {&R, &Jt, &nv, &brv, &nbv, &tol, &ctl, &err};
+    QR_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_sj_sweeps, dim3((unsigned)grid), dim3(SJ_NT),
+                                            args, smem, st));
+    note_launch();
+  }
+  k_sj_norms<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(R, Jt, n, ld, s2, jn);
+  note_launch();
+  k_sj_rank<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(s2, n, w, order);
+  note_launch();
+  k_sj_gather<<<(unsigned)ceil_div((long long)n * n, 256), 256, 0, st>>>(Jt, order, jn, n, ld, Vh);
+  note_launch();
+  QR_CUDA_TRY(cudaGetLastError());
+  if (sweeps) QR_CUDA_TRY(cudaMemcpyAsync(sweeps, &ctl->sweeps, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  return QRTEBD_OK;
+}
 
 size_t herm_eig_scratch_elems(int n) {
   // V (n x n) + rotations (n/2+1 Rot = 40 B each, in double2 units) + 2 doubles

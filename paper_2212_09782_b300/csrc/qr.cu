@@ -554,31 +554,6 @@ constexpr int WY_NT = 256;
 constexpr int WY_NC = 128;
 constexpr int WY_KB = 32;
 
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* err) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    volatile unsigned* gen = bar + 1;
-    const unsigned g = *gen;
-    __threadfence();
-    if (atomicAdd(bar, 1u) == nblocks - 1) {
-      atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);
-    } else {
-      long long i = 0;
-      while (*gen == g) {
-        if (++i > kSpinLimit) { ok = 0; atomicOr(err, DEVERR_TIMEOUT); break; }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-    s_ok = ok;
-  }
-  __syncthreads();
-  return s_ok != 0;
-}
 
 template <typename T>
 __global__ void __launch_bounds__(WY_NT) k_apply_wy(cx<T>* C, long long ldc, const cx<T>* V,

@@ -70,6 +70,8 @@ def _load():
         "qrtebd_autotune_entry": (I, [I, C.POINTER(I), C.POINTER(I), C.POINTER(D)]),
         "qrtebd_autotune_set": (I, [C.POINTER(I), C.POINTER(I)]),
         "qrtebd_autotune_clear": (None, []),
+        "qrtebd_cbe_decompose_workspace_size": (S, [I, I]),
+        "qrtebd_cbe_decompose": (I, [I, I, P, LL, P, P, P, S, P, P]),
         "qrtebd_householder_qr": (I, [I, I, I, P, LL, P, LL, P, S, P]),
         "qrtebd_qr_workspace_size": (S, [I, I, I]),
         "qrtebd_profile_enable": (I, [I]),
@@ -418,6 +420,23 @@ class MPS:
         obj.stream = stream
         obj.L, obj.d, obj.infinite = L, d, bool(inf)
         return obj
+
+
+def cbe_decompose(precision, Rz, stream=None):
+    """Step (iv) of CBE for a square torch CUDA tensor Rz: returns (w, Vh, sweeps) with w the
+    eigenvalues of Rz Rz^dag (descending, float64) and Vh its conjugated eigenvectors as
+    rows (complex128), Rz Rz^dag = Vh^dag diag(w) Vh."""
+    import torch
+    prec = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
+    n = Rz.shape[0]
+    w = torch.empty(n, dtype=torch.float64, device=Rz.device)
+    Vh = torch.empty(n, n, dtype=torch.complex128, device=Rz.device)
+    nb = _lib.qrtebd_cbe_decompose_workspace_size(prec, n)
+    ws = torch.empty(nb, dtype=torch.uint8, device=Rz.device)
+    sw = torch.zeros(1, dtype=torch.int32, device=Rz.device)
+    check(_lib.qrtebd_cbe_decompose(prec, n, _ptr(Rz), Rz.stride(0), _ptr(w), _ptr(Vh), _ptr(ws), nb,
+                                    _ptr(sw), stream_handle(stream)), "cbe_decompose")
+    return w, Vh, sw
 
 
 def autotune_bond(precision, chi_l, d, chi_m, chi_r, trunc, xi_kind=1, theta_given=False,
