@@ -566,6 +566,46 @@ def run_svd_arm(args):
     return 0
 
 
+def run_cbe_eig(args):
+    """CBE step (iv) alone (qrtebd_cbe_decompose) on an upper-triangular Rz of order n with a
+    decaying spectrum, the shape C3 reaches at chi = 1024 (eta = 1126): ms per decomposition,
+    Jacobi sweeps, and the error of the eigenvalues against numpy (FP64, host)."""
+    import torch
+    from paper_2212_09782_b300 import lib as L
+    from paper_2212_09782_b300 import workloads as W
+    n = args.eig_n
+    r = W.rng(W.BASE_SEED + n)
+    A = W.complex_gaussian(r, (n, n)) * np.exp(-np.arange(n) / (n / 6))[None, :]
+    Rz = np.linalg.qr(A)[1]
+    dt = torch.complex128 if args.precision == "c128" else torch.complex64
+    Rd = torch.from_numpy(Rz).to(device="cuda", dtype=dt)
+    for _ in range(args.warmup):
+        w, Vh, sw = L.cbe_decompose(args.precision, Rd)
+    torch.cuda.synchronize()
+    n0 = L.launch_count()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        w, Vh, sw = L.cbe_decompose(args.precision, Rd)
+    b.record()
+    torch.cuda.synchronize()
+    L.stream_check()
+    ms = a.elapsed_time(b) / args.steps
+    Rr = Rd.cpu().numpy().astype(np.complex128)
+    ref = np.sort(np.linalg.eigvalsh(Rr @ Rr.conj().T))[::-1]
+    wv, V = w.cpu().numpy(), Vh.cpu().numpy()
+    line = {"metric": "CBE step (iv) decompositions/s (L^dag L = V^dag S^2 V)", "value": 1e3 / ms,
+            "unit": "decompositions/s", "ms_per_step": ms, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "n_gpus": 1, "dtype": args.precision, "data": "synthetic",
+            "sweeps": int(sw.item()), "gpu_launches": L.launch_count() - n0,
+            "max_abs_dw_over_w0": float(np.abs(wv - ref).max() / ref[0]),
+            "max_abs_VVdag_minus_1": float(np.abs(V @ V.conj().T - np.eye(n)).max()),
+            "config": {"workload": f"CBE decomposition n={n} (Rz = R of a Gaussian matrix with "
+                                   f"column scales exp(-6 j / n))"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_c1(args):
     """C1: finite chain L = 16, d = 3, g = 1.5, quench from |0...0>, Strang dt = 0.05,
     20 steps, chi_max = 32, plain QR, complex128. The whole run on the GPU (wall time,
@@ -677,7 +717,9 @@ def main():
     ap.add_argument("--d", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", choices=["bond", "chain", "serve", "svd", "c1", "c3"], default="bond")
+    ap.add_argument("--workload", choices=["bond", "chain", "serve", "svd", "c1", "c3", "cbe_eig"],
+                    default="bond")
+    ap.add_argument("--eig-n", type=int, default=1126, help="cbe_eig workload: the order n")
     ap.add_argument("--c3-steps", type=int, default=200)
     ap.add_argument("--c3-seconds", type=float, default=240.0)
     ap.add_argument("--serve-requests", type=int, default=12)
@@ -707,6 +749,8 @@ def main():
         return run_c1(args)
     if args.workload == "c3":
         return run_c3(args)
+    if args.workload == "cbe_eig":
+        return run_cbe_eig(args)
     return run_ours(args)
 
 
