@@ -172,6 +172,8 @@ __device__ __forceinline__ void reflector(T xn2, T alr, T ali, T& beta, T& tr, T
   }
 }
 
+template <typename T> struct __align__(16) VXp { cx<T> v, x; };
+
 template <typename T> struct PanelSmem {
   static constexpr int HDR = 16;
   static constexpr int MSG = HDR + SLOTS * (int)sizeof(cx<T>);
@@ -189,7 +191,7 @@ template <typename T> struct PanelSmem {
 // local rows: the panel's first kb rows (every CTA) followed by this CTA's slab
 template <typename T> __host__ __device__ inline size_t panel_smem_bytes(int rps, int kb) {
   const size_t rows = (size_t)kb + rps;
-  return a16(rows * (kb + 1) * sizeof(cx<T>)) + a16(rows * sizeof(cx<T>)) + PanelSmem<T>::fixed(PT / 32);
+  return a16(rows * (kb + 1) * sizeof(cx<T>)) + a16(rows * 2 * sizeof(cx<T>)) + PanelSmem<T>::fixed(PT / 32);
 }
 template <typename T>
 __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
@@ -215,7 +217,9 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
 
   unsigned char* q = sm;
   cx<T>* P = reinterpret_cast<cx<T>*>(q); q += a16((size_t)(kb + rps) * ldp * sizeof(cx<T>));
-  cx<T>* VB = reinterpret_cast<cx<T>*>(q); q += a16((size_t)(kb + rps) * sizeof(cx<T>));
+  // per row: v of the reflector being applied and x of the next pivot column, side by side
+  // so that phase 2 reads both with one broadcast load
+  VXp<T>* VX = reinterpret_cast<VXp<T>*>(q); q += a16((size_t)(kb + rps) * sizeof(VXp<T>));
   unsigned char* recvm = q; q += a16(2 * 16 * L::MSG);
   cx<T>* pivb = reinterpret_cast<cx<T>*>(q); q += a16(2 * SLOTS * sizeof(cx<T>));
   T* wpn = reinterpret_cast<T*>(q); q += a16((size_t)NW * 16);
@@ -264,10 +268,10 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
       if (jp >= 0) { v0 = (p == jp) ? mk<T>(1, 0) : cmul<T>(scale, u0); v1 = cmul<T>(scale, u1); }
       r0 = csub<T>(r0, cmul<T>(v0, cwn));
       r1 = csub<T>(r1, cmul<T>(v1, cwn));
-      P[p * ldp + jn] = r0; VB[p] = v0;
+      P[p * ldp + jn] = r0; VX[p] = VXp<T>{v0, r0};
       if (p > jn && (top_counts || p >= kb)) { nacc.add_sq(r0.x); nacc.add_sq(r0.y); }
       if (two) {
-        P[(p + 32) * ldp + jn] = r1; VB[p + 32] = v1;
+        P[(p + 32) * ldp + jn] = r1; VX[p + 32] = VXp<T>{v1, r1};
         if (p + 32 > jn && (top_counts || p + 32 >= kb)) { nacc.add_sq(r1.x); nacc.add_sq(r1.y); }
       }
     }
@@ -278,7 +282,7 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
     const int slo = max(plo, min(p1, jn + 1));
     const int alo = top_counts ? slo : max(slo, min(p1, kb));
     for (int p = plo; p < alo; ++p) {
-      const cx<T> y = csub<T>(P[p * ldp + col], cmul<T>(VB[p], cw));
+      const cx<T> y = csub<T>(P[p * ldp + col], cmul<T>(VX[p].v, cw));
       if (upd) P[p * ldp + col] = y;
     }
     cx<T> acc0 = zero, acc1 = zero;
@@ -286,7 +290,10 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
     for (; p + 3 < p1; p += 4) {
       cx<T> v[4], x[4], y[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) { v[u] = VB[p + u]; x[u] = P[(p + u) * ldp + jn]; y[u] = P[(p + u) * ldp + col]; }
+      for (int u = 0; u < 4; ++u) {
+        const VXp<T> t = VX[p + u];
+        v[u] = t.v; x[u] = t.x; y[u] = P[(p + u) * ldp + col];
+      }
 #pragma unroll
       for (int u = 0; u < 4; ++u) y[u] = csub<T>(y[u], cmul<T>(v[u], cw));
       if (upd) {
@@ -299,7 +306,8 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
       cfma<T>(acc1, cconj<T>(x[3]), y[3]);
     }
     for (; p < p1; ++p) {
-      const cx<T> v0 = VB[p], x0 = P[p * ldp + jn];
+      const VXp<T> t = VX[p];
+      const cx<T> v0 = t.v, x0 = t.x;
       const cx<T> y0 = csub<T>(P[p * ldp + col], cmul<T>(v0, cw));
       if (upd) P[p * ldp + col] = y0;
       cfma<T>(acc0, cconj<T>(x0), y0);
