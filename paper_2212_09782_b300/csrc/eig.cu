@@ -155,10 +155,10 @@ __global__ void k_sort_out(const double2* A, const double2* V, int n, double* w,
 // Blocked: the rows form blocks of br (8, 4, 2 or 1, the largest whose block pair fits
 // shared memory; the row count is padded with zero rows to a multiple of br). A sweep
 // pairs the blocks in the round-robin order (nb'/2 disjoint block pairs per round, nb'-1
-// rounds); one CTA per block pair loads its 2 br rows into shared memory, runs one
-// sweep over all pairs among them (2 br - 1 inner rounds of br disjoint pairs, a warp per
-// pair), writes them back and applies the accumulated 2br x 2br rotation W to the same
-// rows of Jt. A grid barrier separates the rounds; sweeps repeat until one applies no
+// rounds); one CTA per block pair loads its 2 br rows into shared memory, rotates its
+// br^2 cross pairs (br inner rounds of br disjoint pairs), writes the rows back and applies
+// the accumulated 2br x 2br rotation W to the same rows of Jt; the pairs inside a block
+// get one such visit per sweep before the rounds. A grid barrier separates the rounds; sweeps repeat until one applies no
 // rotation (at most SJ_MAX_SWEEPS). No FP64 instruction in the loop (B300's FP64 pipe,
 // about one FMA per clock per SM, made the reductions alone the critical path): the rows
 // are FP32, four FP32 partial sums per lane are combined across the warp in double-float
@@ -171,9 +171,10 @@ __global__ void k_sort_out(const double2* A, const double2* V, int n, double* w,
 // normalised (at n = 1126 this took the rows' orthonormality from 3e-5 to 3e-6 and
 // sum_i S_i^2 to within 1e-7 of ||Rz||^2). Global loads bypass L1 (ld.global.cg): other
 // CTAs rewrite rows between rounds.
-constexpr int SJ_NT = 256;
-constexpr int SJ_MAX_SWEEPS = 40;
 constexpr int SJ_BRMAX = 8;
+constexpr int SJ_WPP = 2;                        // warps per row pair
+constexpr int SJ_NT = 32 * SJ_WPP * SJ_BRMAX;    // 512: SJ_WPP warps for each of br pairs
+constexpr int SJ_MAX_SWEEPS = 40;
 struct SjCtl {
   unsigned bar[2];
   unsigned rot[SJ_MAX_SWEEPS];  // rotations applied per sweep
@@ -196,9 +197,9 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
   const float h = s + e;
   return DF{h, e - (h - s)};
 }
-// the lane's four partial sums, then the whole warp (every lane ends with the total)
-__device__ __forceinline__ DF warp_sum_df(const float f[4]) {
-  DF v = df_add(df_add(DF{f[0], 0.f}, DF{f[1], 0.f}), df_add(DF{f[2], 0.f}, DF{f[3], 0.f}));
+// the lane's two partial sums, then the whole warp (every lane ends with the total)
+__device__ __forceinline__ DF warp_sum_df2(const float f[2]) {
+  DF v = df_add(DF{f[0], 0.f}, DF{f[1], 0.f});
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1)
     v = df_add(v, DF{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
@@ -209,129 +210,182 @@ __host__ __device__ inline size_t sj_smem_bytes(int n, int br) {
   return (size_t)2 * br * n * sizeof(float2) + (size_t)(2 * SJ_BRMAX) * (2 * SJ_BRMAX) * sizeof(float2);
 }
 
-// n: the row length (even; a zero column pads an odd order), nb: blocks of br rows
-__global__ void __launch_bounds__(SJ_NT) k_sj_sweeps(float2* R, float2* Jt, int n, int br, int nb,
-                                                     double tol, SjCtl* ctl, unsigned* err) {
+// n: the row length (even; a zero column pads an odd order), nb: blocks of br rows.
+// A sweep visits every row pair once: first each block alone (its br(br-1)/2 pairs, one
+// CTA per block), then the block round robin, where a block pair's visit handles only its
+// br x br cross pairs (br inner rounds pairing row i of the first block with row
+// (i + j) mod br of the second). SJ_WPP warps share a row pair: each sums its share of the
+// row, the pair's warps combine their partials through shared memory behind a named
+// barrier, and each then forms the same rotation and applies it to its own share.
+__global__ void __launch_bounds__(SJ_NT, 1) k_sj_sweeps(float2* R, float2* Jt, int n, int br, int nb,
+                                                        double tol, SjCtl* ctl, unsigned* err) {
   extern __shared__ __align__(16) unsigned char sj_sm[];
   float2* X = reinterpret_cast<float2*>(sj_sm);              // [2 br][n]
   float2* Wm = X + (size_t)2 * br * n;                         // [2 br][2 br]
+  __shared__ float red[SJ_BRMAX][SJ_WPP][4];                   // per pair slot and warp: g (hi, lo)
+  __shared__ DF nrm[2 * SJ_BRMAX];                             // ||row||^2 of the rows held
   __shared__ unsigned s_cnt, s_vis;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nr = 2 * br;                    // rows held per visit
+  const int quad = warp / SJ_WPP, qw = warp % SJ_WPP;          // pair slot, warp within it
+  const int qt = qw * 32 + lane;                               // thread within the pair slot
   const int nbp = (nb % 2) ? nb + 1 : nb;   // blocks, with an idle partner when odd
   const float tolf = (float)tol;
+
+  // One visit: rows grow(0..nrow-1) into shared memory, the inner rounds (cross: br rounds
+  // of br pairs between the halves; else the round robin among the nrow rows), then the
+  // rows back and W applied to the same rows of Jt when anything rotated.
+  auto visit = [&](int nrow, bool cross, auto grow) {
+    {
+      // 16-byte asynchronous copies that bypass L1, all in flight at once (n is even: rows
+      // are 16-byte aligned)
+      const int h = n / 2, tot = nrow * h;
+      for (int idx = tid; idx < tot; idx += SJ_NT) {
+        const int a = idx / h, o = 2 * (idx - a * h);
+        const float2* src = R + (long long)grow(a) * n + o;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                         (unsigned)__cvta_generic_to_shared(X + (size_t)a * n + o)),
+                     "l"(src)
+                     : "memory");
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    for (int e = tid; e < nrow * nrow; e += SJ_NT) Wm[e] = make_float2(e / nrow == e % nrow ? 1.f : 0.f, 0.f);
+    if (tid == 0) s_vis = 0;
+    __syncthreads();
+    // the rows' squared norms once per visit (double-float); each rotation then updates them
+    // in closed form, a' = a - t|g|, b' = b + t|g|, so the inner rounds sum only g
+    for (int a = warp; a < nrow; a += SJ_NT / 32) {
+      const float2* xr = X + (size_t)a * n;
+      float f[2] = {0.f, 0.f};
+      int i = lane;
+      for (; i + 32 < n; i += 64) {
+        const float2 x = xr[i], y = xr[i + 32];
+        f[0] = fmaf(x.x, x.x, fmaf(x.y, x.y, f[0]));
+        f[1] = fmaf(y.x, y.x, fmaf(y.y, y.y, f[1]));
+      }
+      if (i < n) { const float2 x = xr[i]; f[0] = fmaf(x.x, x.x, fmaf(x.y, x.y, f[0])); }
+      const DF v = warp_sum_df2(f);
+      if (lane == 0) nrm[a] = v;
+    }
+    __syncthreads();
+    const int rounds = cross ? br : nrow - 1;
+    const int pairs = cross ? br : nrow / 2;
+    for (int ir = 0; ir < rounds; ++ir) {
+      if (quad < pairs) {                   // slot-uniform
+        int a, b;
+        if (cross) { a = quad; b = br + (quad + ir) % br; }
+        else pair_of(ir, quad, nrow, a, b);
+        float2* xa = X + (size_t)a * n;
+        float2* xb = X + (size_t)b * n;
+        float fr[2] = {0, 0}, fi[2] = {0, 0};
+        auto acc = [&](int u, int j) {
+          const float2 x = xa[j], y = xb[j];
+          fr[u] = fmaf(x.x, y.x, fmaf(x.y, y.y, fr[u]));   // Re(x conj y)
+          fi[u] = fmaf(x.y, y.x, fmaf(-x.x, y.y, fi[u]));  // Im(x conj y)
+        };
+        constexpr int QT = 32 * SJ_WPP;
+        int i = qt;
+        for (; i + QT < n; i += 2 * QT) { acc(0, i); acc(1, i + QT); }
+        if (i < n) acc(0, i);
+        DF sums[2] = {warp_sum_df2(fr), warp_sum_df2(fi)};
+        if (SJ_WPP > 1) {
+          if (lane == 0) {
+#pragma unroll
+            for (int v = 0; v < 2; ++v) { red[quad][qw][2 * v] = sums[v].hi; red[quad][qw][2 * v + 1] = sums[v].lo; }
+          }
+          asm volatile("bar.sync %0, %1;" ::"r"(1 + quad), "n"(32 * SJ_WPP) : "memory");
+#pragma unroll
+          for (int v = 0; v < 2; ++v) {     // the slot's total, in the same order in every warp
+            DF t{red[quad][0][2 * v], red[quad][0][2 * v + 1]};
+#pragma unroll
+            for (int w = 1; w < SJ_WPP; ++w) t = df_add(t, DF{red[quad][w][2 * v], red[quad][w][2 * v + 1]});
+            sums[v] = t;
+          }
+        }
+        const DF Ad = nrm[a], Bd = nrm[b];
+        const float A = Ad.hi, B = Bd.hi, Gr = sums[0].hi, Gi = sums[1].hi;
+        const float ab = hypotf(Gr, Gi);
+        if (ab > 0.f && ab > tolf * sqrtf(A) * sqrtf(B)) {  // slot-uniform
+          const float inv = 1.f / ab;
+          // z = (b - a) / 2|g| with b - a from the double-float norms (no cancellation)
+          const float z = ((Bd.hi - Ad.hi) + (Bd.lo - Ad.lo)) * (0.5f * inv);
+          // t = tan(theta); for |z| beyond 1e18, 1 + z^2 overflows and t = 1/(2z) ~ 0
+          const float t = fabsf(z) > 1e18f ? 0.5f / z
+                                           : copysignf(1.f, z) / (fabsf(z) + sqrtf(fmaf(z, z, 1.f)));
+          // c = 1/sqrt(1 + t^2) as 1 - t^2 / (q (1 + q)), q = sqrt(1 + t^2): rounded once,
+          // so that small rotations do not drift the norms (c ~ 1 - t^2/2 rounded to 1)
+          const float qq = sqrtf(fmaf(t, t, 1.f));
+          const float c = 1.f - (t * t) / (qq * (1.f + qq)), sn = t * c;
+          const float er = sn * (Gr * inv), ei = sn * (Gi * inv);
+          // row_a' = c x - (s e) y ; row_b' = conj(s e) x + c y (each warp its share)
+          for (int j2 = qt; j2 < n; j2 += QT) {
+            const float2 x = xa[j2], y = xb[j2];
+            xa[j2] = make_float2(c * x.x - (er * y.x - ei * y.y), c * x.y - (er * y.y + ei * y.x));
+            xb[j2] = make_float2((er * x.x + ei * x.y) + c * y.x, (er * x.y - ei * x.x) + c * y.y);
+          }
+          if (qw == 0) {
+            if (lane < nrow) {
+              const float2 x = Wm[a * nrow + lane], y = Wm[b * nrow + lane];
+              Wm[a * nrow + lane] = make_float2(c * x.x - (er * y.x - ei * y.y), c * x.y - (er * y.y + ei * y.x));
+              Wm[b * nrow + lane] = make_float2((er * x.x + ei * x.y) + c * y.x, (er * x.y - ei * x.x) + c * y.y);
+            }
+            if (lane == 0) {
+              atomicAdd(&s_vis, 1u);
+              const float tg = t * ab, tge = fmaf(t, ab, -tg);  // t|g| exactly as hi + lo
+              nrm[a] = df_add(Ad, DF{-tg, -tge});
+              nrm[b] = df_add(Bd, DF{tg, tge});
+            }
+          }
+        }
+      }
+      __syncthreads();  // the next inner round pairs other rows; red and nrm are reused
+    }
+    if (s_vis) {
+      const int h = n / 2, tot = nrow * h;
+      for (int idx = tid; idx < tot; idx += SJ_NT) {
+        const int a = idx / h, o = 2 * (idx - a * h);
+        *reinterpret_cast<float4*>(R + (long long)grow(a) * n + o) =
+            *reinterpret_cast<const float4*>(X + (size_t)a * n + o);
+      }
+      for (int c = tid; c < n; c += SJ_NT) {
+        float2 in[2 * SJ_BRMAX];
+#pragma unroll
+        for (int a = 0; a < 2 * SJ_BRMAX; ++a)
+          if (a < nrow) in[a] = __ldcg(Jt + (long long)grow(a) * n + c);
+#pragma unroll
+        for (int a = 0; a < 2 * SJ_BRMAX; ++a) {
+          if (a < nrow) {
+            float2 o = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int b = 0; b < 2 * SJ_BRMAX; ++b) {
+              if (b < nrow) {
+                const float2 wv = Wm[a * nrow + b];
+                o.x = fmaf(wv.x, in[b].x, fmaf(-wv.y, in[b].y, o.x));
+                o.y = fmaf(wv.x, in[b].y, fmaf(wv.y, in[b].x, o.y));
+              }
+            }
+            Jt[(long long)grow(a) * n + c] = o;
+          }
+        }
+      }
+      if (tid == 0) s_cnt += s_vis;
+    }
+    __syncthreads();  // X, Wm and s_vis are reused by the next visit
+  };
+
   for (int sweep = 0; sweep < SJ_MAX_SWEEPS; ++sweep) {
     if (tid == 0) s_cnt = 0;
-    for (int r = 0; r < nbp - 1; ++r) {
+    if (br > 1) {  // the pairs inside each block
+      for (int blk = blockIdx.x; blk < nb; blk += gridDim.x)
+        visit(br, false, [&](int a) { return blk * br + a; });
+      if (!grid_barrier(ctl->bar, gridDim.x, err)) return;
+    }
+    for (int r = 0; r < nbp - 1; ++r) {  // the cross pairs of each block pair
       for (int k = blockIdx.x; k < nbp / 2; k += gridDim.x) {
         int P, Q;
         pair_of(r, k, nbp, P, Q);
-        const bool haveQ = Q < nb;          // uniform in the CTA
-        const int rows = haveQ ? nr : br;
-        // global row of local row a: block P's rows, then block Q's
-        auto grow = [&](int a) { return a < br ? P * br + a : Q * br + (a - br); };
-        {
-          // the rows into shared memory: 16-byte asynchronous copies that bypass L1, all in
-          // flight at once (n is even: rows are 16-byte aligned)
-          const int h = n / 2, tot = rows * h;
-          for (int idx = tid; idx < tot; idx += SJ_NT) {
-            const int a = idx / h, o = 2 * (idx - a * h);
-            const float2* src = R + (long long)grow(a) * n + o;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                             (unsigned)__cvta_generic_to_shared(X + (size_t)a * n + o)),
-                         "l"(src)
-                         : "memory");
-          }
-          asm volatile("cp.async.wait_all;" ::: "memory");
-        }
-        for (int e = tid; e < nr * nr; e += SJ_NT) Wm[e] = make_float2(e / nr == e % nr ? 1.f : 0.f, 0.f);
-        if (tid == 0) s_vis = 0;
-        __syncthreads();
-        // one sweep over the pairs among the rows held (round robin, a warp per pair)
-        const int np2 = rows;               // even: br pairs per inner round when haveQ
-        for (int ir = 0; ir < np2 - 1; ++ir) {
-          if (warp < np2 / 2) {
-            int a, b;
-            pair_of(ir, warp, np2, a, b);
-            float2* xa = X + (size_t)a * n;
-            float2* xb = X + (size_t)b * n;
-            float fa[4] = {0, 0, 0, 0}, fb[4] = {0, 0, 0, 0}, fr[4] = {0, 0, 0, 0}, fi[4] = {0, 0, 0, 0};
-            auto acc = [&](int u, int j) {
-              const float2 x = xa[j], y = xb[j];
-              fa[u] = fmaf(x.x, x.x, fmaf(x.y, x.y, fa[u]));
-              fb[u] = fmaf(y.x, y.x, fmaf(y.y, y.y, fb[u]));
-              fr[u] = fmaf(x.x, y.x, fmaf(x.y, y.y, fr[u]));   // Re(x conj y)
-              fi[u] = fmaf(x.y, y.x, fmaf(-x.x, y.y, fi[u]));  // Im(x conj y)
-            };
-            int i = lane;
-            for (; i + 96 < n; i += 128) {
-#pragma unroll
-              for (int u = 0; u < 4; ++u) acc(u, i + 32 * u);
-            }
-            for (; i < n; i += 32) acc(0, i);
-            const DF Ad = warp_sum_df(fa), Bd = warp_sum_df(fb), Grd = warp_sum_df(fr), Gid = warp_sum_df(fi);
-            const float A = Ad.hi, B = Bd.hi, Gr = Grd.hi, Gi = Gid.hi;
-            const float ab = hypotf(Gr, Gi);
-            // warp-uniform: every lane holds the same sums (xor reduction)
-            if (ab > 0.f && ab > tolf * sqrtf(A) * sqrtf(B)) {
-              // z = (b - a) / 2|g| with b - a from the double-float sums (no cancellation)
-              const float z = ((Bd.hi - Ad.hi) + (Bd.lo - Ad.lo)) / (2.f * ab);
-              // t = tan(theta); for |z| beyond 1e18, 1 + z^2 overflows and t = 1/(2z) ~ 0
-              const float t = fabsf(z) > 1e18f ? 0.5f / z
-                                               : copysignf(1.f, z) / (fabsf(z) + sqrtf(fmaf(z, z, 1.f)));
-              // c = 1/sqrt(1 + t^2) as 1 - t^2 / (q (1 + q)), q = sqrt(1 + t^2): rounded once,
-              // so that small rotations do not drift the norms (c ~ 1 - t^2/2 rounded to 1)
-              const float qq = sqrtf(fmaf(t, t, 1.f));
-              const float c = 1.f - (t * t) / (qq * (1.f + qq)), sn = t * c;
-              const float er = sn * (Gr / ab), ei = sn * (Gi / ab);
-              // row_a' = c x - (s e) y ; row_b' = conj(s e) x + c y
-              for (int j = lane; j < n; j += 32) {
-                const float2 x = xa[j], y = xb[j];
-                xa[j] = make_float2(c * x.x - (er * y.x - ei * y.y), c * x.y - (er * y.y + ei * y.x));
-                xb[j] = make_float2((er * x.x + ei * x.y) + c * y.x, (er * x.y - ei * x.x) + c * y.y);
-              }
-              if (lane < nr) {
-                const float2 x = Wm[a * nr + lane], y = Wm[b * nr + lane];
-                Wm[a * nr + lane] = make_float2(c * x.x - (er * y.x - ei * y.y), c * x.y - (er * y.y + ei * y.x));
-                Wm[b * nr + lane] = make_float2((er * x.x + ei * x.y) + c * y.x, (er * x.y - ei * x.x) + c * y.y);
-              }
-              if (lane == 0) { atomicAdd(&s_vis, 1u); }
-            }
-          }
-          __syncthreads();
-        }
-        // when anything rotated: the rows back, and Jt rows <- W (Jt rows)
-        if (s_vis) {
-          const int h = n / 2, tot = rows * h;
-          for (int idx = tid; idx < tot; idx += SJ_NT) {
-            const int a = idx / h, o = 2 * (idx - a * h);
-            *reinterpret_cast<float4*>(R + (long long)grow(a) * n + o) =
-                *reinterpret_cast<const float4*>(X + (size_t)a * n + o);
-          }
-          for (int c = tid; c < n; c += SJ_NT) {
-            float2 in[2 * SJ_BRMAX];
-#pragma unroll
-            for (int a = 0; a < 2 * SJ_BRMAX; ++a)
-              if (a < rows) in[a] = __ldcg(Jt + (long long)grow(a) * n + c);
-#pragma unroll
-            for (int a = 0; a < 2 * SJ_BRMAX; ++a) {
-              if (a < rows) {
-                float2 o = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int b = 0; b < 2 * SJ_BRMAX; ++b) {
-                  if (b < rows) {
-                    const float2 wv = Wm[a * nr + b];
-                    o.x = fmaf(wv.x, in[b].x, fmaf(-wv.y, in[b].y, o.x));
-                    o.y = fmaf(wv.x, in[b].y, fmaf(wv.y, in[b].x, o.y));
-                  }
-                }
-                Jt[(long long)grow(a) * n + c] = o;
-              }
-            }
-          }
-          if (tid == 0) s_cnt += s_vis;
-        }
-        __syncthreads();  // X, Wm and s_vis are reused by this CTA's next block pair
+        if (Q < nb)                          // uniform in the CTA; the idle partner has none
+          visit(2 * br, true, [&](int a) { return a < br ? P * br + a : Q * br + (a - br); });
       }
       if (!grid_barrier(ctl->bar, gridDim.x, err)) return;
     }
