@@ -131,13 +131,14 @@ __global__ void k_offnorm(const double2* A, int n, double* out) {
 __global__ void k_sort_out(const double2* A, const double2* V, int n, double* w, double2* Vh) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  double li = A[(long long)i * n + i].x;
+  auto key = [](double x) { return isnan(x) ? -INFINITY : x; };  // ranks stay a permutation
+  double li = key(A[(long long)i * n + i].x);
   int rank = 0;
   for (int j = 0; j < n; ++j) {
-    double lj = A[(long long)j * n + j].x;
+    double lj = key(A[(long long)j * n + j].x);
     if (lj > li || (lj == li && j < i)) ++rank;
   }
-  w[rank] = li;
+  w[rank] = A[(long long)i * n + i].x;
   for (int r = 0; r < n; ++r) {
     double2 v = V[(long long)r * n + i];
     Vh[(long long)rank * n + r] = make_double2(v.x, -v.y);
@@ -152,17 +153,19 @@ __global__ void k_sort_out(const double2* A, const double2* V, int n, double* w,
 // singular values. A pair's rotation is the 2 x 2 Hermitian Jacobi step of the rows'
 // Gram matrix [[a, g], [conj g, b]] (a = ||r_p||^2, b = ||r_q||^2, g = r_p r_q^dag), as in
 // k_jac_rot: rows p, q <- G^dag (rows p, q).
-// Blocked: the rows form blocks of br (8, 4, 2 or 1, the largest whose block pair fits
+// Blocked: the rows form blocks of br (4, 2 or 1, the largest whose block pair fits
 // shared memory; the row count is padded with zero rows to a multiple of br). A sweep
 // pairs the blocks in the round-robin order (nb'/2 disjoint block pairs per round, nb'-1
 // rounds); one CTA per block pair loads its 2 br rows into shared memory, rotates its
 // br^2 cross pairs (br inner rounds of br disjoint pairs), writes the rows back and applies
 // the accumulated 2br x 2br rotation W to the same rows of Jt; the pairs inside a block
-// get one such visit per sweep before the rounds. A grid barrier separates the rounds; sweeps repeat until one applies no
-// rotation (at most SJ_MAX_SWEEPS). No FP64 instruction in the loop (B300's FP64 pipe,
-// about one FMA per clock per SM, made the reductions alone the critical path): the rows
-// are FP32, four FP32 partial sums per lane are combined across the warp in double-float
-// (TwoSum), and the rotation is formed in FP32 from those sums with c = 1 - t^2/(q(1+q)),
+// get one such visit per sweep before the rounds. A grid barrier separates the rounds;
+// sweeps repeat until one applies no rotation (at most SJ_MAX_SWEEPS). No FP64
+// instruction in the loop (B300's FP64 pipe, about one FMA per clock per SM, made the
+// reductions alone the critical path): the rows are FP32, the partial sums of r_a r_b^dag
+// are combined across the pair's warps in double-float (TwoSum), the rows' squared norms
+// are summed the same way once per visit and then updated in closed form by each rotation,
+// and the rotation is formed in FP32 from those sums with c = 1 - t^2/(q(1+q)),
 // q = sqrt(1+t^2), rounded once. Both matter: an FP32 tree, or c = 1/q directly, each
 // left the singular values ~10x less accurate (an FP32 emulation at n = 256: 1.4e-5 vs
 // 1.1e-6 relative to the largest squared value). The rotations are unitary only to
@@ -171,9 +174,9 @@ __global__ void k_sort_out(const double2* A, const double2* V, int n, double* w,
 // normalised (at n = 1126 this took the rows' orthonormality from 3e-5 to 3e-6 and
 // sum_i S_i^2 to within 1e-7 of ||Rz||^2). Global loads bypass L1 (ld.global.cg): other
 // CTAs rewrite rows between rounds.
-constexpr int SJ_BRMAX = 8;
+constexpr int SJ_BRMAX = 4;                      // rows per block (8 and 2 measured slower)
 constexpr int SJ_WPP = 2;                        // warps per row pair
-constexpr int SJ_NT = 32 * SJ_WPP * SJ_BRMAX;    // 512: SJ_WPP warps for each of br pairs
+constexpr int SJ_NT = 32 * SJ_WPP * SJ_BRMAX;    // 256: SJ_WPP warps for each of br pairs
 constexpr int SJ_MAX_SWEEPS = 40;
 struct SjCtl {
   unsigned bar[2];
@@ -305,7 +308,9 @@ __global__ void __launch_bounds__(SJ_NT, 1) k_sj_sweeps(float2* R, float2* Jt, i
         const DF Ad = nrm[a], Bd = nrm[b];
         const float A = Ad.hi, B = Bd.hi, Gr = sums[0].hi, Gi = sums[1].hi;
         const float ab = hypotf(Gr, Gi);
-        if (ab > 0.f && ab > tolf * sqrtf(A) * sqrtf(B)) {  // slot-uniform
+        // |g| below 1e-30 is a product of rows at the FP32 noise floor of a unit-norm
+        // matrix; the floor also keeps 1/|g| finite (a denormal |g| overflowed it)
+        if (ab > 1e-30f && ab > tolf * sqrtf(A) * sqrtf(B)) {  // slot-uniform
           const float inv = 1.f / ab;
           // z = (b - a) / 2|g| with b - a from the double-float norms (no cancellation)
           const float z = ((Bd.hi - Ad.hi) + (Bd.lo - Ad.lo)) * (0.5f * inv);
@@ -426,27 +431,34 @@ __global__ void k_sj_norms(const float2* R, const float2* Jt, int n, int ld, dou
   }
 }
 
-// descending order of s2 (stable): w[rank] = s2[i], order[rank] = i
+// descending order of s2 (stable): w[rank] = s2[i], order[rank] = i. A NaN sorts as -inf,
+// so the ranks are a permutation whatever the values (order[] is then fully written).
 __global__ void k_sj_rank(const double* s2, int n, double* w, int* order) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double li = s2[i];
+  auto key = [](double x) { return isnan(x) ? -INFINITY : x; };
+  const double li = key(s2[i]);
   int rank = 0;
   for (int j = 0; j < n; ++j) {
-    const double lj = s2[j];
+    const double lj = key(s2[j]);
     if (lj > li || (lj == li && j < i)) ++rank;
   }
-  w[rank] = li;
+  w[rank] = s2[i];
   order[rank] = i;
 }
 
-// Vh[rank] = row order[rank] of Jt, normalised (FP64)
+// Vh[rank] = row order[rank] of Jt, normalised (FP64); an index out of range (impossible
+// while order is a permutation) sets DEVERR_BOUNDS and is skipped
 __global__ void k_sj_gather(const float2* Jt, const int* order, const double* jn, int n, int ld,
-                            double2* Vh) {
+                            double2* Vh, unsigned* err) {
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= (long long)n * n) return;
   const int r = (int)(idx / n), c = (int)(idx % n);
   const int src = order[r];
+  if (src < 0 || src >= n) {
+    if (c == 0) atomicOr(err, DEVERR_BOUNDS);
+    return;
+  }
   const float2 v = Jt[(long long)src * ld + c];
   const double f = jn[src];
   Vh[idx] = make_double2(f * v.x, f * v.y);
@@ -527,7 +539,7 @@ int svd_rows_jacobi32(const float2* Rz, long long ldr, int n, double* w, double2
   note_launch();
   k_sj_rank<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(s2, n, w, order);
   note_launch();
-  k_sj_gather<<<(unsigned)ceil_div((long long)n * n, 256), 256, 0, st>>>(Jt, order, jn, n, ld, Vh);
+  k_sj_gather<<<(unsigned)ceil_div((long long)n * n, 256), 256, 0, st>>>(Jt, order, jn, n, ld, Vh, err);
   note_launch();
   QR_CUDA_TRY(cudaGetLastError());
   if (sweeps) QR_CUDA_TRY(cudaMemcpyAsync(sweeps, &ctl->sweeps, sizeof(int), cudaMemcpyDeviceToDevice, st));

@@ -218,17 +218,20 @@ def test_reorth_restores_isometry(prec):
 
 def _spectrum_matrix(r, n, spec):
     """A square matrix U diag(s) W^dag with a chosen singular spectrum s (descending)."""
-    s = {"flat": np.ones(n), "graded": 10.0 ** (-6.0 * np.arange(n) / max(n - 1, 1)),
-         "decay": np.exp(-np.arange(n) / max(n / 8, 1)),
-         "rankdef": np.r_[np.linspace(1, 0.1, n - n // 2), np.zeros(n // 2)]}[spec]
+    s = {"flat": lambda: np.ones(n), "graded": lambda: 10.0 ** (-6.0 * np.arange(n) / max(n - 1, 1)),
+         "decay": lambda: np.exp(-np.arange(n) / max(n / 8, 1)),
+         "rankdef": lambda: np.r_[np.linspace(1, 0.1, n - n // 2), np.zeros(n // 2)],
+         # values whose row products underflow FP32 (the product-state start of a CBE run)
+         "underflow": lambda: np.r_[1.0, 0.5, 10.0 ** -np.linspace(18, 30, n - 2)]}[spec]()
     U = np.linalg.qr(W.complex_gaussian(r, (n, n)))[0]
     V = np.linalg.qr(W.complex_gaussian(r, (n, n)))[0]
     return (U * s) @ V.conj().T, s
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64_3xtf32"])
-@pytest.mark.parametrize("n,spec", [(1, "flat"), (2, "flat"), (17, "graded"), (64, "rankdef"),
-                                    (128, "graded"), (257, "decay"), (300, "flat")])
+@pytest.mark.parametrize("n,spec", [(1, "flat"), (2, "flat"), (5, "underflow"), (17, "graded"),
+                                    (33, "underflow"), (64, "rankdef"), (128, "graded"),
+                                    (257, "decay"), (300, "flat")])
 def test_cbe_decompose(prec, n, spec):
     # step (iv) alone: w = eigenvalues of Rz Rz^dag (= s^2), descending; the rows of Vh are
     # orthonormal and diagonalise Rz Rz^dag (degenerate spectra: any basis of each eigenspace)
@@ -241,6 +244,7 @@ def test_cbe_decompose(prec, n, spec):
     w, Vh, sweeps = L.cbe_decompose(prec, to_dev(Rz, prec))
     L.stream_check()
     w, Vh, sweeps = w.cpu().numpy(), Vh.cpu().numpy(), int(sweeps.item())
+    assert np.all(np.isfinite(w)) and np.all(np.isfinite(Vh))
     # complex64: FP32 rows and rotations (~sqrt(sweeps * n) roundings per row; measured
     # up to 7.2e-6 at n = 257)
     tol = 1e-12 if prec == "c128" else 2e-5
