@@ -46,7 +46,7 @@ FP64_ALU_TFLOPS = 1.25
 # complex64, 2464 x 32 panel, 680192 bytes read, 0 written, against 3 x 2464 x 32 x 8
 # algorithmic bytes). Traffic grows with the panel's rows, so a launch's traffic is this
 # ratio times its algorithmic bytes.
-PANEL_NCU_DRAM_OVER_ALGORITHMIC = 680192 / (3 * 2464 * 32 * 8)
+PANEL_NCU_DRAM_OVER_ALGORITHMIC = 675328 / (3 * 2464 * 32 * 8)
 
 
 def prof_families(L):
@@ -250,8 +250,12 @@ def run_ours(args):
     up = L.BondUpdater(prec, chi, d, chi, chi, tr, xi_kind=0, theta_given=True)
     stream = torch.cuda.current_stream()
     tune = None
-    if args.autotune:  # tile shapes of this update's tensor-core products, before any timing
+    if args.autotune_load:  # a table tuned earlier (e.g. outside a profiler)
+        tune = {"loaded_entries": L.autotune_load(args.autotune_load), "from": args.autotune_load}
+    elif args.autotune:  # tile shapes of this update's tensor-core products, before any timing
         tune = autotune_shapes(L, prec, [(chi, d, chi, chi)], tr, xi_kind=0, theta_given=True)
+    if args.autotune_save:
+        L.autotune_save(args.autotune_save)
 
     def barrier():
         torch.cuda.synchronize()
@@ -727,6 +731,11 @@ def main():
     ap.add_argument("--chain-L", type=int, default=128)
     ap.add_argument("--chain-chi", type=int, default=512)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--autotune-save", default=None,
+                    help="bond workload: write the tuned table (JSON) after tuning")
+    ap.add_argument("--autotune-load", default=None,
+                    help="bond workload: load a tuned table instead of tuning (for runs under a "
+                         "profiler, whose serialised replay would skew the tuner's timings)")
     ap.add_argument("--reorth", type=int, default=-1, choices=[-1, 0, 1],
                     help="re-orthogonalisation pass (qrtebd_trunc.reorth; -1 = the library default)")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",

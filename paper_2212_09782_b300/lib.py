@@ -471,6 +471,23 @@ def autotune_clear():
     _lib.qrtebd_autotune_clear()
 
 
+def autotune_save(path):
+    """Write the autotuner's table as JSON (shape, config, timings per entry)."""
+    import json
+    with open(path, "w") as f:
+        json.dump(autotune_entries(), f)
+
+
+def autotune_load(path):
+    """Insert every entry of a table written by autotune_save; returns the entry count."""
+    import json
+    with open(path) as f:
+        ents = json.load(f)
+    for e in ents:
+        autotune_set(tuple(e["shape"]), tuple(e["config"]))
+    return len(ents)
+
+
 def layer_workers():
     """Worker streams (and bond-update workspaces) of the batched-layer executor."""
     return int(_lib.qrtebd_layer_workers())

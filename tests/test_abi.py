@@ -110,3 +110,19 @@ def test_autotune_table_host(L):
         assert n.value == 0
     finally:
         L.autotune_clear()
+
+
+def test_autotune_table_save_load(L, tmp_path):
+    # a table saved as JSON and loaded again gives the same shapes and configurations
+    L.autotune_clear()
+    try:
+        L.autotune_set((1024, 128, 5120, 1), (128, 8, 0))
+        L.autotune_set((4992, 896, 128, 1), (256, 1, 0))
+        path = str(tmp_path / "tune.json")
+        L.autotune_save(path)
+        before = [(e["shape"], e["config"]) for e in L.autotune_entries()]
+        L.autotune_clear()
+        assert L.autotune_load(path) == 2
+        assert [(e["shape"], e["config"]) for e in L.autotune_entries()] == before
+    finally:
+        L.autotune_clear()
