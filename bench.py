@@ -191,13 +191,14 @@ def job_throughput(units_per_rank, ws, t_max_ms):
     return ws * units_per_rank / (t_max_ms / 1e3)
 
 
-def cpu_oracle_update(wl, chi):
+def cpu_oracle_update(wl, chi, want_result=False):
     from oracle import bond
     th = wl["theta"].astype(np.complex128)
     Bn = wl["Bn"].astype(np.complex128)
     t0 = time.perf_counter()
-    bond.qr_update(None, None, Bn, wl["U"], chi_max=chi, theta=th)
-    return time.perf_counter() - t0
+    out = bond.qr_update(None, None, Bn, wl["U"], chi_max=chi, theta=th)
+    dt = time.perf_counter() - t0
+    return (dt, out) if want_result else dt
 
 
 def run_reference(args):
@@ -385,10 +386,19 @@ def run_ours(args):
     roof = roofs.get(PROF_NAMES[dom])
 
     cpu = None
+    err = None
     if not args.no_cpu_baseline and ws == 1:
-        t = cpu_oracle_update(wl, chi)
+        t, orc = cpu_oracle_update(wl, chi, want_result=True)
         cpu = {"value": 1.0 / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"1 full bond update chi={chi} d={d} (complex128 NumPy/LAPACK)"}
+        # the timed update's result against the FP64 oracle on the same inputs (gauge
+        # invariant: the Schmidt values of Xi~ and eps)
+        _bm, xi_g, _bn, st_g = up.outputs()
+        s_g = np.linalg.svd(xi_g.cpu().numpy().astype(np.complex128), compute_uv=False)
+        s_o = np.linalg.svd(orc["Xi_new"], compute_uv=False)
+        err = {"schmidt_rel": float(np.linalg.norm(s_g - s_o) / np.linalg.norm(s_o)),
+               "eps_rel": float(abs(float(st_g[0]) - orc["eps"]) / orc["eps"]),
+               "reference": "oracle (complex128), same inputs"}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -405,7 +415,7 @@ def run_ours(args):
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "kernel_breakdown": breakdown, "dominant_family": PROF_NAMES[dom],
         "roofline_by_family": roofs, "profiled_ms_per_step": prof_step_ms, "clocks": clk,
-        "autotune": tune,
+        "autotune": tune, "error_vs_oracle": err,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -132,7 +132,24 @@ def bond_workspace_size(precision, chi_l, d, chi_m, chi_r, trunc, xi_kind=1, the
 
 
 def _ptr(t):
-    return None if t is None else C.c_void_p(t.data_ptr())
+    """Device pointer of a tensor the C ABI reads as dense row-major data. A tensor with any
+    other strides (a transpose, a permuted view) would be read in the wrong order, so it is
+    refused rather than copied behind the caller's back."""
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError(f"the library takes contiguous (row-major) tensors; got shape "
+                         f"{tuple(t.shape)} with strides {t.stride()} (call .contiguous())")
+    return C.c_void_p(t.data_ptr())
+
+
+def _ptr_rows(t):
+    """Device pointer of a 2-D tensor passed with its row stride as the leading dimension:
+    rows may be spaced out, the elements of a row must be adjacent."""
+    if t.dim() != 2 or t.stride(1) != 1 or t.stride(0) < t.shape[1]:
+        raise ValueError(f"expected a 2-D tensor with unit column stride; got shape "
+                         f"{tuple(t.shape)} with strides {t.stride()}")
+    return C.c_void_p(t.data_ptr())
 
 
 def stream_handle(stream=None):
@@ -434,7 +451,7 @@ def cbe_decompose(precision, Rz, stream=None):
     nb = _lib.qrtebd_cbe_decompose_workspace_size(prec, n)
     ws = torch.empty(nb, dtype=torch.uint8, device=Rz.device)
     sw = torch.zeros(1, dtype=torch.int32, device=Rz.device)
-    check(_lib.qrtebd_cbe_decompose(prec, n, _ptr(Rz), Rz.stride(0), _ptr(w), _ptr(Vh), _ptr(ws), nb,
+    check(_lib.qrtebd_cbe_decompose(prec, n, _ptr_rows(Rz), Rz.stride(0), _ptr(w), _ptr(Vh), _ptr(ws), nb,
                                     _ptr(sw), stream_handle(stream)), "cbe_decompose")
     return w, Vh, sw
 

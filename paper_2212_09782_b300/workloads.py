@@ -32,7 +32,8 @@ def random_unitary(r, n):
 def random_right_isometry(r, chi_l, d, chi_r):
     """B of shape (chi_l, d, chi_r) with B B^dag = 1 over (d, chi_r); needs chi_l <= d chi_r."""
     q, _ = np.linalg.qr(complex_gaussian(r, (d * chi_r, chi_l)))
-    return q.conj().T.reshape(chi_l, d, chi_r)
+    # a transpose is a strided view: copy to the row-major layout the device code reads
+    return np.ascontiguousarray(q.conj().T.reshape(chi_l, d, chi_r))
 
 
 def bond_microbench(chi, d, seed=BASE_SEED + 2, dtype=np.complex64):
@@ -45,7 +46,8 @@ def bond_microbench(chi, d, seed=BASE_SEED + 2, dtype=np.complex64):
     th /= np.linalg.norm(th)
     U = random_unitary(r, d * d)
     Bn = random_right_isometry(r, chi, d, chi)
-    return {"theta": th.astype(dtype), "U": U, "Bn": Bn.astype(dtype)}
+    return {"theta": np.ascontiguousarray(th, dtype=dtype), "U": np.ascontiguousarray(U),
+            "Bn": np.ascontiguousarray(Bn, dtype=dtype)}
 
 
 def random_bond(chiL, d, chiM, chiR, seed, xi="dense"):

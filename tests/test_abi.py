@@ -126,3 +126,29 @@ def test_autotune_table_save_load(L, tmp_path):
         assert [(e["shape"], e["config"]) for e in L.autotune_entries()] == before
     finally:
         L.autotune_clear()
+
+
+def test_binding_refuses_strided_tensors(L):
+    # the C ABI reads dense row-major data: a transposed or permuted view would be read in
+    # the wrong order, so the binding refuses it instead of passing its base pointer
+    import torch
+    t = torch.zeros(4, 6, dtype=torch.complex64)
+    assert L._ptr(t) is not None
+    with pytest.raises(ValueError):
+        L._ptr(t.t())
+    with pytest.raises(ValueError):
+        L._ptr(torch.zeros(3, 4, 5, dtype=torch.complex64).permute(0, 2, 1))
+    # a row-strided block (leading dimension > width) is fine where the ABI takes it
+    big = torch.zeros(8, 8, dtype=torch.complex64)
+    assert L._ptr_rows(big[:4, :4]) is not None
+    with pytest.raises(ValueError):
+        L._ptr_rows(big.t())
+
+
+def test_workload_arrays_are_row_major():
+    from paper_2212_09782_b300 import workloads as W
+    wl = W.bond_microbench(16, 3)
+    for k in ("theta", "U", "Bn"):
+        assert wl[k].flags["C_CONTIGUOUS"], k
+    r = W.rng(1)
+    assert W.random_right_isometry(r, 5, 3, 4).flags["C_CONTIGUOUS"]
