@@ -261,3 +261,28 @@ def test_cbe_decompose(prec, n, spec):
         sv = np.sqrt(np.maximum(w, 0))
         sref = np.sqrt(np.maximum(ref, 0))
         assert np.abs(sv - sref).max() <= 1e-5 * sref[0]
+
+
+def test_inputs_passed_as_the_bench_does():
+    # bench.py hands the workload arrays to the binding as they come (torch.from_numpy +
+    # .cuda()), not through this suite's row-major copies: the same update must match the
+    # oracle that way too
+    import torch
+    from paper_2212_09782_b300 import lib as L
+    wl = W.bond_microbench(128, 5)
+    orc = bond.qr_update(None, None, wl["Bn"].astype(np.complex128), wl["U"], chi_max=128,
+                         theta=wl["theta"].astype(np.complex128))
+    up = L.BondUpdater("c64_3xtf32", 128, 5, 128, 128, L.trunc_default(L.PLAIN, 128), xi_kind=0,
+                       theta_given=True)
+    up.run(torch.from_numpy(wl["U"]).cuda(), torch.from_numpy(wl["Bn"]).cuda(),
+           theta=torch.from_numpy(wl["theta"]).cuda())
+    L.stream_check()
+    _bm, xi, _bn, st = up.outputs()
+    s_g = np.linalg.svd(xi.cpu().numpy().astype(np.complex128), compute_uv=False)
+    s_o = np.linalg.svd(orc["Xi_new"], compute_uv=False)
+    assert np.linalg.norm(s_g - s_o) / np.linalg.norm(s_o) < 1e-5
+    assert abs(float(st[0]) - orc["eps"]) / orc["eps"] < 1e-5
+    # a strided view is refused rather than read in the wrong order
+    with pytest.raises(ValueError):
+        up.run(torch.from_numpy(wl["U"]).cuda(), torch.from_numpy(wl["Bn"]).cuda().permute(2, 1, 0),
+               theta=torch.from_numpy(wl["theta"]).cuda())
