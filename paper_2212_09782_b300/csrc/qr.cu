@@ -366,17 +366,19 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
         const T* hh = reinterpret_cast<const T*>(recvm + (buf * 16 + (lane & 15)) * L::MSG);
         ns.add(hh[0], hh[1]);
       }
-      cx<T> S0 = zero, S1 = zero;
+      cx<T> S;
       {
+        // all ranks' slots loaded at once (a fixed, predicated unroll), then a sum tree
         const unsigned char* base = recvm + buf * 16 * L::MSG + L::HDR + min(lane, kb - 1) * sizeof(cx<T>);
-        int r = 0;
-        for (; r + 1 < CS; r += 2) {
-          S0 = cadd<T>(S0, *reinterpret_cast<const cx<T>*>(base + r * L::MSG));
-          S1 = cadd<T>(S1, *reinterpret_cast<const cx<T>*>(base + (r + 1) * L::MSG));
-        }
-        if (r < CS) S0 = cadd<T>(S0, *reinterpret_cast<const cx<T>*>(base + r * L::MSG));
+        cx<T> v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = r < CS ? *reinterpret_cast<const cx<T>*>(base + r * L::MSG) : zero;
+#pragma unroll
+        for (int h = 8; h > 0; h >>= 1)
+#pragma unroll
+          for (int r = 0; r < h; ++r) v[r] = cadd<T>(v[r], v[r + h]);
+        S = v[0];
       }
-      const cx<T> S = cadd<T>(S0, S1);
       const cx<T> pc = piv[min(lane, kb - 1)];
       const cx<T> alpha = piv[jn];
       ns.template shfl_sum<16>();
