@@ -69,10 +69,32 @@ __global__ void k_scale_rows(const cx<T>* in, cx<T>* out, const cx<T>* xi, long 
 template <typename T>
 __global__ void k_norm2_partial(const cx<T>* __restrict__ x, long long n, double* partial) {
   double s = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    cx<T> v = x[i];
-    s += (double)v.x * v.x + (double)v.y * v.y;
+  if constexpr (std::is_same<T, float>::value) {
+    // complex64: each thread accumulates in double-float (exact FP32 squares by FMA,
+    // TwoSum additions, ~48-bit significand) and only its total goes to FP64: per-element
+    // FP64 arithmetic made this pass FP64-bound on B300 (~4x its memory time)
+    float hi = 0.f, lo = 0.f;
+    auto add_sq = [&](float v) {
+      const float p = v * v, e = fmaf(v, v, -p);
+      const float t = hi + p, bb = t - hi;
+      const float err = (hi - (t - bb)) + (p - bb);
+      const float l = lo + err + e;
+      hi = t + l;
+      lo = l - (hi - t);
+    };
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+      const cx<T> v = x[i];
+      add_sq(v.x);
+      add_sq(v.y);
+    }
+    s = (double)hi + (double)lo;
+  } else {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+      cx<T> v = x[i];
+      s += (double)v.x * v.x + (double)v.y * v.y;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   __shared__ double ws[32];
