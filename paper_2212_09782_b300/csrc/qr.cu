@@ -514,31 +514,44 @@ __global__ void __launch_bounds__(TO_NT) k_t_outer(cx<T>* Tb, int ldt, const cx<
       __syncthreads();
       Gb = Gs; ldgb = w;
     }
-    // tmp = G[0:c0, c0:c0+w] T[c0:c0+w, c0:c0+w]
-    for (int o = threadIdx.x; o < c0 * w; o += TO_NT) {
-      const int i = o / w, j = o % w;
-      cx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0);
-      int k = 0;
-      for (; k + 1 <= j; k += 2) {
-        cfma<T>(a0, Gb[(long long)i * ldgb + k], Ts[(c0 + k) * ldT + c0 + j]);
-        cfma<T>(a1, Gb[(long long)i * ldgb + k + 1], Ts[(c0 + k + 1) * ldT + c0 + j]);
+    // tmp = G[0:c0, c0:c0+w] T[c0:c0+w, c0:c0+w]: 2 x 2 output tiles per thread (the
+    // diagonal block is upper triangular, so k runs to the tile's last column)
+    const int tr = (c0 + 1) / 2, tc = (w + 1) / 2;
+    for (int o = threadIdx.x; o < tr * tc; o += TO_NT) {
+      const int i0 = 2 * (o / tc), j0 = 2 * (o % tc);
+      cx<T> a00 = mk<T>(0, 0), a01 = a00, a10 = a00, a11 = a00;
+      const int kend = min(w, j0 + 2);
+      const bool i1 = i0 + 1 < c0, j1 = j0 + 1 < w;
+      for (int k = 0; k < kend; ++k) {
+        const cx<T> g0 = Gb[(long long)i0 * ldgb + k];
+        const cx<T> g1 = i1 ? Gb[(long long)(i0 + 1) * ldgb + k] : mk<T>(0, 0);
+        const cx<T> t0 = Ts[(c0 + k) * ldT + c0 + j0];
+        const cx<T> t1 = j1 ? Ts[(c0 + k) * ldT + c0 + j0 + 1] : mk<T>(0, 0);
+        cfma<T>(a00, g0, t0); cfma<T>(a01, g0, t1); cfma<T>(a10, g1, t0); cfma<T>(a11, g1, t1);
       }
-      if (k <= j) cfma<T>(a0, Gb[(long long)i * ldgb + k], Ts[(c0 + k) * ldT + c0 + j]);
-      tmp[o] = cadd<T>(a0, a1);
+      tmp[i0 * w + j0] = a00;
+      if (j1) tmp[i0 * w + j0 + 1] = a01;
+      if (i1) { tmp[(i0 + 1) * w + j0] = a10; if (j1) tmp[(i0 + 1) * w + j0 + 1] = a11; }
     }
     __syncthreads();
-    // T[0:c0, c0:c0+w] = -T[0:c0, 0:c0] tmp
-    for (int o = threadIdx.x; o < c0 * w; o += TO_NT) {
-      const int i = o / w, j = o % w;
-      cx<T> a0 = mk<T>(0, 0), a1 = mk<T>(0, 0);
-      int k = i;
-      for (; k + 1 < c0; k += 2) {
-        cfma<T>(a0, Ts[i * ldT + k], tmp[k * w + j]);
-        cfma<T>(a1, Ts[i * ldT + k + 1], tmp[(k + 1) * w + j]);
+    // T[0:c0, c0:c0+w] = -T[0:c0, 0:c0] tmp (T upper triangular: k from the tile's row)
+    for (int o = threadIdx.x; o < tr * tc; o += TO_NT) {
+      const int i0 = 2 * (o / tc), j0 = 2 * (o % tc);
+      cx<T> a00 = mk<T>(0, 0), a01 = a00, a10 = a00, a11 = a00;
+      const bool i1 = i0 + 1 < c0, j1 = j0 + 1 < w;
+      for (int k = i0; k < c0; ++k) {
+        const cx<T> u0 = Ts[i0 * ldT + k];
+        const cx<T> u1 = i1 ? Ts[(i0 + 1) * ldT + k] : mk<T>(0, 0);  // 0 for k = i0 (lower part)
+        const cx<T> m0 = tmp[k * w + j0];
+        const cx<T> m1 = j1 ? tmp[k * w + j0 + 1] : mk<T>(0, 0);
+        cfma<T>(a00, u0, m0); cfma<T>(a01, u0, m1); cfma<T>(a10, u1, m0); cfma<T>(a11, u1, m1);
       }
-      if (k < c0) cfma<T>(a0, Ts[i * ldT + k], tmp[k * w + j]);
-      const cx<T> r = cadd<T>(a0, a1);
-      Ts[i * ldT + c0 + j] = mk<T>(-r.x, -r.y);
+      Ts[i0 * ldT + c0 + j0] = mk<T>(-a00.x, -a00.y);
+      if (j1) Ts[i0 * ldT + c0 + j0 + 1] = mk<T>(-a01.x, -a01.y);
+      if (i1) {
+        Ts[(i0 + 1) * ldT + c0 + j0] = mk<T>(-a10.x, -a10.y);
+        if (j1) Ts[(i0 + 1) * ldT + c0 + j0 + 1] = mk<T>(-a11.x, -a11.y);
+      }
     }
     __syncthreads();
   }
