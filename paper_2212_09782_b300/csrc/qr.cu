@@ -281,9 +281,23 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
     const bool upd = lane > jn && lane < kb;
     const int slo = max(plo, min(p1, jn + 1));
     const int alo = top_counts ? slo : max(slo, min(p1, kb));
-    for (int p = plo; p < alo; ++p) {
-      const cx<T> y = csub<T>(P[p * ldp + col], cmul<T>(VX[p].v, cw));
-      if (upd) P[p * ldp + col] = y;
+    {
+      // rows that take the update only (the replicated pivot rows outside rank 0's sums):
+      // four rows' loads ahead of their stores
+      int p = plo;
+      for (; p + 3 < alo; p += 4) {
+        cx<T> y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) y[u] = csub<T>(P[(p + u) * ldp + col], cmul<T>(VX[p + u].v, cw));
+        if (upd) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) P[(p + u) * ldp + col] = y[u];
+        }
+      }
+      for (; p < alo; ++p) {
+        const cx<T> y = csub<T>(P[p * ldp + col], cmul<T>(VX[p].v, cw));
+        if (upd) P[p * ldp + col] = y;
+      }
     }
     cx<T> acc0 = zero, acc1 = zero;
     int p = alo;
