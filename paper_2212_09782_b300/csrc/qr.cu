@@ -45,11 +45,6 @@ template <typename T> struct PanelArgs {
 __host__ __device__ inline size_t a16(size_t x) { return (x + 15) & ~size_t(15); }
 
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 template <typename T> __device__ __forceinline__ T warp_sum_t(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -95,6 +90,21 @@ template <> struct NAcc<float> {
     for (int o = W / 2; o > 0; o >>= 1) {
       const float h = __shfl_xor_sync(0xffffffffu, hi, o), l = __shfl_xor_sync(0xffffffffu, lo, o);
       add(h, l);
+    }
+  }
+  // += (a_hi, a_lo) without renormalising: the exact TwoSum of the high words, and the
+  // low words (each ~2^-24 of the high ones) plus its error summed in FP32; two fewer
+  // dependent operations per add, for reductions where the pair is only read at the end
+  __device__ __forceinline__ void add_nr(float a, float b) {
+    const float s = hi + a, bb = s - hi, e = (hi - (s - bb)) + (a - bb);
+    hi = s; lo = (lo + b) + e;
+  }
+  __device__ __forceinline__ void add_nr(const NAcc& o) { add_nr(o.hi, o.lo); }
+  __device__ __forceinline__ void shfl_sum_nr() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h = __shfl_xor_sync(0xffffffffu, hi, o), l = __shfl_xor_sync(0xffffffffu, lo, o);
+      add_nr(h, l);
     }
   }
   __device__ __forceinline__ float value() const { return hi + lo; }
@@ -193,6 +203,157 @@ template <typename T> __host__ __device__ inline size_t panel_smem_bytes(int rps
   const size_t rows = (size_t)kb + rps;
   return a16(rows * (kb + 1) * sizeof(cx<T>)) + a16(rows * 2 * sizeof(cx<T>)) + PanelSmem<T>::fixed(PT / 32);
 }
+// Shared-memory blocks common to both panel kernels, carved after the row storage in
+// the order PanelSmem::fixed counts them.
+template <typename T> struct PanelShared {
+  unsigned char* recvm; cx<T>* pivb; T* wpn; cx<T>* wps;
+  cx<T>* taus; cx<T>* scl; cx<T>* bet; cx<T>* Ts; cx<T>* bc; uint64_t* mb;
+};
+template <typename T> __device__ __forceinline__ PanelShared<T> carve_panel_shared(unsigned char* q, int nw) {
+  using L = PanelSmem<T>;
+  PanelShared<T> sh;
+  sh.recvm = q; q += a16(2 * 16 * L::MSG);
+  sh.pivb = reinterpret_cast<cx<T>*>(q); q += a16(2 * SLOTS * sizeof(cx<T>));
+  sh.wpn = reinterpret_cast<T*>(q); q += a16((size_t)nw * 16);
+  sh.wps = reinterpret_cast<cx<T>*>(q); q += a16((size_t)nw * SLOTS * sizeof(cx<T>));
+  sh.taus = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * sizeof(cx<T>));
+  sh.scl = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * sizeof(cx<T>));
+  sh.bet = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * sizeof(cx<T>));
+  sh.Ts = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * (KBMAX + 1) * sizeof(cx<T>));
+  sh.bc = reinterpret_cast<cx<T>*>(q); q += a16(2 * (SLOTS + 2) * sizeof(cx<T>));
+  sh.mb = reinterpret_cast<uint64_t*>(q);
+  return sh;
+}
+
+// Phases 3 and 4 of column jn. On entry (after a CTA barrier) each warp's norm partial
+// is in wpn and its slot partials in wps; prow is this CTA's copy of panel row jn. On
+// exit (after a CTA barrier) bc[buf] holds conj(tau) w_c for every column and the
+// reflector's scale, and tau, scale, beta and the Gram values of column jn are stored.
+template <typename T, int NW>
+__device__ __forceinline__ void panel_exchange(const PanelShared<T>& sh, const cx<T>* prow, int jn, int kb,
+                                               int rank, int CS, unsigned* err, bool& ok) {
+  using L = PanelSmem<T>;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const cx<T> zero = mk<T>(0, 0);
+  const uint32_t txb = (uint32_t)(CS * L::MSG);
+  // ---- 3. exchange: every warp forms the CTA's message (the warps' partials summed)
+  //      and pushes it to its share of the ranks (r = warp, warp + NW, ...), so the
+  //      remote stores issue in parallel; warp 0 also copies the pivot row and arms
+  //      this CTA's barrier
+  const int buf = jn & 1;
+  {
+    cx<T> s = zero;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) s = cadd<T>(s, sh.wps[w * SLOTS + lane]);
+    NAcc<T> n;
+    {
+      const int w = lane & (NW - 1);  // each group of NW lanes holds every warp's partial
+      if constexpr (std::is_same<T, float>::value) n.add(sh.wpn[w * 4], sh.wpn[w * 4 + 1]);
+      else n.add(sh.wpn[w * 2], T(0));
+    }
+    n.template shfl_sum<NW>();
+    cx<T> h;
+    if constexpr (std::is_same<T, float>::value) h = mk<T>(n.hi, n.lo); else h = mk<T>(n.value(), 0);
+    if (warp == 0) {
+      sh.pivb[buf * SLOTS + lane] = prow[min(lane, kb - 1)];
+      __syncwarp();
+      if (lane == 0) mbar_arm(&sh.mb[buf], txb);  // release: the pivot copy is visible to the waiters
+    }
+    const uint32_t mine = smem_addr(sh.recvm + (buf * 16 + rank) * L::MSG);
+    const uint32_t mbl = smem_addr(&sh.mb[buf]);
+    if constexpr (std::is_same<T, float>::value) {
+      // 17 chunks of 16 bytes: (norm hi, lo, 0, 0), then slot pairs
+      const cx<T> sa = shfl_cx<T>(s, (2 * lane + 30) & 31), sb = shfl_cx<T>(s, (2 * lane + 31) & 31);
+      const float4 ch = lane == 0 ? make_float4(h.x, h.y, 0.f, 0.f) : make_float4(sa.x, sa.y, sb.x, sb.y);
+      if (lane < 17)
+        for (int r = warp; r < CS; r += NW) st_async_16(map_rank(mine + 16 * lane, r), ch, map_rank(mbl, r));
+    } else {
+      for (int r = warp; r < CS; r += NW) {
+        const uint32_t rb = map_rank(mine, r), rm = map_rank(mbl, r);
+        st_async_16(rb + 16 + 16 * lane, s, rm);
+        if (lane == 0) st_async_16(rb, h, rm);
+      }
+    }
+  }
+  if (warp == 0) {
+    if (!mbar_wait_cl(&sh.mb[buf], (uint32_t)((jn >> 1) & 1))) ok = false;
+    const cx<T>* piv = sh.pivb + buf * SLOTS;
+    NAcc<T> ns;
+    if ((lane & 15) < CS) {  // both half-warps hold every rank's norm partial
+      const T* hh = reinterpret_cast<const T*>(sh.recvm + (buf * 16 + (lane & 15)) * L::MSG);
+      ns.add(hh[0], hh[1]);
+    }
+    cx<T> S;
+    {
+      // all ranks' slots loaded at once (a fixed, predicated unroll), then a sum tree
+      const unsigned char* base = sh.recvm + buf * 16 * L::MSG + L::HDR + min(lane, kb - 1) * sizeof(cx<T>);
+      cx<T> v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = r < CS ? *reinterpret_cast<const cx<T>*>(base + r * L::MSG) : zero;
+#pragma unroll
+      for (int h = 8; h > 0; h >>= 1)
+#pragma unroll
+        for (int r = 0; r < h; ++r) v[r] = cadd<T>(v[r], v[r + h]);
+      S = v[0];
+    }
+    const cx<T> pc = piv[min(lane, kb - 1)];
+    const cx<T> alpha = piv[jn];
+    ns.template shfl_sum<16>();
+    T beta, tr, ti, sr, si;
+    reflector(ns.value(), alpha.x, alpha.y, beta, tr, ti, sr, si);
+    if (lane == 0 && rank == 0 && !(isfinite(beta) && isfinite(sr) && isfinite(si)))
+      atomicOr(err, DEVERR_NUMERIC);
+    const cx<T> sc = mk<T>(sr, si), tau = mk<T>(tr, ti);
+    const bool u = lane > jn && lane < kb;
+    const cx<T> cwl = u ? cmul<T>(cconj<T>(tau), cadd<T>(pc, cmul<T>(cconj<T>(sc), S))) : zero;
+    if (lane < jn) {
+      const cx<T> gv = cmul<T>(cconj<T>(sh.scl[lane]), cadd<T>(cconj<T>(pc), cmul<T>(sc, cconj<T>(S))));
+      sh.Ts[lane * (KBMAX + 1) + jn] = gv;
+    }
+    cx<T>* bb = sh.bc + buf * (SLOTS + 2);
+    bb[lane] = cwl;
+    if (lane == 0) { bb[SLOTS] = sc; sh.taus[jn] = tau; sh.scl[jn] = sc; sh.bet[jn] = mk<T>(beta, 0); }
+  }
+  asm volatile("bar.sync 1, %0;" ::"n"(NW * 32) : "memory");
+}
+
+// Compact-WY T of the panel (and tau) into global memory, from the Gram values and tau
+// the column loop left in shared memory; run by one CTA of the cluster.
+template <typename T, int NW>
+__device__ __forceinline__ void panel_t_factor(const PanelShared<T>& sh, int kb, const PanelArgs<T>& a) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const cx<T> zero = mk<T>(0, 0);
+  const long long k0 = a.k0;
+  // compact-WY T (the last rank, whose slab is the shortest): with U the strict upper
+  // part of V^dag V (held in sh.Ts), T^{-1} = diag(1/tau) + U, so column j of T solves
+  // t_i = tau_i (delta_ij - sum_{k > i} U_ik t_k), i = j, j-1, ..., 0; this form also
+  // covers tau_i = 0 (H_i = I, row i of T zero). Warp w takes columns w, w + NW, ...,
+  // lane = row; each step finalises t_k on lane k and broadcasts it.
+  constexpr int CPW = (KBMAX + NW - 1) / NW;
+  cx<T> acc[CPW], t[CPW];
+#pragma unroll
+  for (int c = 0; c < CPW; ++c) { acc[c] = zero; t[c] = zero; }
+  const cx<T> tau_l = lane < kb ? sh.taus[lane] : zero;
+  for (int k = kb - 1; k >= 0; --k) {
+    const cx<T> uk = lane < k ? sh.Ts[lane * (KBMAX + 1) + k] : zero;
+#pragma unroll
+    for (int c = 0; c < CPW; ++c) {
+      const int j = warp + c * NW;
+      if (k <= j && j < kb) {  // warp-uniform
+        if (lane == k) t[c] = cmul<T>(tau_l, csub<T>(mk<T>(k == j ? T(1) : T(0), T(0)), acc[c]));
+        const cx<T> tk = shfl_cx<T>(t[c], k);
+        cfma<T>(acc[c], uk, tk);  // uk = 0 on lanes >= k
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < CPW; ++c) {
+    const int j = warp + c * NW;
+    if (j < kb && lane < kb) a.Tf[lane * a.ldt + j] = t[c];  // t = 0 below the diagonal
+  }
+  if (tid < kb) a.tau[k0 + tid] = sh.taus[tid];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
   constexpr int NT = PT;
@@ -220,16 +381,10 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
   // per row: v of the reflector being applied and x of the next pivot column, side by side
   // so that phase 2 reads both with one broadcast load
   VXp<T>* VX = reinterpret_cast<VXp<T>*>(q); q += a16((size_t)(kb + rps) * sizeof(VXp<T>));
-  unsigned char* recvm = q; q += a16(2 * 16 * L::MSG);
-  cx<T>* pivb = reinterpret_cast<cx<T>*>(q); q += a16(2 * SLOTS * sizeof(cx<T>));
-  T* wpn = reinterpret_cast<T*>(q); q += a16((size_t)NW * 16);
-  cx<T>* wps = reinterpret_cast<cx<T>*>(q); q += a16((size_t)NW * SLOTS * sizeof(cx<T>));
-  cx<T>* taus = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * sizeof(cx<T>));
-  cx<T>* scl = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * sizeof(cx<T>));
-  cx<T>* bet = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * sizeof(cx<T>));
-  cx<T>* Ts = reinterpret_cast<cx<T>*>(q); q += a16(KBMAX * (KBMAX + 1) * sizeof(cx<T>));
-  cx<T>* bc = reinterpret_cast<cx<T>*>(q); q += a16(2 * (SLOTS + 2) * sizeof(cx<T>));
-  uint64_t* mb = reinterpret_cast<uint64_t*>(q);
+  const PanelShared<T> sh = carve_panel_shared<T>(q, NW);
+  uint64_t* mb = sh.mb;
+  cx<T>* wps = sh.wps; T* wpn = sh.wpn;
+  cx<T>* scl = sh.scl; cx<T>* bet = sh.bet; cx<T>* bc = sh.bc;
 
   const long long k0 = a.k0;
   if (tid == 0) {
@@ -248,7 +403,6 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
   asm volatile("cp.async.wait_all;" ::: "memory");
   cl.sync();  // every CTA's barriers exist before anyone sends; panel loaded
   bool ok = true;
-  const uint32_t txb = (uint32_t)(CS * L::MSG);
 
   const cx<T> zero = mk<T>(0, 0);
   cx<T> scale = zero, cw = zero, cwn = zero;
@@ -333,85 +487,8 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
       else { wpn[warp * 2 + 0] = nacc.value(); wpn[warp * 2 + 1] = 0; }
     }
     __syncthreads();
-    // ---- 3. exchange: every warp forms the CTA's message (the warps' partials summed)
-    //      and pushes it to its share of the ranks (r = warp, warp + NW, ...), so the
-    //      remote stores issue in parallel; warp 0 also copies the pivot row and arms
-    //      this CTA's barrier
+    panel_exchange<T, NW>(sh, P + jn * ldp, jn, kb, rank, CS, a.err, ok);
     const int buf = jn & 1;
-    {
-      cx<T> s = zero;
-#pragma unroll
-      for (int w = 0; w < NW; ++w) s = cadd<T>(s, wps[w * SLOTS + lane]);
-      NAcc<T> n;
-      {
-        const int w = lane & (NW - 1);  // each group of NW lanes holds every warp's partial
-        if constexpr (std::is_same<T, float>::value) n.add(wpn[w * 4], wpn[w * 4 + 1]);
-        else n.add(wpn[w * 2], T(0));
-      }
-      n.template shfl_sum<NW>();
-      cx<T> h;
-      if constexpr (std::is_same<T, float>::value) h = mk<T>(n.hi, n.lo); else h = mk<T>(n.value(), 0);
-      if (warp == 0) {
-        pivb[buf * SLOTS + lane] = P[jn * ldp + min(lane, kb - 1)];
-        __syncwarp();
-        if (lane == 0) mbar_arm(&mb[buf], txb);  // release: the pivot copy is visible to the waiters
-      }
-      const uint32_t mine = smem_addr(recvm + (buf * 16 + rank) * L::MSG);
-      const uint32_t mbl = smem_addr(&mb[buf]);
-      if constexpr (std::is_same<T, float>::value) {
-        // 17 chunks of 16 bytes: (norm hi, lo, 0, 0), then slot pairs
-        const cx<T> sa = shfl_cx<T>(s, (2 * lane + 30) & 31), sb = shfl_cx<T>(s, (2 * lane + 31) & 31);
-        const float4 ch = lane == 0 ? make_float4(h.x, h.y, 0.f, 0.f) : make_float4(sa.x, sa.y, sb.x, sb.y);
-        if (lane < 17)
-          for (int r = warp; r < CS; r += NW) st_async_16(map_rank(mine + 16 * lane, r), ch, map_rank(mbl, r));
-      } else {
-        for (int r = warp; r < CS; r += NW) {
-          const uint32_t rb = map_rank(mine, r), rm = map_rank(mbl, r);
-          st_async_16(rb + 16 + 16 * lane, s, rm);
-          if (lane == 0) st_async_16(rb, h, rm);
-        }
-      }
-    }
-    if (warp == 0) {
-      if (!mbar_wait_cl(&mb[buf], (uint32_t)((jn >> 1) & 1))) ok = false;
-      const cx<T>* piv = pivb + buf * SLOTS;
-      NAcc<T> ns;
-      if ((lane & 15) < CS) {  // both half-warps hold every rank's norm partial
-        const T* hh = reinterpret_cast<const T*>(recvm + (buf * 16 + (lane & 15)) * L::MSG);
-        ns.add(hh[0], hh[1]);
-      }
-      cx<T> S;
-      {
-        // all ranks' slots loaded at once (a fixed, predicated unroll), then a sum tree
-        const unsigned char* base = recvm + buf * 16 * L::MSG + L::HDR + min(lane, kb - 1) * sizeof(cx<T>);
-        cx<T> v[16];
-#pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = r < CS ? *reinterpret_cast<const cx<T>*>(base + r * L::MSG) : zero;
-#pragma unroll
-        for (int h = 8; h > 0; h >>= 1)
-#pragma unroll
-          for (int r = 0; r < h; ++r) v[r] = cadd<T>(v[r], v[r + h]);
-        S = v[0];
-      }
-      const cx<T> pc = piv[min(lane, kb - 1)];
-      const cx<T> alpha = piv[jn];
-      ns.template shfl_sum<16>();
-      T beta, tr, ti, sr, si;
-      reflector(ns.value(), alpha.x, alpha.y, beta, tr, ti, sr, si);
-      if (lane == 0 && rank == 0 && !(isfinite(beta) && isfinite(sr) && isfinite(si)))
-        atomicOr(a.err, DEVERR_NUMERIC);
-      const cx<T> sc = mk<T>(sr, si), tau = mk<T>(tr, ti);
-      const bool u = lane > jn && lane < kb;
-      const cx<T> cwl = u ? cmul<T>(cconj<T>(tau), cadd<T>(pc, cmul<T>(cconj<T>(sc), S))) : zero;
-      if (lane < jn) {
-        const cx<T> gv = cmul<T>(cconj<T>(scl[lane]), cadd<T>(cconj<T>(pc), cmul<T>(sc, cconj<T>(S))));
-        Ts[lane * (KBMAX + 1) + jn] = gv;
-      }
-      cx<T>* bb = bc + buf * (SLOTS + 2);
-      bb[lane] = cwl;
-      if (lane == 0) { bb[SLOTS] = sc; taus[jn] = tau; scl[jn] = sc; bet[jn] = mk<T>(beta, 0); }
-    }
-    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
     {
       const cx<T>* bb = bc + buf * (SLOTS + 2);
       scale = bb[SLOTS];
@@ -422,37 +499,7 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
   if (!ok && tid == 0) atomicOr(a.err, DEVERR_TIMEOUT);
   __syncthreads();
 
-  if (rank == CS - 1) {
-    // compact-WY T (the last rank, whose slab is the shortest): with U the strict upper
-    // part of V^dag V (held in Ts), T^{-1} = diag(1/tau) + U, so column j of T solves
-    // t_i = tau_i (delta_ij - sum_{k > i} U_ik t_k), i = j, j-1, ..., 0; this form also
-    // covers tau_i = 0 (H_i = I, row i of T zero). One warp per KBMAX / NW columns,
-    // lane = row; each step finalises t_k on lane k and broadcasts it.
-    constexpr int CPW = KBMAX / NW;
-    static_assert(KBMAX % NW == 0, "columns per warp");
-    cx<T> acc[CPW], t[CPW];
-#pragma unroll
-    for (int c = 0; c < CPW; ++c) { acc[c] = zero; t[c] = zero; }
-    const cx<T> tau_l = lane < kb ? taus[lane] : zero;
-    for (int k = kb - 1; k >= 0; --k) {
-      const cx<T> uk = lane < k ? Ts[lane * (KBMAX + 1) + k] : zero;
-#pragma unroll
-      for (int c = 0; c < CPW; ++c) {
-        const int j = warp + c * NW;
-        if (k <= j) {  // warp-uniform
-          if (lane == k) t[c] = cmul<T>(tau_l, csub<T>(mk<T>(k == j ? T(1) : T(0), T(0)), acc[c]));
-          const cx<T> tk = shfl_cx<T>(t[c], k);
-          cfma<T>(acc[c], uk, tk);  // uk = 0 on lanes >= k
-        }
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < CPW; ++c) {
-      const int j = warp + c * NW;
-      if (j < kb && lane < kb) a.Tf[lane * a.ldt + j] = t[c];  // t = 0 below the diagonal
-    }
-    if (tid < kb) a.tau[k0 + tid] = taus[tid];
-  }
+  if (rank == CS - 1) panel_t_factor<T, NW>(sh, kb, a);
   // ---- V (v = scale * raw column below the pivot, unit diagonal) and R / zeros into A;
   //      lane = column, the top block from rank 0 only
   if (lane < kb) {
@@ -472,6 +519,320 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
       for (int u = 0; u < 4; ++u) put(p + u, pv[u]);
     }
     for (; p < p1; ++p) put(p, P[p * ldp + lane]);
+  }
+  cl.sync();
+}
+
+// Register-file form of the panel (complex64), used when each warp's share of the slab
+// fits in RF_RPW rows of registers, lane = column; the replicated top kb rows stay in
+// shared memory (every step needs the pivot row from there), split over the warps.
+// It also takes the application of reflector j-1 to the trailing columns off the
+// critical path: column j+1 of step j is computed alone (lane = row), and the partial
+// sums go out against the columns as they were before reflector j-1,
+//   S'_c = sum_{g > j} conj(x_g) P[g, c],   h = sum_{g > j} conj(x_g) x^{(j-1)}_g,
+// from which the receiver forms S_c = S'_c - h scale_{j-1} conj(tau_{j-1}) w_c (one more
+// scalar in the message header). The trailing update by reflector j-1 then runs while
+// the messages are in flight. Arrays in shared memory: X (double-buffered), the raw pivot
+// column x_j of every local row; Y, the slab values of the next pivot column, published
+// by that lane during the trailing update. The coefficients cws = scale conj(tau) w_c of
+// the lanes fold the reflector's scale into the update of the raw column. Warp 0 holds no
+// rows: it waits for the messages and forms the reflector while warps 1..11 apply the
+// trailing update, so that update leaves the critical path.
+constexpr int RF_NT = 384;  // threads per CTA: the reflector warp and 11 row warps
+constexpr int RF_RPW = 30;  // slab rows per row warp held in registers (11 x 30 = 330 per CTA)
+
+template <typename T> __host__ __device__ inline size_t panel_rf_smem_bytes(int kb) {
+  constexpr int slots = (RF_NT / 32 - 1) * RF_RPW;
+  return a16((size_t)kb * (kb + 1) * sizeof(cx<T>)) + a16((size_t)(2 * (kb + slots) + slots) * sizeof(cx<T>)) +
+         a16((size_t)(RF_NT / 32 - 1) * 32 * 16) + 16 + PanelSmem<T>::fixed(RF_NT / 32);
+}
+
+// p - v c with every rounding fixed (four explicit FMAs), so that the trailing update and
+// the column pass produce the same bits for the pivot column
+__device__ __forceinline__ cx<float> upd_rn(cx<float> p, cx<float> v, cx<float> c) {
+  return mk<float>(__fmaf_rn(-v.x, c.x, __fmaf_rn(v.y, c.y, p.x)), __fmaf_rn(-v.x, c.y, __fmaf_rn(-v.y, c.x, p.y)));
+}
+__device__ __forceinline__ cx<float> sub_rn(cx<float> p, cx<float> c) {
+  return mk<float>(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y));
+}
+
+template <int RPW>
+__global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
+  using T = float;
+  using L = PanelSmem<T>;
+  constexpr int NT = RF_NT, NW = NT / 32, RW = NW - 1;  // warps 1 .. RW hold the rows
+  static_assert(RW <= 16 && RPW <= 32, "one tree level per halving; one slab row per lane");
+  constexpr int TPW = (KBMAX + RW - 1) / RW;          // top rows per row warp: t = rw + RW i
+  pdl_launch_dependents();
+  pdl_wait();
+  extern __shared__ __align__(16) unsigned char sm[];
+  cg::cluster_group cl = cg::this_cluster();
+  const int CS = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int kb = a.kb, ldp = kb + 1, rps = a.rps;
+  const int mr = a.m - a.k0;
+  const int s0 = kb + rank * rps;                  // first slab row (panel index)
+  const int nslab = max(0, min(rps, mr - s0));
+  const int rw = warp - 1;                         // row-warp index; -1 for the reflector warp
+  const int spw = (nslab + RW - 1) / RW;           // slab rows per row warp, <= RPW (host-checked)
+  const int q0 = rw < 0 ? 0 : min(nslab, rw * spw);
+  const int cnt = rw < 0 ? 0 : min(nslab, q0 + spw) - q0;  // this warp's slab rows q0 .. q0 + cnt - 1
+  const int tcnt = rw < 0 ? 0 : TPW;               // top rows t = rw + RW i < kb, i < tcnt
+  const bool top_counts = rank == 0;               // top rows enter rank 0's sums only
+  // X: the top rows, then RPW slots per row warp (rows past cnt stay zero, so the row
+  // loops below run over all RPW slots without guards); Y: RPW slots per row warp
+  const int xs = kb + RW * RPW;
+  const int xb = rw < 0 ? 0 : rw * RPW;            // this warp's first slab slot
+
+  unsigned char* q = sm;
+  cx<T>* Pt = reinterpret_cast<cx<T>*>(q); q += a16((size_t)kb * ldp * sizeof(cx<T>));
+  cx<T>* X = reinterpret_cast<cx<T>*>(q);
+  cx<T>* Y = X + 2 * xs; q += a16((size_t)(2 * xs + RW * RPW) * sizeof(cx<T>));
+  float4* pn = reinterpret_cast<float4*>(q); q += a16((size_t)RW * 32 * sizeof(float4));  // lane partials
+  float4* hdr = reinterpret_cast<float4*>(q); q += 16;                                  // the CTA's header
+  const PanelShared<T> sh = carve_panel_shared<T>(q, NW);
+  const long long k0 = a.k0;
+  const cx<T> zero = mk<T>(0, 0);
+  if (tid == 0) {
+    mbar_init1(&sh.mb[0]);
+    mbar_init1(&sh.mb[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = tid; i < 2 * xs + RW * RPW; i += NT) X[i] = zero;
+  __syncthreads();
+  // load, lane = column: the top rows into shared memory (cp.async), the slab into registers
+  if (lane < kb && rw >= 0)
+    for (int t = rw; t < kb; t += RW)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(Pt + t * ldp + lane)),
+                   "l"(a.A + (k0 + t) * a.lda + k0 + lane), "n"((int)sizeof(cx<T>)) : "memory");
+  cx<T> R[RPW];
+  {
+    const cx<T>* src = a.A + (k0 + s0 + q0) * a.lda + k0 + min(lane, kb - 1);
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) R[r] = (r < cnt && lane < kb) ? src[r * a.lda] : zero;
+  }
+  if (lane == 0 && rw >= 0) {
+#pragma unroll
+    for (int r = 0; r < RPW; ++r) Y[xb + r] = R[r];
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  cl.sync();  // every CTA's barriers exist before anyone sends; top rows and Y in place
+  bool ok = true;
+  const uint32_t txb = (uint32_t)(CS * L::MSG);
+  const int col = min(lane, kb - 1);
+  cx<T> cw = zero, cws = zero;  // this lane's conj(tau) w_c of reflector j-1, and scale_{j-1} cw
+
+  for (int jn = 0; jn < kb; ++jn) {
+    const int jp = jn - 1, buf = jn & 1;
+    const cx<T>* Xp = X + ((jn + 1) & 1) * xs;  // raw column jp
+    cx<T>* Xn = X + buf * xs;                   // raw column jn
+    const cx<T> cwj = shfl_cx<T>(cw, jn), cwsj = shfl_cx<T>(cws, jn);
+    NAcc<T> nacc, nacc2;
+    cx<T> hp = zero, hp2 = zero;
+    // ---- A. column jn alone, lane = row (one slab row per lane, cnt <= 32, and lanes
+    //      0 .. tcnt-1 one top row each, as two independent chains): x_jn = column jn after
+    //      reflector jp; norm and h partials
+    if (lane < cnt) {
+      cx<T> x = Y[xb + lane];
+      if (jp >= 0) {
+        const cx<T> u = Xp[kb + xb + lane];
+        x = upd_rn(x, u, cwsj);
+        cfma<T>(hp, cconj<T>(x), u);
+      }
+      Xn[kb + xb + lane] = x;
+      nacc.add_sq(x.x); nacc.add_sq(x.y);
+    }
+    if (lane < tcnt) {
+      const int t = rw + RW * lane;
+      if (t < kb) {
+        cx<T> x = Pt[t * ldp + jn];
+        if (jp >= 0 && t >= jp) x = (t == jp) ? sub_rn(x, cwj) : upd_rn(x, Xp[t], cwsj);
+        Xn[t] = x;
+        if (top_counts && t > jn) {
+          nacc2.add_sq(x.x); nacc2.add_sq(x.y);
+          if (jp >= 0) cfma<T>(hp2, cconj<T>(x), Xp[t]);
+        }
+      }
+    }
+    nacc.add_nr(nacc2);
+    hp = cadd<T>(hp, hp2);
+    // the lane partials of the norm and of h go to the reflector warp, which sums them
+    // while the row warps run pass B
+    if (rw >= 0) {
+      pn[rw * 32 + lane] = make_float4(nacc.hi, nacc.lo, hp.x, hp.y);
+      asm volatile("bar.arrive 2, %0;" ::"n"(NT) : "memory");
+    }
+    __syncwarp();
+    // ---- B. S'_c over this warp's rows below pivot jn, lane = column, the columns as they
+    //      were before reflector jp; the owner of row jn copies it for the reflector
+    cx<T> acc0 = zero, acc1 = zero;
+    if (rw >= 0) {  // warp-uniform: the reflector warp skips the predicated row loops
+      const cx<T>* Xs = Xn + kb + xb;
+      cx<T> acc2 = zero, acc3 = zero;
+#pragma unroll
+      for (int r = 0; r < RPW; r += 4) {
+        cfma<T>(acc0, cconj<T>(Xs[r]), R[r]);
+        if (r + 1 < RPW) cfma<T>(acc1, cconj<T>(Xs[r + 1]), R[r + 1]);
+        if (r + 2 < RPW) cfma<T>(acc2, cconj<T>(Xs[r + 2]), R[r + 2]);
+        if (r + 3 < RPW) cfma<T>(acc3, cconj<T>(Xs[r + 3]), R[r + 3]);
+      }
+      acc0 = cadd<T>(acc0, acc2);
+      acc1 = cadd<T>(acc1, acc3);
+    }
+    if (top_counts) {
+#pragma unroll
+      for (int i = 0; i < TPW; ++i) {
+        const int t = rw + RW * i;
+        if (i < tcnt && t < kb && t > jn) cfma<T>(acc1, cconj<T>(Xn[t]), Pt[t * ldp + col]);
+      }
+    }
+    if (rw == jn % RW) sh.pivb[buf * SLOTS + lane] = Pt[jn * ldp + col];
+    if (rw >= 0) {
+      sh.wps[warp * SLOTS + lane] = cadd<T>(acc0, acc1);
+    } else {
+      // the reflector warp: the CTA's norm (double-float) and h from the lane partials
+      asm volatile("bar.sync 2, %0;" ::"n"(NT) : "memory");
+      NAcc<T> nw[RW];
+      float hxw[RW], hyw[RW];
+#pragma unroll
+      for (int w = 0; w < RW; ++w) {
+        const float4 e = pn[w * 32 + lane];
+        nw[w].hi = e.x; nw[w].lo = e.y; hxw[w] = e.z; hyw[w] = e.w;
+      }
+#pragma unroll
+      for (int h = 8; h > 0; h >>= 1)  // tree over the row warps (RW <= 16)
+#pragma unroll
+        for (int w = 0; w < h; ++w)
+          if (w + h < RW) { nw[w].add_nr(nw[w + h]); hxw[w] += hxw[w + h]; hyw[w] += hyw[w + h]; }
+      NAcc<T> n0 = nw[0];
+      float hx = hxw[0], hy = hyw[0];
+      n0.shfl_sum_nr();
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        hx += __shfl_xor_sync(0xffffffffu, hx, o);
+        hy += __shfl_xor_sync(0xffffffffu, hy, o);
+      }
+      if (lane == 0) *hdr = make_float4(n0.hi, n0.lo, hx, hy);
+    }
+    __syncthreads();
+    // ---- C. send: every warp sums the CTA's message and pushes it to its share of the ranks
+    {
+      cx<T> s = zero;
+#pragma unroll
+      for (int w = 1; w < NW; ++w) s = cadd<T>(s, sh.wps[w * SLOTS + lane]);
+      const float4 h4 = *hdr;
+      if (warp == 0 && lane == 0) mbar_arm(&sh.mb[buf], txb);
+      const uint32_t mine = smem_addr(sh.recvm + (buf * 16 + rank) * L::MSG);
+      const uint32_t mbl = smem_addr(&sh.mb[buf]);
+      // 17 chunks of 16 bytes: (norm hi, lo, h), then slot pairs
+      const cx<T> sa = shfl_cx<T>(s, (2 * lane + 30) & 31), sb = shfl_cx<T>(s, (2 * lane + 31) & 31);
+      const float4 ch = lane == 0 ? h4 : make_float4(sa.x, sa.y, sb.x, sb.y);
+      if (lane < 17)
+        for (int r = warp; r < CS; r += NW) st_async_16(map_rank(mine + 16 * lane, r), ch, map_rank(mbl, r));
+    }
+    // ---- D. while the messages fly: reflector jp on the trailing columns (lanes c >= jn;
+    //      cws = 0 elsewhere), in registers and on this warp's top rows; lane jn + 1
+    //      publishes its slab values for the next step's column pass
+    if (jp >= 0 && rw >= 0) {
+      const cx<T>* Vs = Xp + kb + xb;
+#pragma unroll
+      for (int r = 0; r < RPW; ++r) R[r] = upd_rn(R[r], Vs[r], cws);
+#pragma unroll
+      for (int i = 0; i < TPW; ++i) {
+        const int t = rw + RW * i;
+        if (i < tcnt && t < kb && t >= jp) {
+          const cx<T> p = Pt[t * ldp + col];
+          const cx<T> y = (t == jp) ? sub_rn(p, cw) : upd_rn(p, Xp[t], cws);
+          if (lane >= jn && lane < kb) Pt[t * ldp + lane] = y;
+        }
+      }
+    }
+    if (rw >= 0 && lane == jn + 1) {
+#pragma unroll
+      for (int r = 0; r < RPW; ++r)
+        Y[xb + r] = R[r];
+    }
+    // ---- E. warp 0: all ranks' sums, the correction by h, reflector jn
+    if (warp == 0) {
+      if (!mbar_wait_cl(&sh.mb[buf], (uint32_t)((jn >> 1) & 1))) ok = false;
+      // every lane sums all ranks' headers (a fixed, predicated unroll and a tree)
+      NAcc<T> ns;
+      float hx, hy;
+      {
+        NAcc<T> nr[16];
+        float hxr[16], hyr[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) {
+          const float4 e = r < CS ? *reinterpret_cast<const float4*>(sh.recvm + (buf * 16 + r) * L::MSG)
+                                  : make_float4(0.f, 0.f, 0.f, 0.f);
+          nr[r].hi = e.x; nr[r].lo = e.y; hxr[r] = e.z; hyr[r] = e.w;
+        }
+#pragma unroll
+        for (int h = 8; h > 0; h >>= 1)
+#pragma unroll
+          for (int r = 0; r < h; ++r) { nr[r].add_nr(nr[r + h]); hxr[r] += hxr[r + h]; hyr[r] += hyr[r + h]; }
+        ns = nr[0]; hx = hxr[0]; hy = hyr[0];
+      }
+      cx<T> S;
+      {
+        const unsigned char* base = sh.recvm + buf * 16 * L::MSG + L::HDR + col * sizeof(cx<T>);
+        cx<T> v[16];
+#pragma unroll
+        for (int r = 0; r < 16; ++r) v[r] = r < CS ? *reinterpret_cast<const cx<T>*>(base + r * L::MSG) : zero;
+#pragma unroll
+        for (int h = 8; h > 0; h >>= 1)
+#pragma unroll
+          for (int r = 0; r < h; ++r) v[r] = cadd<T>(v[r], v[r + h]);
+        S = v[0];
+      }
+      cx<T> pc = sh.pivb[buf * SLOTS + col];
+      if (jp >= 0) {
+        S = csub<T>(S, cmul<T>(mk<T>(hx, hy), cws));
+        pc = upd_rn(pc, Xp[jn], cws);
+      }
+      const cx<T> alpha = shfl_cx<T>(pc, jn);
+      T beta, tr, ti, sr, si;
+      reflector(ns.value(), alpha.x, alpha.y, beta, tr, ti, sr, si);
+      if (lane == 0 && rank == 0 && !(isfinite(beta) && isfinite(sr) && isfinite(si)))
+        atomicOr(a.err, DEVERR_NUMERIC);
+      const cx<T> sc = mk<T>(sr, si), tau = mk<T>(tr, ti);
+      const bool u = lane > jn && lane < kb;
+      const cx<T> cwl = u ? cmul<T>(cconj<T>(tau), cadd<T>(pc, cmul<T>(cconj<T>(sc), S))) : zero;
+      if (lane < jn) {
+        const cx<T> gv = cmul<T>(cconj<T>(sh.scl[lane]), cadd<T>(cconj<T>(pc), cmul<T>(sc, cconj<T>(S))));
+        sh.Ts[lane * (KBMAX + 1) + jn] = gv;
+      }
+      cx<T>* bb = sh.bc + buf * (SLOTS + 2);
+      bb[lane] = cwl;
+      if (lane == 0) { bb[SLOTS] = sc; sh.taus[jn] = tau; sh.scl[jn] = sc; sh.bet[jn] = mk<T>(beta, 0); }
+    }
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+    {
+      const cx<T>* bb = sh.bc + buf * (SLOTS + 2);
+      cw = bb[lane];
+      cws = cmul<T>(bb[SLOTS], cw);
+    }
+  }
+  if (!ok && tid == 0) atomicOr(a.err, DEVERR_TIMEOUT);
+  __syncthreads();
+
+  if (rank == CS - 1) panel_t_factor<T, NW>(sh, kb, a);
+  // ---- V (v = scale * raw column below the pivot, unit diagonal) and R / zeros into A:
+  //      the top rows from rank 0's shared memory, the slab from registers
+  if (lane < kb) {
+    const cx<T> sc = sh.scl[lane], be = sh.bet[lane];
+    if (rank == 0 && rw >= 0)
+      for (int t = rw; t < kb; t += RW) {
+        const cx<T> pv = Pt[t * ldp + lane];
+        a.V[(k0 + t) * a.ldv + k0 + lane] = (t == lane) ? mk<T>(1, 0) : (t > lane ? cmul<T>(sc, pv) : zero);
+        a.A[(k0 + t) * a.lda + k0 + lane] = (lane > t) ? pv : (lane == t ? be : zero);
+      }
+    cx<T>* vd = a.V + (k0 + s0 + q0) * a.ldv + k0 + lane;
+    cx<T>* ad = a.A + (k0 + s0 + q0) * a.lda + k0 + lane;
+#pragma unroll
+    for (int r = 0; r < RPW; ++r)
+      if (r < cnt) { vd[r * a.ldv] = cmul<T>(sc, R[r]); ad[r * a.lda] = zero; }
   }
   cl.sync();
 }
@@ -835,6 +1196,11 @@ template <typename T> int set_panel_attrs() {
   if (g_attr_done<T>) return QRTEBD_OK;
   QR_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_cap()));
   QR_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  if constexpr (std::is_same<T, float>::value) {
+    QR_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel_rf<RF_RPW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem_cap()));
+    QR_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel_rf<RF_RPW>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  }
   g_attr_done<T> = true;
   return QRTEBD_OK;
 }
@@ -858,7 +1224,9 @@ template <typename T> int probe_max_cluster() {
 }
 
 template <typename T> int launch_panel(const PanelArgs<T>& pa, int cs, cudaStream_t st) {
-  const size_t smem = panel_smem_bytes<T>(pa.rps, pa.kb);
+  // the register-file form whenever each warp's slab share fits (complex64)
+  const bool rf = std::is_same<T, float>::value && pa.rps <= (RF_NT / 32 - 1) * RF_RPW;
+  const size_t smem = rf ? panel_rf_smem_bytes<T>(pa.kb) : panel_smem_bytes<T>(pa.rps, pa.kb);
   const int mr = pa.m - pa.k0;
   if (pa.kb < 1 || pa.kb > KBMAX || mr < pa.kb || cs < 1 || cs > 16 || pa.rps < 0 ||
       (long long)pa.rps * cs < mr - pa.kb || smem > (size_t)smem_cap()) {
@@ -868,7 +1236,7 @@ template <typename T> int launch_panel(const PanelArgs<T>& pa, int cs, cudaStrea
   QR_TRY(set_panel_attrs<T>());
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(cs, 1, 1);
-  cfg.blockDim = dim3(PT, 1, 1);
+  cfg.blockDim = dim3(rf ? RF_NT : PT, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[2];
@@ -880,7 +1248,12 @@ template <typename T> int launch_panel(const PanelArgs<T>& pa, int cs, cudaStrea
   // algorithmic work of a Householder panel: 8 mr kb^2 real flops; traffic: the panel
   // read once, V and R/zeros written once
   ProfScope prof(PROF_QR_PANEL, st, 8.0 * mr * pa.kb * pa.kb, 3.0 * mr * pa.kb * sizeof(cx<T>));
-  QR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_qr_panel<T>, pa));
+  if constexpr (std::is_same<T, float>::value) {
+    if (rf) QR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_qr_panel_rf<RF_RPW>, pa));
+    else QR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_qr_panel<T>, pa));
+  } else {
+    QR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_qr_panel<T>, pa));
+  }
   note_launch();
   return QRTEBD_OK;
 }

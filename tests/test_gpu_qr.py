@@ -40,6 +40,23 @@ def test_qr_matches_lapack(prec, m, n):
 
 
 @pytest.mark.parametrize("prec", list(TOL))
+@pytest.mark.parametrize("m,n", [(5152, 33), (6000, 40)])
+def test_qr_tall_panels(prec, m, n):
+    # panels of up to 320 slab rows per CTA of a 16-CTA cluster hold the slab in registers
+    # (complex64); taller ones keep every row in shared memory: both forms, one row past
+    # a full register share and a ragged last panel
+    A = W.complex_gaussian(W.rng(m + n), (m, n))
+    if prec != "c128":
+        A = A.astype(np.complex64).astype(np.complex128)
+    Q, R = _run(prec, A)
+    tol = TOL[prec]
+    assert np.linalg.norm(Q @ R - A) / np.linalg.norm(A) < tol
+    assert np.abs(Q.conj().T @ Q - np.eye(n)).max() < tol * 5
+    Rl = np.linalg.qr(A, mode="r")
+    assert np.linalg.norm(R - Rl) / np.linalg.norm(Rl) < tol * 10
+
+
+@pytest.mark.parametrize("prec", list(TOL))
 def test_qr_rank_deficient_gives_isometry(prec):
     # Householder returns an exact isometry even for rank-deficient input (Sec. II
     # readings: never CholeskyQR), the case eta > rank theta~
