@@ -543,7 +543,7 @@ constexpr int RF_RPW = 30;  // slab rows per row warp held in registers (11 x 30
 
 template <typename T> __host__ __device__ inline size_t panel_rf_smem_bytes(int kb) {
   constexpr int slots = (RF_NT / 32 - 1) * RF_RPW;
-  return a16((size_t)kb * (kb + 1) * sizeof(cx<T>)) + a16((size_t)(2 * (kb + slots) + slots) * sizeof(cx<T>)) +
+  return a16((size_t)kb * (kb + 1) * sizeof(cx<T>)) + a16((size_t)(2 * (KBMAX + slots) + slots) * sizeof(cx<T>)) +
          a16((size_t)(RF_NT / 32 - 1) * 32 * 16) + 16 + PanelSmem<T>::fixed(RF_NT / 32);
 }
 
@@ -561,7 +561,8 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
   using T = float;
   using L = PanelSmem<T>;
   constexpr int NT = RF_NT, NW = NT / 32, RW = NW - 1;  // warps 1 .. RW hold the rows
-  static_assert(RW <= 16 && RPW <= 32, "one tree level per halving; one slab row per lane");
+  static_assert(RW <= 16 && RPW <= 32 && RPW % 2 == 0,
+                "one tree level per halving; one slab row per lane; slab rows in 16-byte pairs");
   constexpr int TPW = (KBMAX + RW - 1) / RW;          // top rows per row warp: t = rw + RW i
   pdl_launch_dependents();
   pdl_wait();
@@ -580,9 +581,10 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
   const int cnt = rw < 0 ? 0 : min(nslab, q0 + spw) - q0;  // this warp's slab rows q0 .. q0 + cnt - 1
   const int tcnt = rw < 0 ? 0 : TPW;               // top rows t = rw + RW i < kb, i < tcnt
   const bool top_counts = rank == 0;               // top rows enter rank 0's sums only
-  // X: the top rows, then RPW slots per row warp (rows past cnt stay zero, so the row
-  // loops below run over all RPW slots without guards); Y: RPW slots per row warp
-  const int xs = kb + RW * RPW;
+  // X: KBMAX top-row slots, then RPW slots per row warp (rows past cnt stay zero, so the
+  // row loops below run over all RPW slots without guards, two rows per 16-byte access);
+  // Y: RPW slots per row warp
+  const int xs = KBMAX + RW * RPW;
   const int xb = rw < 0 ? 0 : rw * RPW;            // this warp's first slab slot
 
   unsigned char* q = sm;
@@ -636,11 +638,11 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
     if (lane < cnt) {
       cx<T> x = Y[xb + lane];
       if (jp >= 0) {
-        const cx<T> u = Xp[kb + xb + lane];
+        const cx<T> u = Xp[KBMAX + xb + lane];
         x = upd_rn(x, u, cwsj);
         cfma<T>(hp, cconj<T>(x), u);
       }
-      Xn[kb + xb + lane] = x;
+      Xn[KBMAX + xb + lane] = x;
       nacc.add_sq(x.x); nacc.add_sq(x.y);
     }
     if (lane < tcnt) {
@@ -668,14 +670,18 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
     //      were before reflector jp; the owner of row jn copies it for the reflector
     cx<T> acc0 = zero, acc1 = zero;
     if (rw >= 0) {  // warp-uniform: the reflector warp skips the predicated row loops
-      const cx<T>* Xs = Xn + kb + xb;
+      const float4* Xs = reinterpret_cast<const float4*>(Xn + KBMAX + xb);
       cx<T> acc2 = zero, acc3 = zero;
 #pragma unroll
-      for (int r = 0; r < RPW; r += 4) {
-        cfma<T>(acc0, cconj<T>(Xs[r]), R[r]);
-        if (r + 1 < RPW) cfma<T>(acc1, cconj<T>(Xs[r + 1]), R[r + 1]);
-        if (r + 2 < RPW) cfma<T>(acc2, cconj<T>(Xs[r + 2]), R[r + 2]);
-        if (r + 3 < RPW) cfma<T>(acc3, cconj<T>(Xs[r + 3]), R[r + 3]);
+      for (int r = 0; r < RPW; r += 2) {
+        const float4 e = Xs[r / 2];
+        if ((r / 2) & 1) {
+          cfma<T>(acc2, mk<T>(e.x, -e.y), R[r]);
+          cfma<T>(acc3, mk<T>(e.z, -e.w), R[r + 1]);
+        } else {
+          cfma<T>(acc0, mk<T>(e.x, -e.y), R[r]);
+          cfma<T>(acc1, mk<T>(e.z, -e.w), R[r + 1]);
+        }
       }
       acc0 = cadd<T>(acc0, acc2);
       acc1 = cadd<T>(acc1, acc3);
@@ -735,9 +741,13 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
     //      cws = 0 elsewhere), in registers and on this warp's top rows; lane jn + 1
     //      publishes its slab values for the next step's column pass
     if (jp >= 0 && rw >= 0) {
-      const cx<T>* Vs = Xp + kb + xb;
+      const float4* Vs = reinterpret_cast<const float4*>(Xp + KBMAX + xb);
 #pragma unroll
-      for (int r = 0; r < RPW; ++r) R[r] = upd_rn(R[r], Vs[r], cws);
+      for (int r = 0; r < RPW; r += 2) {
+        const float4 e = Vs[r / 2];
+        R[r] = upd_rn(R[r], mk<T>(e.x, e.y), cws);
+        R[r + 1] = upd_rn(R[r + 1], mk<T>(e.z, e.w), cws);
+      }
 #pragma unroll
       for (int i = 0; i < TPW; ++i) {
         const int t = rw + RW * i;
@@ -751,28 +761,29 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
     if (rw >= 0 && lane == jn + 1) {
 #pragma unroll
       for (int r = 0; r < RPW; ++r)
-        Y[xb + r] = R[r];
+        if (r % 2 == 0) reinterpret_cast<float4*>(Y + xb)[r / 2] = make_float4(R[r].x, R[r].y, R[r + 1].x, R[r + 1].y);
     }
-    // ---- E. warp 0: all ranks' sums, the correction by h, reflector jn
+    // ---- E. warp 0: the pivot row, alpha and the Gram scales need no message (formed
+    //      before the wait); then all ranks' sums, the correction by h, reflector jn
     if (warp == 0) {
+      cx<T> pc = sh.pivb[buf * SLOTS + col];
+      if (jp >= 0) pc = upd_rn(pc, Xp[jn], cws);
+      const cx<T> alpha = shfl_cx<T>(pc, jn);
+      const cx<T> scl_l = lane < jn ? sh.scl[lane] : zero;
       if (!mbar_wait_cl(&sh.mb[buf], (uint32_t)((jn >> 1) & 1))) ok = false;
-      // every lane sums all ranks' headers (a fixed, predicated unroll and a tree)
+      // headers: lane r of each half-warp holds rank r's, summed over the half-warp
       NAcc<T> ns;
-      float hx, hy;
-      {
-        NAcc<T> nr[16];
-        float hxr[16], hyr[16];
+      float hx = 0.f, hy = 0.f;
+      if ((lane & 15) < CS) {
+        const float4 e = *reinterpret_cast<const float4*>(sh.recvm + (buf * 16 + (lane & 15)) * L::MSG);
+        ns.hi = e.x; ns.lo = e.y; hx = e.z; hy = e.w;
+      }
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
-          const float4 e = r < CS ? *reinterpret_cast<const float4*>(sh.recvm + (buf * 16 + r) * L::MSG)
-                                  : make_float4(0.f, 0.f, 0.f, 0.f);
-          nr[r].hi = e.x; nr[r].lo = e.y; hxr[r] = e.z; hyr[r] = e.w;
-        }
-#pragma unroll
-        for (int h = 8; h > 0; h >>= 1)
-#pragma unroll
-          for (int r = 0; r < h; ++r) { nr[r].add_nr(nr[r + h]); hxr[r] += hxr[r + h]; hyr[r] += hyr[r + h]; }
-        ns = nr[0]; hx = hxr[0]; hy = hyr[0];
+      for (int o = 8; o > 0; o >>= 1) {
+        const float h = __shfl_xor_sync(0xffffffffu, ns.hi, o), l = __shfl_xor_sync(0xffffffffu, ns.lo, o);
+        ns.add_nr(h, l);
+        hx += __shfl_xor_sync(0xffffffffu, hx, o);
+        hy += __shfl_xor_sync(0xffffffffu, hy, o);
       }
       cx<T> S;
       {
@@ -786,12 +797,7 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
           for (int r = 0; r < h; ++r) v[r] = cadd<T>(v[r], v[r + h]);
         S = v[0];
       }
-      cx<T> pc = sh.pivb[buf * SLOTS + col];
-      if (jp >= 0) {
-        S = csub<T>(S, cmul<T>(mk<T>(hx, hy), cws));
-        pc = upd_rn(pc, Xp[jn], cws);
-      }
-      const cx<T> alpha = shfl_cx<T>(pc, jn);
+      if (jp >= 0) S = csub<T>(S, cmul<T>(mk<T>(hx, hy), cws));
       T beta, tr, ti, sr, si;
       reflector(ns.value(), alpha.x, alpha.y, beta, tr, ti, sr, si);
       if (lane == 0 && rank == 0 && !(isfinite(beta) && isfinite(sr) && isfinite(si)))
@@ -800,7 +806,7 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
       const bool u = lane > jn && lane < kb;
       const cx<T> cwl = u ? cmul<T>(cconj<T>(tau), cadd<T>(pc, cmul<T>(cconj<T>(sc), S))) : zero;
       if (lane < jn) {
-        const cx<T> gv = cmul<T>(cconj<T>(sh.scl[lane]), cadd<T>(cconj<T>(pc), cmul<T>(sc, cconj<T>(S))));
+        const cx<T> gv = cmul<T>(cconj<T>(scl_l), cadd<T>(cconj<T>(pc), cmul<T>(sc, cconj<T>(S))));
         sh.Ts[lane * (KBMAX + 1) + jn] = gv;
       }
       cx<T>* bb = sh.bc + buf * (SLOTS + 2);
