@@ -860,91 +860,78 @@ template <typename T> __device__ __forceinline__ void cp_async_cx(cx<T>* dst_sme
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 // ------------------------------------------------------ outer compact-WY factor
-// T of an outer block from its inner blocks' factors (on the diagonal of Tb) and the Gram
-// matrix G = V^dag V of the block: column block by column block,
-//   T[0:c0, c0:c0+w] = -T[0:c0, 0:c0] G[0:c0, c0:c0+w] T[c0:c0+w, c0:c0+w].
-// One CTA; tmp holds G T_cc (c0 x w).
-constexpr int TO_NT = 1024;
+// T of an outer block straight from its Householder scalars and the Gram matrix
+// G = V^dag V of the block: with U the strict upper part of G, T^{-1} = diag(1/tau) + U,
+// so column j of T solves t_i = tau_i (delta_ij - sum_{k > i} U_ik t_k), i = j, ..., 0 (a
+// form that also covers tau_i = 0, H_i = I). The columns are independent: one warp per
+// column, lane = row (rows lane + 32 q); step k finalises t_k on its lane and broadcasts
+// it, and the rows above take U_ik t_k, with U_ik = conj(G[k, i]) read along row k of G.
+constexpr int TB_NT = 256;
+// complex64 stages the rows of G the CTA's columns read into shared memory (at most
+// NBO x NBO x 8 bytes = 128 KB); complex128 reads G in place
+template <typename T> constexpr bool kTbStage = sizeof(cx<T>) == 8;
+template <typename T> size_t t_block_smem(int kbo, int cta) {
+  const int rows = std::min(kbo, (cta + 1) * (TB_NT / 32));
+  return kTbStage<T> ? (size_t)rows * kbo * sizeof(cx<T>) : 0;
+}
 template <typename T>
-__global__ void __launch_bounds__(TO_NT) k_t_outer(cx<T>* Tb, int ldt, const cx<T>* G, int ldg,
-                                                   int kbo, int nb, cx<T>* tmp_g) {
-  // T (kbo x kbo, upper) in shared memory when it fits (complex64), else in place
+__global__ void __launch_bounds__(TB_NT) k_t_block(cx<T>* Tb, int ldt, const cx<T>* __restrict__ G, int ldg,
+                                                   const cx<T>* __restrict__ tau, int kbo) {
   extern __shared__ __align__(16) unsigned char sm[];
   pdl_launch_dependents();
   pdl_wait();
-  const bool in_smem = sizeof(cx<T>) == 8;
-  const int lds = kbo + 1;
-  cx<T>* Ts = in_smem ? reinterpret_cast<cx<T>*>(sm) : Tb;
-  const int ldT = in_smem ? lds : ldt;
-  cx<T>* tmp = in_smem ? Ts + (size_t)kbo * lds : tmp_g;
-  cx<T>* Gs = in_smem ? tmp + (size_t)kbo * nb : nullptr;  // G[0:c0, c0:c0+w]
-  if (in_smem) {
-    for (int o = threadIdx.x; o < kbo * kbo; o += TO_NT)
-      cp_async_cx<T>(Ts + (o / kbo) * lds + o % kbo, Tb + (long long)(o / kbo) * ldt + o % kbo);
+  constexpr int Q = NBO / 32;  // rows per lane
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (TB_NT / 32) + (threadIdx.x >> 5);
+  const int rows = min(kbo, (int)(blockIdx.x + 1) * (TB_NT / 32));  // rows of G this CTA reads
+  const cx<T>* Gr = G;
+  int ldr = ldg;
+  if constexpr (kTbStage<T>) {
+    cx<T>* Gs = reinterpret_cast<cx<T>*>(sm);
+    for (int o = threadIdx.x; o < rows * kbo; o += TB_NT)
+      cp_async_cx<T>(Gs + o, G + (long long)(o / kbo) * ldg + o % kbo);
     cp_async_wait_all();
     __syncthreads();
+    Gr = Gs; ldr = kbo;
   }
-  for (int c0 = nb; c0 < kbo; c0 += nb) {
-    const int w = min(nb, kbo - c0);
-    const cx<T>* Gb = G + c0;
-    int ldgb = ldg;
-    if (in_smem) {
-      for (int o = threadIdx.x; o < c0 * w; o += TO_NT)
-        cp_async_cx<T>(Gs + o, G + (long long)(o / w) * ldg + c0 + o % w);
-      cp_async_wait_all();
-      __syncthreads();
-      Gb = Gs; ldgb = w;
-    }
-    // tmp = G[0:c0, c0:c0+w] T[c0:c0+w, c0:c0+w]: 2 x 2 output tiles per thread (the
-    // diagonal block is upper triangular, so k runs to the tile's last column)
-    const int tr = (c0 + 1) / 2, tc = (w + 1) / 2;
-    for (int o = threadIdx.x; o < tr * tc; o += TO_NT) {
-      const int i0 = 2 * (o / tc), j0 = 2 * (o % tc);
-      cx<T> a00 = mk<T>(0, 0), a01 = a00, a10 = a00, a11 = a00;
-      const int kend = min(w, j0 + 2);
-      const bool i1 = i0 + 1 < c0, j1 = j0 + 1 < w;
-      for (int k = 0; k < kend; ++k) {
-        const cx<T> g0 = Gb[(long long)i0 * ldgb + k];
-        const cx<T> g1 = i1 ? Gb[(long long)(i0 + 1) * ldgb + k] : mk<T>(0, 0);
-        const cx<T> t0 = Ts[(c0 + k) * ldT + c0 + j0];
-        const cx<T> t1 = j1 ? Ts[(c0 + k) * ldT + c0 + j0 + 1] : mk<T>(0, 0);
-        cfma<T>(a00, g0, t0); cfma<T>(a01, g0, t1); cfma<T>(a10, g1, t0); cfma<T>(a11, g1, t1);
-      }
-      tmp[i0 * w + j0] = a00;
-      if (j1) tmp[i0 * w + j0 + 1] = a01;
-      if (i1) { tmp[(i0 + 1) * w + j0] = a10; if (j1) tmp[(i0 + 1) * w + j0 + 1] = a11; }
-    }
-    __syncthreads();
-    // T[0:c0, c0:c0+w] = -T[0:c0, 0:c0] tmp (T upper triangular: k from the tile's row)
-    for (int o = threadIdx.x; o < tr * tc; o += TO_NT) {
-      const int i0 = 2 * (o / tc), j0 = 2 * (o % tc);
-      cx<T> a00 = mk<T>(0, 0), a01 = a00, a10 = a00, a11 = a00;
-      const bool i1 = i0 + 1 < c0, j1 = j0 + 1 < w;
-      for (int k = i0; k < c0; ++k) {
-        const cx<T> u0 = Ts[i0 * ldT + k];
-        const cx<T> u1 = i1 ? Ts[(i0 + 1) * ldT + k] : mk<T>(0, 0);  // 0 for k = i0 (lower part)
-        const cx<T> m0 = tmp[k * w + j0];
-        const cx<T> m1 = j1 ? tmp[k * w + j0 + 1] : mk<T>(0, 0);
-        cfma<T>(a00, u0, m0); cfma<T>(a01, u0, m1); cfma<T>(a10, u1, m0); cfma<T>(a11, u1, m1);
-      }
-      Ts[i0 * ldT + c0 + j0] = mk<T>(-a00.x, -a00.y);
-      if (j1) Ts[i0 * ldT + c0 + j0 + 1] = mk<T>(-a01.x, -a01.y);
-      if (i1) {
-        Ts[(i0 + 1) * ldT + c0 + j0] = mk<T>(-a10.x, -a10.y);
-        if (j1) Ts[(i0 + 1) * ldT + c0 + j0 + 1] = mk<T>(-a11.x, -a11.y);
-      }
-    }
-    __syncthreads();
+  if (j >= kbo) return;
+  const cx<T> zero = mk<T>(0, 0);
+  cx<T> acc[Q], t[Q], tl[Q], g[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int i = lane + 32 * q;
+    acc[q] = zero; t[q] = zero;
+    tl[q] = i < kbo ? tau[i] : zero;
+    g[q] = (i < j) ? Gr[(long long)j * ldr + i] : zero;  // row j, for the first step
   }
-  if (in_smem)
-    for (int o = threadIdx.x; o < kbo * kbo; o += TO_NT)
-      Tb[(long long)(o / kbo) * ldt + o % kbo] = Ts[(o / kbo) * lds + o % kbo];
+  for (int k = j; k >= 0; --k) {
+    const int qk = k >> 5, lk = k & 31;
+    // row k - 1 of G for the next step, loaded ahead of this step's arithmetic
+    cx<T> gn[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int i = lane + 32 * q;
+      gn[q] = (k > 0 && i < k - 1) ? Gr[(long long)(k - 1) * ldr + i] : zero;
+    }
+    cx<T> ak = acc[0], tk_l = tl[0];
+#pragma unroll
+    for (int q = 1; q < Q; ++q)
+      if (qk == q) { ak = acc[q]; tk_l = tl[q]; }
+    const cx<T> tk = shfl_cx<T>(cmul<T>(tk_l, csub<T>(mk<T>(k == j ? T(1) : T(0), T(0)), ak)), lk);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      if (qk == q && lane == lk) t[q] = tk;
+      cfma<T>(acc[q], cconj<T>(g[q]), tk);  // g = 0 on rows i >= k
+      g[q] = gn[q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int i = lane + 32 * q;
+    if (i < kbo) Tb[(long long)i * ldt + j] = t[q];  // t = 0 below the diagonal
+  }
 }
-
-template <typename T> size_t t_outer_smem(int kbo, int nb) {
-  return sizeof(cx<T>) == 8 ? ((size_t)kbo * (kbo + 1) + 2 * (size_t)kbo * nb) * sizeof(cx<T>) : 0;
-}
-template <typename T> bool g_to_attr = false;
+template <typename T> bool g_tb_attr = false;
 
 // ------------------------------------------------------ fused narrow block-reflector update
 // C <- (I - V T V^dag)^dag C = C - V T^dag (V^dag C) for the columns of an outer block right
@@ -1323,7 +1310,6 @@ template <typename T> void qr_carve(Arena& ar, int m, int n, QrScratch<T>& s) {
   s.W2 = ar.take<cx<T>>((size_t)nbo * n);
   s.W2s = ar.take<cx<T>>((size_t)nbo * n);
   s.G = ar.take<cx<T>>((size_t)nbo * nbo);
-  s.tmp = ar.take<cx<T>>((size_t)nbo * KBMAX);
   s.wy_part = ar.take<cx<T>>((size_t)std::max(num_sms(), 1) * WY_KB * WY_NC);
   s.wy_W = ar.take<cx<T>>((size_t)WY_KB * WY_NC);
   s.bar = ar.take<unsigned>(64);
@@ -1395,18 +1381,17 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
     }
     const cx<T>* Vb = s.V + (long long)ko * ldv + ko;
     if (kbo > nb) {
-      // T of the outer block from the inner ones: with G = V^dag V,
-      // T[0:c0, c0:c0+w] = -T[0:c0, 0:c0] G[0:c0, c0:c0+w] T[c0:c0+w, c0:c0+w]
+      // T of the outer block from G = V^dag V and the Householder scalars
       GemmArgs<T> gg{kbo, kbo, mo, Vb, 1, ldv, true, Vb, ldv, 1, false, s.G, nbo, 1, one, zero};
       QR_TRY(run_gemm<T>(gg, s, st, gm));
-      const size_t tsm = t_outer_smem<T>(kbo, nb);
-      if (!g_to_attr<T>) {
-        QR_CUDA_TRY(cudaFuncSetAttribute(k_t_outer<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)t_outer_smem<T>(NBO, KBMAX)));
-        g_to_attr<T> = true;
+      if (!g_tb_attr<T>) {
+        QR_CUDA_TRY(cudaFuncSetAttribute(k_t_block<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)t_block_smem<T>(NBO, NBO)));
+        g_tb_attr<T> = true;
       }
-      QR_CUDA_TRY(launch_pdl(k_t_outer<T>, dim3(1), dim3(TO_NT), tsm, st, Tb, nbo,
-                             static_cast<const cx<T>*>(s.G), nbo, kbo, nb, s.tmp));
+      const int nct = (int)ceil_div(kbo, TB_NT / 32);
+      QR_CUDA_TRY(launch_pdl(k_t_block<T>, dim3((unsigned)nct), dim3(TB_NT), t_block_smem<T>(kbo, nct - 1), st, Tb,
+                             nbo, static_cast<const cx<T>*>(s.G), nbo, static_cast<const cx<T>*>(s.tau + ko), kbo));
       note_launch();
     }
     // VT = V T of this block, kept for the trailing updates and the explicit Q

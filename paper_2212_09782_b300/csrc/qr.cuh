@@ -23,7 +23,6 @@ template <typename T> struct QrScratch {
   cx<T>* W2 = nullptr;     // nb x n
   cx<T>* W2s = nullptr;    // W2 of the look-ahead (side-stream) updates
   cx<T>* G = nullptr;      // outer-block Gram matrix V^dag V
-  cx<T>* tmp = nullptr;    // T assembly scratch
   cx<T>* wy_part = nullptr;  // fused narrow update: per-CTA partials of V^dag C
   cx<T>* wy_W = nullptr;     // and their sum
   unsigned* bar = nullptr;   // grid-barrier counter and generation
