@@ -42,11 +42,11 @@ FP32_ALU_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 FP64_ALU_TFLOPS = 1.25
 
 
-# DRAM traffic of the panel kernel from one ncu capture (profiles/k_qr_panel_chi512.md:
-# complex64, 2464 x 32 panel, 675328 bytes read, 0 written, against 3 x 2464 x 32 x 8
-# algorithmic bytes). Traffic grows with the panel's rows, so a launch's traffic is this
-# ratio times its algorithmic bytes.
-PANEL_NCU_DRAM_OVER_ALGORITHMIC = 675328 / (3 * 2464 * 32 * 8)
+# DRAM traffic of the panel kernel (k_qr_panel_rf) from one ncu capture
+# (profiles/k_qr_panel_chi512.md: complex64, 2464 x 32 panel, 696064 bytes read, 0 written,
+# against 3 x 2464 x 32 x 8 algorithmic bytes). Traffic grows with the panel's rows, so a
+# launch's traffic is this ratio times its algorithmic bytes.
+PANEL_NCU_DRAM_OVER_ALGORITHMIC = 696064 / (3 * 2464 * 32 * 8)
 
 
 def prof_families(L):
@@ -89,7 +89,8 @@ def family_roofline(L, fam, ms, n, flops, nbytes, prec, peaks, src):
         out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "peak_source": "derived CUDA-core peak (SMs x lanes x clock)",
                     "algorithmic_flops_per_launch": flops / n,
-                    "kernel": {L.PROF_QR_PANEL: "k_qr_panel", L.PROF_SIMT_GEMM: "k_gemm",
+                    "kernel": {L.PROF_QR_PANEL: "k_qr_panel" if prec == L.C128 else "k_qr_panel_rf",
+                               L.PROF_SIMT_GEMM: "k_apply_wy / k_gemm",
                                L.PROF_BOND_GEMM: "k_gemm", L.PROF_TC_GEMM: "k_gemm"}[fam]})
         if fam == L.PROF_QR_PANEL:
             out["limiter"] = "latency: one cluster-wide exchange per column (sequential in the column)"
