@@ -182,6 +182,27 @@ __device__ __forceinline__ void reflector(T xn2, T alr, T ali, T& beta, T& tr, T
   }
 }
 
+// The same scalars for the complex64 register panel with one division on the critical
+// path: 1/beta and 1/|alpha - beta|^2 in parallel, tau and scale by products (about one
+// unit in the last place from correctly rounded, as LAPACK's own reciprocal forms). When
+// |alpha - beta|^2 could overflow the Smith form above is used.
+__device__ __forceinline__ void reflector_rf(float xn2, float alr, float ali, float& beta, float& tr, float& ti,
+                                             float& sr, float& si) {
+  const float tot = alr * alr + ali * ali + xn2;
+  if (!(tot < 1e37f)) { reflector<float>(xn2, alr, ali, beta, tr, ti, sr, si); return; }
+  beta = alr; tr = ti = sr = si = 0.f;
+  if (!(xn2 == 0.f && ali == 0.f) && tot > 16.f * std::numeric_limits<float>::min()) {
+    const float nrm = sqrtf(tot);
+    beta = alr >= 0.f ? -nrm : nrm;
+    const float dr = alr - beta, di = ali;
+    const float rb = 1.f / beta, q = 1.f / fmaf(dr, dr, di * di);
+    tr = -dr * rb;
+    ti = -ali * rb;
+    sr = dr * q;
+    si = -di * q;
+  }
+}
+
 template <typename T> struct __align__(16) VXp { cx<T> v, x; };
 
 template <typename T> struct PanelSmem {
@@ -799,7 +820,7 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
       }
       if (jp >= 0) S = csub<T>(S, cmul<T>(mk<T>(hx, hy), cws));
       T beta, tr, ti, sr, si;
-      reflector(ns.value(), alpha.x, alpha.y, beta, tr, ti, sr, si);
+      reflector_rf(ns.value(), alpha.x, alpha.y, beta, tr, ti, sr, si);
       if (lane == 0 && rank == 0 && !(isfinite(beta) && isfinite(sr) && isfinite(si)))
         atomicOr(a.err, DEVERR_NUMERIC);
       const cx<T> sc = mk<T>(sr, si), tau = mk<T>(tr, ti);
@@ -1124,6 +1145,11 @@ int apply_wy(cx<T>* C, long long ldc, const cx<T>* V, long long ldv, const cx<T>
              int nc, int kb, int rpb, const QrScratch<T>& s, cudaStream_t st, unsigned* err) {
   const int G = (int)ceil_div(mr, rpb);
   const size_t smem = wy_smem<T>(rpb, kb, nc);
+  // the partial sums hold one block per CTA, for at most one CTA per SM
+  if (G > std::max(num_sms(), 1)) {
+    set_last_message("QR narrow update: more CTAs than its partial-sum buffer holds");
+    return QRTEBD_ERR_INVALID_ARG;
+  }
   if (!g_wy_attr<T>) {
     QR_CUDA_TRY(cudaFuncSetAttribute(k_apply_wy<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      48 * 1024 * 4));
