@@ -891,12 +891,12 @@ constexpr int TB_NT = 256;
 // complex64 stages the rows of G the CTA's columns read into shared memory (at most
 // NBO x NBO x 8 bytes = 128 KB); complex128 reads G in place
 template <typename T> constexpr bool kTbStage = sizeof(cx<T>) == 8;
-template <typename T> size_t t_block_smem(int kbo, int cta) {
+template <typename T> size_t t_cols_smem(int kbo, int cta) {
   const int rows = std::min(kbo, (cta + 1) * (TB_NT / 32));
   return kTbStage<T> ? (size_t)rows * kbo * sizeof(cx<T>) : 0;
 }
 template <typename T>
-__global__ void __launch_bounds__(TB_NT) k_t_block(cx<T>* Tb, int ldt, const cx<T>* __restrict__ G, int ldg,
+__global__ void __launch_bounds__(TB_NT) k_t_cols(cx<T>* Tb, int ldt, const cx<T>* __restrict__ G, int ldg,
                                                    const cx<T>* __restrict__ tau, int kbo) {
   extern __shared__ __align__(16) unsigned char sm[];
   pdl_launch_dependents();
@@ -949,6 +949,94 @@ __global__ void __launch_bounds__(TB_NT) k_t_block(cx<T>* Tb, int ldt, const cx<
 #pragma unroll
   for (int q = 0; q < Q; ++q) {
     const int i = lane + 32 * q;
+    if (i < kbo) Tb[(long long)i * ldt + j] = t[q];  // t = 0 below the diagonal
+  }
+}
+template <typename T> bool g_tc_attr = false;
+
+// Blocked form for inner panels of 32 columns: the inner factors T_bb that the panels left on
+// the diagonal of Tb are the inverses of the diagonal blocks of D + U, so column j of T is
+// solved block by block, b = block(j), ..., 0:
+//   t_b = T_bb (e_j[b] - acc_b),   acc_a += U_ab t_b for a < b,
+// U_ab[i][k] = G[32a + i][32b + k] = conj(G[32b + k][32a + i]). The tau_i = 0 rows come
+// out zero as in the column form, since those rows of T_bb are zero. One warp per column,
+// lane = row within a block; the vectors a step broadcasts go through a per-warp buffer.
+constexpr int TBB = 32;
+template <typename T> size_t t_block_smem(int kbo) {
+  const int nbk = (int)ceil_div(kbo, TBB), ur = TBB * (nbk - 1);
+  return ((size_t)ur * ur + (size_t)TBB * nbk * (TBB + 1) + (size_t)(TB_NT / 32) * TBB) * sizeof(cx<T>);
+}
+template <typename T>
+__global__ void __launch_bounds__(TB_NT) k_t_block(cx<T>* Tb, int ldt, const cx<T>* __restrict__ G, int ldg,
+                                                   int kbo) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  pdl_launch_dependents();
+  pdl_wait();
+  constexpr int Q = NBO / TBB, LDD = TBB + 1;
+  const int nbk = (int)ceil_div(kbo, TBB), ur = TBB * (nbk - 1);
+  cx<T>* Us = reinterpret_cast<cx<T>*>(sm);  // G[32 + r][c], r, c < ur (rows past kbo zero)
+  cx<T>* Dg = Us + (size_t)ur * ur;          // the diagonal blocks of T, row i: T[i][32 block(i) + k]
+  cx<T>* wb = Dg + (size_t)TBB * nbk * LDD;  // per warp: the vector being broadcast
+  const cx<T> zero = mk<T>(0, 0);
+  for (int o = threadIdx.x; o < ur * ur; o += TB_NT) {
+    const int r = o / ur, c = o % ur;
+    Us[o] = (TBB + r < kbo) ? G[(long long)(TBB + r) * ldg + c] : zero;
+  }
+  for (int o = threadIdx.x; o < TBB * nbk * TBB; o += TB_NT) {
+    const int i = o / TBB, k = o % TBB, c = (i / TBB) * TBB + k;
+    Dg[i * LDD + k] = (i < kbo && c < kbo) ? Tb[(long long)i * ldt + c] : zero;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int j = blockIdx.x * (TB_NT / 32) + warp;
+  if (j >= kbo) return;
+  cx<T>* w = wb + warp * TBB;
+  const int qj = j / TBB, jl = j % TBB;
+  cx<T> acc[Q], t[Q];
+#pragma unroll
+  for (int q = 0; q < Q; ++q) { acc[q] = zero; t[q] = zero; }
+  for (int b = qj; b >= 0; --b) {
+    cx<T> r = zero;
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      if (q == b) r = csub<T>(mk<T>(b == qj && lane == jl ? T(1) : T(0), T(0)), acc[q]);
+    w[lane] = r;
+    __syncwarp();
+    // t_b = T_bb r (upper triangular: the zeros below its diagonal are stored)
+    cx<T> s0 = zero, s1 = zero;
+    const cx<T>* drow = Dg + (TBB * b + lane) * LDD;
+#pragma unroll
+    for (int k = 0; k < TBB; k += 2) {
+      cfma<T>(s0, drow[k], w[k]);
+      cfma<T>(s1, drow[k + 1], w[k + 1]);
+    }
+    const cx<T> tb = cadd<T>(s0, s1);
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < Q; ++q)
+      if (q == b) t[q] = tb;
+    if (b == 0) break;
+    w[lane] = tb;
+    __syncwarp();
+    // acc_a += U_ab t_b for the blocks a < b
+    const cx<T>* urow = Us + (size_t)(TBB * b - TBB) * ur;
+#pragma unroll
+    for (int a = 0; a < Q - 1; ++a) {
+      if (a < b) {
+        cx<T> u0 = zero, u1 = zero;
+#pragma unroll
+        for (int k = 0; k < TBB; k += 2) {
+          cfma<T>(u0, cconj<T>(urow[(size_t)k * ur + TBB * a + lane]), w[k]);
+          cfma<T>(u1, cconj<T>(urow[(size_t)(k + 1) * ur + TBB * a + lane]), w[k + 1]);
+        }
+        acc[a] = cadd<T>(acc[a], cadd<T>(u0, u1));
+      }
+    }
+    __syncwarp();
+  }
+#pragma unroll
+  for (int q = 0; q < Q; ++q) {
+    const int i = TBB * q + lane;
     if (i < kbo) Tb[(long long)i * ldt + j] = t[q];  // t = 0 below the diagonal
   }
 }
@@ -1410,14 +1498,25 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
       // T of the outer block from G = V^dag V and the Householder scalars
       GemmArgs<T> gg{kbo, kbo, mo, Vb, 1, ldv, true, Vb, ldv, 1, false, s.G, nbo, 1, one, zero};
       QR_TRY(run_gemm<T>(gg, s, st, gm));
-      if (!g_tb_attr<T>) {
-        QR_CUDA_TRY(cudaFuncSetAttribute(k_t_block<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)t_block_smem<T>(NBO, NBO)));
-        g_tb_attr<T> = true;
-      }
       const int nct = (int)ceil_div(kbo, TB_NT / 32);
-      QR_CUDA_TRY(launch_pdl(k_t_block<T>, dim3((unsigned)nct), dim3(TB_NT), t_block_smem<T>(kbo, nct - 1), st, Tb,
-                             nbo, static_cast<const cx<T>*>(s.G), nbo, static_cast<const cx<T>*>(s.tau + ko), kbo));
+      if (nb == TBB) {
+        if (!g_tb_attr<T>) {
+          QR_CUDA_TRY(cudaFuncSetAttribute(k_t_block<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)t_block_smem<T>(NBO)));
+          g_tb_attr<T> = true;
+        }
+        QR_CUDA_TRY(launch_pdl(k_t_block<T>, dim3((unsigned)nct), dim3(TB_NT), t_block_smem<T>(kbo), st, Tb, nbo,
+                               static_cast<const cx<T>*>(s.G), nbo, kbo));
+      } else {
+        if (!g_tc_attr<T>) {
+          QR_CUDA_TRY(cudaFuncSetAttribute(k_t_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)t_cols_smem<T>(NBO, NBO)));
+          g_tc_attr<T> = true;
+        }
+        QR_CUDA_TRY(launch_pdl(k_t_cols<T>, dim3((unsigned)nct), dim3(TB_NT), t_cols_smem<T>(kbo, nct - 1), st,
+                               Tb, nbo, static_cast<const cx<T>*>(s.G), nbo, static_cast<const cx<T>*>(s.tau + ko),
+                               kbo));
+      }
       note_launch();
     }
     // VT = V T of this block, kept for the trailing updates and the explicit Q
