@@ -978,14 +978,18 @@ __global__ void __launch_bounds__(TB_NT) k_t_block(cx<T>* Tb, int ldt, const cx<
   cx<T>* Dg = Us + (size_t)ur * ur;          // the diagonal blocks of T, row i: T[i][32 block(i) + k]
   cx<T>* wb = Dg + (size_t)TBB * nbk * LDD;  // per warp: the vector being broadcast
   const cx<T> zero = mk<T>(0, 0);
+  // staged with cp.async (no load waits on its store), zeros stored directly
   for (int o = threadIdx.x; o < ur * ur; o += TB_NT) {
     const int r = o / ur, c = o % ur;
-    Us[o] = (TBB + r < kbo) ? G[(long long)(TBB + r) * ldg + c] : zero;
+    if (TBB + r < kbo) cp_async_cx<T>(Us + o, G + (long long)(TBB + r) * ldg + c);
+    else Us[o] = zero;
   }
   for (int o = threadIdx.x; o < TBB * nbk * TBB; o += TB_NT) {
     const int i = o / TBB, k = o % TBB, c = (i / TBB) * TBB + k;
-    Dg[i * LDD + k] = (i < kbo && c < kbo) ? Tb[(long long)i * ldt + c] : zero;
+    if (i < kbo && c < kbo) cp_async_cx<T>(Dg + i * LDD + k, Tb + (long long)i * ldt + c);
+    else Dg[i * LDD + k] = zero;
   }
+  cp_async_wait_all();
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int j = blockIdx.x * (TB_NT / 32) + warp;
