@@ -84,6 +84,12 @@ template <> struct NAcc<float> {
   }
   __device__ __forceinline__ void add_sq(float x) { const float p = x * x; add(p, fmaf(x, x, -p)); }
   __device__ __forceinline__ void add(const NAcc& o) { add(o.hi, o.lo); }
+  // the pair = x^2 + y^2 (error-free products, TwoSum of their high words)
+  __device__ __forceinline__ void set_abs2(float x, float y) {
+    const float a = x * x, b = y * y, ea = fmaf(x, x, -a), eb = fmaf(y, y, -b);
+    const float s = a + b, bb = s - a, e = (a - (s - bb)) + (b - bb);
+    hi = s; lo = e + (ea + eb);
+  }
   // sum over aligned groups of W lanes (every lane of a group ends with the group's sum)
   template <int W = 32> __device__ __forceinline__ void shfl_sum() {
 #pragma unroll
@@ -573,6 +579,9 @@ template <typename T> __host__ __device__ inline size_t panel_rf_smem_bytes(int 
 __device__ __forceinline__ cx<float> upd_rn(cx<float> p, cx<float> v, cx<float> c) {
   return mk<float>(__fmaf_rn(-v.x, c.x, __fmaf_rn(v.y, c.y, p.x)), __fmaf_rn(-v.x, c.y, __fmaf_rn(-v.y, c.x, p.y)));
 }
+__device__ __forceinline__ cx<float> cmul_rn(cx<float> a, cx<float> b) {
+  return mk<float>(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+}
 __device__ __forceinline__ cx<float> sub_rn(cx<float> p, cx<float> c) {
   return mk<float>(__fsub_rn(p.x, c.x), __fsub_rn(p.y, c.y));
 }
@@ -645,12 +654,12 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
   const uint32_t txb = (uint32_t)(CS * L::MSG);
   const int col = min(lane, kb - 1);
   cx<T> cw = zero, cws = zero;  // this lane's conj(tau) w_c of reflector j-1, and scale_{j-1} cw
+  cx<T> cwj = zero, cwsj = zero;  // the same two for column jn, the step's pivot column
 
   for (int jn = 0; jn < kb; ++jn) {
     const int jp = jn - 1, buf = jn & 1;
     const cx<T>* Xp = X + ((jn + 1) & 1) * xs;  // raw column jp
     cx<T>* Xn = X + buf * xs;                   // raw column jn
-    const cx<T> cwj = shfl_cx<T>(cw, jn), cwsj = shfl_cx<T>(cws, jn);
     NAcc<T> nacc, nacc2;
     cx<T> hp = zero, hp2 = zero;
     // ---- A. column jn alone, lane = row (one slab row per lane, cnt <= 32, and lanes
@@ -664,7 +673,7 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
         cfma<T>(hp, cconj<T>(x), u);
       }
       Xn[KBMAX + xb + lane] = x;
-      nacc.add_sq(x.x); nacc.add_sq(x.y);
+      nacc.set_abs2(x.x, x.y);
     }
     if (lane < tcnt) {
       const int t = rw + RW * lane;
@@ -673,7 +682,7 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
         if (jp >= 0 && t >= jp) x = (t == jp) ? sub_rn(x, cwj) : upd_rn(x, Xp[t], cwsj);
         Xn[t] = x;
         if (top_counts && t > jn) {
-          nacc2.add_sq(x.x); nacc2.add_sq(x.y);
+          nacc2.set_abs2(x.x, x.y);
           if (jp >= 0) cfma<T>(hp2, cconj<T>(x), Xp[t]);
         }
       }
@@ -838,7 +847,10 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
     {
       const cx<T>* bb = sh.bc + buf * (SLOTS + 2);
       cw = bb[lane];
-      cws = cmul<T>(bb[SLOTS], cw);
+      cws = cmul_rn(bb[SLOTS], cw);
+      // the next pivot column's pair, read directly (bit-identical to its lane's cws)
+      cwj = bb[min(jn + 1, SLOTS - 1)];
+      cwsj = cmul_rn(bb[SLOTS], cwj);
     }
   }
   if (!ok && tid == 0) atomicOr(a.err, DEVERR_TIMEOUT);
