@@ -571,7 +571,7 @@ constexpr int RF_RPW = 30;  // slab rows per row warp held in registers (11 x 30
 template <typename T> __host__ __device__ inline size_t panel_rf_smem_bytes(int kb) {
   constexpr int slots = (RF_NT / 32 - 1) * RF_RPW;
   return a16((size_t)kb * (kb + 1) * sizeof(cx<T>)) + a16((size_t)(2 * (KBMAX + slots) + slots) * sizeof(cx<T>)) +
-         a16((size_t)(RF_NT / 32 - 1) * 32 * 16) + 16 + PanelSmem<T>::fixed(RF_NT / 32);
+         a16((size_t)(RF_NT / 32 - 1) * 32 * 16) + 2 * 16 * 16 + PanelSmem<T>::fixed(RF_NT / 32);
 }
 
 // p - v c with every rounding fixed (four explicit FMAs), so that the trailing update and
@@ -622,13 +622,16 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
   cx<T>* X = reinterpret_cast<cx<T>*>(q);
   cx<T>* Y = X + 2 * xs; q += a16((size_t)(2 * xs + RW * RPW) * sizeof(cx<T>));
   float4* pn = reinterpret_cast<float4*>(q); q += a16((size_t)RW * 32 * sizeof(float4));  // lane partials
-  float4* hdr = reinterpret_cast<float4*>(q); q += 16;                                  // the CTA's header
+  float* recvh = reinterpret_cast<float*>(q); q += 2 * 16 * 16;  // [2][16 ranks] headers (norm hi, lo, h)
   const PanelShared<T> sh = carve_panel_shared<T>(q, NW);
   const long long k0 = a.k0;
   const cx<T> zero = mk<T>(0, 0);
+  uint64_t* mbh = sh.mb + 2;  // header barriers; sh.mb[0..1] count the slot messages
   if (tid == 0) {
     mbar_init1(&sh.mb[0]);
     mbar_init1(&sh.mb[1]);
+    mbar_init1(&mbh[0]);
+    mbar_init1(&mbh[1]);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int i = tid; i < 2 * xs + RW * RPW; i += NT) X[i] = zero;
@@ -651,7 +654,8 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
   asm volatile("cp.async.wait_all;" ::: "memory");
   cl.sync();  // every CTA's barriers exist before anyone sends; top rows and Y in place
   bool ok = true;
-  const uint32_t txb = (uint32_t)(CS * L::MSG);
+  constexpr int MSGS = SLOTS * (int)sizeof(cx<T>);      // a slot message: 16 chunks of 16 bytes
+  const uint32_t txs = (uint32_t)(CS * MSGS), txh = (uint32_t)(CS * 16);
   const int col = min(lane, kb - 1);
   cx<T> cw = zero, cws = zero;  // this lane's conj(tau) w_c of reflector j-1, and scale_{j-1} cw
   cx<T> cwj = zero, cwsj = zero;  // the same two for column jn, the step's pivot column
@@ -726,8 +730,53 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
     if (rw == jn % RW) sh.pivb[buf * SLOTS + lane] = Pt[jn * ldp + col];
     if (rw >= 0) {
       sh.wps[warp * SLOTS + lane] = cadd<T>(acc0, acc1);
+      // every row warp's slot partials and the pivot row copy are in place
+      asm volatile("bar.sync 3, %0;" ::"n"(NT) : "memory");
+      // ---- C. the row warps sum the CTA's slots and push them to their share of the
+      //      ranks: 16 chunks of 16 bytes (slot pairs) on the slot barrier
+      {
+        cx<T> s = zero;
+#pragma unroll
+        for (int w = 1; w < NW; ++w) s = cadd<T>(s, sh.wps[w * SLOTS + lane]);
+        if (rw == 0 && lane == 0) mbar_arm(&sh.mb[buf], txs);
+        const uint32_t mine = smem_addr(sh.recvm + (buf * 16 + rank) * MSGS);
+        const uint32_t mbl = smem_addr(&sh.mb[buf]);
+        const cx<T> sa = shfl_cx<T>(s, (2 * lane) & 31), sb = shfl_cx<T>(s, (2 * lane + 1) & 31);
+        if (lane < 16) {
+          const float4 ch = make_float4(sa.x, sa.y, sb.x, sb.y);
+          for (int r = rw; r < CS; r += RW) st_async_16(map_rank(mine + 16 * lane, r), ch, map_rank(mbl, r));
+        }
+      }
+      // ---- D. while the messages fly: reflector jp on the trailing columns (lanes c >= jn;
+      //      cws = 0 elsewhere), in registers and on this warp's top rows; lane jn + 1
+      //      publishes its slab values for the next step's column pass
+      if (jp >= 0) {
+        const float4* Vs = reinterpret_cast<const float4*>(Xp + KBMAX + xb);
+#pragma unroll
+        for (int r = 0; r < RPW; r += 2) {
+          const float4 e = Vs[r / 2];
+          R[r] = upd_rn(R[r], mk<T>(e.x, e.y), cws);
+          R[r + 1] = upd_rn(R[r + 1], mk<T>(e.z, e.w), cws);
+        }
+#pragma unroll
+        for (int i = 0; i < TPW; ++i) {
+          const int t = rw + RW * i;
+          if (i < tcnt && t < kb && t >= jp) {
+            const cx<T> p = Pt[t * ldp + col];
+            const cx<T> y = (t == jp) ? sub_rn(p, cw) : upd_rn(p, Xp[t], cws);
+            if (lane >= jn && lane < kb) Pt[t * ldp + lane] = y;
+          }
+        }
+      }
+      if (lane == jn + 1) {
+#pragma unroll
+        for (int r = 0; r < RPW; ++r)
+          if (r % 2 == 0)
+            reinterpret_cast<float4*>(Y + xb)[r / 2] = make_float4(R[r].x, R[r].y, R[r + 1].x, R[r + 1].y);
+      }
     } else {
-      // the reflector warp: the CTA's norm (double-float) and h from the lane partials
+      // ---- the reflector warp. The CTA's norm (double-float) and h from the lane partials
+      //      (during pass B), pushed at once to every rank on the header barrier
       asm volatile("bar.sync 2, %0;" ::"n"(NT) : "memory");
       NAcc<T> nw[RW];
       float hxw[RW], hyw[RW];
@@ -749,90 +798,51 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
         hx += __shfl_xor_sync(0xffffffffu, hx, o);
         hy += __shfl_xor_sync(0xffffffffu, hy, o);
       }
-      if (lane == 0) *hdr = make_float4(n0.hi, n0.lo, hx, hy);
-    }
-    __syncthreads();
-    // ---- C. send: every warp sums the CTA's message and pushes it to its share of the ranks
-    {
-      cx<T> s = zero;
-#pragma unroll
-      for (int w = 1; w < NW; ++w) s = cadd<T>(s, sh.wps[w * SLOTS + lane]);
-      const float4 h4 = *hdr;
-      if (warp == 0 && lane == 0) mbar_arm(&sh.mb[buf], txb);
-      const uint32_t mine = smem_addr(sh.recvm + (buf * 16 + rank) * L::MSG);
-      const uint32_t mbl = smem_addr(&sh.mb[buf]);
-      // 17 chunks of 16 bytes: (norm hi, lo, h), then slot pairs
-      const cx<T> sa = shfl_cx<T>(s, (2 * lane + 30) & 31), sb = shfl_cx<T>(s, (2 * lane + 31) & 31);
-      const float4 ch = lane == 0 ? h4 : make_float4(sa.x, sa.y, sb.x, sb.y);
-      if (lane < 17)
-        for (int r = warp; r < CS; r += NW) st_async_16(map_rank(mine + 16 * lane, r), ch, map_rank(mbl, r));
-    }
-    // ---- D. while the messages fly: reflector jp on the trailing columns (lanes c >= jn;
-    //      cws = 0 elsewhere), in registers and on this warp's top rows; lane jn + 1
-    //      publishes its slab values for the next step's column pass
-    if (jp >= 0 && rw >= 0) {
-      const float4* Vs = reinterpret_cast<const float4*>(Xp + KBMAX + xb);
-#pragma unroll
-      for (int r = 0; r < RPW; r += 2) {
-        const float4 e = Vs[r / 2];
-        R[r] = upd_rn(R[r], mk<T>(e.x, e.y), cws);
-        R[r + 1] = upd_rn(R[r + 1], mk<T>(e.z, e.w), cws);
-      }
-#pragma unroll
-      for (int i = 0; i < TPW; ++i) {
-        const int t = rw + RW * i;
-        if (i < tcnt && t < kb && t >= jp) {
-          const cx<T> p = Pt[t * ldp + col];
-          const cx<T> y = (t == jp) ? sub_rn(p, cw) : upd_rn(p, Xp[t], cws);
-          if (lane >= jn && lane < kb) Pt[t * ldp + lane] = y;
-        }
-      }
-    }
-    if (rw >= 0 && lane == jn + 1) {
-#pragma unroll
-      for (int r = 0; r < RPW; ++r)
-        if (r % 2 == 0) reinterpret_cast<float4*>(Y + xb)[r / 2] = make_float4(R[r].x, R[r].y, R[r + 1].x, R[r + 1].y);
-    }
-    // ---- E. warp 0: the pivot row, alpha and the Gram scales need no message (formed
-    //      before the wait); then all ranks' sums, the correction by h, reflector jn
-    if (warp == 0) {
+      if (lane == 0) mbar_arm(&mbh[buf], txh);
+      if (lane < CS)
+        st_async_16(map_rank(smem_addr(recvh + (buf * 16 + rank) * 4), lane), make_float4(n0.hi, n0.lo, hx, hy),
+                    map_rank(smem_addr(&mbh[buf]), lane));
+      asm volatile("bar.sync 3, %0;" ::"n"(NT) : "memory");
+      // ---- E. the pivot row (copied in pass B), alpha and the Gram scales; then all ranks'
+      //      headers and the reflector scalars while the slot messages are still in flight;
+      //      then the slots, the correction by h and conj(tau) w_c
       cx<T> pc = sh.pivb[buf * SLOTS + col];
       if (jp >= 0) pc = upd_rn(pc, Xp[jn], cws);
       const cx<T> alpha = shfl_cx<T>(pc, jn);
       const cx<T> scl_l = lane < jn ? sh.scl[lane] : zero;
-      if (!mbar_wait_cl(&sh.mb[buf], (uint32_t)((jn >> 1) & 1))) ok = false;
-      // headers: lane r of each half-warp holds rank r's, summed over the half-warp
+      if (!mbar_wait_cl(&mbh[buf], (uint32_t)((jn >> 1) & 1))) ok = false;
       NAcc<T> ns;
-      float hx = 0.f, hy = 0.f;
-      if ((lane & 15) < CS) {
-        const float4 e = *reinterpret_cast<const float4*>(sh.recvm + (buf * 16 + (lane & 15)) * L::MSG);
-        ns.hi = e.x; ns.lo = e.y; hx = e.z; hy = e.w;
+      float hxs = 0.f, hys = 0.f;
+      if ((lane & 15) < CS) {  // lane r of each half-warp holds rank r's header
+        const float4 e = *reinterpret_cast<const float4*>(recvh + (buf * 16 + (lane & 15)) * 4);
+        ns.hi = e.x; ns.lo = e.y; hxs = e.z; hys = e.w;
       }
 #pragma unroll
       for (int o = 8; o > 0; o >>= 1) {
         const float h = __shfl_xor_sync(0xffffffffu, ns.hi, o), l = __shfl_xor_sync(0xffffffffu, ns.lo, o);
         ns.add_nr(h, l);
-        hx += __shfl_xor_sync(0xffffffffu, hx, o);
-        hy += __shfl_xor_sync(0xffffffffu, hy, o);
+        hxs += __shfl_xor_sync(0xffffffffu, hxs, o);
+        hys += __shfl_xor_sync(0xffffffffu, hys, o);
       }
+      T beta, tr, ti, sr, si;
+      reflector_rf(ns.value(), alpha.x, alpha.y, beta, tr, ti, sr, si);
+      if (lane == 0 && rank == 0 && !(isfinite(beta) && isfinite(sr) && isfinite(si)))
+        atomicOr(a.err, DEVERR_NUMERIC);
+      const cx<T> sc = mk<T>(sr, si), tau = mk<T>(tr, ti);
+      if (!mbar_wait_cl(&sh.mb[buf], (uint32_t)((jn >> 1) & 1))) ok = false;
       cx<T> S;
       {
-        const unsigned char* base = sh.recvm + buf * 16 * L::MSG + L::HDR + col * sizeof(cx<T>);
+        const unsigned char* base = sh.recvm + buf * 16 * MSGS + col * sizeof(cx<T>);
         cx<T> v[16];
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = r < CS ? *reinterpret_cast<const cx<T>*>(base + r * L::MSG) : zero;
+        for (int r = 0; r < 16; ++r) v[r] = r < CS ? *reinterpret_cast<const cx<T>*>(base + r * MSGS) : zero;
 #pragma unroll
         for (int h = 8; h > 0; h >>= 1)
 #pragma unroll
           for (int r = 0; r < h; ++r) v[r] = cadd<T>(v[r], v[r + h]);
         S = v[0];
       }
-      if (jp >= 0) S = csub<T>(S, cmul<T>(mk<T>(hx, hy), cws));
-      T beta, tr, ti, sr, si;
-      reflector_rf(ns.value(), alpha.x, alpha.y, beta, tr, ti, sr, si);
-      if (lane == 0 && rank == 0 && !(isfinite(beta) && isfinite(sr) && isfinite(si)))
-        atomicOr(a.err, DEVERR_NUMERIC);
-      const cx<T> sc = mk<T>(sr, si), tau = mk<T>(tr, ti);
+      if (jp >= 0) S = csub<T>(S, cmul<T>(mk<T>(hxs, hys), cws));
       const bool u = lane > jn && lane < kb;
       const cx<T> cwl = u ? cmul<T>(cconj<T>(tau), cadd<T>(pc, cmul<T>(cconj<T>(sc), S))) : zero;
       if (lane < jn) {
