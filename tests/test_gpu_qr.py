@@ -40,11 +40,12 @@ def test_qr_matches_lapack(prec, m, n):
 
 
 @pytest.mark.parametrize("prec", list(TOL))
-@pytest.mark.parametrize("m,n", [(5152, 33), (6000, 40)])
+@pytest.mark.parametrize("m,n", [(5152, 33), (6000, 40), (13000, 40)])
 def test_qr_tall_panels(prec, m, n):
     # panels of up to 320 slab rows per CTA of a 16-CTA cluster hold the slab in registers
     # (complex64); taller ones keep every row in shared memory: both forms, one row past
-    # a full register share and a ragged last panel
+    # a full register share and a ragged last panel; at 13000 rows the panel narrows to fit
+    # shared memory, and the outer T takes its column-by-column form
     A = W.complex_gaussian(W.rng(m + n), (m, n))
     if prec != "c128":
         A = A.astype(np.complex64).astype(np.complex128)
