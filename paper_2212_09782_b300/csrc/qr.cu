@@ -1598,6 +1598,13 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
     const cx<T>* VTb = s.VT + (long long)ko * ldv + ko;
     cx<T>* Qs = Q + (long long)ko * ldq + ko;
     // Q_s <- (I - V T V^dag) Q_s = Q_s - (V T)(V^dag Q_s)
+    if (p == npo - 1) {
+      // Q_s = [I; 0] here, so V^dag Q_s is the conjugate transpose of V's first nq rows:
+      // one GEMM, Q_s -= (V T) V_top^dag
+      GemmArgs<T> g0{mo, nq, kbo, VTb, ldv, 1, false, Vb, 1, ldv, true, Qs, ldq, 1, mone, one};
+      QR_TRY(run_gemm<T>(g0, s, st, gm));
+      continue;
+    }
     GemmArgs<T> g1{kbo, nq, mo, Vb, 1, ldv, true, Qs, ldq, 1, false, s.W, nq, 1, one, zero};
     QR_TRY(run_gemm<T>(g1, s, st, gm));
     GemmArgs<T> g3{mo, nq, kbo, VTb, ldv, 1, false, s.W, nq, 1, false, Qs, ldq, 1, mone, one};
