@@ -1081,7 +1081,7 @@ constexpr int WY_NC = 128;
 constexpr int WY_KB = 32;
 
 
-template <typename T>
+template <typename T, int NQ>  // NQ = ceil(nc / 32) column groups of 32 (nc <= WY_NC)
 __global__ void __launch_bounds__(WY_NT) k_apply_wy(cx<T>* C, long long ldc, const cx<T>* V,
                                                     long long ldv, const cx<T>* Tt, int ldt, int mr,
                                                     int nc, int kb, int rpb, cx<T>* part, cx<T>* Wg,
@@ -1104,7 +1104,7 @@ __global__ void __launch_bounds__(WY_NT) k_apply_wy(cx<T>* C, long long ldc, con
   // register tiles: columns c_q = lane + 32 q (q < 4), and reflectors a_p (phase 1, 3a)
   // or rows r_p (phase 3b) = warp + 8 p; 16 independent accumulators per thread
   const int lane = tid & 31, wg = tid >> 5;
-  constexpr int NQ = WY_NC / 32, NP = WY_KB / 8;
+  constexpr int NP = WY_KB / 8;
   // (1) partial V^dag C
   {
     cx<T> acc[NP][NQ];
@@ -1265,8 +1265,10 @@ int apply_wy(cx<T>* C, long long ldc, const cx<T>* V, long long ldv, const cx<T>
     return QRTEBD_ERR_INVALID_ARG;
   }
   if (!g_wy_attr<T>) {
-    QR_CUDA_TRY(cudaFuncSetAttribute(k_apply_wy<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     48 * 1024 * 4));
+    QR_CUDA_TRY(cudaFuncSetAttribute(k_apply_wy<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024 * 4));
+    QR_CUDA_TRY(cudaFuncSetAttribute(k_apply_wy<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024 * 4));
+    QR_CUDA_TRY(cudaFuncSetAttribute(k_apply_wy<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024 * 4));
+    QR_CUDA_TRY(cudaFuncSetAttribute(k_apply_wy<T, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024 * 4));
     g_wy_attr<T> = true;
   }
   cudaLaunchConfig_t cfg = {};
@@ -1279,8 +1281,17 @@ int apply_wy(cx<T>* C, long long ldc, const cx<T>* V, long long ldv, const cx<T>
   at[0].val.cooperative = 1;
   cfg.attrs = at; cfg.numAttrs = 1;
   ProfScope prof(PROF_SIMT_GEMM, st, 16.0 * mr * nc * kb);
-  QR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_apply_wy<T>, C, ldc, V, ldv, Tt, ldt, mr, nc, kb, rpb,
-                                 s.wy_part, s.wy_W, s.bar, err));
+  // register tiles only as wide as the columns: ceil(nc / 32) groups of 32
+  switch ((nc + 31) / 32) {
+    case 1: QR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_apply_wy<T, 1>, C, ldc, V, ldv, Tt, ldt, mr, nc, kb, rpb,
+                                           s.wy_part, s.wy_W, s.bar, err)); break;
+    case 2: QR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_apply_wy<T, 2>, C, ldc, V, ldv, Tt, ldt, mr, nc, kb, rpb,
+                                           s.wy_part, s.wy_W, s.bar, err)); break;
+    case 3: QR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_apply_wy<T, 3>, C, ldc, V, ldv, Tt, ldt, mr, nc, kb, rpb,
+                                           s.wy_part, s.wy_W, s.bar, err)); break;
+    default: QR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_apply_wy<T, 4>, C, ldc, V, ldv, Tt, ldt, mr, nc, kb, rpb,
+                                            s.wy_part, s.wy_W, s.bar, err)); break;
+  }
   note_launch();
   return QRTEBD_OK;
 }
