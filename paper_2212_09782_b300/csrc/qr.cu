@@ -1079,6 +1079,7 @@ template <typename T> bool g_tb_attr = false;
 constexpr int WY_NT = 256;
 constexpr int WY_NC = 128;
 constexpr int WY_KB = 32;
+constexpr int WY_PW = 19;  // partials a warp sums in phase (2): CTAs <= 8 x 19 = 152
 
 
 template <typename T, int NQ>  // NQ = ceil(nc / 32) column groups of 32 (nc <= WY_NC)
@@ -1139,36 +1140,47 @@ __global__ void __launch_bounds__(WY_NT) k_apply_wy(cx<T>* C, long long ldc, con
   if (!grid_barrier(bar, G, err)) return;
   // (2) one CTA per column c: lane = reflector index a, the warps split the G partials
   //     of W[:, c] = V^dag C[:, c] (stored [CTA][column][a], so a warp reads 32 consecutive
-  //     values); warp 0 sums them and applies T^dag (W[k] by shuffle), so W2 = T^dag W is
-  //     formed once
+  //     values; each warp's share of the partials is loaded at once, then summed as a tree);
+  //     warp 0 sums the warps' values and applies T^dag, so W2 = T^dag W is formed once
   {
     __shared__ cx<T> red[WY_NT / 32][32];
+    __shared__ cx<T> wsum[32];
     const int warp = tid >> 5, lane2 = tid & 31;
     constexpr unsigned WS = WY_NT / 32;
     for (int c = b; c < nc; c += (int)G) {
-      cx<T> s0 = zero, s1 = zero, s2 = zero, s3 = zero;
+      cx<T> acc = zero;
       if (lane2 < kb) {
         const size_t off = (size_t)c * kb + lane2, stride = (size_t)kb * nc;
-        unsigned z = warp;
-        for (; z + 3 * WS < G; z += 4 * WS) {
-          s0 = cadd<T>(s0, part[z * stride + off]);
-          s1 = cadd<T>(s1, part[(z + WS) * stride + off]);
-          s2 = cadd<T>(s2, part[(z + 2 * WS) * stride + off]);
-          s3 = cadd<T>(s3, part[(z + 3 * WS) * stride + off]);
+        cx<T> v[WY_PW];
+#pragma unroll
+        for (int i = 0; i < WY_PW; ++i) {
+          const unsigned z = warp + WS * i;
+          v[i] = z < G ? part[z * stride + off] : zero;
         }
-        for (; z < G; z += WS) s0 = cadd<T>(s0, part[z * stride + off]);
+#pragma unroll
+        for (int h = 16; h > 0; h >>= 1)
+#pragma unroll
+          for (int i = 0; i < h; ++i)
+            if (i + h < WY_PW) v[i] = cadd<T>(v[i], v[i + h]);
+        acc = v[0];
       }
-      red[warp][lane2] = cadd<T>(cadd<T>(s0, s1), cadd<T>(s2, s3));
+      red[warp][lane2] = acc;
       __syncthreads();
       if (warp == 0) {
         cx<T> wv = zero;
         for (int w = 0; w < (int)WS; ++w) wv = cadd<T>(wv, red[w][lane2]);
-        cx<T> w2 = zero;
-        for (int k = 0; k < kb; ++k) {
-          const cx<T> wk = shfl_cx<T>(wv, k);
-          if (k <= lane2 && lane2 < kb) cfma<T>(w2, cconj<T>(Ts[k * kb + lane2]), wk);
+        wsum[lane2] = wv;
+        __syncwarp();
+        // W2[a] = sum_k conj(T[k][a]) W[k] (T upper triangular: its zeros are stored)
+        cx<T> a0 = zero, a1 = zero;
+        if (lane2 < kb) {
+          for (int k = 0; k + 1 < kb; k += 2) {
+            cfma<T>(a0, cconj<T>(Ts[k * kb + lane2]), wsum[k]);
+            cfma<T>(a1, cconj<T>(Ts[(k + 1) * kb + lane2]), wsum[k + 1]);
+          }
+          if (kb & 1) cfma<T>(a0, cconj<T>(Ts[(kb - 1) * kb + lane2]), wsum[kb - 1]);
+          Wg[(size_t)lane2 * nc + c] = cadd<T>(a0, a1);
         }
-        if (lane2 < kb) Wg[(size_t)lane2 * nc + c] = w2;
       }
       __syncthreads();
     }
@@ -1247,7 +1259,7 @@ template <typename T> size_t wy_smem(int rpb, int kb, int nc) {
 // cooperative launch), at least 8 rows per CTA.
 template <typename T> int wy_rows_per_block(int mr, int kb, int nc) {
   if (kb < 1 || kb > WY_KB || nc < 1 || nc > WY_NC || mr < 1) return 0;
-  const int rpb = std::max(8, (int)ceil_div(mr, num_sms()));
+  const int rpb = std::max(8, (int)ceil_div(mr, std::min(num_sms(), (WY_NT / 32) * WY_PW)));
   if (wy_smem<T>(rpb, kb, nc) > (size_t)48 * 1024 * 4) return 0;
   return rpb;
 }
@@ -1260,7 +1272,7 @@ int apply_wy(cx<T>* C, long long ldc, const cx<T>* V, long long ldv, const cx<T>
   const int G = (int)ceil_div(mr, rpb);
   const size_t smem = wy_smem<T>(rpb, kb, nc);
   // the partial sums hold one block per CTA, for at most one CTA per SM
-  if (G > std::max(num_sms(), 1)) {
+  if (G > std::max(num_sms(), 1) || G > (WY_NT / 32) * WY_PW) {
     set_last_message("QR narrow update: more CTAs than its partial-sum buffer holds");
     return QRTEBD_ERR_INVALID_ARG;
   }
