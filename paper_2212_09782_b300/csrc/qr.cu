@@ -162,6 +162,10 @@ __device__ __forceinline__ void st_async_16(uint32_t addr, float4 v, uint32_t mb
   asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
                ::"r"(addr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(mbar) : "memory");
 }
+__device__ __forceinline__ void st_async_8(uint32_t addr, float2 v, uint32_t mbar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f32 [%0], {%1, %2}, [%3];"
+               ::"r"(addr), "f"(v.x), "f"(v.y), "r"(mbar) : "memory");
+}
 __device__ __forceinline__ void st_async_16(uint32_t addr, double2 v, uint32_t mbar) {
   asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.f64 [%0], {%1, %2}, [%3];"
                ::"r"(addr), "d"(v.x), "d"(v.y), "r"(mbar) : "memory");
@@ -654,7 +658,7 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
   asm volatile("cp.async.wait_all;" ::: "memory");
   cl.sync();  // every CTA's barriers exist before anyone sends; top rows and Y in place
   bool ok = true;
-  constexpr int MSGS = SLOTS * (int)sizeof(cx<T>);      // a slot message: 16 chunks of 16 bytes
+  constexpr int MSGS = SLOTS * (int)sizeof(cx<T>);      // a slot message: 32 slots of 8 bytes
   const uint32_t txs = (uint32_t)(CS * MSGS), txh = (uint32_t)(CS * 16);
   const int col = min(lane, kb - 1);
   cx<T> cw = zero, cws = zero;  // this lane's conj(tau) w_c of reflector j-1, and scale_{j-1} cw
@@ -733,7 +737,7 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
       // every row warp's slot partials and the pivot row copy are in place
       asm volatile("bar.sync 3, %0;" ::"n"(NT) : "memory");
       // ---- C. the row warps sum the CTA's slots and push them to their share of the
-      //      ranks: 16 chunks of 16 bytes (slot pairs) on the slot barrier
+      //      ranks: 32 chunks of 8 bytes on the slot barrier
       {
         cx<T> s = zero;
 #pragma unroll
@@ -741,11 +745,8 @@ __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
         if (rw == 0 && lane == 0) mbar_arm(&sh.mb[buf], txs);
         const uint32_t mine = smem_addr(sh.recvm + (buf * 16 + rank) * MSGS);
         const uint32_t mbl = smem_addr(&sh.mb[buf]);
-        const cx<T> sa = shfl_cx<T>(s, (2 * lane) & 31), sb = shfl_cx<T>(s, (2 * lane + 1) & 31);
-        if (lane < 16) {
-          const float4 ch = make_float4(sa.x, sa.y, sb.x, sb.y);
-          for (int r = rw; r < CS; r += RW) st_async_16(map_rank(mine + 16 * lane, r), ch, map_rank(mbl, r));
-        }
+        // every lane sends its own slot (8 bytes)
+        for (int r = rw; r < CS; r += RW) st_async_8(map_rank(mine + 8 * lane, r), make_float2(s.x, s.y), map_rank(mbl, r));
       }
       // ---- D. while the messages fly: reflector jp on the trailing columns (lanes c >= jn;
       //      cws = 0 elsewhere), in registers and on this warp's top rows; lane jn + 1
