@@ -1417,7 +1417,8 @@ template <typename T> int launch_panel(const PanelArgs<T>& pa, int cs, cudaStrea
 
 // Side streams for look-ahead, one per (device, main stream), with reusable events.
 struct SideStream {
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr;  // the look-ahead work, least priority
+  cudaStream_t hp = nullptr;  // the panel chain, greatest priority (forked from the caller's)
   std::vector<cudaEvent_t> ev;
 };
 std::mutex g_side_mu;
@@ -1429,11 +1430,13 @@ int side_stream(cudaStream_t main, int nev, SideStream** out) {
   std::lock_guard<std::mutex> lk(g_side_mu);
   SideStream& ss = g_side[std::make_pair(dev, main)];
   if (!ss.st) {
-    // lowest priority: the look-ahead work yields SMs to the panel chain on the caller's
-    // stream whenever both have blocks waiting
+    // the look-ahead work at the least priority, the panel chain at the greatest, so that
+    // freed SMs go to the chain whenever both have blocks waiting (the caller's stream
+    // itself may have the least priority)
     int lo = 0, hi = 0;
     QR_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&lo, &hi));
     QR_CUDA_TRY(cudaStreamCreateWithPriority(&ss.st, cudaStreamNonBlocking, lo));
+    QR_CUDA_TRY(cudaStreamCreateWithPriority(&ss.hp, cudaStreamNonBlocking, hi));
   }
   while ((int)ss.ev.size() < nev) {
     cudaEvent_t e;
@@ -1489,8 +1492,9 @@ template <typename T> void qr_carve(Arena& ar, int m, int n, QrScratch<T>& s) {
 
 template <typename T>
 int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ldq,
-                   QrScratch<T>& s, cudaStream_t st, unsigned* err, const QrGemm<T>* gm,
+                   QrScratch<T>& s, cudaStream_t st_in, unsigned* err, const QrGemm<T>* gm,
                    const QrGemm<T>* side) {
+  cudaStream_t st = st_in;  // the panel chain; with look-ahead, a greatest-priority fork
   if (m < n || n < 1) return QRTEBD_ERR_INVALID_ARG;
   QR_TRY(probe_max_cluster<T>());
   const int nb = qr_panel_width(m, n, sizeof(cx<T>));
@@ -1498,14 +1502,18 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
   const long long ldv = n;
   const int nbo = NBO;  // outer block: inner panels of nb columns inside it
   const cx<T> one = mk<T>(1, 0), zero = mk<T>(0, 0), mone = mk<T>(-1, 0);
+  const int nblk = (int)ceil_div(n, nbo);
+  SideStream* ss = nullptr;
+  if (side && side->fn && nblk > 2) {
+    QR_TRY(side_stream(st_in, 2 * nblk + 2, &ss));
+    QR_CUDA_TRY(cudaEventRecord(ss->ev[2 * nblk], st_in));
+    QR_CUDA_TRY(cudaStreamWaitEvent(ss->hp, ss->ev[2 * nblk], 0));
+    st = ss->hp;
+  }
   // V must be zero above each panel's diagonal block: an outer block reads the rows
   // above its later inner panels, which those panels do not write
   QR_CUDA_TRY(cudaMemsetAsync(s.V, 0, (size_t)m * n * sizeof(cx<T>), st));
   QR_CUDA_TRY(cudaMemsetAsync(s.bar, 0, 2 * sizeof(unsigned), st));
-
-  const int nblk = (int)ceil_div(n, nbo);
-  SideStream* ss = nullptr;
-  if (side && side->fn && nblk > 2) QR_TRY(side_stream(st, 2 * nblk, &ss));
   std::vector<char> rec(nblk, 0);  // which blocks recorded a side-stream update
   // latest side-stream update of a block <= k (the side stream runs them in order)
   auto latest = [&](int k) { for (int j = std::min(k, nblk - 1); j >= 0; --j) if (rec[j]) return j; return -1; };
@@ -1633,6 +1641,10 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
     QR_TRY(run_gemm<T>(g1, s, st, gm));
     GemmArgs<T> g3{mo, nq, kbo, VTb, ldv, 1, false, s.W, nq, 1, false, Qs, ldq, 1, mone, one};
     QR_TRY(run_gemm<T>(g3, s, st, gm));
+  }
+  if (st != st_in) {  // join the caller's stream
+    QR_CUDA_TRY(cudaEventRecord(ss->ev[2 * nblk + 1], st));
+    QR_CUDA_TRY(cudaStreamWaitEvent(st_in, ss->ev[2 * nblk + 1], 0));
   }
   return QRTEBD_OK;
 }
