@@ -1476,6 +1476,12 @@ template <typename T> void qr_carve(Arena& ar, int m, int n, QrScratch<T>& s) {
   s.W = ar.take<cx<T>>((size_t)nbo * n);
   s.W2 = ar.take<cx<T>>((size_t)nbo * n);
   s.W2s = ar.take<cx<T>>((size_t)nbo * n);
+  if (std::is_same<T, float>::value) {
+    s.Tall = ar.take<cx<T>>((size_t)n * n);
+    s.Cb = ar.take<cx<T>>((size_t)n * nbo);
+    s.Xb = ar.take<cx<T>>((size_t)n * nbo);
+    s.Wq = ar.take<cx<T>>((size_t)n * n);
+  }
   s.G = ar.take<cx<T>>((size_t)nbo * nbo);
   s.wy_part = ar.take<cx<T>>((size_t)std::max(num_sms(), 1) * WY_KB * WY_NC);
   s.wy_W = ar.take<cx<T>>((size_t)WY_KB * WY_NC);
@@ -1505,7 +1511,7 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
   const int nblk = (int)ceil_div(n, nbo);
   SideStream* ss = nullptr;
   if (side && side->fn && nblk > 2) {
-    QR_TRY(side_stream(st_in, 2 * nblk + 2, &ss));
+    QR_TRY(side_stream(st_in, 3 * nblk + 3, &ss));
     QR_CUDA_TRY(cudaEventRecord(ss->ev[2 * nblk], st_in));
     QR_CUDA_TRY(cudaStreamWaitEvent(ss->hp, ss->ev[2 * nblk], 0));
     st = ss->hp;
@@ -1514,6 +1520,11 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
   // above its later inner panels, which those panels do not write
   QR_CUDA_TRY(cudaMemsetAsync(s.V, 0, (size_t)m * n * sizeof(cx<T>), st));
   QR_CUDA_TRY(cudaMemsetAsync(s.bar, 0, 2 * sizeof(unsigned), st));
+  // complex64 with look-ahead: the compact-WY factor of the whole QR is assembled on the side
+  // stream block by block, and the explicit Q then takes two GEMMs,
+  // Q = [I; 0] - V (T_all V_top^dag), instead of one backward step per outer block
+  const bool qfast = std::is_same<T, float>::value && ss != nullptr && s.Tall != nullptr;
+  if (qfast) QR_CUDA_TRY(cudaMemsetAsync(s.Tall, 0, (size_t)n * n * sizeof(cx<T>), st));
   std::vector<char> rec(nblk, 0);  // which blocks recorded a side-stream update
   // latest side-stream update of a block <= k (the side stream runs them in order)
   auto latest = [&](int k) { for (int j = std::min(k, nblk - 1); j >= 0; --j) if (rec[j]) return j; return -1; };
@@ -1610,9 +1621,30 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
         rec[kblk] = 1;
       }
     }
+    if (qfast) {
+      // T_all's block column of this block, on the side stream:
+      //   T_all[b, b] = T_b,  T_all[0:k, b] = -T_all[0:k, 0:k] (V[:, 0:k]^dag V_b) T_b
+      // (V_b is zero above row ko, so the product runs over rows ko .. m-1)
+      QR_CUDA_TRY(cudaEventRecord(ss->ev[2 * nblk + 2 + kblk], st));
+      QR_CUDA_TRY(cudaStreamWaitEvent(ss->st, ss->ev[2 * nblk + 2 + kblk], 0));
+      QR_CUDA_TRY(cudaMemcpy2DAsync(s.Tall + (long long)ko * n + ko, (size_t)n * sizeof(cx<T>), Tb,
+                                    (size_t)nbo * sizeof(cx<T>), (size_t)kbo * sizeof(cx<T>), (size_t)kbo,
+                                    cudaMemcpyDeviceToDevice, ss->st));
+      if (ko > 0) {
+        GemmArgs<T> gc{ko, kbo, mo, s.V + (long long)ko * ldv, 1, ldv, true, Vb, ldv, 1, false, s.Cb, kbo, 1,
+                       one, zero};
+        QR_TRY(run_gemm<T>(gc, s, ss->st, side));
+        GemmArgs<T> gx{ko, kbo, kbo, s.Cb, kbo, 1, false, Tb, nbo, 1, false, s.Xb, kbo, 1, one, zero};
+        QR_TRY(run_gemm<T>(gx, s, ss->st, side));
+        GemmArgs<T> gt{ko, kbo, ko, s.Tall, n, 1, false, s.Xb, kbo, 1, false, s.Tall + ko, n, 1, mone, zero};
+        QR_TRY(run_gemm<T>(gt, s, ss->st, side));
+      }
+    }
   }
-  if (ss && latest(nblk - 1) >= 0)
-    QR_CUDA_TRY(cudaStreamWaitEvent(st, ss->ev[nblk + latest(nblk - 1)], 0));
+  if (ss) {  // everything on the side stream (its updates, T_all) before the explicit Q
+    QR_CUDA_TRY(cudaEventRecord(ss->ev[3 * nblk + 2], ss->st));
+    QR_CUDA_TRY(cudaStreamWaitEvent(st, ss->ev[3 * nblk + 2], 0));
+  }
 
   // explicit Q by backward accumulation over the outer blocks
   {
@@ -1621,7 +1653,14 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());
   }
-  const int npo = (int)ceil_div(n, nbo);
+  const int npo = qfast ? 0 : (int)ceil_div(n, nbo);
+  if (qfast) {
+    // Wq = T_all V_top^dag (V_top: the first n rows of V), then Q = [I; 0] - V Wq
+    GemmArgs<T> gw{n, n, n, s.Tall, n, 1, false, s.V, 1, ldv, true, s.Wq, n, 1, one, zero};
+    QR_TRY(run_gemm<T>(gw, s, st, gm));
+    GemmArgs<T> gq{m, n, n, s.V, ldv, 1, false, s.Wq, n, 1, false, Q, ldq, 1, mone, one};
+    QR_TRY(run_gemm<T>(gq, s, st, gm));
+  }
   for (int p = npo - 1; p >= 0; --p) {
     const int ko = p * nbo;
     const int kbo = std::min(nbo, n - ko);

@@ -23,6 +23,10 @@ template <typename T> struct QrScratch {
   cx<T>* W2 = nullptr;     // nb x n
   cx<T>* W2s = nullptr;    // W2 of the look-ahead (side-stream) updates
   cx<T>* G = nullptr;      // outer-block Gram matrix V^dag V
+  cx<T>* Tall = nullptr;   // n x n compact-WY factor of the whole QR (complex64 with look-ahead)
+  cx<T>* Cb = nullptr;     // n x nbo: V[:, 0:k]^dag V_b, then times T_b, for T_all's block columns
+  cx<T>* Xb = nullptr;
+  cx<T>* Wq = nullptr;     // n x n: T_all V_top^dag for the explicit Q
   cx<T>* wy_part = nullptr;  // fused narrow update: per-CTA partials of V^dag C
   cx<T>* wy_W = nullptr;     // and their sum
   unsigned* bar = nullptr;   // grid-barrier counter and generation
