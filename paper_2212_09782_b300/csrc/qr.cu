@@ -1563,10 +1563,11 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
       }
     }
     const cx<T>* Vb = s.V + (long long)ko * ldv + ko;
-    if (kbo > nb) {
-      // T of the outer block from G = V^dag V and the Householder scalars
-      GemmArgs<T> gg{kbo, kbo, mo, Vb, 1, ldv, true, Vb, ldv, 1, false, s.G, nbo, 1, one, zero};
-      QR_TRY(run_gemm<T>(gg, s, st, gm));
+    cx<T>* VTb = s.VT + (long long)ko * ldv + ko;
+    const int nc = n - ko - kbo;
+    const int n1 = ss ? std::min(nbo, nc) : nc;
+    // T of the outer block from G = V^dag V (leading dimension ldg) and the Householder scalars
+    auto launch_t = [&](const cx<T>* G, int ldg) -> int {
       const int nct = (int)ceil_div(kbo, TB_NT / 32);
       if (nb == TBB) {
         if (!g_tb_attr<T>) {
@@ -1575,7 +1576,7 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
           g_tb_attr<T> = true;
         }
         QR_CUDA_TRY(launch_pdl(k_t_block<T>, dim3((unsigned)nct), dim3(TB_NT), t_block_smem<T>(kbo), st, Tb, nbo,
-                               static_cast<const cx<T>*>(s.G), nbo, kbo));
+                               G, ldg, kbo));
       } else {
         if (!g_tc_attr<T>) {
           QR_CUDA_TRY(cudaFuncSetAttribute(k_t_cols<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1583,42 +1584,78 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
           g_tc_attr<T> = true;
         }
         QR_CUDA_TRY(launch_pdl(k_t_cols<T>, dim3((unsigned)nct), dim3(TB_NT), t_cols_smem<T>(kbo, nct - 1), st,
-                               Tb, nbo, static_cast<const cx<T>*>(s.G), nbo, static_cast<const cx<T>*>(s.tau + ko),
-                               kbo));
+                               Tb, nbo, G, ldg, static_cast<const cx<T>*>(s.tau + ko), kbo));
       }
       note_launch();
-    }
-    // VT = V T of this block, kept for the trailing updates and the explicit Q
-    cx<T>* VTb = s.VT + (long long)ko * ldv + ko;
-    {
-      GemmArgs<T> gv{mo, kbo, kbo, Vb, ldv, 1, false, Tb, nbo, 1, false, VTb, ldv, 1, one, zero};
-      QR_TRY(run_gemm<T>(gv, s, st, gm));
-    }
+      return QRTEBD_OK;
+    };
     // outer trailing update: C <- (I - V T V^dag)^dag C. With look-ahead the next outer
     // block's columns are updated here and the rest on the side stream, overlapping the
     // next block's panels.
-    const int nc = n - ko - kbo;
-    if (nc > 0) {
-      auto update = [&](int c0, int cw, cudaStream_t stream, cx<T>* W2, const QrGemm<T>* g) -> int {
-        cx<T>* C = A + (long long)ko * lda + ko + kbo + c0;
-        // W2 = T^dag V^dag C = (V T)^dag C, then C -= V W2
-        GemmArgs<T> g1{kbo, cw, mo, VTb, 1, ldv, true, C, lda, 1, false, W2, cw, 1, one, zero};
-        QR_TRY(run_gemm<T>(g1, s, stream, g));
-        GemmArgs<T> g3{mo, cw, kbo, Vb, ldv, 1, false, W2, cw, 1, false, C, lda, 1, mone, one};
-        QR_TRY(run_gemm<T>(g3, s, stream, g));
-        return QRTEBD_OK;
-      };
-      const int n1 = ss ? std::min(nbo, nc) : nc;
-      // the next block's columns also carry block k-1's side-stream update: order after it
-      if (ss && latest(kblk - 1) >= 0)
-        QR_CUDA_TRY(cudaStreamWaitEvent(st, ss->ev[nblk + latest(kblk - 1)], 0));
-      QR_TRY(update(0, n1, st, s.W2, gm));
-      if (ss && nc > n1) {
+    auto update = [&](int c0, int cw, cudaStream_t stream, cx<T>* W2, const QrGemm<T>* g) -> int {
+      cx<T>* C = A + (long long)ko * lda + ko + kbo + c0;
+      // W2 = T^dag V^dag C = (V T)^dag C, then C -= V W2
+      GemmArgs<T> g1{kbo, cw, mo, VTb, 1, ldv, true, C, lda, 1, false, W2, cw, 1, one, zero};
+      QR_TRY(run_gemm<T>(g1, s, stream, g));
+      GemmArgs<T> g3{mo, cw, kbo, Vb, ldv, 1, false, W2, cw, 1, false, C, lda, 1, mone, one};
+      QR_TRY(run_gemm<T>(g3, s, stream, g));
+      return QRTEBD_OK;
+    };
+    // VT = V T of this block, for the trailing updates that take it
+    auto form_vt = [&](cudaStream_t stream, const QrGemm<T>* g) -> int {
+      GemmArgs<T> gv{mo, kbo, kbo, Vb, ldv, 1, false, Tb, nbo, 1, false, VTb, ldv, 1, one, zero};
+      return run_gemm<T>(gv, s, stream, g);
+    };
+    // complex64 with look-ahead and a full next block: its 128 columns C1 are copied beside V
+    // (into the next block's V storage, zero until its panels), one GEMM forms
+    // [G | P] = V^dag [V | C1], T comes from G, and C1 -= V (T^dag P); V T, needed only by
+    // the side stream's update (the explicit Q takes T_all), is formed there
+    const bool gpf = qfast && kbo > nb && nc >= nbo;
+    if (gpf) {
+      cx<T>* C1 = A + (long long)ko * lda + ko + kbo;
+      cx<T>* C1c = s.V + (long long)ko * ldv + ko + kbo;
+      // C1 also carries block k-1's side-stream update: order after it
+      if (latest(kblk - 1) >= 0) QR_CUDA_TRY(cudaStreamWaitEvent(st, ss->ev[nblk + latest(kblk - 1)], 0));
+      QR_CUDA_TRY(cudaMemcpy2DAsync(C1c, (size_t)ldv * sizeof(cx<T>), C1, (size_t)lda * sizeof(cx<T>),
+                                    (size_t)nbo * sizeof(cx<T>), (size_t)mo, cudaMemcpyDeviceToDevice, st));
+      GemmArgs<T> ggp{kbo, kbo + nbo, mo, Vb, 1, ldv, true, Vb, ldv, 1, false, s.Wq, kbo + nbo, 1, one, zero};
+      QR_TRY(run_gemm<T>(ggp, s, st, gm));
+      // the next block's V is zero above its panels' diagonal blocks again
+      QR_CUDA_TRY(cudaMemset2DAsync(C1c, (size_t)ldv * sizeof(cx<T>), 0, (size_t)nbo * sizeof(cx<T>),
+                                    (size_t)std::min(mo, kbo + nbo), st));
+      QR_TRY(launch_t(s.Wq, kbo + nbo));
+      GemmArgs<T> gw{kbo, nbo, kbo, Tb, 1, nbo, true, s.Wq + kbo, kbo + nbo, 1, false, s.W2, nbo, 1, one, zero};
+      QR_TRY(run_gemm<T>(gw, s, st, gm));
+      if (nc > nbo) {
         QR_CUDA_TRY(cudaEventRecord(ss->ev[kblk], st));  // V, T of this block are ready
         QR_CUDA_TRY(cudaStreamWaitEvent(ss->st, ss->ev[kblk], 0));
-        QR_TRY(update(n1, nc - n1, ss->st, s.W2s, side));
+        QR_TRY(form_vt(ss->st, side));
+        QR_TRY(update(nbo, nc - nbo, ss->st, s.W2s, side));
         QR_CUDA_TRY(cudaEventRecord(ss->ev[nblk + kblk], ss->st));
         rec[kblk] = 1;
+      }
+      GemmArgs<T> g3{mo, nbo, kbo, Vb, ldv, 1, false, s.W2, nbo, 1, false, C1, lda, 1, mone, one};
+      QR_TRY(run_gemm<T>(g3, s, st, gm));
+    } else {
+      if (kbo > nb) {
+        GemmArgs<T> gg{kbo, kbo, mo, Vb, 1, ldv, true, Vb, ldv, 1, false, s.G, nbo, 1, one, zero};
+        QR_TRY(run_gemm<T>(gg, s, st, gm));
+        QR_TRY(launch_t(s.G, nbo));
+      }
+      // V T for this block's updates, and for the backward explicit Q when T_all is not formed
+      if (!qfast || nc > 0) QR_TRY(form_vt(st, gm));
+      if (nc > 0) {
+        // the next block's columns also carry block k-1's side-stream update: order after it
+        if (ss && latest(kblk - 1) >= 0)
+          QR_CUDA_TRY(cudaStreamWaitEvent(st, ss->ev[nblk + latest(kblk - 1)], 0));
+        QR_TRY(update(0, n1, st, s.W2, gm));
+        if (ss && nc > n1) {
+          QR_CUDA_TRY(cudaEventRecord(ss->ev[kblk], st));  // V, T of this block are ready
+          QR_CUDA_TRY(cudaStreamWaitEvent(ss->st, ss->ev[kblk], 0));
+          QR_TRY(update(n1, nc - n1, ss->st, s.W2s, side));
+          QR_CUDA_TRY(cudaEventRecord(ss->ev[nblk + kblk], ss->st));
+          rec[kblk] = 1;
+        }
       }
     }
     if (qfast) {
