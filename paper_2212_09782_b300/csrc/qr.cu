@@ -897,6 +897,15 @@ __global__ void k_eye(cx<T>* Q, long long ldq, int m, int n) {
   Q[i * ldq + j] = mk<T>(i == j ? T(1) : T(0), 0);
 }
 
+// Q[i][i] += 1 for i < n (the identity of Q = [I; 0] - V W added after the GEMM)
+template <typename T>
+__global__ void k_add_eye(cx<T>* Q, long long ldq, int n) {
+  pdl_launch_dependents();
+  pdl_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) Q[i * ldq + i].x += T(1);
+}
+
 template <typename T> __device__ __forceinline__ void cp_async_cx(cx<T>* dst_smem, const cx<T>* src) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
                "l"(src), "n"((int)sizeof(cx<T>)) : "memory");
@@ -1624,8 +1633,9 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
       QR_CUDA_TRY(cudaMemset2DAsync(C1c, (size_t)ldv * sizeof(cx<T>), 0, (size_t)nbo * sizeof(cx<T>),
                                     (size_t)std::min(mo, kbo + nbo), st));
       QR_TRY(launch_t(s.Wq, kbo + nbo));
+      // a 128^3 product: the CUDA-core GEMM, which needs no operand preparation
       GemmArgs<T> gw{kbo, nbo, kbo, Tb, 1, nbo, true, s.Wq + kbo, kbo + nbo, 1, false, s.W2, nbo, 1, one, zero};
-      QR_TRY(run_gemm<T>(gw, s, st, gm));
+      QR_TRY(gemm_simt<T>(gw, st, s.gemm_scratch, s.gemm_scratch_elems));
       if (nc > nbo) {
         QR_CUDA_TRY(cudaEventRecord(ss->ev[kblk], st));  // V, T of this block are ready
         QR_CUDA_TRY(cudaStreamWaitEvent(ss->st, ss->ev[kblk], 0));
@@ -1683,8 +1693,9 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
     QR_CUDA_TRY(cudaStreamWaitEvent(st, ss->ev[3 * nblk + 2], 0));
   }
 
-  // explicit Q by backward accumulation over the outer blocks
-  {
+  // explicit Q: with T_all, Q = -V W then its identity added; else backward accumulation
+  // over the outer blocks from Q = [I; 0]
+  if (!qfast) {
     long long tot = (long long)m * n;
     QR_CUDA_TRY(launch_pdl(k_eye<T>, dim3((unsigned)ceil_div(tot, 256)), dim3(256), 0, st, Q, ldq, m, n));
     note_launch();
@@ -1695,8 +1706,10 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
     // Wq = T_all V_top^dag (V_top: the first n rows of V), then Q = [I; 0] - V Wq
     GemmArgs<T> gw{n, n, n, s.Tall, n, 1, false, s.V, 1, ldv, true, s.Wq, n, 1, one, zero};
     QR_TRY(run_gemm<T>(gw, s, st, gm));
-    GemmArgs<T> gq{m, n, n, s.V, ldv, 1, false, s.Wq, n, 1, false, Q, ldq, 1, mone, one};
+    GemmArgs<T> gq{m, n, n, s.V, ldv, 1, false, s.Wq, n, 1, false, Q, ldq, 1, mone, zero};
     QR_TRY(run_gemm<T>(gq, s, st, gm));
+    QR_CUDA_TRY(launch_pdl(k_add_eye<T>, dim3((unsigned)ceil_div(n, 256)), dim3(256), 0, st, Q, ldq, n));
+    note_launch();
   }
   for (int p = npo - 1; p >= 0; --p) {
     const int ko = p * nbo;
