@@ -319,8 +319,11 @@ void qrtebd_autotune_clear(void);
  * diagonal, LAPACK geqrf sign convention) and zeros below; Q (m x n, ldq) holds the
  * explicit isometry. Blocked Householder: thread-block-cluster panels with FP64
  * reflector norms, compact-WY trailing updates. workspace: device, at least
- * qrtebd_qr_workspace_size bytes. Enqueued on `stream`. INVALID_ARG if m < n, n < 1
- * or the panel does not fit shared memory. */
+ * qrtebd_qr_workspace_size bytes. Enqueued on `stream`; with more than two 128-column
+ * blocks part of the work runs on two library-owned streams (a greatest-priority one for
+ * the panel chain, a least-priority one for the look-ahead) forked from `stream` by events
+ * and joined back into it, which stream capture records as graph edges. INVALID_ARG if
+ * m < n, n < 1 or the panel does not fit shared memory. */
 int qrtebd_householder_qr(int precision, int m, int n, void* A, long long lda, void* Q,
                           long long ldq, void* workspace, size_t workspace_bytes, void* stream);
 size_t qrtebd_qr_workspace_size(int precision, int m, int n);
