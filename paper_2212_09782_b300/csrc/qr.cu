@@ -568,7 +568,10 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
 // by that lane during the trailing update. The coefficients cws = scale conj(tau) w_c of
 // the lanes fold the reflector's scale into the update of the raw column. Warp 0 holds no
 // rows: it waits for the messages and forms the reflector while warps 1..11 apply the
-// trailing update, so that update leaves the critical path.
+// trailing update, so that update leaves the critical path. The norm and h travel ahead
+// of the slot sums: warp 0 reduces the row warps' lane partials during their pass B and
+// pushes the CTA's 16-byte header on a barrier of its own, so the reflector scalars are
+// formed while the slot messages are still in flight.
 constexpr int RF_NT = 384;  // threads per CTA: the reflector warp and 11 row warps
 constexpr int RF_RPW = 30;  // slab rows per row warp held in registers (11 x 30 = 330 per CTA)
 
@@ -593,7 +596,6 @@ __device__ __forceinline__ cx<float> sub_rn(cx<float> p, cx<float> c) {
 template <int RPW>
 __global__ void __launch_bounds__(RF_NT, 1) k_qr_panel_rf(PanelArgs<float> a) {
   using T = float;
-  using L = PanelSmem<T>;
   constexpr int NT = RF_NT, NW = NT / 32, RW = NW - 1;  // warps 1 .. RW hold the rows
   static_assert(RW <= 16 && RPW <= 32 && RPW % 2 == 0,
                 "one tree level per halving; one slab row per lane; slab rows in 16-byte pairs");
