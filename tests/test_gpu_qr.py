@@ -23,8 +23,10 @@ def _run(prec, A):
 
 @pytest.mark.parametrize("prec", list(TOL))
 @pytest.mark.parametrize("m,n", [(1, 1), (5, 3), (32, 32), (99, 33), (99, 32), (100, 65),
-                                 (300, 130), (640, 256), (1200, 257)])
+                                 (300, 130), (640, 256), (1200, 257), (400, 385), (1000, 640)])
 def test_qr_matches_lapack(prec, m, n):
+    # more than two 128-column blocks take the look-ahead paths (whole-factor T, the next
+    # block's columns beside V); 400 x 385 ends on a one-column block with 16 rows below
     A = W.complex_gaussian(W.rng(m * 7 + n), (m, n))
     if prec != "c128":
         A = A.astype(np.complex64).astype(np.complex128)
