@@ -102,6 +102,52 @@ def family_roofline(L, fam, ms, n, flops, nbytes, prec, peaks, src):
     return out
 
 
+def measure_matmul_peaks(torch):
+    """TF32 and FP64 dense peaks measured on this GPU the way MEASURED_PEAKS.json measures
+    BF16: torch.matmul, best of several CUDA-event-timed runs (TF32 at 8192^3 with TF32
+    tensor cores allowed, FP64 at 4096^3)."""
+    out = {}
+    prev = torch.backends.cuda.matmul.allow_tf32
+    try:
+        for key, dt, n, reps, tf32 in (("tf32_tflops", torch.float32, 8192, 10, True),
+                                        ("fp64_tflops", torch.float64, 4096, 4, False)):
+            torch.backends.cuda.matmul.allow_tf32 = tf32
+            a = torch.randn(n, n, device="cuda", dtype=dt)
+            b = torch.randn(n, n, device="cuda", dtype=dt)
+            c = torch.empty(n, n, device="cuda", dtype=dt)
+            torch.matmul(a, b, out=c)
+            torch.cuda.synchronize()
+            best = float("inf")
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                torch.cuda.synchronize()
+                best = min(best, e0.elapsed_time(e1))
+            out[key] = 2.0 * n ** 3 / (best / 1e3) / 1e12
+            out[key + "_how"] = f"torch.matmul {n}^3, best of {reps}, CUDA events"
+            del a, b, c
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+    torch.cuda.empty_cache()
+    return out
+
+
+def update_flops(chi_l, d, chi_m, chi_r, eta, theta_given=True, xi_dense=False):
+    """Algorithmic real flops of one plain bond update (8 per complex MAC): the gate, X = theta~ Y0^dag,
+    the QR of X (factor + explicit Q), Y = Q^dag theta~, the QR of Y^dag, B~^m = theta~' B~^n^dag,
+    plus theta' = B^m B^n and a dense Xi when they are formed."""
+    m1, m2 = d * chi_l, d * chi_r
+    qr = lambda m, n: 2 * (m * n * n - n ** 3 / 3.0)
+    cmac = d ** 4 * chi_l * chi_r + 3 * d * d * chi_l * chi_r * eta + qr(m1, eta) + qr(m2, eta)
+    if not theta_given:
+        cmac += d * d * chi_l * chi_m * chi_r
+    if xi_dense:
+        cmac += d * d * chi_l * chi_l * chi_r
+    return 8.0 * cmac
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -249,6 +295,8 @@ def run_ours(args):
     bn = torch.from_numpy(wl["Bn"]).to(dtype=cdt, device="cuda")
     gate = torch.from_numpy(wl["U"]).to("cuda")
     tr = L.trunc_default(L.PLAIN, chi)
+    # the dense tensor peaks the metric's roofline is taken against (before any workspace)
+    mpk = None if args.no_peaks else measure_matmul_peaks(torch)
     up = L.BondUpdater(prec, chi, d, chi, chi, tr, xi_kind=0, theta_given=True)
     stream = torch.cuda.current_stream()
     tune = None
@@ -386,12 +434,35 @@ def run_ours(args):
     dom = max((f for f in prof if prof[f][1] > 0), key=lambda f: prof[f][0])
     roof = roofs.get(PROF_NAMES[dom])
 
+    # ---- the metric's "% TC roofline": the whole update's algorithmic flops over its time,
+    #      against the TF32 (complex128: FP64) peak measured on this GPU just now
+    tc_roof = None
+    if mpk:
+        fl = update_flops(chi, d, chi, chi, chi)
+        key = "fp64_tflops" if prec == L.C128 else "tf32_tflops"
+        ach = fl / (t_max / args.steps / 1e3) / 1e12
+        tc_roof = {"algorithmic_flops_per_update": fl, "achieved_tflops": ach, "peak_tflops": mpk[key],
+                   "frac": ach / mpk[key], "peak_source": f"measured in this run: {mpk[key + '_how']}",
+                   "note": "the whole update (GEMMs, QRs, gate) against the dense tensor peak of its "
+                           "arithmetic; 3xTF32 issues three TF32 products per complex GEMM MAC"}
+        if prec != L.C128:
+            tc_roof["frac_vs_derived_tf32"] = ach / (peaks.get("bf16_tflops", PEAKS_FALLBACK["bf16_tflops"])
+                                                     * TF32_PER_BF16)
+
     cpu = None
     err = None
     if not args.no_cpu_baseline and ws == 1:
         t, orc = cpu_oracle_update(wl, chi, want_result=True)
         cpu = {"value": 1.0 / t, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"1 full bond update chi={chi} d={d} (complex128 NumPy/LAPACK)"}
+        try:
+            from threadpoolctl import threadpool_limits
+            with threadpool_limits(limits=1):
+                t1 = cpu_oracle_update(wl, chi)
+            cpu["one_thread"] = {"value": 1.0 / t1, "cores": 1,
+                                 "sample": "the same update with BLAS/LAPACK limited to one thread"}
+        except ImportError:
+            pass
         # the timed update's result against the FP64 oracle on the same inputs (gauge
         # invariant: the Schmidt values of Xi~ and eps)
         _bm, xi_g, _bn, st_g = up.outputs()
@@ -400,6 +471,14 @@ def run_ours(args):
         err = {"schmidt_rel": float(np.linalg.norm(s_g - s_o) / np.linalg.norm(s_o)),
                "eps_rel": float(abs(float(st_g[0]) - orc["eps"]) / orc["eps"]),
                "reference": "oracle (complex128), same inputs"}
+
+    # ---- the paper's comparison (Fig. 5) on this GPU, outside every timed region above
+    arms = None
+    if not args.no_svd_arm and ws == 1:
+        up = ups = None  # release the timed updaters' workspaces
+        torch.cuda.empty_cache()
+        arms = comparison_arms(torch, L, wl, chi, d, prec, cdt, 1, 3, stream)
+        arms["qr_precision"] = args.precision
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -413,7 +492,8 @@ def run_ours(args):
                                f"(theta given, Xi=1)", "global_batch": ws,
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                    "l2": "inputs larger than L2 (theta 210 MB)", "precision": args.precision},
-        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+        "roofline": roof, "tc_roofline": tc_roof, "measured_peaks": mpk, "comparison_arms": arms,
+        "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
         "kernel_breakdown": breakdown, "dominant_family": PROF_NAMES[dom],
         "roofline_by_family": roofs, "profiled_ms_per_step": prof_step_ms, "clocks": clk,
         "autotune": tune, "error_vs_oracle": err,
@@ -519,15 +599,56 @@ def run_serve(args):
     return 0
 
 
+def comparison_arms(torch, L, wl, chi, d, prec, cdt, warmup, steps, stream):
+    """QR update of this library against the SVD-based and the eigendecomposition-based
+    updates run through torch's cuSOLVER calls, on the same theta (chi, d, d, chi): the
+    paper's Fig. 5 comparison restated on this GPU. Measurement only: the library never
+    calls a solver. SVD arm: theta = U S V^dag (reduced), keep chi, B~m = theta V_chi.
+    EIG arm: theta^dag theta = V S^2 V^dag (Hermitian eigensolver), keep the chi largest,
+    B~m = theta V_chi. Both arms skip the gate (theta supplied); the QR arm runs every
+    step of the update, gate included."""
+    def timed(fn, n_warm, n_steps):
+        for _ in range(n_warm):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n_steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / n_steps
+
+    th = torch.from_numpy(wl["theta"]).to(dtype=cdt, device="cuda")
+    bn = torch.from_numpy(wl["Bn"]).to(dtype=cdt, device="cuda")
+    gate = torch.from_numpy(wl["U"]).to("cuda")
+    tr = L.trunc_default(L.PLAIN, chi)
+    up = L.BondUpdater(prec, chi, d, chi, chi, tr, xi_kind=0, theta_given=True)
+    qr_ms = timed(lambda: up.run(gate, bn, theta=th), warmup, steps)
+    L.stream_check()
+    M = th.reshape(chi * d, d * chi)
+
+    def svd_arm():
+        _U, _S, Vh = torch.linalg.svd(M, full_matrices=False)
+        return M @ Vh[:chi].conj().T
+
+    def eig_arm():
+        _w, V = torch.linalg.eigh(M.conj().T @ M)
+        return M @ V[:, -chi:]
+
+    svd_ms = timed(svd_arm, 1, max(1, min(steps, 2)))
+    eig_ms = timed(eig_arm, 1, max(1, min(steps, 5)))
+    out = {"qr_ms": qr_ms, "svd_ms": svd_ms, "eig_ms": eig_ms, "qr_speedup_over_svd": svd_ms / qr_ms,
+           "qr_speedup_over_eig": eig_ms / qr_ms,
+           "svd_eig_solver": "torch.linalg.svd / torch.linalg.eigh (cuSOLVER), measurement only"}
+    del th, bn, up, M
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_svd_arm(args):
-    """Comparison arms of the single-gate benchmark (the paper's Fig. 5 comparison,
-    restated on this GPU): the QR update of this library against the SVD-based update
-    and the eigendecomposition-based update run through torch's cuSOLVER calls, on the
-    same theta (chi, d, d, chi). Measurement only: the library never calls a solver.
-    SVD arm: theta = U S V^dag (reduced), keep chi, B~m = theta V_chi. EIG arm:
-    theta^dag theta = V S^2 V^dag (Hermitian eigensolver), keep the chi largest,
-    B~m = theta V_chi. Both arms skip the gate (supplied theta), as the QR arm does not:
-    the QR arm includes the gate and every step of the update."""
+    """Comparison arms of the single-gate benchmark as their own JSON line (see
+    comparison_arms); --svd-c128 adds the complex128 arms."""
     import torch
     from paper_2212_09782_b300 import lib as L
     from paper_2212_09782_b300 import workloads as W
@@ -537,46 +658,12 @@ def run_svd_arm(args):
     out = {"metric": f"single bond update time, QR (this library) vs SVD / EIG (cuSOLVER via torch), chi={chi} d={d}",
            "unit": "ms per update", "higher_is_better": False, "data": "synthetic",
            "steps": args.steps, "warmup": args.warmup, "arms": {}}
-
-    def timed(fn):
-        for _ in range(args.warmup):
-            fn()
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(args.steps):
-            fn()
-        b.record(stream)
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / args.steps
-
     arms = [("c64_3xtf32", torch.complex64)] + ([("c128", torch.complex128)] if args.svd_c128 else [])
     for prec, cdt in arms:
-        th = torch.from_numpy(wl["theta"]).to(dtype=cdt, device="cuda")
-        bn = torch.from_numpy(wl["Bn"]).to(dtype=cdt, device="cuda")
-        gate = torch.from_numpy(wl["U"]).to("cuda")
-        tr = L.trunc_default(L.PLAIN, chi)
-        up = L.BondUpdater(L.PRECISIONS[prec], chi, d, chi, chi, tr, xi_kind=0, theta_given=True)
-        qr_ms = timed(lambda: up.run(gate, bn, theta=th))
-        L.stream_check()
-        M = th.reshape(chi * d, d * chi)
-
-        def svd_arm():
-            U, S, Vh = torch.linalg.svd(M, full_matrices=False)
-            return M @ Vh[:chi].conj().T
-
-        def eig_arm():
-            w, V = torch.linalg.eigh(M.conj().T @ M)
-            return M @ V[:, -chi:]
-
-        svd_ms = timed(svd_arm)
-        eig_ms = timed(eig_arm)
         key = "c64" if prec != "c128" else "c128"
-        out["arms"][key] = {"qr_ms": qr_ms, "svd_ms": svd_ms, "eig_ms": eig_ms,
-                            "qr_speedup_over_svd": svd_ms / qr_ms, "qr_speedup_over_eig": eig_ms / qr_ms,
-                            "qr_precision": prec}
-        del th, bn, up, M
-        torch.cuda.empty_cache()
+        out["arms"][key] = comparison_arms(torch, L, wl, chi, d, L.PRECISIONS[prec], cdt, args.warmup,
+                                           args.steps, stream)
+        out["arms"][key]["qr_precision"] = prec
     print(json.dumps(out), flush=True)
     return 0
 
@@ -732,6 +819,10 @@ def main():
     ap.add_argument("--d", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-svd-arm", action="store_true",
+                    help="bond workload: skip the SVD / EIG comparison arms after the timed runs")
+    ap.add_argument("--no-peaks", action="store_true",
+                    help="skip the TF32 / FP64 matmul peak measurement (and the tc_roofline it feeds)")
     ap.add_argument("--workload", choices=["bond", "chain", "serve", "svd", "c1", "c3", "cbe_eig"],
                     default="bond")
     ap.add_argument("--eig-n", type=int, default=1126, help="cbe_eig workload: the order n")

@@ -147,6 +147,19 @@ int qrtebd_bond_update(const qrtebd_bond_io* io, const qrtebd_trunc* tr, void* s
  * set by kernels since the last check. */
 int qrtebd_stream_check(void* stream);
 
+/* Failure detection (the paper has no counterpart). Every wait of a kernel on another
+ * CTA is bounded; on expiry the kernel sets the device error word and returns, and the
+ * next qrtebd_stream_check reports QRTEBD_ERR_TIMEOUT, leaving the context usable.
+ * qrtebd_set_spin_limit: poll limit of the grid-wide barriers (the fused QR updates, the
+ * CBE Jacobi sweeps) on the current device; polls <= 0 restores the default 2^24. The
+ * mbarrier waits of the tensor-core and QR-panel pipelines keep the fixed 2^24 limit, as
+ * their expiry path must drain copies still in flight. Synchronous host call.
+ * qrtebd_selftest_barrier_timeout: enqueues on `stream` one CTA that waits at a grid
+ * barrier sized for two CTAs, which nothing releases, so its bounded wait runs out; the
+ * next qrtebd_stream_check on that stream then returns QRTEBD_ERR_TIMEOUT. */
+int qrtebd_set_spin_limit(long long polls);
+int qrtebd_selftest_barrier_timeout(void* stream);
+
 /* ------------------------------------------------------------------ MPS state */
 /* A matrix-product state in the right-isometric form of Sec. II (Eq. 1, Fig. 1):
  * site tensors B[m] (chi_m, d, chi_{m+1}) and bond matrices Xi[m] on the bond left
@@ -182,7 +195,10 @@ int qrtebd_mps_destroy(qrtebd_mps* mps);
  * the bonds of `parity` are read and copied. tr: truncation for every bond.
  * eps_out: optional host array of nbonds doubles receiving each updated bond's eps
  * (others untouched); passing it synchronises the stream. Bonds of one layer are
- * independent (Fig. 2a) and are updated in sequence on the handle's stream. */
+ * independent (Fig. 2a): a layer of one bond is updated on the handle's stream; a layer
+ * of two or more bonds runs on the worker-stream executor of
+ * qrtebd_apply_gate_layer_batched (ordered after earlier work on the handle's stream and
+ * before later work on it). */
 int qrtebd_apply_gate_layer(qrtebd_mps* mps, int parity, const double* gates_host,
                             const qrtebd_trunc* tr, double* eps_out);
 /* <O> at `site` (nsites = 1: op is d x d, Fig. 1c: tr[(Xi B)^dag O (Xi B)]) or on
@@ -199,6 +215,11 @@ int qrtebd_truncation_error(qrtebd_mps* mps, int bond, double* out);
  * to unit 2-norm) into host S (capacity entries); *n receives the bond dimension.
  * Synchronises. INVALID_ARG if capacity is too small. */
 int qrtebd_schmidt(qrtebd_mps* mps, int bond, double* S, int capacity, int* n);
+/* Von Neumann entanglement entropy of bond `bond` (Fig. 4 plots it on the central bond):
+ * S_vN = -sum_k p_k ln p_k with p_k = S_k^2 from the normalised Schmidt values of
+ * qrtebd_schmidt, natural log, FP64; terms with p_k <= 1e-300 are skipped. *out: host
+ * double. Synchronises. INVALID_ARG for a bond outside the state or a NULL pointer. */
+int qrtebd_entropy(qrtebd_mps* mps, int bond, double* out);
 /* Current bond dimensions (finite: L+1 values, uniform: L values) into dims. */
 int qrtebd_bond_dims(qrtebd_mps* mps, int* dims, int capacity, int* n);
 /* Wait for all work on the handle's stream; reports device-side errors. */
@@ -258,7 +279,11 @@ size_t qrtebd_zgemm_workspace_size(int m, int n, int k);
  * file-scope device array of QRTEBD_NOALLOC_SCRATCH_BYTES, held on every GPU that
  * loads the library until the process exits; the caller still passes A, B and C.
  * precision: QRTEBD_C64_3XTF32 or QRTEBD_C64_TF32 only; m, n, k each at most
- * QRTEBD_NOALLOC_MAX_DIM, otherwise QRTEBD_ERR_INVALID_ARG with a message. The first
+ * QRTEBD_NOALLOC_MAX_DIM, otherwise QRTEBD_ERR_INVALID_ARG with a message. Empty sizes
+ * behave as in qrtebd_zgemm: m or n = 0 returns OK with nothing written, k = 0 scales C
+ * by beta. Its kernels' waits are bounded: an expired wait returns nothing here, it sets
+ * the device error word, which the next qrtebd_stream_check on `stream` reports as
+ * QRTEBD_ERR_TIMEOUT. The first
  * call on a device looks up the array's device address (cudaGetSymbolAddress), so
  * make one call on each device before any stream capture. All calls share the array:
  * calls that overlap on the GPU (several streams or host threads) race on it and must

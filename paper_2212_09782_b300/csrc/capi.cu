@@ -36,6 +36,27 @@ unsigned* device_error_word() {
   return g_err_ptr[dev];
 }
 
+std::vector<const void*>& barrier_spin_symbols() {
+  static std::vector<const void*> v;
+  return v;
+}
+std::mutex& barrier_spin_mu() {
+  static std::mutex m;
+  return m;
+}
+int register_barrier_spin(const void* host_symbol) {
+  std::lock_guard<std::mutex> lk(barrier_spin_mu());
+  barrier_spin_symbols().push_back(host_symbol);
+  return (int)barrier_spin_symbols().size();
+}
+
+namespace {
+__device__ unsigned g_selftest_bar[2];
+// One CTA waits at a grid barrier sized for two: the counter that would release it is never
+// advanced, so the bounded wait runs out, sets DEVERR_TIMEOUT and the kernel returns.
+__global__ void k_selftest_barrier(unsigned* bar, unsigned* err) { (void)grid_barrier(bar, 2u, err); }
+}  // namespace
+
 // Read-and-clear the device error word (synchronises the stream first).
 int check_device_error(cudaStream_t st) {
   QR_CUDA_TRY(cudaStreamSynchronize(st));
@@ -296,6 +317,26 @@ void qrtebd_autotune_clear(void) { tc_tune_clear(); }
 
 int qrtebd_stream_check(void* stream) { return check_device_error(static_cast<cudaStream_t>(stream)); }
 
+int qrtebd_set_spin_limit(long long polls) {
+  const long long v = polls <= 0 ? kSpinLimit : polls;
+  std::lock_guard<std::mutex> lk(barrier_spin_mu());
+  for (const void* sym : barrier_spin_symbols()) QR_CUDA_TRY(cudaMemcpyToSymbol(sym, &v, sizeof v));
+  return QRTEBD_OK;
+}
+
+int qrtebd_selftest_barrier_timeout(void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  unsigned* err = device_error_word();
+  if (!err) { set_last_message("device error word unavailable"); return QRTEBD_ERR_CUDA; }
+  void* bar = nullptr;
+  QR_CUDA_TRY(cudaGetSymbolAddress(&bar, g_selftest_bar));
+  QR_CUDA_TRY(cudaMemsetAsync(bar, 0, sizeof(g_selftest_bar), st));
+  k_selftest_barrier<<<1, 32, 0, st>>>(static_cast<unsigned*>(bar), err);
+  note_launch();
+  QR_CUDA_TRY(cudaGetLastError());
+  return QRTEBD_OK;
+}
+
 int qrtebd_zgemm(int precision, int m, int n, int k, const void* A, long long sam, long long sak,
                  int conj_a, const void* B, long long sbk, long long sbn, int conj_b, void* C,
                  long long scm, long long scn, const double* alpha, const double* beta,
@@ -316,6 +357,8 @@ int qrtebd_zgemm(int precision, int m, int n, int k, const void* A, long long sa
                     make_float2((float)beta[0], (float)beta[1])};
   if (precision == QRTEBD_C64_FP32) return gemm_simt<float>(g, st, nullptr, 0);
   if (precision != QRTEBD_C64_3XTF32 && precision != QRTEBD_C64_TF32) return QRTEBD_ERR_INVALID_ARG;
+  if (m == 0 || n == 0) return QRTEBD_OK;
+  if (k == 0) return gemm_simt<float>(g, st, nullptr, 0);  // C = beta C
   Arena ar;
   ar.base = static_cast<char*>(workspace);
   ar.cap = workspace_bytes;

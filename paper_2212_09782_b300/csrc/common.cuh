@@ -60,6 +60,18 @@ enum : unsigned { DEVERR_TIMEOUT = 1u, DEVERR_NUMERIC = 2u, DEVERR_BOUNDS = 4u }
 // Iteration limit for every spin on an mbarrier or a flag (~1 s on B300).
 constexpr long long kSpinLimit = 1ll << 24;
 
+// Poll limit of the grid-wide barriers (waits on a counter other CTAs advance, with no
+// asynchronous copy in flight): each translation unit keeps a device copy, which
+// qrtebd_set_spin_limit rewrites on the current device. The mbarrier waits of the TMA and
+// cluster pipelines keep the compile-time kSpinLimit, since their expiry path drains
+// copies still in flight and a tiny limit would cut that short.
+static __device__ long long g_barrier_spin = kSpinLimit;
+// Host side: records one translation unit's copy (its host shadow symbol); defined in capi.cu.
+int register_barrier_spin(const void* host_symbol);
+namespace {
+[[maybe_unused]] const int g_barrier_spin_registered = register_barrier_spin(&g_barrier_spin);
+}
+
 #define QR_CUDA_TRY(expr)                                                           \
   do {                                                                              \
     cudaError_t e_ = (expr);                                                        \
@@ -147,8 +159,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, un
       atomicAdd(bar + 1, 1u);
     } else {
       long long i = 0;
+      const long long lim = g_barrier_spin;
       while (*gen == g) {
-        if (++i > kSpinLimit) { ok = 0; atomicOr(err, DEVERR_TIMEOUT); break; }
+        if (++i > lim) { ok = 0; atomicOr(err, DEVERR_TIMEOUT); break; }
         __nanosleep(64);
       }
     }

@@ -433,6 +433,21 @@ int qrtebd_schmidt(qrtebd_mps* s, int bond, double* S, int capacity, int* n) {
                                      : schmidt_t<float>(s, bond, S, capacity, n);
 }
 
+int qrtebd_entropy(qrtebd_mps* s, int bond, double* out) {
+  if (!s || !out || bond < 0 || bond >= (s->infinite ? s->L : s->L + 1)) return QRTEBD_ERR_INVALID_ARG;
+  std::vector<double> S((size_t)std::max(s->chi[bond], 1));
+  int n = 0;
+  QR_TRY(qrtebd_schmidt(s, bond, S.data(), (int)S.size(), &n));
+  // S is normalised to unit 2-norm, so p_k = S_k^2 sums to one; FP64, natural log
+  double e = 0.0;
+  for (int k = 0; k < n; ++k) {
+    const double p = S[k] * S[k];
+    if (p > 1e-300) e -= p * std::log(p);
+  }
+  *out = e;
+  return QRTEBD_OK;
+}
+
 int qrtebd_bond_dims(qrtebd_mps* s, int* dims, int capacity, int* n) {
   if (!s || !dims || !n) return QRTEBD_ERR_INVALID_ARG;
   *n = s->nbonds_store;
@@ -480,17 +495,44 @@ int qrtebd_mps_load(const char* path, void* stream, qrtebd_mps** out) {
   *out = nullptr;
   FILE* f = fopen(path, "rb");
   if (!f) { set_last_message("mps_load: cannot open file"); return QRTEBD_ERR_INVALID_ARG; }
+  auto reject = [&](const char* why) { fclose(f); set_last_message(why); return QRTEBD_ERR_INVALID_ARG; };
   int hdr[6];
-  if (fread(hdr, sizeof hdr, 1, f) != 1 || hdr[0] != (int)kMagic) {
-    fclose(f); set_last_message("mps_load: not a qrtebd checkpoint"); return QRTEBD_ERR_INVALID_ARG;
+  if (fread(hdr, sizeof hdr, 1, f) != 1 || hdr[0] != (int)kMagic) return reject("mps_load: not a qrtebd checkpoint");
+  const int L = hdr[1], d = hdr[2], inf = hdr[3], chi_max = hdr[4], prec = hdr[5];
+  if (d < 2 || d > 8 || chi_max < 1 || L < 2 || L > (1 << 20) || (inf != 0 && inf != 1) || (inf && L % 2) ||
+      prec < QRTEBD_C128 || prec > QRTEBD_C64_FP32)
+    return reject("mps_load: corrupt header");
+  // Everything is checked on the host before any device memory is taken: the bond
+  // dimensions against the capacities mps_create gives, and the file length against
+  // the bytes those dimensions imply, so that a truncated or padded file is refused.
+  const int nb = inf ? L : L + 1;
+  std::vector<int> chi(nb);
+  std::vector<char> diag(nb);
+  if (fread(chi.data(), sizeof(int), nb, f) != (size_t)nb || fread(diag.data(), 1, nb, f) != (size_t)nb)
+    return reject("mps_load: truncated or corrupt file");
+  const size_t esz = prec == QRTEBD_C128 ? sizeof(double2) : sizeof(float2);
+  size_t body = (size_t)nb * sizeof(double);
+  for (int b = 0; b < nb; ++b) {
+    const long long cap = inf ? chi_max
+                              : (b == 0 || b == L) ? 1
+                              : std::min<long long>(std::min(sat_pow(d, b, chi_max), sat_pow(d, L - b, chi_max)),
+                                                    chi_max);
+    if (chi[b] < 1 || chi[b] > cap) return reject("mps_load: bond dimension out of range");
+    body += ((size_t)chi[b] * chi[b] + chi[b]) * esz;
   }
-  qrtebd_mps_desc desc{hdr[1], hdr[2], hdr[3], hdr[4], hdr[5], nullptr};
+  for (int m = 0; m < L; ++m) body += (size_t)chi[m] * d * chi[inf ? (m + 1) % L : m + 1] * esz;
+  const long long here = ftell(f);
+  if (here < 0 || fseek(f, 0, SEEK_END) != 0) return reject("mps_load: cannot read file");
+  const long long total = ftell(f);
+  if (total != here + (long long)body || fseek(f, here, SEEK_SET) != 0)
+    return reject("mps_load: truncated or corrupt file");
+  qrtebd_mps_desc desc{L, d, inf, chi_max, prec, nullptr};
   qrtebd_mps* s = nullptr;
   int rc = qrtebd_mps_create(&desc, stream, &s);
   if (rc != QRTEBD_OK) { fclose(f); return rc; }
-  bool ok = fread(s->chi.data(), sizeof(int), s->chi.size(), f) == s->chi.size();
-  ok = ok && fread(s->xi_diag.data(), 1, s->xi_diag.size(), f) == s->xi_diag.size();
-  for (int b = 0; ok && b < s->nbonds_store; ++b) ok = s->chi[b] >= 1 && s->chi[b] <= s->cap[b];
+  s->chi = chi;
+  for (int b = 0; b < nb; ++b) s->xi_diag[b] = diag[b];
+  bool ok = true;
   std::vector<char> buf;
   auto load = [&](void* dptr, size_t bytes) {
     buf.resize(bytes);

@@ -66,10 +66,18 @@ extern "C" int qrtebd_zgemm_noalloc(int precision, int m, int n, int k, const vo
     set_last_message("zgemm_noalloc: only the tensor-core precisions C64_3XTF32 / C64_TF32");
     return QRTEBD_ERR_INVALID_ARG;
   }
-  if (m < 1 || n < 1 || k < 1 || !A || !B || !C || !alpha || !beta) return QRTEBD_ERR_INVALID_ARG;
+  if (m < 0 || n < 0 || k < 0 || !A || !B || !C || !alpha || !beta) return QRTEBD_ERR_INVALID_ARG;
   if (m > kMaxDim || n > kMaxDim || k > kMaxDim) {
     set_last_message("zgemm_noalloc: m, n and k must not exceed QRTEBD_NOALLOC_MAX_DIM (512)");
     return QRTEBD_ERR_INVALID_ARG;
+  }
+  if (m == 0 || n == 0) return QRTEBD_OK;  // an empty C: nothing to write
+  if (k == 0) {  // C = beta C: the CUDA-core kernel, which needs no scratch
+    GemmArgs<float> g0{m, n, 0, static_cast<const float2*>(A), sam, sak, false,
+                       static_cast<const float2*>(B), sbk, sbn, false, static_cast<float2*>(C), scm, scn,
+                       make_float2((float)alpha[0], (float)alpha[1]), make_float2((float)beta[0], (float)beta[1])};
+    ProfSuppress no_events;
+    return gemm_simt<float>(g0, static_cast<cudaStream_t>(stream), nullptr, 0);
   }
   float* base = nullptr;
   QR_TRY(scratch_address(&base));

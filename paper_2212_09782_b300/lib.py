@@ -56,6 +56,8 @@ def _load():
         "qrtebd_bond_workspace_size": (I, [I, I, I, I, I, I, I, C.POINTER(Trunc), C.POINTER(S)]),
         "qrtebd_bond_update": (I, [C.POINTER(BondIO), C.POINTER(Trunc), P, C.POINTER(BondInfo)]),
         "qrtebd_stream_check": (I, [P]),
+        "qrtebd_set_spin_limit": (I, [LL]),
+        "qrtebd_selftest_barrier_timeout": (I, [P]),
         "qrtebd_zgemm": (I, [I, I, I, I, P, LL, LL, I, P, LL, LL, I, P, LL, LL,
                              C.POINTER(D), C.POINTER(D), P, S, P]),
         "qrtebd_zgemm_workspace_size": (S, [I, I, I]),
@@ -255,6 +257,16 @@ def stream_check(stream=None):
     check(_lib.qrtebd_stream_check(stream_handle(stream)), "stream_check")
 
 
+def set_spin_limit(polls=0):
+    """Poll limit of the library's grid-wide barriers on the current device (0: default)."""
+    check(_lib.qrtebd_set_spin_limit(int(polls)), "set_spin_limit")
+
+
+def selftest_barrier_timeout(stream=None):
+    """Enqueue one CTA whose grid barrier nothing releases; stream_check then raises TIMEOUT."""
+    check(_lib.qrtebd_selftest_barrier_timeout(stream_handle(stream)), "selftest_barrier_timeout")
+
+
 def householder_qr(precision, A, stream=None):
     """QR of a 2-D torch CUDA tensor (m x n, m >= n): returns (Q, R); A is left untouched."""
     import torch
@@ -309,6 +321,7 @@ def _mps_sigs():
         "qrtebd_expectation": (I, [P, I, I, C.POINTER(D), C.POINTER(D)]),
         "qrtebd_truncation_error": (I, [P, I, C.POINTER(D)]),
         "qrtebd_schmidt": (I, [P, I, C.POINTER(D), I, C.POINTER(I)]),
+        "qrtebd_entropy": (I, [P, I, C.POINTER(D)]),
         "qrtebd_bond_dims": (I, [P, C.POINTER(I), I, C.POINTER(I)]),
         "qrtebd_sync": (I, [P]),
         "qrtebd_mps_save": (I, [P, C.c_char_p]),
@@ -400,10 +413,9 @@ class MPS:
         return S[: n.value]
 
     def entropy(self, bond):
-        s = self.schmidt(bond)
-        p = s ** 2
-        p = p[p > 1e-300]
-        return float(-(p * np.log(p)).sum())
+        out = C.c_double(0)
+        check(_lib.qrtebd_entropy(self.h, bond, C.byref(out)), "entropy")
+        return out.value
 
     def sync(self):
         check(_lib.qrtebd_sync(self.h), "sync")

@@ -164,8 +164,7 @@ def test_exact_when_eta_covers_rank(prec):
     assert gpu["eps"] < (1e-14 if prec == "c128" else 1e-6)
 
 
-def test_c2_full_size_against_oracle():
-    """The bench workload (chi = 1024, d = 5, complex64 3xTF32) against the full oracle."""
+def _c2_full_size(prec, tol):
     import torch
     from paper_2212_09782_b300 import lib as L
     wl = W.bond_microbench(1024, 5)
@@ -173,24 +172,38 @@ def test_c2_full_size_against_oracle():
     Bn = wl["Bn"].astype(np.complex128)
     U = wl["U"]
     orc = bond.qr_update(None, None, Bn, U, chi_max=1024, theta=th)
-    gpu = run_gpu("c64_3xtf32", None, None, Bn, U, L.trunc_default(L.PLAIN, 1024), theta=th)
+    gpu = run_gpu(prec, None, None, Bn, U, L.trunc_default(L.PLAIN, 1024), theta=th)
     s_g = np.linalg.svd(gpu["Xi_new"], compute_uv=False)
     s_o = np.linalg.svd(orc["Xi_new"], compute_uv=False)
-    assert np.linalg.norm(s_g - s_o) / np.linalg.norm(s_o) < 1e-5
-    assert abs(gpu["eps"] - orc["eps"]) / orc["eps"] < 1e-5
+    errs = {"schmidt": np.linalg.norm(s_g - s_o) / np.linalg.norm(s_o),
+            "eps": abs(gpu["eps"] - orc["eps"]) / orc["eps"]}
     # principal angles between the GPU and oracle right spaces: all cosines ~ 1
     Bg = gpu["Bn_new"].reshape(1024, -1)
     Bo = orc["Bn_new"].reshape(1024, -1)
     cosines = np.linalg.svd(Bg @ Bo.conj().T, compute_uv=False)
-    assert 1 - cosines.min() < 1e-5
+    errs["angles"] = 1 - cosines.min()
     # B~^m B~^n applied to random probes
     r = W.rng(9)
     v = W.complex_gaussian(r, (Bg.shape[1], 8))
     bm_g = gpu["Bm_new"].reshape(-1, 1024)
     bm_o = orc["Bm_new"].reshape(-1, 1024)
     a, b = bm_g @ (Bg @ v), bm_o @ (Bo @ v)
-    assert np.linalg.norm(a - b) / np.linalg.norm(b) < 1e-5
+    errs["BB"] = np.linalg.norm(a - b) / np.linalg.norm(b)
+    print(prec, errs)
+    bad = {k: e for k, e in errs.items() if not e < tol}
+    assert not bad, (bad, errs)
     torch.cuda.synchronize()
+
+
+def test_c2_full_size_against_oracle():
+    """The bench workload (chi = 1024, d = 5, complex64 3xTF32) against the full oracle."""
+    _c2_full_size("c64_3xtf32", 1e-5)
+
+
+@pytest.mark.slow
+def test_c2_full_size_c128_against_oracle():
+    """The same workload on the complex128 path (FP64 throughout) at the 1e-10 bar."""
+    _c2_full_size("c128", 1e-10)
 
 
 @pytest.mark.parametrize("prec", ["c64_tf32", "c64_3xtf32"])

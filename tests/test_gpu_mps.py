@@ -133,3 +133,15 @@ def test_checkpoint_resume_bit_exact(tmp_path):
     assert za == zb
     assert a.truncation_error(-1) == b.truncation_error(-1)
     assert a.bond_dims() == b.bond_dims()
+
+
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-10), ("c64_3xtf32", 1e-5)])
+def test_entropy_matches_oracle(prec, tol):
+    # S_vN on every bond, computed by the library (qrtebd_entropy), against the oracle's
+    L, d, g, dt, steps, chi = 10, 3, 1.5, 0.05, 6, 32
+    o, s, _zo, _zg = run_both(L, d, g, dt, steps, chi, "plain", prec)
+    for b in range(L + 1):
+        eo = obond.entropy(o.Xi[b])
+        eg = s.entropy(b)
+        assert abs(eg - eo) <= tol * max(1.0, eo), (b, eg, eo)
+    s.close()

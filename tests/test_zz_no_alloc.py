@@ -15,6 +15,16 @@ from paper_2212_09782_b300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
+def _fn(L):
+    f = L.raw().qrtebd_zgemm_noalloc
+    f.restype = C.c_int
+    f.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_longlong, C.c_longlong,
+                  C.c_int, C.c_void_p, C.c_longlong, C.c_longlong, C.c_int, C.c_void_p,
+                  C.c_longlong, C.c_longlong, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                  C.c_void_p]
+    return f
+
+
 def _noalloc(L, prec, A, B, Cm, ta, ca, tb, cb, alpha, beta):
     m = A.shape[1] if ta else A.shape[0]
     k = A.shape[0] if ta else A.shape[1]
@@ -23,12 +33,7 @@ def _noalloc(L, prec, A, B, Cm, ta, ca, tb, cb, alpha, beta):
     sbk, sbn = (1, B.shape[1]) if tb else (B.shape[1], 1)
     al = (C.c_double * 2)(alpha.real, alpha.imag)
     be = (C.c_double * 2)(beta.real, beta.imag)
-    f = L.raw().qrtebd_zgemm_noalloc
-    f.restype = C.c_int
-    f.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_longlong, C.c_longlong,
-                  C.c_int, C.c_void_p, C.c_longlong, C.c_longlong, C.c_int, C.c_void_p,
-                  C.c_longlong, C.c_longlong, C.POINTER(C.c_double), C.POINTER(C.c_double),
-                  C.c_void_p]
+    f = _fn(L)
     return f(L.PRECISIONS[prec], m, n, k, C.c_void_p(A.data_ptr()), sam, sak, int(ca),
              C.c_void_p(B.data_ptr()), sbk, sbn, int(cb), C.c_void_p(Cm.data_ptr()),
              Cm.shape[1], 1, al, be, L.stream_handle())
@@ -38,8 +43,12 @@ def _noalloc(L, prec, A, B, Cm, ta, ca, tb, cb, alpha, beta):
 def test_noalloc_matches_zgemm_twice(prec):
     import torch
     from paper_2212_09782_b300 import lib as L
+    # 512^3 fills the embedded B'^T region exactly and leaves room for only two split-K
+    # partial blocks; 300 x 512 x 512 takes the N > M swap at the cap
     cases = [((200, 300, 400), "nn", 0.7 - 0.2j, 0.0),
-             ((512, 96, 512), "ct", 1.0, -0.5 + 0.25j)]
+             ((512, 96, 512), "ct", 1.0, -0.5 + 0.25j),
+             ((512, 512, 512), "nc", 0.3 + 0.1j, 1.0),
+             ((300, 512, 512), "tn", 1.0, 0.0)]
     for (m, n, k), ops, alpha, beta in cases:
         r = W.rng(m + n + k)
         ta, tb = ops[0] in "tc", ops[1] in "tc"
@@ -57,6 +66,34 @@ def test_noalloc_matches_zgemm_twice(prec):
         tol = 3e-7 * np.sqrt(k) + 2e-6 if prec == "c64_3xtf32" else 4e-3
         err = (got - ref).abs().max().item() / scale
         assert err < tol, err
+
+
+def test_noalloc_empty_sizes_as_zgemm():
+    import torch
+    from paper_2212_09782_b300 import lib as L
+    f = _fn(L)
+    A = torch.ones(8, 4, dtype=torch.complex64, device="cuda")
+    B = torch.ones(4, 6, dtype=torch.complex64, device="cuda")
+    C0 = torch.full((8, 6), 2 - 1j, dtype=torch.complex64, device="cuda")
+    al = (C.c_double * 2)(1.0, 0.0)
+    be = (C.c_double * 2)(0.0, 0.5)
+    ptr = lambda t: C.c_void_p(t.data_ptr())
+
+    def call(m, n, k, Cm):
+        return f(L.C64_3XTF32, m, n, k, ptr(A), 4, 1, 0, ptr(B), 6, 1, 0, ptr(Cm), 6, 1, al, be,
+                 L.stream_handle())
+    # k = 0: C = beta C
+    got = C0.clone()
+    assert call(8, 6, 0, got) == 0
+    L.stream_check()
+    assert torch.allclose(got, C0 * 0.5j)
+    # m = 0 or n = 0: nothing written
+    for m, n in ((0, 6), (8, 0)):
+        got = C0.clone()
+        assert call(m, n, 4, got) == 0
+        L.stream_check()
+        assert torch.equal(got, C0)
+    assert call(-1, 6, 4, C0.clone()) == L.ERR_INVALID_ARG
 
 
 def test_noalloc_rejects_oversize_and_cuda_core_precisions():
