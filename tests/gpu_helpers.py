@@ -2,7 +2,25 @@
 gauge-invariant quantities with the oracle on identical inputs."""
 import numpy as np
 
-TOL = {"c128": 1e-10, "c64_3xtf32": 1e-5, "c64_fp32": 1e-5, "c64_tf32": 3e-2}
+# 1xTF32 (10-bit products) is outside the 1e-5 bar: measured against the oracle at
+# chi ~ 100-250, d = 3-4: Schmidt values ~4e-5, eps ~1e-4, projector-type invariants ~2e-3
+TOL = {"c128": 1e-10, "c64_3xtf32": 1e-5, "c64_fp32": 1e-5, "c64_tf32": 5e-3}
+
+# Unit perturbation of the bond matrix that the arithmetic leaves (relative to its norm):
+# complex64 stores X, Q, Y and L in FP32 (unit roundoff 6e-8) between FP32-accumulated
+# products; complex128 stores them in FP64.
+PERTURB = {"c128": 1e-15, "c64_3xtf32": 1e-7, "c64_fp32": 1e-7, "c64_tf32": 1e-7}
+
+
+def subspace_tol(tol, prec, S, c):
+    """Tolerance of the kept-subspace invariants (projector, B~^m B~^n, G) after a cut at c
+    values of the spectrum S (descending): the kept space moves by up to |E| / gap under a
+    perturbation E of L (Davis-Kahan), gap = (S[c-1] - S[c]) / S[0], so the comparison is held
+    to max(tol, PERTURB / gap); the Schmidt values and eps stay at tol."""
+    if c >= len(S) or S[0] <= 0:
+        return tol
+    gap = (S[c - 1] - S[c]) / S[0]
+    return max(tol, PERTURB[prec] / max(gap, 1e-300))
 
 
 def to_dev(a, prec):
@@ -62,14 +80,16 @@ def rel(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def compare(gpu, orc, tol, keys=("s", "P", "BB", "G"), eps=True):
+def compare(gpu, orc, tol, keys=("s", "P", "BB", "G"), eps=True, sub_tol=None):
+    """sub_tol: the tolerance of the kept-subspace invariants (P, BB, G), default tol."""
     ig, io = invariants(gpu), invariants(orc)
     errs = {k: rel(ig[k], io[k]) for k in keys}
     if eps:
         errs["eps"] = abs(gpu["eps"] - orc["eps"]) / max(abs(orc["eps"]), 1e-300)
         if orc["eps"] < 1e-7:
             errs["eps"] = abs(gpu["eps"] - orc["eps"])
-    bad = {k: v for k, v in errs.items() if not (v <= tol)}
+    lim = {k: (sub_tol if (sub_tol is not None and k in ("P", "BB", "G")) else tol) for k in errs}
+    bad = {k: v for k, v in errs.items() if not (v <= lim[k])}
     assert not bad, (bad, errs)
     # exact isometry of B~^n (Sec. II: Q^[n] has orthonormal rows)
     c = gpu["Xi_new"].shape[0]

@@ -9,7 +9,7 @@ import pytest
 
 from oracle import bond
 from paper_2212_09782_b300 import workloads as W
-from tests.gpu_helpers import TOL, compare, rounded, run_gpu
+from tests.gpu_helpers import TOL, compare, rounded, run_gpu, subspace_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -92,11 +92,11 @@ def test_cbe(prec, dims):
     assert gpu["chi_new"] == orc["chi_new"]
     S = orc["S"]
     k = S >= 1e-6 * S[0]
-    assert np.allclose(gpu["S"][: len(S)][k], S[k], rtol=TOL[prec] * 10, atol=0)
+    assert np.allclose(gpu["S"][: len(S)][k], S[k], rtol=TOL[prec], atol=0)
     # Xi~ diagonal, positive, descending (canonical form)
     x = gpu["Xi_new"]
     assert np.abs(x - np.diag(np.diag(x))).max() < 1e-6
-    compare(gpu, orc, TOL[prec] * 10 if prec != "c128" else TOL[prec])
+    compare(gpu, orc, TOL[prec], sub_tol=subspace_tol(TOL[prec], prec, S, orc["chi_new"]))
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64_3xtf32", "c64_fp32"])
@@ -114,8 +114,10 @@ def test_cbe_many_jacobi_rounds(prec, dims):
     assert gpu["chi_new"] == orc["chi_new"] == chi_max
     S = orc["S"]
     k = S >= 1e-4 * S[0]
-    assert np.allclose(gpu["S"][: len(S)][k], S[k], rtol=TOL[prec] * 10, atol=0)
-    compare(gpu, orc, TOL[prec] * 10 if prec != "c128" else TOL[prec])
+    assert np.allclose(gpu["S"][: len(S)][k], S[k], rtol=TOL[prec], atol=0)
+    # the cut falls inside a dense spectrum (gap ~1.8e-3 S_1): the kept space is resolved to
+    # PERTURB / gap (measured 1.6e-5 for the projector in complex64 3xTF32, 9e-6 on CUDA cores)
+    compare(gpu, orc, TOL[prec], sub_tol=subspace_tol(TOL[prec], prec, S, orc["chi_new"]))
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64_3xtf32"])
@@ -139,8 +141,8 @@ def test_cbe_eps_target(prec):
     gpu = run_gpu(prec, bd["Xi"], bd["Bm"], bd["Bn"], bd["U"], t, xi_kind=2)
     assert gpu["chi_new"] == orc["chi_new"] == c_want
     k = S >= 1e-6 * S[0]
-    assert np.allclose(gpu["S"][: len(S)][k], S[k], rtol=TOL[prec] * 10, atol=0)
-    compare(gpu, orc, TOL[prec] * 10 if prec != "c128" else TOL[prec])
+    assert np.allclose(gpu["S"][: len(S)][k], S[k], rtol=TOL[prec], atol=0)
+    compare(gpu, orc, TOL[prec], sub_tol=subspace_tol(TOL[prec], prec, S, orc["chi_new"]))
 
 
 @pytest.mark.parametrize("prec", ["c128", "c64_3xtf32"])

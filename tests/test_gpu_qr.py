@@ -42,7 +42,7 @@ def test_qr_matches_lapack(prec, m, n):
 
 
 @pytest.mark.parametrize("prec", list(TOL))
-@pytest.mark.parametrize("m,n", [(5152, 33), (6000, 40), (13000, 40)])
+@pytest.mark.parametrize("m,n", [(5152, 33), (6000, 40), (13000, 40), (5120, 160), (3000, 128), (330, 64)])
 def test_qr_tall_panels(prec, m, n):
     # panels of up to 320 slab rows per CTA of a 16-CTA cluster hold the slab in registers
     # (complex64); taller ones keep every row in shared memory: both forms, one row past
@@ -71,6 +71,24 @@ def test_qr_rank_deficient_gives_isometry(prec):
     tol = TOL[prec]
     assert np.abs(Q.conj().T @ Q - np.eye(60)).max() < tol * 5
     assert np.linalg.norm(Q @ R - A) / np.linalg.norm(A) < tol
+
+
+@pytest.mark.parametrize("prec", list(TOL))
+@pytest.mark.parametrize("m,n,rank", [(2000, 64, 10), (5120, 96, 40)])
+def test_qr_tall_rank_deficient(prec, m, n, rank):
+    # tall panels of a rank-deficient matrix: the complex64 panels run as a tall-skinny tree
+    # (several leaves and a combine); the reflectors of the noise directions are arbitrary,
+    # but Q must stay an exact isometry with Q R = A
+    r = W.rng(m + rank)
+    A = W.complex_gaussian(r, (m, rank)) @ W.complex_gaussian(r, (rank, n))
+    if prec != "c128":
+        A = A.astype(np.complex64).astype(np.complex128)
+    Q, R = _run(prec, A)
+    tol = TOL[prec]
+    assert np.isfinite(Q).all() and np.isfinite(R).all()
+    assert np.abs(Q.conj().T @ Q - np.eye(n)).max() < tol * 5
+    assert np.linalg.norm(Q @ R - A) / np.linalg.norm(A) < tol
+    assert np.abs(np.tril(R, -1)).max() == 0
 
 
 @pytest.mark.parametrize("prec", list(TOL))
