@@ -79,13 +79,20 @@ def cbe_cut(S, chi_max, svd_min=1e-14, tie_tol=1e-10, eps_target=0.0):
 
 
 def qr_update(Xi, Bm, Bn, U, *, scheme="plain", chi_max, eta=None, dchi_min=100,
-              dchi_frac=0.1, svd_min=1e-14, tie_tol=1e-10, eps_target=0.0, theta=None, Y0=None):
+              dchi_frac=0.1, svd_min=1e-14, tie_tol=1e-10, eps_target=0.0, theta=None, Y0=None,
+              sweeps=1):
     """One QR-TEBD bond update.
 
     theta, if given, is theta' = B^m B^n of shape (chi_L, d, d, chi_R) (then Bm is
     unused). Returns a dict with the new tensors Bm_new (chi_L, d, chi~),
     Xi_new (chi~, chi~), Bn_new (chi~, d, chi_R), the truncation error eps and
     the intermediates Q, L, Qn (and S, V for CBE).
+
+    sweeps > 1 iterates steps (i)-(ii) as the alternating least-squares solver of Sec. II
+    (comments after the algorithm): each further sweep keeps the isometry Y = Q^[n] of the
+    previous one, forms the optimal X = theta~ Y^dag, gauges it with a QR, updates
+    Y = Q^dag theta~ and takes its LQ again. The paper uses one sweep for gates close to
+    the identity; a generic theta~ (e.g. a circuit gate, Sec. V) needs more.
     """
     if theta is None:
         theta = theta_prime(Bm, Bn)
@@ -121,6 +128,15 @@ def qr_update(Xi, Bm, Bn, U, *, scheme="plain", chi_max, eta=None, dchi_min=100,
     Qh, Rh = np.linalg.qr(Y.conj().T, mode="reduced")
     L = Rh.conj().T
     Qn = Qh.conj().T
+
+    # further sweeps of the alternating least-squares solver (Sec. II comments): Y0 = Q^[n]
+    for _ in range(int(sweeps) - 1):
+        X = T @ Qn.conj().T
+        Q, _R = np.linalg.qr(X, mode="reduced")
+        Y = Q.conj().T @ T
+        Qh, Rh = np.linalg.qr(Y.conj().T, mode="reduced")
+        L = Rh.conj().T
+        Qn = Qh.conj().T
 
     out = {"Q": Q, "L": L, "Qn": Qn, "eta": eta, "X": X, "Y": Y}
     nrm2_theta = float(np.vdot(T, T).real)

@@ -238,3 +238,67 @@ def test_eta_policy():
     assert bond.choose_eta("cbe", 1024, 1024, 1024, 5, 1024) == 1024 + 103
     assert bond.choose_eta("cbe", 10, 10, 10, 3, 1024) == 30
     assert bond.choose_eta("cbe", 400, 400, 400, 5, 1024, 100, 0.1) == 500
+
+
+def _designed_theta(r, m, n, spec):
+    """theta~ = Ua diag(spec) Vb^dag with random unitaries (a chosen singular spectrum)."""
+    Ua = np.linalg.qr(W.complex_gaussian(r, (m, m)))[0][:, : len(spec)]
+    Vb = np.linalg.qr(W.complex_gaussian(r, (n, n)))[0][:, : len(spec)]
+    return (Ua * spec) @ Vb.conj().T
+
+
+def test_sweeps_one_is_the_single_update():
+    bd = W.random_bond(8, 3, 8, 8, seed=71, xi="dense")
+    a = bond.qr_update(bd["Xi"], bd["Bm"], bd["Bn"], bd["U"], chi_max=8)
+    b = bond.qr_update(bd["Xi"], bd["Bm"], bd["Bn"], bd["U"], chi_max=8, sweeps=1)
+    assert np.array_equal(a["Xi_new"], b["Xi_new"]) and a["eps"] == b["eps"]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_sweeps_never_increase_eps_and_reach_svd_optimum(seed):
+    # Sec. II: each half sweep minimises ||theta~ - X Y|| exactly over one factor (X = theta~ Y^dag
+    # for an isometric Y, then Y = Q^dag theta~), so eps cannot grow from sweep to sweep; the
+    # iteration is a subspace iteration on theta~^dag theta~, so with a gap below eta it reaches
+    # the Eckart-Young optimum (the SVD truncation error). A random gate (far from the identity)
+    # on a random bond
+    r = W.rng(300 + seed)
+    chiL, d, chiM, chiR = 10, 3, 6, 10
+    bd = W.random_bond(chiL, d, chiM, chiR, seed=400 + seed, xi="dense")
+    U = W.random_unitary(r, d * d)
+    eps = [bond.qr_update(bd["Xi"], bd["Bm"], bd["Bn"], U, chi_max=chiM, sweeps=k)["eps"]
+           for k in range(1, 41)]
+    assert all(b <= a * (1 + 1e-12) + 1e-15 for a, b in zip(eps, eps[1:])), eps
+    opt = bond.svd_update(bd["Xi"], bd["Bm"], bd["Bn"], U, chi_max=chiM)["eps"]
+    assert eps[0] > opt * (1 + 1e-6)          # one sweep is not optimal for a generic gate
+    assert abs(eps[-1] - opt) <= 1e-8 * opt   # forty sweeps are
+
+
+def test_sweeps_converge_at_the_subspace_iteration_rate():
+    # theta~ with singular values 1 (x eta) then r (x the rest): the right space after k sweeps
+    # is Y0 (theta~^dag theta~)^k orthonormalised, so the angle to the dominant space shrinks
+    # by r^2 per sweep and the excess error eps_k - eps_opt by r^4
+    rr = 0.5
+    r = W.rng(77)
+    m, n, eta = 24, 30, 6
+    spec = np.r_[np.ones(eta), rr * np.ones(8)]
+    T = _designed_theta(r, m, n, spec).reshape(m // 3, 3, 3, n // 3)
+    Y0 = np.linalg.qr(W.complex_gaussian(r, (n, eta)))[0].conj().T
+    opt = float(np.sum(spec[eta:] ** 2) / np.sum(spec ** 2))
+    ex = []
+    for k in range(1, 9):
+        out = bond.qr_update(None, None, None, np.eye(9), chi_max=eta, eta=eta, theta=T, Y0=Y0, sweeps=k)
+        ex.append(out["eps"] - opt)
+    ratios = [b / a for a, b in zip(ex[3:], ex[4:])]
+    assert all(0.5 * rr ** 4 < q < 2.0 * rr ** 4 for q in ratios), (ex, ratios)
+
+
+def test_sweeps_reach_the_dominant_singular_values():
+    # converged, the kept Schmidt values are the eta largest singular values of theta~
+    r = W.rng(78)
+    m, n, eta = 24, 30, 5
+    spec = np.r_[np.linspace(1.0, 0.6, eta), 0.3 * np.linspace(1.0, 0.1, 10)]
+    T = _designed_theta(r, m, n, spec).reshape(m // 3, 3, 3, n // 3)
+    Y0 = np.linalg.qr(W.complex_gaussian(r, (n, eta)))[0].conj().T
+    out = bond.qr_update(None, None, None, np.eye(9), chi_max=eta, eta=eta, theta=T, Y0=Y0, sweeps=60)
+    s = np.linalg.svd(out["Xi_new"], compute_uv=False) * out["norm_L"]
+    assert np.allclose(s, spec[:eta], rtol=1e-10, atol=0)
