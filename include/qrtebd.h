@@ -81,6 +81,13 @@ typedef struct qrtebd_trunc {
                          max |B B^dag - 1| 9e-4 -> 1e-6 after 1xTF32; after 3xTF32 it is
                          already ~6e-7, the level the pass's Gram matrix resolves).
                          -1 (default): on for QRTEBD_C64_TF32 only; 0: off; 1: on. */
+  int sweeps;         /* sweeps of the alternating least-squares solver that steps (i)-(ii)
+                         are one of (Sec. II, comments after the algorithm): 0 or 1 (default)
+                         is the paper's single sweep, enough for gates close to the identity;
+                         k > 1 repeats X = theta~ Q^[n]^dag, QR, Y = Q^dag theta~, LQ with the
+                         previous sweep's Q^[n] as Y0, for gates far from the identity (Sec. V:
+                         circuit gates). eps never grows from sweep to sweep and reaches the
+                         SVD optimum when the spectrum has a gap at eta. 1 <= k <= 1000. */
 } qrtebd_trunc;
 /* eta policy (Sec. II last paragraph, Sec. III):
  *   PLAIN: eta = min(chi_max, d chi_l, d chi_r); initial guess Y0 = B^n if

@@ -441,6 +441,25 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
   if (Zc) QR_CUDA_TRY(cudaMemcpyAsync(Zc, Z, (size_t)nR * eta * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st));
   QR_TRY(householder_qr<T>(Z, eta, (int)nR, eta, Qz, eta, qs, st, err, &qg, &qg_side));
 
+  // further sweeps of the alternating least-squares solver (Sec. II comments): the isometry
+  // Q^[n] = Qz^dag of the last sweep is kept, X = theta~ Q^[n]^dag = theta~ Qz is the optimal
+  // left factor for it, its QR gauges it, and Y = Q^dag theta~ (as Z = theta~^dag Q) is
+  // factored again
+  for (int sweep = 1; sweep < tr->sweeps; ++sweep) {
+    {
+      GemmArgs<T> g{(int)mL, eta, (int)nR, theta_t, nR, 1, false, Qz, eta, 1, false, X, eta, 1, one, zero};
+      g.reuse_a = true;
+      QR_TRY(runner.run(g, st, true));
+    }
+    QR_TRY(householder_qr<T>(X, eta, (int)mL, eta, Q, eta, qs, st, err, &qg, &qg_side));
+    {
+      GemmArgs<T> g{(int)nR, eta, (int)mL, theta_t, 1, nR, true, Q, eta, 1, false, Z, eta, 1, one, zero};
+      QR_TRY(runner.run(g, st, true));
+    }
+    if (Zc) QR_CUDA_TRY(cudaMemcpyAsync(Zc, Z, (size_t)nR * eta * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st));
+    QR_TRY(householder_qr<T>(Z, eta, (int)nR, eta, Qz, eta, qs, st, err, &qg, &qg_side));
+  }
+
   // the re-orthogonalisation passes run in 3xTF32 whatever the precision
   const GemmRunner<T> runner3{use_tc ? (int)QRTEBD_C64_3XTF32 : io->precision, runner.tc,
                               runner.simt_scratch, runner.simt_scratch_elems};
@@ -592,6 +611,10 @@ int bond_update(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t s
     return QRTEBD_ERR_INVALID_ARG;
   if (io->xi_kind < 0 || io->xi_kind > 2) return QRTEBD_ERR_INVALID_ARG;
   if (tr->scheme != QRTEBD_PLAIN && tr->scheme != QRTEBD_CBE) return QRTEBD_ERR_INVALID_ARG;
+  if (tr->sweeps < 0 || tr->sweeps > 1000) {
+    set_last_message("bond_update: sweeps must lie in 0..1000");
+    return QRTEBD_ERR_INVALID_ARG;
+  }
   if (!bytes) {
     if (!io->bn || !io->gate || !io->bm_out || !io->xi_out || !io->bn_out) return QRTEBD_ERR_INVALID_ARG;
     if (!io->theta && !io->bm) return QRTEBD_ERR_INVALID_ARG;

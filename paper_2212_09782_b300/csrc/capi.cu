@@ -191,6 +191,7 @@ int qrtebd_trunc_default(qrtebd_trunc* tr, int scheme, int chi_max) {
   tr->eps_explicit = 0;
   tr->eps_target = 0.0;
   tr->reorth = -1;
+  tr->sweeps = 1;
   return QRTEBD_OK;
 }
 

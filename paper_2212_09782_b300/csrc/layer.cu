@@ -152,7 +152,7 @@ int qrtebd_apply_gate_layer_batched(qrtebd_mps* const* states, int nstates, int 
   std::vector<Task> tasks;
   size_t need[kWorkers] = {};
   std::vector<long long> key = {parity, tr->scheme, tr->chi_max, tr->eta, tr->dchi_min,
-                                tr->eps_explicit, tr->reorth};
+                                tr->eps_explicit, tr->reorth, tr->sweeps};
   for (int i = 0; i < nstates; ++i) {
     qrtebd_mps* s = states[i];
     key.push_back(reinterpret_cast<long long>(s));

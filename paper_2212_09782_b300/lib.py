@@ -22,7 +22,8 @@ PRECISIONS = {"c128": C128, "c64_3xtf32": C64_3XTF32, "c64_tf32": C64_TF32, "c64
 class Trunc(C.Structure):
     _fields_ = [("scheme", C.c_int), ("chi_max", C.c_int), ("eta", C.c_int), ("dchi_min", C.c_int),
                 ("dchi_frac", C.c_double), ("svd_min", C.c_double), ("tie_tol", C.c_double),
-                ("eps_explicit", C.c_int), ("eps_target", C.c_double), ("reorth", C.c_int)]
+                ("eps_explicit", C.c_int), ("eps_target", C.c_double), ("reorth", C.c_int),
+                ("sweeps", C.c_int)]
 
 
 class BondIO(C.Structure):

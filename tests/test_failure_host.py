@@ -90,3 +90,13 @@ def test_missing_checkpoint_is_refused(L, tmp_path):
     h = C.c_void_p()
     st = L.raw().qrtebd_mps_load(str(tmp_path / "absent").encode(), None, C.byref(h))
     assert st == L.ERR_INVALID_ARG and not h.value
+
+
+def test_sweeps_out_of_range_is_refused(L):
+    nb = C.c_size_t(0)
+    for k in (-1, 1001):
+        t = L.trunc_default(L.PLAIN, 8, sweeps=k)
+        st = L.raw().qrtebd_bond_workspace_size(L.C64_3XTF32, 8, 2, 8, 8, 1, 0, C.byref(t), C.byref(nb))
+        assert st == L.ERR_INVALID_ARG
+    t = L.trunc_default(L.PLAIN, 8)
+    assert t.sweeps == 1

@@ -53,3 +53,26 @@ def test_set_site_and_bond_roundtrip():
     for m in range(L):
         assert abs(s.expectation(m, np.eye(d)) - 1) < 1e-12
     assert np.allclose(s.schmidt(3), np.sort(np.abs(Xi[3]))[::-1], atol=1e-12)
+
+
+def test_batched_layer_sweeps_is_part_of_the_replayed_shape():
+    # a plain layer is captured as a graph on its second sighting; the same shapes with a
+    # different number of ALS sweeps must not replay it
+    import numpy as np
+    from paper_2212_09782_b300 import lib as L
+    Lc, d, chi = 8, 3, 9
+    runs = {}
+    for sweeps in (1, 1, 1, 3):
+        s = L.MPS(Lc, d, chi, precision="c128")
+        U = np.linalg.qr(np.random.default_rng(5).normal(size=(9, 9)) + 1j * np.random.default_rng(6).normal(size=(9, 9)))[0]
+        gates = np.stack([U] * (Lc - 1))
+        tr = L.trunc_default(L.PLAIN, chi, sweeps=sweeps)
+        for _ in range(3):
+            L.apply_layer_batched([s], 0, [gates], tr)
+            L.apply_layer_batched([s], 1, [gates], tr)
+        s.sync()
+        runs.setdefault(sweeps, []).append(s.truncation_error(-1))
+        s.close()
+    # identical runs agree (graph replay included); three sweeps truncate less
+    assert np.allclose(runs[1], runs[1][0], rtol=1e-12, atol=0)
+    assert runs[3][0] < runs[1][0]

@@ -301,3 +301,28 @@ def test_inputs_passed_as_the_bench_does():
     with pytest.raises(ValueError):
         up.run(torch.from_numpy(wl["U"]).cuda(), torch.from_numpy(wl["Bn"]).cuda().permute(2, 1, 0),
                theta=torch.from_numpy(wl["theta"]).cuda())
+
+
+@pytest.mark.parametrize("prec", ["c128", "c64_3xtf32"])
+@pytest.mark.parametrize("scheme", ["plain", "cbe"])
+def test_als_sweeps_match_oracle(prec, scheme):
+    # a random unitary gate (far from the identity, Sec. V) on a random bond: the single sweep
+    # of the paper and four sweeps of the alternating least-squares solver (Sec. II comments)
+    # against the oracle's, and the extra sweeps lower eps
+    from paper_2212_09782_b300 import lib as L
+    dims = (40, 3, 24, 40)
+    bd = _case(dims, seed=1234, xi="diag", prec=prec)
+    chi_max = 24 if scheme == "plain" else 30
+    kw = {} if scheme == "plain" else dict(dchi_min=6, dchi_frac=0.1)
+    eps = {}
+    for k in (1, 4):
+        orc = bond.qr_update(bd["Xi"], bd["Bm"], bd["Bn"], bd["U"], scheme=scheme, chi_max=chi_max,
+                             sweeps=k, **kw)
+        t = L.trunc_default(L.PLAIN if scheme == "plain" else L.CBE, chi_max, sweeps=k, **kw)
+        gpu = run_gpu(prec, bd["Xi"], bd["Bm"], bd["Bn"], bd["U"], t, xi_kind=2)
+        assert gpu["chi_new"] == orc.get("chi_new", orc["eta"])
+        sub = subspace_tol(TOL[prec], prec, orc["S"], orc["chi_new"]) if scheme == "cbe" else None
+        compare(gpu, orc, TOL[prec], sub_tol=sub)
+        eps[k] = gpu["eps"]
+    assert eps[4] < eps[1]
+
