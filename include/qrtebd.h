@@ -49,11 +49,17 @@ extern "C" {
  *              cores as three TF32 products (hi*hi + hi*lo + lo*hi) with FP32
  *              accumulation; Householder norms and all reductions in FP64.
  *   C64_TF32   as C64_3XTF32 with one TF32 product (about 1e-3 relative error).
- *   C64_FP32   complex64 tensors, FP32 CUDA-core arithmetic (no tensor cores). */
+ *   C64_FP32   complex64 tensors, FP32 CUDA-core arithmetic (no tensor cores).
+ *   C128_OZ    complex128 tensors; the large complex products run as FP64 emulated on the
+ *              TF32 tensor cores (Ozaki splitting: every row scaled by a power of two and cut
+ *              into 8 integer slices of 7 bits, the slice products summed exactly in FP32
+ *              over 1024 terms and accumulated in FP64), about 1e-15 relative to the exact
+ *              product; panels, norms and small products stay in FP64 on CUDA cores. */
 #define QRTEBD_C128 0
 #define QRTEBD_C64_3XTF32 1
 #define QRTEBD_C64_TF32 2
 #define QRTEBD_C64_FP32 3
+#define QRTEBD_C128_OZ 4
 
 /* -------------------------------------------------------------- truncation */
 #define QRTEBD_PLAIN 0 /* Sec. II: eta fixed a priori, Xi~ = L (non-diagonal) */
@@ -268,14 +274,15 @@ int qrtebd_mps_set_bond(qrtebd_mps* mps, int bond, const double* xi_host, int ch
  * opB(k, j) = B[k*sbk + j*sbn] (conjugated if conj_b), C(i, j) = C[i*scm + j*scn];
  * strides in complex elements, so transposes are stride choices. alpha, beta:
  * host complex128 (2 doubles each). precision as above: C128 / C64_FP32 run on
- * CUDA cores; C64_3XTF32 / C64_TF32 on tcgen05 tensor cores and need `workspace`
- * of qrtebd_zgemm_workspace_size(m, n, k) bytes (device; NULL/0 allowed for the
- * CUDA-core precisions). Enqueued on `stream`, no synchronisation. */
+ * CUDA cores; C64_3XTF32 / C64_TF32 / C128_OZ on tcgen05 tensor cores and need
+ * `workspace` of qrtebd_zgemm_workspace_size(m, n, k) bytes (device; NULL/0 allowed
+ * for the CUDA-core precisions). C128_OZ runs products too small to fill the GPU on
+ * the FP64 CUDA cores. Enqueued on `stream`, no synchronisation. */
 int qrtebd_zgemm(int precision, int m, int n, int k, const void* A, long long sam, long long sak,
                  int conj_a, const void* B, long long sbk, long long sbn, int conj_b, void* C,
                  long long scm, long long scn, const double* alpha, const double* beta,
                  void* workspace, size_t workspace_bytes, void* stream);
-size_t qrtebd_zgemm_workspace_size(int m, int n, int k);
+size_t qrtebd_zgemm_workspace_size(int m, int n, int k);  /* enough for every precision */
 
 /* Variant of qrtebd_zgemm that allocates nothing (the paper has no counterpart).
  * For callers that cannot call cudaMalloc around a GEMM: code recorded into a CUDA

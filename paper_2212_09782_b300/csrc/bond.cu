@@ -273,12 +273,15 @@ struct GemmRunner {
   TcWorkspace* tc;
   cx<T>* simt_scratch;
   size_t simt_scratch_elems;
+  OzWorkspace* oz = nullptr;  // complex128 with FP64 emulated on the tensor cores
   // bond: a bond-level contraction (profiled as PROF_BOND_GEMM), else a QR-internal one
   int run(const GemmArgs<T>& g, cudaStream_t st, bool bond = false) const;
 };
 
 template <>
 int GemmRunner<double>::run(const GemmArgs<double>& g, cudaStream_t st, bool bond) const {
+  if (precision == QRTEBD_C128_OZ && oz && oz_gemm_eligible(g))
+    return oz_gemm(g, *oz, st, bond ? PROF_BOND_GEMM : PROF_TC_GEMM);
   return gemm_simt<double>(g, st, simt_scratch, simt_scratch_elems,
                            bond ? PROF_BOND_GEMM : PROF_SIMT_GEMM);
 }
@@ -370,6 +373,16 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
   if (use_tc) tc_carve(ar, (int)std::max(mL, nR), (int)std::max(mL, nR), eta, tcw);
   // the QR's look-ahead updates run on a side stream with their own workspaces
   if (use_tc) tc_carve(ar, (int)std::max(mL, nR), (int)std::max(mL, nR), eta, tcw_side);
+  // complex128 on the tensor cores: slices of the larger and the smaller operand of every
+  // product (theta' = B^m B^n, when formed, is the widest: both of its sides are large)
+  const bool use_oz = std::is_same<T, double>::value && io->precision == QRTEBD_C128_OZ;
+  OzWorkspace ozw, ozw_side;
+  if (use_oz) {
+    const int mx = (int)std::max(mL, nR);
+    const int nmax = theta_given ? std::max(eta, chiL) : std::max<int>(eta, (int)std::min(mL, nR));
+    oz_carve(ar, mx, mx, nmax, ozw);
+    oz_carve(ar, mx, mx, eta, ozw_side);
+  }
   cx<T>* simt_scratch_side = simt_elems ? ar.take<cx<T>>(simt_elems) : nullptr;
 
   if (measuring) { *bytes = ar.off; return QRTEBD_OK; }
@@ -378,9 +391,10 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
     return QRTEBD_ERR_OOM;
   }
   unsigned* err = device_error_word();
-  GemmRunner<T> runner{io->precision, use_tc ? &tcw : nullptr, simt_scratch, simt_elems};
+  GemmRunner<T> runner{io->precision, use_tc ? &tcw : nullptr, simt_scratch, simt_elems, use_oz ? &ozw : nullptr};
   QrGemm<T> qg{qr_gemm_thunk<T>, &runner};
-  GemmRunner<T> runner_side{io->precision, use_tc ? &tcw_side : nullptr, simt_scratch_side, simt_elems};
+  GemmRunner<T> runner_side{io->precision, use_tc ? &tcw_side : nullptr, simt_scratch_side, simt_elems,
+                            use_oz ? &ozw_side : nullptr};
   QrGemm<T> qg_side{qr_gemm_thunk<T>, &runner_side};
   const cx<T> one = mk<T>(1, 0), zero = mk<T>(0, 0);
 
@@ -621,7 +635,8 @@ int bond_update(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t s
     if (io->xi_kind != 0 && !io->xi) return QRTEBD_ERR_INVALID_ARG;
   }
   switch (io->precision) {
-    case QRTEBD_C128: return bond_update_t<double>(io, tr, st, info, bytes);
+    case QRTEBD_C128:
+    case QRTEBD_C128_OZ: return bond_update_t<double>(io, tr, st, info, bytes);
     case QRTEBD_C64_3XTF32:
     case QRTEBD_C64_TF32:
     case QRTEBD_C64_FP32: return bond_update_t<float>(io, tr, st, info, bytes);

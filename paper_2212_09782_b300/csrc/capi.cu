@@ -137,19 +137,25 @@ int qr_entry(int precision, int m, int n, void* A, long long lda, void* Q, long 
   QrScratch<T> qs;
   qr_carve<T>(ar, m, n, qs);
   TcWorkspace tcw, tcw_side;
+  OzWorkspace ozw, ozw_side;
   const bool tc = std::is_same<T, float>::value &&
                   (precision == QRTEBD_C64_3XTF32 || precision == QRTEBD_C64_TF32);
+  const bool oz = std::is_same<T, double>::value && precision == QRTEBD_C128_OZ;
   if (tc) tc_carve(ar, std::max(m, n), m, std::max(m, n), tcw);
   if (tc) tc_carve(ar, std::max(m, n), m, std::max(m, n), tcw_side);
+  if (oz) oz_carve(ar, std::max(m, n), m, n, ozw);
+  if (oz) oz_carve(ar, std::max(m, n), m, n, ozw_side);
   if (need) { *need = ar.off; return QRTEBD_OK; }
   if (ar.overflow() || !ws) { set_last_message("qr: workspace too small"); return QRTEBD_ERR_OOM; }
-  struct Ctx { TcWorkspace* w; bool three; bool tc; };
-  Ctx ctx{&tcw, precision == QRTEBD_C64_3XTF32, tc};
-  Ctx ctx_side{&tcw_side, precision == QRTEBD_C64_3XTF32, tc};
+  struct Ctx { TcWorkspace* w; OzWorkspace* o; bool three; bool tc; bool oz; };
+  Ctx ctx{&tcw, &ozw, precision == QRTEBD_C64_3XTF32, tc, oz};
+  Ctx ctx_side{&tcw_side, &ozw_side, precision == QRTEBD_C64_3XTF32, tc, oz};
   auto fn = [](const GemmArgs<T>& g, cudaStream_t s, void* c) -> int {
     Ctx* x = static_cast<Ctx*>(c);
     if constexpr (std::is_same<T, float>::value) {
       if (x->tc && tc_gemm_eligible(g)) return tc_gemm(g, x->three, *x->w, s);
+    } else {
+      if (x->oz && oz_gemm_eligible(g)) return oz_gemm(g, *x->o, s);
     }
     return gemm_simt<T>(g, s, nullptr, 0);
   };
@@ -344,11 +350,20 @@ int qrtebd_zgemm(int precision, int m, int n, int k, const void* A, long long sa
                  void* workspace, size_t workspace_bytes, void* stream) {
   if (m < 0 || n < 0 || k < 0 || !A || !B || !C || !alpha || !beta) return QRTEBD_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (precision == QRTEBD_C128) {
+  if (prec_is_c128(precision)) {
     GemmArgs<double> g{m, n, k, static_cast<const double2*>(A), sam, sak, conj_a != 0,
                        static_cast<const double2*>(B), sbk, sbn, conj_b != 0,
                        static_cast<double2*>(C), scm, scn,
                        make_double2(alpha[0], alpha[1]), make_double2(beta[0], beta[1])};
+    if (precision == QRTEBD_C128_OZ && m > 0 && n > 0 && k > 0 && oz_gemm_eligible(g)) {
+      Arena ar;
+      ar.base = static_cast<char*>(workspace);
+      ar.cap = workspace_bytes;
+      OzWorkspace w;
+      oz_carve(ar, std::max(m, n), k, std::min(m, n), w);
+      if (ar.overflow() || !workspace) { set_last_message("zgemm: workspace too small"); return QRTEBD_ERR_OOM; }
+      return oz_gemm(g, w, st);
+    }
     return gemm_simt<double>(g, st, nullptr, 0);
   }
   GemmArgs<float> g{m, n, k, static_cast<const float2*>(A), sam, sak, conj_a != 0,
@@ -374,7 +389,11 @@ size_t qrtebd_zgemm_workspace_size(int m, int n, int k) {
   ar.measuring = true;
   TcWorkspace w;
   tc_carve(ar, std::max(m, n), k, std::max(m, n), w);
-  return ar.off;
+  Arena ao;
+  ao.measuring = true;
+  OzWorkspace ow;
+  oz_carve(ao, std::max(m, n), k, std::min(m, n), ow);
+  return std::max(ar.off, ao.off);
 }
 
 
@@ -382,16 +401,16 @@ int qrtebd_householder_qr(int precision, int m, int n, void* A, long long lda, v
                           long long ldq, void* workspace, size_t workspace_bytes, void* stream) {
   if (m < n || n < 1 || !A || !Q || lda < n || ldq < n) return QRTEBD_ERR_INVALID_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (precision == QRTEBD_C128)
+  if (prec_is_c128(precision))
     return qr_entry<double>(precision, m, n, A, lda, Q, ldq, workspace, workspace_bytes, st, nullptr);
-  if (precision < QRTEBD_C128 || precision > QRTEBD_C64_FP32) return QRTEBD_ERR_INVALID_ARG;
+  if (!prec_valid(precision)) return QRTEBD_ERR_INVALID_ARG;
   return qr_entry<float>(precision, m, n, A, lda, Q, ldq, workspace, workspace_bytes, st, nullptr);
 }
 
 size_t qrtebd_qr_workspace_size(int precision, int m, int n) {
   size_t need = 0;
   if (m < n || n < 1) return 0;
-  if (precision == QRTEBD_C128)
+  if (prec_is_c128(precision))
     qr_entry<double>(precision, m, n, nullptr, n, nullptr, n, nullptr, 0, nullptr, &need);
   else
     qr_entry<float>(precision, m, n, nullptr, n, nullptr, n, nullptr, 0, nullptr, &need);
@@ -400,7 +419,7 @@ size_t qrtebd_qr_workspace_size(int precision, int m, int n) {
 
 size_t qrtebd_cbe_decompose_workspace_size(int precision, int n) {
   if (n < 1) return 0;
-  if (precision == QRTEBD_C128)
+  if (prec_is_c128(precision))
     return (2 * (size_t)n * n + herm_eig_scratch_elems(n)) * sizeof(double2) +
            gemm_simt_scratch_elems(n, n, n, 1) * sizeof(double2) + 1024;
   return svd32_work_bytes(n);
@@ -409,11 +428,11 @@ size_t qrtebd_cbe_decompose_workspace_size(int precision, int n) {
 int qrtebd_cbe_decompose(int precision, int n, const void* Rz, long long ldr, double* w, void* Vh,
                          void* workspace, size_t workspace_bytes, int* sweeps, void* stream) {
   if (n < 1 || ldr < n || !Rz || !w || !Vh || !workspace) return QRTEBD_ERR_INVALID_ARG;
-  if (precision < QRTEBD_C128 || precision > QRTEBD_C64_FP32) return QRTEBD_ERR_INVALID_ARG;
+  if (!prec_valid(precision)) return QRTEBD_ERR_INVALID_ARG;
   if (workspace_bytes < qrtebd_cbe_decompose_workspace_size(precision, n)) return QRTEBD_ERR_OOM;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   unsigned* err = device_error_word();
-  if (precision != QRTEBD_C128)
+  if (!prec_is_c128(precision))
     return svd_rows_jacobi32(static_cast<const float2*>(Rz), ldr, n, w, static_cast<double2*>(Vh),
                              workspace, workspace_bytes, st, err, sweeps);
   // complex128: M = Rz Rz^dag (FP64), two-sided Jacobi

@@ -172,6 +172,10 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, un
   return s_ok != 0;
 }
 
+// complex128 storage (FP64 arithmetic, or FP64 emulated on the tensor cores)
+inline bool prec_is_c128(int p) { return p == QRTEBD_C128 || p == QRTEBD_C128_OZ; }
+inline bool prec_valid(int p) { return p >= QRTEBD_C128 && p <= QRTEBD_C128_OZ; }
+
 __host__ __device__ __forceinline__ long long ceil_div(long long a, long long b) {
   return (a + b - 1) / b;
 }

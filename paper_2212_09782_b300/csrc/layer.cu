@@ -264,7 +264,7 @@ int qrtebd_mps_set_site(qrtebd_mps* s, int site, const double* B_host, int chi_l
   const int bl = site, br = s->infinite ? (site + 1) % s->L : site + 1;
   if (chi_l < 1 || chi_r < 1 || chi_l > s->cap[bl] || chi_r > s->cap[br]) return QRTEBD_ERR_INVALID_ARG;
   const size_t n = (size_t)chi_l * s->d * chi_r;
-  if (s->precision == QRTEBD_C128) {
+  if (prec_is_c128(s->precision)) {
     QR_CUDA_TRY(cudaMemcpyAsync(s->B[site], B_host, n * sizeof(double2), cudaMemcpyHostToDevice, s->st));
   } else {
     std::vector<float2> h(n);
@@ -288,7 +288,7 @@ int qrtebd_mps_set_bond(qrtebd_mps* s, int bond, const double* xi_host, int chi,
     std::memcpy(dense.data(), xi_host, 2 * n * sizeof(double));
   }
   auto put = [&](void* dst, const double* src, size_t cnt) -> int {
-    if (s->precision == QRTEBD_C128) {
+    if (prec_is_c128(s->precision)) {
       QR_CUDA_TRY(cudaMemcpyAsync(dst, src, cnt * sizeof(double2), cudaMemcpyHostToDevice, s->st));
     } else {
       std::vector<float2> h(cnt);

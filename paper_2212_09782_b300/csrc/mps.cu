@@ -350,7 +350,7 @@ int mps_bond_ws_need(const qrtebd_mps* s, int m, const qrtebd_trunc* tr, size_t*
 
 int mps_update_bond(qrtebd_mps* s, int m, const qrtebd_trunc* tr, cudaStream_t st, void* ws,
                     size_t ws_bytes) {
-  return s->precision == QRTEBD_C128 ? update_bond_t<double>(s, m, tr, st, ws, ws_bytes)
+  return prec_is_c128(s->precision) ? update_bond_t<double>(s, m, tr, st, ws, ws_bytes)
                                      : update_bond_t<float>(s, m, tr, st, ws, ws_bytes);
 }
 
@@ -365,15 +365,15 @@ int qrtebd_mps_create(const qrtebd_mps_desc* desc, void* stream, qrtebd_mps** ou
   *out = nullptr;
   if (desc->d < 2 || desc->d > 8 || desc->chi_max < 1 || desc->L < 2) return QRTEBD_ERR_INVALID_ARG;
   if (desc->infinite && (desc->L % 2)) return QRTEBD_ERR_INVALID_ARG;
-  if (desc->precision < QRTEBD_C128 || desc->precision > QRTEBD_C64_FP32) return QRTEBD_ERR_INVALID_ARG;
+  if (!prec_valid(desc->precision)) return QRTEBD_ERR_INVALID_ARG;
   qrtebd_mps* s = new qrtebd_mps();
   s->L = desc->L; s->d = desc->d; s->infinite = desc->infinite ? 1 : 0;
   s->chi_max = desc->chi_max; s->precision = desc->precision;
   s->st = static_cast<cudaStream_t>(stream);
-  s->esz = desc->precision == QRTEBD_C128 ? sizeof(double2) : sizeof(float2);
+  s->esz = prec_is_c128(desc->precision) ? sizeof(double2) : sizeof(float2);
   int rc = allocate(s);
   if (rc == QRTEBD_OK)
-    rc = desc->precision == QRTEBD_C128 ? init_product<double>(s, desc->product_state)
+    rc = prec_is_c128(desc->precision) ? init_product<double>(s, desc->product_state)
                                         : init_product<float>(s, desc->product_state);
   if (rc != QRTEBD_OK) { free_all(s); delete s; return rc; }
   *out = s;
@@ -401,13 +401,13 @@ int qrtebd_apply_gate_layer(qrtebd_mps* s, int parity, const double* gates_host,
     double* const eps[1] = {eps_out};
     return qrtebd_apply_gate_layer_batched(states, 1, parity, gates, tr, eps);
   }
-  return s->precision == QRTEBD_C128 ? apply_layer_t<double>(s, parity, gates_host, tr, eps_out)
+  return prec_is_c128(s->precision) ? apply_layer_t<double>(s, parity, gates_host, tr, eps_out)
                                      : apply_layer_t<float>(s, parity, gates_host, tr, eps_out);
 }
 
 int qrtebd_expectation(qrtebd_mps* s, int site, int nsites, const double* op_host, double* out) {
   if (!s || !op_host || !out) return QRTEBD_ERR_INVALID_ARG;
-  return s->precision == QRTEBD_C128 ? expectation_t<double>(s, site, nsites, op_host, out)
+  return prec_is_c128(s->precision) ? expectation_t<double>(s, site, nsites, op_host, out)
                                      : expectation_t<float>(s, site, nsites, op_host, out);
 }
 
@@ -429,7 +429,7 @@ int qrtebd_truncation_error(qrtebd_mps* s, int bond, double* out) {
 
 int qrtebd_schmidt(qrtebd_mps* s, int bond, double* S, int capacity, int* n) {
   if (!s || !S || !n || bond < 0 || bond >= (s->infinite ? s->L : s->L + 1)) return QRTEBD_ERR_INVALID_ARG;
-  return s->precision == QRTEBD_C128 ? schmidt_t<double>(s, bond, S, capacity, n)
+  return prec_is_c128(s->precision) ? schmidt_t<double>(s, bond, S, capacity, n)
                                      : schmidt_t<float>(s, bond, S, capacity, n);
 }
 
@@ -500,7 +500,7 @@ int qrtebd_mps_load(const char* path, void* stream, qrtebd_mps** out) {
   if (fread(hdr, sizeof hdr, 1, f) != 1 || hdr[0] != (int)kMagic) return reject("mps_load: not a qrtebd checkpoint");
   const int L = hdr[1], d = hdr[2], inf = hdr[3], chi_max = hdr[4], prec = hdr[5];
   if (d < 2 || d > 8 || chi_max < 1 || L < 2 || L > (1 << 20) || (inf != 0 && inf != 1) || (inf && L % 2) ||
-      prec < QRTEBD_C128 || prec > QRTEBD_C64_FP32)
+      !prec_valid(prec))
     return reject("mps_load: corrupt header");
   // Everything is checked on the host before any device memory is taken: the bond
   // dimensions against the capacities mps_create gives, and the file length against
@@ -510,7 +510,7 @@ int qrtebd_mps_load(const char* path, void* stream, qrtebd_mps** out) {
   std::vector<char> diag(nb);
   if (fread(chi.data(), sizeof(int), nb, f) != (size_t)nb || fread(diag.data(), 1, nb, f) != (size_t)nb)
     return reject("mps_load: truncated or corrupt file");
-  const size_t esz = prec == QRTEBD_C128 ? sizeof(double2) : sizeof(float2);
+  const size_t esz = prec_is_c128(prec) ? sizeof(double2) : sizeof(float2);
   size_t body = (size_t)nb * sizeof(double);
   for (int b = 0; b < nb; ++b) {
     const long long cap = inf ? chi_max

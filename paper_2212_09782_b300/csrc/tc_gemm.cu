@@ -129,6 +129,15 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
         "=r"(r[31])                                                                          \
       : "r"(taddr))
 
+#define TMEM_LD16(taddr, r)                                                                  \
+  asm volatile(                                                                              \
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13," \
+      "%14,%15}, [%16];"                                                                     \
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),  \
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),          \
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])                                                \
+      : "r"(taddr))
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(s_u32(b)) : "memory");
 }
@@ -476,6 +485,320 @@ __global__ void k_prep(PrepJob a, PrepJob b, int three) {
     prep_b_tile(j.src, j.s0, j.s1, j.conj, j.K, j.rows, j.hi, j.lo, j.ld, three, blockIdx.x, blockIdx.y, t);
 }
 
+// ------------------------------------------------------------------ FP64 emulation
+// Operand preparation in two passes. Pass 1: the power-of-two exponent E of every row of A'
+// (over Re and Im of opA(m, :)) and of every complex column n of opB, E = frexp exponent of
+// the largest magnitude, so that |x| 2^-E < 1 (zero rows keep a sentinel below every real
+// exponent). Pass 2: the slices d_p = rint(t 2^OZ_BITS), t <- t 2^OZ_BITS - d_p, exact in
+// FP64 and in TF32 (|d_p| <= 2^OZ_BITS), written as A'_p / B'^T_p rows in the layout of the
+// complex64 path (interleaved Re, Im; the 2 x 2 real embedding for B).
+constexpr int OZ_SENT = -(1 << 30);
+
+__device__ __forceinline__ int oz_exp_of(double x) {
+  int e = 0;
+  (void)frexp(x, &e);
+  return x > 0.0 ? e : OZ_SENT;
+}
+
+struct OzJob {
+  const double2* src; long long s0, s1; int conj, rows, K;  // rows: M (A) or N (B)
+  int* e; float* out; long long slice_stride; int ld;
+  int gx, gy;  // tiles along K and along rows
+  int is_b;
+};
+
+// pass 1: one 32 x 32 tile; the warps reduce its rows' maxima, one atomic per row and tile
+__global__ void k_oz_exp(OzJob a, OzJob b) {
+  __shared__ double t[32][33];
+  pdl_launch_dependents();
+  pdl_wait();
+  const OzJob& j = blockIdx.z == 0 ? a : b;
+  if ((int)blockIdx.x >= j.gx || (int)blockIdx.y >= j.gy) return;
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  // A: element (row m, k) at m s0 + k s1; B: (row n, k) at k s0 + n s1
+  const long long srow = j.is_b ? j.s1 : j.s0, sk = j.is_b ? j.s0 : j.s1;
+  const bool kc = (sk == 1);
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int rr = kc ? r : threadIdx.x, kk = kc ? threadIdx.x : r;
+    const int row = r0 + rr, k = k0 + kk;
+    double v = 0.0;
+    if (row < j.rows && k < j.K) {
+      const double2 x = j.src[row * srow + k * sk];
+      v = fmax(fabs(x.x), fabs(x.y));
+    }
+    t[rr][kk] = v;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    double v = t[r][threadIdx.x];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0 && r0 + r < j.rows && v > 0.0) atomicMax(j.e + r0 + r, oz_exp_of(v));
+  }
+}
+
+// pass 2: slices of one 32 x 32 tile, stores coalesced along K
+__global__ void k_oz_slice(OzJob a, OzJob b) {
+  __shared__ double2 t[32][33];
+  pdl_launch_dependents();
+  pdl_wait();
+  const OzJob& j = blockIdx.z == 0 ? a : b;
+  if ((int)blockIdx.x >= j.gx || (int)blockIdx.y >= j.gy) return;
+  const int r0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+  const long long srow = j.is_b ? j.s1 : j.s0, sk = j.is_b ? j.s0 : j.s1;
+  const bool kc = (sk == 1);
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int rr = kc ? r : threadIdx.x, kk = kc ? threadIdx.x : r;
+    const int row = r0 + rr, k = k0 + kk;
+    double2 v = make_double2(0.0, 0.0);
+    if (row < j.rows && k < j.K) v = j.src[row * srow + k * sk];
+    if (j.conj) v.y = -v.y;
+    t[rr][kk] = v;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+    const int row = r0 + r, k = k0 + threadIdx.x;
+    if (row >= j.rows || k >= j.K) continue;
+    const int e = j.e[row];
+    const double2 v = t[r][threadIdx.x];
+    double tr = e == OZ_SENT ? 0.0 : ldexp(v.x, -e), ti = e == OZ_SENT ? 0.0 : ldexp(v.y, -e);
+#pragma unroll
+    for (int p = 0; p < OZ_SLICES; ++p) {
+      tr *= (double)(1 << OZ_BITS);
+      ti *= (double)(1 << OZ_BITS);
+      const double dr = rint(tr), di = rint(ti);
+      tr -= dr;
+      ti -= di;
+      float* o = j.out + (long long)p * j.slice_stride;
+      if (!j.is_b) {
+        *reinterpret_cast<float2*>(o + (long long)row * j.ld + 2 * k) = make_float2((float)dr, (float)di);
+      } else {
+        const long long o0 = (long long)(2 * row) * j.ld + 2 * k;
+        *reinterpret_cast<float2*>(o + o0) = make_float2((float)dr, (float)-di);
+        *reinterpret_cast<float2*>(o + o0 + j.ld) = make_float2((float)di, (float)dr);
+      }
+    }
+  }
+}
+
+struct OzEpi {
+  double2* C; long long scm, scn;
+  double2 alpha, beta;
+  int M, Nc;
+  const int* ea; const int* eb;
+};
+struct OzPairs { int n; signed char p[64], q[64]; };
+
+// The GEMM: one 128 x 128 real output tile per CTA, the K loop run once per slice pair
+// (A'_p against B'^T_q, fetched by TMA from the stacked slices), the same roles as k_tc_gemm
+// (warp 0 TMA, warp 1 TMEM and MMA; here sixteen epilogue warps 2..17). A chunk (CHUNK stages, 128 real K
+// terms) never straddles two pairs: its exact FP32 sum is added into FP64 registers with the
+// pair's weight, and the rows' and columns' exponents are applied at the end.
+constexpr int OZ_BN = 128;
+constexpr int OZ_B_TILE = OZ_BN * BK * 4;
+constexpr int OZ_STAGE = A_TILE + OZ_B_TILE;
+constexpr int OZ_STAGES = (192 * 1024) / OZ_STAGE;
+constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024 + 256;
+constexpr uint32_t OZ_IDESC = Cfg<false, OZ_BN>::IDESC;
+constexpr int OZ_CHUNK = 32;                 // stages per exact FP32 chunk: 32 x 32 = 1024 real K terms
+constexpr int OZ_NEPI = 16;                  // epilogue warps: four lane quarters x four column quarters
+constexpr int OZ_NT = 64 + 32 * OZ_NEPI;
+
+__global__ void __launch_bounds__(OZ_NT, 1)
+    k_oz_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, OzEpi epi,
+              int Kp, int a_rows, int b_rows, OzPairs pr, unsigned* err) {
+  static_assert(BM * (OZ_BN / 2 + 1) * 16 <= OZ_STAGES * OZ_STAGE, "staged epilogue tile");
+  constexpr int HW = OZ_BN / 4;  // real columns per epilogue thread (four column quarters)
+  pdl_launch_dependents();
+  pdl_wait();
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024 - (s_u32(smem_raw) & 1023)) & 1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + OZ_STAGES * OZ_STAGE);
+  uint64_t* empty = full + OZ_STAGES;
+  uint64_t* accf = empty + OZ_STAGES;
+  uint64_t* acce = accf + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * OZ_BN, m0 = blockIdx.y * BM;
+  const int nk = (Kp + BK - 1) / BK;
+  const int cpp = (nk + OZ_CHUNK - 1) / OZ_CHUNK;  // chunks per pair
+  const int npairs = pr.n;
+  const int total = npairs * nk;
+  const int nchunks = npairs * cpp;
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < OZ_STAGES; ++st) { mbar_init(&full[st], 1); mbar_init(&empty[st], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], OZ_NEPI); }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_u32(tmem_slot)),
+                 "r"(2 * OZ_BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  auto stage_a = [&](int st) { return smem + st * OZ_STAGE; };
+  auto stage_b = [&](int st) { return smem + st * OZ_STAGE + A_TILE; };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      bool ok = true;
+      int issued = 0;
+      for (int it = 0; it < total && ok; ++it) {
+        const int st = it % OZ_STAGES;
+        const uint32_t ph = (uint32_t)((it / OZ_STAGES) & 1);
+        if (!mbar_wait(&empty[st], ph ^ 1u)) { ok = false; break; }
+        const int p = it / nk, i = it % nk;
+        mbar_expect_tx(&full[st], OZ_STAGE);
+        tma_load(stage_a(st), &tA, &full[st], i * BK, pr.p[p] * a_rows + m0);
+        tma_load(stage_b(st), &tB, &full[st], i * BK, pr.q[p] * b_rows + n0);
+        ++issued;
+      }
+      if (!ok) atomicOr(err, DEVERR_TIMEOUT);
+      for (int it = (issued > OZ_STAGES ? issued - OZ_STAGES : 0); it < issued; ++it) {
+        if (!mbar_wait(&full[it % OZ_STAGES], (uint32_t)((it / OZ_STAGES) & 1))) {
+          atomicOr(err, DEVERR_TIMEOUT);
+          break;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      bool ok = true;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int b = c & 1;
+        if (c >= 2 && !mbar_wait(&acce[b], (uint32_t)(((c >> 1) - 1) & 1))) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t acc_t = tmem + (uint32_t)(b * OZ_BN);
+        const int p = c / cpp, kc = c % cpp;
+        const int i0 = kc * OZ_CHUNK, i1 = min(nk, i0 + OZ_CHUNK);
+        for (int i = i0; i < i1; ++i) {
+          const int it = p * nk + i;
+          const int st = it % OZ_STAGES;
+          if (!mbar_wait(&full[st], (uint32_t)((it / OZ_STAGES) & 1))) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a0 = s_u32(stage_a(st)), b0 = s_u32(stage_b(st));
+#pragma unroll
+          for (int k = 0; k < BK / 8; ++k) {
+            const uint32_t off = k * 32;
+            tc_mma(acc_t, desc_sw128(a0 + off), desc_sw128(b0 + off), OZ_IDESC, (i > i0 || k > 0) ? 1u : 0u);
+          }
+          tc_commit(&empty[st]);
+        }
+        tc_commit(&accf[b]);
+      }
+      if (!ok) atomicOr(err, DEVERR_TIMEOUT);
+    }
+  } else {
+    const int q = warp & 3;
+    const int h = (warp - 2) >> 2;  // column quarter
+    const int row = m0 + q * 32 + lane;
+    // Each chunk is an exact integer of at most 2^24 in magnitude, added into FP64 registers
+    // with its pair's power-of-two weight (one DFMA per element and chunk of 1024 K terms).
+    double acc[HW];
+#pragma unroll
+    for (int jj = 0; jj < HW; ++jj) acc[jj] = 0.0;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int b = c & 1;
+      if (!mbar_wait(&accf[b], (uint32_t)((c >> 1) & 1))) { ok = false; break; }
+      tc_fence_after();
+      const int p = c / cpp;
+      const double w = ldexp(1.0, -OZ_BITS * (pr.p[p] + pr.q[p] + 2));
+#pragma unroll
+      for (int blk = 0; blk < HW / 16; ++blk) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * OZ_BN + h * HW + blk * 16);
+        TMEM_LD16(taddr, r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int jj = 0; jj < 16; ++jj) acc[blk * 16 + jj] = fma((double)__uint_as_float(r[jj]), w, acc[blk * 16 + jj]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[b]);
+    }
+    if (!ok && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
+    auto sum = [&](int jj) { return acc[jj]; };
+    const bool use_beta = (epi.beta.x != 0.0 || epi.beta.y != 0.0);
+    const int ea = (row < epi.M) ? epi.ea[row] : OZ_SENT;
+    if (epi.scn == 1) {
+      // stage the tile (complex128 results, row exponents applied) in the idle pipeline
+      // buffers, then each warp writes whole row segments
+      constexpr int LDT = OZ_BN / 2 + 1;  // complex values per staged row (odd: no bank conflicts)
+      double2* tile = reinterpret_cast<double2*>(smem);
+      if (ok) {
+        double2* trow = tile + (q * 32 + lane) * LDT + h * (HW / 2);
+#pragma unroll
+        for (int jj = 0; jj < HW / 2; ++jj)
+          trow[jj] = ea == OZ_SENT ? make_double2(0.0, 0.0)
+                                   : make_double2(ldexp(sum(2 * jj), ea), ldexp(sum(2 * jj + 1), ea));
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * OZ_NEPI) : "memory");
+      if (ok) {
+        for (int r = warp - 2; r < BM; r += OZ_NEPI) {
+          const int grow = m0 + r;
+          if (grow >= epi.M) break;
+          const double2* tr = tile + r * LDT;
+          double2* crow = epi.C + (long long)grow * epi.scm;
+          for (int cc = lane; cc < OZ_BN / 2; cc += 32) {
+            const int n = n0 / 2 + cc;
+            if (n < epi.Nc) {
+              const int eb = epi.eb[n];
+              const double2 a = eb == OZ_SENT ? make_double2(0.0, 0.0)
+                                              : make_double2(ldexp(tr[cc].x, eb), ldexp(tr[cc].y, eb));
+              double2 v;
+              v.x = epi.alpha.x * a.x - epi.alpha.y * a.y;
+              v.y = epi.alpha.x * a.y + epi.alpha.y * a.x;
+              if (use_beta) {
+                const double2 cv = crow[n];
+                v.x += epi.beta.x * cv.x - epi.beta.y * cv.y;
+                v.y += epi.beta.x * cv.y + epi.beta.y * cv.x;
+              }
+              crow[n] = v;
+            }
+          }
+        }
+      }
+    } else if (ok && row < epi.M) {
+      const int col0 = n0 + h * HW;
+      double2* crow = epi.C + (long long)row * epi.scm;
+#pragma unroll
+      for (int jj = 0; jj < HW / 2; ++jj) {
+        const int n = (col0 >> 1) + jj;
+        if (n < epi.Nc) {
+          const int eb = epi.eb[n];
+          const bool z = (ea == OZ_SENT || eb == OZ_SENT);
+          const double ar = z ? 0.0 : ldexp(sum(2 * jj), ea + eb), ai = z ? 0.0 : ldexp(sum(2 * jj + 1), ea + eb);
+          double2 v;
+          v.x = epi.alpha.x * ar - epi.alpha.y * ai;
+          v.y = epi.alpha.x * ai + epi.alpha.y * ar;
+          double2* pp = crow + (long long)n * epi.scn;
+          if (use_beta) {
+            const double2 cv = *pp;
+            v.x += epi.beta.x * cv.x - epi.beta.y * cv.y;
+            v.y += epi.beta.x * cv.y + epi.beta.y * cv.x;
+          }
+          *pp = v;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    if (nchunks > 0) {
+      const int c = nchunks - 1;
+      if (!mbar_wait(&accf[c & 1], (uint32_t)((c >> 1) & 1)) && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
+    }
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * OZ_BN) : "memory");
+  }
+}
+
 // ------------------------------------------------------------------ host
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::once_flag g_encode_once;
@@ -710,6 +1033,82 @@ __global__ void k_fill_test(float2* x, long long n, unsigned seed) {
   x[i] = make_float2((float)(h & 0xffff) / 32768.f - 1.f, (float)(h >> 16) / 32768.f - 1.f);
 }
 }  // namespace
+
+void oz_carve(Arena& ar, int max_m, int max_k, int max_n, OzWorkspace& w) {
+  const size_t ld = (size_t)ld_for(max_k);
+  w.a_cap = (size_t)OZ_SLICES * max_m * ld;
+  w.b_cap = (size_t)OZ_SLICES * 2 * max_n * ld;
+  w.ea_cap = (size_t)max_m;
+  w.eb_cap = (size_t)max_n;
+  w.a = ar.take<float>(w.a_cap);
+  w.b = ar.take<float>(w.b_cap);
+  w.ea = ar.take<int>(w.ea_cap);
+  w.eb = ar.take<int>(w.eb_cap);
+}
+
+bool oz_gemm_eligible(const GemmArgs<double>& g) {
+  // enough 128 x 128 tiles to fill the GPU (no split-K in this form) and K >= 64; smaller
+  // products stay on the FP64 CUDA cores
+  const long long mm = std::max(g.M, g.N), nn = std::min(g.M, g.N);
+  return g.batch == 1 && g.K >= 64 && ceil_div(mm, BM) * ceil_div(2 * nn, OZ_BN) >= 64;
+}
+
+int oz_gemm(const GemmArgs<double>& g0, OzWorkspace& w, cudaStream_t st, int prof_family) {
+  // as the complex64 path: C = A B with N > M runs as C^T = B^T A^T
+  GemmArgs<double> g = g0;
+  if (g0.N > g0.M) {
+    g.M = g0.N; g.N = g0.M;
+    g.A = g0.B; g.sam = g0.sbn; g.sak = g0.sbk; g.conj_a = g0.conj_b;
+    g.B = g0.A; g.sbk = g0.sak; g.sbn = g0.sam; g.conj_b = g0.conj_a;
+    g.scm = g0.scn; g.scn = g0.scm;
+  }
+  const int M = g.M, N = g.N, K = g.K;
+  if (M <= 0 || N <= 0) return QRTEBD_OK;
+  const int ld = ld_for(K);
+  if (K <= 0 || (size_t)OZ_SLICES * M * ld > w.a_cap || (size_t)OZ_SLICES * 2 * N * ld > w.b_cap ||
+      (size_t)M > w.ea_cap || (size_t)N > w.eb_cap || !w.a || !w.b)
+    return gemm_simt<double>(g0, st, nullptr, 0, prof_family == PROF_TC_GEMM ? PROF_SIMT_GEMM : prof_family);
+  QR_TRY(get_encode());
+  // exponents (memset 0x80 bytes: a sentinel below every exponent), then the slices
+  QR_CUDA_TRY(cudaMemsetAsync(w.ea, 0x80, (size_t)M * sizeof(int), st));
+  QR_CUDA_TRY(cudaMemsetAsync(w.eb, 0x80, (size_t)N * sizeof(int), st));
+  OzJob ja{g.A, g.sam, g.sak, g.conj_a ? 1 : 0, M, K, w.ea, w.a, (long long)M * ld, ld,
+           (int)ceil_div(K, 32), (int)ceil_div(M, 32), 0};
+  OzJob jb{g.B, g.sbk, g.sbn, g.conj_b ? 1 : 0, N, K, w.eb, w.b, (long long)2 * N * ld, ld,
+           (int)ceil_div(K, 32), (int)ceil_div(N, 32), 1};
+  {
+    dim3 grid((unsigned)std::max(ja.gx, jb.gx), (unsigned)std::max(ja.gy, jb.gy), 2);
+    ProfScope prof(PROF_PREP, st, 0, 16.0 * (M + N) * (double)K * 2 + 4.0 * OZ_SLICES * 2 * K * ((double)M + 2.0 * N));
+    QR_CUDA_TRY(launch_pdl(k_oz_exp, grid, dim3(32, 8), 0, st, ja, jb));
+    note_launch();
+    QR_CUDA_TRY(launch_pdl(k_oz_slice, grid, dim3(32, 8), 0, st, ja, jb));
+    note_launch();
+  }
+  // the slices of every operand stacked as one tensor: slice p's rows start at p * rows
+  CUtensorMap ta, tb;
+  QR_TRY(make_map(&ta, w.a, OZ_SLICES * M, 2 * K, ld, BM));
+  QR_TRY(make_map(&tb, w.b, OZ_SLICES * 2 * N, 2 * K, ld, OZ_BN));
+  OzPairs pr{};
+  for (int p = 0; p < OZ_SLICES; ++p)
+    for (int q = 0; q < OZ_SLICES; ++q)
+      if (p + q <= OZ_SLICES - 1) { pr.p[pr.n] = (signed char)p; pr.q[pr.n] = (signed char)q; ++pr.n; }
+  OzEpi epi{g.C, g.scm, g.scn, make_double2(g.alpha.x, g.alpha.y), make_double2(g.beta.x, g.beta.y), M, N,
+            w.ea, w.eb};
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(once, [] { attr_err = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM); });
+  QR_CUDA_TRY(attr_err);
+  dim3 grid((unsigned)ceil_div(2LL * N, OZ_BN), (unsigned)ceil_div(M, BM), 1);
+  {
+    // algorithmic work: the complex product (8 M N K real flops), as for every GEMM family
+    ProfScope prof(prof_family, st, 8.0 * M * N * K);
+    QR_CUDA_TRY(launch_pdl(k_oz_gemm, grid, dim3(OZ_NT), OZ_SMEM, st, ta, tb, epi, 2 * K, M, 2 * N, pr,
+                           device_error_word()));
+    note_launch();
+    QR_CUDA_TRY(cudaGetLastError());
+  }
+  return QRTEBD_OK;
+}
 
 void tc_record_begin() {
   std::lock_guard<std::mutex> lk(g_tune_mu);

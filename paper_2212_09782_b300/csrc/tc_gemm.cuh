@@ -47,6 +47,30 @@ int tc_gemm(const GemmArgs<float>& g, bool three, TcWorkspace& w, cudaStream_t s
 // Invalidate cached prepared operands (call when their sources may change).
 void tc_invalidate(TcWorkspace& w);
 
+// ---- complex128 GEMM by FP64 emulation on the TF32 tensor cores (Ozaki splitting)
+// Every row of A' (and of the embedded B'^T) is scaled by a power of two to |x| < 1 and cut
+// into OZ_SLICES integer slices of OZ_BITS bits, x 2^-E = sum_p d_p 2^(-OZ_BITS (p+1)) with
+// |d_p| <= 2^OZ_BITS, each exactly representable in TF32. A slice product summed over 1024 K
+// terms stays within 2^24, so the tensor core's FP32 accumulation is exact; every such chunk
+// is added into FP64 registers with its weight 2^(-OZ_BITS (p+q+2)), over the slice pairs
+// p + q <= OZ_SLICES - 1 (0-based). Truncation error ~2^-56 of |A||B| per K term, below the
+// complex128 rounding of the result.
+constexpr int OZ_SLICES = 8;
+constexpr int OZ_BITS = 7;
+struct OzWorkspace {
+  float* a = nullptr;  // OZ_SLICES x max_m rows x ld floats
+  float* b = nullptr;  // OZ_SLICES x 2 max_n rows x ld floats
+  int* ea = nullptr;   // per row of A' (max_m)
+  int* eb = nullptr;   // per complex column of opB (max_n)
+  size_t a_cap = 0, b_cap = 0, ea_cap = 0, eb_cap = 0;
+};
+void oz_carve(Arena& ar, int max_m, int max_k, int max_n, OzWorkspace& w);
+// Shapes worth (and able to be) run on the tensor cores in emulated FP64.
+bool oz_gemm_eligible(const GemmArgs<double>& g);
+// C = alpha opA opB + beta C (complex128) on the tensor cores; falls back to the FP64
+// CUDA-core GEMM when the slices would not fit the workspace.
+int oz_gemm(const GemmArgs<double>& g, OzWorkspace& w, cudaStream_t st, int prof_family = PROF_TC_GEMM);
+
 // ---- launch configurations and the autotuner's table
 // A product's shape as the kernel sees it (after the N > M swap): M >= N.
 struct TcShape {

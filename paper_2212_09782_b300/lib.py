@@ -14,9 +14,16 @@ LIB_PATH = os.path.join(_HERE, "libqrtebd.so")
 
 OK = 0
 ERR_INVALID_ARG, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_NUMERIC, ERR_NOT_ADMITTED = -1, -2, -3, -4, -5, -6
-C128, C64_3XTF32, C64_TF32, C64_FP32 = 0, 1, 2, 3
+C128, C64_3XTF32, C64_TF32, C64_FP32, C128_OZ = 0, 1, 2, 3, 4
 PLAIN, CBE = 0, 1
-PRECISIONS = {"c128": C128, "c64_3xtf32": C64_3XTF32, "c64_tf32": C64_TF32, "c64_fp32": C64_FP32}
+PRECISIONS = {"c128": C128, "c64_3xtf32": C64_3XTF32, "c64_tf32": C64_TF32, "c64_fp32": C64_FP32,
+              "c128_oz": C128_OZ}
+
+
+def is_c128(precision):
+    """complex128 storage (FP64 arithmetic, or FP64 emulated on the tensor cores)."""
+    p = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
+    return p in (C128, C128_OZ)
 
 
 class Trunc(C.Structure):
@@ -164,7 +171,7 @@ def stream_handle(stream=None):
 class BondUpdater:
     """Holds the workspace and output buffers for repeated updates of one shape.
 
-    Inputs are torch CUDA tensors of the precision's dtype (complex128 for c128,
+    Inputs are torch CUDA tensors of the precision's dtype (complex128 for c128 / c128_oz,
     complex64 otherwise); ``gate`` is a complex128 CUDA tensor (d^2, d^2).
     """
 
@@ -173,7 +180,7 @@ class BondUpdater:
         import torch
         self.torch = torch
         self.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
-        self.dtype = torch.complex128 if self.precision == C128 else torch.complex64
+        self.dtype = torch.complex128 if is_c128(self.precision) else torch.complex64
         self.dims = (chi_l, d, chi_m, chi_r)
         self.trunc = trunc
         self.xi_kind = xi_kind
@@ -296,7 +303,7 @@ def zgemm(precision, A, B, conj_a=False, conj_b=False, trans_a=False, trans_b=Fa
         C_out = torch.zeros(m, n, dtype=A.dtype, device=A.device)
     ws = None
     nb = 0
-    if prec in (C64_3XTF32, C64_TF32):
+    if prec in (C64_3XTF32, C64_TF32, C128_OZ):
         nb = _lib.qrtebd_zgemm_workspace_size(m, n, k)
         ws = torch.empty(nb, dtype=torch.uint8, device=A.device)
     al = (C.c_double * 2)(complex(alpha).real, complex(alpha).imag)

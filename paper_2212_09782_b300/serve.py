@@ -54,7 +54,7 @@ def chain_caps(Lc, d, chi_max):
 
 def state_bytes(req, precision):
     """Device bytes of one resident state at its bond-dimension caps."""
-    esz = 16 if L.PRECISIONS.get(precision, precision) == L.C128 else 8
+    esz = 16 if L.is_c128(precision) else 8
     caps = chain_caps(req.L, req.d, req.chi_max)
     sites = sum(caps[m] * req.d * caps[m + 1] for m in range(req.L))
     bonds = sum(c * c + c for c in caps)

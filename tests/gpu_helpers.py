@@ -4,12 +4,12 @@ import numpy as np
 
 # 1xTF32 (10-bit products) is outside the 1e-5 bar: measured against the oracle at
 # chi ~ 100-250, d = 3-4: Schmidt values ~4e-5, eps ~1e-4, projector-type invariants ~2e-3
-TOL = {"c128": 1e-10, "c64_3xtf32": 1e-5, "c64_fp32": 1e-5, "c64_tf32": 5e-3}
+TOL = {"c128": 1e-10, "c128_oz": 1e-10, "c64_3xtf32": 1e-5, "c64_fp32": 1e-5, "c64_tf32": 5e-3}
 
 # Unit perturbation of the bond matrix that the arithmetic leaves (relative to its norm):
 # complex64 stores X, Q, Y and L in FP32 (unit roundoff 6e-8) between FP32-accumulated
 # products; complex128 stores them in FP64.
-PERTURB = {"c128": 1e-15, "c64_3xtf32": 1e-7, "c64_fp32": 1e-7, "c64_tf32": 1e-7}
+PERTURB = {"c128": 1e-15, "c128_oz": 1e-14, "c64_3xtf32": 1e-7, "c64_fp32": 1e-7, "c64_tf32": 1e-7}
 
 
 def subspace_tol(tol, prec, S, c):
@@ -25,7 +25,7 @@ def subspace_tol(tol, prec, S, c):
 
 def to_dev(a, prec):
     import torch
-    dt = torch.complex128 if prec == "c128" else torch.complex64
+    dt = torch.complex128 if prec.startswith("c128") else torch.complex64
     return torch.from_numpy(np.ascontiguousarray(a)).to(dtype=dt, device="cuda")
 
 
@@ -35,7 +35,7 @@ def host(a):
 
 def rounded(a, prec):
     """Inputs as the device sees them (complex64 paths store complex64)."""
-    return a.astype(np.complex64).astype(np.complex128) if prec != "c128" else np.asarray(a, np.complex128)
+    return a.astype(np.complex64).astype(np.complex128) if not prec.startswith("c128") else np.asarray(a, np.complex128)
 
 
 def run_gpu(prec, Xi, Bm, Bn, U, trunc, theta=None, xi_kind=None):

@@ -326,3 +326,26 @@ def test_als_sweeps_match_oracle(prec, scheme):
         eps[k] = gpu["eps"]
     assert eps[4] < eps[1]
 
+
+
+@pytest.mark.parametrize("scheme", ["plain", "cbe"])
+def test_emulated_fp64_bond_against_oracle(scheme):
+    # complex128 with the large products on the tensor cores (Ozaki slices): a bond whose
+    # contractions and QR updates are big enough for that path, at the complex128 bar
+    from paper_2212_09782_b300 import lib as L
+    dims = (400, 5, 400, 400)
+    bd = _case(dims, seed=4004, xi="diag", prec="c128_oz")
+    chi_max = 400 if scheme == "plain" else 380
+    kw = {} if scheme == "plain" else dict(dchi_min=40, dchi_frac=0.1)
+    orc = bond.qr_update(bd["Xi"], bd["Bm"], bd["Bn"], bd["U"], scheme=scheme, chi_max=chi_max, **kw)
+    t = L.trunc_default(L.PLAIN if scheme == "plain" else L.CBE, chi_max, **kw)
+    gpu = run_gpu("c128_oz", bd["Xi"], bd["Bm"], bd["Bn"], bd["U"], t, xi_kind=2)
+    sub = subspace_tol(TOL["c128_oz"], "c128_oz", orc["S"], orc["chi_new"]) if scheme == "cbe" else None
+    errs = compare(gpu, orc, TOL["c128_oz"], sub_tol=sub)
+    print(scheme, errs)
+
+
+@pytest.mark.slow
+def test_c2_full_size_c128_oz_against_oracle():
+    """The bench workload with FP64 emulated on the tensor cores, at the 1e-10 bar."""
+    _c2_full_size("c128_oz", 1e-10)

@@ -8,7 +8,7 @@ from paper_2212_09782_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"c128": 1e-13, "c64_fp32": 3e-7, "c64_3xtf32": 3e-7, "c64_tf32": 4e-3}
+TOL = {"c128": 1e-13, "c128_oz": 1e-13, "c64_fp32": 3e-7, "c64_3xtf32": 3e-7, "c64_tf32": 4e-3}
 
 
 def tol(prec, k):
@@ -32,8 +32,8 @@ def test_zgemm(prec, m, n, k, ops):
     A = W.complex_gaussian(r, (k, m) if ta else (m, k))
     B = W.complex_gaussian(r, (n, k) if tb else (k, n))
     C0 = W.complex_gaussian(r, (m, n))
-    dt = torch.complex128 if prec == "c128" else torch.complex64
-    if prec != "c128":
+    dt = torch.complex128 if prec.startswith("c128") else torch.complex64
+    if not prec.startswith("c128"):
         A, B, C0 = (x.astype(np.complex64).astype(np.complex128) for x in (A, B, C0))
     opA = A.T if ta else A
     opA = opA.conj() if ca else opA
@@ -138,3 +138,53 @@ def test_autotune_bond_table_and_parity():
         compare(gpu, orc, BTOL["c64_3xtf32"])
     finally:
         L.autotune_clear()
+
+
+@pytest.mark.parametrize("m,n,k", [(2048, 1024, 777), (1500, 600, 2048), (1030, 2100, 333), (5120, 256, 130)])
+@pytest.mark.parametrize("ops", ["nn", "ct", "tc", "nc"])
+def test_zgemm_emulated_fp64(m, n, k, ops):
+    # complex128 on the tensor cores (Ozaki slices): products large enough for the tensor-core
+    # path (>= 64 output tiles), ragged in every dimension, transposed and conjugated operands;
+    # relative to the FP64 product the error must stay at complex128 level
+    import torch
+    from paper_2212_09782_b300 import lib as L
+    r = W.rng(m + 7 * n + 13 * k)
+    ta, tb = ops[0] in "tc", ops[1] in "tc"
+    ca, cb = ops[0] == "c", ops[1] == "c"
+    A = W.complex_gaussian(r, (k, m) if ta else (m, k))
+    B = W.complex_gaussian(r, (n, k) if tb else (k, n))
+    # rows of very different magnitudes: each row takes its own power-of-two scale
+    A = A * (10.0 ** r.uniform(-6, 6, size=(A.shape[0], 1)))
+    C0 = W.complex_gaussian(r, (m, n))
+    opA = (A.T if ta else A)
+    opA = opA.conj() if ca else opA
+    opB = (B.T if tb else B)
+    opB = opB.conj() if cb else opB
+    alpha, beta = 0.7 - 0.2j, -0.5 + 0.25j
+    ref = alpha * (opA @ opB) + beta * C0
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=torch.complex128)
+    Cd = dev(C0)
+    L.zgemm("c128_oz", dev(A), dev(B), conj_a=ca, conj_b=cb, trans_a=ta, trans_b=tb, alpha=alpha,
+            beta=beta, C_out=Cd)
+    L.stream_check()
+    got = Cd.cpu().numpy()
+    # error of each row relative to the size of that row's terms
+    row_scale = np.abs(opA) @ np.abs(opB) * abs(alpha) + abs(beta) * np.abs(C0)
+    err = (np.abs(got - ref) / row_scale).max()
+    assert err < 1e-13, err
+
+
+def test_zgemm_emulated_fp64_exact_on_integers():
+    # integer operands of up to 8 bits are single slices: every product and every 128-term
+    # chunk sum is an integer below 2^24, so the emulated product must be exact
+    import torch
+    from paper_2212_09782_b300 import lib as L
+    r = W.rng(99)
+    m, n, k = 1024, 1024, 1000
+    A = r.integers(-127, 128, size=(m, k)) + 1j * r.integers(-127, 128, size=(m, k))
+    B = r.integers(-127, 128, size=(k, n)) + 1j * r.integers(-127, 128, size=(k, n))
+    ref = A @ B
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=torch.complex128)
+    out = L.zgemm("c128_oz", dev(A), dev(B))
+    L.stream_check()
+    assert np.array_equal(out.cpu().numpy(), ref)
