@@ -604,14 +604,34 @@ def run_serve(args):
     srv = serve.QuenchServer(precision=args.precision)
     for r in reqs:
         srv.submit(r)
-    m = srv.run()
+    m = srv.run(max_seconds=args.serve_max_seconds)
+    # per-request parity: the cheapest finished requests replayed by the complex128 oracle
+    # (same L, d, g, dt, chi_max, steps, plain scheme), <Z> of the middle site step by step
+    parity = []
+    if args.serve_oracle > 0:
+        from oracle import clock as oclock
+        from oracle import mps as omps
+        done = sorted(srv.done, key=lambda r: r.L * r.chi_max ** 2 * r.d ** 3)[: args.serve_oracle]
+        for r in done:
+            t0 = time.perf_counter()
+            o = omps.product_state(r.L, r.d, 0, True)
+            half, full = omps.strang_gates(r.L, r.d, r.g, r.dt, True)
+            Z, _X = oclock.clock_operators(r.d)
+            zo = []
+            for _ in range(len(r.z_mid)):
+                omps.tebd_step(o, half, full, scheme="plain", chi_max=r.chi_max)
+                zo.append(omps.expectation_1site(o, r.L // 2, Z))
+            dz = np.abs(np.array(r.z_mid) - np.array(zo))
+            parity.append({"rid": r.rid, "L": r.L, "d": r.d, "chi_max": r.chi_max, "g": round(r.g, 4),
+                           "steps": len(zo), "max_abs_dZ_mid": float(dz.max()),
+                           "oracle_seconds": round(time.perf_counter() - t0, 1)})
     line = {"metric": "quench serving: aggregate bond updates/s, p50/p99 per-step latency",
             "value": m["bond_updates_per_s"], "unit": UNIT, "n_gpus": 1,
             "p50_ms": m["p50_step_latency_ms"], "p99_ms": m["p99_step_latency_ms"],
             "higher_is_better": True, "dtype": args.precision, "data": "synthetic",
             "config": {"workload": f"{args.serve_requests} quench requests, Poisson 4/s, "
                                    f"{args.serve_steps} Strang steps each"},
-            "detail": m}
+            "detail": m, "oracle_parity": parity}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -847,6 +867,10 @@ def main():
     ap.add_argument("--c3-seconds", type=float, default=240.0)
     ap.add_argument("--serve-requests", type=int, default=12)
     ap.add_argument("--serve-steps", type=int, default=6)
+    ap.add_argument("--serve-max-seconds", type=float, default=None,
+                    help="serve workload: stop admitting and ticking after this wall time")
+    ap.add_argument("--serve-oracle", type=int, default=2,
+                    help="serve workload: replay this many of the cheapest finished requests on the oracle")
     ap.add_argument("--chain-L", type=int, default=128)
     ap.add_argument("--chain-chi", type=int, default=512)
     ap.add_argument("--no-batch", action="store_true")

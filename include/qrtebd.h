@@ -149,7 +149,8 @@ int qrtebd_bond_workspace_size(int precision, int chi_l, int d, int chi_m, int c
  *   CBE:   L^dag L = V^dag S^2 V, keep chi~ values, B~^n = P V Q^[n], Xi~ = P S P / ||.||;
  *   B~^m = theta~' B~^n^dag (Hastings form, Sec. II).
  * Enqueued on `stream`. For PLAIN the call returns without synchronising; for
- * CBE it synchronises `stream` once to read chi~. Errors: INVALID_ARG for bad
+ * CBE every kernel after the cut reads chi~ on the device, and the call synchronises
+ * `stream` once, after enqueuing all its work, to return chi~ in *info. Errors: INVALID_ARG for bad
  * sizes or eta > min(d chi_l, d chi_r) or eta > chi_m*... (see trunc), OOM if the
  * workspace is too small, CUDA on a launch failure, TIMEOUT if a kernel gave up a
  * bounded wait (reported at the next synchronising call). */
@@ -249,16 +250,22 @@ int qrtebd_mps_load(const char* path, void* stream, qrtebd_mps** out);
  * earlier work on each state's stream and before later work on it. gates_host[i]: the
  * gates of state i (as for qrtebd_apply_gate_layer); eps_out: NULL, or per-state arrays
  * (entries may be NULL) that receive each updated bond's eps (synchronises). For the
- * PLAIN scheme no host synchronisation happens, and a layer whose shapes repeat is
- * recorded as a CUDA graph the second time and replayed afterwards; CBE reads each new
- * bond dimension back. A state may appear at most once. Not thread-safe per device. */
+ * PLAIN scheme no host synchronisation happens; CBE keeps every cut on the device until the
+ * whole layer is enqueued and then reads the new bond dimensions back once per state. A
+ * layer whose shapes repeat (plain, or complex64 CBE) is recorded as a CUDA graph the second
+ * time and replayed afterwards. A state may appear at most once. Not thread-safe per device. */
 int qrtebd_apply_gate_layer_batched(qrtebd_mps* const* states, int nstates, int parity,
                                     const double* const* gates_host, const qrtebd_trunc* tr,
                                     double* const* eps_out);
 
 /* Number of worker streams of the batched-layer executor. Each worker holds one bond-update
- * workspace sized for the largest bond it has run, so a caller budgeting device memory for
- * batched layers (e.g. an admission policy) reserves this many workspaces. */
+ * workspace sized for the largest bond it has run. Bonds whose workspace exceeds
+ * QRTEBD_LAYER_BIG_BOND_BYTES run on the first QRTEBD_LAYER_BIG_WORKERS workers only (the
+ * other bonds of such a layer on the rest), so a caller budgeting device memory for batched
+ * layers (e.g. an admission policy) reserves QRTEBD_LAYER_BIG_WORKERS of its largest
+ * workspaces plus, for the rest, workspaces of at most QRTEBD_LAYER_BIG_BOND_BYTES. */
+#define QRTEBD_LAYER_BIG_BOND_BYTES (512ull << 20)
+#define QRTEBD_LAYER_BIG_WORKERS 8
 int qrtebd_layer_workers(void);
 /* Load a site tensor / bond matrix from host complex128 data (e.g. a random
  * right-canonical state, or a state produced elsewhere). B_host: (chi_l, d, chi_r);

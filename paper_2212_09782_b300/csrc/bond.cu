@@ -125,13 +125,46 @@ __global__ void k_sum_partials(const double* partial, int n, double* out) {
 // stats = {eps, ||theta~||^2, kept, chi_new}; scal[0] = 1/sqrt(kept_norm), the scale that
 // normalises the kept values (kept_norm: nullptr = kept)
 __global__ void k_finalize(const double* th2, const double* kept, double chi_new, double* stats,
-                           double* scal, unsigned* err, const double* kept_norm = nullptr) {
+                           double* scal, unsigned* err, const double* kept_norm = nullptr,
+                           const int* chi_dev = nullptr) {
   double t = *th2, k = *kept, kn = kept_norm ? *kept_norm : k;
   double eps = t > 0 ? 1.0 - k / t : 0.0;
   if (eps < 0) eps = 0;
   if (!isfinite(t) || !isfinite(k) || !isfinite(kn)) atomicOr(err, DEVERR_NUMERIC);
-  if (stats) { stats[0] = eps; stats[1] = t; stats[2] = k; stats[3] = chi_new; }
+  if (stats) { stats[0] = eps; stats[1] = t; stats[2] = k; stats[3] = chi_dev ? (double)*chi_dev : chi_new; }
   scal[0] = kn > 0 ? 1.0 / sqrt(kn) : 0.0;
+}
+
+// ---- the CBE tail with the cut chi~ on the device (chi = *chi_dev, n the expansion eta)
+// Vt = V with its rows from chi~ on zeroed (the projector P of step (v)), n x n
+template <typename T> __global__ void k_from_c128_rows(const double2* in, cx<T>* out, int n, const int* chi_dev) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)n * n) return;
+  const int c = *chi_dev;
+  out[i] = (i / n < c) ? mk<T>((T)in[i].x, (T)in[i].y) : mk<T>(0, 0);
+}
+// dst[0 : chi~ cols) = src[0 : chi~ cols): the first chi~ rows of a row-major matrix
+template <typename T> __global__ void k_copy_rows_dev(const cx<T>* src, cx<T>* dst, long long cols, int n, const int* chi_dev) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= (long long)n * cols) return;
+  if (i < (long long)*chi_dev * cols) dst[i] = src[i];
+}
+// dst (rows x chi~, leading dimension chi~) = the first chi~ columns of src (leading dimension n)
+template <typename T> __global__ void k_copy_cols_dev(const cx<T>* src, int n, cx<T>* dst, long long rows, const int* chi_dev) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i >= rows * n) return;
+  const int c = *chi_dev;
+  const long long r = i / n;
+  const int j = (int)(i % n);
+  if (j < c) dst[r * c + j] = src[i];
+}
+// Xi~ = diag(S[0 : chi~]) / ||.|| as a dense chi~ x chi~ matrix (grid over n x n)
+template <typename T> __global__ void k_diag_xi_dev(const double* S, const int* chi_dev, int n, const double* scal, cx<T>* xi) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int c = *chi_dev;
+  if (idx >= (long long)c * c || idx >= (long long)n * n) return;
+  const int i = (int)(idx / c), j = (int)(idx % c);
+  xi[idx] = mk<T>(i == j ? (T)(S[i] * scal[0]) : T(0), 0);
 }
 
 // explicit eps = ||theta~ - approx||^2 / ||theta~||^2 overrides stats[0]
@@ -240,15 +273,6 @@ __global__ void k_cbe_cut(const double* w, int n, int chi_max, double svd_min, d
   *chi_out = c;
 }
 
-// Xi~ = diag(S[0:c]) / sqrt(kept), dense c x c
-template <typename T>
-__global__ void k_diag_xi(const double* S, int c, const double* scal, cx<T>* xi) {
-  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= (long long)c * c) return;
-  int i = (int)(idx / c), j = (int)(idx % c);
-  xi[idx] = mk<T>(i == j ? (T)(S[i] * scal[0]) : T(0), 0);
-}
-
 // D = v * identity (n x n)
 template <typename T> __global__ void k_scaled_eye(cx<T>* D, int n, T v) {
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -301,7 +325,7 @@ template <typename T> int qr_gemm_thunk(const GemmArgs<T>& g, cudaStream_t st, v
 
 template <typename T>
 int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t st,
-                  qrtebd_bond_info* info, size_t* bytes) {
+                  qrtebd_bond_info* info, size_t* bytes, bool sync_chi) {
   const int chiL = io->chi_l, d = io->d, chiM = io->chi_m, chiR = io->chi_r;
   const bool measuring = (bytes != nullptr);
   const long long mL = (long long)chiL * d, nR = (long long)d * chiR;
@@ -342,6 +366,7 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
   constexpr bool kOneSided = std::is_same<T, float>::value;
   double2* M = nullptr; double2* Vh = nullptr; double* w = nullptr; double2* eig_scr = nullptr;
   double* Sv = nullptr; cx<T>* Vt = nullptr; int* chi_dev = nullptr; char* sj_work = nullptr;
+  cx<T>* Bn_full = nullptr; cx<T>* Bm_full = nullptr;
   size_t eig_elems = 0, sj_bytes = 0;
   if (cbe) {
     Vh = ar.take<double2>((size_t)eta * eta);
@@ -349,6 +374,10 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
     Sv = ar.take<double>(eta);
     Vt = ar.take<cx<T>>((size_t)eta * eta);
     chi_dev = ar.take<int>(4);
+    // the last products run at the expansion eta (rows of V beyond chi~ zeroed) into these,
+    // and their first chi~ rows / columns are copied into the outputs' layout
+    Bn_full = ar.take<cx<T>>((size_t)eta * nR);
+    Bm_full = ar.take<cx<T>>((size_t)mL * eta);
     if (kOneSided) {
       sj_bytes = svd32_work_bytes(eta);
       sj_work = ar.take<char>(sj_bytes);
@@ -550,41 +579,41 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
                                Sv, scal + 1, scal + 5, chi_dev);
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());
-    int chi_h = 0;
-    QR_CUDA_TRY(cudaMemcpyAsync(&chi_h, chi_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
-    QR_CUDA_TRY(cudaStreamSynchronize(st));
-    chi_new = chi_h;
-    if (chi_new < 1 || chi_new > eta) { set_last_message("CBE: bad cut"); return QRTEBD_ERR_NUMERIC; }
     if (io->schmidt_out)
       QR_CUDA_TRY(cudaMemcpyAsync(io->schmidt_out, Sv, eta * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    k_finalize<<<1, 1, 0, st>>>(scal + 0, scal + 1, (double)chi_new,
-                                io->stats_out ? io->stats_out : stats_local, scal + 2, err, scal + 5);
+    k_finalize<<<1, 1, 0, st>>>(scal + 0, scal + 1, 0.0, io->stats_out ? io->stats_out : stats_local, scal + 2,
+                                err, scal + 5, chi_dev);
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());
-    // (v) B~^n = P V Q^[n] = Vh[0:c] Qz^dag; Xi~ = diag(S[0:c]) / ||.||
-    k_from_c128<T><<<(unsigned)ceil_div(ee, 256), 256, 0, st>>>(Vh, Vt, ee);
+    // (v) with chi~ on the device: Vt = P V (rows from chi~ on zeroed), B~^n = P V Q^[n] at
+    // eta rows (Bn_full = Vt Qz^dag), Xi~ = diag(S[0:chi~]) / ||.||, B~^m = theta~' B~^n^dag at
+    // eta columns; the outputs take the first chi~ rows / columns
+    const unsigned gb = (unsigned)ceil_div(ee, 256);
+    k_from_c128_rows<T><<<gb, 256, 0, st>>>(Vh, Vt, eta, chi_dev);
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());
     {
-      GemmArgs<T> g{chi_new, (int)nR, eta, Vt, eta, 1, false, Qz, 1, eta, true, bn_out, nR, 1,
+      GemmArgs<T> g{eta, (int)nR, eta, Vt, eta, 1, false, Qz, 1, eta, true, Bn_full, nR, 1, one, zero};
+      QR_TRY(runner.run(g, st, true));
+    }
+    k_copy_rows_dev<T><<<(unsigned)ceil_div((long long)eta * nR, 256), 256, 0, st>>>(Bn_full, bn_out, nR, eta, chi_dev);
+    note_launch();
+    k_diag_xi_dev<T><<<gb, 256, 0, st>>>(Sv, chi_dev, eta, scal + 2, xi_out);
+    note_launch();
+    QR_CUDA_TRY(cudaGetLastError());
+    {
+      GemmArgs<T> g{(int)mL, eta, (int)nR, theta_tp, nR, 1, false, Bn_full, 1, nR, true, Bm_full, eta, 1,
                     one, zero};
       QR_TRY(runner.run(g, st, true));
     }
-    k_diag_xi<T><<<(unsigned)ceil_div((long long)chi_new * chi_new, 256), 256, 0, st>>>(
-        Sv, chi_new, scal + 2, xi_out);
+    k_copy_cols_dev<T><<<(unsigned)ceil_div((long long)mL * eta, 256), 256, 0, st>>>(Bm_full, eta, bm_out, mL, chi_dev);
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());
-    {
-      GemmArgs<T> g{(int)mL, chi_new, (int)nR, theta_tp, nR, 1, false, bn_out, 1, nR, true, bm_out,
-                    chi_new, 1, one, zero};
-      QR_TRY(runner.run(g, st, true));
-    }
     if (eps_explicit) {
-      // approx = Q L V_c^dag B~^n; residual theta~ - approx (Sec. IV)
-      GemmArgs<T> g1{eta, chi_new, eta, Z, 1, eta, true, Vt, 1, eta, true, LV, chi_new, 1, one, zero};
+      // approx = Q L V_c^dag B~^n = Q (L Vt^dag) Bn_full; residual theta~ - approx (Sec. IV)
+      GemmArgs<T> g1{eta, eta, eta, Z, 1, eta, true, Vt, 1, eta, true, LV, eta, 1, one, zero};
       QR_TRY(runner.run(g1, st));
-      GemmArgs<T> g2{eta, (int)nR, chi_new, LV, chi_new, 1, false, bn_out, nR, 1, false, Yt, nR, 1,
-                     one, zero};
+      GemmArgs<T> g2{eta, (int)nR, eta, LV, eta, 1, false, Bn_full, nR, 1, false, Yt, nR, 1, one, zero};
       QR_TRY(runner.run(g2, st));
       QR_CUDA_TRY(cudaMemcpyAsync(Rbuf, theta_t, (size_t)mL * nR * sizeof(cx<T>), cudaMemcpyDeviceToDevice, st));
       GemmArgs<T> r{(int)mL, (int)nR, eta, Q, eta, 1, false, Yt, nR, 1, false, Rbuf, nR, 1,
@@ -594,6 +623,14 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
       k_eps_explicit<<<1, 1, 0, st>>>(scal + 0, scal + 3, io->stats_out ? io->stats_out : stats_local);
       note_launch();
       QR_CUDA_TRY(cudaGetLastError());
+    }
+    chi_new = -1;
+    if (sync_chi) {
+      int chi_h = 0;
+      QR_CUDA_TRY(cudaMemcpyAsync(&chi_h, chi_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+      QR_CUDA_TRY(cudaStreamSynchronize(st));
+      if (chi_h < 1 || chi_h > eta) { set_last_message("CBE: bad cut"); return QRTEBD_ERR_NUMERIC; }
+      chi_new = chi_h;
     }
   }
   if (info) { info->eta = eta; info->chi_new = chi_new; }
@@ -619,7 +656,7 @@ int choose_eta(const qrtebd_trunc* tr, int chi_l, int d, int chi_m, int chi_r) {
 }
 
 int bond_update(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t st,
-                qrtebd_bond_info* info, size_t* bytes) {
+                qrtebd_bond_info* info, size_t* bytes, bool sync_chi) {
   if (!io || !tr) return QRTEBD_ERR_INVALID_ARG;
   if (io->chi_l < 1 || io->d < 2 || io->chi_m < 1 || io->chi_r < 1 || tr->chi_max < 1)
     return QRTEBD_ERR_INVALID_ARG;
@@ -636,10 +673,10 @@ int bond_update(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t s
   }
   switch (io->precision) {
     case QRTEBD_C128:
-    case QRTEBD_C128_OZ: return bond_update_t<double>(io, tr, st, info, bytes);
+    case QRTEBD_C128_OZ: return bond_update_t<double>(io, tr, st, info, bytes, sync_chi);
     case QRTEBD_C64_3XTF32:
     case QRTEBD_C64_TF32:
-    case QRTEBD_C64_FP32: return bond_update_t<float>(io, tr, st, info, bytes);
+    case QRTEBD_C64_FP32: return bond_update_t<float>(io, tr, st, info, bytes, sync_chi);
     default: return QRTEBD_ERR_INVALID_ARG;
   }
 }

@@ -8,8 +8,12 @@ namespace qrtebd {
 
 // Shared implementation of qrtebd_bond_workspace_size / qrtebd_bond_update:
 // with bytes != nullptr only the workspace is measured (no GPU work).
+// CBE: the cut chi~ stays on the device (stats_out[3], as a double) and every kernel after the
+// cut reads it there; sync_chi = true reads it back at the end (one stream synchronisation) into
+// info->chi_new, sync_chi = false leaves info->chi_new = -1 for the caller to collect later
+// (no synchronisation: a CBE update can then be recorded into a CUDA graph).
 int bond_update(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t st,
-                qrtebd_bond_info* info, size_t* bytes);
+                qrtebd_bond_info* info, size_t* bytes, bool sync_chi = true);
 
 // Effective eta for these sizes (the policy of qrtebd_trunc).
 int choose_eta(const qrtebd_trunc* tr, int chi_l, int d, int chi_m, int chi_r);

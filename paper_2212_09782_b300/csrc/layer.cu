@@ -23,6 +23,13 @@ namespace qrtebd {
 namespace {
 
 constexpr int kWorkers = 16;
+// Bonds whose workspace exceeds QRTEBD_LAYER_BIG_BOND_BYTES run on the first
+// QRTEBD_LAYER_BIG_WORKERS workers only, so the executor holds at most that many of the largest
+// workspaces (a chi = 1024, d = 5 bond needs ~3 GB); the other bonds of such a layer take the
+// remaining workers.
+constexpr size_t kBigBond = QRTEBD_LAYER_BIG_BOND_BYTES;
+constexpr int kBigWorkers = QRTEBD_LAYER_BIG_WORKERS;
+static_assert(kBigWorkers >= 1 && kBigWorkers < kWorkers, "big-bond workers");
 
 struct Worker {
   cudaStream_t st = nullptr;
@@ -148,23 +155,37 @@ int qrtebd_apply_gate_layer_batched(qrtebd_mps* const* states, int nstates, int 
   std::lock_guard<std::mutex> lk(ex.mu);
   QR_TRY(executor_init(ex, dev));
 
-  // tasks, round-robin over the workers, and the workspace each worker needs
+  // tasks, round-robin over the workers (the largest bonds over the first kBigWorkers only),
+  // and the workspace each worker needs
   std::vector<Task> tasks;
+  std::vector<size_t> task_need;
   size_t need[kWorkers] = {};
+  auto bits = [](double v) { long long b; std::memcpy(&b, &v, sizeof b); return b; };
   std::vector<long long> key = {parity, tr->scheme, tr->chi_max, tr->eta, tr->dchi_min,
-                                tr->eps_explicit, tr->reorth, tr->sweeps};
+                                tr->eps_explicit, tr->reorth, tr->sweeps, bits(tr->dchi_frac),
+                                bits(tr->svd_min), bits(tr->tie_tol), bits(tr->eps_target)};
+  bool any_big = false;
   for (int i = 0; i < nstates; ++i) {
     qrtebd_mps* s = states[i];
     key.push_back(reinterpret_cast<long long>(s));
     for (int b : s->chi) key.push_back(b);
     for (char c : s->xi_diag) key.push_back(c);
     for (int m = parity; m < mps_gate_count(s); m += 2) {
-      const int wk = (int)(tasks.size() % kWorkers);
       size_t nb = 0;
       QR_TRY(mps_bond_ws_need(s, m, tr, &nb));
-      need[wk] = std::max(need[wk], nb);
-      tasks.push_back(Task{s, m, wk});
+      any_big = any_big || nb > kBigBond;
+      tasks.push_back(Task{s, m, 0});
+      task_need.push_back(nb);
     }
+  }
+  int rr_big = 0, rr_small = 0;
+  for (size_t t = 0; t < tasks.size(); ++t) {
+    int wk;
+    if (task_need[t] > kBigBond) wk = rr_big++ % kBigWorkers;
+    else if (any_big) wk = kBigWorkers + rr_small++ % (kWorkers - kBigWorkers);
+    else wk = rr_small++ % kWorkers;
+    tasks[t].worker = wk;
+    need[wk] = std::max(need[wk], task_need[t]);
   }
   for (int k = 0; k < kWorkers; ++k) QR_TRY(worker_reserve(ex, ex.w[k], need[k]));
 
@@ -181,7 +202,13 @@ int qrtebd_apply_gate_layer_batched(qrtebd_mps* const* states, int nstates, int 
     QR_CUDA_TRY(cudaStreamWaitEvent(ex.origin, ex.state_ev[i], 0));
   }
 
-  const bool capturable = (tr->scheme == QRTEBD_PLAIN);
+  // a CBE layer keeps its cuts on the device (collected after the join), so it can be recorded
+  // too, except in complex128, whose FP64 eigensolver synchronises with the host per sweep
+  bool capturable = (tr->scheme == QRTEBD_PLAIN);
+  if (tr->scheme == QRTEBD_CBE) {
+    capturable = true;
+    for (int i = 0; i < nstates; ++i) capturable = capturable && !prec_is_c128(states[i]->precision);
+  }
   GraphEntry* ge = nullptr;
   if (capturable) {
     for (auto& g : ex.graphs)
@@ -199,12 +226,17 @@ int qrtebd_apply_gate_layer_batched(qrtebd_mps* const* states, int nstates, int 
   if (ge && ge->exec) {
     QR_CUDA_TRY(cudaGraphLaunch(ge->exec, ex.origin));
     note_launch(ge->nkernels);
-    // host bookkeeping the graph does not do: new bond dimensions (plain: eta)
+    // host bookkeeping the graph does not do: new bond dimensions (plain: eta; CBE: the cut
+    // on the device, collected after the join)
     for (auto& t : tasks) {
       qrtebd_mps* s = t.s;
       const int bl = s->infinite ? t.m % s->L : t.m;
       const int bmid = s->infinite ? (t.m + 1) % s->L : t.m + 1;
       const int br = s->infinite ? (t.m + 2) % s->L : t.m + 2;
+      if (tr->scheme == QRTEBD_CBE) {
+        s->chi_pending[bmid] = 1;
+        continue;
+      }
       qrtebd_trunc tt = *tr;
       if (tt.chi_max > s->cap[bmid]) tt.chi_max = s->cap[bmid];
       s->chi[bmid] = choose_eta(&tt, s->chi[bl], s->d, s->chi[bmid], s->chi[br]);
@@ -213,18 +245,43 @@ int qrtebd_apply_gate_layer_batched(qrtebd_mps* const* states, int nstates, int 
   } else if (ge && ge->seen >= 2) {
     // second sighting of this shape: capture, then launch
     ProfSuppress no_events;
-    std::vector<int> chi_before;
-    for (int i = 0; i < nstates; ++i) chi_before.insert(chi_before.end(), states[i]->chi.begin(), states[i]->chi.end());
+    // the host bookkeeping of the enqueue (bond dimensions) is kept so that a capture that
+    // fails can be undone and the layer run without a graph
+    std::vector<std::vector<int>> chi_before(nstates);
+    std::vector<std::vector<char>> diag_before(nstates), pend_before(nstates);
+    for (int i = 0; i < nstates; ++i) {
+      chi_before[i] = states[i]->chi;
+      diag_before[i] = states[i]->xi_diag;
+      pend_before[i] = states[i]->chi_pending;
+    }
     QR_CUDA_TRY(cudaStreamBeginCapture(ex.origin, cudaStreamCaptureModeRelaxed));
     int rc = enqueue_layer(ex, tasks, tr);
     cudaGraph_t graph = nullptr;
     cudaError_t ec = cudaStreamEndCapture(ex.origin, &graph);
     if (rc != QRTEBD_OK || ec != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
+      // worker streams drawn into the failed capture leave it too
+      for (auto& w : ex.w) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(w.st, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+          cudaGraph_t g2 = nullptr;
+          if (cudaStreamEndCapture(w.st, &g2) == cudaSuccess && g2) cudaGraphDestroy(g2);
+        }
+      }
       (void)cudaGetLastError();
-      set_last_message("batched layer: graph capture failed");
-      return rc != QRTEBD_OK ? rc : QRTEBD_ERR_CUDA;
+      if (rc != QRTEBD_OK && ec == cudaSuccess) return rc;  // a real failure of the enqueue
+      for (int i = 0; i < nstates; ++i) {
+        states[i]->chi = chi_before[i];
+        states[i]->xi_diag = diag_before[i];
+        states[i]->chi_pending = pend_before[i];
+      }
+      ge->seen = -(1 << 30);  // never capture this shape again
+      QR_TRY(enqueue_layer(ex, tasks, tr));
+      graph = nullptr;
     }
+    if (!graph) {
+      // ran without a graph (capture refused)
+    } else {
     // the capture already updated the host bond dimensions; the graph has not run yet
     size_t nn = 0;
     QR_CUDA_TRY(cudaGraphGetNodes(graph, nullptr, &nn));
@@ -238,12 +295,15 @@ int qrtebd_apply_gate_layer_batched(qrtebd_mps* const* states, int nstates, int 
     QR_CUDA_TRY(cudaGraphInstantiate(&ge->exec, graph, 0));
     cudaGraphDestroy(graph);
     QR_CUDA_TRY(cudaGraphLaunch(ge->exec, ex.origin));
+    }
   } else {
     QR_TRY(enqueue_layer(ex, tasks, tr));
   }
 
   QR_CUDA_TRY(cudaEventRecord(ex.join, ex.origin));
   for (int i = 0; i < nstates; ++i) QR_CUDA_TRY(cudaStreamWaitEvent(states[i]->st, ex.join, 0));
+  // CBE: every state's cuts in one read-back per state, after the whole layer
+  for (int i = 0; i < nstates; ++i) QR_TRY(mps_collect_cuts(states[i]));
 
   if (eps_out) {
     for (int i = 0; i < nstates; ++i) {

@@ -23,9 +23,11 @@ template <typename T> __global__ void k_to_c128v(const cx<T>* in, double2* out, 
   long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (i < n) out[i] = make_double2((double)in[i].x, (double)in[i].y);
 }
-template <typename T> __global__ void k_diag_of(const cx<T>* M, int n, cx<T>* v) {
+// the diagonal of the dense n x n bond matrix, n = the cut chi~ read from stats[3] on the device
+template <typename T> __global__ void k_diag_of(const cx<T>* M, const double* stats, int cap, cx<T>* v) {
+  const int n = (int)stats[3];
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) v[i] = M[(long long)i * n + i];
+  if (i < n && i < cap) v[i] = M[(long long)i * n + i];
 }
 __global__ void k_acc_eps(const double* stats, double* acc, double* layer_slot) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -121,6 +123,7 @@ int allocate(qrtebd_mps* s) {
   s->Xi.assign(s->nbonds_store, nullptr);
   s->xiv.assign(s->nbonds_store, nullptr);
   s->xi_diag.assign(s->nbonds_store, 1);
+  s->chi_pending.assign(s->nbonds_store, 0);
   for (int m = 0; m < L; ++m) {
     int r = s->infinite ? (m + 1) % L : m + 1;
     QR_TRY(dev_alloc(&s->B[m], (size_t)s->cap[m] * d * s->cap[r] * s->esz));
@@ -179,13 +182,17 @@ int update_bond_t(qrtebd_mps* s, int m, const qrtebd_trunc* tr, cudaStream_t st,
   qrtebd_trunc t = *tr;
   if (t.chi_max > s->cap[bmid]) t.chi_max = s->cap[bmid];
   qrtebd_bond_info info;
-  QR_TRY(bond_update(&io, &t, st, &info, nullptr));
-  s->chi[bmid] = info.chi_new;
-  s->xi_diag[bmid] = (t.scheme == QRTEBD_CBE) ? 1 : 0;
-  if (s->xi_diag[bmid]) {
-    k_diag_of<T><<<(unsigned)ceil_div(info.chi_new, 128), 128, 0, st>>>(
-        static_cast<cx<T>*>(s->Xi[bmid]), info.chi_new, static_cast<cx<T>*>(s->xiv[bmid]));
+  // no host synchronisation: a CBE cut stays on the device (stats[3]) until mps_collect_cuts
+  QR_TRY(bond_update(&io, &t, st, &info, nullptr, /*sync_chi=*/false));
+  if (t.scheme == QRTEBD_CBE) {
+    s->chi_pending[bmid] = 1;
+    k_diag_of<T><<<(unsigned)ceil_div(s->cap[bmid], 128), 128, 0, st>>>(
+        static_cast<cx<T>*>(s->Xi[bmid]), s->stats + 4 * (size_t)m, s->cap[bmid],
+        static_cast<cx<T>*>(s->xiv[bmid]));
     note_launch();
+  } else {
+    s->chi[bmid] = info.chi_new;
+    s->xi_diag[bmid] = 0;
   }
   k_acc_eps<<<1, 1, 0, st>>>(s->stats + 4 * (size_t)m, s->eps_acc + bmid, s->layer_eps + m);
   note_launch();
@@ -204,6 +211,7 @@ int apply_layer_t(qrtebd_mps* s, int parity, const double* gates_host, const qrt
     QR_TRY(ensure_ws(s, need));
     QR_TRY(update_bond_t<T>(s, m, tr, s->st, s->ws, s->ws_bytes));
   }
+  QR_TRY(mps_collect_cuts(s));
   if (eps_out) {
     std::vector<double> le(ng + 1);
     QR_CUDA_TRY(cudaMemcpyAsync(le.data(), s->layer_eps, ng * sizeof(double), cudaMemcpyDeviceToHost, s->st));
@@ -346,6 +354,26 @@ int mps_bond_ws_need(const qrtebd_mps* s, int m, const qrtebd_trunc* tr, size_t*
   qrtebd_trunc t = *tr;
   if (t.chi_max > s->cap[bmid]) t.chi_max = s->cap[bmid];
   return bond_update(&io, &t, nullptr, nullptr, need);
+}
+
+int mps_collect_cuts(qrtebd_mps* s) {
+  bool any = false;
+  for (char c : s->chi_pending) any = any || c;
+  if (!any) return QRTEBD_OK;
+  const int ng = gate_count(s);
+  std::vector<double> st(4 * (size_t)ng);
+  QR_CUDA_TRY(cudaMemcpyAsync(st.data(), s->stats, st.size() * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+  QR_CUDA_TRY(cudaStreamSynchronize(s->st));
+  for (int m = 0; m < ng; ++m) {
+    const int bmid = bond_index(s, m + 1);
+    if (!s->chi_pending[bmid]) continue;
+    const int c = (int)st[4 * (size_t)m + 3];
+    if (c < 1 || c > s->cap[bmid]) { set_last_message("CBE: bad cut"); return QRTEBD_ERR_NUMERIC; }
+    s->chi[bmid] = c;
+    s->xi_diag[bmid] = 1;
+    s->chi_pending[bmid] = 0;
+  }
+  return QRTEBD_OK;
 }
 
 int mps_update_bond(qrtebd_mps* s, int m, const qrtebd_trunc* tr, cudaStream_t st, void* ws,

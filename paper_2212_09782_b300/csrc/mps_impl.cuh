@@ -13,6 +13,7 @@ struct qrtebd_mps {
   std::vector<void*> Xi;          // per bond, dense cap x cap
   std::vector<void*> xiv;         // per bond, diagonal vector (valid if xi_diag)
   std::vector<char> xi_diag;
+  std::vector<char> chi_pending;  // CBE cut of this bond still on the device (stats slot of its gate)
   double* eps_acc = nullptr;      // per bond, device
   double* stats = nullptr;        // device double[4 * ngates]: one slot per gate bond
   double* layer_eps = nullptr;    // device, per gate bond
@@ -34,6 +35,9 @@ int mps_bond_ws_need(const qrtebd_mps* s, int m, const qrtebd_trunc* tr, size_t*
 // eps into layer_eps[m] and adds it to the bond's accumulated eps.
 int mps_update_bond(qrtebd_mps* s, int m, const qrtebd_trunc* tr, cudaStream_t st, void* ws,
                     size_t ws_bytes);
+// Read back the CBE cuts of the bonds updated since the last call (their stats slots; one
+// synchronisation of the state's stream) into the host bond dimensions.
+int mps_collect_cuts(qrtebd_mps* s);
 // Drop every captured layer graph that references this state (before it is freed).
 void executor_forget_state(qrtebd_mps* s);
 }  // namespace qrtebd

@@ -606,7 +606,9 @@ constexpr int OZ_NT = 64 + 32 * OZ_NEPI;
 
 __global__ void __launch_bounds__(OZ_NT, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, OzEpi epi,
-              int Kp, int a_rows, int b_rows, OzPairs pr, unsigned* err) {
+              int Kp, int a_rows, int b_rows, OzPairs pr, double2* part, unsigned* err) {
+  // grid.z > 1 splits the slice pairs over CTAs (products with few output tiles): CTA z takes
+  // pairs [p_lo, p_hi) and writes its scaled partial tile to part[z] for k_oz_sum
   static_assert(BM * (OZ_BN / 2 + 1) * 16 <= OZ_STAGES * OZ_STAGE, "staged epilogue tile");
   constexpr int HW = OZ_BN / 4;  // real columns per epilogue thread (four column quarters)
   pdl_launch_dependents();
@@ -622,7 +624,9 @@ __global__ void __launch_bounds__(OZ_NT, 1)
   const int n0 = blockIdx.x * OZ_BN, m0 = blockIdx.y * BM;
   const int nk = (Kp + BK - 1) / BK;
   const int cpp = (nk + OZ_CHUNK - 1) / OZ_CHUNK;  // chunks per pair
-  const int npairs = pr.n;
+  const int per_z = (pr.n + (int)gridDim.z - 1) / (int)gridDim.z;
+  const int p_lo = min(pr.n, (int)blockIdx.z * per_z), p_hi = min(pr.n, p_lo + per_z);
+  const int npairs = p_hi - p_lo;
   const int total = npairs * nk;
   const int nchunks = npairs * cpp;
   if (threadIdx.x == 0) {
@@ -651,7 +655,7 @@ __global__ void __launch_bounds__(OZ_NT, 1)
         const int st = it % OZ_STAGES;
         const uint32_t ph = (uint32_t)((it / OZ_STAGES) & 1);
         if (!mbar_wait(&empty[st], ph ^ 1u)) { ok = false; break; }
-        const int p = it / nk, i = it % nk;
+        const int p = p_lo + it / nk, i = it % nk;
         mbar_expect_tx(&full[st], OZ_STAGE);
         tma_load(stage_a(st), &tA, &full[st], i * BK, pr.p[p] * a_rows + m0);
         tma_load(stage_b(st), &tB, &full[st], i * BK, pr.q[p] * b_rows + n0);
@@ -673,10 +677,10 @@ __global__ void __launch_bounds__(OZ_NT, 1)
         if (c >= 2 && !mbar_wait(&acce[b], (uint32_t)(((c >> 1) - 1) & 1))) { ok = false; break; }
         tc_fence_after();
         const uint32_t acc_t = tmem + (uint32_t)(b * OZ_BN);
-        const int p = c / cpp, kc = c % cpp;
+        const int pl = c / cpp, kc = c % cpp;  // pair p_lo + pl
         const int i0 = kc * OZ_CHUNK, i1 = min(nk, i0 + OZ_CHUNK);
         for (int i = i0; i < i1; ++i) {
-          const int it = p * nk + i;
+          const int it = pl * nk + i;
           const int st = it % OZ_STAGES;
           if (!mbar_wait(&full[st], (uint32_t)((it / OZ_STAGES) & 1))) { ok = false; break; }
           tc_fence_after();
@@ -706,7 +710,7 @@ __global__ void __launch_bounds__(OZ_NT, 1)
       const int b = c & 1;
       if (!mbar_wait(&accf[b], (uint32_t)((c >> 1) & 1))) { ok = false; break; }
       tc_fence_after();
-      const int p = c / cpp;
+      const int p = p_lo + c / cpp;
       const double w = ldexp(1.0, -OZ_BITS * (pr.p[p] + pr.q[p] + 2));
 #pragma unroll
       for (int blk = 0; blk < HW / 16; ++blk) {
@@ -725,7 +729,23 @@ __global__ void __launch_bounds__(OZ_NT, 1)
     auto sum = [&](int jj) { return acc[jj]; };
     const bool use_beta = (epi.beta.x != 0.0 || epi.beta.y != 0.0);
     const int ea = (row < epi.M) ? epi.ea[row] : OZ_SENT;
-    if (epi.scn == 1) {
+    if (part) {
+      // this CTA's share of the pairs, exponents applied, into its partial tile
+      if (ok && row < epi.M) {
+        const int col0 = n0 + h * HW;
+        double2* prow = part + ((long long)blockIdx.z * epi.M + row) * epi.Nc;
+#pragma unroll
+        for (int jj = 0; jj < HW / 2; ++jj) {
+          const int n = (col0 >> 1) + jj;
+          if (n < epi.Nc) {
+            const int eb = epi.eb[n];
+            const bool z = (ea == OZ_SENT || eb == OZ_SENT);
+            prow[n] = z ? make_double2(0.0, 0.0)
+                        : make_double2(ldexp(sum(2 * jj), ea + eb), ldexp(sum(2 * jj + 1), ea + eb));
+          }
+        }
+      }
+    } else if (epi.scn == 1) {
       // stage the tile (complex128 results, row exponents applied) in the idle pipeline
       // buffers, then each warp writes whole row segments
       constexpr int LDT = OZ_BN / 2 + 1;  // complex values per staged row (odd: no bank conflicts)
@@ -797,6 +817,31 @@ __global__ void __launch_bounds__(OZ_NT, 1)
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * OZ_BN) : "memory");
   }
+}
+
+// C = alpha sum_z part[z] + beta C for a pair-split emulated product (part: splits x M x N)
+__global__ void k_oz_sum(const double2* part, int splits, OzEpi epi) {
+  pdl_launch_dependents();
+  pdl_wait();
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long MN = (long long)epi.M * epi.Nc;
+  if (idx >= MN) return;
+  const int m = (int)(idx / epi.Nc), n = (int)(idx % epi.Nc);
+  double ar = 0.0, ai = 0.0;
+  for (int z = 0; z < splits; ++z) {
+    const double2 v = part[(long long)z * MN + idx];
+    ar += v.x; ai += v.y;
+  }
+  double2 v;
+  v.x = epi.alpha.x * ar - epi.alpha.y * ai;
+  v.y = epi.alpha.x * ai + epi.alpha.y * ar;
+  double2* c = epi.C + (long long)m * epi.scm + (long long)n * epi.scn;
+  if (epi.beta.x != 0.0 || epi.beta.y != 0.0) {
+    const double2 cv = *c;
+    v.x += epi.beta.x * cv.x - epi.beta.y * cv.y;
+    v.y += epi.beta.x * cv.y + epi.beta.y * cv.x;
+  }
+  *c = v;
 }
 
 // ------------------------------------------------------------------ host
@@ -1044,13 +1089,18 @@ void oz_carve(Arena& ar, int max_m, int max_k, int max_n, OzWorkspace& w) {
   w.b = ar.take<float>(w.b_cap);
   w.ea = ar.take<int>(w.ea_cap);
   w.eb = ar.take<int>(w.eb_cap);
+  w.part_cap = (size_t)1 << 21;  // 32 MB of pair-split partial tiles (complex128)
+  w.part = ar.take<double2>(w.part_cap);
 }
 
 bool oz_gemm_eligible(const GemmArgs<double>& g) {
-  // enough 128 x 128 tiles to fill the GPU (no split-K in this form) and K >= 64; smaller
-  // products stay on the FP64 CUDA cores
+  // products with enough work to amortise the slicing: at least 64 output tiles, or fewer
+  // tiles with a long K whose slice pairs are split over CTAs; the rest stay on the FP64
+  // CUDA cores
   const long long mm = std::max(g.M, g.N), nn = std::min(g.M, g.N);
-  return g.batch == 1 && g.K >= 64 && ceil_div(mm, BM) * ceil_div(2 * nn, OZ_BN) >= 64;
+  if (g.batch != 1 || g.K < 64) return false;
+  const long long tiles = ceil_div(mm, BM) * ceil_div(2 * nn, OZ_BN);
+  return tiles >= 64 || (g.K >= 512 && (double)g.M * g.N * g.K >= (double)(1 << 25));
 }
 
 int oz_gemm(const GemmArgs<double>& g0, OzWorkspace& w, cudaStream_t st, int prof_family) {
@@ -1098,12 +1148,26 @@ int oz_gemm(const GemmArgs<double>& g0, OzWorkspace& w, cudaStream_t st, int pro
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] { attr_err = cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, OZ_SMEM); });
   QR_CUDA_TRY(attr_err);
-  dim3 grid((unsigned)ceil_div(2LL * N, OZ_BN), (unsigned)ceil_div(M, BM), 1);
+  const int nx = (int)ceil_div(2LL * N, OZ_BN), ny = (int)ceil_div(M, BM);
+  // few output tiles: split the slice pairs over CTAs (as many groups as fill the SMs, within
+  // the partial-tile buffer), then sum the partial tiles
+  int splits = 1;
+  if (nx * ny < 148 && w.part) {
+    splits = std::min<int>(pr.n, (int)ceil_div(148, nx * ny));
+    while (splits > 1 && (size_t)splits * M * N > w.part_cap) --splits;
+  }
+  dim3 grid((unsigned)nx, (unsigned)ny, (unsigned)splits);
   {
     // algorithmic work: the complex product (8 M N K real flops), as for every GEMM family
     ProfScope prof(prof_family, st, 8.0 * M * N * K);
     QR_CUDA_TRY(launch_pdl(k_oz_gemm, grid, dim3(OZ_NT), OZ_SMEM, st, ta, tb, epi, 2 * K, M, 2 * N, pr,
-                           device_error_word()));
+                           splits > 1 ? w.part : static_cast<double2*>(nullptr), device_error_word()));
+    note_launch();
+    QR_CUDA_TRY(cudaGetLastError());
+  }
+  if (splits > 1) {
+    QR_CUDA_TRY(launch_pdl(k_oz_sum, dim3((unsigned)ceil_div((long long)M * N, 256)), dim3(256), 0, st,
+                           static_cast<const double2*>(w.part), splits, epi));
     note_launch();
     QR_CUDA_TRY(cudaGetLastError());
   }

@@ -62,7 +62,8 @@ struct OzWorkspace {
   float* b = nullptr;  // OZ_SLICES x 2 max_n rows x ld floats
   int* ea = nullptr;   // per row of A' (max_m)
   int* eb = nullptr;   // per complex column of opB (max_n)
-  size_t a_cap = 0, b_cap = 0, ea_cap = 0, eb_cap = 0;
+  double2* part = nullptr;  // partial tiles of a product whose slice pairs are split over CTAs
+  size_t a_cap = 0, b_cap = 0, ea_cap = 0, eb_cap = 0, part_cap = 0;
 };
 void oz_carve(Arena& ar, int max_m, int max_k, int max_n, OzWorkspace& w);
 // Shapes worth (and able to be) run on the tensor cores in emulated FP64.

@@ -26,6 +26,10 @@ import numpy as np
 
 from . import lib as L
 
+# mirrors of qrtebd.h's QRTEBD_LAYER_BIG_BOND_BYTES / QRTEBD_LAYER_BIG_WORKERS
+LAYER_BIG_BOND_BYTES = 512 << 20
+LAYER_BIG_WORKERS = 8
+
 
 @dataclass
 class Request:
@@ -103,16 +107,24 @@ class QuenchServer:
         import torch
         return torch.cuda.mem_get_info()[1]
 
+    def executor_bytes(self, ws):
+        """Workspace the executor holds once it has run bonds needing `ws` bytes each: bonds
+        above QRTEBD_LAYER_BIG_BOND_BYTES use only the first LAYER_BIG_WORKERS workers, the
+        other workers hold workspaces of at most that size."""
+        if ws > LAYER_BIG_BOND_BYTES:
+            return LAYER_BIG_WORKERS * ws + (self.workers - LAYER_BIG_WORKERS) * LAYER_BIG_BOND_BYTES
+        return self.workers * ws
+
     def footprint(self, req):
         """Bytes admitting `req` would add: its state plus any growth of the shared
-        worker workspaces (the executor keeps one bond workspace per worker stream)."""
-        need_ws = self.workers * workspace_bytes(req, self.precision)
+        worker workspaces."""
+        need_ws = self.executor_bytes(workspace_bytes(req, self.precision))
         return state_bytes(req, self.precision) + max(0, need_ws - self.ws_peak)
 
     def _fits(self, req):
         """(fits now, could ever fit)."""
         need = self.footprint(req) + self.reserve
-        alone = state_bytes(req, self.precision) + self.workers * workspace_bytes(req, self.precision)
+        alone = state_bytes(req, self.precision) + self.executor_bytes(workspace_bytes(req, self.precision))
         return need <= self.mem_free(), alone + self.reserve <= self.mem_total()
 
     def _admit(self, now):
@@ -134,7 +146,7 @@ class QuenchServer:
             full = L.clock_layer_gates(req.L, req.d, req.g, req.dt)
             req.admitted_at = now
             req.status = "running"
-            self.ws_peak = max(self.ws_peak, self.workers * workspace_bytes(req, self.precision))
+            self.ws_peak = max(self.ws_peak, self.executor_bytes(workspace_bytes(req, self.precision)))
             self.active.append((req, mps, half, full))
 
     def _tick(self, t0):
@@ -184,7 +196,8 @@ class QuenchServer:
     def metrics(self, wall):
         lat = []
         updates = 0
-        for r in self.done:
+        # finished requests, and the steps that requests still running at a time cap completed
+        for r in self.done + [a[0] for a in self.active]:
             prev = r.admitted_at
             for t in r.step_done:
                 lat.append(t - prev)
@@ -194,6 +207,8 @@ class QuenchServer:
             updates += per_step * len(r.step_done)
         lat = np.array(lat) if lat else np.zeros(1)
         return {"requests_done": len(self.done), "requests_rejected": len(self.rejected),
+                "requests_running_at_end": len(self.active), "requests_waiting_at_end": len(self.pending),
+                "step_latency_samples": int(lat.size),
                 "wall_s": wall, "bond_updates": updates,
                 "bond_updates_per_s": updates / wall if wall > 0 else 0.0,
                 "p50_step_latency_ms": 1e3 * float(np.percentile(lat, 50)),

@@ -76,3 +76,36 @@ def test_batched_layer_sweeps_is_part_of_the_replayed_shape():
     # identical runs agree (graph replay included); three sweeps truncate less
     assert np.allclose(runs[1], runs[1][0], rtol=1e-12, atol=0)
     assert runs[3][0] < runs[1][0]
+
+
+@pytest.mark.parametrize("prec,tol", [("c128", 1e-10), ("c64_3xtf32", 1e-5)])
+@pytest.mark.parametrize("scheme", ["plain", "cbe"])
+def test_batched_against_oracle(prec, tol, scheme):
+    # several states of different L, d and chi_max evolved by batched layers (CBE cuts kept
+    # on the device and read back once per layer; repeated shapes replayed as graphs) against
+    # the oracle's TEBD of each
+    from oracle import mps as omps
+    from paper_2212_09782_b300 import lib as Lb
+    specs = [(8, 3, 9, 1.5), (6, 4, 16, 0.7), (10, 2, 8, 1.0)]
+    dt, steps = 0.05, 8
+    kw = dict(dchi_min=8) if scheme == "cbe" else {}
+    states, orcs, halves, fulls = [], [], [], []
+    for L, d, chi, g in specs:
+        states.append(Lb.MPS(L, d, chi, precision=prec))
+        orcs.append((omps.product_state(L, d, 0, True), omps.strang_gates(L, d, g, dt, True), chi))
+        halves.append(Lb.clock_layer_gates(L, d, g, dt / 2))
+        fulls.append(Lb.clock_layer_gates(L, d, g, dt))
+    tr = Lb.trunc_default(Lb.CBE if scheme == "cbe" else Lb.PLAIN, 1 << 20, **kw)
+    for _ in range(steps):
+        Lb.tebd_step_batched(states, halves, fulls, tr)
+        for o, (half, full), chi in orcs:
+            omps.tebd_step(o, half, full, scheme=scheme, chi_max=chi, **kw)
+    for s, (o, _g, _chi), (L, d, _c, _gg) in zip(states, orcs, specs):
+        s.sync()
+        Z, _ = clock.clock_operators(d)
+        zg = np.array([s.expectation(m, Z) for m in range(L)])
+        zo = np.array([omps.expectation_1site(o, m, Z) for m in range(L)])
+        assert np.abs(zg - zo).max() < tol, (L, d, np.abs(zg - zo).max())
+        if scheme == "plain":
+            assert s.bond_dims() == o.bond_dims()
+        s.close()

@@ -140,11 +140,13 @@ def test_autotune_bond_table_and_parity():
         L.autotune_clear()
 
 
-@pytest.mark.parametrize("m,n,k", [(2048, 1024, 777), (1500, 600, 2048), (1030, 2100, 333), (5120, 256, 130)])
+@pytest.mark.parametrize("m,n,k", [(2048, 1024, 777), (1500, 600, 2048), (1030, 2100, 333), (5120, 256, 130),
+                                   (128, 256, 5000), (1024, 100, 4097), (300, 130, 2000)])
 @pytest.mark.parametrize("ops", ["nn", "ct", "tc", "nc"])
 def test_zgemm_emulated_fp64(m, n, k, ops):
     # complex128 on the tensor cores (Ozaki slices): products large enough for the tensor-core
-    # path (>= 64 output tiles), ragged in every dimension, transposed and conjugated operands;
+    # path (>= 64 output tiles), and products of few tiles and a long K whose slice pairs are
+    # split over CTAs and summed; ragged in every dimension, transposed and conjugated operands;
     # relative to the FP64 product the error must stay at complex128 level
     import torch
     from paper_2212_09782_b300 import lib as L

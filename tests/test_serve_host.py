@@ -51,3 +51,26 @@ def test_admission_reserves_one_workspace_per_executor_worker():
     assert srv.workers == nw
     req = serve.Request(0, 32, 3, 128, 1.0, 2)
     assert srv.footprint(req) == serve.state_bytes(req, srv.precision) + nw * serve.workspace_bytes(req, srv.precision)
+
+
+def test_big_bonds_hold_only_the_big_workers_workspaces():
+    # a chi = 1024, d = 5 request: its bonds need more than the big-bond threshold, so the
+    # executor holds LAYER_BIG_WORKERS of its workspaces and threshold-sized ones elsewhere
+    srv = serve.QuenchServer(mem_free=lambda: 1 << 40, mem_total=lambda: 1 << 40, reserve_bytes=0)
+    big = serve.Request(0, 128, 5, 1024, 1.0, 2)
+    ws = serve.workspace_bytes(big, srv.precision)
+    assert ws > serve.LAYER_BIG_BOND_BYTES
+    expect = (serve.LAYER_BIG_WORKERS * ws +
+              (srv.workers - serve.LAYER_BIG_WORKERS) * serve.LAYER_BIG_BOND_BYTES)
+    assert srv.footprint(big) == serve.state_bytes(big, srv.precision) + expect
+    assert expect < srv.workers * ws
+
+
+def test_header_constants_mirrored():
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                            "qrtebd.h")).read()
+    assert re.search(r"#define QRTEBD_LAYER_BIG_BOND_BYTES \(512ull << 20\)", hdr)
+    assert serve.LAYER_BIG_BOND_BYTES == 512 << 20
+    assert re.search(r"#define QRTEBD_LAYER_BIG_WORKERS (\d+)", hdr).group(1) == str(serve.LAYER_BIG_WORKERS)
