@@ -702,16 +702,32 @@ __global__ void __launch_bounds__(OZ_NT, 1)
     const int row = m0 + q * 32 + lane;
     // Each chunk is an exact integer of at most 2^24 in magnitude, added into FP64 registers
     // with its pair's power-of-two weight (one DFMA per element and chunk of 1024 K terms).
+    // Chunks of one weight level (p + q; the pairs come ordered by level) are exact integers
+    // of at most 2^24 in magnitude: they are summed exactly in int32 (at most 127 chunks per
+    // flush), and only a finished level sum is added into the FP64 registers with its weight
+    // 2^(-OZ_BITS (p+q+2)). The FP64 pipe, much narrower than the tensor core's chunk rate,
+    // then does one FMA per element and level instead of one per chunk.
     double acc[HW];
+    int iacc[HW];
 #pragma unroll
-    for (int jj = 0; jj < HW; ++jj) acc[jj] = 0.0;
+    for (int jj = 0; jj < HW; ++jj) { acc[jj] = 0.0; iacc[jj] = 0; }
+    int lvl = -1, nin = 0;
+    auto flush = [&]() {
+      if (lvl >= 0 && nin > 0) {
+        const double w = ldexp(1.0, -OZ_BITS * (lvl + 2));
+#pragma unroll
+        for (int jj = 0; jj < HW; ++jj) { acc[jj] = fma((double)iacc[jj], w, acc[jj]); iacc[jj] = 0; }
+      }
+      nin = 0;
+    };
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
       const int b = c & 1;
       if (!mbar_wait(&accf[b], (uint32_t)((c >> 1) & 1))) { ok = false; break; }
       tc_fence_after();
       const int p = p_lo + c / cpp;
-      const double w = ldexp(1.0, -OZ_BITS * (pr.p[p] + pr.q[p] + 2));
+      const int l = pr.p[p] + pr.q[p];
+      if (l != lvl || nin == 127) { flush(); lvl = l; }
 #pragma unroll
       for (int blk = 0; blk < HW / 16; ++blk) {
         uint32_t r[16];
@@ -719,12 +735,14 @@ __global__ void __launch_bounds__(OZ_NT, 1)
         TMEM_LD16(taddr, r);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int jj = 0; jj < 16; ++jj) acc[blk * 16 + jj] = fma((double)__uint_as_float(r[jj]), w, acc[blk * 16 + jj]);
+        for (int jj = 0; jj < 16; ++jj) iacc[blk * 16 + jj] += __float2int_rn(__uint_as_float(r[jj]));
       }
+      ++nin;
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&acce[b]);
     }
+    flush();
     if (!ok && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
     auto sum = [&](int jj) { return acc[jj]; };
     const bool use_beta = (epi.beta.x != 0.0 || epi.beta.y != 0.0);
@@ -1138,10 +1156,11 @@ int oz_gemm(const GemmArgs<double>& g0, OzWorkspace& w, cudaStream_t st, int pro
   CUtensorMap ta, tb;
   QR_TRY(make_map(&ta, w.a, OZ_SLICES * M, 2 * K, ld, BM));
   QR_TRY(make_map(&tb, w.b, OZ_SLICES * 2 * N, 2 * K, ld, OZ_BN));
+  // the slice pairs p + q <= OZ_SLICES - 1, ordered by level p + q (the kernel sums a level's
+  // chunks in integers before one FP64 add)
   OzPairs pr{};
-  for (int p = 0; p < OZ_SLICES; ++p)
-    for (int q = 0; q < OZ_SLICES; ++q)
-      if (p + q <= OZ_SLICES - 1) { pr.p[pr.n] = (signed char)p; pr.q[pr.n] = (signed char)q; ++pr.n; }
+  for (int l = 0; l <= OZ_SLICES - 1; ++l)
+    for (int p = 0; p <= l; ++p) { pr.p[pr.n] = (signed char)p; pr.q[pr.n] = (signed char)(l - p); ++pr.n; }
   OzEpi epi{g.C, g.scm, g.scn, make_double2(g.alpha.x, g.alpha.y), make_double2(g.beta.x, g.beta.y), M, N,
             w.ea, w.eb};
   static std::once_flag once;
