@@ -264,7 +264,7 @@ int qrtebd_apply_gate_layer_batched(qrtebd_mps* const* states, int nstates, int 
  * other bonds of such a layer on the rest), so a caller budgeting device memory for batched
  * layers (e.g. an admission policy) reserves QRTEBD_LAYER_BIG_WORKERS of its largest
  * workspaces plus, for the rest, workspaces of at most QRTEBD_LAYER_BIG_BOND_BYTES. */
-#define QRTEBD_LAYER_BIG_BOND_BYTES (512ull << 20)
+#define QRTEBD_LAYER_BIG_BOND_BYTES (1024ull << 20)
 #define QRTEBD_LAYER_BIG_WORKERS 8
 int qrtebd_layer_workers(void);
 /* Load a site tensor / bond matrix from host complex128 data (e.g. a random

@@ -27,7 +27,7 @@ import numpy as np
 from . import lib as L
 
 # mirrors of qrtebd.h's QRTEBD_LAYER_BIG_BOND_BYTES / QRTEBD_LAYER_BIG_WORKERS
-LAYER_BIG_BOND_BYTES = 512 << 20
+LAYER_BIG_BOND_BYTES = 1024 << 20
 LAYER_BIG_WORKERS = 8
 
 

@@ -71,6 +71,6 @@ def test_header_constants_mirrored():
     import re
     hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
                             "qrtebd.h")).read()
-    assert re.search(r"#define QRTEBD_LAYER_BIG_BOND_BYTES \(512ull << 20\)", hdr)
-    assert serve.LAYER_BIG_BOND_BYTES == 512 << 20
+    assert re.search(r"#define QRTEBD_LAYER_BIG_BOND_BYTES \(1024ull << 20\)", hdr)
+    assert serve.LAYER_BIG_BOND_BYTES == 1024 << 20
     assert re.search(r"#define QRTEBD_LAYER_BIG_WORKERS (\d+)", hdr).group(1) == str(serve.LAYER_BIG_WORKERS)
