@@ -15,6 +15,9 @@ householder a textbook Householder QR used to cross-check the LAPACK QR on tiny 
 mps         finite and uniform MPS in right-isometric form (Eq. 1, Fig. 1) and the
             Strang-split TEBD driver (Fig. 2a)
 exact       state-vector references: Trotterised state vector and Krylov evolution
+symmetric   CBE with Z_d charge sectors (Sec. III, closing paragraphs): the clock model in
+            the charge (Fourier) basis, per-block expansion, one cut over all blocks that
+            sets each block's dimension, and a finite-chain driver
 
 Every function runs in complex128 / float64. Library primitives (matmul, LAPACK
 QR, eigh, SVD, expm) serve as single steps; nothing is blocked, fused or reordered

@@ -89,3 +89,44 @@ def random_right_canonical_mps(L, d, chi_max, seed):
         x = np.sort(r.random(dims[b]))[::-1] + 1e-3
         Xi.append(x / np.linalg.norm(x))
     return dims, B, Xi
+
+
+# ------------------------------------------------------------------ Z_d charge sectors
+def random_charges(r, n, d, sort=True):
+    """n bond charges drawn uniformly from 0..d-1 (sorted: each sector a contiguous run)."""
+    c = r.integers(0, d, n)
+    return np.sort(c) if sort else c
+
+
+def charge_rule_theta(charge_l, charge_r, d):
+    """Boolean (chi_l, d, d, chi_r) pattern c_l(alpha) + i + j = c_r(delta) (mod d) of a
+    charge-conserving two-site block."""
+    cl, cr = np.asarray(charge_l), np.asarray(charge_r)
+    s = (cl[:, None, None, None] + np.arange(d)[None, :, None, None]
+         + np.arange(d)[None, None, :, None]) % d
+    return s == cr[None, None, None, :]
+
+
+def symmetric_theta(r, charge_l, charge_r, d):
+    """Complex Gaussian theta' on the charge-conserving pattern, zero elsewhere, unit norm."""
+    m = charge_rule_theta(charge_l, charge_r, d)
+    th = complex_gaussian(r, m.shape) * m
+    return th / np.linalg.norm(th)
+
+
+def charge_conserving_unitary(r, d, scale=None):
+    """A d^2 x d^2 unitary that keeps i + j (mod d): one random unitary per pair-charge block
+    (Haar-like), or exp(-i scale H) of a random block-diagonal Hermitian H when scale is set."""
+    t = np.add.outer(np.arange(d), np.arange(d)).reshape(-1) % d
+    U = np.zeros((d * d, d * d), np.complex128)
+    for q in range(d):
+        idx = np.nonzero(t == q)[0]
+        n = len(idx)
+        if scale is None:
+            blk = random_unitary(r, n)
+        else:
+            A = complex_gaussian(r, (n, n))
+            w, V = np.linalg.eigh((A + A.conj().T) / 2)
+            blk = (V * np.exp(-1j * scale * w)) @ V.conj().T
+        U[np.ix_(idx, idx)] = blk
+    return U
