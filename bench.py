@@ -745,6 +745,83 @@ def run_cbe_eig(args):
     return 0
 
 
+def run_sym(args):
+    """Charge-sector CBE (Sec. III with Z_d charges) at chi = --chi, d = --d: theta' of the C2
+    shape restricted to the Z_d charge rule (bond charges drawn uniformly and sorted, so each
+    block is chi x chi and holds 1/d of the entries), a random charge-conserving gate, the
+    middle bond's chi states spread over the charges (chi_q ~ chi/d, eta_q = chi_q + 100),
+    chi_max = chi. Updates/s of qrtebd_sym_bond_update beside the dense CBE update on the same
+    theta' (eta = chi + 103), and the result against the oracle on the same inputs."""
+    import torch
+    from paper_2212_09782_b300 import lib as L
+    from paper_2212_09782_b300 import workloads as W
+    sys.path.insert(0, ROOT)
+    from oracle import symmetric as osym
+    chi, d, prec = args.chi, args.d, args.precision
+    r = W.rng(W.BASE_SEED + 31)
+    cl, cm, cr = (W.random_charges(r, chi, d) for _ in range(3))
+    th = W.symmetric_theta(r, cl, cr, d)
+    U = W.charge_conserving_unitary(r, d)
+    cdt = torch.complex128 if prec.startswith("c128") else torch.complex64
+    th_d = torch.from_numpy(th).to(device="cuda", dtype=cdt)
+    gate = torch.from_numpy(U).cuda()
+    tr = L.trunc_default(L.CBE, chi)
+    up = L.SymBondUpdater(prec, d, cl, cm, cr, tr, xi_kind=0)
+    dense = L.BondUpdater(prec, chi, d, chi, chi, tr, xi_kind=0, theta_given=True)
+    bn_d = torch.zeros(chi * d * chi, dtype=cdt, device="cuda")  # not read by CBE (Y0 from theta~)
+
+    def timed(fn, n):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ts = []
+        for _ in range(n):
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return ts
+    sym_fn = lambda: up.run(gate, theta=th_d)
+    den_fn = lambda: dense.run(gate, bn_d, theta=th_d)
+    timed(sym_fn, args.warmup)
+    n0 = L.launch_count()
+    ts = timed(sym_fn, args.steps)
+    launches = (L.launch_count() - n0) / max(args.steps, 1)
+    L.stream_check()
+    Bm, x, Bn, ch, st = up.outputs()
+    got_S = np.real(x.cpu().numpy().astype(np.complex128))
+    got_eps = float(st[0].item())
+    timed(den_fn, args.warmup)
+    td = timed(den_fn, max(3, args.steps // 2))
+    L.stream_check()
+    line = {"metric": f"charge-sector CBE bond updates/s, chi={chi} d={d} (Z_{d} charges)",
+            "value": 1e3 / statistics.median(ts), "unit": "bond updates/s", "higher_is_better": True,
+            "ms_per_step": statistics.median(ts), "ms_p99": sorted(ts)[max(0, int(0.99 * len(ts)) - 1)],
+            "dense_cbe_ms": statistics.median(td), "speedup_vs_dense_cbe": statistics.median(td) / statistics.median(ts),
+            "chi_new": up.info.chi_new, "eta_sum": up.info.eta, "chi_sector": up.chi_sector.tolist(),
+            "gpu_launches_per_update": launches, "steps": args.steps, "warmup": args.warmup,
+            "n_gpus": 1, "dtype": prec, "data": "synthetic",
+            "config": {"workload": f"theta' (chi={chi}, d={d}, d, chi) on the Z_{d} charge rule, "
+                                   f"unit norm; chi_max={chi}, dchi_min=100, dchi_frac=0.1",
+                       "l2": "theta' larger than L2"}}
+    if not args.no_cpu_baseline:
+        thr = th.astype(np.complex64).astype(np.complex128) if not prec.startswith("c128") else th
+        t0 = time.perf_counter()
+        o = osym.sym_qr_update(thr, None, U, cl, cm, cr, chi_max=chi)
+        t_or = time.perf_counter() - t0
+        ok = np.array_equal(up.chi_sector, o["chi_sector"])
+        errS = None
+        if ok:
+            errS = max(float(np.max(np.abs(got_S[o["charge_new"] == q] - o["xi_new"][o["charge_new"] == q])))
+                       for q in range(d) if np.any(o["charge_new"] == q))
+        line["error_vs_oracle"] = {"chi_sector_equal": bool(ok), "max_abs_dS": errS,
+                                   "abs_deps": abs(got_eps - o["eps"])}
+        line["cpu_baseline"] = {"value": 1.0 / t_or, "unit": "bond updates/s", "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": "one update (complex128 NumPy/LAPACK)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_c1(args):
     """C1: finite chain L = 16, d = 3, g = 1.5, quench from |0...0>, Strang dt = 0.05,
     20 steps, chi_max = 32, plain QR, complex128. The whole run on the GPU (wall time,
@@ -860,7 +937,8 @@ def main():
                     help="bond workload: skip the SVD / EIG comparison arms after the timed runs")
     ap.add_argument("--no-peaks", action="store_true",
                     help="skip the TF32 / FP64 matmul peak measurement (and the tc_roofline it feeds)")
-    ap.add_argument("--workload", choices=["bond", "chain", "serve", "svd", "c1", "c3", "cbe_eig"],
+    ap.add_argument("--workload", choices=["bond", "chain", "serve", "svd", "c1", "c3", "cbe_eig",
+                                           "sym"],
                     default="bond")
     ap.add_argument("--eig-n", type=int, default=1126, help="cbe_eig workload: the order n")
     ap.add_argument("--c3-steps", type=int, default=200)
@@ -901,6 +979,8 @@ def main():
         return run_c1(args)
     if args.workload == "c3":
         return run_c3(args)
+    if args.workload == "sym":
+        return run_sym(args)
     if args.workload == "cbe_eig":
         return run_cbe_eig(args)
     return run_ours(args)

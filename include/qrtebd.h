@@ -157,6 +157,65 @@ int qrtebd_bond_workspace_size(int precision, int chi_l, int d, int chi_m, int c
 int qrtebd_bond_update(const qrtebd_bond_io* io, const qrtebd_trunc* tr, void* stream,
                        qrtebd_bond_info* info);
 
+/* ------------------------------------------ CBE with Z_d charge sectors (Sec. III, last part)
+ * With a global Z_d symmetry (for the clock model, Eqs. 2-3, the product of X over all sites,
+ * in the basis where X is diagonal) every bond index carries a charge in 0..d-1 and the
+ * tensors are block-sparse: B^i_{alpha beta} != 0 only if c(alpha) + i = c(beta) (mod d).
+ * CBE expands every block of the central bond on its own and one cut over the Schmidt
+ * values of all blocks picks chi~ and with it each block's dimension chi~_q, so the block
+ * dimensions follow the state instead of being fixed before the step (Sec. III).
+ *
+ * Block q of theta~ (a (chi_l d) x (d chi_r) matrix, rows alpha*d + i, columns j*chi_r + delta)
+ * holds the rows with c_l(alpha) + i = q and the columns with c_r(delta) - j = q, each in that
+ * dense order. Per block: eta_q = min(chi_q + dchi_q, rows_q, cols_q), chi_q = the number of
+ * old middle-bond states of charge q, dchi_q = max(tr->dchi_min, ceil(tr->dchi_frac chi_q));
+ * Y0_q = the first eta_q rows of theta~_q; steps (i)-(iv) as in qrtebd_bond_update. The cut:
+ * all Schmidt values in one descending list (equal values ordered by charge, then position),
+ * then the rule of qrtebd_trunc (svd_min relative to the norm of all of them, chi_max,
+ * eps_target, never inside a multiplet). The new middle bond lists the kept states block by
+ * block in increasing charge, each block in descending Schmidt order. eps = 1 - kept /
+ * ||theta~||^2 over all blocks (tr->eps_explicit is ignored). */
+typedef struct qrtebd_sym_bond_io {
+  int precision;           /* any QRTEBD_C* precision */
+  int chi_l, d, chi_m, chi_r; /* 2 <= d <= 16 */
+  const int* charge_l;     /* HOST int[chi_l]: charges of the left bond, 0..d-1 */
+  const int* charge_m;     /* HOST int[chi_m]: charges of the old middle bond (sets chi_q) */
+  const int* charge_r;     /* HOST int[chi_r]: charges of the right bond */
+  int xi_kind;             /* 0: Xi = identity; 2: diagonal, xi holds chi_l entries */
+  const void* xi;
+  const void* theta;       /* theta' (chi_l, d, d, chi_r), device, storage type; only the
+                              entries with c_l(alpha) + i + j = c_r(delta) are read */
+  const void* bm;          /* with theta NULL: B^m (chi_l, d, chi_m) and B^n (chi_m, d, chi_r), */
+  const void* bn;          /* device, and theta' = B^m B^n is formed first (one dense product) */
+  const void* gate;        /* U, device complex128 d^2 x d^2, keeping i + j (mod d): only its
+                              entries with i + j = i' + j' are read */
+  void* bm_out;            /* B~^m (chi_l, d, chi_new), zero outside the charge rule;
+                              capacity chi_l*d*cap, cap = min(chi_max, eta_sum) */
+  void* xi_out;            /* the diagonal of Xi~ (chi_new entries, storage type, unit norm) */
+  void* bn_out;            /* B~^n (chi_new, d, chi_r); capacity cap*d*chi_r */
+  int* charge_out;         /* HOST int[cap]: charges of the new middle bond */
+  int* chi_sector_out;     /* optional HOST int[d]: chi~_q */
+  double* stats_out;       /* optional device double[4]: eps, ||theta~||^2, kept, chi_new */
+  void* workspace;         /* device scratch of qrtebd_sym_bond_workspace_size bytes */
+  size_t workspace_bytes;
+} qrtebd_sym_bond_io;
+
+/* Workspace bytes and eta_sum = sum_q eta_q for these charges (host call, no GPU work).
+ * Errors: INVALID_ARG for d outside 2..16, a charge outside 0..d-1, a scheme other than
+ * CBE, tr->eta != 0 or xi_kind 1. */
+int qrtebd_sym_bond_workspace_size(int precision, int chi_l, int d, int chi_m, int chi_r,
+                                   const int* charge_l, const int* charge_m, const int* charge_r,
+                                   int xi_kind, int theta_given, const qrtebd_trunc* tr,
+                                   size_t* bytes, int* eta_sum);
+
+/* One charge-conserving CBE update, enqueued on `stream`: theta~'_q = U theta' gathered block
+ * by block (one kernel), the blocks' dense CBE updates one after another, one cut over all
+ * blocks and the scatter into the dense outputs on the device; the call synchronises `stream`
+ * once at the end to fill charge_out / chi_sector_out and info (eta = eta_sum, chi_new).
+ * Errors as qrtebd_bond_update. */
+int qrtebd_sym_bond_update(const qrtebd_sym_bond_io* io, const qrtebd_trunc* tr, void* stream,
+                           qrtebd_bond_info* info);
+
 /* Synchronise `stream` and report any device-side error word (TIMEOUT / NUMERIC)
  * set by kernels since the last check. */
 int qrtebd_stream_check(void* stream);
@@ -323,8 +382,10 @@ int qrtebd_zgemm_noalloc(int precision, int m, int n, int k, const void* A, long
  * descending order, and Vh (device complex128 n x n, row-major) the conjugated
  * eigenvectors as rows: Rz Rz^dag = Vh^dag diag(w) Vh. Complex64 precisions: one-sided
  * Jacobi in FP32 on the rows of Rz (FP64 norms and rotation parameters), one cooperative
- * launch; C128: Rz Rz^dag in FP64, then two-sided FP64 Jacobi. sweeps (device int, may be
- * NULL): Jacobi sweeps run by the one-sided solver (41 = stopped unconverged; 0 for C128).
+ * launch; C128 / C128_OZ: the same one-sided Jacobi with FP64 rows, sums and rotations (one
+ * cooperative launch) for n up to ~6800 (a pair of row blocks fits shared memory), beyond
+ * that Rz Rz^dag in FP64 and a two-sided FP64 Jacobi. sweeps (device int, may be NULL):
+ * Jacobi sweeps run by a one-sided solver (41 = stopped unconverged; 0 for the two-sided).
  * workspace: device, at least qrtebd_cbe_decompose_workspace_size bytes, else OOM.
  * INVALID_ARG for n < 1, ldr < n or a null pointer. Enqueued on `stream`. */
 size_t qrtebd_cbe_decompose_workspace_size(int precision, int n);
@@ -381,6 +442,13 @@ size_t qrtebd_qr_workspace_size(int precision, int m, int n);
  * at the outer site of a finite chain's end bonds (wl or wr = 1). */
 int qrtebd_clock_bond_gate(int d, double g, double wl, double wr, double tau_re, double tau_im,
                            double* U_out);
+
+/* Host-only: the same gate in the charge basis of the Z_d symmetry, (F x F)^dag U (F x F) with
+ * F[n][k] = w^(nk) / sqrt(d) (column k: the eigenvector of X with eigenvalue w^k, so Z raises
+ * the charge k by one); the entries with i + j != i' + j' (mod d), rounding noise of the basis
+ * change, are set to zero. */
+int qrtebd_clock_bond_gate_charge(int d, double g, double wl, double wr, double tau_re,
+                                  double tau_im, double* U_out);
 
 /* ------------------------------------------------------------ instrumentation */
 /* Kernel families timed by qrtebd_profile_read. */

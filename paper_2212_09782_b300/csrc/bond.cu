@@ -325,7 +325,7 @@ template <typename T> int qr_gemm_thunk(const GemmArgs<T>& g, cudaStream_t st, v
 
 template <typename T>
 int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t st,
-                  qrtebd_bond_info* info, size_t* bytes, bool sync_chi) {
+                  qrtebd_bond_info* info, size_t* bytes, bool sync_chi, bool theta_gated) {
   const int chiL = io->chi_l, d = io->d, chiM = io->chi_m, chiR = io->chi_r;
   const bool measuring = (bytes != nullptr);
   const long long mL = (long long)chiL * d, nR = (long long)d * chiR;
@@ -342,13 +342,15 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
   if (!measuring) { ar.base = static_cast<char*>(io->workspace); ar.cap = io->workspace_bytes; }
 
   cx<T>* theta_p = theta_given ? nullptr : ar.take<cx<T>>((size_t)mL * nR);
-  cx<T>* theta_tp = ar.take<cx<T>>((size_t)mL * nR);
+  // theta_gated: io->theta already holds theta~' = U theta' (read only from here on)
+  cx<T>* theta_tp = theta_gated ? const_cast<cx<T>*>(static_cast<const cx<T>*>(io->theta))
+                                : ar.take<cx<T>>((size_t)mL * nR);
   cx<T>* theta_t = (io->xi_kind == 0) ? theta_tp : ar.take<cx<T>>((size_t)mL * nR);
   cx<T>* X = ar.take<cx<T>>((size_t)mL * eta);
   cx<T>* Q = ar.take<cx<T>>((size_t)mL * eta);
   cx<T>* Z = ar.take<cx<T>>((size_t)nR * eta);
   cx<T>* Qz = ar.take<cx<T>>((size_t)nR * eta);
-  cx<T>* Ut = (d > 5) ? ar.take<cx<T>>((size_t)d * d * d * d) : nullptr;
+  cx<T>* Ut = (d > 5 && !theta_gated) ? ar.take<cx<T>>((size_t)d * d * d * d) : nullptr;
   QrScratch<T> qs;
   qr_carve<T>(ar, (int)std::max(mL, nR), eta, qs);
   double* partial = ar.take<double>(RED_BLOCKS);
@@ -364,6 +366,9 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
   // CBE: the decomposition of L^dag L. complex128: two-sided FP64 Jacobi on M = Rz Rz^dag;
   // complex64: one-sided FP32 Jacobi on the rows of Rz (M is never formed)
   constexpr bool kOneSided = std::is_same<T, float>::value;
+  // complex128: the one-sided FP64 Jacobi whenever a block pair of rows fits shared memory,
+  // else the two-sided solver on M = Rz Rz^dag
+  const bool sj64 = !kOneSided && cbe && svd64_supported(eta);
   double2* M = nullptr; double2* Vh = nullptr; double* w = nullptr; double2* eig_scr = nullptr;
   double* Sv = nullptr; cx<T>* Vt = nullptr; int* chi_dev = nullptr; char* sj_work = nullptr;
   cx<T>* Bn_full = nullptr; cx<T>* Bm_full = nullptr;
@@ -378,8 +383,8 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
     // and their first chi~ rows / columns are copied into the outputs' layout
     Bn_full = ar.take<cx<T>>((size_t)eta * nR);
     Bm_full = ar.take<cx<T>>((size_t)mL * eta);
-    if (kOneSided) {
-      sj_bytes = svd32_work_bytes(eta);
+    if (kOneSided || sj64) {
+      sj_bytes = kOneSided ? svd32_work_bytes(eta) : svd64_work_bytes(eta);
       sj_work = ar.take<char>(sj_bytes);
     } else {
       M = ar.take<double2>((size_t)eta * eta);
@@ -438,7 +443,15 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
   // (i) gate (and diagonal Xi)
   const double2* U = static_cast<const double2*>(io->gate);
   const cx<T>* xi = static_cast<const cx<T>*>(io->xi);
-  if (d <= 5) {
+  if (theta_gated) {
+    if (io->xi_kind == 2) {
+      long long tot = mL * nR;
+      k_scale_rows<T><<<(unsigned)ceil_div(tot, 256), 256, 0, st>>>(theta_tp, theta_t, xi, chiL,
+                                                                   d * nR);
+      note_launch();
+      QR_CUDA_TRY(cudaGetLastError());
+    }
+  } else if (d <= 5) {
     QR_TRY(launch_gate<T>(th, theta_tp, U, chiL, d, chiR, io->xi_kind == 2 ? xi : nullptr,
                           io->xi_kind == 2 ? theta_t : nullptr, st));
   } else {
@@ -561,6 +574,9 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
     if constexpr (kOneSided) {
       QR_TRY(svd_rows_jacobi32(reinterpret_cast<const float2*>(Z), eta, eta, w, Vh, sj_work, sj_bytes,
                                st, err));
+    } else if (sj64) {
+      QR_TRY(svd_rows_jacobi64(reinterpret_cast<const double2*>(Z), eta, eta, w, Vh, sj_work, sj_bytes,
+                               st, err));
     } else {
       double2* Rz64 = M;  // reuse: first convert Rz, then form M in Vh's buffer, swap
       k_to_c128<T><<<(unsigned)ceil_div(ee, 256), 256, 0, st>>>(Z, Rz64, ee);
@@ -656,9 +672,10 @@ int choose_eta(const qrtebd_trunc* tr, int chi_l, int d, int chi_m, int chi_r) {
 }
 
 int bond_update(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t st,
-                qrtebd_bond_info* info, size_t* bytes, bool sync_chi) {
+                qrtebd_bond_info* info, size_t* bytes, bool sync_chi, bool theta_gated) {
   if (!io || !tr) return QRTEBD_ERR_INVALID_ARG;
-  if (io->chi_l < 1 || io->d < 2 || io->chi_m < 1 || io->chi_r < 1 || tr->chi_max < 1)
+  if (theta_gated && !bytes && !io->theta) return QRTEBD_ERR_INVALID_ARG;
+  if (io->chi_l < 1 || io->d < (theta_gated ? 1 : 2) || io->chi_m < 1 || io->chi_r < 1 || tr->chi_max < 1)
     return QRTEBD_ERR_INVALID_ARG;
   if (io->xi_kind < 0 || io->xi_kind > 2) return QRTEBD_ERR_INVALID_ARG;
   if (tr->scheme != QRTEBD_PLAIN && tr->scheme != QRTEBD_CBE) return QRTEBD_ERR_INVALID_ARG;
@@ -667,16 +684,16 @@ int bond_update(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t s
     return QRTEBD_ERR_INVALID_ARG;
   }
   if (!bytes) {
-    if (!io->bn || !io->gate || !io->bm_out || !io->xi_out || !io->bn_out) return QRTEBD_ERR_INVALID_ARG;
+    if (!io->bn || (!io->gate && !theta_gated) || !io->bm_out || !io->xi_out || !io->bn_out) return QRTEBD_ERR_INVALID_ARG;
     if (!io->theta && !io->bm) return QRTEBD_ERR_INVALID_ARG;
     if (io->xi_kind != 0 && !io->xi) return QRTEBD_ERR_INVALID_ARG;
   }
   switch (io->precision) {
     case QRTEBD_C128:
-    case QRTEBD_C128_OZ: return bond_update_t<double>(io, tr, st, info, bytes, sync_chi);
+    case QRTEBD_C128_OZ: return bond_update_t<double>(io, tr, st, info, bytes, sync_chi, theta_gated);
     case QRTEBD_C64_3XTF32:
     case QRTEBD_C64_TF32:
-    case QRTEBD_C64_FP32: return bond_update_t<float>(io, tr, st, info, bytes, sync_chi);
+    case QRTEBD_C64_FP32: return bond_update_t<float>(io, tr, st, info, bytes, sync_chi, theta_gated);
     default: return QRTEBD_ERR_INVALID_ARG;
   }
 }

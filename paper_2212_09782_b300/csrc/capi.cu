@@ -419,9 +419,11 @@ size_t qrtebd_qr_workspace_size(int precision, int m, int n) {
 
 size_t qrtebd_cbe_decompose_workspace_size(int precision, int n) {
   if (n < 1) return 0;
-  if (prec_is_c128(precision))
+  if (prec_is_c128(precision)) {
+    if (svd64_supported(n)) return svd64_work_bytes(n);
     return (2 * (size_t)n * n + herm_eig_scratch_elems(n)) * sizeof(double2) +
            gemm_simt_scratch_elems(n, n, n, 1) * sizeof(double2) + 1024;
+  }
   return svd32_work_bytes(n);
 }
 
@@ -435,7 +437,10 @@ int qrtebd_cbe_decompose(int precision, int n, const void* Rz, long long ldr, do
   if (!prec_is_c128(precision))
     return svd_rows_jacobi32(static_cast<const float2*>(Rz), ldr, n, w, static_cast<double2*>(Vh),
                              workspace, workspace_bytes, st, err, sweeps);
-  // complex128: M = Rz Rz^dag (FP64), two-sided Jacobi
+  if (svd64_supported(n))
+    return svd_rows_jacobi64(static_cast<const double2*>(Rz), ldr, n, w, static_cast<double2*>(Vh),
+                             workspace, workspace_bytes, st, err, sweeps);
+  // complex128 beyond the one-sided solver's shared memory: M = Rz Rz^dag (FP64), two-sided Jacobi
   const size_t nn = (size_t)n * n;
   double2* M = static_cast<double2*>(workspace);
   double2* M2 = M + nn;
@@ -482,6 +487,34 @@ int qrtebd_clock_bond_gate(int d, double g, double wl, double wr, double tau_re,
     for (int c = 0; c < n; ++c) {
       zc s = 0;
       for (int k = 0; k < n; ++k) s += V[(size_t)r * n + k] * std::exp(-I * tau * w[k]) * std::conj(V[(size_t)c * n + k]);
+      U_out[2 * ((size_t)r * n + c)] = s.real();
+      U_out[2 * ((size_t)r * n + c) + 1] = s.imag();
+    }
+  return QRTEBD_OK;
+}
+
+int qrtebd_clock_bond_gate_charge(int d, double g, double wl, double wr, double tau_re,
+                                  double tau_im, double* U_out) {
+  if (d < 2 || d > 64 || !U_out) return QRTEBD_ERR_INVALID_ARG;
+  const int n = d * d;
+  std::vector<double> Uz(2 * (size_t)n * n);
+  QR_TRY(qrtebd_clock_bond_gate(d, g, wl, wr, tau_re, tau_im, Uz.data()));
+  const double pi = 3.14159265358979323846;
+  // F2[(a b), (i j)] = F[a][i] F[b][j], F[a][i] = w^(a i) / sqrt(d)
+  auto F = [&](int a, int i) { return std::polar(1.0 / std::sqrt((double)d), 2 * pi * ((a * i) % d) / d); };
+  std::vector<zc> T((size_t)n * n);  // T = U F2
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) {
+      zc s = 0;
+      for (int k = 0; k < n; ++k)
+        s += zc(Uz[2 * ((size_t)r * n + k)], Uz[2 * ((size_t)r * n + k) + 1]) * F(k / d, c / d) * F(k % d, c % d);
+      T[(size_t)r * n + c] = s;
+    }
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) {
+      zc s = 0;
+      if ((r / d + r % d) % d == (c / d + c % d) % d)
+        for (int k = 0; k < n; ++k) s += std::conj(F(k / d, r / d) * F(k % d, r % d)) * T[(size_t)k * n + c];
       U_out[2 * ((size_t)r * n + c)] = s.real();
       U_out[2 * ((size_t)r * n + c) + 1] = s.imag();
     }

@@ -546,6 +546,232 @@ int svd_rows_jacobi32(const float2* Rz, long long ldr, int n, double* w, double2
   return QRTEBD_OK;
 }
 
+namespace {
+
+// ---------------------------------------------------------------- one-sided Jacobi, FP64
+// The complex128 form of svd_rows_jacobi32: the same blocked one-sided Jacobi on the rows of
+// Rz (block pairs in the round-robin order, one CTA per block pair, a bounded grid barrier
+// between rounds, the whole iteration one cooperative launch), with the rows, the Gram sums
+// and the rotations in FP64. It replaces the two-sided solver for CBE step (iv) in
+// complex128: that one issues three launches per rotation step and reads the off-diagonal
+// norm back once per sweep (~10^4 launches and ~10 stream synchronisations at n ~ 300).
+// The singular values of L come out with the relative accuracy of the FP64 rows, and
+// L^dag L is never formed.
+constexpr int SJ64_BRMAX = 4;
+constexpr int SJ64_WPP = 2;
+constexpr int SJ64_NT = 32 * SJ64_WPP * SJ64_BRMAX;  // 256
+constexpr int SJ64_MAX_SWEEPS = 40;
+struct Sj64Ctl {
+  unsigned bar[2];
+  unsigned rot[SJ64_MAX_SWEEPS];
+  int sweeps;
+};
+
+__host__ __device__ inline size_t sj64_smem_bytes(int n, int br) {
+  return (size_t)2 * br * n * sizeof(double2) + (size_t)(2 * SJ64_BRMAX) * (2 * SJ64_BRMAX) * sizeof(double2);
+}
+
+__global__ void __launch_bounds__(SJ64_NT, 1) k_sj64_sweeps(double2* R, double2* Jt, int n, int br, int nb,
+                                                            double tol, Sj64Ctl* ctl, unsigned* err) {
+  extern __shared__ __align__(16) unsigned char sj64_sm[];
+  double2* X = reinterpret_cast<double2*>(sj64_sm);            // [2 br][n]
+  double2* Wm = X + (size_t)2 * br * n;                         // [2 br][2 br]
+  __shared__ double red[SJ64_BRMAX][SJ64_WPP][2];               // per pair slot and warp: g
+  __shared__ double nrm[2 * SJ64_BRMAX];                        // ||row||^2 of the rows held
+  __shared__ unsigned s_cnt, s_vis;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int quad = warp / SJ64_WPP, qw = warp % SJ64_WPP;
+  const int qt = qw * 32 + lane;
+  const int nbp = (nb % 2) ? nb + 1 : nb;
+
+  auto visit = [&](int nrow, bool cross, auto grow) {
+    for (int idx = tid; idx < nrow * n; idx += SJ64_NT) {
+      const int a = idx / n, o = idx - a * n;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                       (unsigned)__cvta_generic_to_shared(X + (size_t)a * n + o)),
+                   "l"(R + (long long)grow(a) * n + o)
+                   : "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    for (int e = tid; e < nrow * nrow; e += SJ64_NT) Wm[e] = make_double2(e / nrow == e % nrow ? 1.0 : 0.0, 0.0);
+    if (tid == 0) s_vis = 0;
+    __syncthreads();
+    for (int a = warp; a < nrow; a += SJ64_NT / 32) {
+      const double2* xr = X + (size_t)a * n;
+      double f = 0.0;
+      for (int i = lane; i < n; i += 32) f = fma(xr[i].x, xr[i].x, fma(xr[i].y, xr[i].y, f));
+      f = warp_sum_d(f);
+      if (lane == 0) nrm[a] = f;
+    }
+    __syncthreads();
+    const int rounds = cross ? br : nrow - 1;
+    const int pairs = cross ? br : nrow / 2;
+    for (int ir = 0; ir < rounds; ++ir) {
+      if (quad < pairs) {
+        int a, b;
+        if (cross) { a = quad; b = br + (quad + ir) % br; }
+        else pair_of(ir, quad, nrow, a, b);
+        double2* xa = X + (size_t)a * n;
+        double2* xb = X + (size_t)b * n;
+        double gr = 0.0, gi = 0.0;  // g = row_a . conj(row_b)
+        for (int i = qt; i < n; i += 32 * SJ64_WPP) {
+          const double2 x = xa[i], y = xb[i];
+          gr = fma(x.x, y.x, fma(x.y, y.y, gr));
+          gi = fma(x.y, y.x, fma(-x.x, y.y, gi));
+        }
+        gr = warp_sum_d(gr);
+        gi = warp_sum_d(gi);
+        if (lane == 0) { red[quad][qw][0] = gr; red[quad][qw][1] = gi; }
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + quad), "n"(32 * SJ64_WPP) : "memory");
+        gr = red[quad][0][0];
+        gi = red[quad][0][1];
+#pragma unroll
+        for (int w = 1; w < SJ64_WPP; ++w) { gr += red[quad][w][0]; gi += red[quad][w][1]; }
+        const double A = nrm[a], B = nrm[b];
+        const double ab = hypot(gr, gi);
+        if (ab > 1e-300 && ab > tol * sqrt(A) * sqrt(B)) {  // slot-uniform
+          const double inv = 1.0 / ab;
+          const double z = (B - A) * (0.5 * inv);
+          const double t = fabs(z) > 1e150 ? 0.5 / z : copysign(1.0, z) / (fabs(z) + sqrt(fma(z, z, 1.0)));
+          const double qq = sqrt(fma(t, t, 1.0));
+          const double c = 1.0 - (t * t) / (qq * (1.0 + qq)), sn = t * c;
+          const double er = sn * (gr * inv), ei = sn * (gi * inv);
+          for (int j2 = qt; j2 < n; j2 += 32 * SJ64_WPP) {
+            const double2 x = xa[j2], y = xb[j2];
+            xa[j2] = make_double2(c * x.x - (er * y.x - ei * y.y), c * x.y - (er * y.y + ei * y.x));
+            xb[j2] = make_double2((er * x.x + ei * x.y) + c * y.x, (er * x.y - ei * x.x) + c * y.y);
+          }
+          if (qw == 0) {
+            if (lane < nrow) {
+              const double2 x = Wm[a * nrow + lane], y = Wm[b * nrow + lane];
+              Wm[a * nrow + lane] = make_double2(c * x.x - (er * y.x - ei * y.y), c * x.y - (er * y.y + ei * y.x));
+              Wm[b * nrow + lane] = make_double2((er * x.x + ei * x.y) + c * y.x, (er * x.y - ei * x.x) + c * y.y);
+            }
+            if (lane == 0) {
+              atomicAdd(&s_vis, 1u);
+              nrm[a] = A - t * ab;
+              nrm[b] = B + t * ab;
+            }
+          }
+        }
+      }
+      __syncthreads();
+    }
+    if (s_vis) {
+      for (int idx = tid; idx < nrow * n; idx += SJ64_NT) {
+        const int a = idx / n, o = idx - a * n;
+        R[(long long)grow(a) * n + o] = X[(size_t)a * n + o];
+      }
+      for (int cc = tid; cc < n; cc += SJ64_NT) {
+        double2 in[2 * SJ64_BRMAX];
+#pragma unroll
+        for (int a = 0; a < 2 * SJ64_BRMAX; ++a)
+          if (a < nrow) in[a] = __ldcg(Jt + (long long)grow(a) * n + cc);
+#pragma unroll
+        for (int a = 0; a < 2 * SJ64_BRMAX; ++a) {
+          if (a < nrow) {
+            double2 o = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int b = 0; b < 2 * SJ64_BRMAX; ++b) {
+              if (b < nrow) {
+                const double2 wv = Wm[a * nrow + b];
+                o.x = fma(wv.x, in[b].x, fma(-wv.y, in[b].y, o.x));
+                o.y = fma(wv.x, in[b].y, fma(wv.y, in[b].x, o.y));
+              }
+            }
+            Jt[(long long)grow(a) * n + cc] = o;
+          }
+        }
+      }
+      if (tid == 0) s_cnt += s_vis;
+    }
+    __syncthreads();
+  };
+
+  for (int sweep = 0; sweep < SJ64_MAX_SWEEPS; ++sweep) {
+    if (tid == 0) s_cnt = 0;
+    if (br > 1) {
+      for (int blk = blockIdx.x; blk < nb; blk += gridDim.x)
+        visit(br, false, [&](int a) { return blk * br + a; });
+      if (!grid_barrier(ctl->bar, gridDim.x, err)) return;
+    }
+    for (int r = 0; r < nbp - 1; ++r) {
+      for (int k = blockIdx.x; k < nbp / 2; k += gridDim.x) {
+        int P, Q;
+        pair_of(r, k, nbp, P, Q);
+        if (Q < nb)
+          visit(2 * br, true, [&](int a) { return a < br ? P * br + a : Q * br + (a - br); });
+      }
+      if (!grid_barrier(ctl->bar, gridDim.x, err)) return;
+    }
+    if (tid == 0 && s_cnt) atomicAdd(&ctl->rot[sweep], s_cnt);
+    if (!grid_barrier(ctl->bar, gridDim.x, err)) return;
+    if (*reinterpret_cast<volatile unsigned*>(&ctl->rot[sweep]) == 0) {
+      if (blockIdx.x == 0 && tid == 0) ctl->sweeps = sweep + 1;
+      return;
+    }
+  }
+  if (blockIdx.x == 0 && tid == 0) ctl->sweeps = SJ64_MAX_SWEEPS + 1;
+}
+
+__global__ void k_eye64_ld(double2* J, int n, int ld) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  const long long r = idx / n, c = idx % n;
+  J[r * ld + c] = make_double2(r == c ? 1.0 : 0.0, 0.0);
+}
+
+// s2[i] = ||r_i||^2 / ||j_i||^2, jn[i] = 1 / ||j_i||, one warp per row (the ratio cancels the
+// drift of a row's norm under rotations that are unitary only to rounding)
+__global__ void k_sj64_norms(const double2* R, const double2* Jt, int n, int ld, double* s2, double* jn) {
+  const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= n) return;
+  double acc = 0.0, accj = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    const double2 x = R[(long long)row * ld + i], y = Jt[(long long)row * ld + i];
+    acc = fma(x.x, x.x, fma(x.y, x.y, acc));
+    accj = fma(y.x, y.x, fma(y.y, y.y, accj));
+  }
+  acc = warp_sum_d(acc);
+  accj = warp_sum_d(accj);
+  if (lane == 0) {
+    s2[row] = accj > 0 ? acc / accj : acc;
+    jn[row] = accj > 0 ? 1.0 / sqrt(accj) : 1.0;
+  }
+}
+
+__global__ void k_sj64_gather(const double2* Jt, const int* order, const double* jn, int n, int ld,
+                              double2* Vh, unsigned* err) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= (long long)n * n) return;
+  const int r = (int)(idx / n), c = (int)(idx % n);
+  const int src = order[r];
+  if (src < 0 || src >= n) {
+    if (c == 0) atomicOr(err, DEVERR_BOUNDS);
+    return;
+  }
+  const double2 v = Jt[(long long)src * ld + c];
+  const double f = jn[src];
+  Vh[idx] = make_double2(f * v.x, f * v.y);
+}
+
+int sj64_rows_per_block(int n) {
+  for (int br = SJ64_BRMAX; br > 1; br /= 2)
+    if (sj64_smem_bytes(n, br) <= 200 * 1024) return br;
+  return sj64_smem_bytes(n, 1) <= 220 * 1024 ? 1 : 0;
+}
+
+int sj64_grid(int npairs, size_t smem) {
+  int dev = 0, sms = 0, per = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_sj64_sweeps, SJ64_NT, smem) != cudaSuccess)
+    return 0;
+  return std::min(npairs, std::min(sms * per, 2 * sms));
+}
+
+}  // namespace
+
 size_t herm_eig_scratch_elems(int n) {
   // V (n x n) + rotations (n/2+1 Rot = 40 B each, in double2 units) + 2 doubles
   return (size_t)n * n + (size_t)(n / 2 + 1) * 3 + 2;
@@ -589,6 +815,71 @@ int herm_eig(double2* A, int n, double* w, double2* Vh, double2* scratch, size_t
   k_sort_out<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(A, V, n, w, Vh);
   note_launch();
   QR_CUDA_TRY(cudaGetLastError());
+  return QRTEBD_OK;
+}
+
+bool svd64_supported(int n) { return n >= 1 && sj64_rows_per_block(n + (n & 1)) >= 1; }
+
+size_t svd64_work_bytes(int n) {
+  const int ld = n + (n & 1);
+  const int br = std::max(1, sj64_rows_per_block(ld));
+  const size_t rows = (size_t)ceil_div(n, br) * br;
+  return align_up(2 * rows * ld * sizeof(double2), 256) + align_up((size_t)n * sizeof(double), 256) +
+         align_up((size_t)n * sizeof(int), 256) + align_up(sizeof(Sj64Ctl), 256) +
+         align_up((size_t)n * sizeof(double), 256);
+}
+
+int svd_rows_jacobi64(const double2* Rz, long long ldr, int n, double* w, double2* Vh, void* work,
+                      size_t work_bytes, cudaStream_t st, unsigned* err, int* sweeps) {
+  if (n < 1 || ldr < n || !Rz || !w || !Vh || !work || work_bytes < svd64_work_bytes(n))
+    return QRTEBD_ERR_INVALID_ARG;
+  const int ld = n + (n & 1);
+  const int br = sj64_rows_per_block(ld);
+  if (br < 1) { set_last_message("svd_rows_jacobi64: rows too long for shared memory"); return QRTEBD_ERR_INVALID_ARG; }
+  const int nb = (int)ceil_div(n, br);
+  const size_t rows = (size_t)nb * br;
+  char* q = static_cast<char*>(work);
+  double2* R = reinterpret_cast<double2*>(q);
+  double2* Jt = R + rows * ld;
+  q += align_up(2 * rows * ld * sizeof(double2), 256);
+  double* s2 = reinterpret_cast<double*>(q); q += align_up((size_t)n * sizeof(double), 256);
+  int* order = reinterpret_cast<int*>(q); q += align_up((size_t)n * sizeof(int), 256);
+  Sj64Ctl* ctl = reinterpret_cast<Sj64Ctl*>(q); q += align_up(sizeof(Sj64Ctl), 256);
+  double* jn = reinterpret_cast<double*>(q);
+  QR_CUDA_TRY(cudaMemsetAsync(R, 0, 2 * rows * ld * sizeof(double2), st));
+  QR_CUDA_TRY(cudaMemcpy2DAsync(R, (size_t)ld * sizeof(double2), Rz, (size_t)ldr * sizeof(double2),
+                                (size_t)n * sizeof(double2), (size_t)n, cudaMemcpyDeviceToDevice, st));
+  k_eye64_ld<<<(unsigned)ceil_div((long long)n * n, 256), 256, 0, st>>>(Jt, n, ld);
+  note_launch();
+  QR_CUDA_TRY(cudaGetLastError());
+  QR_CUDA_TRY(cudaMemsetAsync(ctl, 0, sizeof(Sj64Ctl), st));
+  if (n > 1) {
+    const size_t smem = sj64_smem_bytes(ld, br);
+    static std::once_flag once;
+    static cudaError_t attr = cudaSuccess;
+    std::call_once(once, [] {
+      attr = cudaFuncSetAttribute(k_sj64_sweeps, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+    });
+    QR_CUDA_TRY(attr);
+    const int nbp = (nb % 2) ? nb + 1 : nb;
+    const int grid = sj64_grid(nbp / 2, smem);
+    if (grid < 1) { set_last_message("svd_rows_jacobi64: no resident CTA"); return QRTEBD_ERR_CUDA; }
+    // orthogonal to FP64 working accuracy: sqrt(n) eps
+    double tol = std::sqrt((double)std::max(n, 16)) * 1.11e-16;
+    int nv = ld, brv = br, nbv = nb;
+    void* args[] = {&R, &Jt, &nv, &brv, &nbv, &tol, &ctl, &err};
+    QR_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_sj64_sweeps, dim3((unsigned)grid), dim3(SJ64_NT),
+                                            args, smem, st));
+    note_launch();
+  }
+  k_sj64_norms<<<(unsigned)ceil_div(n, 8), 256, 0, st>>>(R, Jt, n, ld, s2, jn);
+  note_launch();
+  k_sj_rank<<<(unsigned)ceil_div(n, 128), 128, 0, st>>>(s2, n, w, order);
+  note_launch();
+  k_sj64_gather<<<(unsigned)ceil_div((long long)n * n, 256), 256, 0, st>>>(Jt, order, jn, n, ld, Vh, err);
+  note_launch();
+  QR_CUDA_TRY(cudaGetLastError());
+  if (sweeps) QR_CUDA_TRY(cudaMemcpyAsync(sweeps, &ctl->sweeps, sizeof(int), cudaMemcpyDeviceToDevice, st));
   return QRTEBD_OK;
 }
 

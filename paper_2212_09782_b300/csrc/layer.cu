@@ -12,6 +12,7 @@
 // time it is seen and replayed afterwards, removing the per-kernel launch cost.
 // CBE reads the new bond dimension back after each update and is not captured.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -203,11 +204,19 @@ int qrtebd_apply_gate_layer_batched(qrtebd_mps* const* states, int nstates, int 
   }
 
   // a CBE layer keeps its cuts on the device (collected after the join), so it can be recorded
-  // too, except in complex128, whose FP64 eigensolver synchronises with the host per sweep
+  // too; in complex128 only while every eta the states can reach fits the one-sided FP64
+  // solver (the two-sided fallback synchronises with the host once per sweep)
   bool capturable = (tr->scheme == QRTEBD_PLAIN);
   if (tr->scheme == QRTEBD_CBE) {
     capturable = true;
-    for (int i = 0; i < nstates; ++i) capturable = capturable && !prec_is_c128(states[i]->precision);
+    for (int i = 0; i < nstates; ++i) {
+      const qrtebd_mps* s = states[i];
+      if (!prec_is_c128(s->precision)) continue;
+      long long dchi = (long long)std::ceil(tr->dchi_frac * s->chi_max - 1e-9);
+      if (dchi < tr->dchi_min) dchi = tr->dchi_min;
+      const long long eta_cap = std::min<long long>((long long)s->d * s->chi_max, s->chi_max + dchi);
+      capturable = capturable && eta_cap <= (1 << 20) && svd64_supported((int)eta_cap);
+    }
   }
   GraphEntry* ge = nullptr;
   if (capturable) {

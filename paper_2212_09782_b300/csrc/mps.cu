@@ -299,6 +299,25 @@ template <typename T> int schmidt_t(qrtebd_mps* s, int b, double* S, int capacit
     QR_CUDA_TRY(cudaMemcpyAsync(h.data(), s->xiv[b], c * sizeof(cx<T>), cudaMemcpyDeviceToHost, s->st));
     QR_CUDA_TRY(cudaStreamSynchronize(s->st));
     for (int i = 0; i < c; ++i) sv[i] = std::sqrt((double)h[i].x * h[i].x + (double)h[i].y * h[i].y);
+  } else if (svd64_supported(c)) {
+    // the singular values of a dense Xi: one-sided FP64 Jacobi on its rows (Xi Xi^dag is never
+    // formed; one cooperative launch)
+    const long long cc = (long long)c * c;
+    const size_t wb = svd64_work_bytes(c);
+    size_t need = (size_t)(2 * cc + 64) * sizeof(double2) + c * sizeof(double) + wb + 4096;
+    QR_TRY(ensure_aux(s, need));
+    Arena ar; ar.base = static_cast<char*>(s->aux); ar.cap = s->aux_bytes;
+    double2* X = ar.take<double2>(cc);
+    double2* Vh = ar.take<double2>(cc);
+    double* w = ar.take<double>(c);
+    char* work = ar.take<char>(wb);
+    if (ar.overflow()) return QRTEBD_ERR_OOM;
+    k_to_c128v<T><<<(unsigned)ceil_div(cc, 256), 256, 0, s->st>>>(static_cast<const cx<T>*>(s->Xi[b]), X, cc);
+    note_launch();
+    QR_TRY(svd_rows_jacobi64(X, c, c, w, Vh, work, wb, s->st, device_error_word()));
+    QR_CUDA_TRY(cudaMemcpyAsync(sv.data(), w, c * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    QR_CUDA_TRY(cudaStreamSynchronize(s->st));
+    for (double& x : sv) x = x > 0 ? std::sqrt(x) : 0.0;
   } else {
     const long long cc = (long long)c * c;
     size_t need = (size_t)(3 * cc + herm_eig_scratch_elems(c) + 64) * sizeof(double2) + c * sizeof(double) + 4096;

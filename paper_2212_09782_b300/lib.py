@@ -42,6 +42,18 @@ class BondIO(C.Structure):
                 ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
 
 
+class SymBondIO(C.Structure):
+    _fields_ = [("precision", C.c_int), ("chi_l", C.c_int), ("d", C.c_int), ("chi_m", C.c_int),
+                ("chi_r", C.c_int), ("charge_l", C.POINTER(C.c_int)),
+                ("charge_m", C.POINTER(C.c_int)), ("charge_r", C.POINTER(C.c_int)),
+                ("xi_kind", C.c_int), ("xi", C.c_void_p), ("theta", C.c_void_p),
+                ("bm", C.c_void_p), ("bn", C.c_void_p),
+                ("gate", C.c_void_p), ("bm_out", C.c_void_p), ("xi_out", C.c_void_p),
+                ("bn_out", C.c_void_p), ("charge_out", C.POINTER(C.c_int)),
+                ("chi_sector_out", C.POINTER(C.c_int)), ("stats_out", C.c_void_p),
+                ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
+
+
 class BondInfo(C.Structure):
     _fields_ = [("eta", C.c_int), ("chi_new", C.c_int)]
 
@@ -63,6 +75,12 @@ def _load():
         "qrtebd_trunc_default": (I, [C.POINTER(Trunc), I, I]),
         "qrtebd_bond_workspace_size": (I, [I, I, I, I, I, I, I, C.POINTER(Trunc), C.POINTER(S)]),
         "qrtebd_bond_update": (I, [C.POINTER(BondIO), C.POINTER(Trunc), P, C.POINTER(BondInfo)]),
+        "qrtebd_sym_bond_workspace_size": (I, [I, I, I, I, I, C.POINTER(I), C.POINTER(I),
+                                               C.POINTER(I), I, I, C.POINTER(Trunc),
+                                               C.POINTER(S), C.POINTER(I)]),
+        "qrtebd_clock_bond_gate_charge": (I, [I, D, D, D, D, D, C.POINTER(D)]),
+        "qrtebd_sym_bond_update": (I, [C.POINTER(SymBondIO), C.POINTER(Trunc), P,
+                                       C.POINTER(BondInfo)]),
         "qrtebd_stream_check": (I, [P]),
         "qrtebd_set_spin_limit": (I, [LL]),
         "qrtebd_selftest_barrier_timeout": (I, [P]),
@@ -130,6 +148,16 @@ def clock_bond_gate(d, g, wl, wr, tau):
     tau = complex(tau)
     check(_lib.qrtebd_clock_bond_gate(d, g, wl, wr, tau.real, tau.imag,
                                       out.ctypes.data_as(C.POINTER(C.c_double))), "clock_bond_gate")
+    return out.view(np.complex128).reshape(d * d, d * d)
+
+
+def clock_bond_gate_charge(d, g, wl, wr, tau):
+    """The clock-model bond gate in the charge (Fourier) basis of the Z_d symmetry."""
+    out = np.zeros(2 * d ** 4, np.float64)
+    tau = complex(tau)
+    check(_lib.qrtebd_clock_bond_gate_charge(d, g, wl, wr, tau.real, tau.imag,
+                                             out.ctypes.data_as(C.POINTER(C.c_double))),
+          "clock_bond_gate_charge")
     return out.view(np.complex128).reshape(d * d, d * d)
 
 
@@ -238,6 +266,90 @@ class BondUpdater:
         return (self.bm_out[: chi_l * d * c].view(chi_l, d, c),
                 self.xi_out[: c * c].view(c, c),
                 self.bn_out[: c * d * chi_r].view(c, d, chi_r),
+                self.stats)
+
+
+def _int_array(v):
+    a = np.ascontiguousarray(np.asarray(v, dtype=np.int32))
+    return a, a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def sym_bond_workspace_size(precision, chi_l, d, chi_m, chi_r, charge_l, charge_m, charge_r,
+                            trunc, xi_kind=2, theta_given=True):
+    """(workspace bytes, eta_sum) of a charge-conserving CBE update."""
+    precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
+    (al, pl), (am, pm), (ar, pr) = _int_array(charge_l), _int_array(charge_m), _int_array(charge_r)
+    n, e = C.c_size_t(0), C.c_int(0)
+    check(_lib.qrtebd_sym_bond_workspace_size(precision, chi_l, d, chi_m, chi_r, pl, pm, pr,
+                                              xi_kind, 1 if theta_given else 0, C.byref(trunc),
+                                              C.byref(n), C.byref(e)),
+          "sym_bond_workspace_size")
+    return n.value, e.value
+
+
+class SymBondUpdater:
+    """Workspace and outputs of one charge-conserving CBE update (Sec. III with Z_d charges).
+
+    The charges of the three bonds are host integer sequences; theta' (chi_l, d, d, chi_r),
+    the diagonal xi (chi_l,) and the complex128 gate (d^2, d^2) are torch CUDA tensors.
+    """
+
+    def __init__(self, precision, d, charge_l, charge_m, charge_r, trunc, xi_kind=2,
+                 theta_given=True, device="cuda"):
+        import torch
+        self.precision = PRECISIONS.get(precision, precision) if isinstance(precision, str) else precision
+        self.dtype = torch.complex128 if is_c128(self.precision) else torch.complex64
+        self.charges = [np.asarray(c, np.int32) for c in (charge_l, charge_m, charge_r)]
+        chi_l, chi_m, chi_r = (len(c) for c in self.charges)
+        self.dims = (chi_l, d, chi_m, chi_r)
+        self.trunc = trunc
+        self.xi_kind = xi_kind
+        nbytes, self.eta_sum = sym_bond_workspace_size(self.precision, chi_l, d, chi_m, chi_r,
+                                                       *self.charges, trunc, xi_kind,
+                                                       theta_given)
+        self.cap = min(trunc.chi_max, self.eta_sum)
+        self.workspace = torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+        self.bm_out = torch.empty(chi_l * d * self.cap, dtype=self.dtype, device=device)
+        self.xi_out = torch.empty(self.cap, dtype=self.dtype, device=device)
+        self.bn_out = torch.empty(self.cap * d * chi_r, dtype=self.dtype, device=device)
+        self.stats = torch.zeros(4, dtype=torch.float64, device=device)
+        self.charge_out = np.zeros(self.cap, np.int32)
+        self.chi_sector = np.zeros(d, np.int32)
+
+    def run(self, gate, theta=None, xi=None, bm=None, bn=None, stream=None):
+        """One update (synchronises the stream once); returns BondInfo (eta_sum, chi_new).
+        theta' is given, or B^m and B^n are (then theta' = B^m B^n in the library)."""
+        chi_l, d, chi_m, chi_r = self.dims
+        io = SymBondIO()
+        io.precision = self.precision
+        io.chi_l, io.d, io.chi_m, io.chi_r = chi_l, d, chi_m, chi_r
+        (cl, io.charge_l), (cm, io.charge_m), (cr, io.charge_r) = (_int_array(c) for c in self.charges)
+        io.xi_kind = self.xi_kind if xi is not None else 0
+        io.xi = _ptr(xi)
+        io.theta = _ptr(theta)
+        io.bm = _ptr(bm)
+        io.bn = _ptr(bn)
+        io.gate = _ptr(gate)
+        io.bm_out = _ptr(self.bm_out)
+        io.xi_out = _ptr(self.xi_out)
+        io.bn_out = _ptr(self.bn_out)
+        io.charge_out = self.charge_out.ctypes.data_as(C.POINTER(C.c_int))
+        io.chi_sector_out = self.chi_sector.ctypes.data_as(C.POINTER(C.c_int))
+        io.stats_out = _ptr(self.stats)
+        io.workspace = _ptr(self.workspace)
+        io.workspace_bytes = self.workspace.numel()
+        info = BondInfo()
+        check(_lib.qrtebd_sym_bond_update(C.byref(io), C.byref(self.trunc), stream_handle(stream),
+                                          C.byref(info)), "sym_bond_update")
+        self.info = info
+        return info
+
+    def outputs(self):
+        """(Bm_new (chi_l, d, c), xi_new (c,), Bn_new (c, d, chi_r), charges (c,), stats)."""
+        chi_l, d, chi_m, chi_r = self.dims
+        c = self.info.chi_new
+        return (self.bm_out[: chi_l * d * c].view(chi_l, d, c), self.xi_out[:c],
+                self.bn_out[: c * d * chi_r].view(c, d, chi_r), self.charge_out[:c].copy(),
                 self.stats)
 
 
