@@ -24,7 +24,8 @@ QR, eigh, SVD, expm) serve as single steps; nothing is blocked, fused or reorder
 beyond what the paper's steps state.
 
 Parity status: every function here is pinned by ``tests/test_oracle_*.py`` against
-closed forms, invariants, brute force or exact references, except the CBE cut
-between near-degenerate Schmidt values (``bond.cbe_cut``), whose tie rule is a
-reading of an unaddressed point: parity unpinned for exact ties.
+closed forms, invariants, brute force or exact references. The tie rule of the CBE cut
+(``bond.cbe_cut``: never cut inside a multiplet) is a reading of a point the paper leaves
+open. It is pinned by the property it exists for: with it, the kept subspace does not
+depend on the initial guess Y0; without it, it does.
 """

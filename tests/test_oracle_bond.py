@@ -302,3 +302,36 @@ def test_sweeps_reach_the_dominant_singular_values():
     out = bond.qr_update(None, None, None, np.eye(9), chi_max=eta, eta=eta, theta=T, Y0=Y0, sweeps=60)
     s = np.linalg.svd(out["Xi_new"], compute_uv=False) * out["norm_L"]
     assert np.allclose(s, spec[:eta], rtol=1e-10, atol=0)
+
+
+def test_tie_rule_makes_the_kept_subspace_unique():
+    # Schmidt values with an exactly degenerate pair straddling chi_max = 3. A cut inside the
+    # pair keeps one vector of the degenerate plane, and which one depends on the path (here
+    # on the initial guess Y0): the truncated state is then not a function of theta~. The
+    # tie rule drops the whole pair, and the kept subspace no longer depends on Y0.
+    r = W.rng(91)
+    n = 12
+    s = np.array([1.0, 0.7, 0.4, 0.4, 0.2, 0.1, 0.05, 0.02, 0.01, 5e-3, 2e-3, 1e-3])
+    Us, Vs = W.random_unitary(r, n), W.random_unitary(r, n)
+    T = (Us * s) @ Vs.conj().T
+    th = T.reshape(6, 2, 2, 6)
+    U = np.eye(4, dtype=np.complex128)
+    Y0s = [T[:n], W.complex_gaussian(r, (n, n))]
+
+    def proj(tie_tol, Y0):
+        o = bond.qr_update(None, None, None, U, scheme="cbe", chi_max=3, eta=n, theta=th, Y0=Y0,
+                           svd_min=0.0, tie_tol=tie_tol)
+        B = o["Bn_new"].reshape(o["chi_new"], -1)
+        return o["chi_new"], B.conj().T @ B
+
+    (ca, Pa), (cb, Pb) = (proj(1e-10, Y0) for Y0 in Y0s)
+    assert ca == cb == 2
+    assert np.max(np.abs(Pa - Pb)) < 1e-12
+    # the two kept vectors are the dominant right singular vectors of theta~
+    Vt = Vs.conj().T[:2]
+    assert np.max(np.abs(Pa - Vt.conj().T @ Vt)) < 1e-12
+    # without the rule (tie_tol = 0 never fires on values equal only to rounding) the cut
+    # falls inside the pair and the kept subspace depends on Y0
+    (ca, Pa), (cb, Pb) = (proj(0.0, Y0) for Y0 in Y0s)
+    assert ca == cb == 3
+    assert np.max(np.abs(Pa - Pb)) > 1e-3
