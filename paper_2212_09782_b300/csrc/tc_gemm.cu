@@ -8,7 +8,7 @@
 //   warp 1      TMEM allocation (512 columns) and the single MMA-issuing thread:
 //               per stage 4 K-steps of tcgen05.mma.kind::tf32 M=128 N=256 K=8
 //               (x3 for hi*hi, hi*lo, lo*hi), tcgen05.commit frees the stage;
-//   warps 2-9   epilogue: every CHUNK stages the accumulator (two TMEM buffers,
+//   warps 2-9   epilogue: every 2 (3xTF32) or 4 stages the accumulator (two TMEM buffers,
 //               ping-pong) is added into FP32 registers, one row and 128 columns
 //               per thread; at the end alpha/beta and complex stores.
 // The promotion matters: the tensor core's own accumulation loses low-order bits
@@ -31,7 +31,13 @@ constexpr int BM = 128, BK = 32;               // BK in fp32 elements = one 128 
 constexpr int A_TILE = BM * BK * 4;            // 16 KB
 constexpr int NEPI = 8;                         // epilogue warps
 constexpr int NTHREADS = 64 + 32 * NEPI;        // producer, MMA, epilogue
-constexpr int CHUNK = 4;                        // stages per FP32 promotion
+constexpr int CHUNK = 4;                        // stages per FP32 promotion (1xTF32; the split
+                                                // heuristics' unit of K)
+// 3xTF32 promotes every 2 stages: a chunk then builds 24 tensor-core accumulations on each
+// other instead of 48. The accumulation in TMEM truncates, so its error is a bias that
+// shrinks norms; at 48 it set the complex64 CBE update's eps error (8e-6 relative on an
+// eta = 351 bond, against 1.3e-6 with FP32 CUDA-core products)
+template <bool THREE> constexpr int promo_chunk() { return THREE ? 2 : CHUNK; }
 
 // BN: real output columns per tile (256, or 128 for narrow or few-tile products); the
 // stage ring fills ~192 KB of shared memory either way
@@ -143,10 +149,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
 }
 
 // Kernel. Roles: warp 0 TMA producer, warp 1 TMEM allocator + MMA issuer, warps
-// 2..9 epilogue. The K loop is cut into chunks of CHUNK stages; each chunk
+// 2..9 epilogue. The K loop is cut into chunks of promo_chunk() stages; each chunk
 // accumulates into one of two TMEM buffers (columns [0,256) and [256,512)) and the
 // epilogue warps add every finished chunk into FP32 registers (each thread one row,
-// 128 columns), so at most 4*CHUNK*3 tensor-core accumulations build on each other
+// 128 columns), so at most 4*2*3 (3xTF32) or 4*4 tensor-core accumulations build on each other
 // before a correctly rounded FP32 add. grid.z splits K (partial != nullptr: raw
 // partial sums are written for a separate reduction).
 template <bool THREE, int BN>
@@ -177,7 +183,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int kt0 = blockIdx.z * kt_per_split;
   const int kt1 = min(nk_all, kt0 + kt_per_split);
   const int nk = max(0, kt1 - kt0);
-  const int nchunks = (nk + CHUNK - 1) / CHUNK;
+  constexpr int KCH = promo_chunk<THREE>();
+  const int nchunks = (nk + KCH - 1) / KCH;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < C::STAGES; ++s) { mbar_init(&full[s], 1); mbar_init(&empty[s], 1); }
@@ -236,8 +243,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         if (c >= 2 && !mbar_wait(&acce[b], (uint32_t)(((c >> 1) - 1) & 1))) { ok = false; break; }
         tc_fence_after();
         const uint32_t acc_t = tmem + (uint32_t)(b * BN);
-        const int i1 = min(nk, (c + 1) * CHUNK);
-        for (int i = c * CHUNK; i < i1; ++i) {
+        const int i1 = min(nk, (c + 1) * KCH);
+        for (int i = c * KCH; i < i1; ++i) {
           const int s = i % C::STAGES;
           if (!mbar_wait(&full[s], (uint32_t)((i / C::STAGES) & 1))) { ok = false; break; }
           tc_fence_after();
@@ -246,7 +253,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 #pragma unroll
           for (int k = 0; k < BK / 8; ++k) {
             const uint32_t off = k * 32;  // 8 tf32 = 32 bytes along K inside the swizzle row
-            const uint32_t acc = (i > c * CHUNK || k > 0) ? 1u : 0u;
+            const uint32_t acc = (i > c * KCH || k > 0) ? 1u : 0u;
             if (THREE) {
               tc_mma(acc_t, desc_sw128(a_lo + off), desc_sw128(b_hi + off), kIdesc, acc);
               tc_mma(acc_t, desc_sw128(a_hi + off), desc_sw128(b_lo + off), kIdesc, 1u);
