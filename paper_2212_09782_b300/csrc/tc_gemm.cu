@@ -507,6 +507,30 @@ __device__ __forceinline__ int oz_exp_of(double x) {
   return x > 0.0 ? e : OZ_SENT;
 }
 
+// The slices of x (row exponent e) as integers: N = rint(x 2^(56 - e)) (|N| < 2^56, exact in
+// int64), then its balanced base-2^7 digits from the least significant up, d_1..d_7 in
+// [-64, 63] and the leading d_0 in [-128, 128]: x 2^-e = sum_p d_p 2^(-7(p+1)) up to half a
+// unit of 2^-56. Two FP64 instructions per value (the power-of-two scaling, the conversion)
+// instead of a multiply, rint and subtract per slice: B300's FP64 pipe runs at ~1/64 of
+// its FP32 rate, and the FP64 form made slicing ~20 % of an emulated complex128 update.
+__device__ __forceinline__ void oz_digits(double x, int e, int (&d)[OZ_SLICES]) {
+  long long N = 0;
+  if (e != OZ_SENT && x != 0.0) {
+    const int sh = OZ_SLICES * OZ_BITS - e;
+    const int be = 1023 + sh;  // 2^sh as a double when it is a normal number
+    const double y = (be >= 1 && be <= 2046) ? x * __longlong_as_double((long long)be << 52) : ldexp(x, sh);
+    N = __double2ll_rn(y);
+  }
+#pragma unroll
+  for (int p = OZ_SLICES - 1; p > 0; --p) {
+    int r = (int)(N & ((1 << OZ_BITS) - 1));
+    if (r >= (1 << (OZ_BITS - 1))) r -= 1 << OZ_BITS;
+    d[p] = r;
+    N = (N - r) >> OZ_BITS;
+  }
+  d[0] = (int)N;
+}
+
 struct OzJob {
   const double2* src; long long s0, s1; int conj, rows, K;  // rows: M (A) or N (B)
   int* e; float* out; long long slice_stride; int ld;
@@ -516,7 +540,7 @@ struct OzJob {
 
 // pass 1: one 32 x 32 tile; the warps reduce its rows' maxima, one atomic per row and tile
 __global__ void k_oz_exp(OzJob a, OzJob b) {
-  __shared__ double t[32][33];
+  __shared__ unsigned long long t[32][33];
   pdl_launch_dependents();
   pdl_wait();
   const OzJob& j = blockIdx.z == 0 ? a : b;
@@ -528,19 +552,27 @@ __global__ void k_oz_exp(OzJob a, OzJob b) {
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
     const int rr = kc ? r : threadIdx.x, kk = kc ? threadIdx.x : r;
     const int row = r0 + rr, k = k0 + kk;
-    double v = 0.0;
+    // |x| compared as the integer bit pattern without the sign (monotone for IEEE doubles;
+    // a NaN sorts above every number): no FP64 instruction in the pass
+    unsigned long long v = 0ull;
     if (row < j.rows && k < j.K) {
       const double2 x = j.src[row * srow + k * sk];
-      v = fmax(fabs(x.x), fabs(x.y));
+      const unsigned long long a = (unsigned long long)__double_as_longlong(x.x) & 0x7fffffffffffffffull;
+      const unsigned long long b = (unsigned long long)__double_as_longlong(x.y) & 0x7fffffffffffffffull;
+      v = a > b ? a : b;
     }
     t[rr][kk] = v;
   }
   __syncthreads();
   for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-    double v = t[r][threadIdx.x];
+    unsigned long long v = t[r][threadIdx.x];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (threadIdx.x == 0 && r0 + r < j.rows && v > 0.0) atomicMax(j.e + r0 + r, oz_exp_of(v));
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+      v = w > v ? w : v;
+    }
+    if (threadIdx.x == 0 && r0 + r < j.rows && v > 0ull)
+      atomicMax(j.e + r0 + r, oz_exp_of(__longlong_as_double((long long)v)));
   }
 }
 
@@ -568,14 +600,12 @@ __global__ void k_oz_slice(OzJob a, OzJob b) {
     if (row >= j.rows || k >= j.K) continue;
     const int e = j.e[row];
     const double2 v = t[r][threadIdx.x];
-    double tr = e == OZ_SENT ? 0.0 : ldexp(v.x, -e), ti = e == OZ_SENT ? 0.0 : ldexp(v.y, -e);
+    int drs[OZ_SLICES], dis[OZ_SLICES];
+    oz_digits(v.x, e, drs);
+    oz_digits(v.y, e, dis);
 #pragma unroll
     for (int p = 0; p < OZ_SLICES; ++p) {
-      tr *= (double)(1 << OZ_BITS);
-      ti *= (double)(1 << OZ_BITS);
-      const double dr = rint(tr), di = rint(ti);
-      tr -= dr;
-      ti -= di;
+      const float dr = (float)drs[p], di = (float)dis[p];
       float* o = j.out + (long long)p * j.slice_stride;
       if (!j.is_b) {
         *reinterpret_cast<float2*>(o + (long long)row * j.ld + 2 * k) = make_float2((float)dr, (float)di);
