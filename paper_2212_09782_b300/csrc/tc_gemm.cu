@@ -16,6 +16,7 @@
 // rather than sqrt(K); chunked promotion restores FP32-like accuracy.
 // Every mbarrier wait is bounded (kSpinLimit); on expiry the kernel sets
 // DEVERR_TIMEOUT in the error word, drains what it issued and returns.
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include <map>
@@ -106,6 +107,15 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
       "l"(a), "l"(b), "r"(idesc), "r"(acc)
       : "memory");
 }
+// the same with FP16 operands (both A and B f16), FP32 accumulation
+__device__ __forceinline__ void tc_mma_f16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc,
+                                           uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
   asm volatile(
       "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -134,6 +144,17 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
         "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),       \
         "=r"(r[31])                                                                          \
       : "r"(taddr))
+
+#define TMEM_ST32(taddr, r)                                                                  \
+  asm volatile(                                                                              \
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,"  \
+      "%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"     \
+      ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), \
+        "r"(r[7]), "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]),     \
+        "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]),  \
+        "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),  \
+        "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])                                       \
+      : "memory")
 
 #define TMEM_LD16(taddr, r)                                                                  \
   asm volatile(                                                                              \
@@ -533,7 +554,7 @@ __device__ __forceinline__ void oz_digits(double x, int e, int (&d)[OZ_SLICES]) 
 
 struct OzJob {
   const double2* src; long long s0, s1; int conj, rows, K;  // rows: M (A) or N (B)
-  int* e; float* out; long long slice_stride; int ld;
+  int* e; __half* out; long long slice_stride; int ld;     // slices in FP16 (exact: |d| <= 128)
   int gx, gy;  // tiles along K and along rows
   int is_b;
 };
@@ -606,13 +627,13 @@ __global__ void k_oz_slice(OzJob a, OzJob b) {
 #pragma unroll
     for (int p = 0; p < OZ_SLICES; ++p) {
       const float dr = (float)drs[p], di = (float)dis[p];
-      float* o = j.out + (long long)p * j.slice_stride;
+      __half* o = j.out + (long long)p * j.slice_stride;
       if (!j.is_b) {
-        *reinterpret_cast<float2*>(o + (long long)row * j.ld + 2 * k) = make_float2((float)dr, (float)di);
+        *reinterpret_cast<__half2*>(o + (long long)row * j.ld + 2 * k) = __floats2half2_rn(dr, di);
       } else {
         const long long o0 = (long long)(2 * row) * j.ld + 2 * k;
-        *reinterpret_cast<float2*>(o + o0) = make_float2((float)dr, (float)-di);
-        *reinterpret_cast<float2*>(o + o0 + j.ld) = make_float2((float)di, (float)dr);
+        *reinterpret_cast<__half2*>(o + o0) = __floats2half2_rn(dr, -di);
+        *reinterpret_cast<__half2*>(o + o0 + j.ld) = __floats2half2_rn(di, dr);
       }
     }
   }
@@ -632,14 +653,22 @@ struct OzPairs { int n; signed char p[64], q[64]; };
 // terms) never straddles two pairs: its exact FP32 sum is added into FP64 registers with the
 // pair's weight, and the rows' and columns' exponents are applied at the end.
 constexpr int OZ_BN = 128;
-constexpr int OZ_B_TILE = OZ_BN * BK * 4;
-constexpr int OZ_STAGE = A_TILE + OZ_B_TILE;
+constexpr int OZ_BKH = 64;                   // FP16 elements per stage row (one 128-byte swizzle row)
+constexpr int OZ_A_TILE = BM * OZ_BKH * 2;   // 16 KB
+constexpr int OZ_B_TILE = OZ_BN * OZ_BKH * 2;
+constexpr int OZ_STAGE = OZ_A_TILE + OZ_B_TILE;
 constexpr int OZ_STAGES = (192 * 1024) / OZ_STAGE;
 constexpr int OZ_SMEM = OZ_STAGES * OZ_STAGE + 1024 + 256;
-constexpr uint32_t OZ_IDESC = Cfg<false, OZ_BN>::IDESC;
-constexpr int OZ_CHUNK = 32;                 // stages per exact FP32 chunk: 32 x 32 = 1024 real K terms
+// instruction descriptor: D fp32, A/B f16 (format 0), both K-major, M = BM, N = OZ_BN
+constexpr uint32_t OZ_IDESC = (1u << 4) | ((uint32_t)(OZ_BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+constexpr int OZ_CHUNK = 16;                 // stages per exact FP32 chunk: 16 x 64 = 1024 real K terms
 constexpr int OZ_NEPI = 16;                  // epilogue warps: four lane quarters x four column quarters
 constexpr int OZ_NT = 64 + 32 * OZ_NEPI;
+// TMEM: the two chunk accumulators in columns [0, 2 OZ_BN), the FP64 level sums above them
+// (each epilogue thread's 32 doubles as 64 words of its own lane: one double per output)
+constexpr int OZ_TMEM_COLS = 512;
+constexpr int OZ_ACC64_COL = 2 * OZ_BN;
+static_assert(OZ_ACC64_COL + 4 * 2 * (OZ_BN / 4) <= OZ_TMEM_COLS, "FP64 sums in TMEM");
 
 __global__ void __launch_bounds__(OZ_NT, 1)
     k_oz_gemm(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tB, OzEpi epi,
@@ -659,7 +688,7 @@ __global__ void __launch_bounds__(OZ_NT, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * OZ_BN, m0 = blockIdx.y * BM;
-  const int nk = (Kp + BK - 1) / BK;
+  const int nk = (Kp + OZ_BKH - 1) / OZ_BKH;
   const int cpp = (nk + OZ_CHUNK - 1) / OZ_CHUNK;  // chunks per pair
   const int per_z = (pr.n + (int)gridDim.z - 1) / (int)gridDim.z;
   const int p_lo = min(pr.n, (int)blockIdx.z * per_z), p_hi = min(pr.n, p_lo + per_z);
@@ -673,7 +702,7 @@ __global__ void __launch_bounds__(OZ_NT, 1)
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(s_u32(tmem_slot)),
-                 "r"(2 * OZ_BN)
+                 "r"(OZ_TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -682,7 +711,7 @@ __global__ void __launch_bounds__(OZ_NT, 1)
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   auto stage_a = [&](int st) { return smem + st * OZ_STAGE; };
-  auto stage_b = [&](int st) { return smem + st * OZ_STAGE + A_TILE; };
+  auto stage_b = [&](int st) { return smem + st * OZ_STAGE + OZ_A_TILE; };
 
   if (warp == 0) {
     if (lane == 0) {
@@ -694,8 +723,8 @@ __global__ void __launch_bounds__(OZ_NT, 1)
         if (!mbar_wait(&empty[st], ph ^ 1u)) { ok = false; break; }
         const int p = p_lo + it / nk, i = it % nk;
         mbar_expect_tx(&full[st], OZ_STAGE);
-        tma_load(stage_a(st), &tA, &full[st], i * BK, pr.p[p] * a_rows + m0);
-        tma_load(stage_b(st), &tB, &full[st], i * BK, pr.q[p] * b_rows + n0);
+        tma_load(stage_a(st), &tA, &full[st], i * OZ_BKH, pr.p[p] * a_rows + m0);
+        tma_load(stage_b(st), &tB, &full[st], i * OZ_BKH, pr.q[p] * b_rows + n0);
         ++issued;
       }
       if (!ok) atomicOr(err, DEVERR_TIMEOUT);
@@ -723,9 +752,9 @@ __global__ void __launch_bounds__(OZ_NT, 1)
           tc_fence_after();
           const uint32_t a0 = s_u32(stage_a(st)), b0 = s_u32(stage_b(st));
 #pragma unroll
-          for (int k = 0; k < BK / 8; ++k) {
-            const uint32_t off = k * 32;
-            tc_mma(acc_t, desc_sw128(a0 + off), desc_sw128(b0 + off), OZ_IDESC, (i > i0 || k > 0) ? 1u : 0u);
+          for (int k = 0; k < OZ_BKH / 16; ++k) {
+            const uint32_t off = k * 32;  // 16 f16 = 32 bytes along K inside the swizzle row
+            tc_mma_f16(acc_t, desc_sw128(a0 + off), desc_sw128(b0 + off), OZ_IDESC, (i > i0 || k > 0) ? 1u : 0u);
           }
           tc_commit(&empty[st]);
         }
@@ -744,16 +773,41 @@ __global__ void __launch_bounds__(OZ_NT, 1)
     // flush), and only a finished level sum is added into the FP64 registers with its weight
     // 2^(-OZ_BITS (p+q+2)). The FP64 pipe, much narrower than the tensor core's chunk rate,
     // then does one FMA per element and level instead of one per chunk.
-    double acc[HW];
+    // The FP64 sums live in TMEM (this thread's lane, columns OZ_ACC64_COL + 2 HW h ..): held
+    // in registers beside the int32 level sums they spilled to local memory. A flush loads
+    // them, adds the level and stores them back; they return to registers only at the end.
     int iacc[HW];
 #pragma unroll
-    for (int jj = 0; jj < HW; ++jj) { acc[jj] = 0.0; iacc[jj] = 0; }
+    for (int jj = 0; jj < HW; ++jj) iacc[jj] = 0;
+    const uint32_t t64 = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(OZ_ACC64_COL + 2 * HW * h);
+    {
+      uint32_t z[32];
+#pragma unroll
+      for (int jj = 0; jj < 32; ++jj) z[jj] = 0u;
+#pragma unroll
+      for (int blk = 0; blk < 2 * HW / 32; ++blk) TMEM_ST32(t64 + blk * 32, z);
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
     int lvl = -1, nin = 0;
     auto flush = [&]() {
       if (lvl >= 0 && nin > 0) {
         const double w = ldexp(1.0, -OZ_BITS * (lvl + 2));
 #pragma unroll
-        for (int jj = 0; jj < HW; ++jj) { acc[jj] = fma((double)iacc[jj], w, acc[jj]); iacc[jj] = 0; }
+        for (int blk = 0; blk < 2 * HW / 32; ++blk) {
+          uint32_t r[32];
+          TMEM_LD32(t64 + blk * 32, r);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            double a = __hiloint2double((int)r[2 * jj + 1], (int)r[2 * jj]);
+            a = fma((double)iacc[blk * 16 + jj], w, a);
+            iacc[blk * 16 + jj] = 0;
+            r[2 * jj] = (uint32_t)__double2loint(a);
+            r[2 * jj + 1] = (uint32_t)__double2hiint(a);
+          }
+          TMEM_ST32(t64 + blk * 32, r);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       }
       nin = 0;
     };
@@ -781,6 +835,15 @@ __global__ void __launch_bounds__(OZ_NT, 1)
     }
     flush();
     if (!ok && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
+    double acc[HW];
+#pragma unroll
+    for (int blk = 0; blk < 2 * HW / 32; ++blk) {
+      uint32_t r[32];
+      TMEM_LD32(t64 + blk * 32, r);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int jj = 0; jj < 16; ++jj) acc[blk * 16 + jj] = __hiloint2double((int)r[2 * jj + 1], (int)r[2 * jj]);
+    }
     auto sum = [&](int jj) { return acc[jj]; };
     const bool use_beta = (epi.beta.x != 0.0 || epi.beta.y != 0.0);
     const int ea = (row < epi.M) ? epi.ea[row] : OZ_SENT;
@@ -870,7 +933,7 @@ __global__ void __launch_bounds__(OZ_NT, 1)
       if (!mbar_wait(&accf[c & 1], (uint32_t)((c >> 1) & 1)) && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
     }
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * OZ_BN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(OZ_TMEM_COLS) : "memory");
   }
 }
 
@@ -930,6 +993,21 @@ int make_map(CUtensorMap* tm, const float* base, int rows, int cols, int ld, int
 }
 
 inline int ld_for(int k) { return (int)align_up((size_t)2 * k, 32); }
+// FP16 slice rows: 2k halves padded to whole 128-byte rows
+inline int ld_for_h(int k) { return (int)align_up((size_t)2 * k, 64); }
+
+int make_map_h(CUtensorMap* tm, const __half* base, int rows, int cols, int ld, int box_rows) {
+  cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)OZ_BKH, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<__half*>(base), gdim,
+                        gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) { set_last_message("cuTensorMapEncodeTiled failed"); return QRTEBD_ERR_CUDA; }
+  return QRTEBD_OK;
+}
 
 template <bool THREE, int BN> int set_attrs_once() {
   static std::once_flag once;
@@ -1135,13 +1213,13 @@ __global__ void k_fill_test(float2* x, long long n, unsigned seed) {
 }  // namespace
 
 void oz_carve(Arena& ar, int max_m, int max_k, int max_n, OzWorkspace& w) {
-  const size_t ld = (size_t)ld_for(max_k);
+  const size_t ld = (size_t)ld_for_h(max_k);
   w.a_cap = (size_t)OZ_SLICES * max_m * ld;
   w.b_cap = (size_t)OZ_SLICES * 2 * max_n * ld;
   w.ea_cap = (size_t)max_m;
   w.eb_cap = (size_t)max_n;
-  w.a = ar.take<float>(w.a_cap);
-  w.b = ar.take<float>(w.b_cap);
+  w.a = ar.take<unsigned short>(w.a_cap);
+  w.b = ar.take<unsigned short>(w.b_cap);
   w.ea = ar.take<int>(w.ea_cap);
   w.eb = ar.take<int>(w.eb_cap);
   w.part_cap = (size_t)1 << 21;  // 32 MB of pair-split partial tiles (complex128)
@@ -1169,7 +1247,7 @@ int oz_gemm(const GemmArgs<double>& g0, OzWorkspace& w, cudaStream_t st, int pro
   }
   const int M = g.M, N = g.N, K = g.K;
   if (M <= 0 || N <= 0) return QRTEBD_OK;
-  const int ld = ld_for(K);
+  const int ld = ld_for_h(K);
   if (K <= 0 || (size_t)OZ_SLICES * M * ld > w.a_cap || (size_t)OZ_SLICES * 2 * N * ld > w.b_cap ||
       (size_t)M > w.ea_cap || (size_t)N > w.eb_cap || !w.a || !w.b)
     return gemm_simt<double>(g0, st, nullptr, 0, prof_family == PROF_TC_GEMM ? PROF_SIMT_GEMM : prof_family);
@@ -1177,13 +1255,15 @@ int oz_gemm(const GemmArgs<double>& g0, OzWorkspace& w, cudaStream_t st, int pro
   // exponents (memset 0x80 bytes: a sentinel below every exponent), then the slices
   QR_CUDA_TRY(cudaMemsetAsync(w.ea, 0x80, (size_t)M * sizeof(int), st));
   QR_CUDA_TRY(cudaMemsetAsync(w.eb, 0x80, (size_t)N * sizeof(int), st));
-  OzJob ja{g.A, g.sam, g.sak, g.conj_a ? 1 : 0, M, K, w.ea, w.a, (long long)M * ld, ld,
+  __half* sa = reinterpret_cast<__half*>(w.a);
+  __half* sb = reinterpret_cast<__half*>(w.b);
+  OzJob ja{g.A, g.sam, g.sak, g.conj_a ? 1 : 0, M, K, w.ea, sa, (long long)M * ld, ld,
            (int)ceil_div(K, 32), (int)ceil_div(M, 32), 0};
-  OzJob jb{g.B, g.sbk, g.sbn, g.conj_b ? 1 : 0, N, K, w.eb, w.b, (long long)2 * N * ld, ld,
+  OzJob jb{g.B, g.sbk, g.sbn, g.conj_b ? 1 : 0, N, K, w.eb, sb, (long long)2 * N * ld, ld,
            (int)ceil_div(K, 32), (int)ceil_div(N, 32), 1};
   {
     dim3 grid((unsigned)std::max(ja.gx, jb.gx), (unsigned)std::max(ja.gy, jb.gy), 2);
-    ProfScope prof(PROF_PREP, st, 0, 16.0 * (M + N) * (double)K * 2 + 4.0 * OZ_SLICES * 2 * K * ((double)M + 2.0 * N));
+    ProfScope prof(PROF_PREP, st, 0, 16.0 * (M + N) * (double)K * 2 + 2.0 * OZ_SLICES * 2 * K * ((double)M + 2.0 * N));
     QR_CUDA_TRY(launch_pdl(k_oz_exp, grid, dim3(32, 8), 0, st, ja, jb));
     note_launch();
     QR_CUDA_TRY(launch_pdl(k_oz_slice, grid, dim3(32, 8), 0, st, ja, jb));
@@ -1191,8 +1271,8 @@ int oz_gemm(const GemmArgs<double>& g0, OzWorkspace& w, cudaStream_t st, int pro
   }
   // the slices of every operand stacked as one tensor: slice p's rows start at p * rows
   CUtensorMap ta, tb;
-  QR_TRY(make_map(&ta, w.a, OZ_SLICES * M, 2 * K, ld, BM));
-  QR_TRY(make_map(&tb, w.b, OZ_SLICES * 2 * N, 2 * K, ld, OZ_BN));
+  QR_TRY(make_map_h(&ta, sa, OZ_SLICES * M, 2 * K, ld, BM));
+  QR_TRY(make_map_h(&tb, sb, OZ_SLICES * 2 * N, 2 * K, ld, OZ_BN));
   // the slice pairs p + q <= OZ_SLICES - 1, ordered by level p + q (the kernel sums a level's
   // chunks in integers before one FP64 add)
   OzPairs pr{};

@@ -58,8 +58,8 @@ void tc_invalidate(TcWorkspace& w);
 constexpr int OZ_SLICES = 8;
 constexpr int OZ_BITS = 7;
 struct OzWorkspace {
-  float* a = nullptr;  // OZ_SLICES x max_m rows x ld floats
-  float* b = nullptr;  // OZ_SLICES x 2 max_n rows x ld floats
+  unsigned short* a = nullptr;  // FP16 slices: OZ_SLICES x max_m rows x ld halves
+  unsigned short* b = nullptr;  // OZ_SLICES x 2 max_n rows x ld halves
   int* ea = nullptr;   // per row of A' (max_m)
   int* eb = nullptr;   // per complex column of opB (max_n)
   double2* part = nullptr;  // partial tiles of a product whose slice pairs are split over CTAs
