@@ -964,7 +964,13 @@ def main():
                          "workloads' shapes before any timing)")
     ap.add_argument("--svd-c128", action="store_true",
                     help="svd workload: add the complex128 arms (the cuSOLVER SVD alone takes ~165 s)")
+    ap.add_argument("--tc-prep", choices=["separate", "kernel"], default="separate",
+                    help="operand preparation of the complex64 tensor-core products: a separate "
+                         "pass (default) or inside the GEMM kernel (128-column tiles)")
     args = ap.parse_args()
+    if args.impl == "ours" and args.tc_prep == "kernel":
+        from paper_2212_09782_b300 import lib as L
+        L.tc_operand_prep(0)
     if args.warmup < 3 and args.impl == "ours":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -419,6 +419,18 @@ int qrtebd_autotune_entry(int i, int shape[4], int config[3], double ms[2]);
 int qrtebd_autotune_set(const int shape[4], const int config[3]);
 void qrtebd_autotune_clear(void);
 
+/* Where the complex64 tensor-core products prepare their operands (the TF32 hi/lo split
+ * and the 2 x 2 real embedding of B). Mode 1 (the default): a separate pass writes the
+ * prepared operands to the workspace, and the GEMM loads them with TMA. Mode 0: inside
+ * the GEMM kernel, whose epilogue warps convert the raw complex64 operands into its
+ * shared-memory stages; this applies to products run with 128-column tiles whose operands
+ * are contiguous along K or along their other index, with 16-byte aligned pairs. Other
+ * products keep the separate pass. Other values: INVALID_ARG. The previous mode is
+ * returned through *previous (may be NULL). The mode is process-wide. The two modes give
+ * identical results: the same products, summed in the same order. The paper has no
+ * counterpart to this tuning and diagnostic switch. */
+int qrtebd_tc_operand_prep(int mode, int* previous);
+
 /* ------------------------------------------------------------- Householder QR */
 /* A = Q R for a device matrix A (m x n, m >= n, row-major, leading dimension lda, in the
  * precision's storage type): the factorisation of Sec. II (i) (and, applied to Y^dag,

@@ -322,6 +322,13 @@ int qrtebd_autotune_set(const int shape[4], const int config[3]) {
 
 void qrtebd_autotune_clear(void) { tc_tune_clear(); }
 
+int qrtebd_tc_operand_prep(int mode, int* previous) {
+  if (mode != 0 && mode != 1) return QRTEBD_ERR_INVALID_ARG;
+  const int prev = tc_prep_mode(mode);
+  if (previous) *previous = prev;
+  return QRTEBD_OK;
+}
+
 int qrtebd_stream_check(void* stream) { return check_device_error(static_cast<cudaStream_t>(stream)); }
 
 int qrtebd_set_spin_limit(long long polls) {

@@ -19,6 +19,7 @@
 #include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
+#include <atomic>
 #include <map>
 #include <mutex>
 
@@ -511,6 +512,340 @@ __global__ void k_prep(PrepJob a, PrepJob b, int three) {
     prep_a_tile(j.src, j.s0, j.s1, j.conj, j.rows, j.K, j.hi, j.lo, j.ld, three, blockIdx.x, blockIdx.y, t);
   else
     prep_b_tile(j.src, j.s0, j.s1, j.conj, j.K, j.rows, j.hi, j.lo, j.ld, three, blockIdx.x, blockIdx.y, t);
+}
+
+// ------------------------------------------------------------------ fused operand preparation
+// The same GEMM with the operand preparation done in the kernel. The eight epilogue warps
+// also convert: one stage ahead they read the raw complex64 operands (16-byte global loads
+// of two complex values), split every value into its TF32 part and remainder (hi = tf32(x),
+// lo = x - hi), and store A' and the 2 x 2 embedded B'^T directly into the stage buffers in
+// the 128-byte-swizzled K-major layout a tiled TMA load would produce (16-byte chunk c of
+// tile row r at byte r * 128 + ((c ^ (r & 7)) << 4), tiles 1024-byte aligned). A proxy fence
+// makes these generic stores visible to the tensor core's reads before each warp arrives on
+// the stage's full barrier. Between stages they drain finished accumulator chunks as before.
+// Layouts handled: opA contiguous along K (sak = 1) or along M (sam = 1), opB contiguous
+// along K (sbk = 1) or along N (sbn = 1), with 16-byte aligned pairs (checked on the host).
+struct RawOp {
+  const float2* p; long long s0, s1;  // A: (m, k) at p[m s0 + k s1]; B: (k, n) at p[k s0 + n s1]
+  int conj, kmajor, rows, K;          // kmajor: A s1 == 1, B s0 == 1; rows: M (A) or N (B)
+};
+
+__device__ __forceinline__ float4 ld_pair(const float2* p, bool two, bool one) {
+  if (two) return *reinterpret_cast<const float4*>(p);
+  if (one) { const float2 v = *p; return make_float4(v.x, v.y, 0.f, 0.f); }
+  return make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ float4 conj4(float4 v, int c) { if (c) { v.y = -v.y; v.w = -v.w; } return v; }
+__device__ __forceinline__ void split_store(uint8_t* hi, uint8_t* lo, uint32_t off, float4 v, bool three) {
+  const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+  *reinterpret_cast<float4*>(hi + off) = h;
+  if (three) *reinterpret_cast<float4*>(lo + off) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+}
+__device__ __forceinline__ uint32_t sw128(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
+
+// Raw values of stage i (complex K from (kt0 + i) * 16) for converter thread ct: A as four
+// 16-byte chunks (K-major: tile row idx / 8, pair idx % 8) or two 2 x 2 blocks (M-major:
+// M pair idx % 64, K pair idx / 64), idx = ct + 256 u; B likewise with BN / 2 columns.
+template <int BN>
+__device__ __forceinline__ void fz_load(float4 (&xa)[4], float4 (&xb)[BN / 64], const RawOp& ra, const RawOp& rb,
+                                        int kt0, int i, int ct, long long ma0, int nc0, int Kc) {
+  constexpr int NB = BN / 64;
+  const int kc0 = (kt0 + i) * (BK / 2);
+  if (ra.kmajor) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = ct + 256 * u, r = idx >> 3, c = idx & 7;
+      const long long m = ma0 + r;
+      const int k = kc0 + 2 * c;
+      const bool in = m < ra.rows;
+      xa[u] = ld_pair(ra.p + m * ra.s0 + k, in && k + 1 < Kc, in && k < Kc);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int idx = ct + 256 * u, mp = idx & 63, kp = idx >> 6;
+      const long long m = ma0 + 2 * mp;
+      const int k = kc0 + 2 * kp;
+      const bool two = m + 1 < ra.rows, one = m < ra.rows;
+      xa[2 * u] = ld_pair(ra.p + (long long)k * ra.s1 + m, two && k < Kc, one && k < Kc);
+      xa[2 * u + 1] = ld_pair(ra.p + (long long)(k + 1) * ra.s1 + m, two && k + 1 < Kc, one && k + 1 < Kc);
+    }
+  }
+  if (rb.kmajor) {
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int idx = ct + 256 * u, nl = idx >> 3, c = idx & 7;
+      const long long n = nc0 + nl;
+      const int k = kc0 + 2 * c;
+      const bool in = n < rb.rows;
+      xb[u] = ld_pair(rb.p + n * rb.s1 + k, in && k + 1 < Kc, in && k < Kc);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < NB / 2; ++u) {
+      const int idx = ct + 256 * u, np = idx % (BN / 4), kp = idx / (BN / 4);
+      const long long n = nc0 + 2 * np;
+      const int k = kc0 + 2 * kp;
+      const bool two = n + 1 < rb.rows, one = n < rb.rows;
+      xb[2 * u] = ld_pair(rb.p + (long long)k * rb.s0 + n, two && k < Kc, one && k < Kc);
+      xb[2 * u + 1] = ld_pair(rb.p + (long long)(k + 1) * rb.s0 + n, two && k + 1 < Kc, one && k + 1 < Kc);
+    }
+  }
+}
+
+// B'^T rows 2 nl: (Re b, -Im b), 2 nl + 1: (Im b, Re b) for the two K values of chunk c
+__device__ __forceinline__ void fz_emb(uint8_t* bhi, uint8_t* blo, int nl, int c, float4 v, int conj, bool three) {
+  v = conj4(v, conj);
+  split_store(bhi, blo, sw128(2 * nl, c), make_float4(v.x, -v.y, v.z, -v.w), three);
+  split_store(bhi, blo, sw128(2 * nl + 1, c), make_float4(v.y, v.x, v.w, v.z), three);
+}
+
+template <bool THREE, int BN>
+__device__ __forceinline__ void fz_store(const float4 (&xa)[4], const float4 (&xb)[BN / 64], const RawOp& ra,
+                                         const RawOp& rb, uint8_t* ahi, uint8_t* alo, uint8_t* bhi, uint8_t* blo,
+                                         int ct) {
+  constexpr int NB = BN / 64;
+  if (ra.kmajor) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = ct + 256 * u, r = idx >> 3, c = idx & 7;
+      split_store(ahi, alo, sw128(r, c), conj4(xa[u], ra.conj), THREE);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const int idx = ct + 256 * u, mp = idx & 63, kp = idx >> 6;
+      const float4 p0 = xa[2 * u], p1 = xa[2 * u + 1];  // (k, m m+1), (k+1, m m+1)
+      split_store(ahi, alo, sw128(2 * mp, kp), conj4(make_float4(p0.x, p0.y, p1.x, p1.y), ra.conj), THREE);
+      split_store(ahi, alo, sw128(2 * mp + 1, kp), conj4(make_float4(p0.z, p0.w, p1.z, p1.w), ra.conj), THREE);
+    }
+  }
+  if (rb.kmajor) {
+#pragma unroll
+    for (int u = 0; u < NB; ++u) {
+      const int idx = ct + 256 * u;
+      fz_emb(bhi, blo, idx >> 3, idx & 7, xb[u], rb.conj, THREE);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < NB / 2; ++u) {
+      const int idx = ct + 256 * u, np = idx % (BN / 4), kp = idx / (BN / 4);
+      const float4 p0 = xb[2 * u], p1 = xb[2 * u + 1];  // (k, n n+1), (k+1, n n+1)
+      fz_emb(bhi, blo, 2 * np, kp, make_float4(p0.x, p0.y, p1.x, p1.y), rb.conj, THREE);
+      fz_emb(bhi, blo, 2 * np + 1, kp, make_float4(p0.z, p0.w, p1.z, p1.w), rb.conj, THREE);
+    }
+  }
+}
+
+// 128-column tiles only: with ten warps one SM sub-partition holds three of them, so a
+// thread has at most 168 registers, which a 256-column tile's 128 FP32 sums plus a stage of
+// raw operand values in flight would exceed (such products keep the separate preparation)
+template <bool THREE, int BN>
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_tc_gemm_fz(RawOp ra, RawOp rb, Epi epi, int kt_per_split, float* partial, int m_off, unsigned* err) {
+  using C = Cfg<THREE, BN>;
+  constexpr int B_TILE = C::B_TILE, TMEM_COLS = C::TMEM_COLS;
+  static_assert(BM * (BN + 4) * 4 <= C::STAGES * C::STAGE_BYTES, "staged epilogue tile");
+  static_assert(BN == 128, "in-kernel preparation: 128-column tiles");
+  constexpr uint32_t kIdesc = C::IDESC;
+  constexpr int HW = BN / 2;   // columns per epilogue thread
+  constexpr int NB = BN / 64;  // B chunks (or 2 x 2 blocks / 2) per converter thread
+  pdl_launch_dependents();
+  pdl_wait();
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = smem_raw + ((1024 - (s_u32(smem_raw) & 1023)) & 1023);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE_BYTES);
+  uint64_t* empty = full + C::STAGES;
+  uint64_t* accf = empty + C::STAGES;
+  uint64_t* acce = accf + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  const int Kc = ra.K;                       // complex K
+  const int nk_all = (2 * Kc + BK - 1) / BK;  // stages of 16 complex K
+  const int kt0 = blockIdx.z * kt_per_split;
+  const int kt1 = min(nk_all, kt0 + kt_per_split);
+  const int nk = max(0, kt1 - kt0);
+  constexpr int KCH = promo_chunk<THREE>();
+  const int nchunks = (nk + KCH - 1) / KCH;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < C::STAGES; ++s) { mbar_init(&full[s], NEPI); mbar_init(&empty[s], 1); }
+    for (int b = 0; b < 2; ++b) { mbar_init(&accf[b], 1); mbar_init(&acce[b], NEPI); }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     s_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  auto stage_a_hi = [&](int s) { return smem + s * C::STAGE_BYTES; };
+  auto stage_b_hi = [&](int s) { return smem + s * C::STAGE_BYTES + A_TILE; };
+  auto stage_a_lo = [&](int s) { return smem + s * C::STAGE_BYTES + A_TILE + B_TILE; };
+  auto stage_b_lo = [&](int s) { return smem + s * C::STAGE_BYTES + 2 * A_TILE + B_TILE; };
+
+  if (warp == 1) {
+    if (lane == 0) {
+      bool ok = true;
+      for (int c = 0; c < nchunks && ok; ++c) {
+        const int b = c & 1;
+        if (c >= 2 && !mbar_wait(&acce[b], (uint32_t)(((c >> 1) - 1) & 1))) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t acc_t = tmem + (uint32_t)(b * BN);
+        const int i1 = min(nk, (c + 1) * KCH);
+        for (int i = c * KCH; i < i1; ++i) {
+          const int s = i % C::STAGES;
+          if (!mbar_wait(&full[s], (uint32_t)((i / C::STAGES) & 1))) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t a_hi = s_u32(stage_a_hi(s)), b_hi = s_u32(stage_b_hi(s));
+          const uint32_t a_lo = s_u32(stage_a_lo(s)), b_lo = s_u32(stage_b_lo(s));
+#pragma unroll
+          for (int k = 0; k < BK / 8; ++k) {
+            const uint32_t off = k * 32;
+            const uint32_t acc = (i > c * KCH || k > 0) ? 1u : 0u;
+            if (THREE) {
+              tc_mma(acc_t, desc_sw128(a_lo + off), desc_sw128(b_hi + off), kIdesc, acc);
+              tc_mma(acc_t, desc_sw128(a_hi + off), desc_sw128(b_lo + off), kIdesc, 1u);
+              tc_mma(acc_t, desc_sw128(a_hi + off), desc_sw128(b_hi + off), kIdesc, 1u);
+            } else {
+              tc_mma(acc_t, desc_sw128(a_hi + off), desc_sw128(b_hi + off), kIdesc, acc);
+            }
+          }
+          tc_commit(&empty[s]);
+        }
+        tc_commit(&accf[b]);
+      }
+      if (!ok) atomicOr(err, DEVERR_TIMEOUT);
+    }
+  } else if (warp >= 2) {
+    // converter + epilogue warps 2..9: TMEM lane quarter q, column half h
+    const int q = warp & 3;
+    const int h = (warp - 2) >> 2;
+    const int ct = threadIdx.x - 64;  // 0 .. 255
+    const int row = m0 + q * 32 + lane;
+    const long long ma0 = (long long)m_off + m0;  // first row of opA in this tile
+    const int nc0 = n0 / 2;                        // first complex column of opB in this tile
+    float sum[HW];
+#pragma unroll
+    for (int j = 0; j < HW; ++j) sum[j] = 0.f;
+    float4 xa[4], xb[NB];
+    // raw values of stage i and their conversion into stage slot s (fz_load / fz_store)
+    bool ok = true;
+    int drained = 0;  // chunks added into the registers so far
+    auto drain = [&](int c) {
+      const int b = c & 1;
+      if (!mbar_wait(&accf[b], (uint32_t)((c >> 1) & 1))) { ok = false; return; }
+      tc_fence_after();
+#pragma unroll
+      for (int blk = 0; blk < HW / 32; ++blk) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * BN + h * HW + blk * 32);
+        TMEM_LD32(taddr, r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sum[blk * 32 + j] += __uint_as_float(r[j]);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acce[b]);
+    };
+    if (nk > 0) fz_load<BN>(xa, xb, ra, rb, kt0, 0, ct, ma0, nc0, Kc);
+    for (int i = 0; i < nk && ok; ++i) {
+      const int s = i % C::STAGES;
+      if (!mbar_wait(&empty[s], (uint32_t)(((i / C::STAGES) & 1) ^ 1))) { ok = false; break; }
+      fz_store<THREE, BN>(xa, xb, ra, rb, stage_a_hi(s), stage_a_lo(s), stage_b_hi(s), stage_b_lo(s), ct);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&full[s]);
+      if (i + 1 < nk) fz_load<BN>(xa, xb, ra, rb, kt0, i + 1, ct, ma0, nc0, Kc);
+      // the previous chunk, once the first stage of the next one is with the tensor core
+      if (i % KCH == 0 && i > 0 && ok) { drain(i / KCH - 1); ++drained; }
+    }
+    while (ok && drained < nchunks) { drain(drained); ++drained; }
+    if (!ok && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");  // every stage consumed: buffers reusable
+    if (partial || epi.scn == 1) {
+      constexpr int LDT = BN + 4;
+      float* tile = reinterpret_cast<float*>(smem);
+      if (ok) {
+        float* trow = tile + (q * 32 + lane) * LDT + h * HW;
+#pragma unroll
+        for (int j = 0; j < HW; j += 4)
+          *reinterpret_cast<float4*>(trow + j) = make_float4(sum[j], sum[j + 1], sum[j + 2], sum[j + 3]);
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(32 * NEPI) : "memory");
+      if (ok) {
+        const bool use_beta = (epi.beta.x != 0.f || epi.beta.y != 0.f);
+        for (int r = warp - 2; r < BM; r += NEPI) {
+          const int grow = m0 + r;
+          if (grow >= epi.M) break;
+          const float* tr = tile + r * LDT;
+          if (partial) {
+            float* prow = partial + ((long long)blockIdx.z * epi.M + grow) * (2LL * epi.Nc);
+            for (int j = lane; j < BN; j += 32)
+              if (n0 + j < 2 * epi.Nc) prow[n0 + j] = tr[j];
+          } else {
+            float2* crow = epi.C + (long long)grow * epi.scm;
+            for (int c = lane; c < BN / 2; c += 32) {
+              const int n = n0 / 2 + c;
+              if (n < epi.Nc) {
+                const float2 a = *reinterpret_cast<const float2*>(tr + 2 * c);
+                float2 v;
+                v.x = epi.alpha.x * a.x - epi.alpha.y * a.y;
+                v.y = epi.alpha.x * a.y + epi.alpha.y * a.x;
+                if (use_beta) {
+                  const float2 cv = crow[n];
+                  v.x += epi.beta.x * cv.x - epi.beta.y * cv.y;
+                  v.y += epi.beta.x * cv.y + epi.beta.y * cv.x;
+                }
+                crow[n] = v;
+              }
+            }
+          }
+        }
+      }
+    } else if (ok && row < epi.M) {
+      const int col0 = n0 + h * HW;
+      const bool use_beta = (epi.beta.x != 0.f || epi.beta.y != 0.f);
+      float2* crow = epi.C + (long long)row * epi.scm;
+#pragma unroll
+      for (int j = 0; j < HW / 2; ++j) {
+        const int n = (col0 >> 1) + j;
+        if (n < epi.Nc) {
+          const float ar = sum[2 * j], ai = sum[2 * j + 1];
+          float2 v;
+          v.x = epi.alpha.x * ar - epi.alpha.y * ai;
+          v.y = epi.alpha.x * ai + epi.alpha.y * ar;
+          float2* p = crow + (long long)n * epi.scn;
+          if (use_beta) {
+            const float2 cv = *p;
+            v.x += epi.beta.x * cv.x - epi.beta.y * cv.y;
+            v.y += epi.beta.x * cv.y + epi.beta.y * cv.x;
+          }
+          *p = v;
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    if (nchunks > 0) {
+      const int c = nchunks - 1;
+      if (!mbar_wait(&accf[c & 1], (uint32_t)((c >> 1) & 1)) && lane == 0) atomicOr(err, DEVERR_TIMEOUT);
+    }
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS)
+                 : "memory");
+  }
 }
 
 // ------------------------------------------------------------------ FP64 emulation
@@ -1030,6 +1365,41 @@ int launch_tc(dim3 grid, cudaStream_t st, const CUtensorMap& a_hi, const CUtenso
   return QRTEBD_OK;
 }
 
+template <bool THREE, int BN> int set_fz_attrs_once() {
+  static std::once_flag once;
+  static cudaError_t e = cudaSuccess;
+  std::call_once(once, [] {
+    e = cudaFuncSetAttribute(k_tc_gemm_fz<THREE, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             Cfg<THREE, BN>::SMEM);
+  });
+  QR_CUDA_TRY(e);
+  return QRTEBD_OK;
+}
+
+template <bool THREE, int BN>
+int launch_fz(dim3 grid, cudaStream_t st, const RawOp& ra, const RawOp& rb, const Epi& e, int per, float* part,
+              int m_off, unsigned* err) {
+  QR_TRY((set_fz_attrs_once<THREE, BN>()));
+  QR_CUDA_TRY(launch_pdl(k_tc_gemm_fz<THREE, BN>, grid, dim3(NTHREADS), Cfg<THREE, BN>::SMEM, st, ra, rb, e,
+                         per, part, m_off, err));
+  return QRTEBD_OK;
+}
+
+// Operand preparation as a separate pass (1, the default) or inside the GEMM kernel (0)
+std::atomic<int> g_prep_mode{1};
+
+// The in-kernel preparation reads pairs of complex values with 16-byte loads: an operand
+// qualifies when it is contiguous along K or along its other index, the other stride is
+// even and the base is 16-byte aligned.
+bool raw_layout(const float2* p, long long s_rows, long long s_k, bool is_b, int* kmajor) {
+  // A: (m, k) at p[m s_rows + k s_k]; B: (k, n) at p[k s_k + n s_rows]
+  if ((reinterpret_cast<uintptr_t>(p) & 15) != 0) return false;
+  if (s_k == 1 && s_rows % 2 == 0) { *kmajor = 1; return true; }
+  if (s_rows == 1 && s_k % 2 == 0) { *kmajor = 0; return true; }
+  (void)is_b;
+  return false;
+}
+
 // tuning table and the recording pass
 std::mutex g_tune_mu;
 std::map<TcShape, TcTuned> g_tune;
@@ -1053,6 +1423,8 @@ void tc_carve(Arena& ar, int max_m, int max_k, int max_n, TcWorkspace& w) {
   w.p_cap = (size_t)1 << 23;  // 32 MB of split-K partial sums
   w.partial = ar.take<float>(w.p_cap);
 }
+
+int tc_prep_mode(int mode) { return g_prep_mode.exchange(mode); }
 
 void tc_invalidate(TcWorkspace& w) {
   w.a[0].valid = w.a[1].valid = false;
@@ -1089,10 +1461,26 @@ int tc_gemm_cfg(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStrea
   if ((size_t)M * ld > w.a_cap || (size_t)2 * N * ld > w.b_cap || !w.a[0].hi || !w.b.hi)
     return gemm_simt<float>(g0, st, nullptr, 0, prof_family == PROF_TC_GEMM ? PROF_SIMT_GEMM : prof_family);
   QR_TRY(get_encode());
-
-  // ---- A' and B'^T, in one launch. A' of an operand marked for reuse lives in slot 0,
-  // which no other operand overwrites, so it survives the GEMMs in between (the QR's);
-  // every other A' goes to slot 1
+  const TcShape key{M, N, K, three ? 1 : 0};
+  TcConfig cfg;
+  bool have = false;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_recording) g_recorded.push_back(key);
+    if (force) { cfg = *force; have = true; }
+    else {
+      auto it = g_tune.find(key);
+      if (it != g_tune.end()) { cfg = it->second.cfg; have = true; }
+    }
+  }
+  const int bn = (have && cfg.bn == 128) ? 128 : 256;
+  // Operand preparation inside the GEMM kernel where the layouts allow, for 128-column
+  // tiles only (register budget); otherwise A' and B'^T in one separate launch. A' of an
+  // operand marked for reuse lives in slot 0, which no other operand overwrites, so it
+  // survives the GEMMs in between (the QR's); every other A' goes to slot 1
+  int a_km = 0, b_km = 0;
+  const bool fused = bn == 128 && g_prep_mode.load() == 0 && raw_layout(g.A, g.sam, g.sak, false, &a_km) &&
+                     raw_layout(g.B, g.sbn, g.sbk, true, &b_km);
   TcSlot* sa = nullptr;
   if (cacheable) {
     TcSlot& s = w.a[0];
@@ -1100,9 +1488,9 @@ int tc_gemm_cfg(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStrea
         s.conj == g.conj_a && s.three == three && s.ld == ld)
       sa = &s;
   }
-  const bool need_a = (sa == nullptr);
-  if (need_a) sa = &w.a[cacheable ? 0 : 1];
-  {
+  const bool need_a = !fused && (sa == nullptr);
+  if (sa == nullptr) sa = &w.a[cacheable ? 0 : 1];
+  if (!fused) {
     PrepJob ja{g.A, g.sam, g.sak, g.conj_a ? 1 : 0, M, K, sa->hi, sa->lo, ld,
                need_a ? (int)ceil_div(K, 32) : 0, need_a ? (int)ceil_div(M, 32) : 0};
     PrepJob jb{g.B, g.sbk, g.sbn, g.conj_b ? 1 : 0, N, K, w.b.hi, w.b.lo, ld,
@@ -1118,24 +1506,15 @@ int tc_gemm_cfg(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStrea
     sa->valid = cacheable; sa->src = g.A; sa->s0 = g.sam; sa->s1 = g.sak; sa->rows = M; sa->cols = K;
     sa->conj = g.conj_a; sa->three = three; sa->ld = ld;
   }
-  const TcShape key{M, N, K, three ? 1 : 0};
-  TcConfig cfg;
-  bool have = false;
-  {
-    std::lock_guard<std::mutex> lk(g_tune_mu);
-    if (g_recording) g_recorded.push_back(key);
-    if (force) { cfg = *force; have = true; }
-    else {
-      auto it = g_tune.find(key);
-      if (it != g_tune.end()) { cfg = it->second.cfg; have = true; }
-    }
-  }
-  const int bn = (have && cfg.bn == 128) ? 128 : 256;
   CUtensorMap ta_hi, ta_lo, tb_hi, tb_lo;
-  QR_TRY(make_map(&ta_hi, sa->hi, M, 2 * K, ld, BM));
-  QR_TRY(make_map(&ta_lo, three ? sa->lo : sa->hi, M, 2 * K, ld, BM));
-  QR_TRY(make_map(&tb_hi, w.b.hi, 2 * N, 2 * K, ld, bn));
-  QR_TRY(make_map(&tb_lo, three ? w.b.lo : w.b.hi, 2 * N, 2 * K, ld, bn));
+  if (!fused) {
+    QR_TRY(make_map(&ta_hi, sa->hi, M, 2 * K, ld, BM));
+    QR_TRY(make_map(&ta_lo, three ? sa->lo : sa->hi, M, 2 * K, ld, BM));
+    QR_TRY(make_map(&tb_hi, w.b.hi, 2 * N, 2 * K, ld, bn));
+    QR_TRY(make_map(&tb_lo, three ? w.b.lo : w.b.hi, 2 * N, 2 * K, ld, bn));
+  }
+  const RawOp ra{g.A, g.sam, g.sak, g.conj_a ? 1 : 0, a_km, M, K};
+  const RawOp rb{g.B, g.sbk, g.sbn, g.conj_b ? 1 : 0, b_km, N, K};
 
   Epi epi{g.C, g.scm, g.scn, g.alpha, g.beta, M, N};
   const int nx = (int)ceil_div(2LL * N, bn), ny = (int)ceil_div(M, BM);
@@ -1154,7 +1533,10 @@ int tc_gemm_cfg(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStrea
     dim3 grid((unsigned)nx, (unsigned)nty, (unsigned)splits);
     {
       ProfScope prof(prof_family, st, 8.0 * e.M * N * K);
-      if (three && bn == 256)
+      if (fused) {
+        if (three) QR_TRY((launch_fz<true, 128>(grid, st, ra, rb, e, per, part, m_off, err)));
+        else QR_TRY((launch_fz<false, 128>(grid, st, ra, rb, e, per, part, m_off, err)));
+      } else if (three && bn == 256)
         QR_TRY((launch_tc<true, 256>(grid, st, ta_hi, ta_lo, tb_hi, tb_lo, e, 2 * K, per, part, m_off, err)));
       else if (three)
         QR_TRY((launch_tc<true, 128>(grid, st, ta_hi, ta_lo, tb_hi, tb_lo, e, 2 * K, per, part, m_off, err)));

@@ -100,5 +100,7 @@ bool tc_tune_get(const TcShape& s, TcConfig* cfg);
 void tc_tune_put(const TcTuned& t);
 std::vector<TcTuned> tc_tune_list();
 void tc_tune_clear();
+// Operand preparation: 0 inside the GEMM kernel (where the layout allows), 1 separate pass.
+int tc_prep_mode(int mode);  // sets the mode, returns the previous one
 
 }  // namespace qrtebd

@@ -98,6 +98,7 @@ def _load():
         "qrtebd_autotune_entry": (I, [I, C.POINTER(I), C.POINTER(I), C.POINTER(D)]),
         "qrtebd_autotune_set": (I, [C.POINTER(I), C.POINTER(I)]),
         "qrtebd_autotune_clear": (None, []),
+        "qrtebd_tc_operand_prep": (I, [I, C.POINTER(I)]),
         "qrtebd_cbe_decompose_workspace_size": (S, [I, I]),
         "qrtebd_cbe_decompose": (I, [I, I, P, LL, P, P, P, S, P, P]),
         "qrtebd_householder_qr": (I, [I, I, I, P, LL, P, LL, P, S, P]),
@@ -618,6 +619,14 @@ def autotune_set(shape, config):
 
 def autotune_clear():
     _lib.qrtebd_autotune_clear()
+
+
+def tc_operand_prep(mode):
+    """Operand preparation of the complex64 tensor-core products: 1 (default) as a separate
+    pass, 0 inside the GEMM kernel (128-column tiles); returns the previous mode."""
+    prev = C.c_int(0)
+    check(_lib.qrtebd_tc_operand_prep(int(mode), C.byref(prev)), "tc_operand_prep")
+    return prev.value
 
 
 def autotune_save(path):

@@ -190,3 +190,61 @@ def test_zgemm_emulated_fp64_exact_on_integers():
     out = L.zgemm("c128_oz", dev(A), dev(B))
     L.stream_check()
     assert np.array_equal(out.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("prec", ["c64_3xtf32", "c64_tf32"])
+@pytest.mark.parametrize("m,n,k", [(128, 64, 128), (640, 384, 1000), (300, 170, 334), (258, 1030, 516),
+                                   (4864, 1024, 512)])
+@pytest.mark.parametrize("ops", ["nn", "nc", "ct", "tn", "cc"])
+def test_zgemm_operand_prep_in_kernel(prec, m, n, k, ops):
+    # 128-column tiles forced through the tuning table, so the in-kernel preparation runs
+    # (raw operands split and embedded by the epilogue warps into swizzled stages) for every
+    # layout it takes: A contiguous along K or M, B along K or N, conjugated, K ragged
+    # against the 16-value stage; it must equal the separate pass bit for bit and numpy
+    import torch
+    from paper_2212_09782_b300 import lib as L
+    three = 1 if prec == "c64_3xtf32" else 0
+    M, N = (n, m) if n > m else (m, n)
+    r = W.rng(m * 1000 + n * 10 + k)
+    ta, tb = ops[0] in "tc", ops[1] in "tc"
+    ca, cb = ops[0] == "c", ops[1] == "c"
+    A = W.complex_gaussian(r, (k, m) if ta else (m, k)).astype(np.complex64)
+    B = W.complex_gaussian(r, (n, k) if tb else (k, n)).astype(np.complex64)
+    C0 = W.complex_gaussian(r, (m, n)).astype(np.complex64)
+    dev = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    alpha, beta = 0.7 - 0.2j, -0.5 + 0.25j
+    outs = []
+    prev = L.tc_operand_prep(0)
+    try:
+        L.autotune_set((M, N, k, three), (128, 0, 1))
+        for mode in (0, 1):
+            L.tc_operand_prep(mode)
+            Cd = dev(C0)
+            L.zgemm(prec, dev(A), dev(B), conj_a=ca, conj_b=cb, trans_a=ta, trans_b=tb, alpha=alpha,
+                    beta=beta, C_out=Cd)
+            L.stream_check()
+            outs.append(Cd.cpu().numpy().astype(np.complex128))
+    finally:
+        L.tc_operand_prep(prev)
+        L.autotune_clear()
+    assert np.array_equal(outs[0], outs[1])
+    opA = A.astype(np.complex128)
+    opA = opA.T if ta else opA
+    opA = opA.conj() if ca else opA
+    opB = B.astype(np.complex128)
+    opB = opB.T if tb else opB
+    opB = opB.conj() if cb else opB
+    ref = alpha * (opA @ opB) + beta * C0.astype(np.complex128)
+    err = np.abs(outs[0] - ref).max() / (np.abs(alpha) * np.sqrt(k) + np.abs(beta))
+    assert err < tol(prec, k), err
+
+
+def test_operand_prep_mode_switch():
+    from paper_2212_09782_b300 import lib as L
+    prev = L.tc_operand_prep(0)
+    try:
+        assert L.tc_operand_prep(1) == 0
+        with pytest.raises(L.QrtebdError):
+            L.tc_operand_prep(2)
+    finally:
+        L.tc_operand_prep(prev)
