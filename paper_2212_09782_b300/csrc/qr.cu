@@ -171,9 +171,10 @@ __device__ __forceinline__ void st_async_16(uint32_t addr, double2 v, uint32_t m
                ::"r"(addr), "d"(v.x), "d"(v.y), "r"(mbar) : "memory");
 }
 
-// reflector scalars (zlarfg convention) from ||x||^2 below the pivot and alpha, with
-// correctly rounded square root and divisions: the unitarity of H = I - tau v v^dag
-// rests on tau and scale agreeing with ||v|| to working precision
+// reflector scalars (zlarfg convention) from ||x||^2 below the pivot and alpha, with a
+// correctly rounded square root and tau, scale within about one unit in the last place of
+// correctly rounded (reciprocal forms, as LAPACK's own): the unitarity of
+// H = I - tau v v^dag rests on tau and scale agreeing with ||v|| to working precision
 template <typename T>
 __device__ __forceinline__ void reflector(T xn2, T alr, T ali, T& beta, T& tr, T& ti, T& sr, T& si) {
   beta = alr; tr = ti = sr = si = T(0);
@@ -183,12 +184,24 @@ __device__ __forceinline__ void reflector(T xn2, T alr, T ali, T& beta, T& tr, T
   if (!(xn2 == T(0) && ali == T(0)) && tot > T(16) * std::numeric_limits<T>::min()) {
     const T nrm = sqrt(tot);
     beta = alr >= T(0) ? -nrm : nrm;
-    tr = (beta - alr) / beta;
-    ti = -ali / beta;
-    // scale = 1 / (alpha - beta) by Smith's division; |alr - beta| >= |ali|
     const T dr = alr - beta, di = ali;
-    const T rt = di / dr, den = dr + di * rt;
-    sr = T(1) / den; si = -rt / den;
+    // |alpha - beta|^2 <= 4 tot: below the overflow edge, 1/beta and 1/|alpha - beta|^2 in
+    // parallel give tau and scale by products (two divisions off each other's path instead
+    // of five in a chain; on B300 each FP64 division is a long FP64 sequence); near it,
+    // the divisions one by one with scale = 1 / (alpha - beta) by Smith's division
+    // (|alr - beta| >= |ali|)
+    if (tot < T(0.25) * std::numeric_limits<T>::max()) {
+      const T rb = T(1) / beta, q = T(1) / (dr * dr + di * di);
+      tr = -dr * rb;
+      ti = -ali * rb;
+      sr = dr * q;
+      si = -di * q;
+    } else {
+      tr = (beta - alr) / beta;
+      ti = -ali / beta;
+      const T rt = di / dr, den = dr + di * rt;
+      sr = T(1) / den; si = -rt / den;
+    }
   }
 }
 
@@ -1341,14 +1354,18 @@ int smem_cap() {
 }
 
 // Cluster size, slab rows per CTA and panel width for a panel of mr rows: the
-// smallest power-of-two cluster giving every CTA at most ~320 slab rows (a 5120-row panel
-// takes 16 CTAs, a 2048-row one 8, which leaves SMs to concurrent updates), grown (then
-// the width halved) until the panel fits in shared memory.
+// smallest power-of-two cluster giving every CTA at most ~320 slab rows for complex64 (a
+// 5120-row panel takes 16 CTAs, a 2048-row one 8, which leaves SMs to concurrent updates;
+// the panel is bound by the latency of its per-column exchange), at most ~24 for
+// complex128, whose panel is bound by the FP64 work of each CTA (~230 cycles per row and
+// column on B300's FP64 pipe, against ~3k for a column's exchange and reflector), grown
+// (then the width halved) until the panel fits in shared memory.
 template <typename T> ClusterChoice choose_cluster(int mr, int kb_want) {
   const int cmax = g_max_cluster > 0 ? g_max_cluster : 16;
   const size_t cap = (size_t)smem_cap();
+  const int rows = std::is_same<T, double>::value ? 24 : 320;
   int cs = 1;
-  while (cs < cmax && (long long)cs * 320 < mr) cs *= 2;
+  while (cs < cmax && (long long)cs * rows < mr) cs *= 2;
   for (int kb = kb_want; kb >= 1; kb /= 2) {
     for (int s = cs; s <= cmax; s *= 2) {
       const int rps = (int)ceil_div(std::max(mr - kb, 0), s);
