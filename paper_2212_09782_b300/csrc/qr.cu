@@ -34,6 +34,7 @@ namespace {
 constexpr int PT = 256;      // threads per panel CTA
 constexpr int KBMAX = 32;    // widest panel
 constexpr int NBO = 128;     // outer block of the two-level blocking
+constexpr int PG_MAX = 148;  // CTAs of the complex128 grid panel (one per SM at most)
 
 template <typename T> struct PanelArgs {
   cx<T>* A; long long lda; int m; int k0; int kb;
@@ -566,6 +567,247 @@ __global__ void __launch_bounds__(PT) k_qr_panel(PanelArgs<T> a) {
   }
   cl.sync();
 }
+
+// Grid form of the complex128 panel. Its cost is the FP64 work of each CTA (~230 cycles per
+// row and column on B300's FP64 pipe), so for tall panels many CTAs with few slab rows beat
+// one cluster of at most 16: a cooperative launch of G CTAs, the local phases of k_qr_panel
+// unchanged (every CTA holds the kb pivot rows and its slab), and per column one exchange
+// through global memory in place of the cluster's remote stores: each CTA writes its
+// partial sums (the 32 slots and the norm) to part[parity][cta], a grid barrier (bounded
+// wait), then every CTA adds the G partials in the same order and forms the same reflector.
+// The parity double buffer lets the next column's writes go ahead while slower CTAs still
+// read this column's sums.
+template <typename T, int NW>
+__device__ __forceinline__ void panel_exchange_g(const PanelShared<T>& sh, const cx<T>* prow, int jn, int kb,
+                                                 int rank, int G, cx<T>* part, unsigned* bar, unsigned* err,
+                                                 bool& ok) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const cx<T> zero = mk<T>(0, 0);
+  const int buf = jn & 1;
+  constexpr int PS = SLOTS + 1;  // a CTA's record: 32 slots, then the norm
+  if (warp == 0) {
+    cx<T> s = zero;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) s = cadd<T>(s, sh.wps[w * SLOTS + lane]);
+    T nrm = T(0);
+#pragma unroll
+    for (int w = 0; w < NW; ++w) nrm += sh.wpn[w * 2];
+    cx<T>* mine = part + ((long long)buf * G + rank) * PS;
+    mine[lane] = s;
+    if (lane == 0) mine[SLOTS] = mk<T>(nrm, T(0));
+    sh.pivb[buf * SLOTS + lane] = prow[min(lane, kb - 1)];
+  }
+  if (!grid_barrier(bar, (unsigned)G, err)) ok = false;
+  // the G records summed in a fixed order, identical in every CTA: warp w loads the records
+  // of CTAs w, w + NW, ... at once (lane = slot, lane 0 also the norm) and adds them in
+  // order, then warp 0 adds the warps' sums in order
+  if (ok) {
+    constexpr int PW = (PG_MAX + NW - 1) / NW;
+    const cx<T>* all = part + (long long)buf * G * PS;
+    cx<T> v[PW];
+    T nv[PW];
+#pragma unroll
+    for (int i = 0; i < PW; ++i) {
+      const int g = warp + NW * i;
+      v[i] = g < G ? __ldcg(all + (long long)g * PS + lane) : zero;
+      nv[i] = (g < G && lane == 0) ? __ldcg(all + (long long)g * PS + SLOTS).x : T(0);
+    }
+    cx<T> sw = zero;
+    T nw = T(0);
+#pragma unroll
+    for (int i = 0; i < PW; ++i) { sw = cadd<T>(sw, v[i]); nw += nv[i]; }
+    sh.wps[warp * SLOTS + lane] = sw;  // the CTA's own partials were read before the barrier
+    if (lane == 0) sh.wpn[warp * 2] = nw;
+  }
+  __syncthreads();
+  if (warp == 0 && ok) {
+    cx<T> S = zero;
+    T ns = T(0);
+#pragma unroll
+    for (int w = 0; w < NW; ++w) { S = cadd<T>(S, sh.wps[w * SLOTS + lane]); ns += sh.wpn[w * 2]; }
+    const cx<T>* piv = sh.pivb + buf * SLOTS;
+    const cx<T> pc = piv[min(lane, kb - 1)];
+    const cx<T> alpha = piv[jn];
+    T beta, tr, ti, sr, si;
+    reflector(ns, alpha.x, alpha.y, beta, tr, ti, sr, si);
+    if (lane == 0 && rank == 0 && !(isfinite(beta) && isfinite(sr) && isfinite(si)))
+      atomicOr(err, DEVERR_NUMERIC);
+    const cx<T> sc = mk<T>(sr, si), tau = mk<T>(tr, ti);
+    const bool u = lane > jn && lane < kb;
+    const cx<T> cwl = u ? cmul<T>(cconj<T>(tau), cadd<T>(pc, cmul<T>(cconj<T>(sc), S))) : zero;
+    if (lane < jn) {
+      const cx<T> gv = cmul<T>(cconj<T>(sh.scl[lane]), cadd<T>(cconj<T>(pc), cmul<T>(sc, cconj<T>(S))));
+      sh.Ts[lane * (KBMAX + 1) + jn] = gv;
+    }
+    cx<T>* bb = sh.bc + buf * (SLOTS + 2);
+    bb[lane] = cwl;
+    if (lane == 0) { bb[SLOTS] = sc; sh.taus[jn] = tau; sh.scl[jn] = sc; sh.bet[jn] = mk<T>(beta, 0); }
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PT) k_qr_panel_g(PanelArgs<T> a, cx<T>* part, unsigned* bar) {
+  constexpr int NT = PT;
+  using L = PanelSmem<T>;
+  pdl_launch_dependents();
+  pdl_wait();
+  constexpr int NW = NT / 32;
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int CS = (int)gridDim.x;
+  const int rank = (int)blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int kb = a.kb, ldp = kb + 1, rps = a.rps;
+  const int mr = a.m - a.k0;
+  const int s0 = kb + rank * rps;                           // first slab row (panel index)
+  const int nslab = max(0, min(rps, mr - s0));
+  const int nloc = kb + nslab;
+  const int rpw = (nloc + NW - 1) / NW;
+  const int p0 = min(nloc, warp * rpw), p1 = min(nloc, p0 + rpw);
+  const bool top_counts = rank == 0;                        // top rows enter rank 0's sums only
+  auto grow = [&](int p) { return p < kb ? p : s0 + (p - kb); };
+
+  unsigned char* q = sm;
+  cx<T>* P = reinterpret_cast<cx<T>*>(q); q += a16((size_t)(kb + rps) * ldp * sizeof(cx<T>));
+  // per row: v of the reflector being applied and x of the next pivot column, side by side
+  // so that phase 2 reads both with one broadcast load
+  VXp<T>* VX = reinterpret_cast<VXp<T>*>(q); q += a16((size_t)(kb + rps) * sizeof(VXp<T>));
+  const PanelShared<T> sh = carve_panel_shared<T>(q, NW);
+  cx<T>* wps = sh.wps; T* wpn = sh.wpn;
+  cx<T>* scl = sh.scl; cx<T>* bet = sh.bet; cx<T>* bc = sh.bc;
+
+  const long long k0 = a.k0;
+  // load: lane = column, this warp's rows, all copies in flight (cp.async, no registers)
+  if (lane < kb) {
+    for (int p = p0; p < p1; ++p) {
+      const cx<T>* src = a.A + (k0 + grow(p)) * a.lda + k0 + lane;
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(smem_addr(P + p * ldp + lane)),
+                   "l"(src), "n"((int)sizeof(cx<T>)) : "memory");
+    }
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+  bool ok = true;
+
+  const cx<T> zero = mk<T>(0, 0);
+  cx<T> scale = zero, cw = zero, cwn = zero;
+
+  for (int jn = 0; jn < kb; ++jn) {
+    const int jp = jn - 1;
+    // local index = panel row for the top block, and g(p) is increasing in p
+    const int plo = max(p0, min(p1, max(jp, 0)));
+    // ---- 1. lane = row
+    NAcc<T> nacc;
+    for (int p = plo + lane; p < p1; p += 64) {
+      const bool two = p + 32 < p1;
+      cx<T> r0 = P[p * ldp + jn], r1 = zero, u0 = zero, u1 = zero;
+      if (jp >= 0) u0 = P[p * ldp + jp];
+      if (two) { r1 = P[(p + 32) * ldp + jn]; if (jp >= 0) u1 = P[(p + 32) * ldp + jp]; }
+      cx<T> v0 = zero, v1 = zero;
+      if (jp >= 0) { v0 = (p == jp) ? mk<T>(1, 0) : cmul<T>(scale, u0); v1 = cmul<T>(scale, u1); }
+      r0 = csub<T>(r0, cmul<T>(v0, cwn));
+      r1 = csub<T>(r1, cmul<T>(v1, cwn));
+      P[p * ldp + jn] = r0; VX[p] = VXp<T>{v0, r0};
+      if (p > jn && (top_counts || p >= kb)) { nacc.add_sq(r0.x); nacc.add_sq(r0.y); }
+      if (two) {
+        P[(p + 32) * ldp + jn] = r1; VX[p + 32] = VXp<T>{v1, r1};
+        if (p + 32 > jn && (top_counts || p + 32 >= kb)) { nacc.add_sq(r1.x); nacc.add_sq(r1.y); }
+      }
+    }
+    __syncwarp();
+    // ---- 2. lane = column
+    const int col = (lane < kb) ? lane : jn;
+    const bool upd = lane > jn && lane < kb;
+    const int slo = max(plo, min(p1, jn + 1));
+    const int alo = top_counts ? slo : max(slo, min(p1, kb));
+    {
+      // rows that take the update only (the replicated pivot rows outside rank 0's sums):
+      // four rows' loads ahead of their stores
+      int p = plo;
+      for (; p + 3 < alo; p += 4) {
+        cx<T> y[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) y[u] = csub<T>(P[(p + u) * ldp + col], cmul<T>(VX[p + u].v, cw));
+        if (upd) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) P[(p + u) * ldp + col] = y[u];
+        }
+      }
+      for (; p < alo; ++p) {
+        const cx<T> y = csub<T>(P[p * ldp + col], cmul<T>(VX[p].v, cw));
+        if (upd) P[p * ldp + col] = y;
+      }
+    }
+    cx<T> acc0 = zero, acc1 = zero;
+    int p = alo;
+    for (; p + 3 < p1; p += 4) {
+      cx<T> v[4], x[4], y[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const VXp<T> t = VX[p + u];
+        v[u] = t.v; x[u] = t.x; y[u] = P[(p + u) * ldp + col];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) y[u] = csub<T>(y[u], cmul<T>(v[u], cw));
+      if (upd) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) P[(p + u) * ldp + col] = y[u];
+      }
+      cfma<T>(acc0, cconj<T>(x[0]), y[0]);
+      cfma<T>(acc1, cconj<T>(x[1]), y[1]);
+      cfma<T>(acc0, cconj<T>(x[2]), y[2]);
+      cfma<T>(acc1, cconj<T>(x[3]), y[3]);
+    }
+    for (; p < p1; ++p) {
+      const VXp<T> t = VX[p];
+      const cx<T> v0 = t.v, x0 = t.x;
+      const cx<T> y0 = csub<T>(P[p * ldp + col], cmul<T>(v0, cw));
+      if (upd) P[p * ldp + col] = y0;
+      cfma<T>(acc0, cconj<T>(x0), y0);
+    }
+    nacc.shfl_sum();
+    wps[warp * SLOTS + lane] = cadd<T>(acc0, acc1);
+    if (lane == 0) {
+      if constexpr (std::is_same<T, float>::value) { wpn[warp * 4 + 0] = nacc.hi; wpn[warp * 4 + 1] = nacc.lo; }
+      else { wpn[warp * 2 + 0] = nacc.value(); wpn[warp * 2 + 1] = 0; }
+    }
+    __syncthreads();
+    panel_exchange_g<T, NW>(sh, P + jn * ldp, jn, kb, rank, CS, part, bar, a.err, ok);
+    if (!ok) break;  // a grid barrier ran out: every CTA's next wait will too
+    const int buf = jn & 1;
+    {
+      const cx<T>* bb = bc + buf * (SLOTS + 2);
+      scale = bb[SLOTS];
+      cw = bb[lane];
+      cwn = (jn + 1 < kb) ? bb[jn + 1] : zero;
+    }
+  }
+  if (!ok && tid == 0) atomicOr(a.err, DEVERR_TIMEOUT);
+  __syncthreads();
+
+  if (rank == CS - 1) panel_t_factor<T, NW>(sh, kb, a);
+  // ---- V (v = scale * raw column below the pivot, unit diagonal) and R / zeros into A;
+  //      lane = column, the top block from rank 0 only
+  if (lane < kb) {
+    const cx<T> sc = scl[lane], bc = bet[lane];
+    const int pstart = (rank == 0) ? p0 : max(p0, kb);
+    auto put = [&](int p, cx<T> pv) {
+      const int g = grow(p);
+      a.V[(k0 + g) * a.ldv + k0 + lane] = (g == lane) ? mk<T>(1, 0) : (g > lane ? cmul<T>(sc, pv) : zero);
+      a.A[(k0 + g) * a.lda + k0 + lane] = (lane > g) ? pv : (lane == g ? bc : zero);
+    };
+    int p = pstart;
+    for (; p + 3 < p1; p += 4) {  // four rows' loads ahead of their stores
+      cx<T> pv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) pv[u] = P[(p + u) * ldp + lane];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) put(p + u, pv[u]);
+    }
+    for (; p < p1; ++p) put(p, P[p * ldp + lane]);
+  }
+}
+
 
 // Register-file form of the panel (complex64), used when each warp's share of the slab
 // fits in RF_RPW rows of registers, lane = column; the replicated top kb rows stay in
@@ -1335,6 +1577,7 @@ int apply_wy(cx<T>* C, long long ldc, const cx<T>* V, long long ldv, const cx<T>
 
 struct ClusterChoice { int cs; int rps; int kb; };
 
+
 // Largest cluster the device co-schedules for the panel kernel (16 needs the
 // non-portable opt-in; probed once per process, falls back to 8), and the opt-in
 // dynamic shared memory per block.
@@ -1373,6 +1616,49 @@ template <typename T> ClusterChoice choose_cluster(int mr, int kb_want) {
     }
   }
   return ClusterChoice{-1, 0, kb_want};
+}
+
+// Complex128 panels whose 16-CTA cluster would hold more than ~24 slab rows a CTA run in the
+// grid form on G <= 148 CTAs of ~40 slab rows (a 5120-row panel: 128 CTAs of 40 rows,
+// against 16 of 320 in the cluster form).
+constexpr int PG_ROWS = 40;
+template <typename T> bool pg_shape(int mr, int kb, int* G, int* rps) {
+  if (!std::is_same<T, double>::value) return false;
+  const int S = mr - kb;
+  if (S <= 16 * 24) return false;
+  const int g = (int)std::min<long long>(std::min(PG_MAX, std::max(num_sms(), 1)), ceil_div(S, PG_ROWS));
+  *G = g;
+  *rps = (int)ceil_div(S, g);
+  return true;
+}
+template <typename T> size_t g_pg_attr = 0;  // dynamic shared memory the attribute allows
+
+template <typename T> int launch_panel_g(const PanelArgs<T>& pa, int G, const QrScratch<T>& s, cudaStream_t st) {
+  const size_t smem = panel_smem_bytes<T>(pa.rps, pa.kb);
+  const int mr = pa.m - pa.k0;
+  // the grid barrier's flag takes a little static shared memory: keep 1 KB of the opt-in size
+  if (pa.kb < 1 || pa.kb > KBMAX || mr < pa.kb || G < 1 || G > PG_MAX || (long long)pa.rps * G < mr - pa.kb ||
+      smem > (size_t)smem_cap() - 1024 || !s.pg) {
+    set_last_message("QR grid panel: invalid shape");
+    return QRTEBD_ERR_INVALID_ARG;
+  }
+  if (g_pg_attr<T> < smem) {
+    QR_CUDA_TRY(cudaFuncSetAttribute(k_qr_panel_g<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    g_pg_attr<T> = smem;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)G, 1, 1);
+  cfg.blockDim = dim3(PT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeCooperative;
+  at[0].val.cooperative = 1;
+  cfg.attrs = at; cfg.numAttrs = 1;
+  ProfScope prof(PROF_QR_PANEL, st, 8.0 * mr * pa.kb * pa.kb, 3.0 * mr * pa.kb * sizeof(cx<T>));
+  QR_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_qr_panel_g<T>, pa, s.pg, s.bar + 16));
+  note_launch();
+  return QRTEBD_OK;
 }
 
 template <typename T> bool g_attr_done = false;
@@ -1487,6 +1773,10 @@ int qr_panel_width(int m, int n, int elem_bytes) {
   int kb = n < KBMAX ? n : KBMAX;
   if (kb < 1) kb = 1;
   if (elem_bytes == 16) {
+    // a complex128 panel in the grid form holds ~40 slab rows a CTA: the full width fits
+    int G = 0, rps = 0;
+    if (pg_shape<double>(m, kb, &G, &rps) && panel_smem_bytes<double>(rps, kb) <= (size_t)smem_cap() - 1024)
+      return kb;
     ClusterChoice c = choose_cluster<double>(m, kb);
     return c.cs < 0 ? -1 : c.kb;
   }
@@ -1513,6 +1803,7 @@ template <typename T> void qr_carve(Arena& ar, int m, int n, QrScratch<T>& s) {
   s.G = ar.take<cx<T>>((size_t)nbo * nbo);
   s.wy_part = ar.take<cx<T>>((size_t)std::max(num_sms(), 1) * WY_KB * WY_NC);
   s.wy_W = ar.take<cx<T>>((size_t)WY_KB * WY_NC);
+  if (std::is_same<T, double>::value) s.pg = ar.take<cx<T>>((size_t)2 * PG_MAX * (SLOTS + 1));
   s.bar = ar.take<unsigned>(64);
   size_t e = 0;
   for (int k = 1; k <= nbo; k *= 2) {
@@ -1547,7 +1838,7 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
   // V must be zero above each panel's diagonal block: an outer block reads the rows
   // above its later inner panels, which those panels do not write
   QR_CUDA_TRY(cudaMemsetAsync(s.V, 0, (size_t)m * n * sizeof(cx<T>), st));
-  QR_CUDA_TRY(cudaMemsetAsync(s.bar, 0, 2 * sizeof(unsigned), st));
+  QR_CUDA_TRY(cudaMemsetAsync(s.bar, 0, 32 * sizeof(unsigned), st));  // [0..1] narrow update, [16..17] grid panel
   // complex64 with look-ahead: the compact-WY factor of the whole QR is assembled on the side
   // stream block by block, and the explicit Q then takes two GEMMs,
   // Q = [I; 0] - V (T_all V_top^dag), instead of one backward step per outer block
@@ -1572,7 +1863,18 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
       if (cc.cs < 0 || cc.kb != kb) { cc.kb = kb; cc.cs = 16; cc.rps = (int)ceil_div(mr - kb, 16); }
       cx<T>* Ti = Tb + (size_t)(ki - ko) * nbo + (ki - ko);
       PanelArgs<T> pa{A, lda, m, ki, kb, s.V, ldv, s.tau, Ti, nbo, cc.rps, err};
-      QR_TRY(launch_panel<T>(pa, cc.cs, st));
+      int pgG = 0, pgR = 0;
+      bool grid_form = false;
+      if constexpr (std::is_same<T, double>::value) grid_form = pg_shape<T>(mr, kb, &pgG, &pgR) && s.pg;
+      if (grid_form) {
+        if constexpr (std::is_same<T, double>::value) {
+          PanelArgs<T> p2 = pa;
+          p2.rps = pgR;
+          QR_TRY(launch_panel_g<T>(p2, pgG, s, st));
+        }
+      } else {
+        QR_TRY(launch_panel<T>(pa, cc.cs, st));
+      }
       // inner update: the rest of this outer block
       const int nc = ko + kbo - ki - kb;
       const int rpb = nc > 0 ? wy_rows_per_block<T>(mr, kb, nc) : 0;

@@ -29,6 +29,7 @@ template <typename T> struct QrScratch {
   cx<T>* Wq = nullptr;     // n x n: T_all V_top^dag for the explicit Q
   cx<T>* wy_part = nullptr;  // fused narrow update: per-CTA partials of V^dag C
   cx<T>* wy_W = nullptr;     // and their sum
+  cx<T>* pg = nullptr;       // complex128 grid panel: per-CTA partial sums, [2][148][33]
   unsigned* bar = nullptr;   // grid-barrier counter and generation
   cx<T>* gemm_scratch = nullptr;
   size_t gemm_scratch_elems = 0;
