@@ -612,19 +612,26 @@ __device__ __forceinline__ void panel_exchange_g(const PanelShared<T>& sh, const
       v[i] = g < G ? __ldcg(all + (long long)g * PS + lane) : zero;
       nv[i] = (g < G && lane == 0) ? __ldcg(all + (long long)g * PS + SLOTS).x : T(0);
     }
-    cx<T> sw = zero;
-    T nw = T(0);
+    // pairwise, so that the FP64 adds form a tree of depth log2(PW) rather than a chain
 #pragma unroll
-    for (int i = 0; i < PW; ++i) { sw = cadd<T>(sw, v[i]); nw += nv[i]; }
-    sh.wps[warp * SLOTS + lane] = sw;  // the CTA's own partials were read before the barrier
-    if (lane == 0) sh.wpn[warp * 2] = nw;
+    for (int h = 1; h < PW; h *= 2)
+#pragma unroll
+      for (int i = 0; i + h < PW; i += 2 * h) { v[i] = cadd<T>(v[i], v[i + h]); nv[i] += nv[i + h]; }
+    sh.wps[warp * SLOTS + lane] = v[0];  // the CTA's own partials were read before the barrier
+    if (lane == 0) sh.wpn[warp * 2] = nv[0];
   }
   __syncthreads();
   if (warp == 0 && ok) {
-    cx<T> S = zero;
-    T ns = T(0);
+    cx<T> vw[NW];
+    T nw[NW];
 #pragma unroll
-    for (int w = 0; w < NW; ++w) { S = cadd<T>(S, sh.wps[w * SLOTS + lane]); ns += sh.wpn[w * 2]; }
+    for (int w = 0; w < NW; ++w) { vw[w] = sh.wps[w * SLOTS + lane]; nw[w] = sh.wpn[w * 2]; }
+#pragma unroll
+    for (int h = 1; h < NW; h *= 2)
+#pragma unroll
+      for (int w = 0; w + h < NW; w += 2 * h) { vw[w] = cadd<T>(vw[w], vw[w + h]); nw[w] += nw[w + h]; }
+    const cx<T> S = vw[0];
+    const T ns = nw[0];
     const cx<T>* piv = sh.pivb + buf * SLOTS;
     const cx<T> pc = piv[min(lane, kb - 1)];
     const cx<T> alpha = piv[jn];
