@@ -89,11 +89,14 @@ def family_roofline(L, fam, ms, n, flops, nbytes, prec, peaks, src):
         out.update({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak, "peak_source": "derived CUDA-core peak (SMs x lanes x clock)",
                     "algorithmic_flops_per_launch": flops / n,
-                    "kernel": {L.PROF_QR_PANEL: "k_qr_panel" if L.is_c128(prec) else "k_qr_panel_rf",
+                    "kernel": {L.PROF_QR_PANEL: "k_qr_panel_g (grid form; k_qr_panel clusters for short panels)"
+                               if L.is_c128(prec) else "k_qr_panel_rf",
                                L.PROF_SIMT_GEMM: "k_apply_wy / k_gemm",
                                L.PROF_BOND_GEMM: "k_gemm", L.PROF_TC_GEMM: "k_gemm"}[fam]})
         if fam == L.PROF_QR_PANEL:
-            out["limiter"] = "latency: one cluster-wide exchange per column (sequential in the column)"
+            out["limiter"] = ("FP64 work per CTA (~40 slab rows and the 32 pivot rows) and one grid barrier per column"
+                              if L.is_c128(prec) else
+                              "latency: one cluster-wide exchange per column (sequential in the column)")
             out["achieved_hbm_gbs"] = nbytes / n / sec / 1e9
             out["algorithmic_bytes_per_launch"] = nbytes / n
             if prec == L.C64_3XTF32:
