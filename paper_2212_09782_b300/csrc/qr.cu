@@ -1525,17 +1525,26 @@ int num_sms() {
   return g_nsm;
 }
 
+thread_local int g_concurrency = 1;  // see QrConcurrency
+
 template <typename T> size_t wy_smem(int rpb, int kb, int nc) {
   return ((size_t)rpb * kb + (size_t)rpb * nc + (size_t)kb * nc + (size_t)kb * kb) * sizeof(cx<T>);
 }
 
 // Rows per CTA of the fused update: one CTA per SM at most (co-residency of a
-// cooperative launch), at least 8 rows per CTA.
+// cooperative launch), at least 8 rows per CTA; beside other bond updates at most
+// num_sms / min(n, 4) CTAs (QrConcurrency).
 template <typename T> int wy_rows_per_block(int mr, int kb, int nc) {
   if (kb < 1 || kb > WY_KB || nc < 1 || nc > WY_NC || mr < 1) return 0;
-  const int rpb = std::max(8, (int)ceil_div(mr, std::min(num_sms(), (WY_NT / 32) * WY_PW)));
-  if (wy_smem<T>(rpb, kb, nc) > (size_t)48 * 1024 * 4) return 0;
-  return rpb;
+  const size_t smax = (size_t)48 * 1024 * 4;
+  const int sms = num_sms();
+  const int full = std::max(8, (int)ceil_div(mr, std::min(sms, (WY_NT / 32) * WY_PW)));
+  if (g_concurrency > 1) {
+    const int cap = std::max(1, sms / std::min(g_concurrency, 4));
+    const int rpb = std::max(8, (int)ceil_div(mr, std::min(cap, (WY_NT / 32) * WY_PW)));
+    if (wy_smem<T>(rpb, kb, nc) <= smax) return rpb;
+  }
+  return wy_smem<T>(full, kb, nc) <= smax ? full : 0;
 }
 
 template <typename T> bool g_wy_attr = false;
@@ -1775,6 +1784,9 @@ int run_gemm(const GemmArgs<T>& g, const QrScratch<T>& s, cudaStream_t st, const
 }
 
 }  // namespace
+
+QrConcurrency::QrConcurrency(int n) : prev_(g_concurrency) { g_concurrency = std::max(1, n); }
+QrConcurrency::~QrConcurrency() { g_concurrency = prev_; }
 
 int qr_panel_width(int m, int n, int elem_bytes) {
   int kb = n < KBMAX ? n : KBMAX;
