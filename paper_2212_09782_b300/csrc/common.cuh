@@ -57,6 +57,24 @@ template <typename T> __host__ __device__ __forceinline__ T cabs2(cx<T> a) {
 // and return; the host maps it to QRTEBD_ERR_TIMEOUT at the next sync point.
 enum : unsigned { DEVERR_TIMEOUT = 1u, DEVERR_NUMERIC = 2u, DEVERR_BOUNDS = 4u };
 
+// How many bond updates the enqueuing host thread runs at the same time (1: one alone),
+// for the lifetime of a ConcurrencyScope (set by the layer executor and by the
+// charge-sector update around their enqueues; defined in qr.cu). Launch shapes chosen to
+// fill an otherwise idle GPU take a share of it instead: the QR's cooperative narrow
+// updates (whose CTAs hold their SMs at the grid barriers until the grid's last CTA runs)
+// and the tensor-core GEMM's K-splits (each split adds a partial-sum pass).
+class ConcurrencyScope {
+ public:
+  explicit ConcurrencyScope(int n);
+  ~ConcurrencyScope();
+  ConcurrencyScope(const ConcurrencyScope&) = delete;
+  ConcurrencyScope& operator=(const ConcurrencyScope&) = delete;
+
+ private:
+  int prev_;
+};
+int concurrency();
+
 // Iteration limit for every spin on an mbarrier or a flag (~1 s on B300).
 constexpr long long kSpinLimit = 1ll << 24;
 

@@ -98,7 +98,7 @@ struct Task { qrtebd_mps* s; int m; int worker; };
 
 // Enqueue every update of the layer on the workers (fork from `origin`, join back).
 int enqueue_layer(Executor& ex, std::vector<Task>& tasks, const qrtebd_trunc* tr) {
-  QrConcurrency conc((int)std::min<size_t>(tasks.size(), kWorkers));
+  ConcurrencyScope conc((int)std::min<size_t>(tasks.size(), kWorkers));
   QR_CUDA_TRY(cudaEventRecord(ex.fork, ex.origin));
   for (auto& w : ex.w) QR_CUDA_TRY(cudaStreamWaitEvent(w.st, ex.fork, 0));
   for (auto& t : tasks) {

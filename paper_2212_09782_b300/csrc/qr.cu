@@ -1525,7 +1525,7 @@ int num_sms() {
   return g_nsm;
 }
 
-thread_local int g_concurrency = 1;  // see QrConcurrency
+thread_local int g_concurrency = 1;  // see ConcurrencyScope
 
 template <typename T> size_t wy_smem(int rpb, int kb, int nc) {
   return ((size_t)rpb * kb + (size_t)rpb * nc + (size_t)kb * nc + (size_t)kb * kb) * sizeof(cx<T>);
@@ -1533,7 +1533,7 @@ template <typename T> size_t wy_smem(int rpb, int kb, int nc) {
 
 // Rows per CTA of the fused update: one CTA per SM at most (co-residency of a
 // cooperative launch), at least 8 rows per CTA; beside other bond updates at most
-// num_sms / min(n, 4) CTAs (QrConcurrency).
+// num_sms / min(n, 4) CTAs (ConcurrencyScope).
 template <typename T> int wy_rows_per_block(int mr, int kb, int nc) {
   if (kb < 1 || kb > WY_KB || nc < 1 || nc > WY_NC || mr < 1) return 0;
   const size_t smax = (size_t)48 * 1024 * 4;
@@ -1785,8 +1785,9 @@ int run_gemm(const GemmArgs<T>& g, const QrScratch<T>& s, cudaStream_t st, const
 
 }  // namespace
 
-QrConcurrency::QrConcurrency(int n) : prev_(g_concurrency) { g_concurrency = std::max(1, n); }
-QrConcurrency::~QrConcurrency() { g_concurrency = prev_; }
+ConcurrencyScope::ConcurrencyScope(int n) : prev_(g_concurrency) { g_concurrency = std::max(1, n); }
+ConcurrencyScope::~ConcurrencyScope() { g_concurrency = prev_; }
+int concurrency() { return g_concurrency; }
 
 int qr_panel_width(int m, int n, int elem_bytes) {
   int kb = n < KBMAX ? n : KBMAX;

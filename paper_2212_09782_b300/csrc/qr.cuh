@@ -35,22 +35,6 @@ template <typename T> struct QrScratch {
   size_t gemm_scratch_elems = 0;
 };
 
-// How many bond updates the enqueuing host thread runs at the same time (1: one alone),
-// for the lifetime of the object. With n > 1 the QR's cooperative narrow updates take
-// num_sms / min(n, 4) CTAs, with more rows each: a CTA of such an update holds its SM at
-// the grid barriers until the grid's last CTA runs, and with concurrent updates that CTA
-// waits for other bonds' kernels to leave the SMs.
-class QrConcurrency {
- public:
-  explicit QrConcurrency(int n);
-  ~QrConcurrency();
-  QrConcurrency(const QrConcurrency&) = delete;
-  QrConcurrency& operator=(const QrConcurrency&) = delete;
-
- private:
-  int prev_;
-};
-
 // Panel width used for an m x n factorisation.
 int qr_panel_width(int m, int n, int elem_bytes);
 

@@ -489,7 +489,7 @@ int sym_update_t(const qrtebd_sym_bond_io* io, const qrtebd_trunc* tr, cudaStrea
   int rc = QRTEBD_OK;
   int nblk = 0;
   for (int q = 0; q < d; ++q) nblk += m.eta[q] > 0;
-  QrConcurrency conc(nblk);
+  ConcurrencyScope conc(nblk);
   for (int q = 0; q < d; ++q) {
     if (m.eta[q] == 0) continue;
     QR_CUDA_TRY(cudaStreamWaitEvent(bs->st[q], bs->fork, 0));

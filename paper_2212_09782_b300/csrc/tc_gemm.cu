@@ -1519,7 +1519,10 @@ int tc_gemm_cfg(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStrea
   Epi epi{g.C, g.scm, g.scn, g.alpha, g.beta, M, N};
   const int nx = (int)ceil_div(2LL * N, bn), ny = (int)ceil_div(M, BM);
   const int nk = (int)ceil_div(2LL * K, BK);
-  const int nsm = 148;
+  // beside n - 1 other bond updates a product sizes its K-splits for its share of the SMs,
+  // and runs no tail split (other updates' kernels fill the SMs a short last wave leaves)
+  const int conc = force ? 1 : concurrency();
+  const int nsm = conc > 1 ? std::max(1, 148 / conc) : 148;
   unsigned* err = device_error_word();
   // one launch over tile rows [ty0, ty0 + nty) with `splits` K-splits (then their sum)
   auto run = [&](int ty0, int nty, int splits) -> int {
@@ -1561,13 +1564,14 @@ int tc_gemm_cfg(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStrea
     return splits;
   };
   const int tiles = nx * ny;
-  if (have && cfg.splits > 1) return run(0, ny, fit_splits(cfg.splits, M));
+  if (have && cfg.splits > 1)
+    return run(0, ny, fit_splits(conc > 1 ? std::min(cfg.splits, (int)ceil_div(nsm, tiles)) : cfg.splits, M));
   if (!(have && cfg.splits == 1) && tiles < 100 && nk >= 2 * CHUNK) {
     // split K when the tile grid leaves most SMs idle
     int splits = std::min<int>((int)ceil_div(nsm, tiles), nk / CHUNK);
     return run(0, ny, fit_splits(splits, M));
   }
-  if ((!have || cfg.tail) && tiles > nsm && nk >= 4 * CHUNK) {
+  if (conc == 1 && (!have || cfg.tail) && tiles > nsm && nk >= 4 * CHUNK) {
     // a last wave of a few tiles would leave most SMs idle for a whole tile's time: run the
     // full waves, then the remaining tile rows with their K split over the idle SMs
     const int tail_rows = (int)ceil_div(tiles % nsm, nx);
