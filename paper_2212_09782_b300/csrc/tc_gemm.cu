@@ -1468,7 +1468,10 @@ int tc_gemm_cfg(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStrea
     std::lock_guard<std::mutex> lk(g_tune_mu);
     if (g_recording) g_recorded.push_back(key);
     if (force) { cfg = *force; have = true; }
-    else {
+    else if (concurrency() == 1) {
+      // the table holds each shape's best configuration when the product runs alone;
+      // beside other bond updates the heuristic one (256-column tiles, K-splits for the
+      // product's share of the SMs) measured faster
       auto it = g_tune.find(key);
       if (it != g_tune.end()) { cfg = it->second.cfg; have = true; }
     }
@@ -1564,8 +1567,7 @@ int tc_gemm_cfg(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStrea
     return splits;
   };
   const int tiles = nx * ny;
-  if (have && cfg.splits > 1)
-    return run(0, ny, fit_splits(conc > 1 ? std::min(cfg.splits, (int)ceil_div(nsm, tiles)) : cfg.splits, M));
+  if (have && cfg.splits > 1) return run(0, ny, fit_splits(cfg.splits, M));
   if (!(have && cfg.splits == 1) && tiles < 100 && nk >= 2 * CHUNK) {
     // split K when the tile grid leaves most SMs idle
     int splits = std::min<int>((int)ceil_div(nsm, tiles), nk / CHUNK);
