@@ -499,14 +499,72 @@ struct PrepJob {
   const float2* src; long long s0, s1; int conj, rows, K;
   float* hi; float* lo; int ld;
   int gx, gy;  // tiles along K and along rows
+  int vec;     // 1: the operand is contiguous along K with 16-byte aligned pairs (vector form)
 };
+
+// Vector form for an operand contiguous along K (A: s1 = 1, rows m at stride s0; B: s0 = 1,
+// columns n at stride s1): no transpose, so each thread converts two complex values at a
+// time with one 16-byte load and 16-byte stores (the tile form stages a 32 x 32 tile in
+// shared memory for every layout). The values written are the tile form's, bit for bit.
+// Units (row, pair of K) are spread over every block of the operand's grid slice.
+__device__ __forceinline__ void prep_vec(const PrepJob& j, bool embed, int three) {
+  const unsigned kp = (unsigned)(j.K + 1) >> 1;
+  const unsigned units = (unsigned)j.rows * kp;  // < 2^31 (host-checked)
+  const unsigned nthr = gridDim.x * gridDim.y * blockDim.x * blockDim.y;
+  const long long rs = embed ? j.s1 : j.s0;
+  for (unsigned u = (blockIdx.y * gridDim.x + blockIdx.x) * (blockDim.x * blockDim.y) +
+                    threadIdx.y * blockDim.x + threadIdx.x;
+       u < units; u += nthr) {
+    const unsigned r = u / kp;
+    const int k = 2 * (int)(u - r * kp);
+    const float2* p = j.src + (long long)r * rs + k;
+    const bool two = k + 1 < j.K;
+    float4 v;
+    if (two) v = *reinterpret_cast<const float4*>(p);
+    else { const float2 x = *p; v = make_float4(x.x, x.y, 0.f, 0.f); }
+    if (j.conj) { v.y = -v.y; v.w = -v.w; }
+    const float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
+    const float4 l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+    if (!embed) {
+      const long long o = (long long)r * j.ld + 2 * k;
+      if (two) {
+        *reinterpret_cast<float4*>(j.hi + o) = h;
+        if (three) *reinterpret_cast<float4*>(j.lo + o) = l;
+      } else {
+        *reinterpret_cast<float2*>(j.hi + o) = make_float2(h.x, h.y);
+        if (three) *reinterpret_cast<float2*>(j.lo + o) = make_float2(l.x, l.y);
+      }
+    } else {
+      // B'^T rows 2n: (Re b, -Im b), 2n+1: (Im b, Re b)
+      const long long o0 = (long long)(2 * r) * j.ld + 2 * k, o1 = o0 + j.ld;
+      if (two) {
+        *reinterpret_cast<float4*>(j.hi + o0) = make_float4(h.x, -h.y, h.z, -h.w);
+        *reinterpret_cast<float4*>(j.hi + o1) = make_float4(h.y, h.x, h.w, h.z);
+        if (three) {
+          *reinterpret_cast<float4*>(j.lo + o0) = make_float4(l.x, -l.y, l.z, -l.w);
+          *reinterpret_cast<float4*>(j.lo + o1) = make_float4(l.y, l.x, l.w, l.z);
+        }
+      } else {
+        *reinterpret_cast<float2*>(j.hi + o0) = make_float2(h.x, -h.y);
+        *reinterpret_cast<float2*>(j.hi + o1) = make_float2(h.y, h.x);
+        if (three) {
+          *reinterpret_cast<float2*>(j.lo + o0) = make_float2(l.x, -l.y);
+          *reinterpret_cast<float2*>(j.lo + o1) = make_float2(l.y, l.x);
+        }
+      }
+    }
+  }
+}
+
 // One launch prepares both operands: blockIdx.z = 0 the A' tiles, 1 the B' tiles
-// (tiles beyond an operand's own grid return at once).
+// (tiles beyond an operand's own grid return at once); an operand in the vector form
+// spreads its units over the whole of its grid slice.
 __global__ void k_prep(PrepJob a, PrepJob b, int three) {
   __shared__ float2 t[32][33];
   pdl_launch_dependents();
   pdl_wait();
   const PrepJob& j = blockIdx.z == 0 ? a : b;
+  if (j.vec) { prep_vec(j, blockIdx.z == 1, three); return; }
   if ((int)blockIdx.x >= j.gx || (int)blockIdx.y >= j.gy) return;
   if (blockIdx.z == 0)
     prep_a_tile(j.src, j.s0, j.s1, j.conj, j.rows, j.K, j.hi, j.lo, j.ld, three, blockIdx.x, blockIdx.y, t);
@@ -1391,6 +1449,12 @@ std::atomic<int> g_prep_mode{1};
 // The in-kernel preparation reads pairs of complex values with 16-byte loads: an operand
 // qualifies when it is contiguous along K or along its other index, the other stride is
 // even and the base is 16-byte aligned.
+// The vector form of the separate preparation: contiguous along K, the other stride even
+// and the base 16-byte aligned, so that every pair of K is one aligned 16-byte load.
+bool vec_layout(const float2* p, long long s_rows, long long s_k) {
+  return s_k == 1 && s_rows % 2 == 0 && (reinterpret_cast<uintptr_t>(p) & 15) == 0;
+}
+
 bool raw_layout(const float2* p, long long s_rows, long long s_k, bool is_b, int* kmajor) {
   // A: (m, k) at p[m s_rows + k s_k]; B: (k, n) at p[k s_k + n s_rows]
   if ((reinterpret_cast<uintptr_t>(p) & 15) != 0) return false;
@@ -1495,10 +1559,25 @@ int tc_gemm_cfg(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStrea
   if (sa == nullptr) sa = &w.a[cacheable ? 0 : 1];
   if (!fused) {
     PrepJob ja{g.A, g.sam, g.sak, g.conj_a ? 1 : 0, M, K, sa->hi, sa->lo, ld,
-               need_a ? (int)ceil_div(K, 32) : 0, need_a ? (int)ceil_div(M, 32) : 0};
+               need_a ? (int)ceil_div(K, 32) : 0, need_a ? (int)ceil_div(M, 32) : 0, 0};
     PrepJob jb{g.B, g.sbk, g.sbn, g.conj_b ? 1 : 0, N, K, w.b.hi, w.b.lo, ld,
-               (int)ceil_div(K, 32), (int)ceil_div(N, 32)};
-    dim3 grid((unsigned)std::max(ja.gx, jb.gx), (unsigned)std::max(ja.gy, jb.gy), 2);
+               (int)ceil_div(K, 32), (int)ceil_div(N, 32), 0};
+    // the vector form where the operand runs along K in 16-byte aligned pairs
+    const long long kp = (K + 1) / 2;
+    ja.vec = need_a && vec_layout(g.A, g.sam, g.sak) && (long long)M * kp < (1LL << 31);
+    jb.vec = vec_layout(g.B, g.sbn, g.sbk) && (long long)N * kp < (1LL << 31);
+    // grid: the tile form's tiles; a vector-form operand wants about two units per thread
+    // on at most 8 blocks per SM (its blocks grid-stride over the rest), laid over the
+    // tile form's rows of blocks when the other operand has some
+    unsigned gx = 1, gy = 1;
+    for (const PrepJob* j : {&ja, &jb})
+      if (!j->vec) { gx = std::max(gx, (unsigned)j->gx); gy = std::max(gy, (unsigned)j->gy); }
+    for (const PrepJob* j : {&ja, &jb})
+      if (j->vec) {
+        const long long blocks = std::min<long long>(ceil_div((long long)j->rows * kp, 512), 148 * 8);
+        gx = std::max(gx, (unsigned)ceil_div(blocks, (long long)gy));
+      }
+    dim3 grid(gx, gy, 2);
     ProfScope prof(PROF_PREP, st, 0,
                    (need_a ? 8.0 * M * K + (three ? 16.0 : 8.0) * M * K : 0.0) +
                        8.0 * N * K + (three ? 32.0 : 16.0) * N * K);
