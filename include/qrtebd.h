@@ -112,7 +112,11 @@ typedef struct qrtebd_bond_io {
   int precision;             /* QRTEBD_C128 / C64_3XTF32 / C64_TF32 / C64_FP32 */
   int chi_l, d, chi_m, chi_r;
   int xi_kind;               /* 0: Xi = identity (xi unused); 1: dense chi_l x chi_l;
-                                2: diagonal, xi holds chi_l complex entries */
+                                2: diagonal, xi holds chi_l complex entries;
+                                3: dense chi_l x chi_l and lower triangular, its zeros stored
+                                (the Xi~ = L / ||L|| a plain update writes): the product
+                                Xi theta~' skips whole blocks above the diagonal, so entries
+                                there must be zero */
   const void* xi;            /* Xi^[m] on the bond left of site m */
   const void* bm;            /* B^[m] (chi_l, d, chi_m); unused when theta != NULL */
   const void* bn;            /* B^[n] (chi_m, d, chi_r); right isometry */
@@ -202,7 +206,7 @@ typedef struct qrtebd_sym_bond_io {
 
 /* Workspace bytes and eta_sum = sum_q eta_q for these charges (host call, no GPU work).
  * Errors: INVALID_ARG for d outside 2..16, a charge outside 0..d-1, a scheme other than
- * CBE, tr->eta != 0 or xi_kind 1. */
+ * CBE, tr->eta != 0 or xi_kind 1 or 3. */
 int qrtebd_sym_bond_workspace_size(int precision, int chi_l, int d, int chi_m, int chi_r,
                                    const int* charge_l, const int* charge_m, const int* charge_r,
                                    int xi_kind, int theta_given, const qrtebd_trunc* tr,

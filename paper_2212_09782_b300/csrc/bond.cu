@@ -471,9 +471,10 @@ int bond_update_t(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t
       QR_CUDA_TRY(cudaGetLastError());
     }
   }
-  if (io->xi_kind == 1) {  // dense Xi: theta~ = Xi theta~' on the left bond index
+  if (io->xi_kind == 1 || io->xi_kind == 3) {  // dense Xi: theta~ = Xi theta~' on the left bond index
     GemmArgs<T> g{chiL, (int)(d * nR), chiL, xi, chiL, 1, false, theta_tp, d * nR, 1, false,
                   theta_t, d * nR, 1, one, zero};
+    g.tri_a = io->xi_kind == 3;  // lower triangular: blocks above the diagonal are skipped
     QR_TRY(runner.run(g, st, true));
   }
   QR_TRY(norm2<T>(theta_t, mL * nR, partial, scal + 0, st));
@@ -677,7 +678,7 @@ int bond_update(const qrtebd_bond_io* io, const qrtebd_trunc* tr, cudaStream_t s
   if (theta_gated && !bytes && !io->theta) return QRTEBD_ERR_INVALID_ARG;
   if (io->chi_l < 1 || io->d < (theta_gated ? 1 : 2) || io->chi_m < 1 || io->chi_r < 1 || tr->chi_max < 1)
     return QRTEBD_ERR_INVALID_ARG;
-  if (io->xi_kind < 0 || io->xi_kind > 2) return QRTEBD_ERR_INVALID_ARG;
+  if (io->xi_kind < 0 || io->xi_kind > 3) return QRTEBD_ERR_INVALID_ARG;
   if (tr->scheme != QRTEBD_PLAIN && tr->scheme != QRTEBD_CBE) return QRTEBD_ERR_INVALID_ARG;
   if (tr->sweeps < 0 || tr->sweeps > 1000) {
     set_last_message("bond_update: sweeps must lie in 0..1000");

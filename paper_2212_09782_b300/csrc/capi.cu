@@ -222,7 +222,7 @@ int qrtebd_bond_update(const qrtebd_bond_io* io, const qrtebd_trunc* tr, void* s
 
 int qrtebd_autotune_bond(int precision, int chi_l, int d, int chi_m, int chi_r, int xi_kind,
                          int theta_given, const qrtebd_trunc* tr, void* stream, int* n_shapes) {
-  if (!tr || chi_l < 1 || d < 1 || chi_m < 1 || chi_r < 1 || xi_kind < 0 || xi_kind > 2)
+  if (!tr || chi_l < 1 || d < 1 || chi_m < 1 || chi_r < 1 || xi_kind < 0 || xi_kind > 3)
     return QRTEBD_ERR_INVALID_ARG;
   if (n_shapes) *n_shapes = 0;
   if (precision != QRTEBD_C64_3XTF32 && precision != QRTEBD_C64_TF32) return QRTEBD_OK;
@@ -233,7 +233,7 @@ int qrtebd_autotune_bond(int precision, int chi_l, int d, int chi_m, int chi_r, 
   if (eta < 1) return QRTEBD_ERR_INVALID_ARG;
   const long long mL = (long long)chi_l * d, nR = (long long)d * chi_r;
   // synthetic operands of the bond's shape (values in [-1, 1]); one allocation
-  const long long n_in[4] = {xi_kind == 1 ? (long long)chi_l * chi_l : chi_l,
+  const long long n_in[4] = {(xi_kind == 1 || xi_kind == 3) ? (long long)chi_l * chi_l : chi_l,
                              theta_given ? 0 : mL * chi_m, (long long)chi_m * nR,
                              theta_given ? mL * nR : 0};
   const long long n_out[3] = {mL * eta, eta * eta, eta * nR};

@@ -22,6 +22,9 @@ template <typename T> struct GemmArgs {
   // tensor-core path only: A is unchanged since an earlier call with the same
   // pointer, strides and shape in this workspace, so its prepared operand may be reused
   bool reuse_a = false;
+  // tensor-core path only: A is lower triangular (A[m][k] = 0 for k > m, zeros stored), so
+  // a tile of rows may stop its K loop after its last row; other paths read the zeros
+  bool tri_a = false;
 };
 
 // Enqueue the GEMM. `scratch` (may be null) lets the launcher split K for

@@ -172,6 +172,7 @@ int qrtebd_apply_gate_layer_batched(qrtebd_mps* const* states, int nstates, int 
     key.push_back(reinterpret_cast<long long>(s));
     for (int b : s->chi) key.push_back(b);
     for (char c : s->xi_diag) key.push_back(c);
+    for (char c : s->xi_lower) key.push_back(c);
     for (int m = parity; m < mps_gate_count(s); m += 2) {
       size_t nb = 0;
       QR_TRY(mps_bond_ws_need(s, m, tr, &nb));
@@ -245,12 +246,14 @@ int qrtebd_apply_gate_layer_batched(qrtebd_mps* const* states, int nstates, int 
       const int br = s->infinite ? (t.m + 2) % s->L : t.m + 2;
       if (tr->scheme == QRTEBD_CBE) {
         s->chi_pending[bmid] = 1;
+        s->xi_lower[bmid] = 0;
         continue;
       }
       qrtebd_trunc tt = *tr;
       if (tt.chi_max > s->cap[bmid]) tt.chi_max = s->cap[bmid];
       s->chi[bmid] = choose_eta(&tt, s->chi[bl], s->d, s->chi[bmid], s->chi[br]);
       s->xi_diag[bmid] = 0;
+      s->xi_lower[bmid] = 1;
     }
   } else if (ge && ge->seen >= 2) {
     // second sighting of this shape: capture, then launch
@@ -258,10 +261,11 @@ int qrtebd_apply_gate_layer_batched(qrtebd_mps* const* states, int nstates, int 
     // the host bookkeeping of the enqueue (bond dimensions) is kept so that a capture that
     // fails can be undone and the layer run without a graph
     std::vector<std::vector<int>> chi_before(nstates);
-    std::vector<std::vector<char>> diag_before(nstates), pend_before(nstates);
+    std::vector<std::vector<char>> diag_before(nstates), lower_before(nstates), pend_before(nstates);
     for (int i = 0; i < nstates; ++i) {
       chi_before[i] = states[i]->chi;
       diag_before[i] = states[i]->xi_diag;
+      lower_before[i] = states[i]->xi_lower;
       pend_before[i] = states[i]->chi_pending;
     }
     QR_CUDA_TRY(cudaStreamBeginCapture(ex.origin, cudaStreamCaptureModeRelaxed));
@@ -283,6 +287,7 @@ int qrtebd_apply_gate_layer_batched(qrtebd_mps* const* states, int nstates, int 
       for (int i = 0; i < nstates; ++i) {
         states[i]->chi = chi_before[i];
         states[i]->xi_diag = diag_before[i];
+        states[i]->xi_lower = lower_before[i];
         states[i]->chi_pending = pend_before[i];
       }
       ge->seen = -(1 << 30);  // never capture this shape again
@@ -373,6 +378,7 @@ int qrtebd_mps_set_bond(qrtebd_mps* s, int bond, const double* xi_host, int chi,
   QR_CUDA_TRY(cudaStreamSynchronize(s->st));
   s->chi[bond] = chi;
   s->xi_diag[bond] = diagonal ? 1 : 0;
+  s->xi_lower[bond] = 0;
   return QRTEBD_OK;
 }
 

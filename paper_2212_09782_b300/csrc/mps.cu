@@ -123,6 +123,7 @@ int allocate(qrtebd_mps* s) {
   s->Xi.assign(s->nbonds_store, nullptr);
   s->xiv.assign(s->nbonds_store, nullptr);
   s->xi_diag.assign(s->nbonds_store, 1);
+  s->xi_lower.assign(s->nbonds_store, 0);
   s->chi_pending.assign(s->nbonds_store, 0);
   for (int m = 0; m < L; ++m) {
     int r = s->infinite ? (m + 1) % L : m + 1;
@@ -172,7 +173,7 @@ int update_bond_t(qrtebd_mps* s, int m, const qrtebd_trunc* tr, cudaStream_t st,
   io.precision = s->precision;
   io.chi_l = s->chi[bl]; io.d = d; io.chi_m = s->chi[bmid]; io.chi_r = s->chi[br];
   const bool diag = s->xi_diag[bl] != 0;
-  io.xi_kind = diag ? 2 : 1;
+  io.xi_kind = diag ? 2 : (s->xi_lower[bl] ? 3 : 1);
   io.xi = diag ? s->xiv[bl] : s->Xi[bl];
   io.bm = s->B[m]; io.bn = s->B[n];
   io.gate = s->gates + (size_t)m * d4;
@@ -186,6 +187,7 @@ int update_bond_t(qrtebd_mps* s, int m, const qrtebd_trunc* tr, cudaStream_t st,
   QR_TRY(bond_update(&io, &t, st, &info, nullptr, /*sync_chi=*/false));
   if (t.scheme == QRTEBD_CBE) {
     s->chi_pending[bmid] = 1;
+    s->xi_lower[bmid] = 0;
     k_diag_of<T><<<(unsigned)ceil_div(s->cap[bmid], 128), 128, 0, st>>>(
         static_cast<cx<T>*>(s->Xi[bmid]), s->stats + 4 * (size_t)m, s->cap[bmid],
         static_cast<cx<T>*>(s->xiv[bmid]));
@@ -193,6 +195,7 @@ int update_bond_t(qrtebd_mps* s, int m, const qrtebd_trunc* tr, cudaStream_t st,
   } else {
     s->chi[bmid] = info.chi_new;
     s->xi_diag[bmid] = 0;
+    s->xi_lower[bmid] = 1;  // Xi~ = L / ||L||
   }
   k_acc_eps<<<1, 1, 0, st>>>(s->stats + 4 * (size_t)m, s->eps_acc + bmid, s->layer_eps + m);
   note_launch();
@@ -367,7 +370,7 @@ int mps_bond_ws_need(const qrtebd_mps* s, int m, const qrtebd_trunc* tr, size_t*
   std::memset(&io, 0, sizeof io);
   io.precision = s->precision;
   io.chi_l = s->chi[bl]; io.d = s->d; io.chi_m = s->chi[bmid]; io.chi_r = s->chi[br];
-  io.xi_kind = s->xi_diag[bl] ? 2 : 1;
+  io.xi_kind = s->xi_diag[bl] ? 2 : (s->xi_lower[bl] ? 3 : 1);
   static const char dummy = 0;
   io.bm = &dummy;
   qrtebd_trunc t = *tr;

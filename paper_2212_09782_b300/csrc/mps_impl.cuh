@@ -13,6 +13,9 @@ struct qrtebd_mps {
   std::vector<void*> Xi;          // per bond, dense cap x cap
   std::vector<void*> xiv;         // per bond, diagonal vector (valid if xi_diag)
   std::vector<char> xi_diag;
+  // per bond: Xi is lower triangular with its zeros stored (the L / ||L|| of a plain update),
+  // so the product Xi theta~' skips the blocks above the diagonal; not saved in checkpoints
+  std::vector<char> xi_lower;
   std::vector<char> chi_pending;  // CBE cut of this bond still on the device (stats slot of its gate)
   double* eps_acc = nullptr;      // per bond, device
   double* stats = nullptr;        // device double[4 * ngates]: one slot per gate bond

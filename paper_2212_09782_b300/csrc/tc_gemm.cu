@@ -181,9 +181,13 @@ template <bool THREE, int BN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_tc_gemm(const __grid_constant__ CUtensorMap tA_hi, const __grid_constant__ CUtensorMap tA_lo,
               const __grid_constant__ CUtensorMap tB_hi, const __grid_constant__ CUtensorMap tB_lo,
-              Epi epi, int Kp, int kt_per_split, float* partial, int m_off, unsigned* err) {
+              Epi epi, int Kp, int kt_per_split, float* partial, int m_off, unsigned* err,
+              int ktri) {
   // m_off: first row of this launch's tiles in A; the epilogue's rows (and epi) are
-  // relative to it
+  // relative to it. ktri: the product's operands are triangular, so a tile's K loop ends
+  // early: 1 = A' lower triangular (real K below 2 (last row of the tile + 1)), 2 = B'^T
+  // upper triangular along K (real K below the tile's last real column + 1); 0 = full K.
+  // The K-tiles skipped hold only zeros of the triangular operand.
   using C = Cfg<THREE, BN>;
   constexpr int B_TILE = C::B_TILE, TMEM_COLS = C::TMEM_COLS;
   static_assert(BM * (BN + 4) * 4 <= C::STAGES * C::STAGE_BYTES, "staged epilogue tile");
@@ -201,7 +205,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
-  const int nk_all = (Kp + BK - 1) / BK;
+  int kreal = Kp;
+  if (ktri == 1) kreal = min(Kp, 2 * (m_off + m0 + BM));
+  else if (ktri == 2) kreal = min(Kp, n0 + BN);
+  const int nk_all = (kreal + BK - 1) / BK;
   const int kt0 = blockIdx.z * kt_per_split;
   const int kt1 = min(nk_all, kt0 + kt_per_split);
   const int nk = max(0, kt1 - kt0);
@@ -1416,10 +1423,10 @@ template <bool THREE, int BN> int set_attrs_once() {
 template <bool THREE, int BN>
 int launch_tc(dim3 grid, cudaStream_t st, const CUtensorMap& a_hi, const CUtensorMap& a_lo,
               const CUtensorMap& b_hi, const CUtensorMap& b_lo, const Epi& e, int Kp, int per,
-              float* part, int m_off, unsigned* err) {
+              float* part, int m_off, unsigned* err, int ktri) {
   QR_TRY((set_attrs_once<THREE, BN>()));
   QR_CUDA_TRY(launch_pdl(k_tc_gemm<THREE, BN>, grid, dim3(NTHREADS), Cfg<THREE, BN>::SMEM, st, a_hi,
-                         a_lo, b_hi, b_lo, e, Kp, per, part, m_off, err));
+                         a_lo, b_hi, b_lo, e, Kp, per, part, m_off, err, ktri));
   return QRTEBD_OK;
 }
 
@@ -1513,6 +1520,9 @@ int tc_gemm_cfg(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStrea
   // smaller one
   GemmArgs<float> g = g0;
   bool cacheable = g0.reuse_a;
+  // a lower-triangular A limits each tile row's K; after the swap below it is the B
+  // operand (upper triangular along K), which limits each tile column's K
+  int ktri = g0.tri_a ? (g0.N > g0.M ? 2 : 1) : 0;
   if (g0.N > g0.M) {
     cacheable = false;
     g.M = g0.N; g.N = g0.M;
@@ -1622,13 +1632,13 @@ int tc_gemm_cfg(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStrea
         if (three) QR_TRY((launch_fz<true, 128>(grid, st, ra, rb, e, per, part, m_off, err)));
         else QR_TRY((launch_fz<false, 128>(grid, st, ra, rb, e, per, part, m_off, err)));
       } else if (three && bn == 256)
-        QR_TRY((launch_tc<true, 256>(grid, st, ta_hi, ta_lo, tb_hi, tb_lo, e, 2 * K, per, part, m_off, err)));
+        QR_TRY((launch_tc<true, 256>(grid, st, ta_hi, ta_lo, tb_hi, tb_lo, e, 2 * K, per, part, m_off, err, ktri)));
       else if (three)
-        QR_TRY((launch_tc<true, 128>(grid, st, ta_hi, ta_lo, tb_hi, tb_lo, e, 2 * K, per, part, m_off, err)));
+        QR_TRY((launch_tc<true, 128>(grid, st, ta_hi, ta_lo, tb_hi, tb_lo, e, 2 * K, per, part, m_off, err, ktri)));
       else if (bn == 256)
-        QR_TRY((launch_tc<false, 256>(grid, st, ta_hi, ta_lo, tb_hi, tb_lo, e, 2 * K, per, part, m_off, err)));
+        QR_TRY((launch_tc<false, 256>(grid, st, ta_hi, ta_lo, tb_hi, tb_lo, e, 2 * K, per, part, m_off, err, ktri)));
       else
-        QR_TRY((launch_tc<false, 128>(grid, st, ta_hi, ta_lo, tb_hi, tb_lo, e, 2 * K, per, part, m_off, err)));
+        QR_TRY((launch_tc<false, 128>(grid, st, ta_hi, ta_lo, tb_hi, tb_lo, e, 2 * K, per, part, m_off, err, ktri)));
       note_launch();
       QR_CUDA_TRY(cudaGetLastError());
     }

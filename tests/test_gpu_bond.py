@@ -350,3 +350,27 @@ def test_emulated_fp64_bond_against_oracle(scheme):
 def test_c2_full_size_c128_oz_against_oracle():
     """The bench workload with FP64 emulated on the tensor cores, at the 1e-10 bar."""
     _c2_full_size("c128_oz", 1e-10)
+
+
+@pytest.mark.parametrize("prec", ["c64_3xtf32", "c64_tf32"])
+@pytest.mark.parametrize("dims", [(256, 3, 200, 256), (144, 3, 48, 16)])
+def test_lower_triangular_xi(prec, dims):
+    # xi_kind 3: a lower-triangular Xi (the L / ||L|| a plain update leaves on its bond). The
+    # product Xi theta~' then stops each tensor-core tile's K loop after the tile's last row
+    # (144 x 144 output, chi_l = d^2 chi_r: no swap) or, after the library's N > M swap,
+    # after the tile's last column (256 x 2304). The K-tiles skipped hold only zeros of Xi, so the update matches
+    # the dense product's to rounding, and the oracle
+    bd = _case(dims, seed=sum(dims) + 3, xi="dense", prec=prec)
+    Xi = np.tril(bd["Xi"])
+    Xi = Xi / np.linalg.norm(Xi)
+    chiM = dims[2]
+    from paper_2212_09782_b300 import lib as L
+    t = L.trunc_default(L.PLAIN, chiM)
+    dense = run_gpu(prec, Xi, bd["Bm"], bd["Bn"], bd["U"], t, xi_kind=1)
+    lower = run_gpu(prec, Xi, bd["Bm"], bd["Bn"], bd["U"], t, xi_kind=3)
+    for k in ("Bm_new", "Xi_new", "Bn_new"):
+        a, b = lower[k], dense[k]
+        assert np.abs(a - b).max() <= 1e-6 * np.abs(b).max(), k
+    assert abs(lower["eps"] - dense["eps"]) <= 1e-6 * max(dense["eps"], 1e-12)
+    orc = bond.qr_update(Xi, bd["Bm"], bd["Bn"], bd["U"], scheme="plain", chi_max=chiM)
+    compare(lower, orc, TOL[prec])
