@@ -25,6 +25,9 @@ template <typename T> struct GemmArgs {
   // tensor-core path only: A is lower triangular (A[m][k] = 0 for k > m, zeros stored), so
   // a tile of rows may stop its K loop after its last row; other paths read the zeros
   bool tri_a = false;
+  // tensor-core path only: B is upper triangular (B[k][n] = 0 for k > n, zeros stored), so
+  // a tile of columns may stop its K loop after its last column
+  bool tri_b = false;
 };
 
 // Enqueue the GEMM. `scratch` (may be null) lets the launcher split K for

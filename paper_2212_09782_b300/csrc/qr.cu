@@ -2045,9 +2045,14 @@ int householder_qr(cx<T>* A, long long lda, int m, int n, cx<T>* Q, long long ld
   const int npo = qfast ? 0 : (int)ceil_div(n, nbo);
   if (qfast) {
     // Wq = T_all V_top^dag (V_top: the first n rows of V), then Q = [I; 0] - V Wq
+    // V_top is unit lower triangular and T_all upper triangular (zeros stored in both), so
+    // V_top^dag and Wq are upper triangular: both products stop each tile column's K loop
+    // at its last column (the K-tiles skipped hold only zeros of the triangular factor)
     GemmArgs<T> gw{n, n, n, s.Tall, n, 1, false, s.V, 1, ldv, true, s.Wq, n, 1, one, zero};
+    gw.tri_b = true;
     QR_TRY(run_gemm<T>(gw, s, st, gm));
     GemmArgs<T> gq{m, n, n, s.V, ldv, 1, false, s.Wq, n, 1, false, Q, ldq, 1, mone, zero};
+    gq.tri_b = true;
     QR_TRY(run_gemm<T>(gq, s, st, gm));
     QR_CUDA_TRY(launch_pdl(k_add_eye<T>, dim3((unsigned)ceil_div(n, 256)), dim3(256), 0, st, Q, ldq, n));
     note_launch();

@@ -1520,9 +1520,10 @@ int tc_gemm_cfg(const GemmArgs<float>& g0, bool three, TcWorkspace& w, cudaStrea
   // smaller one
   GemmArgs<float> g = g0;
   bool cacheable = g0.reuse_a;
-  // a lower-triangular A limits each tile row's K; after the swap below it is the B
-  // operand (upper triangular along K), which limits each tile column's K
-  int ktri = g0.tri_a ? (g0.N > g0.M ? 2 : 1) : 0;
+  // a lower-triangular A limits each tile row's K, an upper-triangular B each tile column's;
+  // the swap below exchanges the two
+  const bool swap = g0.N > g0.M;
+  const int ktri = g0.tri_a ? (swap ? 2 : 1) : g0.tri_b ? (swap ? 1 : 2) : 0;
   if (g0.N > g0.M) {
     cacheable = false;
     g.M = g0.N; g.N = g0.M;
