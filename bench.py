@@ -560,8 +560,21 @@ def run_chain(args):
         # every distinct bond shape of the chain (dense Xi after the first update, theta formed)
         shapes = sorted({(dims[m], d, dims[m + 1], dims[m + 2]) for m in range(Lc - 1)})
         tune = autotune_shapes(L, L.PRECISIONS[args.precision], shapes, tr, xi_kind=1, theta_given=False)
-    step = (lambda: L.tebd_step(s, gh, gf, tr)) if args.no_batch else \
-        (lambda: L.tebd_step_batched([s], [gh], [gf], tr))
+    # a Strang step layer by layer (the library's tebd_step / tebd_step_batched), each layer
+    # between two events on the state's stream (torch's current stream) when `lay` is given
+    def step(lay=None):
+        for p, gates in ((0, gh), (1, gf), (0, gh)):
+            a = torch.cuda.Event(enable_timing=True) if lay is not None else None
+            if a is not None:
+                a.record()
+            if args.no_batch:
+                s.apply_layer(p, gates, tr)
+            else:
+                L.apply_layer_batched([s], p, [gates], tr)
+            if a is not None:
+                e = torch.cuda.Event(enable_timing=True)
+                e.record()
+                lay.append((p, a, e))
     for _ in range(args.warmup):
         step()
     s.sync()
@@ -569,10 +582,11 @@ def run_chain(args):
     n0 = L.launch_count()
     t0 = time.perf_counter()
     ev = []
+    lay = []
     for _ in range(args.steps):
         a = torch.cuda.Event(enable_timing=True)
         a.record()
-        step()
+        step(lay)
         ev.append(a)
     b = torch.cuda.Event(enable_timing=True)
     b.record()
@@ -582,12 +596,18 @@ def run_chain(args):
     ms = ev[0].elapsed_time(b)
     per_step = [ev[i].elapsed_time(ev[i + 1] if i + 1 < len(ev) else b) for i in range(len(ev))]
     nupd = sum(len(range(p, Lc - 1, 2)) for p in (0, 1, 0))
+    # per-layer latency: even layers (64 bonds at L = 128) and odd layers (63 bonds)
+    lay_ms = {p: [a.elapsed_time(e) for q, a, e in lay if q == p] for p in (0, 1)}
+    layer_latency = {("even" if p == 0 else "odd"): {
+        "bonds": len(range(p, Lc - 1, 2)), "p50_ms": statistics.median(v),
+        "p99_ms": float(np.percentile(v, 99)), "layers": len(v)} for p, v in lay_ms.items() if v}
     line = {
         "metric": "TEBD bond updates/s, finite chain L=128 d=4 chi<=512 (batched layers)",
         "value": args.steps * nupd / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "p50_ms": statistics.median(per_step), "p99_ms": float(np.percentile(per_step, 99)),
-        "host_wall_s": wall, "updates_per_step": nupd, "gpu_launches": L.launch_count() - n0,
+        "host_wall_s": wall, "updates_per_step": nupd, "layer_latency": layer_latency,
+        "gpu_launches": L.launch_count() - n0,
         "dtype": args.precision, "data": "synthetic",
         "config": {"workload": f"finite chain L={Lc} d=4 chi<={chi} plain, Strang step",
                    "batched": not args.no_batch},
