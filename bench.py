@@ -81,7 +81,7 @@ def family_roofline(L, fam, ms, n, flops, nbytes, prec, peaks, src):
         peak = peaks.get("hbm_gbs", PEAKS_FALLBACK["hbm_gbs"])
         out.update({"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak, "peak_source": f"{src} copy bandwidth",
-                    "kernel": "k_prep_a / k_prep_b" if fam == L.PROF_PREP else "k_gate",
+                    "kernel": "k_prep (A' and B'^T, one launch)" if fam == L.PROF_PREP else "k_gate",
                     "algorithmic_bytes_per_launch": nbytes / n})
     else:
         achieved = flops / n / sec / 1e12
