@@ -100,3 +100,21 @@ def test_sweeps_out_of_range_is_refused(L):
         assert st == L.ERR_INVALID_ARG
     t = L.trunc_default(L.PLAIN, 8)
     assert t.sweeps == 1
+
+
+def test_xi_kinds_on_the_host(L):
+    # xi_kind 3 (a lower-triangular Xi with its zeros stored) takes the dense kind's workspace;
+    # kinds outside 0..3 are refused before any device work
+    t = L.trunc_default(L.PLAIN, 40)
+    for prec in ("c128", "c64_3xtf32"):
+        p = L.PRECISIONS[prec]
+        dense = L.bond_workspace_size(p, 40, 3, 40, 40, t, xi_kind=1)
+        assert L.bond_workspace_size(p, 40, 3, 40, 40, t, xi_kind=3) == dense
+    nb = C.c_size_t(0)
+    for k in (-1, 4):
+        st = L.raw().qrtebd_bond_workspace_size(L.C64_3XTF32, 40, 3, 40, 40, k, 0, C.byref(t), C.byref(nb))
+        assert st == L.ERR_INVALID_ARG
+    io = _io(L, L.C64_3XTF32, 40, 3, 40, 40, 1 << 30)
+    io.xi_kind = 4
+    info = L.BondInfo()
+    assert L.raw().qrtebd_bond_update(C.byref(io), C.byref(t), None, C.byref(info)) == L.ERR_INVALID_ARG
